@@ -1,0 +1,366 @@
+"""Plain FP64 CPU oracle of phaseless AFQMC with a stochastically sampled trial.
+
+ORACLE / TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this
+module; only tests, the smoke check and the CPU-baseline leg of the benchmark
+may.  It shares no code with the CUDA path: the two meet only through the
+seeded inputs of ``afqmc_inputs`` and the published Philox definition, which
+each side implements on its own.
+
+It is written for a reader checking it against the paper by eye: every step
+follows the paper's order and notation, uses numpy library routines (matmul,
+slogdet, inv, eigh, qr, einsum) as single steps, and does no blocking, fusion or
+reordering.  Notation: N orbitals, n_up/n_dn electrons, Gamma Cholesky vectors
+L_g, K hidden variables, W walkers, P paths (trial samples) per walker, tau the
+time step.  A "pair" is one (walker, path).
+
+Readings of points where the paper is silent or ambiguous (R1-R14):
+  R1  H = sum_ij h_ij c+_i c_j + 1/2 sum_ijkl V_ijkl c+_i c+_k c_l c_j with
+      V_ijkl = sum_g L_g,ij L_g,kl; so H = T + 1/2 sum_g L_g^2 (Eq. (3)) with
+      T = h - 1/2 sum_g L_g L_g.
+  R3  force bias xbar_g = -i sqrt(tau) <L_g> (the sqrt(-tau) of Eq. (4) carried
+      into Eq. (15)); no mean-field subtraction.
+  R4  the mixed estimate reports Re of the walker-averaged local energy.
+  R5  weight update variants: combined angle (default), separate cosines,
+      half-plane hand-off.
+  R6  exp(A) of the auxiliary-field propagator = Taylor series to 6th order
+      applied to the orbitals; exp(-tau T/2) and exp(sum_k x_k U_k) exact.
+  R7  Metropolis accepts iff u < alpha with u in [0, 1) (53-bit).
+  R8  proposals: independent draws from the prior p_T (the paper's choice),
+      or preconditioned Crank-Nicolson x' = sqrt(1-beta^2) x + beta xi.
+  R9  walkers are re-orthonormalised every step (QR, diag(R) > 0).
+  R10 no population control; weights carried, optional constant E_T.
+  R11 initial walkers phi_w = Phi(x_w), x_w ~ p; paths x_wp ~ p; W = 1;
+      n_burn Metropolis sweeps at fixed phi before the first step.
+  R14 the local energy is measured every step at the start of the step.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import philox as px
+
+__all__ = ["OracleConfig", "Hamiltonian", "State", "prepare", "trial_orbitals", "log_overlap",
+           "green", "local_energy_force_bias", "measure", "init", "step", "reorthonormalise",
+           "propagate_walker", "mcmc_sweep", "CONSTRAINTS"]
+
+CONSTRAINTS = ("combined", "separate", "half_plane")
+
+
+@dataclasses.dataclass
+class OracleConfig:
+    dtau: float
+    n_walkers: int
+    n_paths: int
+    seed: int
+    n_sweeps: int = 1            # Metropolis sweeps M per step
+    n_burn: int = 20             # sweeps before the first step (R11)
+    constraint: str = "combined"
+    proposal: str = "prior"      # "prior" or "pcn"
+    pcn_beta: float = 1.0
+    e_shift: float = 0.0         # constant E_T, weights *= exp(tau E_T) per step
+    taylor_order: int = 6
+    kill_threshold: float = 1e-10  # |sum_p S_p| below this kills the walker
+
+
+@dataclasses.dataclass
+class Hamiltonian:
+    h: np.ndarray          # (N, N)
+    L: np.ndarray          # (G, N, N)
+    Phi0: np.ndarray       # (N, n_up)
+    U: np.ndarray          # (K, N, N)
+    n_up: int
+    n_dn: int
+    T: np.ndarray          # h - 1/2 sum_g L_g L_g
+    expT_half: np.ndarray  # exp(-tau T / 2)
+
+
+@dataclasses.dataclass
+class State:
+    step: int
+    phi_up: np.ndarray     # (W, N, n_up) complex128
+    phi_dn: np.ndarray     # (W, N, n_dn) complex128
+    weight: np.ndarray     # (W,) float64
+    x: np.ndarray          # (W, P, K) float64 hidden variables of each path
+    Phi: np.ndarray        # (W, P, N, n_up) float64, Phi(x); spin down uses the first n_dn columns
+
+    def copy(self) -> "State":
+        return State(self.step, self.phi_up.copy(), self.phi_dn.copy(), self.weight.copy(),
+                     self.x.copy(), self.Phi.copy())
+
+
+# ---------------------------------------------------------------------------
+# Hamiltonian and trial (Sec. II A, Eq. (1)-(5); Sec. II C, Eq. (20)-(21))
+# ---------------------------------------------------------------------------
+
+def _expm_sym(A: np.ndarray) -> np.ndarray:
+    """exp of a real symmetric matrix (batched) through its eigendecomposition."""
+    lam, V = np.linalg.eigh(A)
+    return (V * np.exp(lam)[..., None, :]) @ np.swapaxes(V, -1, -2)
+
+
+def prepare(h, L, Phi0, U, n_up: int, n_dn: int, dtau: float) -> Hamiltonian:
+    """One-body operator of the Monte Carlo form, Eq. (3) with reading R1, and
+    the exact half-step kinetic propagator exp(-tau T/2) of Eq. (5)."""
+    h = np.asarray(h, dtype=np.float64)
+    L = np.asarray(L, dtype=np.float64)
+    T = h - 0.5 * np.einsum("gij,gjk->ik", L, L)
+    return Hamiltonian(h, L, np.asarray(Phi0, dtype=np.float64), np.asarray(U, dtype=np.float64),
+                       n_up, n_dn, T, _expm_sym(-0.5 * dtau * T))
+
+
+def trial_orbitals(ham: Hamiltonian, x: np.ndarray) -> np.ndarray:
+    """Phi(x) = exp(sum_k x_k U_k) Phi0, the determinant of one hidden-variable
+    sample of the trial, Eq. (20)-(21) with one slice; x has shape (..., K)."""
+    S = np.einsum("...k,kij->...ij", x, ham.U)
+    return _expm_sym(S) @ ham.Phi0
+
+
+# ---------------------------------------------------------------------------
+# Overlaps, mixed Green's function, local energy and force bias
+# ---------------------------------------------------------------------------
+
+def _slog(A: np.ndarray) -> np.ndarray:
+    """log det A as a complex number: log|det A| + i Arg det A."""
+    if A.shape[-1] == 0:
+        return np.zeros(A.shape[:-2], dtype=np.complex128)
+    sign, logabs = np.linalg.slogdet(A)
+    return logabs + 1j * np.angle(sign)
+
+
+def log_overlap(ham: Hamiltonian, Phi: np.ndarray, phi_up: np.ndarray, phi_dn: np.ndarray) -> np.ndarray:
+    """log <Phi|phi> = sum over spins of log det(Phi_s^T phi_s) (Eq. (25), (26));
+    Phi is real so Phi^dagger = Phi^T.  Shapes broadcast over leading axes."""
+    Pu = Phi
+    Pd = Phi[..., : ham.n_dn]
+    return _slog(np.swapaxes(Pu, -1, -2) @ phi_up) + _slog(np.swapaxes(Pd, -1, -2) @ phi_dn)
+
+
+def green(Phi_s: np.ndarray, phi_s: np.ndarray) -> np.ndarray:
+    """Mixed one-body Green's function of one spin, G_ij = <Phi|c+_i c_j|phi>/<Phi|phi>
+    = [phi (Phi^T phi)^-1 Phi^T]_ji."""
+    A = np.swapaxes(Phi_s, -1, -2) @ phi_s
+    M = phi_s @ np.linalg.inv(A) @ np.swapaxes(Phi_s, -1, -2)
+    return np.swapaxes(M, -1, -2)
+
+
+def local_energy_force_bias(ham: Hamiltonian, Phi: np.ndarray, phi_up: np.ndarray, phi_dn: np.ndarray):
+    """Local energy E_L = <Phi|H|phi>/<Phi|phi> and the local values
+    v_g = <Phi|L_g|phi>/<Phi|phi> of every Cholesky vector, for one pair.
+
+    By Wick's theorem with G^s_ij = <c+_i c_j>:
+      E_L = sum_s sum_ij h_ij G^s_ij
+          + 1/2 sum_ijkl V_ijkl [ sum_st G^s_ij G^t_kl - sum_s G^s_il G^s_kj ],
+    with V_ijkl = sum_g L_g,ij L_g,kl (reading R1).  v_g = sum_s sum_ij L_g,ij G^s_ij
+    is the local value of L_g used by the force bias, Eq. (15).
+    """
+    Gs = [green(Phi, phi_up)]
+    if ham.n_dn > 0:
+        Gs.append(green(Phi[:, : ham.n_dn], phi_dn))
+    L = ham.L
+    e1 = sum(np.einsum("ij,ij->", ham.h, G) for G in Gs)
+    v = sum(np.einsum("gij,ij->g", L, G) for G in Gs)
+    coul = 0.5 * np.sum(v * v)
+    exch = 0.0
+    for G in Gs:
+        exch = exch + 0.5 * np.einsum("gij,gkl,il,kj->", L, L, G, G, optimize=True)
+    return e1 + coul - exch, v
+
+
+def measure(ham: Hamiltonian, st: State):
+    """Per-pair log-overlaps, local energies and force-bias values at the
+    current walkers, and their path-sign-weighted averages over each walker's
+    paths (Eq. (26)-(27))."""
+    W, P = st.x.shape[:2]
+    G = ham.L.shape[0]
+    logov = np.empty((W, P), dtype=np.complex128)
+    e_pair = np.empty((W, P), dtype=np.complex128)
+    v_pair = np.empty((W, P, G), dtype=np.complex128)
+    for w in range(W):
+        for p in range(P):
+            logov[w, p] = log_overlap(ham, st.Phi[w, p], st.phi_up[w], st.phi_dn[w])
+            e_pair[w, p], v_pair[w, p] = local_energy_force_bias(ham, st.Phi[w, p], st.phi_up[w], st.phi_dn[w])
+    S = np.exp(1j * logov.imag)                 # Eq. (26): phase of each path's overlap
+    sumS = S.sum(axis=1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        e_bar = (S * e_pair).sum(axis=1) / sumS  # Eq. (27) with O = H
+        v_bar = (S[:, :, None] * v_pair).sum(axis=1) / sumS[:, None]  # Eq. (27) with O = L_g
+    return dict(logov=logov, e_pair=e_pair, v_pair=v_pair, S=S, sumS=sumS, e_bar=e_bar, v_bar=v_bar)
+
+
+def mixed_energy(weight: np.ndarray, e_bar: np.ndarray):
+    """Mixed estimator, Eq. (16), real part (R4); walkers with W = 0 do not enter."""
+    alive = weight > 0
+    num = float(np.sum(weight[alive] * e_bar[alive].real))
+    den = float(np.sum(weight[alive]))
+    return num, den
+
+
+# ---------------------------------------------------------------------------
+# Propagation (Eq. (5), (12)-(15)), Metropolis on the paths (Eq. (23)), reorthonormalisation
+# ---------------------------------------------------------------------------
+
+def propagate_walker(ham: Hamiltonian, phi: np.ndarray, y: np.ndarray, dtau: float, order: int) -> np.ndarray:
+    """phi' = exp(-tau T/2) exp(i sqrt(tau) sum_g y_g L_g) exp(-tau T/2) phi,
+    i.e. B(x - xbar) of Eq. (5) and (12) with y = x - xbar; the middle exponential is its
+    Taylor series to ``order`` (R6)."""
+    A = 1j * math.sqrt(dtau) * np.einsum("g,gij->ij", y, ham.L)
+    psi = ham.expT_half @ phi
+    term = psi
+    acc = psi.copy()
+    for m in range(1, order + 1):
+        term = (A @ term) / m
+        acc = acc + term
+    return ham.expT_half @ acc
+
+
+def reorthonormalise(phi: np.ndarray) -> np.ndarray:
+    """phi = Q R with diag(R) real positive; return Q (R9).  The determinant
+    ratios and Green's functions are unchanged because phi -> phi R^-1 only
+    rescales every overlap by the same det R."""
+    if phi.shape[-1] == 0:
+        return phi.copy()
+    Q, R = np.linalg.qr(phi)
+    d = np.diagonal(R, axis1=-2, axis2=-1)
+    return Q * (d / np.abs(d))[..., None, :]
+
+
+def mcmc_sweep(ham: Hamiltonian, cfg: OracleConfig, st: State, logov_cur: np.ndarray, alive: np.ndarray,
+               step: int, sweep: int, tag_prop: int, tag_acc: int) -> int:
+    """One Metropolis update of every path of every live walker against the
+    walkers' current orbitals (leapfrog step 2, Sec. III A; Appendix B.2):
+    propose x' (from the prior p_T, or pCN), build Phi(x'), accept iff
+    u < |<Phi(x')|phi>| / |<Phi(x)|phi>|.  Updates st.x, st.Phi and logov_cur in
+    place; returns the number of accepted moves."""
+    W, P, K = st.x.shape
+    pair_ids = np.arange(W * P)
+    xi = px.normals(cfg.seed, tag_prop, step, pair_ids, sweep, K).reshape(W, P, K)
+    u = px.uniforms(cfg.seed, tag_acc, step, pair_ids, sweep, 1).reshape(W, P)
+    if cfg.proposal == "prior":
+        x_new = xi
+    elif cfg.proposal == "pcn":
+        b = cfg.pcn_beta
+        x_new = math.sqrt(1.0 - b * b) * st.x + b * xi
+    else:
+        raise ValueError(cfg.proposal)
+    n_acc = 0
+    for w in range(W):
+        if not alive[w]:
+            continue
+        for p in range(P):
+            Phi_new = trial_orbitals(ham, x_new[w, p])
+            lo_new = log_overlap(ham, Phi_new, st.phi_up[w], st.phi_dn[w])
+            delta = lo_new.real - logov_cur[w, p].real
+            if delta >= 0.0 or u[w, p] < math.exp(delta):
+                st.x[w, p] = x_new[w, p]
+                st.Phi[w, p] = Phi_new
+                logov_cur[w, p] = lo_new
+                n_acc += 1
+    return n_acc
+
+
+def init(ham: Hamiltonian, cfg: OracleConfig) -> State:
+    """Initial composite walkers (reading R11 of Appendix B.1)."""
+    W, P = cfg.n_walkers, cfg.n_paths
+    K = ham.U.shape[0]
+    xw = px.normals(cfg.seed, px.TAG_INIT_WALKER, 0, np.arange(W), 0, K)
+    Phiw = trial_orbitals(ham, xw)                                   # (W, N, n_up)
+    phi_up = reorthonormalise(Phiw.astype(np.complex128))
+    phi_dn = reorthonormalise(Phiw[:, :, : ham.n_dn].astype(np.complex128))
+    x = px.normals(cfg.seed, px.TAG_INIT_PATH, 0, np.arange(W * P), 0, K).reshape(W, P, K)
+    Phi = trial_orbitals(ham, x)
+    st = State(0, phi_up, phi_dn, np.ones(W), x, Phi)
+    logov = np.empty((W, P), dtype=np.complex128)
+    for w in range(W):
+        for p in range(P):
+            logov[w, p] = log_overlap(ham, Phi[w, p], phi_up[w], phi_dn[w])
+    alive = np.ones(W, dtype=bool)
+    for b in range(cfg.n_burn):
+        mcmc_sweep(ham, cfg, st, logov, alive, 0, b, px.TAG_BURN_PROPOSE, px.TAG_BURN_ACCEPT)
+    return st
+
+
+def _wrap(a):
+    return np.angle(np.exp(1j * a))
+
+
+def step(ham: Hamiltonian, cfg: OracleConfig, st: State):
+    """One leapfrog step (Sec. III A and the propagation outline of Appendix B.2).
+
+    Returns the new state and a dict of diagnostics; ``mixed`` holds the mixed
+    energy numerator and denominator measured at the start of the step (R14).
+    """
+    i = st.step
+    W, P, K = st.x.shape
+    G = ham.L.shape[0]
+    tau = cfg.dtau
+    new = st.copy()
+
+    # Local energies, force-bias values and path signs at phi (Eq. (26)-(27)).
+    m = measure(ham, st)
+    mixed = mixed_energy(st.weight, m["e_bar"])
+    alive = (st.weight > 0) & (np.abs(m["sumS"]) > cfg.kill_threshold)
+    new.weight[~alive] = 0.0
+
+    # Leapfrog step 1: fields, force bias (Eq. (15)), propagation (Eq. (12)).
+    xi = px.normals(cfg.seed, px.TAG_FIELD, i, np.arange(W), 0, G)
+    xbar = -1j * math.sqrt(tau) * m["v_bar"]
+    y = xi - xbar
+    logov_new = m["logov"].copy()
+    ratio = np.ones(W, dtype=np.complex128)
+    old_sum = np.zeros(W, dtype=np.complex128)
+    I_abs = np.zeros(W)
+    I_full = np.zeros(W, dtype=np.complex128)
+    for w in range(W):
+        if not alive[w]:
+            continue
+        new.phi_up[w] = propagate_walker(ham, st.phi_up[w], y[w], tau, cfg.taylor_order)
+        new.phi_dn[w] = propagate_walker(ham, st.phi_dn[w], y[w], tau, cfg.taylor_order)
+        for p in range(P):
+            logov_new[w, p] = log_overlap(ham, st.Phi[w, p], new.phi_up[w], new.phi_dn[w])
+        # Overlap ratio estimated with the sampled trial, Eq. (25).
+        terms = m["S"][w] * np.exp(logov_new[w] - m["logov"][w])
+        old_sum[w] = terms.sum()
+        ratio[w] = old_sum[w] / m["sumS"][w]
+        # Importance function Eq. (14): p(x - xbar)/p(x) times the ratio.
+        log_shift = np.sum(xi[w] * xbar[w] - 0.5 * xbar[w] * xbar[w])
+        I_full[w] = np.exp(log_shift) * ratio[w]
+        I_abs[w] = abs(I_full[w])
+
+    # Leapfrog step 2: Metropolis update of the paths at phi' (Sec. III A).
+    n_acc = 0
+    for s in range(cfg.n_sweeps):
+        n_acc += mcmc_sweep(ham, cfg, new, logov_new, alive, i, s, px.TAG_PROPOSE, px.TAG_ACCEPT)
+
+    # Hand-off ratio Eq. (28) and the constraints Eq. (17), (29).
+    for w in range(W):
+        if not alive[w]:
+            continue
+        S_new = np.exp(1j * logov_new[w].imag)
+        dtheta = np.angle(ratio[w])
+        dtheta_T = np.angle(S_new.sum()) - np.angle(old_sum[w])
+        if cfg.constraint == "combined":
+            f = max(0.0, math.cos(dtheta + dtheta_T))
+        elif cfg.constraint == "separate":
+            f = max(0.0, math.cos(dtheta)) * max(0.0, math.cos(dtheta_T))
+        elif cfg.constraint == "half_plane":
+            f = max(0.0, math.cos(dtheta)) * (1.0 if abs(_wrap(dtheta_T)) <= 0.5 * math.pi else 0.0)
+        else:
+            raise ValueError(cfg.constraint)
+        wnew = st.weight[w] * I_abs[w] * f * math.exp(tau * cfg.e_shift)
+        new.weight[w] = wnew if math.isfinite(wnew) else 0.0
+
+    # Reorthonormalise the propagated walkers (R9).
+    for w in range(W):
+        if alive[w]:
+            new.phi_up[w] = reorthonormalise(new.phi_up[w])
+            new.phi_dn[w] = reorthonormalise(new.phi_dn[w])
+    new.step = i + 1
+    diag = dict(mixed=mixed, n_accept=n_acc, n_proposed=int(alive.sum()) * P * cfg.n_sweeps,
+                alive=alive, e_bar=m["e_bar"], v_bar=m["v_bar"], ratio=ratio, measure=m,
+                old_sum=old_sum, new_sum=np.exp(1j * logov_new.imag).sum(axis=1), logov_new=logov_new,
+                xi=xi, I_abs=I_abs, I=I_full)
+    return new, diag
