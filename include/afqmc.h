@@ -1,0 +1,183 @@
+/*
+ * afqmc.h -- C ABI of the GB300 library for phaseless auxiliary-field quantum
+ * Monte Carlo with a stochastically sampled (hidden-variable) trial wave
+ * function (arXiv 2505.18519).
+ *
+ * The paper's method (Sec. III A, Appendix B.2): every random walker phi_w is
+ * tethered to P Metropolis paths x_wp over the trial's hidden variables; the
+ * trial sample of a path is the Slater determinant
+ *     Phi(x) = exp(sum_k x_k U_k) Phi0                      (Eq. (20)-(21), one slice)
+ * and one leapfrog step
+ *   (1) measures, for every pair (w, p), the overlap det(Phi^T phi), the mixed
+ *       Green's function, the force-bias values <L_g> and the local energy,
+ *       and averages them over the paths with the path signs S_p (Eq. (25)-(27));
+ *   (2) propagates phi_w by B(x - xbar) (Eq. (5), (12), (15)) and updates the
+ *       weight with the phaseless importance function (Eq. (14), (17));
+ *   (3) re-equilibrates the paths by Metropolis against the new walker
+ *       (Eq. (23)) and applies the hand-off constraint (Eq. (28)-(29));
+ *   (4) re-orthonormalises the walkers.
+ *
+ * Conventions for every entry point
+ *   - Arrays are row-major, FP64 (complex numbers as interleaved re, im pairs).
+ *   - "Host or device pointer": any pointer the CUDA runtime can copy from with
+ *     cudaMemcpyDefault (pageable or pinned host memory, or device memory).
+ *   - The caller owns every array it passes; the library copies what it needs
+ *     before the call returns and never keeps a caller pointer, except the
+ *     device workspace given to afqmc_init, which must stay allocated until
+ *     afqmc_destroy.
+ *   - The library never calls cudaMalloc/cudaFree: all device memory it uses
+ *     is the caller's workspace.  Host memory for the context is malloc'ed.
+ *   - Every call returns a status and never aborts the process.  Device-side
+ *     numerical problems (a singular overlap, a non-finite weight) set a
+ *     device status word that afqmc_energy and afqmc_stats report.
+ *   - Work is enqueued on the CUDA stream given at init; calls that return
+ *     values to the host synchronise that stream.
+ *   - Not thread-safe per context; distinct contexts are independent.
+ */
+#ifndef AFQMC_H
+#define AFQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afqmc_ctx afqmc_ctx;
+
+typedef enum {
+    AFQMC_OK = 0,
+    AFQMC_ERR_ARG = 1,        /* invalid argument, or a size this build does not support */
+    AFQMC_ERR_CUDA = 2,       /* a CUDA runtime call failed (the message says which) */
+    AFQMC_ERR_WORKSPACE = 3,  /* workspace missing, too small, or not 256-byte aligned */
+    AFQMC_ERR_NUMERIC = 4,    /* the device flagged a singular overlap or a non-finite value */
+    AFQMC_ERR_STATE = 5       /* a state buffer of the wrong size or shape */
+} afqmc_status;
+
+/* weight update of the hand-off (Sec. III A, Eq. (17), (29)) */
+enum {
+    AFQMC_CONSTRAINT_COMBINED = 0,   /* W *= |I| max(0, cos(dtheta + dtheta_T)) (default) */
+    AFQMC_CONSTRAINT_SEPARATE = 1,   /* W *= |I| max(0, cos dtheta) max(0, cos dtheta_T) */
+    AFQMC_CONSTRAINT_HALF_PLANE = 2  /* W *= |I| max(0, cos dtheta), and W = 0 if |dtheta_T| > pi/2 */
+};
+
+/* Metropolis proposal for the paths (Sec. III A; Appendix B.2) */
+enum {
+    AFQMC_PROPOSAL_PRIOR = 0,  /* independent draw x' ~ N(0, I) (the paper's sampler) */
+    AFQMC_PROPOSAL_PCN = 1     /* x' = sqrt(1 - beta^2) x + beta xi, xi ~ N(0, I) */
+};
+
+/* arithmetic of the two big contractions (R = Phi^T L_g and M = R Theta) */
+enum {
+    AFQMC_PRECISION_FP64 = 0   /* FP64 everywhere */
+};
+
+typedef struct {
+    int N;              /* orbitals (basis size) */
+    int n_up, n_dn;     /* electrons per spin; 0 <= n_dn <= n_up, n_up >= 1 */
+    int n_chol;         /* Cholesky vectors Gamma (Eq. (3)) */
+    int K;              /* hidden variables of the trial */
+    int n_walkers;      /* W */
+    int n_paths;        /* P, paths tethered to each walker */
+    int n_sweeps;       /* Metropolis sweeps M per step (>= 1) */
+    int n_burn;         /* Metropolis sweeps at fixed walkers during afqmc_init (>= 0) */
+    int constraint;     /* AFQMC_CONSTRAINT_* */
+    int proposal;       /* AFQMC_PROPOSAL_* */
+    int precision;      /* AFQMC_PRECISION_* */
+    int taylor_order;   /* order of the auxiliary-field propagator's Taylor series (6) */
+    int history_capacity; /* per-step energy records kept on the device (ring buffer, >= 1) */
+    double dtau;        /* imaginary time step tau > 0 */
+    double pcn_beta;    /* beta of the pCN proposal, 0 < beta <= 1 */
+    double e_shift;     /* constant E_T: every step multiplies weights by exp(tau E_T) */
+    double kill_threshold; /* a walker whose |sum_p S_p| is below this gets weight 0 */
+    uint64_t seed;      /* key of the Philox4x32-10 streams */
+} afqmc_config;
+
+/* Fill *cfg with defaults (combined constraint, prior proposal, FP64, Taylor
+ * order 6, one sweep, 20 burn-in sweeps, kill threshold 1e-10) and zero sizes. */
+void afqmc_config_default(afqmc_config* cfg);
+
+/* Bytes of device workspace the configuration needs (0 if cfg is invalid). */
+size_t afqmc_workspace_bytes(const afqmc_config* cfg);
+
+/* Create a context.
+ *   h     N*N          one-body matrix h_ij (symmetric)                 host or device
+ *   L     n_chol*N*N   Cholesky vectors L_g,ij (each symmetric), so that
+ *                      V_ijkl = sum_g L_g,ij L_g,kl (Eq. (1), (3))        host or device
+ *   Phi0  N*n_up       trial orbitals (spin down uses the first n_dn)    host or device
+ *   U     K*N*N        hidden-variable operators U_k (each symmetric)    host or device
+ *   workspace, workspace_bytes: device memory of at least
+ *                      afqmc_workspace_bytes(cfg) bytes, 256-byte aligned,
+ *                      owned by the caller, kept alive until afqmc_destroy
+ *   stream             cudaStream_t to run on (NULL = legacy default stream)
+ * It forms T = h - 1/2 sum_g L_g L_g and exp(-tau T/2), draws the initial
+ * walkers phi_w = orthonormalised Phi(x_w) and paths x_wp from the prior, sets
+ * W = 1, runs n_burn Metropolis sweeps, and synchronises the stream.
+ * The step counter starts at 0.  On error *out is NULL. */
+afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, const double* L,
+                        const double* Phi0, const double* U, void* workspace,
+                        size_t workspace_bytes, void* stream, afqmc_ctx** out);
+
+/* Enqueue n_steps leapfrog steps (asynchronous).  Each step first measures the
+ * walkers it starts from and appends {sum_w W_w Re E_w, sum_w W_w,
+ * sum_w W_w |sum_p S_p|/P, accepted moves} to the device history. */
+afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps);
+
+/* Measure the current state (no step is taken) and synchronise:
+ *   e_mix     = sum_w W_w Re E_w / sum_w W_w           (Eq. (16), real part)
+ *   sum_w     = sum_w W_w
+ *   mean_sign = sum_w W_w |sum_p S_p| / (P sum_w W_w)  (Sec. III A, path-sign average)
+ *   e_walker  (nullable) 2*W doubles: E_w = sum_p S_p E_L,wp / sum_p S_p as re, im
+ * Walkers of weight 0 do not enter the sums.  Returns AFQMC_ERR_NUMERIC if the
+ * device status word is set (the values are still written). */
+afqmc_status afqmc_energy(afqmc_ctx* ctx, double* e_mix, double* sum_w, double* mean_sign,
+                          double* e_walker);
+
+/* After afqmc_energy: copy per-pair and per-walker measurements to host arrays
+ * (each nullable):
+ *   logov       2*W*P       log <Phi(x_wp)|phi_w> = log|det| + i Arg det (both spins)
+ *   e_local     2*W*P       local energy E_L,wp (re, im)
+ *   force_bias  2*W*n_chol  path-averaged <L_g>_w (re, im), Eq. (27) */
+afqmc_status afqmc_observables(afqmc_ctx* ctx, double* logov, double* e_local, double* force_bias);
+
+/* Copy the last min(n, steps taken, capacity) per-step records, oldest first,
+ * into out[4*i + {0,1,2,3}] = {sum W Re E, sum W, sum W |sum S|/P, accepted};
+ * *n_out receives the count.  Synchronises. */
+afqmc_status afqmc_history(afqmc_ctx* ctx, double* out, int n, int* n_out);
+
+/* Statistics since init (synchronises); out[0..len) receives, as available:
+ *   0 steps taken, 1 accepted moves, 2 proposed moves, 3 live walkers,
+ *   4 device status word (0 = fine), 5 min weight, 6 max weight, 7 sum weight */
+afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len);
+
+/* Checkpoint.  The state buffer (host memory) is, in order, with no padding:
+ *   uint64  magic 0x4146514D43535431, N, n_up, n_dn, K, W, P, step
+ *   double  phi     W*N*(n_up+n_dn)*2  walker orbitals, column c < n_up spin up,
+ *                                       column n_up + c spin down (re, im)
+ *   double  weight  W
+ *   double  x       W*P*K              hidden variables of the paths
+ *   double  Phi     W*P*N*n_up         Phi(x_wp), kept so a resumed run is exact
+ * afqmc_state_save with buf NULL stores the size in *len; otherwise *len must
+ * be at least that size.  afqmc_state_load validates magic and shape.  The
+ * random streams are counter based, so save + load + k steps is bitwise equal
+ * to k steps without the interruption. */
+afqmc_status afqmc_state_save(afqmc_ctx* ctx, void* buf, size_t* len);
+afqmc_status afqmc_state_load(afqmc_ctx* ctx, const void* buf, size_t len);
+
+/* Release the context (not the caller's workspace). */
+void afqmc_destroy(afqmc_ctx* ctx);
+
+/* Message of the last error in this thread (static storage). */
+const char* afqmc_last_error(void);
+
+/* The library's Philox4x32-10 (Salmon et al., SC'11) on the device, for
+ * checking the generator: out[4*i + j] = word j of Philox(counter_i, key) with
+ * counter_i = {c0 + i, c1, c2, c3}, i < n.  out is a device pointer. */
+afqmc_status afqmc_philox_fill(uint32_t* out, int64_t n, uint32_t c0, uint32_t c1, uint32_t c2,
+                               uint32_t c3, uint64_t key, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFQMC_H */

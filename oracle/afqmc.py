@@ -86,10 +86,15 @@ class State:
     weight: np.ndarray     # (W,) float64
     x: np.ndarray          # (W, P, K) float64 hidden variables of each path
     Phi: np.ndarray        # (W, P, N, n_up) float64, Phi(x); spin down uses the first n_dn columns
+    walker_index: np.ndarray = None  # global index of each walker in the random streams (default 0..W-1)
+
+    def __post_init__(self):
+        if self.walker_index is None:
+            self.walker_index = np.arange(self.weight.shape[0])
 
     def copy(self) -> "State":
         return State(self.step, self.phi_up.copy(), self.phi_dn.copy(), self.weight.copy(),
-                     self.x.copy(), self.Phi.copy())
+                     self.x.copy(), self.Phi.copy(), self.walker_index.copy())
 
 
 # ---------------------------------------------------------------------------
@@ -236,7 +241,7 @@ def mcmc_sweep(ham: Hamiltonian, cfg: OracleConfig, st: State, logov_cur: np.nda
     u < |<Phi(x')|phi>| / |<Phi(x)|phi>|.  Updates st.x, st.Phi and logov_cur in
     place; returns the number of accepted moves."""
     W, P, K = st.x.shape
-    pair_ids = np.arange(W * P)
+    pair_ids = (st.walker_index[:, None] * P + np.arange(P)[None, :]).reshape(-1)
     xi = px.normals(cfg.seed, tag_prop, step, pair_ids, sweep, K).reshape(W, P, K)
     u = px.uniforms(cfg.seed, tag_acc, step, pair_ids, sweep, 1).reshape(W, P)
     if cfg.proposal == "prior":
@@ -306,7 +311,7 @@ def step(ham: Hamiltonian, cfg: OracleConfig, st: State):
     new.weight[~alive] = 0.0
 
     # Leapfrog step 1: fields, force bias (Eq. (15)), propagation (Eq. (12)).
-    xi = px.normals(cfg.seed, px.TAG_FIELD, i, np.arange(W), 0, G)
+    xi = px.normals(cfg.seed, px.TAG_FIELD, i, st.walker_index, 0, G)
     xbar = -1j * math.sqrt(tau) * m["v_bar"]
     y = xi - xbar
     logov_new = m["logov"].copy()

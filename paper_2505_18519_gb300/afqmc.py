@@ -1,0 +1,257 @@
+"""Python binding of ``libafqmc.so`` (the C ABI in include/afqmc.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides the device workspace and the CUDA stream.
+There is no CPU fallback: without the built library or a GPU every call
+raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libafqmc.so")
+
+CONSTRAINTS = {"combined": 0, "separate": 1, "half_plane": 2}
+PROPOSALS = {"prior": 0, "pcn": 1}
+PRECISIONS = {"fp64": 0}
+STATE_MAGIC = 0x4146514D43535431
+
+
+class AfqmcConfig(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int), ("n_up", ctypes.c_int), ("n_dn", ctypes.c_int), ("n_chol", ctypes.c_int),
+        ("K", ctypes.c_int), ("n_walkers", ctypes.c_int), ("n_paths", ctypes.c_int), ("n_sweeps", ctypes.c_int),
+        ("n_burn", ctypes.c_int), ("constraint", ctypes.c_int), ("proposal", ctypes.c_int),
+        ("precision", ctypes.c_int), ("taylor_order", ctypes.c_int), ("history_capacity", ctypes.c_int),
+        ("dtau", ctypes.c_double), ("pcn_beta", ctypes.c_double), ("e_shift", ctypes.c_double),
+        ("kill_threshold", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+_lib = None
+
+EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc_step", "afqmc_energy",
+           "afqmc_observables", "afqmc_history", "afqmc_stats", "afqmc_state_save", "afqmc_state_load",
+           "afqmc_destroy", "afqmc_last_error", "afqmc_philox_fill")
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2505_18519_gb300.build`")
+    lib = ctypes.CDLL(path)
+    P, D, I, U64, SZ = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t
+    cfgp = ctypes.POINTER(AfqmcConfig)
+    lib.afqmc_config_default.argtypes = [cfgp]
+    lib.afqmc_config_default.restype = None
+    lib.afqmc_workspace_bytes.argtypes = [cfgp]
+    lib.afqmc_workspace_bytes.restype = SZ
+    lib.afqmc_init.argtypes = [cfgp, P, P, P, P, P, SZ, P, ctypes.POINTER(P)]
+    lib.afqmc_init.restype = I
+    lib.afqmc_step.argtypes = [P, I]
+    lib.afqmc_step.restype = I
+    lib.afqmc_energy.argtypes = [P, D, D, D, P]
+    lib.afqmc_energy.restype = I
+    lib.afqmc_observables.argtypes = [P, P, P, P]
+    lib.afqmc_observables.restype = I
+    lib.afqmc_history.argtypes = [P, P, I, ctypes.POINTER(I)]
+    lib.afqmc_history.restype = I
+    lib.afqmc_stats.argtypes = [P, P, I]
+    lib.afqmc_stats.restype = I
+    lib.afqmc_state_save.argtypes = [P, P, ctypes.POINTER(SZ)]
+    lib.afqmc_state_save.restype = I
+    lib.afqmc_state_load.argtypes = [P, P, SZ]
+    lib.afqmc_state_load.restype = I
+    lib.afqmc_destroy.argtypes = [P]
+    lib.afqmc_destroy.restype = None
+    lib.afqmc_last_error.argtypes = []
+    lib.afqmc_last_error.restype = ctypes.c_char_p
+    lib.afqmc_philox_fill.argtypes = [P, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                      ctypes.c_uint32, U64, P]
+    lib.afqmc_philox_fill.restype = I
+    _lib = lib
+    return lib
+
+
+class AfqmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"afqmc status {status}: {msg}")
+        self.status = status
+
+
+def _check(st: int):
+    if st != 0:
+        raise AfqmcError(st, load_library().afqmc_last_error().decode())
+
+
+def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_sweeps=1, n_burn=20,
+                constraint="combined", proposal="prior", precision="fp64", taylor_order=6, history_capacity=1024,
+                pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10) -> AfqmcConfig:
+    lib = load_library()
+    c = AfqmcConfig()
+    lib.afqmc_config_default(ctypes.byref(c))
+    c.N, c.n_up, c.n_dn, c.n_chol, c.K = N, n_up, n_dn, n_chol, K
+    c.n_walkers, c.n_paths, c.n_sweeps, c.n_burn = n_walkers, n_paths, n_sweeps, n_burn
+    c.constraint, c.proposal, c.precision = CONSTRAINTS[constraint], PROPOSALS[proposal], PRECISIONS[precision]
+    c.taylor_order, c.history_capacity = taylor_order, history_capacity
+    c.dtau, c.pcn_beta, c.e_shift, c.kill_threshold, c.seed = dtau, pcn_beta, e_shift, kill_threshold, seed
+    return c
+
+
+def workspace_bytes(cfg: AfqmcConfig) -> int:
+    return int(load_library().afqmc_workspace_bytes(ctypes.byref(cfg)))
+
+
+def _ptr(a):
+    """(pointer, keepalive) of a float64 C-contiguous numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                a = a.to(torch.float64).contiguous()
+            return a.data_ptr(), a
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.ctypes.data, a
+
+
+class Context:
+    """One AFQMC run: configuration, Hamiltonian, walkers and paths on one GPU."""
+
+    def __init__(self, cfg: AfqmcConfig, h, L, Phi0, U, device=None, stream=None):
+        import torch
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.cfg = cfg
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = workspace_bytes(cfg)
+        if nbytes == 0:
+            # let the library report why
+            st = lib.afqmc_init(ctypes.byref(cfg), None, None, None, None, None, 0, None, ctypes.byref(ctypes.c_void_p()))
+            _check(st)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        keep = [_ptr(x) for x in (h, L, Phi0, U)]
+        self._ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.afqmc_init(ctypes.byref(cfg), keep[0][0], keep[1][0], keep[2][0], keep[3][0], self._ws_ptr,
+                                  nbytes, self.stream.cuda_stream, ctypes.byref(self._ctx)))
+        self.W, self.P, self.G, self.K = cfg.n_walkers, cfg.n_paths, cfg.n_chol, cfg.K
+        self.N, self.nu, self.nd = cfg.N, cfg.n_up, cfg.n_dn
+
+    # -- stepping and measurement -------------------------------------------------
+    def step(self, n_steps: int = 1):
+        _check(load_library().afqmc_step(self._ctx, int(n_steps)))
+
+    def energy(self, walkers: bool = False):
+        e, sw, ms = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        ew = np.empty(2 * self.W) if walkers else None
+        st = load_library().afqmc_energy(self._ctx, ctypes.byref(e), ctypes.byref(sw), ctypes.byref(ms),
+                                         ew.ctypes.data if walkers else None)
+        _check(st)
+        out = dict(e_mix=e.value, sum_w=sw.value, mean_sign=ms.value)
+        if walkers:
+            out["e_walker"] = ew.view(np.complex128)
+        return out
+
+    def observables(self):
+        lo = np.empty(2 * self.W * self.P)
+        el = np.empty(2 * self.W * self.P)
+        fb = np.empty(2 * self.W * self.G)
+        _check(load_library().afqmc_observables(self._ctx, lo.ctypes.data, el.ctypes.data, fb.ctypes.data))
+        return dict(logov=lo.view(np.complex128).reshape(self.W, self.P),
+                    e_local=el.view(np.complex128).reshape(self.W, self.P),
+                    force_bias=fb.view(np.complex128).reshape(self.W, self.G))
+
+    def history(self, n: int):
+        out = np.empty(4 * max(n, 1))
+        k = ctypes.c_int()
+        _check(load_library().afqmc_history(self._ctx, out.ctypes.data, int(n), ctypes.byref(k)))
+        return out[: 4 * k.value].reshape(k.value, 4)
+
+    def stats(self):
+        out = np.empty(8)
+        _check(load_library().afqmc_stats(self._ctx, out.ctypes.data, 8))
+        keys = ("steps", "accepted", "proposed", "live_walkers", "status", "min_weight", "max_weight", "sum_weight")
+        return dict(zip(keys, out.tolist()))
+
+    # -- checkpoint ---------------------------------------------------------------
+    def save_state(self) -> bytes:
+        lib = load_library()
+        n = ctypes.c_size_t()
+        _check(lib.afqmc_state_save(self._ctx, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib.afqmc_state_save(self._ctx, buf, ctypes.byref(n)))
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        _check(load_library().afqmc_state_load(self._ctx, blob, len(blob)))
+
+    def state_arrays(self) -> dict:
+        return unpack_state(self.save_state())
+
+    def load_state_arrays(self, st: dict):
+        self.load_state(pack_state(st))
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            load_library().afqmc_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unpack_state(blob: bytes) -> dict:
+    """Split a state buffer (layout in include/afqmc.h) into numpy arrays."""
+    hdr = struct.unpack_from("<8Q", blob, 0)
+    if hdr[0] != STATE_MAGIC:
+        raise ValueError("not an afqmc state buffer")
+    N, nu, nd, K, W, P, step = hdr[1:]
+    nt = nu + nd
+    o = 64
+    def take(count, dtype):
+        nonlocal o
+        a = np.frombuffer(blob, dtype=dtype, count=count, offset=o).copy()
+        o += a.nbytes
+        return a
+    phi = take(W * N * nt, np.complex128).reshape(W, N, nt)
+    weight = take(W, np.float64)
+    x = take(W * P * K, np.float64).reshape(W, P, K)
+    Phi = take(W * P * N * nu, np.float64).reshape(W, P, N, nu)
+    return dict(step=int(step), phi_up=phi[:, :, :nu].copy(), phi_dn=phi[:, :, nu:].copy(), weight=weight, x=x, Phi=Phi)
+
+
+def pack_state(st: dict) -> bytes:
+    W, N, nu = st["phi_up"].shape
+    nd = st["phi_dn"].shape[2]
+    P, K = st["x"].shape[1:]
+    phi = np.concatenate([st["phi_up"], st["phi_dn"]], axis=2).astype(np.complex128)
+    hdr = struct.pack("<8Q", STATE_MAGIC, N, nu, nd, K, W, P, int(st["step"]))
+    return b"".join([hdr, np.ascontiguousarray(phi).tobytes(), np.ascontiguousarray(st["weight"], np.float64).tobytes(),
+                     np.ascontiguousarray(st["x"], np.float64).tobytes(),
+                     np.ascontiguousarray(st["Phi"], np.float64).tobytes()])
+
+
+def philox_fill(out, n: int, c0: int, c1: int, c2: int, c3: int, key: int, stream=None):
+    """Fill the device uint32 tensor ``out`` (4n words) with the library's Philox4x32-10."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(load_library().afqmc_philox_fill(out.data_ptr(), int(n), c0, c1, c2, c3, int(key), s.cuda_stream))

@@ -1,0 +1,454 @@
+// C ABI of the library (declared in include/afqmc.h): configuration checks,
+// the workspace layout, and the order of kernels in init, step and measure.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "kernels.cuh"
+
+using namespace afq;
+
+static thread_local char g_err[512] = "";
+
+static afqmc_status fail(afqmc_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(AFQMC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char* afqmc_last_error(void) { return g_err; }
+
+extern "C" void afqmc_config_default(afqmc_config* c) {
+    memset(c, 0, sizeof *c);
+    c->n_sweeps = 1;
+    c->n_burn = 20;
+    c->constraint = AFQMC_CONSTRAINT_COMBINED;
+    c->proposal = AFQMC_PROPOSAL_PRIOR;
+    c->precision = AFQMC_PRECISION_FP64;
+    c->taylor_order = 6;
+    c->history_capacity = 1024;
+    c->pcn_beta = 1.0;
+    c->kill_threshold = 1e-10;
+}
+
+static const char* check_config(const afqmc_config* c) {
+    if (!c) return "config is NULL";
+    if (c->N < 1 || c->N > 256) return "N must be in [1, 256]";
+    if (c->n_up < 1 || c->n_up > c->N || c->n_up > 64) return "n_up must be in [1, min(N, 64)]";
+    if (c->n_dn < 0 || c->n_dn > c->n_up) return "n_dn must be in [0, n_up]";
+    if (c->n_chol < 1 || c->K < 1) return "n_chol and K must be >= 1";
+    if (c->n_walkers < 1 || c->n_paths < 1 || c->n_paths > 1024) return "n_walkers >= 1 and 1 <= n_paths <= 1024";
+    if ((long long)c->n_walkers * c->n_paths > (1ll << 31)) return "too many walker-path pairs";
+    if (c->n_sweeps < 1 || c->n_burn < 0) return "n_sweeps >= 1 and n_burn >= 0";
+    if (c->constraint < 0 || c->constraint > 2) return "unknown constraint";
+    if (c->proposal < 0 || c->proposal > 1) return "unknown proposal";
+    if (c->precision != AFQMC_PRECISION_FP64) return "unknown precision";
+    if (c->taylor_order < 1 || c->taylor_order > 32) return "taylor_order must be in [1, 32]";
+    if (c->history_capacity < 1) return "history_capacity must be >= 1";
+    if (!(c->dtau > 0.0)) return "dtau must be > 0";
+    if (c->proposal == AFQMC_PROPOSAL_PCN && !(c->pcn_beta > 0.0 && c->pcn_beta <= 1.0)) return "pcn_beta in (0, 1]";
+    if (!(c->kill_threshold >= 0.0)) return "kill_threshold must be >= 0";
+    if (!contract_fp64_supported(c->N, c->n_up, c->n_dn)) return "sizes too large for the FP64 contraction kernel";
+    if (2ull * c->N * (c->n_up + c->n_dn) * 16 > 220 * 1024) return "sizes too large for the propagation kernel";
+    return nullptr;
+}
+
+static Dims dims_of(const afqmc_config* c) {
+    Dims d;
+    d.N = c->N; d.nu = c->n_up; d.nd = c->n_dn; d.nt = c->n_up + c->n_dn;
+    d.G = c->n_chol; d.K = c->K; d.W = c->n_walkers; d.P = c->n_paths;
+    d.pairs = (long long)c->n_walkers * c->n_paths;
+    return d;
+}
+
+// Carve the workspace into 256-byte aligned buffers; with base == nullptr
+// only the total is computed.
+static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
+    Dims d = dims_of(c);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        off = (off + 255) & ~(size_t)255;
+        void* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    size_t N = d.N, NN = N * N, nt = d.nt, nu = d.nu, G = d.G, K = d.K, W = d.W, pairs = d.pairs;
+    Workspace w{};
+    w.h = (double*)take(NN * 8);
+    w.L = (double*)take(G * NN * 8);
+    w.Phi0 = (double*)take(N * nu * 8);
+    w.U = (double*)take(K * NN * 8);
+    w.T = (double*)take(NN * 8);
+    w.expT = (double*)take(NN * 8);
+    w.scratchNN = (double*)take(3 * NN * 8);
+    w.phi = (double2*)take(W * N * nt * 16);
+    w.weight = (double*)take(W * 8);
+    w.x = (double*)take(pairs * K * 8);
+    w.Phi = (double*)take(pairs * N * nu * 8);
+    w.logdet = (double2*)take(pairs * 2 * 16);
+    w.logov = (double2*)take(pairs * 16);
+    w.Theta = (double2*)take(pairs * N * nt * 16);
+    w.vpair = (double2*)take(pairs * G * 16);
+    w.epair = (double2*)take(pairs * 16);
+    w.logdet_new = (double2*)take(pairs * 2 * 16);
+    w.logov_cur = (double2*)take(pairs * 16);
+    w.sumS = (double2*)take(W * 16);
+    w.vbar = (double2*)take(W * G * 16);
+    w.ebar = (double2*)take(W * 16);
+    w.y = (double2*)take(W * G * 16);
+    w.logshift = (double2*)take(W * 16);
+    w.Aplanes = (double*)take(2 * W * NN * 8);
+    w.phi_new = (double2*)take(W * N * nt * 16);
+    w.old_sum = (double2*)take(W * 16);
+    w.ratio = (double2*)take(W * 16);
+    w.Iabs = (double*)take(W * 8);
+    w.alive = (int*)take(W * 4);
+    w.xprop = (double*)take(pairs * K * 8);
+    w.Sprop = (double*)take(pairs * NN * 8);
+    w.Phiprop = (double*)take(pairs * N * nu * 8);
+    w.logdet_prop = (double2*)take(pairs * 2 * 16);
+    w.history = (double*)take((size_t)c->history_capacity * 4 * 8);
+    w.reduce = (double*)take(8 * 8);
+    w.counters = (unsigned long long*)take(8 * 8);
+    w.status = (int*)take(4);
+    w.total = (off + 255) & ~(size_t)255;
+    if (ws) *ws = w;
+    return w.total;
+}
+
+extern "C" size_t afqmc_workspace_bytes(const afqmc_config* cfg) {
+    if (check_config(cfg)) return 0;
+    return layout(cfg, nullptr, nullptr);
+}
+
+static StepParams params_of(const afqmc_config* c) {
+    StepParams p;
+    p.seed = c->seed; p.dtau = c->dtau; p.pcn_beta = c->pcn_beta; p.e_shift = c->e_shift;
+    p.kill_threshold = c->kill_threshold; p.constraint = c->constraint; p.proposal = c->proposal;
+    p.taylor_order = c->taylor_order; p.history_capacity = c->history_capacity;
+    return p;
+}
+
+// One Metropolis sweep of every path against the walker orbitals `orbitals`
+// (phi' during a step, phi during burn-in).
+static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t tag_prop, uint32_t tag_acc,
+                               uint32_t sweep) {
+    const Dims& d = ctx->d;
+    Workspace& w = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    StepParams p = params_of(&ctx->cfg);
+    CK(propose(s, d, p, w.counters, tag_prop, sweep, w.x, w.alive, w.xprop));
+    gemm_nn_f64(s, (int)d.pairs, d.N * d.N, d.K, 1.0, w.xprop, d.K, w.U, (long long)d.N * d.N, 0.0, w.Sprop,
+                (long long)d.N * d.N);
+    CK(cudaGetLastError());
+    CK(trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phiprop, w.alive, d.P, w.status));
+    for (int spin = 0; spin < 2; ++spin)
+        CK(overlap_lu(s, d, spin, w.Phiprop, (long long)d.N * d.nu, orbitals, w.logdet_prop, nullptr, w.alive, w.status,
+                      d.pairs, d.P));
+    CK(accept(s, d, p, w.counters, tag_acc, sweep, w.logdet_prop, w.xprop, w.Phiprop, w.alive, w.logov_cur, w.x, w.Phi,
+              w.counters));
+    return AFQMC_OK;
+}
+
+// Local energies, force-bias values and path signs at the current walkers,
+// and the mixed-estimator sums into ws.reduce[0..2].
+static afqmc_status measure(afqmc_ctx* ctx) {
+    const Dims& d = ctx->d;
+    Workspace& w = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    for (int spin = 0; spin < 2; ++spin)
+        CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P));
+    CK(contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
+    CK(walker_average(s, d, w.logdet, w.vpair, w.epair, w.logov, w.sumS, w.vbar, w.ebar));
+    CK(energy_reduce(s, d, w.weight, w.ebar, w.sumS, w.reduce));
+    return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, const double* L, const double* Phi0,
+                                   const double* U, void* workspace, size_t workspace_bytes, void* stream,
+                                   afqmc_ctx** out) {
+    if (!out) return fail(AFQMC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (const char* m = check_config(cfg)) return fail(AFQMC_ERR_ARG, "%s", m);
+    if (!h || !L || !Phi0 || !U) return fail(AFQMC_ERR_ARG, "h, L, Phi0 and U must not be NULL");
+    size_t need = layout(cfg, nullptr, nullptr);
+    if (!workspace || workspace_bytes < need)
+        return fail(AFQMC_ERR_WORKSPACE, "workspace needs %zu bytes, got %zu", need, workspace_bytes);
+    if (((uintptr_t)workspace & 255) != 0) return fail(AFQMC_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(AFQMC_ERR_WORKSPACE, "workspace is not device memory");
+    }
+    afqmc_ctx* ctx = (afqmc_ctx*)calloc(1, sizeof(afqmc_ctx));
+    if (!ctx) return fail(AFQMC_ERR_ARG, "out of host memory");
+    ctx->cfg = *cfg;
+    ctx->d = dims_of(cfg);
+    ctx->stream = (cudaStream_t)stream;
+    layout(cfg, (char*)workspace, &ctx->ws);
+    afqmc_status st = AFQMC_OK;
+    do {
+        const Dims& d = ctx->d;
+        Workspace& w = ctx->ws;
+        cudaStream_t s = ctx->stream;
+        size_t NN = (size_t)d.N * d.N;
+        auto copy_in = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+        };
+        cudaError_t e = copy_in(w.h, h, NN * 8);
+        if (e == cudaSuccess) e = copy_in(w.L, L, (size_t)d.G * NN * 8);
+        if (e == cudaSuccess) e = copy_in(w.Phi0, Phi0, (size_t)d.N * d.nu * 8);
+        if (e == cudaSuccess) e = copy_in(w.U, U, (size_t)d.K * NN * 8);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 8 * 8, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, 4, s);
+        if (e != cudaSuccess) { st = fail(AFQMC_ERR_CUDA, "copying inputs: %s", cudaGetErrorString(e)); break; }
+        StepParams p = params_of(cfg);
+        if ((e = one_body_propagator(s, d.N, d.G, cfg->dtau, w.h, w.L, w.T, w.scratchNN, w.expT)) != cudaSuccess) {
+            st = fail(AFQMC_ERR_CUDA, "one-body propagator: %s", cudaGetErrorString(e));
+            break;
+        }
+        // initial walkers phi_w = Phi(x_w), x_w ~ N(0, I), orthonormalised
+        fill_normals(s, w.xprop, d.W, d.K, p.seed, TAG_INIT_WALKER, w.counters, 0);
+        gemm_nn_f64(s, d.W, (int)NN, d.K, 1.0, w.xprop, d.K, w.U, NN, 0.0, w.Sprop, NN);
+        trial_orbitals(s, d.N, d.nu, d.W, w.Sprop, w.Phi0, w.Phiprop, nullptr, 1, w.status);
+        walkers_from_trial(s, d, w.Phiprop, w.phi_new);
+        reorthonormalise(s, d, w.phi_new, w.phi, nullptr, w.status, d.W);
+        // paths x_wp ~ N(0, I) and their orbitals
+        fill_normals(s, w.x, d.pairs, d.K, p.seed, TAG_INIT_PATH, w.counters, 0);
+        gemm_nn_f64(s, (int)d.pairs, (int)NN, d.K, 1.0, w.x, d.K, w.U, NN, 0.0, w.Sprop, NN);
+        trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phi, nullptr, d.P, w.status);
+        set_value(s, w.weight, d.W, 1.0);
+        set_int(s, w.alive, d.W, 1);
+        for (int spin = 0; spin < 2; ++spin)
+            overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet_new, nullptr, nullptr, w.status,
+                       d.pairs, d.P);
+        combine_logdet(s, d.pairs, w.logdet_new, w.logov_cur);
+        if ((e = cudaGetLastError()) != cudaSuccess) { st = fail(AFQMC_ERR_CUDA, "init kernels: %s", cudaGetErrorString(e)); break; }
+        for (int b = 0; b < cfg->n_burn && st == AFQMC_OK; ++b) st = mcmc_sweep(ctx, w.phi, TAG_BURN_PROPOSE, TAG_BURN_ACCEPT, b);
+        if (st != AFQMC_OK) break;
+        // the burn-in acceptances are not counted in the run statistics
+        if ((e = cudaMemsetAsync(w.counters, 0, 8 * 8, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+            st = fail(AFQMC_ERR_CUDA, "init: %s", cudaGetErrorString(e));
+            break;
+        }
+    } while (0);
+    if (st != AFQMC_OK) {
+        free(ctx);
+        return st;
+    }
+    *out = ctx;
+    return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
+    if (!ctx) return fail(AFQMC_ERR_ARG, "ctx is NULL");
+    if (n_steps < 0) return fail(AFQMC_ERR_ARG, "n_steps must be >= 0");
+    const Dims& d = ctx->d;
+    Workspace& w = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    StepParams p = params_of(&ctx->cfg);
+    for (int it = 0; it < n_steps; ++it) {
+        afqmc_status st = measure(ctx);                 // Eq. (25)-(27), (16) at phi
+        if (st != AFQMC_OK) return st;
+        CK(fields(s, d, p, w.counters, w.vbar, w.sumS, w.weight, w.alive, (double*)w.y, w.logshift));
+        gemm_nn_f64(s, 2 * d.W, d.N * d.N, d.G, 1.0, (const double*)w.y, d.G, w.L, (long long)d.N * d.N, 0.0,
+                    w.Aplanes, (long long)d.N * d.N);
+        CK(cudaGetLastError());
+        CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive));          // Eq. (12)
+        for (int spin = 0; spin < 2; ++spin)
+            CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi_new, w.logdet_new, nullptr, w.alive, w.status,
+                          d.pairs, d.P));
+        CK(ratios(s, d, w.logov, w.logdet_new, w.sumS, w.logshift, w.alive, w.logov_cur, w.old_sum, w.ratio, w.Iabs));
+        for (int m = 0; m < ctx->cfg.n_sweeps; ++m) {                                  // Eq. (23)
+            st = mcmc_sweep(ctx, w.phi_new, TAG_PROPOSE, TAG_ACCEPT, (uint32_t)m);
+            if (st != AFQMC_OK) return st;
+        }
+        CK(handoff(s, d, p, w.logov_cur, w.old_sum, w.ratio, w.Iabs, w.alive, w.weight, w.status));  // Eq. (28)-(29)
+        CK(reorthonormalise(s, d, w.phi_new, w.phi, w.alive, w.status, d.W));
+        CK(step_end(s, p, w.reduce, w.history, w.counters));
+        ctx->steps_taken++;
+    }
+    ctx->measured = false;
+    return AFQMC_OK;
+}
+
+static afqmc_status read_status(afqmc_ctx* ctx, int* status) {
+    CK(cudaMemcpyAsync(status, ctx->ws.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_energy(afqmc_ctx* ctx, double* e_mix, double* sum_w, double* mean_sign,
+                                     double* e_walker) {
+    if (!ctx) return fail(AFQMC_ERR_ARG, "ctx is NULL");
+    afqmc_status st = measure(ctx);
+    if (st != AFQMC_OK) return st;
+    double r[3];
+    CK(cudaMemcpyAsync(r, ctx->ws.reduce, sizeof r, cudaMemcpyDeviceToHost, ctx->stream));
+    if (e_walker)
+        CK(cudaMemcpyAsync(e_walker, ctx->ws.ebar, (size_t)ctx->d.W * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    int status = 0;
+    if ((st = read_status(ctx, &status)) != AFQMC_OK) return st;
+    ctx->measured = true;
+    if (e_mix) *e_mix = r[1] > 0 ? r[0] / r[1] : 0.0;
+    if (sum_w) *sum_w = r[1];
+    if (mean_sign) *mean_sign = r[1] > 0 ? r[2] / r[1] : 0.0;
+    if (status) return fail(AFQMC_ERR_NUMERIC, "device status word 0x%x (1 singular overlap, 2 non-finite value)", status);
+    return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_observables(afqmc_ctx* ctx, double* logov, double* e_local, double* force_bias) {
+    if (!ctx) return fail(AFQMC_ERR_ARG, "ctx is NULL");
+    if (!ctx->measured) return fail(AFQMC_ERR_ARG, "call afqmc_energy first");
+    const Dims& d = ctx->d;
+    if (logov) CK(cudaMemcpyAsync(logov, ctx->ws.logov, d.pairs * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    if (e_local) CK(cudaMemcpyAsync(e_local, ctx->ws.epair, d.pairs * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    if (force_bias)
+        CK(cudaMemcpyAsync(force_bias, ctx->ws.vbar, (size_t)d.W * d.G * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_history(afqmc_ctx* ctx, double* out, int n, int* n_out) {
+    if (!ctx || !out || n < 0) return fail(AFQMC_ERR_ARG, "bad arguments");
+    int cap = ctx->cfg.history_capacity;
+    long long taken = ctx->steps_taken;
+    long long k = n;
+    if (k > taken) k = taken;
+    if (k > cap) k = cap;
+    for (long long i = 0; i < k; ++i) {
+        long long st = taken - k + i;
+        CK(cudaMemcpyAsync(out + 4 * i, ctx->ws.history + 4 * (st % cap), 32, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (n_out) *n_out = (int)k;
+    return AFQMC_OK;
+}
+
+__global__ void weight_stats_kernel(int W, const double* __restrict__ weight, double* out4) {
+    __shared__ double smin[256], smax[256], ssum[256], slive[256];
+    double mn = INFINITY, mx = -INFINITY, sm = 0.0, lv = 0.0;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        double v = weight[w];
+        mn = fmin(mn, v); mx = fmax(mx, v); sm += v; lv += (v > 0.0);
+    }
+    smin[threadIdx.x] = mn; smax[threadIdx.x] = mx; ssum[threadIdx.x] = sm; slive[threadIdx.x] = lv;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + off]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + off]);
+            ssum[threadIdx.x] += ssum[threadIdx.x + off];
+            slive[threadIdx.x] += slive[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out4[0] = slive[0]; out4[1] = smin[0]; out4[2] = smax[0]; out4[3] = ssum[0]; }
+}
+
+extern "C" afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len) {
+    if (!ctx || !out || len < 0) return fail(AFQMC_ERR_ARG, "bad arguments");
+    unsigned long long c[8];
+    double ws4[4];
+    int status = 0;
+    weight_stats_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d.W, ctx->ws.weight, ctx->ws.reduce + 4);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c, ctx->ws.counters, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ws4, ctx->ws.reduce + 4, sizeof ws4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&status, ctx->ws.status, sizeof status, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double v[8] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3]};
+    for (int i = 0; i < len && i < 8; ++i) out[i] = v[i];
+    return AFQMC_OK;
+}
+
+static const uint64_t STATE_MAGIC = 0x4146514D43535431ull;
+
+static size_t state_bytes(const Dims& d) {
+    return 8 * 8 + (size_t)d.W * d.N * d.nt * 16 + (size_t)d.W * 8 + (size_t)d.pairs * d.K * 8 +
+           (size_t)d.pairs * d.N * d.nu * 8;
+}
+
+extern "C" afqmc_status afqmc_state_save(afqmc_ctx* ctx, void* buf, size_t* len) {
+    if (!ctx || !len) return fail(AFQMC_ERR_ARG, "bad arguments");
+    const Dims& d = ctx->d;
+    size_t need = state_bytes(d);
+    if (!buf) { *len = need; return AFQMC_OK; }
+    if (*len < need) return fail(AFQMC_ERR_STATE, "state buffer needs %zu bytes", need);
+    char* p = (char*)buf;
+    unsigned long long step = 0;
+    CK(cudaMemcpyAsync(&step, ctx->ws.counters, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    uint64_t hdr[8] = {STATE_MAGIC, (uint64_t)d.N, (uint64_t)d.nu, (uint64_t)d.nd, (uint64_t)d.K, (uint64_t)d.W,
+                       (uint64_t)d.P, step};
+    memcpy(p, hdr, sizeof hdr);
+    p += sizeof hdr;
+    size_t b;
+    CK(cudaMemcpyAsync(p, ctx->ws.phi, b = (size_t)d.W * d.N * d.nt * 16, cudaMemcpyDeviceToHost, ctx->stream)); p += b;
+    CK(cudaMemcpyAsync(p, ctx->ws.weight, b = (size_t)d.W * 8, cudaMemcpyDeviceToHost, ctx->stream)); p += b;
+    CK(cudaMemcpyAsync(p, ctx->ws.x, b = (size_t)d.pairs * d.K * 8, cudaMemcpyDeviceToHost, ctx->stream)); p += b;
+    CK(cudaMemcpyAsync(p, ctx->ws.Phi, b = (size_t)d.pairs * d.N * d.nu * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *len = need;
+    return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_state_load(afqmc_ctx* ctx, const void* buf, size_t len) {
+    if (!ctx || !buf) return fail(AFQMC_ERR_ARG, "bad arguments");
+    const Dims& d = ctx->d;
+    if (len != state_bytes(d)) return fail(AFQMC_ERR_STATE, "state has %zu bytes, expected %zu", len, state_bytes(d));
+    uint64_t hdr[8];
+    memcpy(hdr, buf, sizeof hdr);
+    if (hdr[0] != STATE_MAGIC || hdr[1] != (uint64_t)d.N || hdr[2] != (uint64_t)d.nu || hdr[3] != (uint64_t)d.nd ||
+        hdr[4] != (uint64_t)d.K || hdr[5] != (uint64_t)d.W || hdr[6] != (uint64_t)d.P)
+        return fail(AFQMC_ERR_STATE, "state header does not match this context");
+    const char* p = (const char*)buf + sizeof hdr;
+    size_t b;
+    CK(cudaMemcpyAsync(ctx->ws.phi, p, b = (size_t)d.W * d.N * d.nt * 16, cudaMemcpyHostToDevice, ctx->stream)); p += b;
+    CK(cudaMemcpyAsync(ctx->ws.weight, p, b = (size_t)d.W * 8, cudaMemcpyHostToDevice, ctx->stream)); p += b;
+    CK(cudaMemcpyAsync(ctx->ws.x, p, b = (size_t)d.pairs * d.K * 8, cudaMemcpyHostToDevice, ctx->stream)); p += b;
+    CK(cudaMemcpyAsync(ctx->ws.Phi, p, b = (size_t)d.pairs * d.N * d.nu * 8, cudaMemcpyHostToDevice, ctx->stream));
+    unsigned long long c[8] = {hdr[7], 0, 0, 0, 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(ctx->ws.counters, c, sizeof c, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->steps_taken = (long long)hdr[7];
+    ctx->measured = false;
+    return AFQMC_OK;
+}
+
+extern "C" void afqmc_destroy(afqmc_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free(ctx);
+}
+
+__global__ void philox_fill_kernel(uint32_t* out, int64_t n, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                   uint32_t k0, uint32_t k1) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Philox4 r = philox4x32_10(c0 + (uint32_t)i, c1, c2, c3, k0, k1);
+    out[4 * i + 0] = r.w[0];
+    out[4 * i + 1] = r.w[1];
+    out[4 * i + 2] = r.w[2];
+    out[4 * i + 3] = r.w[3];
+}
+
+extern "C" afqmc_status afqmc_philox_fill(uint32_t* out, int64_t n, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          uint64_t key, void* stream) {
+    if (!out || n < 0) return fail(AFQMC_ERR_ARG, "bad arguments");
+    if (n == 0) return AFQMC_OK;
+    philox_fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(out, n, c0, c1, c2, c3,
+                                                                                     (uint32_t)key, (uint32_t)(key >> 32));
+    CK(cudaGetLastError());
+    return AFQMC_OK;
+}

@@ -1,0 +1,184 @@
+// Shared device helpers of the AFQMC library: complex arithmetic on double2,
+// the counter-based generator, and the context/workspace layout.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "../../include/afqmc.h"
+
+namespace afq {
+
+// ---------------------------------------------------------------- complex helpers
+__host__ __device__ __forceinline__ double2 cmk(double re, double im) { return make_double2(re, im); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return cmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return cmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return cmk(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return cmk(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return cmk(a.x, -a.y); }
+// a += b * c
+__host__ __device__ __forceinline__ void cfma(double2& a, double2 b, double2 c) {
+    a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));
+    a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
+}
+__device__ __forceinline__ double cabs_(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    // Smith's algorithm
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return cmk((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        double r = b.x / b.y, d = b.x * r + b.y;
+        return cmk((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+__device__ __forceinline__ double2 cexp_(double2 z) {
+    double s, c;
+    sincos(z.y, &s, &c);
+    double m = exp(z.x);
+    return cmk(m * c, m * s);
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Counter-based generator of Salmon, Moraes, Dror and Shaw (SC'11): ten rounds,
+// each multiplying counter words 0 and 2 by fixed odd constants and mixing
+// the products' halves with words 1, 3 and the round key; the key advances by
+// two Weyl increments between rounds.
+struct Philox4 { uint32_t w[4]; };
+
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                         uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint32_t lo0 = M0 * c0, hi0 = mulhi32(M0, c0);
+        uint32_t lo1 = M1 * c2, hi1 = mulhi32(M1, c2);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    Philox4 o; o.w[0] = c0; o.w[1] = c1; o.w[2] = c2; o.w[3] = c3;
+    return o;
+}
+
+// Random-stream tags (counter word 3 = tag << 24 | sweep).
+enum : uint32_t {
+    TAG_INIT_WALKER = 1, TAG_INIT_PATH = 2, TAG_FIELD = 3, TAG_PROPOSE = 4,
+    TAG_ACCEPT = 5, TAG_BURN_PROPOSE = 6, TAG_BURN_ACCEPT = 7
+};
+
+__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
+    uint64_t v = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+    return (double)v * 0x1.0p-53;
+}
+
+// Block j of a draw: counter = (j, entity, step, tag<<24|sweep).
+__device__ __forceinline__ Philox4 stream_block(uint64_t seed, uint32_t tag, uint32_t step, uint32_t entity,
+                                                uint32_t sweep, uint32_t j) {
+    return philox4x32_10(j, entity, step, (tag << 24) | (sweep & 0xFFFFFFu), (uint32_t)seed,
+                         (uint32_t)(seed >> 32));
+}
+
+// Two standard normals (Box-Muller) from block j: numbers 2j and 2j+1 of the draw.
+__device__ __forceinline__ double2 normal_pair(uint64_t seed, uint32_t tag, uint32_t step, uint32_t entity,
+                                              uint32_t sweep, uint32_t j) {
+    Philox4 b = stream_block(seed, tag, step, entity, sweep, j);
+    double u0 = u53(b.w[0], b.w[1]), u1 = u53(b.w[2], b.w[3]);
+    double r = sqrt(-2.0 * log1p(-u0));
+    double s, c;
+    sincospi(2.0 * u1, &s, &c);
+    return cmk(r * c, r * s);
+}
+
+__device__ __forceinline__ double normal_at(uint64_t seed, uint32_t tag, uint32_t step, uint32_t entity,
+                                           uint32_t sweep, uint32_t idx) {
+    double2 z = normal_pair(seed, tag, step, entity, sweep, idx >> 1);
+    return (idx & 1) ? z.y : z.x;
+}
+
+__device__ __forceinline__ double uniform_at0(uint64_t seed, uint32_t tag, uint32_t step, uint32_t entity,
+                                             uint32_t sweep) {
+    Philox4 b = stream_block(seed, tag, step, entity, sweep, 0);
+    return u53(b.w[0], b.w[1]);
+}
+
+// ---------------------------------------------------------------- status word bits
+enum : int { STATUS_SINGULAR = 1, STATUS_NONFINITE = 2 };
+
+// ---------------------------------------------------------------- workspace layout
+// Every buffer of a context lives in the caller's workspace, 256-byte aligned.
+struct Workspace {
+    // Hamiltonian and trial (copied at init)
+    double* h;        // N*N
+    double* L;        // G*N*N
+    double* Phi0;     // N*n_up
+    double* U;        // K*N*N
+    double* T;        // N*N, h - 1/2 sum_g L_g L_g
+    double* expT;     // N*N, exp(-tau T / 2)
+    double* scratchNN;  // 3*N*N for the matrix exponential at init
+    // composite walkers
+    double2* phi;     // W*N*nt (nt = n_up + n_dn)
+    double* weight;   // W
+    double* x;        // W*P*K
+    double* Phi;      // W*P*N*n_up
+    // per step, per pair
+    double2* logdet;     // W*P*2   per spin, at phi
+    double2* logov;      // W*P     sum over spins, at phi
+    double2* Theta;      // W*P*N*nt
+    double2* vpair;      // W*P*G
+    double2* epair;      // W*P
+    double2* logdet_new; // W*P*2   at phi'
+    double2* logov_cur;  // W*P     current paths at phi'
+    // per step, per walker
+    double2* sumS;    // W
+    double2* vbar;    // W*G
+    double2* ebar;    // W
+    double2* y;       // W*G   x - xbar
+    double2* logshift;  // W  sum_g (xi xbar - xbar^2/2)
+    double* Aplanes;  // 2W*N*N  rows 2w: sum_g Re(y) L_g ; 2w+1: sum_g Im(y) L_g
+    double2* phi_new; // W*N*nt
+    double2* old_sum; // W   sum_p S_p ov'/ov
+    double2* ratio;   // W
+    double* Iabs;     // W
+    int* alive;       // W
+    // Metropolis
+    double* xprop;    // W*P*K
+    double* Sprop;    // W*P*N*N   sum_k x'_k U_k
+    double* Phiprop;  // W*P*N*n_up
+    double2* logdet_prop; // W*P*2
+    // accounting
+    double* history;  // capacity*4
+    double* reduce;   // 8 doubles of scratch for reductions
+    unsigned long long* counters;  // [0] step, [1] accepted (total), [2] proposed (total), [3] accepted this step
+    int* status;      // 1 int
+    size_t total;
+};
+
+struct Dims {
+    int N, nu, nd, nt, G, K, W, P;
+    long long pairs;
+};
+
+}  // namespace afq
+
+struct afqmc_ctx {
+    afqmc_config cfg;
+    afq::Dims d;
+    afq::Workspace ws;
+    cudaStream_t stream;
+    long long steps_taken;   // host mirror of the device step counter
+    bool measured;           // afqmc_energy has filled the per-pair buffers
+};

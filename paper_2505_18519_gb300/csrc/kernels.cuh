@@ -1,0 +1,60 @@
+// Declarations of the library's kernels and their host launchers.
+#pragma once
+#include "common.cuh"
+
+namespace afq {
+
+// linalg_fp64.cu
+void gemm_nn_f64(cudaStream_t s, int M, int Nc, int K, double alpha, const double* A, long long lda, const double* B,
+                 long long ldb, double beta, double* C, long long ldc);
+cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
+                       const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
+                       long long pairs, int P);
+cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, double2* dst, const int* alive,
+                             int* status, int n_walkers);
+cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,
+                           double* Out, const int* alive, int P, int* status);
+cudaError_t one_body_propagator(cudaStream_t s, int N, int G, double dtau, const double* h, const double* L, double* T,
+                                double* scratch3, double* expT);
+
+// contract_fp64.cu
+cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
+                          const double2* Theta, double2* vpair, double2* epair, long long pairs);
+bool contract_fp64_supported(int N, int nu, int nd);
+
+// walker.cu
+struct StepParams {
+    uint64_t seed;
+    double dtau, pcn_beta, e_shift, kill_threshold;
+    int constraint, proposal, taylor_order, history_capacity;
+};
+cudaError_t fill_normals(cudaStream_t s, double* out, long long rows, int cols, uint64_t seed, uint32_t tag,
+                         const unsigned long long* step_ctr, uint32_t sweep);
+cudaError_t walkers_from_trial(cudaStream_t s, const Dims& d, const double* Phi_w, double2* phi);
+cudaError_t walker_average(cudaStream_t s, const Dims& d, const double2* logdet, const double2* vpair,
+                           const double2* epair, double2* logov, double2* sumS, double2* vbar, double2* ebar);
+cudaError_t energy_reduce(cudaStream_t s, const Dims& d, const double* weight, const double2* ebar,
+                          const double2* sumS, double* out3);
+cudaError_t fields(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr,
+                   const double2* vbar, const double2* sumS, double* weight, int* alive, double* yplanes,
+                   double2* logshift);
+cudaError_t propagate(cudaStream_t s, const Dims& d, const StepParams& p, const double* expT, const double* Aplanes,
+                      const double2* phi, double2* phi_new, const int* alive);
+cudaError_t ratios(cudaStream_t s, const Dims& d, const double2* logov, const double2* logdet_new,
+                   const double2* sumS, const double2* logshift, const int* alive, double2* logov_cur,
+                   double2* old_sum, double2* ratio, double* Iabs);
+cudaError_t propose(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
+                    uint32_t sweep, const double* x, const int* alive, double* xprop);
+cudaError_t accept(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
+                   uint32_t sweep, const double2* logdet_prop, const double* xprop, const double* Phiprop,
+                   const int* alive, double2* logov_cur, double* x, double* Phi, unsigned long long* counters);
+cudaError_t combine_logdet(cudaStream_t s, long long pairs, const double2* logdet, double2* logov);
+cudaError_t handoff(cudaStream_t s, const Dims& d, const StepParams& p, const double2* logov_cur,
+                    const double2* old_sum, const double2* ratio, const double* Iabs, const int* alive,
+                    double* weight, int* status);
+cudaError_t step_end(cudaStream_t s, const StepParams& p, const double* measured3, double* history,
+                     unsigned long long* counters);
+cudaError_t set_value(cudaStream_t s, double* out, long long n, double v);
+cudaError_t set_int(cudaStream_t s, int* out, long long n, int v);
+
+}  // namespace afq

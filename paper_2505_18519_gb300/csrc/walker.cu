@@ -1,0 +1,502 @@
+// Per-walker kernels of the leapfrog step (Sec. III A; Appendix B.2):
+// path-sign averages (Eq. (25)-(27)), the mixed estimator (Eq. (16)), fields
+// and force bias (Eq. (4), (15)), propagation B(x - xbar) (Eq. (5), (12)), the
+// importance function (Eq. (14)), Metropolis proposals and acceptance of the
+// paths (Eq. (23)), and the hand-off constraint (Eq. (17), (28)-(29)).
+#include "kernels.cuh"
+
+namespace afq {
+
+__device__ __forceinline__ uint32_t step_of(const unsigned long long* ctr) { return (uint32_t)ctr[0]; }
+
+// ---------------------------------------------------------------- random draws
+// out[r * cols + k] = normal number k of draw (tag, step, entity r, sweep).
+__global__ void fill_normals_kernel(double* out, long long rows, int cols, uint64_t seed, uint32_t tag,
+                                    const unsigned long long* ctr, uint32_t sweep) {
+    int blocks_per_row = (cols + 1) / 2;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * blocks_per_row) return;
+    long long r = t / blocks_per_row;
+    int j = (int)(t - r * blocks_per_row);
+    double2 z = normal_pair(seed, tag, step_of(ctr), (uint32_t)r, sweep, (uint32_t)j);
+    out[r * cols + 2 * j] = z.x;
+    if (2 * j + 1 < cols) out[r * cols + 2 * j + 1] = z.y;
+}
+
+cudaError_t fill_normals(cudaStream_t s, double* out, long long rows, int cols, uint64_t seed, uint32_t tag,
+                         const unsigned long long* ctr, uint32_t sweep) {
+    long long n = rows * ((cols + 1) / 2);
+    if (n <= 0) return cudaSuccess;
+    fill_normals_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, rows, cols, seed, tag, ctr, sweep);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- initial walkers
+// phi_w = Phi(x_w) for both spins (spin down: first n_dn columns), as complex.
+__global__ void walkers_from_trial_kernel(int N, int nu, int nd, const double* __restrict__ Phi_w, double2* phi) {
+    long long w = blockIdx.x;
+    int nt = nu + nd;
+    for (int e = threadIdx.x; e < N * nt; e += blockDim.x) {
+        int i = e / nt, c = e - i * nt;
+        int src = c < nu ? c : c - nu;
+        phi[w * (long long)N * nt + e] = cmk(Phi_w[w * (long long)N * nu + (long long)i * nu + src], 0.0);
+    }
+}
+
+cudaError_t walkers_from_trial(cudaStream_t s, const Dims& d, const double* Phi_w, double2* phi) {
+    walkers_from_trial_kernel<<<d.W, 128, 0, s>>>(d.N, d.nu, d.nd, Phi_w, phi);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- block reductions
+template <int NT>
+__device__ __forceinline__ double2 bsum2(double2 v, double2* red) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+    }
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = (lane < NT / 32) ? red[lane] : cmk(0.0, 0.0);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+        }
+        if (lane == 0) red[0] = v;
+    }
+    __syncthreads();
+    double2 r = red[0];
+    __syncthreads();
+    return r;   // every thread
+}
+
+// ---------------------------------------------------------------- path-sign averages
+// logov_p = log det(up) + log det(down); S_p = exp(i Im logov_p) (Eq. (26));
+// vbar_g = sum_p S_p v_pg / sum_p S_p and ebar = sum_p S_p E_p / sum_p S_p (Eq. (27)).
+// The sums over p run in order p = 0..P-1 (deterministic).
+__global__ void __launch_bounds__(256) walker_average_kernel(int P, int G, const double2* __restrict__ logdet,
+                                                             const double2* __restrict__ vpair, const double2* __restrict__ epair,
+                                                             double2* logov, double2* sumS_out, double2* vbar, double2* ebar) {
+    extern __shared__ double2 sS[];   // P path signs
+    long long w = blockIdx.x;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        long long pair = w * P + p;
+        double2 lo = cadd(logdet[2 * pair], logdet[2 * pair + 1]);
+        logov[pair] = lo;
+        double s, c;
+        sincos(lo.y, &s, &c);
+        sS[p] = cmk(c, s);
+    }
+    __syncthreads();
+    double2 sumS = cmk(0.0, 0.0), se = cmk(0.0, 0.0);
+    for (int p = 0; p < P; ++p) {
+        sumS = cadd(sumS, sS[p]);
+        se = cadd(se, cmul(sS[p], epair[w * P + p]));
+    }
+    double2 inv = cdiv(cmk(1.0, 0.0), sumS);
+    if (threadIdx.x == 0) {
+        sumS_out[w] = sumS;
+        ebar[w] = cmul(se, inv);
+    }
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        double2 sv = cmk(0.0, 0.0);
+        for (int p = 0; p < P; ++p) cfma(sv, sS[p], vpair[(w * P + p) * (long long)G + g]);
+        vbar[w * (long long)G + g] = cmul(sv, inv);
+    }
+}
+
+cudaError_t walker_average(cudaStream_t s, const Dims& d, const double2* logdet, const double2* vpair,
+                           const double2* epair, double2* logov, double2* sumS, double2* vbar, double2* ebar) {
+    walker_average_kernel<<<d.W, 256, d.P * sizeof(double2), s>>>(d.P, d.G, logdet, vpair, epair, logov, sumS, vbar, ebar);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- mixed estimator
+// out3 = {sum_w W_w Re ebar_w, sum_w W_w, sum_w W_w |sum_p S_p| / P} over W_w > 0,
+// one block, fixed-order tree reduction.
+__global__ void __launch_bounds__(1024) energy_reduce_kernel(int W, int P, const double* __restrict__ weight,
+                                                             const double2* __restrict__ ebar, const double2* __restrict__ sumS,
+                                                             double* out3) {
+    __shared__ double r0[1024], r1[1024], r2[1024];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        double wt = weight[w];
+        if (wt > 0.0) {
+            a += wt * ebar[w].x;
+            b += wt;
+            c += wt * cabs_(sumS[w]) / P;
+        }
+    }
+    r0[threadIdx.x] = a; r1[threadIdx.x] = b; r2[threadIdx.x] = c;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            r0[threadIdx.x] += r0[threadIdx.x + off];
+            r1[threadIdx.x] += r1[threadIdx.x + off];
+            r2[threadIdx.x] += r2[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out3[0] = r0[0]; out3[1] = r1[0]; out3[2] = r2[0]; }
+}
+
+cudaError_t energy_reduce(cudaStream_t s, const Dims& d, const double* weight, const double2* ebar,
+                          const double2* sumS, double* out3) {
+    energy_reduce_kernel<<<1, 1024, 0, s>>>(d.W, d.P, weight, ebar, sumS, out3);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fields and force bias
+// Walkers with W = 0 or |sum_p S_p| <= threshold are dead (W = 0) and frozen.
+// xi_g ~ N(0,1) (Philox, tag FIELD, entity w); xbar_g = -i sqrt(tau) vbar_g;
+// y = xi - xbar written as planes (row 2w: Re y, row 2w+1: Im y);
+// logshift = sum_g (xi_g xbar_g - xbar_g^2 / 2), the log of p(x - xbar)/p(x).
+__global__ void __launch_bounds__(256) fields_kernel(int G, uint64_t seed, double dtau, double thr,
+                                                     const unsigned long long* ctr, const double2* __restrict__ vbar,
+                                                     const double2* __restrict__ sumS, double* weight, int* alive,
+                                                     double* yplanes, double2* logshift) {
+    __shared__ double2 red[8];
+    long long w = blockIdx.x;
+    bool live = weight[w] > 0.0 && cabs_(sumS[w]) > thr;
+    double* yre = yplanes + (2 * w) * (long long)G;
+    double* yim = yre + G;
+    if (!live) {
+        for (int g = threadIdx.x; g < G; g += blockDim.x) { yre[g] = 0.0; yim[g] = 0.0; }
+        if (threadIdx.x == 0) { weight[w] = 0.0; alive[w] = 0; logshift[w] = cmk(0.0, 0.0); }
+        return;
+    }
+    uint32_t step = step_of(ctr);
+    double st = sqrt(dtau);
+    double2 acc = cmk(0.0, 0.0);
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        double xi = normal_at(seed, TAG_FIELD, step, (uint32_t)w, 0, (uint32_t)g);
+        double2 v = vbar[w * (long long)G + g];
+        double2 xb = cmk(st * v.y, -st * v.x);          // -i sqrt(tau) v
+        yre[g] = xi - xb.x;
+        yim[g] = -xb.y;
+        double2 xb2 = cmul(xb, xb);
+        acc.x += xi * xb.x - 0.5 * xb2.x;
+        acc.y += xi * xb.y - 0.5 * xb2.y;
+    }
+    double2 tot = bsum2<256>(acc, red);
+    if (threadIdx.x == 0) { alive[w] = 1; logshift[w] = tot; }
+}
+
+cudaError_t fields(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr,
+                   const double2* vbar, const double2* sumS, double* weight, int* alive, double* yplanes,
+                   double2* logshift) {
+    fields_kernel<<<d.W, 256, 0, s>>>(d.G, p.seed, p.dtau, p.kill_threshold, ctr, vbar, sumS, weight, alive, yplanes,
+                                      logshift);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- propagation
+// phi' = E (sum_{m<=order} A^m / m!) E phi with E = exp(-tau T/2) and
+// A = i sqrt(tau) sum_g y_g L_g = -sqrt(tau) Q + i sqrt(tau) P, where
+// P = sum_g Re(y_g) L_g, Q = sum_g Im(y_g) L_g (rows 2w, 2w+1 of Aplanes).
+// One block per walker, both spins at once (N x nt complex); the running sum
+// is kept in phi_new (global) and the current term in shared memory.
+__global__ void __launch_bounds__(256) propagate_kernel(int N, int nt, int order, double dtau, const double* __restrict__ E,
+                                                        const double* __restrict__ Aplanes, const double2* __restrict__ phi,
+                                                        double2* phi_new, const int* __restrict__ alive) {
+    extern __shared__ double2 sv[];
+    double2* V = sv;                       // N x nt
+    double2* Wt = sv + (size_t)N * nt;     // N x nt
+    long long w = blockIdx.x;
+    const double2* in = phi + w * (long long)N * nt;
+    double2* acc = phi_new + w * (long long)N * nt;
+    int nn = N * nt;
+    if (!alive[w]) {
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) acc[e] = in[e];
+        return;
+    }
+    const double* Pm = Aplanes + (2 * w) * (long long)N * N;
+    const double* Qm = Pm + (long long)N * N;
+    double st = sqrt(dtau);
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) V[e] = in[e];
+    __syncthreads();
+    // V <- E V ; acc <- V
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        int i = e / nt, c = e - i * nt;
+        double2 s = cmk(0.0, 0.0);
+        for (int j = 0; j < N; ++j) {
+            double ev = E[(long long)i * N + j];
+            double2 v = V[j * nt + c];
+            s.x = fma(ev, v.x, s.x);
+            s.y = fma(ev, v.y, s.y);
+        }
+        Wt[e] = s;
+        acc[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) V[e] = Wt[e];
+    __syncthreads();
+    for (int m = 1; m <= order; ++m) {
+        double inv = 1.0 / m;
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            int i = e / nt, c = e - i * nt;
+            double pr = 0.0, pi = 0.0, qr = 0.0, qi = 0.0;   // (P V), (Q V)
+            for (int j = 0; j < N; ++j) {
+                double pv = Pm[(long long)i * N + j], qv = Qm[(long long)i * N + j];
+                double2 v = V[j * nt + c];
+                pr = fma(pv, v.x, pr); pi = fma(pv, v.y, pi);
+                qr = fma(qv, v.x, qr); qi = fma(qv, v.y, qi);
+            }
+            // A V = (-st Q + i st P) V
+            double2 t = cmk(st * (-qr - pi) * inv, st * (-qi + pr) * inv);
+            Wt[e] = t;
+            acc[e] = cadd(acc[e], t);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) V[e] = Wt[e];
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) V[e] = acc[e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        int i = e / nt, c = e - i * nt;
+        double2 s = cmk(0.0, 0.0);
+        for (int j = 0; j < N; ++j) {
+            double ev = E[(long long)i * N + j];
+            double2 v = V[j * nt + c];
+            s.x = fma(ev, v.x, s.x);
+            s.y = fma(ev, v.y, s.y);
+        }
+        acc[e] = s;
+    }
+}
+
+cudaError_t propagate(cudaStream_t s, const Dims& d, const StepParams& p, const double* expT, const double* Aplanes,
+                      const double2* phi, double2* phi_new, const int* alive) {
+    size_t smem = 2 * (size_t)d.N * d.nt * sizeof(double2);
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    propagate_kernel<<<d.W, 256, smem, s>>>(d.N, d.nt, p.taylor_order, p.dtau, expT, Aplanes, phi, phi_new, alive);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- overlap ratio and importance function
+// For live walkers: logov'_p at phi' of the current paths; the sampled-trial
+// ratio (Eq. (25)) = sum_p S_p exp(logov'_p - logov_p) / sum_p S_p, and
+// |I| = |exp(logshift) * ratio| (Eq. (14)).
+__global__ void __launch_bounds__(128) ratios_walker_kernel(int P, const double2* __restrict__ logov,
+                                                            const double2* __restrict__ logdet_new,
+                                                            const double2* __restrict__ sumS,
+                                                            const double2* __restrict__ logshift,
+                                                            const int* __restrict__ alive, double2* logov_cur,
+                                                            double2* old_sum, double2* ratio, double* Iabs) {
+    long long w = blockIdx.x;
+    if (!alive[w]) return;
+    __shared__ double2 terms[1024];
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        long long pair = w * P + p;
+        double2 lo = logov[pair];
+        double2 ln = cadd(logdet_new[2 * pair], logdet_new[2 * pair + 1]);
+        logov_cur[pair] = ln;
+        double s, c;
+        sincos(lo.y, &s, &c);
+        terms[p] = cmul(cmk(c, s), cexp_(csub(ln, lo)));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 os = cmk(0.0, 0.0);
+        for (int p = 0; p < P; ++p) os = cadd(os, terms[p]);
+        double2 r = cdiv(os, sumS[w]);
+        old_sum[w] = os;
+        ratio[w] = r;
+        double2 I = cmul(cexp_(logshift[w]), r);
+        Iabs[w] = cabs_(I);
+    }
+}
+
+cudaError_t ratios(cudaStream_t s, const Dims& d, const double2* logov, const double2* logdet_new,
+                   const double2* sumS, const double2* logshift, const int* alive, double2* logov_cur,
+                   double2* old_sum, double2* ratio, double* Iabs) {
+    if (d.P > 1024) return cudaErrorInvalidValue;
+    ratios_walker_kernel<<<d.W, 128, 0, s>>>(d.P, logov, logdet_new, sumS, logshift, alive, logov_cur, old_sum, ratio,
+                                             Iabs);
+    return cudaGetLastError();
+}
+
+// logov = sum over spins of logdet (used at init, before the burn-in sweeps).
+__global__ void combine_logdet_kernel(long long pairs, const double2* __restrict__ logdet, double2* logov) {
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < pairs) logov[p] = cadd(logdet[2 * p], logdet[2 * p + 1]);
+}
+
+cudaError_t combine_logdet(cudaStream_t s, long long pairs, const double2* logdet, double2* logov) {
+    combine_logdet_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(pairs, logdet, logov);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Metropolis on the paths
+// Proposal for pair q: prior x' = xi, or pCN x' = sqrt(1 - beta^2) x + beta xi,
+// xi ~ N(0, I) (Philox, tag PROPOSE or BURN_PROPOSE, entity q, this sweep).
+__global__ void propose_kernel(long long pairs, int P, int K, uint64_t seed, uint32_t tag, uint32_t sweep,
+                               const unsigned long long* ctr, int proposal, double beta, const double* __restrict__ x,
+                               const int* __restrict__ alive, double* xprop) {
+    int bpr = (K + 1) / 2;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= pairs * bpr) return;
+    long long q = t / bpr;
+    int j = (int)(t - q * bpr);
+    double* out = xprop + q * K;
+    if (!alive[q / P]) {
+        out[2 * j] = 0.0;
+        if (2 * j + 1 < K) out[2 * j + 1] = 0.0;
+        return;
+    }
+    double2 z = normal_pair(seed, tag, step_of(ctr), (uint32_t)q, sweep, (uint32_t)j);
+    if (proposal == AFQMC_PROPOSAL_PCN) {
+        double a = sqrt(1.0 - beta * beta);
+        const double* xo = x + q * K;
+        z.x = fma(a, xo[2 * j], beta * z.x);
+        if (2 * j + 1 < K) z.y = fma(a, xo[2 * j + 1], beta * z.y);
+    }
+    out[2 * j] = z.x;
+    if (2 * j + 1 < K) out[2 * j + 1] = z.y;
+}
+
+cudaError_t propose(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
+                    uint32_t sweep, const double* x, const int* alive, double* xprop) {
+    long long n = d.pairs * ((d.K + 1) / 2);
+    propose_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d.pairs, d.P, d.K, p.seed, tag, sweep, ctr, p.proposal,
+                                                               p.pcn_beta, x, alive, xprop);
+    return cudaGetLastError();
+}
+
+// Accept iff Re(logov'' - logov') >= 0 or u < exp(Re(logov'' - logov')) with
+// u the first 53-bit uniform of (tag, step, pair, sweep); on acceptance copy
+// x', Phi(x') and logov'' into the path.  One block per pair.
+__global__ void __launch_bounds__(128) accept_kernel(int N, int nu, int K, int P, uint64_t seed, uint32_t tag,
+                                                     uint32_t sweep, const unsigned long long* ctr,
+                                                     const double2* __restrict__ logdet_prop,
+                                                     const double* __restrict__ xprop, const double* __restrict__ Phiprop,
+                                                     const int* __restrict__ alive, double2* logov_cur, double* x,
+                                                     double* Phi, unsigned long long* counters) {
+    long long q = blockIdx.x;
+    if (!alive[q / P]) return;
+    __shared__ int acc;
+    if (threadIdx.x == 0) {
+        double2 ln = cadd(logdet_prop[2 * q], logdet_prop[2 * q + 1]);
+        double delta = ln.x - logov_cur[q].x;
+        double u = uniform_at0(seed, tag, step_of(ctr), (uint32_t)q, sweep);
+        int a = (delta >= 0.0) || (u < exp(delta));
+        acc = a;
+        if (a) {
+            logov_cur[q] = ln;
+            atomicAdd(&counters[3], 1ull);
+        }
+        atomicAdd(&counters[4], 1ull);
+    }
+    __syncthreads();
+    if (!acc) return;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) x[q * K + k] = xprop[q * K + k];
+    long long nn = (long long)N * nu;
+    for (long long e = threadIdx.x; e < nn; e += blockDim.x) Phi[q * nn + e] = Phiprop[q * nn + e];
+}
+
+cudaError_t accept(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
+                   uint32_t sweep, const double2* logdet_prop, const double* xprop, const double* Phiprop,
+                   const int* alive, double2* logov_cur, double* x, double* Phi, unsigned long long* counters) {
+    accept_kernel<<<(unsigned)d.pairs, 128, 0, s>>>(d.N, d.nu, d.K, d.P, p.seed, tag, sweep, ctr, logdet_prop, xprop,
+                                                    Phiprop, alive, logov_cur, x, Phi, counters);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- hand-off constraint
+// dtheta = Arg ratio; dtheta_T = Arg sum_p S'_p - Arg old_sum (Eq. (28)), then
+// combined:   W *= |I| max(0, cos(dtheta + dtheta_T))
+// separate:   W *= |I| max(0, cos dtheta) max(0, cos dtheta_T)
+// half-plane: W *= |I| max(0, cos dtheta) [|wrap(dtheta_T)| <= pi/2]
+// and W *= exp(tau E_T).  Non-finite weights become 0.  One warp per walker.
+__global__ void handoff_kernel(int W, int P, int constraint, double dtau, double e_shift,
+                               const double2* __restrict__ logov_cur, const double2* __restrict__ old_sum,
+                               const double2* __restrict__ ratio, const double* __restrict__ Iabs,
+                               const int* __restrict__ alive, double* weight, int* status) {
+    long long w = blockIdx.x;
+    if (!alive[w]) return;
+    int lane = threadIdx.x;
+    // fixed-order sum over paths: lane 0 adds sequentially for bitwise determinism
+    if (lane != 0) return;
+    double2 ns = cmk(0.0, 0.0);
+    for (int p = 0; p < P; ++p) {
+        double s, c;
+        sincos(logov_cur[w * P + p].y, &s, &c);
+        ns = cadd(ns, cmk(c, s));
+    }
+    double dth = atan2(ratio[w].y, ratio[w].x);
+    double dthT = atan2(ns.y, ns.x) - atan2(old_sum[w].y, old_sum[w].x);
+    double f;
+    if (constraint == AFQMC_CONSTRAINT_COMBINED) {
+        f = fmax(0.0, cos(dth + dthT));
+    } else if (constraint == AFQMC_CONSTRAINT_SEPARATE) {
+        f = fmax(0.0, cos(dth)) * fmax(0.0, cos(dthT));
+    } else {
+        double wr = atan2(sin(dthT), cos(dthT));
+        f = fmax(0.0, cos(dth)) * (fabs(wr) <= 0.5 * M_PI ? 1.0 : 0.0);
+    }
+    double wn = weight[w] * Iabs[w] * f * exp(dtau * e_shift);
+    if (!isfinite(wn)) {
+        wn = 0.0;
+        atomicOr(status, STATUS_NONFINITE);
+    }
+    weight[w] = wn;
+}
+
+cudaError_t handoff(cudaStream_t s, const Dims& d, const StepParams& p, const double2* logov_cur,
+                    const double2* old_sum, const double2* ratio, const double* Iabs, const int* alive,
+                    double* weight, int* status) {
+    handoff_kernel<<<d.W, 32, 0, s>>>(d.W, d.P, p.constraint, p.dtau, p.e_shift, logov_cur, old_sum, ratio, Iabs, alive,
+                                      weight, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- step bookkeeping
+// counters: [0] steps taken, [1] accepted total, [2] proposed total,
+// [3] accepted this step, [4] proposed this step.
+__global__ void step_end_kernel(int cap, const double* measured3, double* history, unsigned long long* counters) {
+    unsigned long long st = counters[0];
+    double* rec = history + 4 * (st % (unsigned long long)cap);
+    rec[0] = measured3[0];
+    rec[1] = measured3[1];
+    rec[2] = measured3[2];
+    rec[3] = (double)counters[3];
+    counters[1] += counters[3];
+    counters[2] += counters[4];
+    counters[3] = 0;
+    counters[4] = 0;
+    counters[0] = st + 1;
+}
+
+cudaError_t step_end(cudaStream_t s, const StepParams& p, const double* measured3, double* history,
+                     unsigned long long* counters) {
+    step_end_kernel<<<1, 1, 0, s>>>(p.history_capacity, measured3, history, counters);
+    return cudaGetLastError();
+}
+
+__global__ void set_value_kernel(double* out, long long n, double v) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = v;
+}
+__global__ void set_int_kernel(int* out, long long n, int v) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = v;
+}
+cudaError_t set_value(cudaStream_t s, double* out, long long n, double v) {
+    if (n > 0) set_value_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, v);
+    return cudaGetLastError();
+}
+cudaError_t set_int(cudaStream_t s, int* out, long long n, int v) {
+    if (n > 0) set_int_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, v);
+    return cudaGetLastError();
+}
+
+}  // namespace afq

@@ -1,0 +1,69 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every entry point the header declares, validates
+configurations, and the state-buffer marshalling round-trips."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2505_18519_gb300 import afqmc as lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2505_18519_gb300 import build
+    build.build()
+    return lib.load_library()
+
+
+def test_exports_every_declared_symbol(L):
+    header = open(os.path.join(ROOT, "include", "afqmc.h")).read()
+    declared = set(re.findall(r"\b(afqmc_[a-z_0-9]+)\s*\(", header))
+    assert "afqmc_init" in declared and "afqmc_step" in declared and "afqmc_energy" in declared
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared >= set(lib.EXPORTS)
+
+
+def test_config_validation(L):
+    good = lib.make_config(8, 4, 4, 32, 8, 64, 16, 0.01, 1)
+    assert lib.workspace_bytes(good) > 0
+    for field, bad in (("N", 0), ("n_up", 0), ("n_dn", 5), ("n_paths", 0), ("dtau", 0.0), ("taylor_order", 0),
+                       ("constraint", 7), ("precision", 9), ("n_chol", 0)):
+        c = lib.make_config(8, 4, 4, 32, 8, 64, 16, 0.01, 1)
+        setattr(c, field, bad)
+        assert lib.workspace_bytes(c) == 0, field
+
+
+def test_init_rejects_bad_workspace_without_touching_a_gpu(L):
+    c = lib.make_config(8, 4, 4, 32, 8, 4, 2, 0.01, 1)
+    out = ctypes.c_void_p()
+    h = np.zeros((8, 8))
+    st = L.afqmc_init(ctypes.byref(c), h.ctypes.data, h.ctypes.data, h.ctypes.data, h.ctypes.data, None, 0, None,
+                      ctypes.byref(out))
+    assert st == 3 and out.value is None                     # AFQMC_ERR_WORKSPACE
+    st = L.afqmc_init(None, None, None, None, None, None, 0, None, ctypes.byref(out))
+    assert st == 1 and b"NULL" in L.afqmc_last_error()      # AFQMC_ERR_ARG
+
+
+def test_workspace_grows_with_walkers(L):
+    a = lib.workspace_bytes(lib.make_config(50, 10, 10, 250, 50, 16, 32, 0.005, 1))
+    b = lib.workspace_bytes(lib.make_config(50, 10, 10, 250, 50, 32, 32, 0.005, 1))
+    assert b > a and a % 256 == 0
+
+
+def test_state_pack_roundtrip():
+    rng = np.random.default_rng(0)
+    W, P, N, nu, nd, K = 3, 2, 5, 3, 2, 4
+    st = dict(step=7, phi_up=rng.normal(size=(W, N, nu)) + 1j * rng.normal(size=(W, N, nu)),
+              phi_dn=rng.normal(size=(W, N, nd)) + 1j * rng.normal(size=(W, N, nd)),
+              weight=rng.random(W), x=rng.normal(size=(W, P, K)), Phi=rng.normal(size=(W, P, N, nu)))
+    back = lib.unpack_state(lib.pack_state(st))
+    assert back["step"] == 7
+    for k in ("phi_up", "phi_dn", "weight", "x", "Phi"):
+        assert np.array_equal(back[k], st[k]), k
