@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the sampled-trial phaseless AFQMC step on GB300.
+
+Metric: walker-sample steps per second including the local energy, i.e.
+(walkers x paths x steps) / device time, with every step running the whole
+leapfrog (overlaps, contraction for force bias and local energy, path
+averages and mixed estimator, fields, propagation, ratios, Metropolis path
+updates, hand-off constraint, re-orthonormalisation).
+
+Workload: the medium FP64 synthetic molecule -- N = 50 orbitals, 10 + 10
+electrons, 250 Cholesky vectors, 50 hidden variables, 512 walkers x 32 paths,
+tau = 0.005, one Metropolis sweep per step, synthetic inputs from
+afqmc_inputs (seed 1001).  With --gpus N (torchrun) every rank runs its own
+block of 512 walkers of one population (weak scaling).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "c1_n50"
+METRIC = "walker-sample steps/s incl. local energy"
+UNIT = "walker-sample steps/s"
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 4 FP64 flop/clk
+# (2 DFMA) x 2070 MHz.
+FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+L2_BYTES = 129e6
+
+
+def workload_desc(spec, run):
+    return (f"{WORKLOAD}: medium FP64 synthetic molecule, N={spec.N} orbitals, {spec.n_up}+{spec.n_dn} electrons, "
+            f"{spec.n_chol} Cholesky vectors, K={spec.K} hidden variables, {run.n_walkers} walkers x "
+            f"{run.n_paths} paths per GPU, tau={run.dtau}, 1 Metropolis sweep/step")
+
+
+def contract_flops_per_pair(spec):
+    """Algorithmic FLOPs of the fused contraction for one (walker, path) pair:
+    R = Phi^T X (X = h and every L_g): 2 n_up N^2 each; M_s = R Theta_s
+    (real x complex): 4 N n_s^2 each; exchange traces Tr(M M): 8 n_s^2 per g."""
+    N, nu, nd, G = spec.N, spec.n_up, spec.n_dn, spec.n_chol
+    return (G + 1) * 2 * nu * N * N + (G + 1) * 4 * N * (nu * nu + nd * nd) + G * 8 * (nu * nu + nd * nd)
+
+
+def step_working_set_bytes(spec, run):
+    N, nt, nu, G, K = spec.N, spec.n_up + spec.n_dn, spec.n_up, spec.n_chol, spec.K
+    pairs = run.n_walkers * run.n_paths
+    return pairs * (N * nt * 16 + N * nu * 8 * 3 + N * N * 8 + G * 16 + K * 16)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle (CPU) legs
+def _oracle_walker_job(args):
+    """Run in a spawned process: the oracle's own step on one walker of the
+    workload.  With ``state`` given, one timed step from that state; otherwise
+    the walker is initialised by the oracle and ``n_warm`` + ``n_timed`` steps
+    run, the last ``n_timed`` timed.  Returns the list of timed step seconds."""
+    state, widx, n_warm, n_timed = args
+    import numpy as np
+    import afqmc_inputs as ai
+    from oracle import afqmc as oa
+    spec, run = ai.CONFIGS[WORKLOAD]
+    s = ai.make_system(spec)
+    ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, run.dtau)
+    cfg = oa.OracleConfig(dtau=run.dtau, n_walkers=1, n_paths=run.n_paths, seed=ai.philox_run_seed(1))
+    if state is None:
+        st = oa.init(ham, cfg, walker_index=np.array([widx]))
+    else:
+        st = oa.State(state["step"], state["phi_up"], state["phi_dn"], state["weight"], state["x"], state["Phi"],
+                      walker_index=np.array([widx]))
+    times = []
+    for k in range(n_warm + n_timed):
+        t0 = time.perf_counter()
+        st, _ = oa.step(ham, cfg, st)
+        if k >= n_warm:
+            times.append(time.perf_counter() - t0)
+    return times
+
+
+def oracle_pool_steps(n_walkers, states, n_warm, n_timed, spread):
+    """Run the oracle on ``n_walkers`` walkers of the workload, one walker per
+    spawned process, all at once; returns (per-step wall seconds, processes)."""
+    import multiprocessing as mp
+    procs = min(n_walkers, os.cpu_count() or 1)
+    # one BLAS thread per process (set before the spawned children import numpy)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    jobs = []
+    for i in range(n_walkers):
+        widx = i * spread
+        st = None if states is None else states[i]
+        jobs.append((st, widx, n_warm, n_timed))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_oracle_walker_job, jobs)
+    # walkers run concurrently: a step's wall time is the slowest walker's, per round of `procs` walkers
+    rounds = math.ceil(n_walkers / procs)
+    per_step = [max(r[k] for r in res) * rounds for k in range(n_timed)]
+    return per_step, procs
+
+
+def cpu_baseline_leg(gpu_state, run):
+    """The oracle, as it stands, on a bounded sample: one step of 16 walkers of
+    the same workload from the GPU's state, one walker per process."""
+    import numpy as np
+    n = 16
+    spread = run.n_walkers // n
+    states = []
+    for i in range(n):
+        w = i * spread
+        states.append(dict(step=gpu_state["step"], phi_up=gpu_state["phi_up"][w:w + 1],
+                           phi_dn=gpu_state["phi_dn"][w:w + 1], weight=gpu_state["weight"][w:w + 1],
+                           x=gpu_state["x"][w:w + 1], Phi=gpu_state["Phi"][w:w + 1]))
+    per_step, procs = oracle_pool_steps(n, states, 0, 1, spread)
+    value = n * run.n_paths / per_step[0]
+    return {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"1 step of {n} of the {run.n_walkers} walkers (x{run.n_paths} paths each) of {WORKLOAD}, "
+                      f"from the GPU run's state, one walker per process, {procs} processes"}
+
+
+def reference_arm(args):
+    import afqmc_inputs as ai
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec, run = ai.CONFIGS[WORKLOAD]
+    n = 16
+    per_step, procs = oracle_pool_steps(n, None, args.warmup, args.steps, run.n_walkers // n)
+    total = sum(per_step)
+    value = n * run.n_paths * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(spec, run)},
+            "cpu_baseline": {"kind": "oracle", "cores": procs, "value": value, "unit": UNIT,
+                             "sample": f"each step: {n} of the {run.n_walkers} walkers (x{run.n_paths} paths), "
+                                       f"oracle-initialised, one walker per process, {procs} processes"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ traffic of the dominant kernel
+def recorded_traffic(kernel_source: str):
+    """DRAM bytes per launch of the contraction from the committed ncu summary,
+    or None if the kernel's source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "contract_fp64_c1_n50.md")
+    if not os.path.exists(path):
+        return None
+    digest = hashlib.sha256(open(kernel_source, "rb").read()).hexdigest()[:16]
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("source_sha256_16") != digest:
+        return None
+    try:
+        return float(fields["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ our arm
+def our_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import afqmc_inputs as ai
+    from paper_2505_18519_gb300 import afqmc as lib
+    from paper_2505_18519_gb300 import build
+    from paper_2505_18519_gb300.sharding import max_over_ranks
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    lib.load_library()
+
+    spec, run = ai.CONFIGS[WORKLOAD]
+    if args.walkers:
+        import dataclasses
+        run = dataclasses.replace(run, n_walkers=args.walkers)
+    s = ai.make_system(spec)
+    W, P = run.n_walkers, run.n_paths
+    seed = ai.philox_run_seed(1)
+    cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
+                          walker_offset=rank * W, e_shift=28.5)
+    with torch.cuda.device(dev):
+        ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
+        stream = ctx.stream
+        for _ in range(args.warmup):
+            ctx.step(1)
+        torch.cuda.synchronize(dev)
+
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ctx.profile(True)
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            l0 = lib.launch_count()
+            e0.record(stream)
+            ctx.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            l1 = lib.launch_count()
+            if world > 1:
+                dist.barrier()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        ms = e0.elapsed_time(e1)
+        ms_max = max_over_ranks(ms)
+        clocks = clk.summary()
+        hist = ctx.history(args.steps)
+        gpu_state = ctx.state_arrays() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+
+        # end to end through the public API: host (pinned) inputs uploaded by
+        # afqmc_init inside the timed region, every step's energy record read back
+        host = [torch.from_numpy(a).pin_memory() for a in (s.h, s.L, s.Phi0, s.U)]
+        h2d = sum(t.numel() * 8 for t in host)
+        e2e_s = None
+        if not args.no_e2e:
+            torch.cuda.synchronize(dev)
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            ctx2 = lib.Context(cfg, *host, device=dev)
+            for _ in range(args.steps):
+                ctx2.step(1)
+                ctx2.history(1)
+            t1 = time.perf_counter()
+            e2e_s = max_over_ranks(t1 - t0)
+            ctx2.close()
+
+    pairs_total = W * P * world
+    value = pairs_total * args.steps / (ms_max / 1e3)
+    e2e_value = pairs_total * args.steps / e2e_s if e2e_s else None
+    contract_ms = prof["ms"]["contract"] / max(1, prof["launches"]["contract"])
+    flops = contract_flops_per_pair(spec) * W * P
+    achieved = flops / (contract_ms / 1e3) / 1e12
+    traffic = recorded_traffic(os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "contract_fp64.cu"))
+    phases = {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = cpu_baseline_leg(gpu_state, run) if gpu_state is not None else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(spec, run), "walkers_total": W * world, "paths": P,
+                   "system_seed": spec.seed, "philox_seed": seed,
+                   "l2": f"working set {step_working_set_bytes(spec, run) / 1e9:.2f} GB per step > 129 MB L2; no flush"},
+        "roofline": {"bound": "alu", "kernel": "contract_fp64_kernel", "achieved": achieved,
+                     "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
+                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (no FP64 figure measured by the driver)",
+                     "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": contract_ms},
+        "cpu_baseline": cpu,
+        "e2e": None if e2e_value is None else {
+            "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 32,
+            "includes": "afqmc_init from pinned host arrays (incl. 20 burn-in sweeps) + K steps, each followed by "
+                        "a device-to-host read of its energy record"},
+        "clocks": clocks, "gpu_launches": int(l1 - l0), "phases_ms_per_step": phases,
+        "mixed_energy_last_step": float(hist[-1, 0] / hist[-1, 1]) if len(hist) else None,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--walkers", type=int, default=0, help="walkers per GPU (profiling runs on a small case)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

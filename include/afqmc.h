@@ -92,6 +92,9 @@ typedef struct {
     double e_shift;     /* constant E_T: every step multiplies weights by exp(tau E_T) */
     double kill_threshold; /* a walker whose |sum_p S_p| is below this gets weight 0 */
     uint64_t seed;      /* key of the Philox4x32-10 streams */
+    int64_t walker_offset; /* global index of walker 0 in the random streams: walker w draws as
+                              walker walker_offset + w, so shards of one population on several
+                              GPUs reproduce the single-GPU run exactly */
 } afqmc_config;
 
 /* Fill *cfg with defaults (combined constraint, prior proposal, FP64, Taylor
@@ -167,6 +170,25 @@ afqmc_status afqmc_state_load(afqmc_ctx* ctx, const void* buf, size_t len);
 
 /* Release the context (not the caller's workspace). */
 void afqmc_destroy(afqmc_ctx* ctx);
+
+/* Phase timing of afqmc_step with CUDA events on the context's stream
+ * (recording does not synchronise).  afqmc_profile(ctx, 1) starts collecting,
+ * afqmc_profile(ctx, 0) stops.  afqmc_profile_read synchronises and writes
+ *   out[i]              milliseconds spent in phase i since the last read,
+ *   out[AFQMC_PHASES+i] kernel launches of phase i,
+ *   out[2*AFQMC_PHASES] steps profiled,
+ * then resets.  Phases, in step order: 0 overlaps, LU and Theta at phi;
+ * 1 fused contraction (force bias, local energy); 2 path-sign averages and the
+ * mixed-estimator sums; 3 fields and the auxiliary-field matrices;
+ * 4 propagation; 5 overlaps at phi' and ratios; 6 proposals and sum_k x_k U_k;
+ * 7 trial orbitals exp(S) Phi0; 8 proposal overlaps; 9 acceptance;
+ * 10 hand-off, re-orthonormalisation and bookkeeping. */
+#define AFQMC_PHASES 11
+afqmc_status afqmc_profile(afqmc_ctx* ctx, int enable);
+afqmc_status afqmc_profile_read(afqmc_ctx* ctx, double* out, int len);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t afqmc_launch_count(void);
 
 /* Message of the last error in this thread (static storage). */
 const char* afqmc_last_error(void);

@@ -267,17 +267,22 @@ def mcmc_sweep(ham: Hamiltonian, cfg: OracleConfig, st: State, logov_cur: np.nda
     return n_acc
 
 
-def init(ham: Hamiltonian, cfg: OracleConfig) -> State:
-    """Initial composite walkers (reading R11 of Appendix B.1)."""
+def init(ham: Hamiltonian, cfg: OracleConfig, walker_index=None) -> State:
+    """Initial composite walkers (reading R11 of Appendix B.1).  ``walker_index``
+    (default 0..W-1) gives the global walker numbers used in the random streams,
+    so a subset of a larger population can be rebuilt on its own."""
     W, P = cfg.n_walkers, cfg.n_paths
     K = ham.U.shape[0]
-    xw = px.normals(cfg.seed, px.TAG_INIT_WALKER, 0, np.arange(W), 0, K)
+    widx = np.arange(W) if walker_index is None else np.asarray(walker_index)
+    W = widx.size
+    xw = px.normals(cfg.seed, px.TAG_INIT_WALKER, 0, widx, 0, K)
     Phiw = trial_orbitals(ham, xw)                                   # (W, N, n_up)
     phi_up = reorthonormalise(Phiw.astype(np.complex128))
     phi_dn = reorthonormalise(Phiw[:, :, : ham.n_dn].astype(np.complex128))
-    x = px.normals(cfg.seed, px.TAG_INIT_PATH, 0, np.arange(W * P), 0, K).reshape(W, P, K)
+    pair_ids = (widx[:, None] * P + np.arange(P)[None, :]).reshape(-1)
+    x = px.normals(cfg.seed, px.TAG_INIT_PATH, 0, pair_ids, 0, K).reshape(W, P, K)
     Phi = trial_orbitals(ham, x)
-    st = State(0, phi_up, phi_dn, np.ones(W), x, Phi)
+    st = State(0, phi_up, phi_dn, np.ones(W), x, Phi, widx.copy())
     logov = np.empty((W, P), dtype=np.complex128)
     for w in range(W):
         for p in range(P):

@@ -31,7 +31,7 @@ class AfqmcConfig(ctypes.Structure):
         ("n_burn", ctypes.c_int), ("constraint", ctypes.c_int), ("proposal", ctypes.c_int),
         ("precision", ctypes.c_int), ("taylor_order", ctypes.c_int), ("history_capacity", ctypes.c_int),
         ("dtau", ctypes.c_double), ("pcn_beta", ctypes.c_double), ("e_shift", ctypes.c_double),
-        ("kill_threshold", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("kill_threshold", ctypes.c_double), ("seed", ctypes.c_uint64), ("walker_offset", ctypes.c_int64),
     ]
 
 
@@ -39,7 +39,11 @@ _lib = None
 
 EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc_step", "afqmc_energy",
            "afqmc_observables", "afqmc_history", "afqmc_stats", "afqmc_state_save", "afqmc_state_load",
-           "afqmc_destroy", "afqmc_last_error", "afqmc_philox_fill")
+           "afqmc_destroy", "afqmc_last_error", "afqmc_philox_fill", "afqmc_profile", "afqmc_profile_read",
+           "afqmc_launch_count")
+
+PHASES = ("overlap", "contract", "average", "fields", "propagate", "ratio", "propose", "trial_orbitals",
+          "mcmc_overlap", "accept", "finish")
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -79,6 +83,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.afqmc_philox_fill.argtypes = [P, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint32, U64, P]
     lib.afqmc_philox_fill.restype = I
+    lib.afqmc_profile.argtypes = [P, I]
+    lib.afqmc_profile.restype = I
+    lib.afqmc_profile_read.argtypes = [P, P, I]
+    lib.afqmc_profile_read.restype = I
+    lib.afqmc_launch_count.argtypes = []
+    lib.afqmc_launch_count.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -96,7 +106,7 @@ def _check(st: int):
 
 def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_sweeps=1, n_burn=20,
                 constraint="combined", proposal="prior", precision="fp64", taylor_order=6, history_capacity=1024,
-                pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10) -> AfqmcConfig:
+                pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10, walker_offset=0) -> AfqmcConfig:
     lib = load_library()
     c = AfqmcConfig()
     lib.afqmc_config_default(ctypes.byref(c))
@@ -105,6 +115,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
     c.constraint, c.proposal, c.precision = CONSTRAINTS[constraint], PROPOSALS[proposal], PRECISIONS[precision]
     c.taylor_order, c.history_capacity = taylor_order, history_capacity
     c.dtau, c.pcn_beta, c.e_shift, c.kill_threshold, c.seed = dtau, pcn_beta, e_shift, kill_threshold, seed
+    c.walker_offset = walker_offset
     return c
 
 
@@ -189,6 +200,17 @@ class Context:
         keys = ("steps", "accepted", "proposed", "live_walkers", "status", "min_weight", "max_weight", "sum_weight")
         return dict(zip(keys, out.tolist()))
 
+    # -- profiling ----------------------------------------------------------------
+    def profile(self, enable: bool = True):
+        _check(load_library().afqmc_profile(self._ctx, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        n = len(PHASES)
+        out = np.zeros(2 * n + 1)
+        _check(load_library().afqmc_profile_read(self._ctx, out.ctypes.data, out.size))
+        return dict(ms=dict(zip(PHASES, out[:n].tolist())), launches=dict(zip(PHASES, out[n:2 * n].astype(int).tolist())),
+                    steps=int(out[2 * n]))
+
     # -- checkpoint ---------------------------------------------------------------
     def save_state(self) -> bytes:
         lib = load_library()
@@ -217,6 +239,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load_library().afqmc_launch_count())
 
 
 def unpack_state(blob: bytes) -> dict:

@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "kernels.cuh"
 
 using namespace afq;
@@ -26,6 +28,83 @@ static afqmc_status fail(afqmc_status st, const char* fmt, ...) {
     } while (0)
 
 extern "C" const char* afqmc_last_error(void) { return g_err; }
+static std::atomic<long long> g_launches{0};
+void afq::count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+extern "C" int64_t afqmc_launch_count(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------- phase profiling
+// While enabled, afqmc_step records a CUDA event on the context's stream at
+// every phase boundary; afqmc_profile_read converts consecutive pairs into
+// per-phase milliseconds.  Recording events does not synchronise the stream.
+static long long g_mark_launches = 0;
+
+static afqmc_status prof_flush(afqmc_ctx* ctx) {
+    if (ctx->prof_used == 0) return AFQMC_OK;
+    CK(cudaEventSynchronize(ctx->prof_events[ctx->prof_used - 1]));
+    for (int i = 1; i < ctx->prof_used; ++i) {
+        int ph = ctx->prof_phase[i];
+        if (ph < 0) continue;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->prof_events[i - 1], ctx->prof_events[i]));
+        ctx->prof_ms[ph] += ms;
+    }
+    ctx->prof_used = 0;
+    return AFQMC_OK;
+}
+
+// phase >= 0: the phase that ends here; phase < 0: a step starts here.
+static afqmc_status prof_mark(afqmc_ctx* ctx, int phase) {
+    if (!ctx->profiling) return AFQMC_OK;
+    long long now = g_launches.load();
+    if (phase >= 0) ctx->prof_launches[phase] += now - g_mark_launches;
+    g_mark_launches = now;
+    if (ctx->prof_used == ctx->prof_cap) {
+        afqmc_status st = prof_flush(ctx);
+        if (st != AFQMC_OK) return st;
+        if (phase >= 0) {   // keep the boundary: re-record the start of this phase is lost, so restart at a step mark
+            phase = -1;
+        }
+    }
+    CK(cudaEventRecord(ctx->prof_events[ctx->prof_used], ctx->stream));
+    ctx->prof_phase[ctx->prof_used] = phase;
+    ctx->prof_used++;
+    return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_profile(afqmc_ctx* ctx, int enable) {
+    if (!ctx) return fail(AFQMC_ERR_ARG, "ctx is NULL");
+    if (enable && !ctx->prof_events) {
+        ctx->prof_cap = 256 * (PH_COUNT + 1);
+        ctx->prof_events = (cudaEvent_t*)calloc(ctx->prof_cap, sizeof(cudaEvent_t));
+        ctx->prof_phase = (int*)calloc(ctx->prof_cap, sizeof(int));
+        if (!ctx->prof_events || !ctx->prof_phase) return fail(AFQMC_ERR_ARG, "out of host memory");
+        for (int i = 0; i < ctx->prof_cap; ++i) CK(cudaEventCreate(&ctx->prof_events[i]));
+    }
+    if (!enable) {
+        afqmc_status st = prof_flush(ctx);
+        if (st != AFQMC_OK) return st;
+    }
+    ctx->profiling = enable != 0;
+    return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_profile_read(afqmc_ctx* ctx, double* out, int len) {
+    if (!ctx || !out || len < 0) return fail(AFQMC_ERR_ARG, "bad arguments");
+    afqmc_status st = prof_flush(ctx);
+    if (st != AFQMC_OK) return st;
+    for (int i = 0; i < len; ++i) {
+        double v = 0.0;
+        if (i < PH_COUNT) v = ctx->prof_ms[i];
+        else if (i < 2 * PH_COUNT) v = (double)ctx->prof_launches[i - PH_COUNT];
+        else if (i == 2 * PH_COUNT) v = (double)ctx->prof_steps;
+        out[i] = v;
+    }
+    for (int i = 0; i < PH_COUNT; ++i) { ctx->prof_ms[i] = 0.0; ctx->prof_launches[i] = 0; }
+    ctx->prof_steps = 0;
+    return AFQMC_OK;
+}
+
 
 extern "C" void afqmc_config_default(afqmc_config* c) {
     memset(c, 0, sizeof *c);
@@ -57,6 +136,8 @@ static const char* check_config(const afqmc_config* c) {
     if (!(c->dtau > 0.0)) return "dtau must be > 0";
     if (c->proposal == AFQMC_PROPOSAL_PCN && !(c->pcn_beta > 0.0 && c->pcn_beta <= 1.0)) return "pcn_beta in (0, 1]";
     if (!(c->kill_threshold >= 0.0)) return "kill_threshold must be >= 0";
+    if (c->walker_offset < 0 || (c->walker_offset + c->n_walkers) * (long long)c->n_paths > (1ll << 32))
+        return "walker_offset out of range of the 32-bit stream entity";
     if (!contract_fp64_supported(c->N, c->n_up, c->n_dn)) return "sizes too large for the FP64 contraction kernel";
     if (2ull * c->N * (c->n_up + c->n_dn) * 16 > 220 * 1024) return "sizes too large for the propagation kernel";
     return nullptr;
@@ -132,7 +213,7 @@ extern "C" size_t afqmc_workspace_bytes(const afqmc_config* cfg) {
 
 static StepParams params_of(const afqmc_config* c) {
     StepParams p;
-    p.seed = c->seed; p.dtau = c->dtau; p.pcn_beta = c->pcn_beta; p.e_shift = c->e_shift;
+    p.seed = c->seed; p.woff = c->walker_offset; p.dtau = c->dtau; p.pcn_beta = c->pcn_beta; p.e_shift = c->e_shift;
     p.kill_threshold = c->kill_threshold; p.constraint = c->constraint; p.proposal = c->proposal;
     p.taylor_order = c->taylor_order; p.history_capacity = c->history_capacity;
     return p;
@@ -146,17 +227,21 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
     Workspace& w = ctx->ws;
     cudaStream_t s = ctx->stream;
     StepParams p = params_of(&ctx->cfg);
+    afqmc_status st;
     CK(propose(s, d, p, w.counters, tag_prop, sweep, w.x, w.alive, w.xprop));
     gemm_nn_f64(s, (int)d.pairs, d.N * d.N, d.K, 1.0, w.xprop, d.K, w.U, (long long)d.N * d.N, 0.0, w.Sprop,
                 (long long)d.N * d.N);
     CK(cudaGetLastError());
+    if ((st = prof_mark(ctx, PH_PROPOSE)) != AFQMC_OK) return st;
     CK(trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phiprop, w.alive, d.P, w.status));
+    if ((st = prof_mark(ctx, PH_TRIAL)) != AFQMC_OK) return st;
     for (int spin = 0; spin < 2; ++spin)
         CK(overlap_lu(s, d, spin, w.Phiprop, (long long)d.N * d.nu, orbitals, w.logdet_prop, nullptr, w.alive, w.status,
                       d.pairs, d.P));
+    if ((st = prof_mark(ctx, PH_MCMC_OVERLAP)) != AFQMC_OK) return st;
     CK(accept(s, d, p, w.counters, tag_acc, sweep, w.logdet_prop, w.xprop, w.Phiprop, w.alive, w.logov_cur, w.x, w.Phi,
               w.counters));
-    return AFQMC_OK;
+    return prof_mark(ctx, PH_ACCEPT);
 }
 
 // Local energies, force-bias values and path signs at the current walkers,
@@ -165,12 +250,15 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     const Dims& d = ctx->d;
     Workspace& w = ctx->ws;
     cudaStream_t s = ctx->stream;
+    afqmc_status st;
     for (int spin = 0; spin < 2; ++spin)
         CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P));
+    if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     CK(contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
+    if ((st = prof_mark(ctx, PH_CONTRACT)) != AFQMC_OK) return st;
     CK(walker_average(s, d, w.logdet, w.vpair, w.epair, w.logov, w.sumS, w.vbar, w.ebar));
     CK(energy_reduce(s, d, w.weight, w.ebar, w.sumS, w.reduce));
-    return AFQMC_OK;
+    return prof_mark(ctx, PH_AVERAGE);
 }
 
 extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, const double* L, const double* Phi0,
@@ -217,13 +305,13 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
             break;
         }
         // initial walkers phi_w = Phi(x_w), x_w ~ N(0, I), orthonormalised
-        fill_normals(s, w.xprop, d.W, d.K, p.seed, TAG_INIT_WALKER, w.counters, 0);
+        fill_normals(s, w.xprop, d.W, d.K, p.woff, p.seed, TAG_INIT_WALKER, w.counters, 0);
         gemm_nn_f64(s, d.W, (int)NN, d.K, 1.0, w.xprop, d.K, w.U, NN, 0.0, w.Sprop, NN);
         trial_orbitals(s, d.N, d.nu, d.W, w.Sprop, w.Phi0, w.Phiprop, nullptr, 1, w.status);
         walkers_from_trial(s, d, w.Phiprop, w.phi_new);
         reorthonormalise(s, d, w.phi_new, w.phi, nullptr, w.status, d.W);
         // paths x_wp ~ N(0, I) and their orbitals
-        fill_normals(s, w.x, d.pairs, d.K, p.seed, TAG_INIT_PATH, w.counters, 0);
+        fill_normals(s, w.x, d.pairs, d.K, p.woff * d.P, p.seed, TAG_INIT_PATH, w.counters, 0);
         gemm_nn_f64(s, (int)d.pairs, (int)NN, d.K, 1.0, w.x, d.K, w.U, NN, 0.0, w.Sprop, NN);
         trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phi, nullptr, d.P, w.status);
         set_value(s, w.weight, d.W, 1.0);
@@ -258,17 +346,21 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
     cudaStream_t s = ctx->stream;
     StepParams p = params_of(&ctx->cfg);
     for (int it = 0; it < n_steps; ++it) {
-        afqmc_status st = measure(ctx);                 // Eq. (25)-(27), (16) at phi
+        afqmc_status st = prof_mark(ctx, -1);
         if (st != AFQMC_OK) return st;
+        if ((st = measure(ctx)) != AFQMC_OK) return st;      // Eq. (25)-(27), (16) at phi
         CK(fields(s, d, p, w.counters, w.vbar, w.sumS, w.weight, w.alive, (double*)w.y, w.logshift));
         gemm_nn_f64(s, 2 * d.W, d.N * d.N, d.G, 1.0, (const double*)w.y, d.G, w.L, (long long)d.N * d.N, 0.0,
                     w.Aplanes, (long long)d.N * d.N);
         CK(cudaGetLastError());
+        if ((st = prof_mark(ctx, PH_FIELDS)) != AFQMC_OK) return st;
         CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive));          // Eq. (12)
+        if ((st = prof_mark(ctx, PH_PROPAGATE)) != AFQMC_OK) return st;
         for (int spin = 0; spin < 2; ++spin)
             CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi_new, w.logdet_new, nullptr, w.alive, w.status,
                           d.pairs, d.P));
         CK(ratios(s, d, w.logov, w.logdet_new, w.sumS, w.logshift, w.alive, w.logov_cur, w.old_sum, w.ratio, w.Iabs));
+        if ((st = prof_mark(ctx, PH_RATIO)) != AFQMC_OK) return st;
         for (int m = 0; m < ctx->cfg.n_sweeps; ++m) {                                  // Eq. (23)
             st = mcmc_sweep(ctx, w.phi_new, TAG_PROPOSE, TAG_ACCEPT, (uint32_t)m);
             if (st != AFQMC_OK) return st;
@@ -276,6 +368,8 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         CK(handoff(s, d, p, w.logov_cur, w.old_sum, w.ratio, w.Iabs, w.alive, w.weight, w.status));  // Eq. (28)-(29)
         CK(reorthonormalise(s, d, w.phi_new, w.phi, w.alive, w.status, d.W));
         CK(step_end(s, p, w.reduce, w.history, w.counters));
+        if ((st = prof_mark(ctx, PH_FINISH)) != AFQMC_OK) return st;
+        if (ctx->profiling) ctx->prof_steps++;
         ctx->steps_taken++;
     }
     ctx->measured = false;
@@ -361,7 +455,7 @@ extern "C" afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len) {
     unsigned long long c[8];
     double ws4[4];
     int status = 0;
-    weight_stats_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d.W, ctx->ws.weight, ctx->ws.reduce + 4);
+    weight_stats_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d.W, ctx->ws.weight, ctx->ws.reduce + 4); count_launches(1);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c, ctx->ws.counters, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ws4, ctx->ws.reduce + 4, sizeof ws4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -429,6 +523,11 @@ extern "C" afqmc_status afqmc_state_load(afqmc_ctx* ctx, const void* buf, size_t
 extern "C" void afqmc_destroy(afqmc_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->prof_events) {
+        for (int i = 0; i < ctx->prof_cap; ++i) cudaEventDestroy(ctx->prof_events[i]);
+        free(ctx->prof_events);
+        free(ctx->prof_phase);
+    }
     free(ctx);
 }
 
@@ -448,7 +547,7 @@ extern "C" afqmc_status afqmc_philox_fill(uint32_t* out, int64_t n, uint32_t c0,
     if (!out || n < 0) return fail(AFQMC_ERR_ARG, "bad arguments");
     if (n == 0) return AFQMC_OK;
     philox_fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(out, n, c0, c1, c2, c3,
-                                                                                     (uint32_t)key, (uint32_t)(key >> 32));
+                                                                                     (uint32_t)key, (uint32_t)(key >> 32)); count_launches(1);
     CK(cudaGetLastError());
     return AFQMC_OK;
 }

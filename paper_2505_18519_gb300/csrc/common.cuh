@@ -174,6 +174,16 @@ struct Dims {
 
 }  // namespace afq
 
+namespace afq {
+// Process-wide count of kernel launches made by this library.
+void count_launches(long long n);
+// Phases of a step timed by afqmc_profile (CUDA events on the context's stream).
+enum Phase : int {
+    PH_OVERLAP = 0, PH_CONTRACT, PH_AVERAGE, PH_FIELDS, PH_PROPAGATE, PH_RATIO, PH_PROPOSE, PH_TRIAL,
+    PH_MCMC_OVERLAP, PH_ACCEPT, PH_FINISH, PH_COUNT
+};
+}  // namespace afq
+
 struct afqmc_ctx {
     afqmc_config cfg;
     afq::Dims d;
@@ -181,4 +191,12 @@ struct afqmc_ctx {
     cudaStream_t stream;
     long long steps_taken;   // host mirror of the device step counter
     bool measured;           // afqmc_energy has filled the per-pair buffers
+    // profiling: events recorded at phase boundaries while enabled
+    bool profiling;
+    int prof_used, prof_cap;
+    cudaEvent_t* prof_events;   // prof_cap events
+    int* prof_phase;            // phase that ends at event i (-1: a step start)
+    double prof_ms[afq::PH_COUNT];
+    long long prof_launches[afq::PH_COUNT];
+    long long prof_steps;
 };

@@ -169,7 +169,7 @@ cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const 
         cudaError_t e = cudaFuncSetAttribute(contract_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    contract_fp64_kernel<<<(unsigned)pairs, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair, epair);
+    contract_fp64_kernel<<<(unsigned)pairs, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair, epair); count_launches(1);
     return cudaGetLastError();
 }
 

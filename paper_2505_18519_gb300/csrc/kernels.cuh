@@ -25,11 +25,12 @@ bool contract_fp64_supported(int N, int nu, int nd);
 // walker.cu
 struct StepParams {
     uint64_t seed;
+    long long woff;   // global index of walker 0
     double dtau, pcn_beta, e_shift, kill_threshold;
     int constraint, proposal, taylor_order, history_capacity;
 };
-cudaError_t fill_normals(cudaStream_t s, double* out, long long rows, int cols, uint64_t seed, uint32_t tag,
-                         const unsigned long long* step_ctr, uint32_t sweep);
+cudaError_t fill_normals(cudaStream_t s, double* out, long long rows, int cols, long long entity0, uint64_t seed,
+                         uint32_t tag, const unsigned long long* step_ctr, uint32_t sweep);
 cudaError_t walkers_from_trial(cudaStream_t s, const Dims& d, const double* Phi_w, double2* phi);
 cudaError_t walker_average(cudaStream_t s, const Dims& d, const double2* logdet, const double2* vpair,
                            const double2* epair, double2* logov, double2* sumS, double2* vbar, double2* ebar);

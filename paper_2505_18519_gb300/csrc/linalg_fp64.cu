@@ -62,7 +62,7 @@ void gemm_nn_f64(cudaStream_t s, int M, int Nc, int K, double alpha, const doubl
                  long long ldb, double beta, double* C, long long ldc) {
     if (M <= 0 || Nc <= 0) return;
     dim3 grid((unsigned)((Nc + 63) / 64), (unsigned)((M + 63) / 64));
-    gemm_nn_f64_kernel<<<grid, 256, 0, s>>>(M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    gemm_nn_f64_kernel<<<grid, 256, 0, s>>>(M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc); count_launches(1);
 }
 
 // ---------------------------------------------------------------- overlap + LU
@@ -218,7 +218,7 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
     }
     long long blocks = (pairs + wpb - 1) / wpb;
     overlap_lu_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nt, n, col0, spin, pairs, P, Phi, Phi_stride,
-                                                               phi, logdet, Theta, alive, status);
+                                                               phi, logdet, Theta, alive, status); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -279,7 +279,7 @@ cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, 
             cudaError_t e = cudaFuncSetAttribute(reorth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        reorth_kernel<<<n_walkers, 32, smem, s>>>(d.N, d.nt, n, spin == 0 ? 0 : d.nu, src, dst, alive, status);
+        reorth_kernel<<<n_walkers, 32, smem, s>>>(d.N, d.nt, n, spin == 0 ? 0 : d.nu, src, dst, alive, status); count_launches(1);
     }
     return cudaGetLastError();
 }
@@ -415,14 +415,14 @@ cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, co
             e = cudaFuncSetAttribute(chebyshev_expm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
             if (e != cudaSuccess) return e;
         }
-        chebyshev_expm_kernel<true><<<(unsigned)problems, 256, full, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status);
+        chebyshev_expm_kernel<true><<<(unsigned)problems, 256, full, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status); count_launches(1);
     } else {
         if (vec > 200 * 1024) return cudaErrorInvalidValue;
         if (vec > 48 * 1024) {
             e = cudaFuncSetAttribute(chebyshev_expm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec);
             if (e != cudaSuccess) return e;
         }
-        chebyshev_expm_kernel<false><<<(unsigned)problems, 256, vec, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status);
+        chebyshev_expm_kernel<false><<<(unsigned)problems, 256, vec, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status); count_launches(1);
     }
     return cudaGetLastError();
 }
@@ -504,8 +504,8 @@ __global__ void __launch_bounds__(1024) expm_small_kernel(int N, double alpha, c
 cudaError_t one_body_propagator(cudaStream_t s, int N, int G, double dtau, const double* h, const double* L, double* T,
                                 double* scratch3, double* expT) {
     long long NN = (long long)N * N;
-    one_body_T_kernel<<<(unsigned)((NN + 127) / 128), 128, 0, s>>>(N, G, h, L, T);
-    expm_small_kernel<<<1, 1024, 0, s>>>(N, -0.5 * dtau, T, scratch3, scratch3 + NN, scratch3 + 2 * NN, expT);
+    one_body_T_kernel<<<(unsigned)((NN + 127) / 128), 128, 0, s>>>(N, G, h, L, T); count_launches(1);
+    expm_small_kernel<<<1, 1024, 0, s>>>(N, -0.5 * dtau, T, scratch3, scratch3 + NN, scratch3 + 2 * NN, expT); count_launches(1);
     return cudaGetLastError();
 }
 

@@ -10,24 +10,24 @@ namespace afq {
 __device__ __forceinline__ uint32_t step_of(const unsigned long long* ctr) { return (uint32_t)ctr[0]; }
 
 // ---------------------------------------------------------------- random draws
-// out[r * cols + k] = normal number k of draw (tag, step, entity r, sweep).
-__global__ void fill_normals_kernel(double* out, long long rows, int cols, uint64_t seed, uint32_t tag,
+// out[r * cols + k] = normal number k of draw (tag, step, entity entity0 + r, sweep).
+__global__ void fill_normals_kernel(double* out, long long rows, int cols, long long entity0, uint64_t seed, uint32_t tag,
                                     const unsigned long long* ctr, uint32_t sweep) {
     int blocks_per_row = (cols + 1) / 2;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= rows * blocks_per_row) return;
     long long r = t / blocks_per_row;
     int j = (int)(t - r * blocks_per_row);
-    double2 z = normal_pair(seed, tag, step_of(ctr), (uint32_t)r, sweep, (uint32_t)j);
+    double2 z = normal_pair(seed, tag, step_of(ctr), (uint32_t)(entity0 + r), sweep, (uint32_t)j);
     out[r * cols + 2 * j] = z.x;
     if (2 * j + 1 < cols) out[r * cols + 2 * j + 1] = z.y;
 }
 
-cudaError_t fill_normals(cudaStream_t s, double* out, long long rows, int cols, uint64_t seed, uint32_t tag,
-                         const unsigned long long* ctr, uint32_t sweep) {
+cudaError_t fill_normals(cudaStream_t s, double* out, long long rows, int cols, long long entity0, uint64_t seed,
+                         uint32_t tag, const unsigned long long* ctr, uint32_t sweep) {
     long long n = rows * ((cols + 1) / 2);
     if (n <= 0) return cudaSuccess;
-    fill_normals_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, rows, cols, seed, tag, ctr, sweep);
+    fill_normals_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, rows, cols, entity0, seed, tag, ctr, sweep); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -44,7 +44,7 @@ __global__ void walkers_from_trial_kernel(int N, int nu, int nd, const double* _
 }
 
 cudaError_t walkers_from_trial(cudaStream_t s, const Dims& d, const double* Phi_w, double2* phi) {
-    walkers_from_trial_kernel<<<d.W, 128, 0, s>>>(d.N, d.nu, d.nd, Phi_w, phi);
+    walkers_from_trial_kernel<<<d.W, 128, 0, s>>>(d.N, d.nu, d.nd, Phi_w, phi); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) walker_average_kernel(int P, int G, const
 
 cudaError_t walker_average(cudaStream_t s, const Dims& d, const double2* logdet, const double2* vpair,
                            const double2* epair, double2* logov, double2* sumS, double2* vbar, double2* ebar) {
-    walker_average_kernel<<<d.W, 256, d.P * sizeof(double2), s>>>(d.P, d.G, logdet, vpair, epair, logov, sumS, vbar, ebar);
+    walker_average_kernel<<<d.W, 256, d.P * sizeof(double2), s>>>(d.P, d.G, logdet, vpair, epair, logov, sumS, vbar, ebar); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(1024) energy_reduce_kernel(int W, int P, const
 
 cudaError_t energy_reduce(cudaStream_t s, const Dims& d, const double* weight, const double2* ebar,
                           const double2* sumS, double* out3) {
-    energy_reduce_kernel<<<1, 1024, 0, s>>>(d.W, d.P, weight, ebar, sumS, out3);
+    energy_reduce_kernel<<<1, 1024, 0, s>>>(d.W, d.P, weight, ebar, sumS, out3); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -155,7 +155,7 @@ cudaError_t energy_reduce(cudaStream_t s, const Dims& d, const double* weight, c
 // xi_g ~ N(0,1) (Philox, tag FIELD, entity w); xbar_g = -i sqrt(tau) vbar_g;
 // y = xi - xbar written as planes (row 2w: Re y, row 2w+1: Im y);
 // logshift = sum_g (xi_g xbar_g - xbar_g^2 / 2), the log of p(x - xbar)/p(x).
-__global__ void __launch_bounds__(256) fields_kernel(int G, uint64_t seed, double dtau, double thr,
+__global__ void __launch_bounds__(256) fields_kernel(int G, long long woff, uint64_t seed, double dtau, double thr,
                                                      const unsigned long long* ctr, const double2* __restrict__ vbar,
                                                      const double2* __restrict__ sumS, double* weight, int* alive,
                                                      double* yplanes, double2* logshift) {
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) fields_kernel(int G, uint64_t seed, doubl
     double st = sqrt(dtau);
     double2 acc = cmk(0.0, 0.0);
     for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        double xi = normal_at(seed, TAG_FIELD, step, (uint32_t)w, 0, (uint32_t)g);
+        double xi = normal_at(seed, TAG_FIELD, step, (uint32_t)(woff + w), 0, (uint32_t)g);
         double2 v = vbar[w * (long long)G + g];
         double2 xb = cmk(st * v.y, -st * v.x);          // -i sqrt(tau) v
         yre[g] = xi - xb.x;
@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(256) fields_kernel(int G, uint64_t seed, doubl
 cudaError_t fields(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr,
                    const double2* vbar, const double2* sumS, double* weight, int* alive, double* yplanes,
                    double2* logshift) {
-    fields_kernel<<<d.W, 256, 0, s>>>(d.G, p.seed, p.dtau, p.kill_threshold, ctr, vbar, sumS, weight, alive, yplanes,
-                                      logshift);
+    fields_kernel<<<d.W, 256, 0, s>>>(d.G, p.woff, p.seed, p.dtau, p.kill_threshold, ctr, vbar, sumS, weight, alive, yplanes,
+                                      logshift); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -278,7 +278,7 @@ cudaError_t propagate(cudaStream_t s, const Dims& d, const StepParams& p, const 
         cudaError_t e = cudaFuncSetAttribute(propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    propagate_kernel<<<d.W, 256, smem, s>>>(d.N, d.nt, p.taylor_order, p.dtau, expT, Aplanes, phi, phi_new, alive);
+    propagate_kernel<<<d.W, 256, smem, s>>>(d.N, d.nt, p.taylor_order, p.dtau, expT, Aplanes, phi, phi_new, alive); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -321,7 +321,7 @@ cudaError_t ratios(cudaStream_t s, const Dims& d, const double2* logov, const do
                    double2* old_sum, double2* ratio, double* Iabs) {
     if (d.P > 1024) return cudaErrorInvalidValue;
     ratios_walker_kernel<<<d.W, 128, 0, s>>>(d.P, logov, logdet_new, sumS, logshift, alive, logov_cur, old_sum, ratio,
-                                             Iabs);
+                                             Iabs); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -332,14 +332,14 @@ __global__ void combine_logdet_kernel(long long pairs, const double2* __restrict
 }
 
 cudaError_t combine_logdet(cudaStream_t s, long long pairs, const double2* logdet, double2* logov) {
-    combine_logdet_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(pairs, logdet, logov);
+    combine_logdet_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(pairs, logdet, logov); count_launches(1);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- Metropolis on the paths
 // Proposal for pair q: prior x' = xi, or pCN x' = sqrt(1 - beta^2) x + beta xi,
 // xi ~ N(0, I) (Philox, tag PROPOSE or BURN_PROPOSE, entity q, this sweep).
-__global__ void propose_kernel(long long pairs, int P, int K, uint64_t seed, uint32_t tag, uint32_t sweep,
+__global__ void propose_kernel(long long pairs, int P, int K, long long woff, uint64_t seed, uint32_t tag, uint32_t sweep,
                                const unsigned long long* ctr, int proposal, double beta, const double* __restrict__ x,
                                const int* __restrict__ alive, double* xprop) {
     int bpr = (K + 1) / 2;
@@ -353,7 +353,7 @@ __global__ void propose_kernel(long long pairs, int P, int K, uint64_t seed, uin
         if (2 * j + 1 < K) out[2 * j + 1] = 0.0;
         return;
     }
-    double2 z = normal_pair(seed, tag, step_of(ctr), (uint32_t)q, sweep, (uint32_t)j);
+    double2 z = normal_pair(seed, tag, step_of(ctr), (uint32_t)(woff * P + q), sweep, (uint32_t)j);
     if (proposal == AFQMC_PROPOSAL_PCN) {
         double a = sqrt(1.0 - beta * beta);
         const double* xo = x + q * K;
@@ -367,15 +367,15 @@ __global__ void propose_kernel(long long pairs, int P, int K, uint64_t seed, uin
 cudaError_t propose(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
                     uint32_t sweep, const double* x, const int* alive, double* xprop) {
     long long n = d.pairs * ((d.K + 1) / 2);
-    propose_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d.pairs, d.P, d.K, p.seed, tag, sweep, ctr, p.proposal,
-                                                               p.pcn_beta, x, alive, xprop);
+    propose_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d.pairs, d.P, d.K, p.woff, p.seed, tag, sweep, ctr, p.proposal,
+                                                               p.pcn_beta, x, alive, xprop); count_launches(1);
     return cudaGetLastError();
 }
 
 // Accept iff Re(logov'' - logov') >= 0 or u < exp(Re(logov'' - logov')) with
 // u the first 53-bit uniform of (tag, step, pair, sweep); on acceptance copy
 // x', Phi(x') and logov'' into the path.  One block per pair.
-__global__ void __launch_bounds__(128) accept_kernel(int N, int nu, int K, int P, uint64_t seed, uint32_t tag,
+__global__ void __launch_bounds__(128) accept_kernel(int N, int nu, int K, int P, long long woff, uint64_t seed, uint32_t tag,
                                                      uint32_t sweep, const unsigned long long* ctr,
                                                      const double2* __restrict__ logdet_prop,
                                                      const double* __restrict__ xprop, const double* __restrict__ Phiprop,
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(128) accept_kernel(int N, int nu, int K, int P
     if (threadIdx.x == 0) {
         double2 ln = cadd(logdet_prop[2 * q], logdet_prop[2 * q + 1]);
         double delta = ln.x - logov_cur[q].x;
-        double u = uniform_at0(seed, tag, step_of(ctr), (uint32_t)q, sweep);
+        double u = uniform_at0(seed, tag, step_of(ctr), (uint32_t)(woff * P + q), sweep);
         int a = (delta >= 0.0) || (u < exp(delta));
         acc = a;
         if (a) {
@@ -406,8 +406,8 @@ __global__ void __launch_bounds__(128) accept_kernel(int N, int nu, int K, int P
 cudaError_t accept(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
                    uint32_t sweep, const double2* logdet_prop, const double* xprop, const double* Phiprop,
                    const int* alive, double2* logov_cur, double* x, double* Phi, unsigned long long* counters) {
-    accept_kernel<<<(unsigned)d.pairs, 128, 0, s>>>(d.N, d.nu, d.K, d.P, p.seed, tag, sweep, ctr, logdet_prop, xprop,
-                                                    Phiprop, alive, logov_cur, x, Phi, counters);
+    accept_kernel<<<(unsigned)d.pairs, 128, 0, s>>>(d.N, d.nu, d.K, d.P, p.woff, p.seed, tag, sweep, ctr, logdet_prop, xprop,
+                                                    Phiprop, alive, logov_cur, x, Phi, counters); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -455,7 +455,7 @@ cudaError_t handoff(cudaStream_t s, const Dims& d, const StepParams& p, const do
                     const double2* old_sum, const double2* ratio, const double* Iabs, const int* alive,
                     double* weight, int* status) {
     handoff_kernel<<<d.W, 32, 0, s>>>(d.W, d.P, p.constraint, p.dtau, p.e_shift, logov_cur, old_sum, ratio, Iabs, alive,
-                                      weight, status);
+                                      weight, status); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -478,7 +478,7 @@ __global__ void step_end_kernel(int cap, const double* measured3, double* histor
 
 cudaError_t step_end(cudaStream_t s, const StepParams& p, const double* measured3, double* history,
                      unsigned long long* counters) {
-    step_end_kernel<<<1, 1, 0, s>>>(p.history_capacity, measured3, history, counters);
+    step_end_kernel<<<1, 1, 0, s>>>(p.history_capacity, measured3, history, counters); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -491,11 +491,11 @@ __global__ void set_int_kernel(int* out, long long n, int v) {
     if (i < n) out[i] = v;
 }
 cudaError_t set_value(cudaStream_t s, double* out, long long n, double v) {
-    if (n > 0) set_value_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, v);
+    if (n > 0) { set_value_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, v); count_launches(1); }
     return cudaGetLastError();
 }
 cudaError_t set_int(cudaStream_t s, int* out, long long n, int v) {
-    if (n > 0) set_int_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, v);
+    if (n > 0) { set_int_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, v); count_launches(1); }
     return cudaGetLastError();
 }
 
