@@ -190,6 +190,38 @@ afqmc_status afqmc_profile_read(afqmc_ctx* ctx, double* out, int len);
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t afqmc_launch_count(void);
 
+/* Local energies, force-bias values and overlaps of a batch of (walker, trial
+ * sample) pairs that allocates nothing.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc or give the library a workspace (code
+ * inside another framework's operator hook whose device memory must come from
+ * that framework's pool, or a loop where an allocation, which may synchronise the
+ * device, is not allowed).  Its intermediate matrices live in one fixed device
+ * array of afqmc_noalloc_scratch_bytes() bytes (32 MiB) that every GPU loading
+ * the library holds until exit; the caller passes only inputs and outputs.
+ *   h           N*N                      one-body matrix                    device
+ *   L           n_chol*N*N               Cholesky vectors                   device
+ *   Phi         n_pairs*N*n_up           trial orbitals of each pair        device
+ *   phi         n_walkers*N*(n_up+n_dn)*2  walker orbitals (re, im; spin-up
+ *                                        columns first); pair q uses walker
+ *                                        q / pairs_per_walker              device
+ *   logov       2*n_pairs   out: log <Phi_q|phi> (log|det| + i Arg det)    device
+ *   e_local     2*n_pairs   out: local energy of each pair                 device
+ *   force_bias  2*n_pairs*n_chol  out: <L_g> of each pair                  device
+ * Runs asynchronously on `stream` on the calling thread's current device.
+ * Returns AFQMC_ERR_ARG, without launching anything, when the batch needs more
+ * than the fixed scratch (about n_pairs * (N*(n_up+n_dn)*16 + 32) bytes).
+ * The first call on each device resolves the array's device address there
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array, so calls that overlap on the GPU race.  A
+ * singular overlap gives log|ov| = -inf for that pair. */
+size_t afqmc_noalloc_scratch_bytes(void);
+afqmc_status afqmc_local_energy_noalloc(int N, int n_up, int n_dn, int n_chol, int64_t n_pairs,
+                                        int pairs_per_walker, const double* h, const double* L,
+                                        const double* Phi, const double* phi, double* logov,
+                                        double* e_local, double* force_bias, void* stream);
+/* Message of the last error of afqmc_local_energy_noalloc in this thread. */
+const char* afqmc_noalloc_last_error(void);
+
 /* Message of the last error in this thread (static storage). */
 const char* afqmc_last_error(void);
 

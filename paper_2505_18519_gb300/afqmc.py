@@ -89,6 +89,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.afqmc_profile_read.restype = I
     lib.afqmc_launch_count.argtypes = []
     lib.afqmc_launch_count.restype = ctypes.c_int64
+    lib.afqmc_noalloc_scratch_bytes.argtypes = []
+    lib.afqmc_noalloc_scratch_bytes.restype = SZ
+    lib.afqmc_local_energy_noalloc.argtypes = [I, I, I, I, ctypes.c_int64, I, P, P, P, P, P, P, P, P]
+    lib.afqmc_local_energy_noalloc.restype = I
+    lib.afqmc_noalloc_last_error.argtypes = []
+    lib.afqmc_noalloc_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -239,6 +245,21 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def local_energy_noalloc(N, n_up, n_dn, n_chol, n_pairs, pairs_per_walker, h, L, Phi, phi, logov, e_local,
+                         force_bias, stream=None):
+    """Local energies of a batch of pairs with no device allocation (all
+    arguments are CUDA float64 tensors; ``phi`` holds re, im pairs).  For callers
+    that cannot allocate device memory; see include/afqmc.h."""
+    import torch
+    lib = load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib.afqmc_local_energy_noalloc(N, n_up, n_dn, n_chol, int(n_pairs), pairs_per_walker, h.data_ptr(),
+                                        L.data_ptr(), Phi.data_ptr(), phi.data_ptr(), logov.data_ptr(),
+                                        e_local.data_ptr(), force_bias.data_ptr(), s.cuda_stream)
+    if st != 0:
+        raise AfqmcError(st, lib.afqmc_noalloc_last_error().decode())
 
 
 def launch_count() -> int:
