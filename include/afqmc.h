@@ -70,7 +70,14 @@ enum {
 
 /* arithmetic of the two big contractions (R = Phi^T L_g and M = R Theta) */
 enum {
-    AFQMC_PRECISION_FP64 = 0   /* FP64 everywhere */
+    AFQMC_PRECISION_FP64 = 0,  /* FP64 everywhere */
+    AFQMC_PRECISION_BF16X3 = 1, /* the fused contraction on the tensor cores in split BF16 (hi*hi + hi*lo +
+                                   lo*hi, FP32 accumulation, traces summed in FP64); everything else FP64.
+                                   N <= 128, n_up <= 32 */
+    AFQMC_PRECISION_FP16X3 = 2  /* the same with each operand row/column scaled by a power of two and split
+                                   into an integer FP16 part (|x| <= 256) and an FP16 remainder (about 20 bits
+                                   relative to the row's largest entry); integer*integer products go to their
+                                   own, exact accumulator, the three correction products to a second one */
 };
 
 typedef struct {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libafqmc.so")
 
 CONSTRAINTS = {"combined": 0, "separate": 1, "half_plane": 2}
 PROPOSALS = {"prior": 0, "pcn": 1}
-PRECISIONS = {"fp64": 0}
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "fp16x3": 2}
 STATE_MAGIC = 0x4146514D43535431
 
 

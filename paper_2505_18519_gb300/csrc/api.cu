@@ -130,7 +130,7 @@ static const char* check_config(const afqmc_config* c) {
     if (c->n_sweeps < 1 || c->n_burn < 0) return "n_sweeps >= 1 and n_burn >= 0";
     if (c->constraint < 0 || c->constraint > 2) return "unknown constraint";
     if (c->proposal < 0 || c->proposal > 1) return "unknown proposal";
-    if (c->precision != AFQMC_PRECISION_FP64) return "unknown precision";
+    if (c->precision < AFQMC_PRECISION_FP64 || c->precision > AFQMC_PRECISION_FP16X3) return "unknown precision";
     if (c->taylor_order < 1 || c->taylor_order > 32) return "taylor_order must be in [1, 32]";
     if (c->history_capacity < 1) return "history_capacity must be >= 1";
     if (!(c->dtau > 0.0)) return "dtau must be > 0";
@@ -138,7 +138,11 @@ static const char* check_config(const afqmc_config* c) {
     if (!(c->kill_threshold >= 0.0)) return "kill_threshold must be >= 0";
     if (c->walker_offset < 0 || (c->walker_offset + c->n_walkers) * (long long)c->n_paths > (1ll << 32))
         return "walker_offset out of range of the 32-bit stream entity";
-    if (!contract_fp64_supported(c->N, c->n_up, c->n_dn)) return "sizes too large for the FP64 contraction kernel";
+    if (c->precision == AFQMC_PRECISION_FP64 && !contract_fp64_supported(c->N, c->n_up, c->n_dn))
+        return "sizes too large for the FP64 contraction kernel";
+    if (c->precision != AFQMC_PRECISION_FP64 &&
+        !contract_tc_supported(c->N, c->n_up, c->n_dn, c->precision == AFQMC_PRECISION_FP16X3))
+        return "sizes not supported by the tensor-core contraction (N <= 128, n_up <= 32)";
     if (2ull * c->N * (c->n_up + c->n_dn) * 16 > 220 * 1024) return "sizes too large for the propagation kernel";
     return nullptr;
 }
@@ -171,6 +175,9 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.T = (double*)take(NN * 8);
     w.expT = (double*)take(NN * 8);
     w.scratchNN = (double*)take(3 * NN * 8);
+    w.Lt = c->precision != AFQMC_PRECISION_FP64
+               ? take(contract_tc_image_bytes(d.N, d.nu, d.nd, d.G, c->precision == AFQMC_PRECISION_FP16X3))
+               : nullptr;
     w.phi = (double2*)take(W * N * nt * 16);
     w.weight = (double*)take(W * 8);
     w.x = (double*)take(pairs * K * 8);
@@ -254,7 +261,11 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     for (int spin = 0; spin < 2; ++spin)
         CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
-    CK(contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
+    if (ctx->cfg.precision != AFQMC_PRECISION_FP64)
+        CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.vpair, w.epair, w.status,
+                       ctx->cfg.precision == AFQMC_PRECISION_FP16X3));
+    else
+        CK(contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
     if ((st = prof_mark(ctx, PH_CONTRACT)) != AFQMC_OK) return st;
     CK(walker_average(s, d, w.logdet, w.vpair, w.epair, w.logov, w.sumS, w.vbar, w.ebar));
     CK(energy_reduce(s, d, w.weight, w.ebar, w.sumS, w.reduce));
@@ -300,6 +311,12 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, 4, s);
         if (e != cudaSuccess) { st = fail(AFQMC_ERR_CUDA, "copying inputs: %s", cudaGetErrorString(e)); break; }
         StepParams p = params_of(cfg);
+        if (cfg->precision != AFQMC_PRECISION_FP64 &&
+            (e = contract_tc_prepare(s, d.N, d.nu, d.nd, d.G, w.h, w.L, w.Lt,
+                                     cfg->precision == AFQMC_PRECISION_FP16X3)) != cudaSuccess) {
+            st = fail(AFQMC_ERR_CUDA, "tensor-core operand image: %s", cudaGetErrorString(e));
+            break;
+        }
         if ((e = one_body_propagator(s, d.N, d.G, cfg->dtau, w.h, w.L, w.T, w.scratchNN, w.expT)) != cudaSuccess) {
             st = fail(AFQMC_ERR_CUDA, "one-body propagator: %s", cudaGetErrorString(e));
             break;
@@ -397,7 +414,9 @@ extern "C" afqmc_status afqmc_energy(afqmc_ctx* ctx, double* e_mix, double* sum_
     if (e_mix) *e_mix = r[1] > 0 ? r[0] / r[1] : 0.0;
     if (sum_w) *sum_w = r[1];
     if (mean_sign) *mean_sign = r[1] > 0 ? r[2] / r[1] : 0.0;
-    if (status) return fail(AFQMC_ERR_NUMERIC, "device status word 0x%x (1 singular overlap, 2 non-finite value)", status);
+    if (status)
+        return fail(AFQMC_ERR_NUMERIC, "device status word 0x%x (1 singular overlap, 2 non-finite value, 4 tensor-core wait timed out)",
+                    status);
     return AFQMC_OK;
 }
 

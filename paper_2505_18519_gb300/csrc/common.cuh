@@ -116,7 +116,7 @@ __device__ __forceinline__ double uniform_at0(uint64_t seed, uint32_t tag, uint3
 }
 
 // ---------------------------------------------------------------- status word bits
-enum : int { STATUS_SINGULAR = 1, STATUS_NONFINITE = 2 };
+enum : int { STATUS_SINGULAR = 1, STATUS_NONFINITE = 2, STATUS_TIMEOUT = 4 };
 
 // ---------------------------------------------------------------- workspace layout
 // Every buffer of a context lives in the caller's workspace, 256-byte aligned.
@@ -129,6 +129,7 @@ struct Workspace {
     double* T;        // N*N, h - 1/2 sum_g L_g L_g
     double* expT;     // N*N, exp(-tau T / 2)
     double* scratchNN;  // 3*N*N for the matrix exponential at init
+    void* Lt;           // split-BF16 image of (h, L_g) for the tensor-core contraction
     // composite walkers
     double2* phi;     // W*N*nt (nt = n_up + n_dn)
     double* weight;   // W

@@ -22,6 +22,14 @@ cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const 
                           const double2* Theta, double2* vpair, double2* epair, long long pairs);
 bool contract_fp64_supported(int N, int nu, int nd);
 
+// contract_tc.cu
+bool contract_tc_supported(int N, int nu, int nd, bool f16);
+size_t contract_tc_image_bytes(int N, int nu, int nd, int G, bool f16);
+cudaError_t contract_tc_prepare(cudaStream_t st, int N, int nu, int nd, int G, const double* h, const double* L,
+                                void* image, bool f16);
+cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const double* Phi, const double2* Theta,
+                        double2* vpair, double2* epair, int* status, bool f16);
+
 // walker.cu
 struct StepParams {
     uint64_t seed;
