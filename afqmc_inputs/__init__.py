@@ -114,12 +114,12 @@ def make_config(name: str):
     return make_system(spec), run
 
 
-def batched_system_specs(n_systems: int = 16, seed: int = 1003):
-    """Sizes of the uneven batch: N ~ U[40, 200] rounded to a multiple of 5,
-    n = N/5 electrons per spin, Gamma = 5N, K = N; system s uses seed 1000*3+s."""
+def batched_system_specs(n_systems: int = 16, seed: int = 1003, n_range=(40, 200)):
+    """Sizes of the uneven batch: N ~ U[n_range] rounded to a multiple of 5,
+    n = N/5 electrons per spin, Gamma = 5N, K = N; system s uses seed 3000+s."""
     rng = np.random.default_rng(seed)
     specs = []
     for s in range(n_systems):
-        N = int(5 * round(rng.uniform(40, 200) / 5))
+        N = int(5 * round(rng.uniform(*n_range) / 5))
         specs.append(SystemSpec(N, N // 5, N // 5, 5 * N, N, True, 3000 + s))
     return specs

@@ -232,6 +232,27 @@ const char* afqmc_noalloc_last_error(void);
 /* Message of the last error in this thread (static storage). */
 const char* afqmc_last_error(void);
 
+/* Launch-shape autotuner: times the candidate shapes of the overlap kernel
+ * (matrices per block), the tensor-core contraction (pairs per block) and the
+ * trial-orbital kernel (threads per block) on this context's own data, keeps
+ * the fastest, and caches the choice per problem shape for the process.
+ * Results do not depend on the shapes.  Synchronises; not during capture.
+ * chosen (nullable) receives the three choices (0 = built-in default). */
+afqmc_status afqmc_autotune(afqmc_ctx* ctx, int* chosen);
+
+/* Several systems (contexts of any sizes and precisions) stepped together: one
+ * leapfrog step of every context is captured once into one CUDA graph (a fork
+ * on `stream`, each context's kernels as a branch on its own stream, a join),
+ * and each afqmc_batch_step launches that graph once per step.  Every context
+ * needs its own non-default stream, distinct from `stream`; the contexts stay
+ * usable one by one (afqmc_energy, save/load, ...) between batch steps after
+ * afqmc_batch_sync.  The batch does not own the contexts. */
+typedef struct afqmc_batch afqmc_batch;
+afqmc_status afqmc_batch_create(int n_systems, afqmc_ctx* const* ctxs, void* stream, afqmc_batch** out);
+afqmc_status afqmc_batch_step(afqmc_batch* batch, int n_steps);  /* asynchronous on `stream` */
+afqmc_status afqmc_batch_sync(afqmc_batch* batch);
+void afqmc_batch_destroy(afqmc_batch* batch);
+
 /* The library's Philox4x32-10 (Salmon et al., SC'11) on the device, for
  * checking the generator: out[4*i + j] = word j of Philox(counter_i, key) with
  * counter_i = {c0 + i, c1, c2, c3}, i < n.  out is a device pointer. */

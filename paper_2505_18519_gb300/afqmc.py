@@ -40,7 +40,8 @@ _lib = None
 EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc_step", "afqmc_energy",
            "afqmc_observables", "afqmc_history", "afqmc_stats", "afqmc_state_save", "afqmc_state_load",
            "afqmc_destroy", "afqmc_last_error", "afqmc_philox_fill", "afqmc_profile", "afqmc_profile_read",
-           "afqmc_launch_count")
+           "afqmc_launch_count", "afqmc_autotune", "afqmc_batch_create", "afqmc_batch_step", "afqmc_batch_sync",
+           "afqmc_batch_destroy")
 
 PHASES = ("overlap", "contract", "average", "fields", "propagate", "ratio", "propose", "trial_orbitals",
           "mcmc_overlap", "accept", "finish")
@@ -89,6 +90,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.afqmc_profile_read.restype = I
     lib.afqmc_launch_count.argtypes = []
     lib.afqmc_launch_count.restype = ctypes.c_int64
+    lib.afqmc_autotune.argtypes = [P, P]
+    lib.afqmc_autotune.restype = I
+    lib.afqmc_batch_create.argtypes = [I, P, P, ctypes.POINTER(P)]
+    lib.afqmc_batch_create.restype = I
+    lib.afqmc_batch_step.argtypes = [P, I]
+    lib.afqmc_batch_step.restype = I
+    lib.afqmc_batch_sync.argtypes = [P]
+    lib.afqmc_batch_sync.restype = I
+    lib.afqmc_batch_destroy.argtypes = [P]
+    lib.afqmc_batch_destroy.restype = None
     lib.afqmc_noalloc_scratch_bytes.argtypes = []
     lib.afqmc_noalloc_scratch_bytes.restype = SZ
     lib.afqmc_local_energy_noalloc.argtypes = [I, I, I, I, ctypes.c_int64, I, P, P, P, P, P, P, P, P]
@@ -206,6 +217,12 @@ class Context:
         keys = ("steps", "accepted", "proposed", "live_walkers", "status", "min_weight", "max_weight", "sum_weight")
         return dict(zip(keys, out.tolist()))
 
+    def autotune(self):
+        """Pick the fastest launch shapes for this context (cached per shape)."""
+        out = (ctypes.c_int * 3)()
+        _check(load_library().afqmc_autotune(self._ctx, out))
+        return dict(overlap_warps_per_block=out[0], tc_pairs_per_block=out[1], trial_threads=out[2])
+
     # -- profiling ----------------------------------------------------------------
     def profile(self, enable: bool = True):
         _check(load_library().afqmc_profile(self._ctx, int(bool(enable))))
@@ -260,6 +277,36 @@ def local_energy_noalloc(N, n_up, n_dn, n_chol, n_pairs, pairs_per_walker, h, L,
                                         e_local.data_ptr(), force_bias.data_ptr(), s.cuda_stream)
     if st != 0:
         raise AfqmcError(st, lib.afqmc_noalloc_last_error().decode())
+
+
+class Batch:
+    """Several contexts stepped together by one CUDA graph launch per step.
+    Each context must have been created with its own stream."""
+
+    def __init__(self, contexts, stream=None):
+        import torch
+        self.contexts = list(contexts)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._ctx.value for c in self.contexts])
+        self._b = ctypes.c_void_p()
+        _check(load_library().afqmc_batch_create(len(self.contexts), arr, self.stream.cuda_stream, ctypes.byref(self._b)))
+
+    def step(self, n_steps: int = 1):
+        _check(load_library().afqmc_batch_step(self._b, int(n_steps)))
+
+    def sync(self):
+        _check(load_library().afqmc_batch_sync(self._b))
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            load_library().afqmc_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count() -> int:

@@ -21,6 +21,14 @@ static afqmc_status fail(afqmc_status st, const char* fmt, ...) {
     return st;
 }
 
+afqmc_status set_error(afqmc_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
 #define CK(call)                                                                                     \
     do {                                                                                             \
         cudaError_t e_ = (call);                                                                     \
@@ -152,6 +160,9 @@ static Dims dims_of(const afqmc_config* c) {
     d.N = c->N; d.nu = c->n_up; d.nd = c->n_dn; d.nt = c->n_up + c->n_dn;
     d.G = c->n_chol; d.K = c->K; d.W = c->n_walkers; d.P = c->n_paths;
     d.pairs = (long long)c->n_walkers * c->n_paths;
+    d.ov_wpb = 0;
+    d.tc_tp = 0;
+    d.cheb_threads = 0;
     return d;
 }
 
@@ -240,7 +251,7 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
                 (long long)d.N * d.N);
     CK(cudaGetLastError());
     if ((st = prof_mark(ctx, PH_PROPOSE)) != AFQMC_OK) return st;
-    CK(trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phiprop, w.alive, d.P, w.status));
+    CK(trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phiprop, w.alive, d.P, w.status, d.cheb_threads));
     if ((st = prof_mark(ctx, PH_TRIAL)) != AFQMC_OK) return st;
     for (int spin = 0; spin < 2; ++spin)
         CK(overlap_lu(s, d, spin, w.Phiprop, (long long)d.N * d.nu, orbitals, w.logdet_prop, nullptr, w.alive, w.status,

@@ -171,6 +171,10 @@ struct Workspace {
 struct Dims {
     int N, nu, nd, nt, G, K, W, P;
     long long pairs;
+    // launch shapes chosen by the autotuner (0 = built-in default)
+    int ov_wpb;        // warps (matrices) per block of the overlap kernel
+    int tc_tp;         // pairs per block of the tensor-core contraction
+    int cheb_threads;  // threads per block of the trial-orbital kernel
 };
 
 }  // namespace afq

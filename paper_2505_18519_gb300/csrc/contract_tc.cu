@@ -582,6 +582,15 @@ cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const
                         double2* vpair, double2* epair, int* status, bool f16) {
     TcShape s;
     if (!tc_shape(d.N, d.nu, d.nd, f16, s)) return cudaErrorInvalidValue;
+    if (d.tc_tp > 0 && d.tc_tp < s.TP) {   // fewer pairs per block: same tensor-memory layout rules, less shared memory
+        s.TP = d.tc_tp;
+        s.NB1 = ((s.TP * d.nu + 15) / 16) * 16;
+        s.c1col = (s.GT / s.GPT) * s.NB1;
+        s.d2col = f16 ? s.c1col + s.NB1 : s.c1col;
+        size_t smem = 1024 + 2 * (size_t)s.NB1 * s.NPAD * 2 + 2 * (size_t)s.TP * s.NB2 * s.NPAD * 2 + 32768 +
+                      2 * (size_t)128 * s.NPAD * 2;
+        s.smem = smem < 120 * 1024 ? 120 * 1024 : smem;
+    }
     long long G1p = (long long)((d.G + 1 + s.GT - 1) / s.GT) * s.GT;
     const int* lexp = reinterpret_cast<const int*>(static_cast<const uint8_t*>(image) +
                                                    (size_t)(G1p / s.GPT) * s.NKB * 32768);

@@ -2,6 +2,9 @@
 #pragma once
 #include "common.cuh"
 
+// api.cu: record an error message for afqmc_last_error and return `st`
+afqmc_status set_error(afqmc_status st, const char* fmt, ...);
+
 namespace afq {
 
 // linalg_fp64.cu
@@ -13,7 +16,7 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
 cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, double2* dst, const int* alive,
                              int* status, int n_walkers);
 cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,
-                           double* Out, const int* alive, int P, int* status);
+                           double* Out, const int* alive, int P, int* status, int threads = 256);
 cudaError_t one_body_propagator(cudaStream_t s, int N, int G, double dtau, const double* h, const double* L, double* T,
                                 double* scratch3, double* expT);
 

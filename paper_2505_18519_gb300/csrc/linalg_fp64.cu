@@ -208,7 +208,7 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
     int n = spin == 0 ? d.nu : d.nd;
     int col0 = spin == 0 ? 0 : d.nu;
     size_t per = overlap_smem_per_warp(n, Theta != nullptr);
-    int wpb = 4;
+    int wpb = d.ov_wpb > 0 ? d.ov_wpb : 4;
     while (wpb > 1 && per * wpb > 200 * 1024) wpb >>= 1;
     if (per * wpb > 220 * 1024) return cudaErrorInvalidValue;
     size_t smem = per * wpb;
@@ -405,8 +405,9 @@ __global__ void __launch_bounds__(256) chebyshev_expm_kernel(int N, int nu, long
 }
 
 cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,
-                           double* Out, const int* alive, int P, int* status) {
+                           double* Out, const int* alive, int P, int* status, int threads) {
     if (problems <= 0) return cudaSuccess;
+    if (threads != 128 && threads != 256) threads = 256;
     size_t vec = 3 * (size_t)N * nu * sizeof(double);
     size_t full = vec + (size_t)N * N * sizeof(double);
     cudaError_t e;
@@ -415,14 +416,14 @@ cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, co
             e = cudaFuncSetAttribute(chebyshev_expm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
             if (e != cudaSuccess) return e;
         }
-        chebyshev_expm_kernel<true><<<(unsigned)problems, 256, full, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status); count_launches(1);
+        chebyshev_expm_kernel<true><<<(unsigned)problems, threads, full, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status); count_launches(1);
     } else {
         if (vec > 200 * 1024) return cudaErrorInvalidValue;
         if (vec > 48 * 1024) {
             e = cudaFuncSetAttribute(chebyshev_expm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec);
             if (e != cudaSuccess) return e;
         }
-        chebyshev_expm_kernel<false><<<(unsigned)problems, 256, vec, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status); count_launches(1);
+        chebyshev_expm_kernel<false><<<(unsigned)problems, threads, vec, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status); count_launches(1);
     }
     return cudaGetLastError();
 }

@@ -1,0 +1,106 @@
+"""Batched stepping of several systems through one CUDA graph per step, and
+the launch-shape autotuner: both must leave every result bit for bit equal to
+stepping each context on its own with the built-in launch shapes."""
+
+import numpy as np
+import pytest
+
+import afqmc_inputs as ai
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2505_18519_gb300 import afqmc as lib  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2505_18519_gb300 import build
+    build.build()
+    lib.load_library()
+
+
+SYSTEMS = [
+    (ai.SystemSpec(8, 4, 4, 32, 8, False, 1000), 16, 8, "fp64"),
+    (ai.SystemSpec(37, 7, 5, 40, 9, True, 77), 6, 5, "fp16x3"),
+    (ai.SystemSpec(50, 10, 10, 250, 50, True, 1001), 4, 8, "fp64"),
+    (ai.SystemSpec(70, 14, 13, 90, 10, True, 81), 3, 7, "bf16x3"),
+]
+
+
+def _ctx(spec, W, P, prec, seed):
+    s = ai.make_system(spec)
+    cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, 0.01, seed, n_burn=2, precision=prec)
+    return lib.Context(cfg, s.h, s.L, s.Phi0, s.U, stream=torch.cuda.Stream())
+
+
+def test_batch_graph_equals_individual_steps():
+    batched = [_ctx(spec, W, P, prec, 50 + i) for i, (spec, W, P, prec) in enumerate(SYSTEMS)]
+    single = [_ctx(spec, W, P, prec, 50 + i) for i, (spec, W, P, prec) in enumerate(SYSTEMS)]
+    b = lib.Batch(batched)
+    before = lib.launch_count()
+    b.step(3)
+    b.sync()
+    graph_kernels = lib.launch_count() - before
+    before = lib.launch_count()
+    for c in single:
+        c.step(3)
+    torch.cuda.synchronize()
+    assert graph_kernels == lib.launch_count() - before   # the graph runs the same kernels
+    for cb, cs in zip(batched, single):
+        assert cb.save_state() == cs.save_state()
+        assert np.array_equal(cb.history(3), cs.history(3))
+    # the contexts stay usable on their own between batch steps
+    e = batched[1].energy()
+    assert np.isfinite(e["e_mix"])
+    b.step(1)
+    b.sync()
+    single[1].step(1)
+    assert batched[1].save_state() == single[1].save_state()
+    b.close()
+    for c in batched + single:
+        c.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x3"])
+def test_autotune_changes_no_result(prec):
+    spec = ai.SystemSpec(50, 10, 10, 250, 50, True, 1001)
+    a = _ctx(spec, 16, 32, prec, 7)
+    ref = _ctx(spec, 16, 32, prec, 7)
+    chosen = a.autotune()
+    assert set(chosen) == {"overlap_warps_per_block", "tc_pairs_per_block", "trial_threads"}
+    ea, er = a.energy(walkers=True), ref.energy(walkers=True)
+    assert np.array_equal(ea["e_walker"], er["e_walker"])
+    a.step(2)
+    ref.step(2)
+    assert a.save_state() == ref.save_state()
+    a.close()
+    ref.close()
+
+
+def test_uneven_batch_of_sixteen_systems():
+    """Sixteen synthetic molecules of uneven size (N ~ U[40, 125], n = N/5,
+    Gamma = 5N, K = N), mixed precision, 32 walkers x 16 paths each, autotuned,
+    one graph launch per step; one system checked against its own run."""
+    specs = ai.batched_system_specs(16, n_range=(40, 125))
+    ctxs = []
+    for i, spec in enumerate(specs):
+        c = _ctx(spec, 32, 16, "fp16x3", 900 + i)
+        c.autotune()
+        ctxs.append(c)
+    b = lib.Batch(ctxs)
+    b.step(2)
+    b.sync()
+    for c in ctxs:
+        h = c.history(2)
+        assert np.all(np.isfinite(h)) and c.stats()["status"] == 0
+    k = 5
+    alone = _ctx(specs[k], 32, 16, "fp16x3", 900 + k)
+    alone.step(2)
+    assert alone.save_state() == ctxs[k].save_state()
+    b.close()
+    for c in ctxs + [alone]:
+        c.close()
