@@ -5,4 +5,4 @@ step and of its counter-based random numbers.  Only ``tests/``, the smoke check
 and the CPU-baseline leg of ``bench.py`` may import it; the CUDA library never
 does, and the two share no code.
 """
-from . import philox, afqmc  # noqa: F401
+from . import philox, afqmc, mlp  # noqa: F401

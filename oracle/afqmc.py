@@ -26,7 +26,9 @@ Readings of points where the paper is silent or ambiguous (R1-R14):
       applied to the orbitals; exp(-tau T/2) and exp(sum_k x_k U_k) exact.
   R7  Metropolis accepts iff u < alpha with u in [0, 1) (53-bit).
   R8  proposals: independent draws from the prior p_T (the paper's choice),
-      or preconditioned Crank-Nicolson x' = sqrt(1-beta^2) x + beta xi.
+      preconditioned Crank-Nicolson x' = sqrt(1-beta^2) x + beta xi, a
+      Gaussian random walk x' = x + s xi, or the learned proposal (oracle.mlp)
+      mixed with the random walk; Metropolis-Hastings with the proposal ratio.
   R9  walkers are re-orthonormalised every step (QR, diag(R) > 0).
   R10 no population control; weights carried, optional constant E_T.
   R11 initial walkers phi_w = Phi(x_w), x_w ~ p; paths x_wp ~ p; W = 1;
@@ -64,6 +66,10 @@ class OracleConfig:
     e_shift: float = 0.0         # constant E_T, weights *= exp(tau E_T) per step
     taylor_order: int = 6
     kill_threshold: float = 1e-10  # |sum_p S_p| below this kills the walker
+    rw_step: float = 0.3         # Gaussian random-walk step (proposal "rw" and the fallback of "mlp")
+    mlp_mix: float = 0.1         # probability of a random-walk move under proposal "mlp"
+    mlp_params: object = None    # flat parameters of the learned proposal (oracle.mlp layout)
+    mlp_hidden: int = 256
 
 
 @dataclasses.dataclass
@@ -234,21 +240,39 @@ def reorthonormalise(phi: np.ndarray) -> np.ndarray:
 
 
 def mcmc_sweep(ham: Hamiltonian, cfg: OracleConfig, st: State, logov_cur: np.ndarray, alive: np.ndarray,
-               step: int, sweep: int, tag_prop: int, tag_acc: int) -> int:
+               step: int, sweep: int, tag_prop: int, tag_acc: int, mlp_mu_logv=None) -> int:
     """One Metropolis update of every path of every live walker against the
     walkers' current orbitals (leapfrog step 2, Sec. III A; Appendix B.2):
-    propose x' (from the prior p_T, or pCN), build Phi(x'), accept iff
-    u < |<Phi(x')|phi>| / |<Phi(x)|phi>|.  Updates st.x, st.Phi and logov_cur in
-    place; returns the number of accepted moves."""
+    propose x', build Phi(x'), accept iff u < alpha with the Metropolis-Hastings
+    ratio alpha of the target p(x)|<Phi(x)|phi>| (Eq. (23)) and the proposal:
+    prior or pCN proposals leave alpha = |<Phi(x')|phi>| / |<Phi(x)|phi>| (the
+    paper's form); the random walk adds p(x')/p(x); the learned proposal
+    q = N(mu_w, diag v_w) adds p(x') q(x) / (p(x) q(x')).  Updates st.x, st.Phi
+    and logov_cur in place; returns the number of accepted moves."""
     W, P, K = st.x.shape
     pair_ids = (st.walker_index[:, None] * P + np.arange(P)[None, :]).reshape(-1)
     xi = px.normals(cfg.seed, tag_prop, step, pair_ids, sweep, K).reshape(W, P, K)
-    u = px.uniforms(cfg.seed, tag_acc, step, pair_ids, sweep, 1).reshape(W, P)
+    uu = px.uniforms(cfg.seed, tag_acc, step, pair_ids, sweep, 2).reshape(W, P, 2)
+    u, u_mix = uu[..., 0], uu[..., 1]
+    extra = np.zeros((W, P))
     if cfg.proposal == "prior":
         x_new = xi
     elif cfg.proposal == "pcn":
         b = cfg.pcn_beta
         x_new = math.sqrt(1.0 - b * b) * st.x + b * xi
+    elif cfg.proposal == "rw":
+        x_new = st.x + cfg.rw_step * xi
+        extra = -0.5 * (np.sum(x_new * x_new, axis=-1) - np.sum(st.x * st.x, axis=-1))
+    elif cfg.proposal == "mlp":
+        mu, logv = mlp_mu_logv
+        use_rw = u_mix < cfg.mlp_mix
+        x_rw = st.x + cfg.rw_step * xi
+        x_q = mu[:, None, :] + np.exp(0.5 * logv)[:, None, :] * xi
+        x_new = np.where(use_rw[..., None], x_rw, x_q)
+        extra = -0.5 * (np.sum(x_new * x_new, axis=-1) - np.sum(st.x * st.x, axis=-1))
+        lq_old = -0.5 * np.sum((st.x - mu[:, None, :]) ** 2 * np.exp(-logv)[:, None, :], axis=-1)
+        lq_new = -0.5 * np.sum((x_new - mu[:, None, :]) ** 2 * np.exp(-logv)[:, None, :], axis=-1)
+        extra = extra + np.where(use_rw, 0.0, lq_old - lq_new)
     else:
         raise ValueError(cfg.proposal)
     n_acc = 0
@@ -258,7 +282,7 @@ def mcmc_sweep(ham: Hamiltonian, cfg: OracleConfig, st: State, logov_cur: np.nda
         for p in range(P):
             Phi_new = trial_orbitals(ham, x_new[w, p])
             lo_new = log_overlap(ham, Phi_new, st.phi_up[w], st.phi_dn[w])
-            delta = lo_new.real - logov_cur[w, p].real
+            delta = lo_new.real - logov_cur[w, p].real + extra[w, p]
             if delta >= 0.0 or u[w, p] < math.exp(delta):
                 st.x[w, p] = x_new[w, p]
                 st.Phi[w, p] = Phi_new
@@ -297,7 +321,7 @@ def _wrap(a):
     return np.angle(np.exp(1j * a))
 
 
-def step(ham: Hamiltonian, cfg: OracleConfig, st: State):
+def step(ham: Hamiltonian, cfg: OracleConfig, st: State, mlp_mu_logv=None):
     """One leapfrog step (Sec. III A and the propagation outline of Appendix B.2).
 
     Returns the new state and a dict of diagnostics; ``mixed`` holds the mixed
@@ -341,9 +365,14 @@ def step(ham: Hamiltonian, cfg: OracleConfig, st: State):
         I_abs[w] = abs(I_full[w])
 
     # Leapfrog step 2: Metropolis update of the paths at phi' (Sec. III A).
+    if cfg.proposal == "mlp" and mlp_mu_logv is None:
+        from . import mlp as _mlp
+        f = _mlp.features(ham.Phi0, ham.U, new.phi_up, new.phi_dn)
+        fw = _mlp.forward(cfg.mlp_params, f, ham.U.shape[0], cfg.mlp_hidden)
+        mlp_mu_logv = (fw["mu"], fw["logv"])
     n_acc = 0
     for s in range(cfg.n_sweeps):
-        n_acc += mcmc_sweep(ham, cfg, new, logov_new, alive, i, s, px.TAG_PROPOSE, px.TAG_ACCEPT)
+        n_acc += mcmc_sweep(ham, cfg, new, logov_new, alive, i, s, px.TAG_PROPOSE, px.TAG_ACCEPT, mlp_mu_logv)
 
     # Hand-off ratio Eq. (28) and the constraints Eq. (17), (29).
     for w in range(W):
