@@ -65,7 +65,10 @@ enum {
 /* Metropolis proposal for the paths (Sec. III A; Appendix B.2) */
 enum {
     AFQMC_PROPOSAL_PRIOR = 0,  /* independent draw x' ~ N(0, I) (the paper's sampler) */
-    AFQMC_PROPOSAL_PCN = 1     /* x' = sqrt(1 - beta^2) x + beta xi, xi ~ N(0, I) */
+    AFQMC_PROPOSAL_PCN = 1,    /* x' = sqrt(1 - beta^2) x + beta xi, xi ~ N(0, I) */
+    AFQMC_PROPOSAL_RW = 2,     /* Gaussian random walk x' = x + rw_step xi */
+    AFQMC_PROPOSAL_MLP = 3     /* learned proposal N(mu(f_w), diag v(f_w)) of an MLP on walker features,
+                                  mixed with the random walk (probability mlp_mix); burn-in uses the prior */
 };
 
 /* arithmetic of the two big contractions (R = Phi^T L_g and M = R Theta) */
@@ -102,6 +105,10 @@ typedef struct {
     int64_t walker_offset; /* global index of walker 0 in the random streams: walker w draws as
                               walker walker_offset + w, so shards of one population on several
                               GPUs reproduce the single-GPU run exactly */
+    double rw_step;     /* random-walk step (AFQMC_PROPOSAL_RW, and the fallback of AFQMC_PROPOSAL_MLP) */
+    double mlp_mix;     /* probability of a random-walk move under AFQMC_PROPOSAL_MLP */
+    double mlp_lr;      /* Adam learning rate of the proposal network */
+    int mlp_train;      /* 1: after every step, one Adam step on the paths' states (online training) */
 } afqmc_config;
 
 /* Fill *cfg with defaults (combined constraint, prior proposal, FP64, Taylor
@@ -239,6 +246,27 @@ const char* afqmc_last_error(void);
  * Results do not depend on the shapes.  Synchronises; not during capture.
  * chosen (nullable) receives the three choices (0 = built-in default). */
 afqmc_status afqmc_autotune(afqmc_ctx* ctx, int* chosen);
+
+/* The learned proposal (AFQMC_PROPOSAL_MLP), an extension the paper allows
+ * (any proposal with an exact Metropolis acceptance, Sec. III A).  Walker
+ * features f_k = Re sum_s Tr[(Phi0_s^T phi_s)^-1 Phi0_s^T U_k phi_s] (the gradient
+ * of log|<Phi(x)|phi>| at x = 0); out = W3 tanh(W2 tanh(W1 f + b1) + b2) + b3 with
+ * hidden width 256; mu = f + out[:K], logv = clip(out[K:], -6, 3).  GEMMs in BF16
+ * with FP32 accumulation; master weights and Adam state FP32.  Parameters: one
+ * flat float vector W1 (256 x K), b1 (256), W2 (256 x 256), b2 (256),
+ * W3 (2K x 256), b3 (2K), row-major; afqmc_mlp_n_params(K) floats. */
+int64_t afqmc_mlp_n_params(int K);
+/* Copy the parameters out (set = 0) or in (set = 1); n must be afqmc_mlp_n_params(K). */
+afqmc_status afqmc_mlp_params(afqmc_ctx* ctx, float* params, int64_t n, int set);
+/* Evaluate the network on host inputs, for B <= n_walkers walkers:
+ *   features B*K, x B*n_paths*K (hidden variables of the paths to fit),
+ *   mu_logv (nullable) B*2K out: mu then logv per walker,
+ *   loss (nullable) out: 1/(B P) sum 1/2 sum_k [(x - mu)^2/v + logv],
+ *   grad (nullable) out: d loss / d params (flat layout).  Synchronises. */
+afqmc_status afqmc_mlp_eval(afqmc_ctx* ctx, int B, const float* features, const double* x, float* mu_logv,
+                            double* loss, float* grad);
+/* Features, mu and logv (each n_walkers*K floats, nullable) the last step used. */
+afqmc_status afqmc_mlp_state(afqmc_ctx* ctx, float* features, float* mu, float* logv);
 
 /* Several systems (contexts of any sizes and precisions) stepped together: one
  * leapfrog step of every context is captured once into one CUDA graph (a fork

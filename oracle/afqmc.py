@@ -312,8 +312,9 @@ def init(ham: Hamiltonian, cfg: OracleConfig, walker_index=None) -> State:
         for p in range(P):
             logov[w, p] = log_overlap(ham, Phi[w, p], phi_up[w], phi_dn[w])
     alive = np.ones(W, dtype=bool)
+    burn_cfg = dataclasses.replace(cfg, proposal="prior") if cfg.proposal == "mlp" else cfg   # no network output yet
     for b in range(cfg.n_burn):
-        mcmc_sweep(ham, cfg, st, logov, alive, 0, b, px.TAG_BURN_PROPOSE, px.TAG_BURN_ACCEPT)
+        mcmc_sweep(ham, burn_cfg, st, logov, alive, 0, b, px.TAG_BURN_PROPOSE, px.TAG_BURN_ACCEPT)
     return st
 
 

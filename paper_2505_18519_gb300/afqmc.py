@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libafqmc.so")
 
 CONSTRAINTS = {"combined": 0, "separate": 1, "half_plane": 2}
-PROPOSALS = {"prior": 0, "pcn": 1}
+PROPOSALS = {"prior": 0, "pcn": 1, "rw": 2, "mlp": 3}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "fp16x3": 2}
 STATE_MAGIC = 0x4146514D43535431
 
@@ -32,6 +32,8 @@ class AfqmcConfig(ctypes.Structure):
         ("precision", ctypes.c_int), ("taylor_order", ctypes.c_int), ("history_capacity", ctypes.c_int),
         ("dtau", ctypes.c_double), ("pcn_beta", ctypes.c_double), ("e_shift", ctypes.c_double),
         ("kill_threshold", ctypes.c_double), ("seed", ctypes.c_uint64), ("walker_offset", ctypes.c_int64),
+        ("rw_step", ctypes.c_double), ("mlp_mix", ctypes.c_double), ("mlp_lr", ctypes.c_double),
+        ("mlp_train", ctypes.c_int),
     ]
 
 
@@ -41,7 +43,7 @@ EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc
            "afqmc_observables", "afqmc_history", "afqmc_stats", "afqmc_state_save", "afqmc_state_load",
            "afqmc_destroy", "afqmc_last_error", "afqmc_philox_fill", "afqmc_profile", "afqmc_profile_read",
            "afqmc_launch_count", "afqmc_autotune", "afqmc_batch_create", "afqmc_batch_step", "afqmc_batch_sync",
-           "afqmc_batch_destroy")
+           "afqmc_batch_destroy", "afqmc_mlp_n_params", "afqmc_mlp_params", "afqmc_mlp_eval", "afqmc_mlp_state")
 
 PHASES = ("overlap", "contract", "average", "fields", "propagate", "ratio", "propose", "trial_orbitals",
           "mcmc_overlap", "accept", "finish")
@@ -100,6 +102,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.afqmc_batch_sync.restype = I
     lib.afqmc_batch_destroy.argtypes = [P]
     lib.afqmc_batch_destroy.restype = None
+    lib.afqmc_mlp_n_params.argtypes = [I]
+    lib.afqmc_mlp_n_params.restype = ctypes.c_int64
+    lib.afqmc_mlp_params.argtypes = [P, P, ctypes.c_int64, I]
+    lib.afqmc_mlp_params.restype = I
+    lib.afqmc_mlp_eval.argtypes = [P, I, P, P, P, P, P]
+    lib.afqmc_mlp_eval.restype = I
+    lib.afqmc_mlp_state.argtypes = [P, P, P, P]
+    lib.afqmc_mlp_state.restype = I
     lib.afqmc_noalloc_scratch_bytes.argtypes = []
     lib.afqmc_noalloc_scratch_bytes.restype = SZ
     lib.afqmc_local_energy_noalloc.argtypes = [I, I, I, I, ctypes.c_int64, I, P, P, P, P, P, P, P, P]
@@ -123,7 +133,8 @@ def _check(st: int):
 
 def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_sweeps=1, n_burn=20,
                 constraint="combined", proposal="prior", precision="fp64", taylor_order=6, history_capacity=1024,
-                pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10, walker_offset=0) -> AfqmcConfig:
+                pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10, walker_offset=0, rw_step=0.3, mlp_mix=0.1,
+                mlp_lr=1e-3, mlp_train=False) -> AfqmcConfig:
     lib = load_library()
     c = AfqmcConfig()
     lib.afqmc_config_default(ctypes.byref(c))
@@ -133,6 +144,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
     c.taylor_order, c.history_capacity = taylor_order, history_capacity
     c.dtau, c.pcn_beta, c.e_shift, c.kill_threshold, c.seed = dtau, pcn_beta, e_shift, kill_threshold, seed
     c.walker_offset = walker_offset
+    c.rw_step, c.mlp_mix, c.mlp_lr, c.mlp_train = rw_step, mlp_mix, mlp_lr, int(bool(mlp_train))
     return c
 
 
@@ -222,6 +234,37 @@ class Context:
         out = (ctypes.c_int * 3)()
         _check(load_library().afqmc_autotune(self._ctx, out))
         return dict(overlap_warps_per_block=out[0], tc_pairs_per_block=out[1], trial_threads=out[2])
+
+    # -- learned proposal ---------------------------------------------------------
+    def mlp_params(self, new=None):
+        """Get (new None) or set the flat FP32 parameters of the proposal network."""
+        lib = load_library()
+        n = int(lib.afqmc_mlp_n_params(self.K))
+        if new is None:
+            out = np.empty(n, dtype=np.float32)
+            _check(lib.afqmc_mlp_params(self._ctx, out.ctypes.data, n, 0))
+            return out
+        a = np.ascontiguousarray(new, dtype=np.float32)
+        _check(lib.afqmc_mlp_params(self._ctx, a.ctypes.data, a.size, 1))
+
+    def mlp_eval(self, features, x):
+        """Network output, loss and flat gradient for features (B, K), x (B, P, K)."""
+        lib = load_library()
+        f = np.ascontiguousarray(features, dtype=np.float32)
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        B = f.shape[0]
+        mu_logv = np.empty((B, 2 * self.K), dtype=np.float32)
+        loss = ctypes.c_double()
+        grad = np.empty(int(lib.afqmc_mlp_n_params(self.K)), dtype=np.float32)
+        _check(lib.afqmc_mlp_eval(self._ctx, B, f.ctypes.data, xx.ctypes.data, mu_logv.ctypes.data, ctypes.byref(loss),
+                                  grad.ctypes.data))
+        return dict(mu=mu_logv[:, :self.K], logv=mu_logv[:, self.K:], loss=loss.value, grad=grad)
+
+    def mlp_state(self):
+        """Features, mu and logv (each (W, K)) used by the last step's proposals."""
+        out = [np.empty((self.W, self.K), dtype=np.float32) for _ in range(3)]
+        _check(load_library().afqmc_mlp_state(self._ctx, *[o.ctypes.data for o in out]))
+        return dict(features=out[0], mu=out[1], logv=out[2])
 
     # -- profiling ----------------------------------------------------------------
     def profile(self, enable: bool = True):

@@ -125,6 +125,10 @@ extern "C" void afqmc_config_default(afqmc_config* c) {
     c->history_capacity = 1024;
     c->pcn_beta = 1.0;
     c->kill_threshold = 1e-10;
+    c->rw_step = 0.3;
+    c->mlp_mix = 0.1;
+    c->mlp_lr = 1e-3;
+    c->mlp_train = 0;
 }
 
 static const char* check_config(const afqmc_config* c) {
@@ -137,7 +141,11 @@ static const char* check_config(const afqmc_config* c) {
     if ((long long)c->n_walkers * c->n_paths > (1ll << 31)) return "too many walker-path pairs";
     if (c->n_sweeps < 1 || c->n_burn < 0) return "n_sweeps >= 1 and n_burn >= 0";
     if (c->constraint < 0 || c->constraint > 2) return "unknown constraint";
-    if (c->proposal < 0 || c->proposal > 1) return "unknown proposal";
+    if (c->proposal < 0 || c->proposal > 3) return "unknown proposal";
+    if ((c->proposal == AFQMC_PROPOSAL_RW || c->proposal == AFQMC_PROPOSAL_MLP) && !(c->rw_step > 0.0))
+        return "rw_step must be > 0";
+    if (c->proposal == AFQMC_PROPOSAL_MLP && !(c->mlp_mix >= 0.0 && c->mlp_mix <= 1.0)) return "mlp_mix in [0, 1]";
+    if (c->proposal == AFQMC_PROPOSAL_MLP && !(c->mlp_lr >= 0.0)) return "mlp_lr must be >= 0";
     if (c->precision < AFQMC_PRECISION_FP64 || c->precision > AFQMC_PRECISION_FP16X3) return "unknown precision";
     if (c->taylor_order < 1 || c->taylor_order > 32) return "taylor_order must be in [1, 32]";
     if (c->history_capacity < 1) return "history_capacity must be >= 1";
@@ -219,6 +227,47 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.reduce = (double*)take(8 * 8);
     w.counters = (unsigned long long*)take(8 * 8);
     w.status = (int*)take(4);
+    if (c->proposal == AFQMC_PROPOSAL_MLP) {
+        MlpBuffers& m = w.mlp;
+        const size_t H = 256, Kp = (K + 15) / 16 * 16, Wp = (W + 15) / 16 * 16, np = (size_t)mlp_n_params(d.K);
+        m.Kp = (int)Kp;
+        m.Wp = (int)Wp;
+        m.UPhi0 = (double*)take(K * N * nu * 8);
+        m.Theta0 = (double2*)take(W * N * nt * 16);
+        m.logdet0 = (double2*)take(W * 2 * 16);
+        m.featf = (float*)take(Wp * Kp * 4);
+        m.featb = (__nv_bfloat16*)take(Wp * Kp * 2);
+        m.theta = (float*)take(np * 4);
+        m.adam_m = (float*)take(np * 4);
+        m.adam_v = (float*)take(np * 4);
+        m.grad = (float*)take(np * 4);
+        m.W1b = (__nv_bfloat16*)take(H * Kp * 2);
+        m.W2b = (__nv_bfloat16*)take(H * H * 2);
+        m.W3b = (__nv_bfloat16*)take(2 * Kp * H * 2);
+        m.Zf = (float*)take(Wp * H * 4);
+        m.H1f = (float*)take(Wp * H * 4);
+        m.H2f = (float*)take(Wp * H * 4);
+        m.dHf = (float*)take(Wp * H * 4);
+        m.dZf = (float*)take(Wp * H * 4);
+        m.H1b = (__nv_bfloat16*)take(Wp * H * 2);
+        m.H2b = (__nv_bfloat16*)take(Wp * H * 2);
+        m.dZb = (__nv_bfloat16*)take(Wp * H * 2);
+        m.outf = (float*)take(Wp * 2 * Kp * 4);
+        m.doutf = (float*)take(Wp * 2 * Kp * 4);
+        m.doutb = (__nv_bfloat16*)take(Wp * 2 * Kp * 2);
+        m.mu = (float*)take(W * K * 4);
+        m.logv = (float*)take(W * K * 4);
+        m.logv_raw = (float*)take(W * K * 4);
+        m.gW1p = (float*)take(H * Kp * 4);
+        m.gb1 = (float*)take(H * 4);
+        m.gW2 = (float*)take(H * H * 4);
+        m.gb2 = (float*)take(H * 4);
+        m.gW3p = (float*)take(2 * Kp * H * 4);
+        m.gb3p = (float*)take(2 * Kp * 4);
+        m.loss_part = (double*)take(W * 8);
+        m.loss = (double*)take(8);
+        m.counter = (unsigned long long*)take(8);
+    }
     w.total = (off + 255) & ~(size_t)255;
     if (ws) *ws = w;
     return w.total;
@@ -232,6 +281,7 @@ extern "C" size_t afqmc_workspace_bytes(const afqmc_config* cfg) {
 static StepParams params_of(const afqmc_config* c) {
     StepParams p;
     p.seed = c->seed; p.woff = c->walker_offset; p.dtau = c->dtau; p.pcn_beta = c->pcn_beta; p.e_shift = c->e_shift;
+    p.rw_step = c->rw_step; p.mlp_mix = c->mlp_mix;
     p.kill_threshold = c->kill_threshold; p.constraint = c->constraint; p.proposal = c->proposal;
     p.taylor_order = c->taylor_order; p.history_capacity = c->history_capacity;
     return p;
@@ -240,13 +290,14 @@ static StepParams params_of(const afqmc_config* c) {
 // One Metropolis sweep of every path against the walker orbitals `orbitals`
 // (phi' during a step, phi during burn-in).
 static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t tag_prop, uint32_t tag_acc,
-                               uint32_t sweep) {
+                               uint32_t sweep, bool burn_in = false) {
     const Dims& d = ctx->d;
     Workspace& w = ctx->ws;
     cudaStream_t s = ctx->stream;
     StepParams p = params_of(&ctx->cfg);
+    if (burn_in && p.proposal == AFQMC_PROPOSAL_MLP) p.proposal = AFQMC_PROPOSAL_PRIOR;   // no network output yet
     afqmc_status st;
-    CK(propose(s, d, p, w.counters, tag_prop, sweep, w.x, w.alive, w.xprop));
+    CK(propose(s, d, p, w.counters, tag_prop, tag_acc, sweep, w.x, w.alive, w.mlp.mu, w.mlp.logv, w.xprop));
     gemm_nn_f64(s, (int)d.pairs, d.N * d.N, d.K, 1.0, w.xprop, d.K, w.U, (long long)d.N * d.N, 0.0, w.Sprop,
                 (long long)d.N * d.N);
     CK(cudaGetLastError());
@@ -257,8 +308,8 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
         CK(overlap_lu(s, d, spin, w.Phiprop, (long long)d.N * d.nu, orbitals, w.logdet_prop, nullptr, w.alive, w.status,
                       d.pairs, d.P));
     if ((st = prof_mark(ctx, PH_MCMC_OVERLAP)) != AFQMC_OK) return st;
-    CK(accept(s, d, p, w.counters, tag_acc, sweep, w.logdet_prop, w.xprop, w.Phiprop, w.alive, w.logov_cur, w.x, w.Phi,
-              w.counters));
+    CK(accept(s, d, p, w.counters, tag_acc, sweep, w.logdet_prop, w.xprop, w.Phiprop, w.alive, w.mlp.mu, w.mlp.logv,
+              w.logov_cur, w.x, w.Phi, w.counters));
     return prof_mark(ctx, PH_ACCEPT);
 }
 
@@ -349,7 +400,13 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
                        d.pairs, d.P);
         combine_logdet(s, d.pairs, w.logdet_new, w.logov_cur);
         if ((e = cudaGetLastError()) != cudaSuccess) { st = fail(AFQMC_ERR_CUDA, "init kernels: %s", cudaGetErrorString(e)); break; }
-        for (int b = 0; b < cfg->n_burn && st == AFQMC_OK; ++b) st = mcmc_sweep(ctx, w.phi, TAG_BURN_PROPOSE, TAG_BURN_ACCEPT, b);
+        if (cfg->proposal == AFQMC_PROPOSAL_MLP &&
+            (e = mlp_prepare(s, d, w.mlp, w.U, w.Phi0, cfg->seed)) != cudaSuccess) {
+            st = fail(AFQMC_ERR_CUDA, "learned proposal set-up: %s", cudaGetErrorString(e));
+            break;
+        }
+        for (int b = 0; b < cfg->n_burn && st == AFQMC_OK; ++b)
+            st = mcmc_sweep(ctx, w.phi, TAG_BURN_PROPOSE, TAG_BURN_ACCEPT, b, true);
         if (st != AFQMC_OK) break;
         // the burn-in acceptances are not counted in the run statistics
         if ((e = cudaMemsetAsync(w.counters, 0, 8 * 8, s)) != cudaSuccess ||
@@ -389,10 +446,16 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
                           d.pairs, d.P));
         CK(ratios(s, d, w.logov, w.logdet_new, w.sumS, w.logshift, w.alive, w.logov_cur, w.old_sum, w.ratio, w.Iabs));
         if ((st = prof_mark(ctx, PH_RATIO)) != AFQMC_OK) return st;
+        if (ctx->cfg.proposal == AFQMC_PROPOSAL_MLP) {       // proposal conditioned on the new walkers
+            CK(mlp_features(s, d, w.mlp, w.Phi0, w.phi_new, w.status));
+            CK(mlp_forward(s, d, w.mlp, d.W));
+        }
         for (int m = 0; m < ctx->cfg.n_sweeps; ++m) {                                  // Eq. (23)
             st = mcmc_sweep(ctx, w.phi_new, TAG_PROPOSE, TAG_ACCEPT, (uint32_t)m);
             if (st != AFQMC_OK) return st;
         }
+        if (ctx->cfg.proposal == AFQMC_PROPOSAL_MLP && ctx->cfg.mlp_train)   // one Adam step on the new states
+            CK(mlp_backward(s, d, w.mlp, d.W, w.x, (float)ctx->cfg.mlp_lr, true));
         CK(handoff(s, d, p, w.logov_cur, w.old_sum, w.ratio, w.Iabs, w.alive, w.weight, w.status));  // Eq. (28)-(29)
         CK(reorthonormalise(s, d, w.phi_new, w.phi, w.alive, w.status, d.W));
         CK(step_end(s, p, w.reduce, w.history, w.counters));

@@ -2,6 +2,7 @@
 // the counter-based generator, and the context/workspace layout.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <math.h>
@@ -77,7 +78,7 @@ __host__ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t 
 // Random-stream tags (counter word 3 = tag << 24 | sweep).
 enum : uint32_t {
     TAG_INIT_WALKER = 1, TAG_INIT_PATH = 2, TAG_FIELD = 3, TAG_PROPOSE = 4,
-    TAG_ACCEPT = 5, TAG_BURN_PROPOSE = 6, TAG_BURN_ACCEPT = 7
+    TAG_ACCEPT = 5, TAG_BURN_PROPOSE = 6, TAG_BURN_ACCEPT = 7, TAG_MLP_INIT = 9
 };
 
 __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
@@ -117,6 +118,26 @@ __device__ __forceinline__ double uniform_at0(uint64_t seed, uint32_t tag, uint3
 
 // ---------------------------------------------------------------- status word bits
 enum : int { STATUS_SINGULAR = 1, STATUS_NONFINITE = 2, STATUS_TIMEOUT = 4 };
+
+// ---------------------------------------------------------------- learned proposal buffers
+struct MlpBuffers {
+    int Kp, Wp;                        // K and W rounded up to 16
+    double* UPhi0;                     // K x N x n_up, U_k Phi0
+    double2* Theta0;                   // W x N x nt, phi (Phi0^T phi)^-1
+    double2* logdet0;                  // W x 2
+    float* featf;                      // Wp x Kp
+    __nv_bfloat16* featb;              // Wp x Kp
+    float *theta, *adam_m, *adam_v, *grad;   // flat parameters, moments, gradient
+    __nv_bfloat16 *W1b, *W2b, *W3b;    // H x Kp, H x H, 2Kp x H
+    float *Zf, *H1f, *H2f, *dHf, *dZf; // Wp x H
+    __nv_bfloat16 *H1b, *H2b, *dZb;    // Wp x H
+    float *outf, *doutf;               // Wp x 2Kp
+    __nv_bfloat16* doutb;              // Wp x 2Kp
+    float *mu, *logv, *logv_raw;       // W x K
+    float *gW1p, *gb1, *gW2, *gb2, *gW3p, *gb3p;   // padded weight gradients, bias sums
+    double *loss_part, *loss;          // W, 1
+    unsigned long long* counter;       // Adam steps taken
+};
 
 // ---------------------------------------------------------------- workspace layout
 // Every buffer of a context lives in the caller's workspace, 256-byte aligned.
@@ -165,6 +186,7 @@ struct Workspace {
     double* reduce;   // 8 doubles of scratch for reductions
     unsigned long long* counters;  // [0] step, [1] accepted (total), [2] proposed (total), [3] accepted this step
     int* status;      // 1 int
+    MlpBuffers mlp;   // learned proposal (only with AFQMC_PROPOSAL_MLP)
     size_t total;
 };
 

@@ -37,7 +37,7 @@ cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const
 struct StepParams {
     uint64_t seed;
     long long woff;   // global index of walker 0
-    double dtau, pcn_beta, e_shift, kill_threshold;
+    double dtau, pcn_beta, e_shift, kill_threshold, rw_step, mlp_mix;
     int constraint, proposal, taylor_order, history_capacity;
 };
 cudaError_t fill_normals(cudaStream_t s, double* out, long long rows, int cols, long long entity0, uint64_t seed,
@@ -56,10 +56,12 @@ cudaError_t ratios(cudaStream_t s, const Dims& d, const double2* logov, const do
                    const double2* sumS, const double2* logshift, const int* alive, double2* logov_cur,
                    double2* old_sum, double2* ratio, double* Iabs);
 cudaError_t propose(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
-                    uint32_t sweep, const double* x, const int* alive, double* xprop);
+                    uint32_t tag_acc, uint32_t sweep, const double* x, const int* alive, const float* mu,
+                    const float* logv, double* xprop);
 cudaError_t accept(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
                    uint32_t sweep, const double2* logdet_prop, const double* xprop, const double* Phiprop,
-                   const int* alive, double2* logov_cur, double* x, double* Phi, unsigned long long* counters);
+                   const int* alive, const float* mu, const float* logv, double2* logov_cur, double* x, double* Phi,
+                   unsigned long long* counters);
 cudaError_t combine_logdet(cudaStream_t s, long long pairs, const double2* logdet, double2* logov);
 cudaError_t handoff(cudaStream_t s, const Dims& d, const StepParams& p, const double2* logov_cur,
                     const double2* old_sum, const double2* ratio, const double* Iabs, const int* alive,
@@ -67,6 +69,17 @@ cudaError_t handoff(cudaStream_t s, const Dims& d, const StepParams& p, const do
 cudaError_t step_end(cudaStream_t s, const StepParams& p, const double* measured3, double* history,
                      unsigned long long* counters);
 cudaError_t set_value(cudaStream_t s, double* out, long long n, double v);
+
+// mlp.cu
+long long mlp_n_params(int K);
+cudaError_t mlp_prepare(cudaStream_t s, const Dims& d, const MlpBuffers& m, const double* U, const double* Phi0,
+                        uint64_t seed);
+cudaError_t mlp_pack(cudaStream_t s, const Dims& d, const MlpBuffers& m);
+cudaError_t mlp_features(cudaStream_t s, const Dims& d, const MlpBuffers& m, const double* Phi0, const double2* phi,
+                         int* status);
+cudaError_t mlp_forward(cudaStream_t s, const Dims& d, const MlpBuffers& m, int rows);
+cudaError_t mlp_backward(cudaStream_t s, const Dims& d, const MlpBuffers& m, int rows, const double* x, float lr,
+                         bool apply);
 cudaError_t set_int(cudaStream_t s, int* out, long long n, int v);
 
 }  // namespace afq

@@ -337,11 +337,21 @@ cudaError_t combine_logdet(cudaStream_t s, long long pairs, const double2* logde
 }
 
 // ---------------------------------------------------------------- Metropolis on the paths
-// Proposal for pair q: prior x' = xi, or pCN x' = sqrt(1 - beta^2) x + beta xi,
-// xi ~ N(0, I) (Philox, tag PROPOSE or BURN_PROPOSE, entity q, this sweep).
-__global__ void propose_kernel(long long pairs, int P, int K, long long woff, uint64_t seed, uint32_t tag, uint32_t sweep,
-                               const unsigned long long* ctr, int proposal, double beta, const double* __restrict__ x,
-                               const int* __restrict__ alive, double* xprop) {
+// Proposal for pair q (xi ~ N(0, I): Philox, tag PROPOSE or BURN_PROPOSE,
+// entity q, this sweep):
+//   prior  x' = xi                       pCN  x' = sqrt(1 - beta^2) x + beta xi
+//   RW     x' = x + s xi                 MLP  x' = mu_w + exp(logv_w / 2) xi, or, with
+//   probability mix (second uniform of the pair's ACCEPT draw), the RW move.
+__device__ __forceinline__ bool mlp_uses_rw(uint64_t seed, uint32_t tag_acc, uint32_t step, uint32_t entity,
+                                            uint32_t sweep, double mix) {
+    Philox4 b = stream_block(seed, tag_acc, step, entity, sweep, 0);
+    return u53(b.w[2], b.w[3]) < mix;
+}
+
+__global__ void propose_kernel(long long pairs, int P, int K, long long woff, uint64_t seed, uint32_t tag, uint32_t tag_acc,
+                               uint32_t sweep, const unsigned long long* ctr, int proposal, double beta, double rw_step,
+                               double mix, const double* __restrict__ x, const int* __restrict__ alive,
+                               const float* __restrict__ mu, const float* __restrict__ logv, double* xprop) {
     int bpr = (K + 1) / 2;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= pairs * bpr) return;
@@ -353,41 +363,81 @@ __global__ void propose_kernel(long long pairs, int P, int K, long long woff, ui
         if (2 * j + 1 < K) out[2 * j + 1] = 0.0;
         return;
     }
-    double2 z = normal_pair(seed, tag, step_of(ctr), (uint32_t)(woff * P + q), sweep, (uint32_t)j);
+    const uint32_t step = step_of(ctr), ent = (uint32_t)(woff * P + q);
+    double2 z = normal_pair(seed, tag, step, ent, sweep, (uint32_t)j);
+    const double* xo = x + q * K;
+    const int k0 = 2 * j, k1 = 2 * j + 1;
+    bool rw = proposal == AFQMC_PROPOSAL_RW ||
+              (proposal == AFQMC_PROPOSAL_MLP && mlp_uses_rw(seed, tag_acc, step, ent, sweep, mix));
+    double v0, v1 = 0.0;
     if (proposal == AFQMC_PROPOSAL_PCN) {
         double a = sqrt(1.0 - beta * beta);
-        const double* xo = x + q * K;
-        z.x = fma(a, xo[2 * j], beta * z.x);
-        if (2 * j + 1 < K) z.y = fma(a, xo[2 * j + 1], beta * z.y);
+        v0 = fma(a, xo[k0], beta * z.x);
+        if (k1 < K) v1 = fma(a, xo[k1], beta * z.y);
+    } else if (rw) {
+        v0 = fma(rw_step, z.x, xo[k0]);
+        if (k1 < K) v1 = fma(rw_step, z.y, xo[k1]);
+    } else if (proposal == AFQMC_PROPOSAL_MLP) {
+        const long long w = q / P;
+        v0 = fma(exp(0.5 * (double)logv[w * K + k0]), z.x, (double)mu[w * K + k0]);
+        if (k1 < K) v1 = fma(exp(0.5 * (double)logv[w * K + k1]), z.y, (double)mu[w * K + k1]);
+    } else {
+        v0 = z.x;
+        v1 = z.y;
     }
-    out[2 * j] = z.x;
-    if (2 * j + 1 < K) out[2 * j + 1] = z.y;
+    out[k0] = v0;
+    if (k1 < K) out[k1] = v1;
 }
 
 cudaError_t propose(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
-                    uint32_t sweep, const double* x, const int* alive, double* xprop) {
+                    uint32_t tag_acc, uint32_t sweep, const double* x, const int* alive, const float* mu,
+                    const float* logv, double* xprop) {
     long long n = d.pairs * ((d.K + 1) / 2);
-    propose_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d.pairs, d.P, d.K, p.woff, p.seed, tag, sweep, ctr, p.proposal,
-                                                               p.pcn_beta, x, alive, xprop); count_launches(1);
+    propose_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d.pairs, d.P, d.K, p.woff, p.seed, tag, tag_acc, sweep, ctr,
+                                                               p.proposal, p.pcn_beta, p.rw_step, p.mlp_mix, x, alive, mu,
+                                                               logv, xprop); count_launches(1);
     return cudaGetLastError();
 }
 
-// Accept iff Re(logov'' - logov') >= 0 or u < exp(Re(logov'' - logov')) with
-// u the first 53-bit uniform of (tag, step, pair, sweep); on acceptance copy
-// x', Phi(x') and logov'' into the path.  One block per pair.
+// Metropolis-Hastings: log alpha = Re(logov'' - logov') + extra with
+//   prior, pCN: extra = 0 (the prior is the proposal's invariant law)
+//   RW:         extra = -(|x'|^2 - |x|^2) / 2
+//   MLP move:   extra = -(|x'|^2 - |x|^2) / 2 + sum_k [(x'-mu)^2 - (x-mu)^2] / (2 v)
+// accept iff log alpha >= 0 or u < exp(log alpha), u the first 53-bit uniform of
+// (tag, step, pair, sweep); on acceptance copy x', Phi(x') and logov''.
+// One block per pair.
 __global__ void __launch_bounds__(128) accept_kernel(int N, int nu, int K, int P, long long woff, uint64_t seed, uint32_t tag,
-                                                     uint32_t sweep, const unsigned long long* ctr,
-                                                     const double2* __restrict__ logdet_prop,
+                                                     uint32_t sweep, const unsigned long long* ctr, int proposal,
+                                                     double mix, const double2* __restrict__ logdet_prop,
                                                      const double* __restrict__ xprop, const double* __restrict__ Phiprop,
-                                                     const int* __restrict__ alive, double2* logov_cur, double* x,
+                                                     const int* __restrict__ alive, const float* __restrict__ mu,
+                                                     const float* __restrict__ logv, double2* logov_cur, double* x,
                                                      double* Phi, unsigned long long* counters) {
     long long q = blockIdx.x;
     if (!alive[q / P]) return;
     __shared__ int acc;
     if (threadIdx.x == 0) {
+        const uint32_t step = step_of(ctr), ent = (uint32_t)(woff * P + q);
         double2 ln = cadd(logdet_prop[2 * q], logdet_prop[2 * q + 1]);
         double delta = ln.x - logov_cur[q].x;
-        double u = uniform_at0(seed, tag, step_of(ctr), (uint32_t)(woff * P + q), sweep);
+        if (proposal == AFQMC_PROPOSAL_RW || proposal == AFQMC_PROPOSAL_MLP) {
+            const double* xo = x + q * K;
+            const double* xn = xprop + q * K;
+            double e = 0.0;
+            for (int k = 0; k < K; ++k) e += xn[k] * xn[k] - xo[k] * xo[k];
+            delta -= 0.5 * e;
+            if (proposal == AFQMC_PROPOSAL_MLP && !mlp_uses_rw(seed, tag, step, ent, sweep, mix)) {
+                const long long w = q / P;
+                double g = 0.0;
+                for (int k = 0; k < K; ++k) {
+                    double m = mu[w * K + k], iv = exp(-(double)logv[w * K + k]);
+                    double rn = xn[k] - m, ro = xo[k] - m;
+                    g += (rn * rn - ro * ro) * iv;
+                }
+                delta += 0.5 * g;
+            }
+        }
+        double u = uniform_at0(seed, tag, step, ent, sweep);
         int a = (delta >= 0.0) || (u < exp(delta));
         acc = a;
         if (a) {
@@ -405,9 +455,11 @@ __global__ void __launch_bounds__(128) accept_kernel(int N, int nu, int K, int P
 
 cudaError_t accept(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
                    uint32_t sweep, const double2* logdet_prop, const double* xprop, const double* Phiprop,
-                   const int* alive, double2* logov_cur, double* x, double* Phi, unsigned long long* counters) {
-    accept_kernel<<<(unsigned)d.pairs, 128, 0, s>>>(d.N, d.nu, d.K, d.P, p.woff, p.seed, tag, sweep, ctr, logdet_prop, xprop,
-                                                    Phiprop, alive, logov_cur, x, Phi, counters); count_launches(1);
+                   const int* alive, const float* mu, const float* logv, double2* logov_cur, double* x, double* Phi,
+                   unsigned long long* counters) {
+    accept_kernel<<<(unsigned)d.pairs, 128, 0, s>>>(d.N, d.nu, d.K, d.P, p.woff, p.seed, tag, sweep, ctr, p.proposal,
+                                                    p.mlp_mix, logdet_prop, xprop, Phiprop, alive, mu, logv, logov_cur, x,
+                                                    Phi, counters); count_launches(1);
     return cudaGetLastError();
 }
 
