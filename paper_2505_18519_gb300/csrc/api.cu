@@ -164,7 +164,7 @@ static const char* check_config(const afqmc_config* c) {
 }
 
 static Dims dims_of(const afqmc_config* c) {
-    Dims d;
+    Dims d{};   // value-initialised: launch shapes at their defaults
     d.N = c->N; d.nu = c->n_up; d.nd = c->n_dn; d.nt = c->n_up + c->n_dn;
     d.G = c->n_chol; d.K = c->K; d.W = c->n_walkers; d.P = c->n_paths;
     d.pairs = (long long)c->n_walkers * c->n_paths;

@@ -87,7 +87,7 @@ extern "C" afqmc_status afqmc_local_energy_noalloc(int N, int n_up, int n_dn, in
     double2* Theta = reinterpret_cast<double2*>(base);
     double2* logdet = reinterpret_cast<double2*>(static_cast<char*>(base) + logdet_off);
     cudaStream_t s = (cudaStream_t)stream;
-    Dims d;
+    Dims d{};   // value-initialised: launch shapes at their defaults
     d.N = N; d.nu = n_up; d.nd = n_dn; d.nt = nt; d.G = n_chol; d.K = 1;
     d.P = pairs_per_walker;
     d.W = (int)((n_pairs + pairs_per_walker - 1) / pairs_per_walker);
