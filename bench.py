@@ -205,13 +205,21 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ traffic of the dominant kernel
+def kernel_digest(kernel_source: str, end_marker: str = "size_t contract_fp64_smem") -> str:
+    """sha256 (16 hex digits) of the device code of the contraction file: its
+    text up to the first host function, so that launcher-only edits keep it."""
+    text = open(kernel_source, "rb").read()
+    cut = text.find(b"\n" + end_marker.encode())
+    return hashlib.sha256(text[:cut + 1] if cut >= 0 else text).hexdigest()[:16]
+
+
 def recorded_traffic(kernel_source: str):
     """DRAM bytes per launch of the contraction from the committed ncu summary,
-    or None if the kernel's source changed since the counters were taken."""
+    or None if the kernel's device code changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "contract_fp64_c1_n50.md")
     if not os.path.exists(path):
         return None
-    digest = hashlib.sha256(open(kernel_source, "rb").read()).hexdigest()[:16]
+    digest = kernel_digest(kernel_source)
     fields = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
@@ -223,6 +231,150 @@ def recorded_traffic(kernel_source: str):
         return float(fields["dram_bytes_per_full_launch"])
     except (KeyError, ValueError):
         return None
+
+
+
+# ------------------------------------------------------------------ the widened paths
+def _timed(step, sync, stream, steps, world, local):
+    """Device time in ms of ``step(steps)`` on ``stream`` (max over ranks),
+    bracketed by barriers and synchronisation, with clocks sampled."""
+    import torch
+    import torch.distributed as dist
+    from paper_2505_18519_gb300 import afqmc as lib
+    from paper_2505_18519_gb300.sharding import max_over_ranks
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        sync()
+        l0 = lib.launch_count()
+        e0.record(stream)
+        step(steps)
+        e1.record(stream)
+        sync()
+        l1 = lib.launch_count()
+        if world > 1:
+            dist.barrier()
+    return max_over_ranks(e0.elapsed_time(e1)), clk.summary(), int(l1 - l0)
+
+
+def tensor_roofline(spec, W, P, prof, kernel):
+    """Algorithmic FLOP rate of the tensor-core contraction against the
+    measured sustained BF16 peak (FP16 has the same nominal rate)."""
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops_sustained")
+    source = "measured bf16 sustained (fp16 nominal ratio 1)"
+    if peak is None:
+        peak, source = 1700.0, "fallback sustained bf16 (fp16 nominal ratio 1)"
+    ms = prof["ms"]["contract"] / max(1, prof["launches"]["contract"])
+    flops = contract_flops_per_pair(spec) * W * P
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_source": source, "traffic": None, "flops_per_launch": flops,
+            "ms_per_launch": ms,
+            "note": "algorithmic FLOPs of the real contraction; the split-FP16 scheme issues 4 MMA products per "
+                    "real product and pads N and n to MMA tile sizes"}
+
+
+def _emix(hist):
+    import numpy as np
+    return np.where(hist[:, 1] > 0, hist[:, 0] / np.where(hist[:, 1] > 0, hist[:, 1], 1.0), np.nan)
+
+
+def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, local, only=None):
+    """The mixed-precision contraction, the learned proposal and the batch of
+    uneven systems, each timed like the headline on this GPU's walker block."""
+    import numpy as np
+    import torch
+    import afqmc_inputs as ai
+    W, P = run.n_walkers, run.n_paths
+    out = {}
+    steps, warmup = args.steps, args.warmup
+
+    if only in (None, "mixed"):
+        cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
+                              walker_offset=rank * W, e_shift=28.5, precision="fp16x3")
+        ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
+        ew = ctx.energy(walkers=True)["e_walker"]
+        for _ in range(warmup):
+            ctx.step(1)
+        ctx.profile(True)
+        ms, clocks, launches = _timed(ctx.step, lambda: torch.cuda.synchronize(dev), ctx.stream, steps, world, local)
+        prof = ctx.profile_read()
+        hist = ctx.history(warmup + steps)
+        ctx.close()
+        d = {"precision": "fp16x3", "what": "same workload and Philox streams as the headline; the contraction "
+             "(force bias + local energy) on the tensor cores in split FP16 with FP32 accumulation, everything "
+             "else FP64", "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+             "gpu_launches": launches, "clocks": clocks,
+             "roofline": tensor_roofline(spec, W, P, prof, "contract_tc_kernel"),
+             "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
+        if ew64 is not None:
+            dw = np.abs(ew.real - ew64.real)
+            d["dE_walker_initial_ha"] = {"median": float(np.median(dw)), "max": float(dw.max()),
+                                         "frac_above_1e-4": float(np.mean(dw > 1e-4))}
+        if hist64 is not None and len(hist64) == len(hist):
+            de = np.abs(_emix(hist) - _emix(hist64))
+            d["dE_mix_ha"] = {"max_over_steps": float(np.nanmax(de)), "last": float(de[-1]),
+                              "steps_compared": int(len(de))}
+        out["mixed_fp16x3"] = d
+
+    if only in (None, "learned"):
+        cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
+                              walker_offset=rank * W, e_shift=28.5, precision="fp16x3", proposal="mlp",
+                              mlp_train=True)
+        ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
+        n_train = max(warmup, 20)
+        for _ in range(n_train):
+            ctx.step(1)
+        ctx.profile(True)
+        ms, clocks, launches = _timed(ctx.step, lambda: torch.cuda.synchronize(dev), ctx.stream, steps, world, local)
+        prof = ctx.profile_read()
+        hist = ctx.history(steps)
+        ctx.close()
+        acc = float(hist[:, 3].sum() / (steps * W * P))
+        d = {"precision": "fp16x3", "proposal": "mlp (K->256->256->2K, BF16 GEMMs, trained online every step)",
+             "what": f"same workload; {n_train} untimed training steps, then the timed steps (training continues)",
+             "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+             "gpu_launches": launches, "clocks": clocks, "acceptance": acc,
+             "roofline": tensor_roofline(spec, W, P, prof, "contract_tc_kernel"),
+             "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
+        if hist64 is not None and len(hist64):
+            d["acceptance_prior_proposal"] = float(hist64[-steps:, 3].sum() / (min(steps, len(hist64)) * W * P))
+        out["learned_proposal"] = d
+
+    if only in (None, "batched"):
+        specs = ai.batched_system_specs(16, n_range=(40, 125))
+        Wb, Pb = 256, 16
+        ctxs = []
+        for i, sp in enumerate(specs):
+            sy = ai.make_system(sp)
+            c = lib.make_config(sp.N, sp.n_up, sp.n_dn, sp.n_chol, sp.K, Wb, Pb, 0.005, ai.philox_run_seed(10 + i),
+                                n_burn=20, walker_offset=rank * Wb, precision="fp16x3")
+            ctx = lib.Context(c, sy.h, sy.L, sy.Phi0, sy.U, device=dev, stream=torch.cuda.Stream(dev))
+            ctx.autotune()
+            ctxs.append(ctx)
+        b = lib.Batch(ctxs, stream=torch.cuda.Stream(dev))
+        b.step(warmup)
+        b.sync()
+        ms, clocks, launches = _timed(b.step, b.sync, b.stream, steps, world, local)
+        stats = [c.stats() for c in ctxs]
+        b.close()
+        for c in ctxs:
+            c.close()
+        units = len(specs) * Wb * Pb * world
+        out["batched_uneven"] = {
+            "precision": "fp16x3", "what": f"{len(specs)} synthetic molecules, N ~ U[40,125] (N = "
+            f"{','.join(str(sp.N) for sp in specs)}), n = N/5 per spin, n_chol = 5N, K = N, {Wb} walkers x {Pb} "
+            "paths each, autotuned launch shapes, one CUDA-graph launch per step for the whole batch",
+            "value": units * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "gpu_launches": launches, "clocks": clocks,
+            "live_walkers_frac": sum(st["live_walkers"] for st in stats) / (len(specs) * Wb),
+            "device_status_words": [int(st["status"]) for st in stats],
+            "status_bits": "1 singular overlap, 2 non-finite value (the walker is removed), 4 tensor-core wait timed out"}
+    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -255,11 +407,21 @@ def our_arm(args):
     s = ai.make_system(spec)
     W, P = run.n_walkers, run.n_paths
     seed = ai.philox_run_seed(1)
+    if args.only:
+        # one widened path alone (a profiling run): no headline, no baselines
+        with torch.cuda.device(dev):
+            v = run_variants(args, lib, s, spec, run, seed, rank, world, dev, None, None, local, only=args.only)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "variants": v}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
                           walker_offset=rank * W, e_shift=28.5)
     with torch.cuda.device(dev):
         ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
         stream = ctx.stream
+        ew64 = ctx.energy(walkers=True)["e_walker"]     # initial state, identical for every precision
         for _ in range(args.warmup):
             ctx.step(1)
         torch.cuda.synchronize(dev)
@@ -285,6 +447,7 @@ def our_arm(args):
         ms_max = max_over_ranks(ms)
         clocks = clk.summary()
         hist = ctx.history(args.steps)
+        hist_all = ctx.history(args.warmup + args.steps)
         gpu_state = ctx.state_arrays() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
         ctx.close()
         del ctx
@@ -307,6 +470,9 @@ def our_arm(args):
             t1 = time.perf_counter()
             e2e_s = max_over_ranks(t1 - t0)
             ctx2.close()
+        variants = None
+        if not args.no_variants:
+            variants = run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist_all, local)
 
     pairs_total = W * P * world
     value = pairs_total * args.steps / (ms_max / 1e3)
@@ -342,6 +508,7 @@ def our_arm(args):
                         "a device-to-host read of its energy record"},
         "clocks": clocks, "gpu_launches": int(l1 - l0), "phases_ms_per_step": phases,
         "mixed_energy_last_step": float(hist[-1, 0] / hist[-1, 1]) if len(hist) else None,
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -357,6 +524,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--walkers", type=int, default=0, help="walkers per GPU (profiling runs on a small case)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the mixed-precision, learned-proposal and batched measurements")
+    ap.add_argument("--only", choices=("mixed", "learned", "batched"), default=None,
+                    help="time one variant alone (profiling); skips the FP64 headline's extras")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -64,7 +64,10 @@ def build(verbose: bool = False, force: bool = False) -> str:
             if verbose and msg:
                 print(msg)
     if force or _stale(OUT, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", OUT, *objs, "-lcudart"]
+        # the CUDA runtime is linked statically: the library keeps its own runtime
+        # state (last error, module registration), apart from any other component
+        # of the process that uses the runtime (e.g. PyTorch)
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", OUT, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -6,6 +6,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "kernels.cuh"
 
@@ -40,6 +43,22 @@ static std::atomic<long long> g_launches{0};
 void afq::count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 extern "C" int64_t afqmc_launch_count(void) { return g_launches.load(); }
+
+static std::mutex g_smem_mu;
+static std::map<std::pair<const void*, int>, size_t> g_smem_limit;   // (kernel, device) -> bytes allowed
+
+cudaError_t afq::raise_smem_limit(const void* kernel, size_t bytes) {
+    if (bytes == 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    size_t& cur = g_smem_limit[std::make_pair(kernel, dev)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 // ---------------------------------------------------------------- phase profiling
 // While enabled, afqmc_step records a CUDA event on the context's stream at
@@ -622,6 +641,7 @@ extern "C" void afqmc_destroy(afqmc_ctx* ctx) {
         free(ctx->prof_phase);
     }
     free(ctx);
+    cudaGetLastError();   // nothing to report from here: leave no error pending for the next call
 }
 
 __global__ void philox_fill_kernel(uint32_t* out, int64_t n, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,

@@ -204,6 +204,12 @@ struct Dims {
 namespace afq {
 // Process-wide count of kernel launches made by this library.
 void count_launches(long long n);
+// Raises the dynamic shared-memory limit of `kernel` on the current device to at
+// least `bytes`.  A block may use 48 KB of shared memory in all (static plus
+// dynamic) without this opt-in, so every launch with dynamic shared memory goes
+// through here.  The limit only ever grows, so kernels captured earlier into a
+// graph with a larger size stay launchable.
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes);
 // Phases of a step timed by afqmc_profile (CUDA events on the context's stream).
 enum Phase : int {
     PH_OVERLAP = 0, PH_CONTRACT, PH_AVERAGE, PH_FIELDS, PH_PROPAGATE, PH_RATIO, PH_PROPOSE, PH_TRIAL,

@@ -165,10 +165,8 @@ cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const 
     int JB = contract_fp64_jb(d.N);
     size_t smem = contract_fp64_smem(d.N, d.nu, d.nd, JB);
     if (!contract_fp64_supported(d.N, d.nu, d.nd)) return cudaErrorInvalidValue;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(contract_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = raise_smem_limit((const void*)contract_fp64_kernel, smem);
+    if (e != cudaSuccess) return e;
     contract_fp64_kernel<<<(unsigned)pairs, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair, epair); count_launches(1);
     return cudaGetLastError();
 }

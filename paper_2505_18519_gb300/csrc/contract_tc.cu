@@ -568,8 +568,7 @@ cudaError_t contract_tc_prepare(cudaStream_t st, int N, int nu, int nd, int G, c
 template <int NPAD, bool F16>
 static cudaError_t launch_tc(cudaStream_t st, const Dims& d, const TcShape& s, const void* image, const int* lexp,
                              const double* Phi, const double2* Theta, double2* vpair, double2* epair, int* status) {
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<NPAD, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)s.smem);
+    cudaError_t e = raise_smem_limit((const void*)contract_tc_kernel<NPAD, F16>, s.smem);
     if (e != cudaSuccess) return e;
     long long blocks = (d.pairs + s.TP - 1) / s.TP;
     contract_tc_kernel<NPAD, F16><<<(unsigned)blocks, TC_THREADS, s.smem, st>>>(

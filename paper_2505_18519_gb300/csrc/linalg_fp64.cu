@@ -212,10 +212,8 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
     while (wpb > 1 && per * wpb > 200 * 1024) wpb >>= 1;
     if (per * wpb > 220 * 1024) return cudaErrorInvalidValue;
     size_t smem = per * wpb;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(overlap_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = raise_smem_limit((const void*)overlap_lu_kernel, smem);
+    if (e != cudaSuccess) return e;
     long long blocks = (pairs + wpb - 1) / wpb;
     overlap_lu_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nt, n, col0, spin, pairs, P, Phi, Phi_stride,
                                                                phi, logdet, Theta, alive, status); count_launches(1);
@@ -275,10 +273,8 @@ cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, 
         int n = spin == 0 ? d.nu : d.nd;
         if (n == 0) continue;
         size_t smem = (size_t)d.N * n * sizeof(double2);
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(reorth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
+        cudaError_t e = raise_smem_limit((const void*)reorth_kernel, smem);
+        if (e != cudaSuccess) return e;
         reorth_kernel<<<n_walkers, 32, smem, s>>>(d.N, d.nt, n, spin == 0 ? 0 : d.nu, src, dst, alive, status); count_launches(1);
     }
     return cudaGetLastError();
@@ -412,17 +408,13 @@ cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, co
     size_t full = vec + (size_t)N * N * sizeof(double);
     cudaError_t e;
     if (full <= 200 * 1024) {
-        if (full > 48 * 1024) {
-            e = cudaFuncSetAttribute(chebyshev_expm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
-            if (e != cudaSuccess) return e;
-        }
+        e = raise_smem_limit((const void*)chebyshev_expm_kernel<true>, full);
+        if (e != cudaSuccess) return e;
         chebyshev_expm_kernel<true><<<(unsigned)problems, threads, full, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status); count_launches(1);
     } else {
         if (vec > 200 * 1024) return cudaErrorInvalidValue;
-        if (vec > 48 * 1024) {
-            e = cudaFuncSetAttribute(chebyshev_expm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vec);
-            if (e != cudaSuccess) return e;
-        }
+        e = raise_smem_limit((const void*)chebyshev_expm_kernel<false>, vec);
+        if (e != cudaSuccess) return e;
         chebyshev_expm_kernel<false><<<(unsigned)problems, threads, vec, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status); count_launches(1);
     }
     return cudaGetLastError();

@@ -265,11 +265,12 @@ cudaError_t mlp_prepare(cudaStream_t s, const Dims& d, const MlpBuffers& m, cons
     // U_k Phi0 for all k: (K N x N) (N x n_up)
     gemm_nn_f64(s, d.K * d.N, d.nu, d.N, 1.0, U, d.N, Phi0, d.nu, 0.0, m.UPhi0, d.nu);
     mlp_init_kernel<<<grid_for(mlp_n_params(d.K)), 256, 0, s>>>(d.K, seed, m.theta); count_launches(1);
-    cudaMemsetAsync(m.adam_m, 0, sizeof(float) * mlp_n_params(d.K), s);
-    cudaMemsetAsync(m.adam_v, 0, sizeof(float) * mlp_n_params(d.K), s);
-    cudaMemsetAsync(m.counter, 0, sizeof(unsigned long long), s);
-    cudaMemsetAsync(m.featf, 0, sizeof(float) * (size_t)m.Wp * m.Kp, s);
-    cudaMemsetAsync(m.featb, 0, sizeof(__nv_bfloat16) * (size_t)m.Wp * m.Kp, s);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(m.adam_m, 0, sizeof(float) * mlp_n_params(d.K), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.adam_v, 0, sizeof(float) * mlp_n_params(d.K), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.counter, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.featf, 0, sizeof(float) * (size_t)m.Wp * m.Kp, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.featb, 0, sizeof(__nv_bfloat16) * (size_t)m.Wp * m.Kp, s)) != cudaSuccess) return e;
     return mlp_pack(s, d, m);
 }
 
@@ -314,8 +315,10 @@ cudaError_t mlp_backward(cudaStream_t s, const Dims& d, const MlpBuffers& m, int
     mlp_loss_grad_kernel<<<rows, 256, 0, s>>>(rows, d.P, K, Kp, x, m.mu, m.logv, m.logv_raw, m.doutf, m.doutb,
                                               m.loss_part); count_launches(1);
     if (R > rows) {
-        cudaMemsetAsync(m.doutf + (size_t)rows * 2 * Kp, 0, sizeof(float) * (size_t)(R - rows) * 2 * Kp, s);
-        cudaMemsetAsync(m.doutb + (size_t)rows * 2 * Kp, 0, sizeof(__nv_bfloat16) * (size_t)(R - rows) * 2 * Kp, s);
+        cudaError_t e = cudaMemsetAsync(m.doutf + (size_t)rows * 2 * Kp, 0, sizeof(float) * (size_t)(R - rows) * 2 * Kp, s);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(m.doutb + (size_t)rows * 2 * Kp, 0, sizeof(__nv_bfloat16) * (size_t)(R - rows) * 2 * Kp, s);
+        if (e != cudaSuccess) return e;
     }
     mlp_sum_kernel<<<1, 32, 0, s>>>(rows, m.loss_part, m.loss); count_launches(1);
     // output layer: gW3 = dout^T H2, gb3 = colsum(dout), dH2 = dout W3

@@ -111,6 +111,8 @@ __global__ void __launch_bounds__(256) walker_average_kernel(int P, int G, const
 
 cudaError_t walker_average(cudaStream_t s, const Dims& d, const double2* logdet, const double2* vpair,
                            const double2* epair, double2* logov, double2* sumS, double2* vbar, double2* ebar) {
+    cudaError_t e = raise_smem_limit((const void*)walker_average_kernel, d.P * sizeof(double2));
+    if (e != cudaSuccess) return e;
     walker_average_kernel<<<d.W, 256, d.P * sizeof(double2), s>>>(d.P, d.G, logdet, vpair, epair, logov, sumS, vbar, ebar); count_launches(1);
     return cudaGetLastError();
 }
@@ -274,10 +276,8 @@ cudaError_t propagate(cudaStream_t s, const Dims& d, const StepParams& p, const 
                       const double2* phi, double2* phi_new, const int* alive) {
     size_t smem = 2 * (size_t)d.N * d.nt * sizeof(double2);
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = raise_smem_limit((const void*)propagate_kernel, smem);
+    if (e != cudaSuccess) return e;
     propagate_kernel<<<d.W, 256, smem, s>>>(d.N, d.nt, p.taylor_order, p.dtau, expT, Aplanes, phi, phi_new, alive); count_launches(1);
     return cudaGetLastError();
 }

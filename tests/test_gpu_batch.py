@@ -104,3 +104,26 @@ def test_uneven_batch_of_sixteen_systems():
     b.close()
     for c in ctxs + [alone]:
         c.close()
+
+
+def test_fresh_process_near_48k_shared_memory():
+    """A first launch whose dynamic shared memory alone is below 48 KB but
+    whose static + dynamic total is above it (trial orbitals at N = 60, n = 12:
+    46,080 B dynamic) must work in a process where no larger launch came before."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import torch, afqmc_inputs as ai\n"
+        "from paper_2505_18519_gb300 import afqmc as lib\n"
+        "sp = ai.SystemSpec(60, 12, 12, 300, 60, True, 3001)\n"
+        "s = ai.make_system(sp)\n"
+        "cfg = lib.make_config(60, 12, 12, 300, 60, 8, 4, 0.005, 5, n_burn=1, precision='fp16x3')\n"
+        "ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U)\n"
+        "ctx.step(1)\n"
+        "print('E', ctx.energy()['e_mix'])\n" % root)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "E " in r.stdout
