@@ -339,12 +339,14 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     Workspace& w = ctx->ws;
     cudaStream_t s = ctx->stream;
     afqmc_status st;
+    const bool f16 = ctx->cfg.precision == AFQMC_PRECISION_FP16X3;
+    const bool walker_side = ctx->cfg.precision != AFQMC_PRECISION_FP64 && contract_tc_walker_side(d.N, d.nu, d.nd, f16);
     for (int spin = 0; spin < 2; ++spin)
-        CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P));
+        CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
+                      walker_side));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64)
-        CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.vpair, w.epair, w.status,
-                       ctx->cfg.precision == AFQMC_PRECISION_FP16X3));
+        CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.vpair, w.epair, w.status, f16));
     else
         CK(contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
     if ((st = prof_mark(ctx, PH_CONTRACT)) != AFQMC_OK) return st;

@@ -95,13 +95,16 @@ extern "C" afqmc_status afqmc_autotune(afqmc_ctx* ctx, int* chosen) {
     int best_tp = 0;
     if (c.precision != AFQMC_PRECISION_FP64) {
         const bool f16 = c.precision == AFQMC_PRECISION_FP16X3;
-        BK(overlap_lu(s, d, 1, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P));
+        const bool ws = contract_tc_walker_side(d.N, d.nu, d.nd, f16);
+        for (int spin = 0; spin < 2; ++spin)
+            BK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs,
+                          d.P, ws));
         best = 1e30f;
         for (int tp : {0, 4, 2, 1}) {
             Dims t = d;
             t.tc_tp = tp;
             float ms;
-            st = time_ms(s, [&] { return contract_tc(s, t, w.Lt, w.Phi, w.Theta, w.vpair, w.epair, w.status, f16); }, 1,
+            st = time_ms(s, [&] { return contract_tc(s, t, w.Lt, w.Phi, w.Theta, w.phi, w.vpair, w.epair, w.status, f16); }, 1,
                          &ms);
             if (st != AFQMC_OK) return st;
             if (ms < best) { best = ms; best_tp = tp; }

@@ -38,7 +38,7 @@
 
 namespace afq {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
 constexpr int TC_MAXTP = 32;
 
 template <bool F16>
@@ -86,6 +86,23 @@ __device__ __forceinline__ void split16d(double x, uint8_t* hi_base, uint8_t* lo
     *reinterpret_cast<typename H::T*>(hi_base + off) = hi;
     *reinterpret_cast<typename H::T*>(lo_base + off) = lo;
 }
+// x = hi + lo as the raw bits of two 16-bit values (same rules as split16).
+template <bool F16>
+__device__ __forceinline__ void split_bits(float x, uint16_t& hi, uint16_t& lo) {
+    typedef Half16<F16> H;
+    typename H::T h, l;
+    if (F16) {
+        const float r = rintf(x);
+        h = H::from(r);
+        l = H::from(x - r);
+    } else {
+        h = H::from(x);
+        l = H::from(x - H::to(h));
+    }
+    hi = *reinterpret_cast<uint16_t*>(&h);
+    lo = *reinterpret_cast<uint16_t*>(&l);
+}
+
 // Exponent e with max * 2^e in [128, 256) (0 for max = 0 or in BF16 mode).
 template <bool F16>
 __device__ __forceinline__ int scale_exp(float m) {
@@ -139,55 +156,89 @@ __global__ void prepare_lt_kernel(int N, int NPAD, int G1, int n_tiles, const do
 }
 
 struct TcShape {
-    int NPAD, GPT, NKB, TP, GT, NB1, NB2, c1col, d2col;
+    int NPAD, GPT, NKB, TP, GT, T, NB1, NB2, S, c1col, d2col;
     size_t smem;
 };
 
 constexpr int TC_MAXSCALE_B2 = 512;   // TP * NB2 column scales of the Theta tiles
+constexpr int TC_MAXSTAGES = 4;       // ring of streamed (h, L_g) operand units
+constexpr uint32_t TC_UNIT = 32768;   // one unit: 128 rows x 64 K, hi then lo (16 KB each)
+constexpr size_t TC_SMEM_MAX = 216 * 1024;   // dynamic shared memory (static use is about 10.1 KB of 227 KB)
 
+// 2^e as a float, for |e| <= 126: exact scaling without ldexpf.
+__device__ __forceinline__ float pow2f(int e) {
+    e = max(-126, min(126, e));
+    return __int_as_float((e + 127) << 23);
+}
+// Exponent that puts the largest entry of a row (its bits as an unsigned) in [128, 256).
+__device__ __forceinline__ int row_exp(unsigned maxbits) {
+    if (maxbits == 0u) return 0;
+    int ex = (int)((maxbits >> 23) & 255u) - 127;
+    return max(-100, min(100, 7 - ex));
+}
+
+// Per block: TP pairs, every g.  Warp roles: thread 0 issues the bulk copies of
+// the (h, L_g) operand image into an S-stage ring and every MMA; all eight
+// warps run the epilogues, warp w on tensor-memory lanes 32 (w % 4) .. +31.
+//   GEMM1 of a block of GT matrices: T = GT / GPT tiles of 128 rows (g, j),
+//     each accumulated in its own columns (F16 mode: hi*hi in one set, the
+//     corrections in a second set), streamed unit by unit from the ring; the
+//     ring is refilled as soon as the MMAs reading a stage have completed, so
+//     the next block's operands load while the per-pair epilogues run.
+//   per pair: epilogue 1 (row maxima of R_g,p over j, then R scaled to
+//     [128, 256) per row, split, stored as the A operand of GEMM2), GEMM2
+//     against Theta_p, epilogue 2 (M to shared memory, traces, sums over a and g).
 template <int NPAD, bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    contract_tc_kernel(int N, int nu, int nd, int G, int TP, int GT, int NB1, int NB2, int c1col, int d2col, long long pairs,
-                       const uint4* __restrict__ Lt, const int* __restrict__ lexp, const double* __restrict__ Phi,
-                       const double2* __restrict__ Theta, double2* __restrict__ vpair, double2* __restrict__ epair,
-                       int* status) {
+    contract_tc_kernel(int N, int nu, int nd, int G, int TP, int GT, int NB1, int NB2, int S, int c1col, int d2col,
+                       long long pairs, const uint8_t* __restrict__ image, const int* __restrict__ lexp,
+                       const double* __restrict__ Phi, const double2* __restrict__ Theta, double2* __restrict__ vpair,
+                       double2* __restrict__ epair, int* status) {
     constexpr int GPT = 128 / NPAD;
     constexpr int NKB = NPAD / 64;
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    const size_t b1_bytes = (size_t)NB1 * NPAD * 2, b2_bytes = (size_t)NB2 * NPAD * 2;
-    uint8_t* B1h = sm;
-    uint8_t* B1l = B1h + b1_bytes;
-    uint8_t* B2 = B1l + b1_bytes;                         // pair p: hi at 2p*b2, lo at (2p+1)*b2
-    uint8_t* A1h = B2 + 2 * (size_t)TP * b2_bytes;
-    uint8_t* A1l = A1h + 16384;
-    uint8_t* A2h = A1l + 16384;
+    uint8_t* A1 = sm;                                          // S stages of one unit
+    uint8_t* A2h = A1 + (size_t)S * TC_UNIT;
     uint8_t* A2l = A2h + (size_t)128 * NPAD * 2;
-    float* Ms = reinterpret_cast<float*>(A1h);             // epilogue-2 staging over A1 and A2
-    __shared__ uint64_t bar;
+    float* Ms = reinterpret_cast<float*>(A2h);                // epilogue-2 staging, over A2
+    uint8_t* B1h = A2l + (size_t)128 * NPAD * 2;
+    const size_t b1_bytes = (size_t)NB1 * NPAD * 2, b2_bytes = (size_t)NB2 * NPAD * 2;
+    uint8_t* B1l = B1h + b1_bytes;
+    uint8_t* B2 = B1l + b1_bytes;                              // pair p: hi at 2p*b2, lo at (2p+1)*b2
+    __shared__ uint64_t full_bar[TC_MAXSTAGES], empty_bar[TC_MAXSTAGES], done_bar, drain_bar;
     __shared__ uint32_t tslot;
-    __shared__ float2 red_tr[TC_THREADS], red_ex[TC_THREADS];
-    __shared__ double2 red_c[TC_THREADS];
+    __shared__ int fail_flag;
+    __shared__ unsigned rowmax[128];
+    __shared__ float2 red_tr[2][128], red_ex[2][128];
+    __shared__ float2 red_cf[128];
     __shared__ double2 eacc[TC_MAXTP];
     __shared__ int sPhi[256];                 // column exponents of B1 (rows (p, a))
     __shared__ int sTh[TC_MAXSCALE_B2];       // column exponents of B2, per pair
-    __shared__ unsigned rowmax[128];          // |R| maxima of the A2 rows (float bits)
-    __shared__ int sR[128];                   // row exponents of A2
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
     const int nt = nu + nd;
     const long long pair0 = (long long)blockIdx.x * TP;
     const int np = (int)min((long long)TP, pairs - pair0);
     const int G1 = G + 1;
-    const int S = nu * nu + nd * nd;
+    const int T = GT / GPT;
+    const int n_gb = (G1 + GT - 1) / GT;
+    const int total = n_gb * T * NKB;                          // units of the image, in order
 
     if (warp == 0) {
         tc::tmem_alloc(&tslot, 512);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(&bar, 1);
+        for (int q = 0; q < S; ++q) {
+            tc::mbar_init(&full_bar[q], 1);
+            tc::mbar_init(&empty_bar[q], 1);
+        }
+        tc::mbar_init(&done_bar, 1);
+        tc::mbar_init(&drain_bar, 1);
         tc::mbar_fence_init();
+        fail_flag = 0;
     }
     if (tid < TC_MAXTP) eacc[tid] = cmk(0.0, 0.0);
     // column exponents of B1 = Phi^T (row (p, a) of the operand) and of B2 = Theta^T
@@ -214,13 +265,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         sTh[q] = scale_exp<F16>(m);
     }
     __syncthreads();
+    // the first S units of the operand image start loading now
+    int loaded = 0;   // units whose copies were issued (meaningful in thread 0)
+    if (tid == 0) {
+        for (; loaded < S && loaded < total; ++loaded) {
+            tc::mbar_arrive_expect_tx(&full_bar[loaded], TC_UNIT);
+            tc::bulk_g2s(A1 + (size_t)loaded * TC_UNIT, image + (size_t)loaded * TC_UNIT, TC_UNIT, &full_bar[loaded]);
+        }
+    }
     // B1: Phi^T of the block's pairs, rows (p, a), K = i
     for (int e = tid; e < NB1 * NPAD; e += TC_THREADS) {
         int r = e / NPAD, i = e % NPAD;
         int p = r / nu, a = r % nu;
-        double x = 0.0;
-        if (p < np && i < N) x = ldexp(Phi[(pair0 + p) * (long long)N * nu + (long long)i * nu + a], sPhi[r]);
-        split16d<F16>(x, B1h, B1l, tc::sw128_offset(NB1, r, i));
+        float x = 0.f;
+        if (p < np && i < N) x = (float)Phi[(pair0 + p) * (long long)N * nu + (long long)i * nu + a] * pow2f(sPhi[r]);
+        split16<F16>(x, B1h, B1l, tc::sw128_offset(NB1, r, i));
     }
     // B2: Theta_p^T as rows c = [Re up | Im up | Re down | Im down], K = j
     for (int p = 0; p < TP; ++p) {
@@ -229,57 +288,68 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const double2* Th = Theta + (pair0 + p) * (long long)N * nt;
         for (int e = tid; e < NB2 * NPAD; e += TC_THREADS) {
             int c = e / NPAD, j = e % NPAD;
-            double x = 0.0;
+            float x = 0.f;
             if (p < np && j < N && c < 2 * nt) {
                 int col, im;
                 if (c < 2 * nu) { col = c % nu; im = c >= nu; }
                 else { int q = c - 2 * nu; col = nu + q % nd; im = q >= nd; }
                 double2 t = Th[(long long)j * nt + col];
-                x = ldexp(im ? t.y : t.x, sTh[p * NB2 + c]);
+                x = (float)(im ? t.y : t.x) * pow2f(sTh[p * NB2 + c]);
             }
-            split16d<F16>(x, bh, bl, tc::sw128_offset(NB2, c, j));
+            split16<F16>(x, bh, bl, tc::sw128_offset(NB2, c, j));
         }
     }
-    // A2 starts zero (rows past GT * nu only ever feed D2 rows that are not read)
+    // A2 starts zero (its rows past GT * nu only ever feed D2 rows that are not read)
     for (int e = tid; e < 128 * NPAD * 2 * 2 / 16; e += TC_THREADS) reinterpret_cast<uint4*>(A2h)[e] = make_uint4(0, 0, 0, 0);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = tslot;
-    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
     const uint32_t id1 = F16 ? tc::idesc_f16_f32(128, NB1) : tc::idesc_bf16_f32(128, NB1);
     const uint32_t id2 = F16 ? tc::idesc_f16_f32(128, NB2) : tc::idesc_bf16_f32(128, NB2);
-    uint32_t phase = 0;
+    uint32_t done_phase = 0;
     bool failed = false;
-    const int tiles_per_block = GT / GPT;
-    const int n_blocks = (G1 + GT - 1) / GT;
-    const int gs = tid / NPAD, jrow = tid % NPAD;       // this thread's D1 lane: (matrix in tile, row j)
+    int consumed = 0;                                         // units whose MMAs were issued
+    const int Lrow = 32 * quarter + lane;                      // this thread's tensor-memory lane
+    const int g_in_tile = Lrow / NPAD, jrow = Lrow % NPAD;     // D1 row (matrix in tile, j)
 
-    for (int gb = 0; gb < n_blocks && !failed; ++gb) {
-        // ---- GEMM1 for the GT matrices of this block
-        for (int k = 0; k < tiles_per_block && !failed; ++k) {
-            const long long t = (long long)gb * tiles_per_block + k;
-            for (int kb = 0; kb < NKB; ++kb) {
-                const uint4* src = Lt + (t * NKB + kb) * 2048;
-                for (int q = tid; q < 2048; q += TC_THREADS) reinterpret_cast<uint4*>(A1h)[q] = src[q];
-                tc::fence_proxy_async();
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
-                if (tid == 0) {
+    // Issue the copy of the next unit into the stage freed by the MMAs of unit
+    // loaded - S (thread 0 only; bounded wait).
+    auto refill_upto = [&](int last_consumed) -> bool {
+        while (loaded < total && loaded - S <= last_consumed) {
+            const int v = loaded - S, st = loaded % S;
+            if (v >= 0 && !tc::mbar_wait(&empty_bar[st], (uint32_t)((v / S) & 1))) return false;
+            tc::mbar_arrive_expect_tx(&full_bar[st], TC_UNIT);
+            tc::bulk_g2s(A1 + (size_t)st * TC_UNIT, image + (size_t)loaded * TC_UNIT, TC_UNIT, &full_bar[st]);
+            ++loaded;
+        }
+        return true;
+    };
+
+    for (int gb = 0; gb < n_gb && !failed; ++gb) {
+        // ---- GEMM1 for the GT matrices of this block (thread 0 issues everything)
+        if (tid == 0) {
+            bool ok = true;
+            for (int k = 0; k < T && ok; ++k) {
+                for (int kb = 0; kb < NKB && ok; ++kb) {
+                    const int u = consumed, st = u % S;
+                    if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint32_t sa = tc::smem_u32(A1 + (size_t)st * TC_UNIT);
                     const uint32_t d = taddr + (uint32_t)(k * NB1);
-                    const uint32_t dc = taddr + (uint32_t)c1col;     // correction accumulator (FP16 mode)
+                    const uint32_t dc = taddr + (uint32_t)(c1col + k * NB1);
 #pragma unroll
                     for (int ss = 0; ss < 4; ++ss) {
-                        uint64_t ah = tc::desc_sw128(tc::smem_u32(A1h) + ss * 32);
-                        uint64_t al = tc::desc_sw128(tc::smem_u32(A1l) + ss * 32);
+                        uint64_t ah = tc::desc_sw128(sa + ss * 32);
+                        uint64_t al = tc::desc_sw128(sa + 16384 + ss * 32);
                         uint64_t bh = tc::desc_sw128(tc::smem_u32(B1h) + kb * NB1 * 128 + ss * 32);
                         uint64_t bl = tc::desc_sw128(tc::smem_u32(B1l) + kb * NB1 * 128 + ss * 32);
-                        const uint32_t first = (kb > 0 || ss > 0) ? 1u : 0u;
-                        tc::mma_f16(d, ah, bh, id1, first);
+                        const uint32_t acc = (kb > 0 || ss > 0) ? 1u : 0u;
+                        tc::mma_f16(d, ah, bh, id1, acc);
                         if (F16) {
-                            tc::mma_f16(dc, ah, bl, id1, first);
+                            tc::mma_f16(dc, ah, bl, id1, acc);
                             tc::mma_f16(dc, al, bh, id1, 1u);
                             tc::mma_f16(dc, al, bl, id1, 1u);
                         } else {
@@ -287,52 +357,45 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             tc::mma_f16(d, al, bh, id1, 1u);
                         }
                     }
-                    tc::mma_commit(&bar);
+                    tc::mma_commit(&empty_bar[st]);
+                    ++consumed;
+                    if (u >= 1 && !refill_upto(u - 1)) ok = false;
                 }
-                __syncwarp();
-                bool ok = tc::mbar_wait(&bar, phase);
-                phase ^= 1;
-                if (__syncthreads_or(!ok)) { failed = true; break; }
-                tc::fence_after_sync();
             }
-            if (F16 && !failed) {
-                // D1 tile += correction accumulator (round to nearest), so the
-                // correction columns can take the next tile
-                for (int c0 = 0; c0 < NB1; c0 += 16) {
-                    float v[16], w[16];
-                    tc::tmem_ld16(taddr + lane_base + (uint32_t)(k * NB1 + c0), v);
-                    tc::tmem_ld16(taddr + lane_base + (uint32_t)(c1col + c0), w);
-                    tc::tmem_ld_wait();
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] += w[q];
-                    tc::tmem_st16(taddr + lane_base + (uint32_t)(k * NB1 + c0), v);
-                }
-                tc::tmem_st_wait();
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
+            if (ok) {
+                tc::mma_commit(&done_bar);
+                // prefetch the next block's first units while the pair epilogues run
+                ok = refill_upto(consumed - 1);
             }
+            if (!ok) fail_flag = 1;
         }
-        if (failed) break;
+        __syncwarp();
+        {
+            bool ok = fail_flag == 0 && tc::mbar_wait(&done_bar, done_phase);
+            done_phase ^= 1;
+            if (__syncthreads_or(!ok || fail_flag)) { failed = true; break; }
+            tc::fence_after_sync();
+        }
         // ---- per pair: epilogue 1 (R -> A2), GEMM2, epilogue 2 (traces)
         for (int p = 0; p < np && !failed; ++p) {
             // R_g,p[a, j] = D1[(g, j), (p, a)] * 2^-(lexp[g] + sPhi[p nu + a])
             if (F16) {
                 if (tid < 128) rowmax[tid] = 0u;
                 __syncthreads();
-                for (int k = 0; k < tiles_per_block; ++k) {
-                    const int gl = k * GPT + gs;
+                for (int k = half; k < T; k += 2) {
+                    const int gl = k * GPT + g_in_tile;
                     const int ge = gb * GT + gl;
                     const int le = ge < G1 ? lexp[ge] : 0;
                     for (int a0 = 0; a0 < nu; a0 += 16) {
-                        float v[16];
+                        float v[16], w[16];
                         tc::tmem_ld16(taddr + lane_base + (uint32_t)(k * NB1 + p * nu + a0), v);
+                        tc::tmem_ld16(taddr + lane_base + (uint32_t)(c1col + k * NB1 + p * nu + a0), w);
                         tc::tmem_ld_wait();
 #pragma unroll
                         for (int q = 0; q < 16; ++q) {
-                            int a = a0 + q;
+                            const int a = a0 + q;
                             if (a < nu) {   // uniform across the warp
-                                float r = ldexpf(v[q], -(le + sPhi[p * nu + a]));
+                                float r = (v[q] + w[q]) * pow2f(-(le + sPhi[p * nu + a]));
                                 unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(r)));
                                 if (lane == 0) atomicMax(&rowmax[gl * nu + a], m);
                             }
@@ -340,23 +403,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
                 __syncthreads();
-                if (tid < 128) sR[tid] = scale_exp<F16>(__uint_as_float(rowmax[tid]));
-                __syncthreads();
             }
-            for (int k = 0; k < tiles_per_block; ++k) {
-                const int gl = k * GPT + gs;
+            for (int k = half; k < T; k += 2) {
+                const int gl = k * GPT + g_in_tile;
                 const int ge = gb * GT + gl;
                 const int le = (F16 && ge < G1) ? lexp[ge] : 0;
                 for (int a0 = 0; a0 < nu; a0 += 16) {
                     float v[16];
                     tc::tmem_ld16(taddr + lane_base + (uint32_t)(k * NB1 + p * nu + a0), v);
-                    tc::tmem_ld_wait();
+                    if (F16) {
+                        float w[16];
+                        tc::tmem_ld16(taddr + lane_base + (uint32_t)(c1col + k * NB1 + p * nu + a0), w);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) v[q] += w[q];
+                    } else {
+                        tc::tmem_ld_wait();
+                    }
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        int a = a0 + q;
+                        const int a = a0 + q;
                         if (a < nu) {
                             float r = v[q];
-                            if (F16) r = ldexpf(r, sR[gl * nu + a] - le - sPhi[p * nu + a]);
+                            if (F16) r *= pow2f(row_exp(rowmax[gl * nu + a]) - le - sPhi[p * nu + a]);
                             split16<F16>(r, A2h, A2l, tc::sw128_offset(128, gl * nu + a, jrow));
                         }
                     }
@@ -377,11 +446,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     uint64_t al = tc::desc_sw128(tc::smem_u32(A2l) + ka);
                     uint64_t bh = tc::desc_sw128(tc::smem_u32(bh_base) + kbo);
                     uint64_t bl = tc::desc_sw128(tc::smem_u32(bl_base) + kbo);
-                    const uint32_t first = s > 0 ? 1u : 0u;
-                    tc::mma_f16(d, ah, bh, id2, first);
+                    const uint32_t acc = s > 0 ? 1u : 0u;
+                    tc::mma_f16(d, ah, bh, id2, acc);
                     if (F16) {
                         const uint32_t dc = d + (uint32_t)NB2;
-                        tc::mma_f16(dc, ah, bl, id2, first);
+                        tc::mma_f16(dc, ah, bl, id2, acc);
                         tc::mma_f16(dc, al, bh, id2, 1u);
                         tc::mma_f16(dc, al, bl, id2, 1u);
                     } else {
@@ -389,19 +458,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         tc::mma_f16(d, al, bh, id2, 1u);
                     }
                 }
-                tc::mma_commit(&bar);
+                tc::mma_commit(&done_bar);
             }
             __syncwarp();
-            bool ok = tc::mbar_wait(&bar, phase);
-            phase ^= 1;
-            if (__syncthreads_or(!ok)) { failed = true; break; }
-            tc::fence_after_sync();
-            // epilogue 2: M rows to shared memory (A1/A2 are free until the next GEMM)
-            const int r = tid;
+            {
+                bool ok = tc::mbar_wait(&done_bar, done_phase);
+                done_phase ^= 1;
+                if (__syncthreads_or(!ok)) { failed = true; break; }
+                tc::fence_after_sync();
+            }
+            // epilogue 2: thread (lane r, half s) holds row r = (gbl, a) of M for spin s;
+            // rows to shared memory as Ms[((gbl * 2 + s) * nu + a) * nu + b] (re, im)
+            const int r = Lrow;
             const int gbl = r / nu, a = r % nu;
-            const bool row_ok = r < GT * nu;
-            const int er = (F16 && row_ok) ? sR[r] : 0;
+            const int spin = half;
+            const int ns = spin ? nd : nu;
+            const int cb = spin ? 2 * nu : 0;
+            const bool row_ok = r < GT * nu && a < ns;
+            const int er = F16 ? row_exp(rowmax[min(r, 127)]) : 0;
             for (int c0 = 0; c0 < NB2; c0 += 16) {
+                if (c0 + 16 <= cb || c0 >= cb + 2 * ns) continue;   // uniform across the warp
                 float v[16];
                 tc::tmem_ld16(taddr + lane_base + (uint32_t)(d2col + c0), v);
                 if (F16) {
@@ -416,70 +492,66 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (row_ok) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        int c = c0 + q;
-                        float x = v[q];
-                        if (F16 && c < 2 * nt) x = ldexpf(x, -(er + sTh[p * NB2 + c]));
-                        if (c < 2 * nu) {
-                            int b = c % nu, im = c >= nu;
-                            Ms[2 * (gbl * S + a * nu + b) + im] = x;
-                        } else if (c < 2 * nt && a < nd) {
-                            int qq = c - 2 * nu;
-                            int b = qq % nd, im = qq >= nd;
-                            Ms[2 * (gbl * S + nu * nu + a * nd + b) + im] = x;
+                        const int c = c0 + q - cb;
+                        if (c >= 0 && c < 2 * ns) {
+                            const int b = c < ns ? c : c - ns, im = c >= ns;
+                            float x = v[q];
+                            if (F16) x *= pow2f(-(er + sTh[p * NB2 + c0 + q]));
+                            Ms[2 * (((gbl * 2 + spin) * nu + a) * nu + b) + im] = x;
                         }
                     }
                 }
             }
             tc::fence_before_sync();
             __syncthreads();
-            if (row_ok) {
-                const float* Mu = Ms + 2 * (gbl * S);
-                const float* Md = Mu + 2 * nu * nu;
-                float trx = Mu[2 * (a * nu + a)], try_ = Mu[2 * (a * nu + a) + 1];
-                float exx = 0.f, exy = 0.f;
-                for (int b = 0; b < nu; ++b) {
-                    float x1 = Mu[2 * (a * nu + b)], y1 = Mu[2 * (a * nu + b) + 1];
-                    float x2 = Mu[2 * (b * nu + a)], y2 = Mu[2 * (b * nu + a) + 1];
-                    exx = fmaf(x1, x2, fmaf(-y1, y2, exx));
-                    exy = fmaf(x1, y2, fmaf(y1, x2, exy));
-                }
-                if (a < nd) {
-                    trx += Md[2 * (a * nd + a)];
-                    try_ += Md[2 * (a * nd + a) + 1];
-                    for (int b = 0; b < nd; ++b) {
-                        float x1 = Md[2 * (a * nd + b)], y1 = Md[2 * (a * nd + b) + 1];
-                        float x2 = Md[2 * (b * nd + a)], y2 = Md[2 * (b * nd + a) + 1];
+            {
+                float2 tr = make_float2(0.f, 0.f), ex = make_float2(0.f, 0.f);
+                if (row_ok) {
+                    const float* Mb = Ms + 2 * ((gbl * 2 + spin) * nu * nu);
+                    tr = make_float2(Mb[2 * (a * nu + a)], Mb[2 * (a * nu + a) + 1]);
+                    float exx = 0.f, exy = 0.f;
+                    for (int b = 0; b < ns; ++b) {
+                        const float x1 = Mb[2 * (a * nu + b)], y1 = Mb[2 * (a * nu + b) + 1];
+                        const float x2 = Mb[2 * (b * nu + a)], y2 = Mb[2 * (b * nu + a) + 1];
                         exx = fmaf(x1, x2, fmaf(-y1, y2, exx));
                         exy = fmaf(x1, y2, fmaf(y1, x2, exy));
                     }
+                    ex = make_float2(exx, exy);
                 }
-                red_tr[r] = make_float2(trx, try_);
-                red_ex[r] = make_float2(exx, exy);
+                red_tr[spin][r] = tr;
+                red_ex[spin][r] = ex;
             }
             __syncthreads();
+            // sums over a and the spins in FP32 (FP64 is slow on this part), one
+            // FP64 accumulation per pair and block of matrices
             if (tid < GT) {
-                double2 tr = cmk(0.0, 0.0), ex = cmk(0.0, 0.0);
-                for (int aa = 0; aa < nu; ++aa) {
-                    float2 x = red_tr[tid * nu + aa], y = red_ex[tid * nu + aa];
-                    tr.x += x.x; tr.y += x.y;
-                    ex.x += y.x; ex.y += y.y;
-                }
+                float trx = 0.f, tryy = 0.f, exx = 0.f, exy = 0.f;
+                for (int sp = 0; sp < 2; ++sp)
+                    for (int aa = 0; aa < nu; ++aa) {
+                        const float2 x = red_tr[sp][tid * nu + aa], y = red_ex[sp][tid * nu + aa];
+                        trx += x.x; tryy += x.y;
+                        exx += y.x; exy += y.y;
+                    }
                 const int ge = gb * GT + tid;    // index into (h, L_0, L_1, ...)
-                double2 c = cmk(0.0, 0.0);
+                float2 c = make_float2(0.f, 0.f);
                 if (ge == 0) {
-                    c = tr;
+                    c = make_float2(trx, tryy);
                 } else if (ge <= G) {
-                    vpair[(pair0 + p) * (long long)G + (ge - 1)] = tr;
-                    double2 t2 = cmul(tr, tr);
-                    c = cmk(0.5 * (t2.x - ex.x), 0.5 * (t2.y - ex.y));
+                    vpair[(pair0 + p) * (long long)G + (ge - 1)] = cmk((double)trx, (double)tryy);
+                    c = make_float2(0.5f * (trx * trx - tryy * tryy - exx), 0.5f * (2.f * trx * tryy - exy));
                 }
-                red_c[tid] = c;
+                red_cf[tid] = c;
             }
             __syncthreads();
-            if (tid == 0) {
-                double2 s = eacc[p];
-                for (int q = 0; q < GT; ++q) s = cadd(s, red_c[q]);
-                eacc[p] = s;
+            if (warp == 0) {
+                float cx = 0.f, cy = 0.f;
+                for (int q = lane; q < GT; q += 32) { cx += red_cf[q].x; cy += red_cf[q].y; }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    cx += __shfl_xor_sync(0xffffffffu, cx, off);
+                    cy += __shfl_xor_sync(0xffffffffu, cy, off);
+                }
+                if (lane == 0) eacc[p] = cadd(eacc[p], cmk((double)cx, (double)cy));
             }
             tc::fence_before_sync();
             __syncthreads();
@@ -487,7 +559,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     }
     if (failed) {
-        if (tid == 0) atomicOr(status, STATUS_TIMEOUT);
+        // drain: every issued copy and MMA completes before the block releases its memory
+        if (tid == 0) {
+            atomicOr(status, STATUS_TIMEOUT);
+            for (int v = max(consumed, loaded - S); v < loaded; ++v)
+                if (v >= 0) tc::mbar_wait(&full_bar[v % S], (uint32_t)((v / S) & 1), 1u << 22);
+            tc::mma_commit(&drain_bar);
+            tc::mbar_wait(&drain_bar, 0, 1u << 22);
+        }
     } else if (tid < np) {
         epair[pair0 + tid] = eacc[tid];
     }
@@ -496,40 +575,492 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) tc::tmem_dealloc(taddr, 512);
 }
 
-// Tile shape for (N, n_up, n_dn): the deepest stack of Cholesky matrices in
-// GEMM2 (GT * n_up <= 128 rows) and then the most pairs per block (TP) that fit
-// tensor memory and shared memory.  Tensor-memory columns, in order: GT/GPT D1
-// tiles of NB1, (FP16 mode) one correction tile of NB1, D2 of NB2, (FP16 mode)
-// its correction of NB2.
+// ---------------------------------------------------------------- walker-side form (N <= 64)
+// With Theta_p = phi_w A_p^-1 and B_p = Phi_p A_p^-T, the matrix
+// M'_g = B_p^T (X_g phi_w) = A_p^-1 M_g A_p has the traces of M_g = Phi_p^T X_g Theta_p,
+// and Y_g = X_g phi_w depends on the walker only.  A block takes PG pairs of one
+// walker, so Y_g is formed once for all of them:
+//   GEMM-Y  D_Y[(g, j), c] = sum_i X_g[j, i] PW[c, i],  PW rows c = [Re phi | Im phi]
+//   GEMM-M  D_M[(p, col), (col', ri)] = sum_k AM[(p, col), k] BY_g[(col', ri), k] with
+//           AM row (p, col)  = [Re B_p[:, col] | Im B_p[:, col]]   (K = 2 x 64),
+//           BY row (col', re) = [Re Y_g[:, col'] | -Im Y_g[:, col']],
+//           BY row (col', im) = [Im Y_g[:, col'] |  Re Y_g[:, col']],
+//   so D_M[(p, col), (col', re/im)] = Re/Im (B_p^T Y_g)[col, col'] (same-spin blocks used).
+// One operand unit of the image holds two matrices (rows (g, j), N <= 64); each
+// iteration runs GEMM-Y on it, builds both BY (per-matrix power-of-two scale),
+// issues both GEMM-M and the next unit's GEMM-Y, and the two halves of the
+// block run epilogue M (shared-memory transpose, traces, sums) for one matrix each.
+constexpr int TCY_MAXPG = 64;
+
+template <bool F16>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    contract_tcy_kernel(int N, int nu, int nd, int G, int P, int PG, int NBY, int S, const uint8_t* __restrict__ image,
+                        const int* __restrict__ lexp, const double2* __restrict__ Bm, const double2* __restrict__ phi,
+                        double2* __restrict__ vpair, double2* __restrict__ epair, int* status) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    const int nt = nu + nd;
+    const int S2 = nu * nu + nd * nd;
+    uint8_t* XR = sm;                                          // S units
+    uint8_t* AMh = XR + (size_t)S * TC_UNIT;                   // 128 rows x 128 K
+    uint8_t* AMl = AMh + 128 * 128 * 2;
+    uint8_t* PWh = AMl + 128 * 128 * 2;                        // NBY rows x 64 K
+    const size_t pw_bytes = (size_t)NBY * 64 * 2;
+    uint8_t* PWl = PWh + pw_bytes;
+    uint8_t* BY = PWl + pw_bytes;                              // matrix h: hi at 2h*by, lo at (2h+1)*by
+    const size_t by_bytes = (size_t)NBY * 128 * 2;
+    float* Ms = reinterpret_cast<float*>(BY + 4 * by_bytes);   // matrix h: PG x S2 complex
+    __shared__ uint64_t full_bar[TC_MAXSTAGES], empty_bar[TC_MAXSTAGES], ybar, mbar, drain_bar;
+    __shared__ uint32_t tslot;
+    __shared__ int fail_flag;
+    __shared__ unsigned ymax[2][2];
+    __shared__ float2 red_tr[2][128], red_ex[2][128];
+    __shared__ double2 eacc[2][TCY_MAXPG];
+    __shared__ float2 red_c2[2][TCY_MAXPG];
+    __shared__ int sPW[128], sA[128];
+    __shared__ float cmul_pw[128];          // 2^-sPW: removes the PW row scales from D_Y
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int bpw = (P + PG - 1) / PG;
+    const long long w = blockIdx.x / bpw;
+    const int p0 = (int)(blockIdx.x % bpw) * PG;
+    const int np = min(PG, P - p0);
+    const long long pairbase = w * P + p0;
+    const int G1 = G + 1;
+    const int n_units = (G1 + 1) / 2;
+    const double2* phw = phi + w * (long long)N * nt;
+
+    if (warp == 0) {
+        tc::tmem_alloc(&tslot, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            tc::mbar_init(&full_bar[q], 1);
+            tc::mbar_init(&empty_bar[q], 1);
+        }
+        tc::mbar_init(&ybar, 1);
+        tc::mbar_init(&mbar, 1);
+        tc::mbar_init(&drain_bar, 1);
+        tc::mbar_fence_init();
+        fail_flag = 0;
+        ymax[0][0] = ymax[0][1] = ymax[1][0] = ymax[1][1] = 0u;
+    }
+    if (tid < 2 * TCY_MAXPG) eacc[tid / TCY_MAXPG][tid % TCY_MAXPG] = cmk(0.0, 0.0);
+    // exponents of the PW rows (walker columns) and of the AM rows (B columns)
+    for (int c = tid; c < 128; c += TC_THREADS) {
+        float m = 0.f;
+        if (F16 && c < 2 * nt) {
+            const int col = c % nt, im = c >= nt;
+            for (int i = 0; i < N; ++i) {
+                const double2 t = phw[(long long)i * nt + col];
+                m = fmaxf(m, (float)fabs(im ? t.y : t.x));
+            }
+        }
+        sPW[c] = scale_exp<F16>(m);
+        cmul_pw[c] = pow2f(-sPW[c]);
+    }
+    for (int r = tid; r < 128; r += TC_THREADS) {
+        const int p = r / nt, col = r % nt;
+        float m = 0.f;
+        if (F16 && p < np) {
+            const double2* Bp = Bm + (pairbase + p) * (long long)N * nt;
+            for (int j = 0; j < N; ++j) {
+                const double2 t = Bp[(long long)j * nt + col];
+                m = fmaxf(m, fmaxf((float)fabs(t.x), (float)fabs(t.y)));
+            }
+        }
+        sA[r] = scale_exp<F16>(m);
+    }
+    __syncthreads();
+    int loaded = 0, consumed = 0;   // meaningful in thread 0
+    if (tid == 0) {
+        for (; loaded < S && loaded < n_units; ++loaded) {
+            tc::mbar_arrive_expect_tx(&full_bar[loaded], TC_UNIT);
+            tc::bulk_g2s(XR + (size_t)loaded * TC_UNIT, image + (size_t)loaded * TC_UNIT, TC_UNIT, &full_bar[loaded]);
+        }
+    }
+    // PW: rows c = [Re phi_w | Im phi_w] (column c), K = i
+    for (int e = tid; e < NBY * 64; e += TC_THREADS) {
+        const int c = e / 64, i = e % 64;
+        float x = 0.f;
+        if (c < 2 * nt && i < N) {
+            const double2 t = phw[(long long)i * nt + (c % nt)];
+            x = (float)(c >= nt ? t.y : t.x) * pow2f(sPW[c]);
+        }
+        split16<F16>(x, PWh, PWl, tc::sw128_offset(NBY, c, i));
+    }
+    // AM: row (p, col) = [Re B_p[:, col] | Im B_p[:, col]]
+    for (int e = tid; e < 128 * 128; e += TC_THREADS) {
+        const int r = e / 128, k = e % 128;
+        const int j = k & 63, ri = k >> 6;
+        const int p = r / nt, col = r % nt;
+        float x = 0.f;
+        if (p < np && j < N) {
+            const double2 t = Bm[(pairbase + p) * (long long)N * nt + (long long)j * nt + col];
+            x = (float)(ri ? t.y : t.x) * pow2f(sA[r]);
+        }
+        split16<F16>(x, AMh, AMl, tc::sw128_offset(128, r, k));
+    }
+    // BY starts zero (rows past 2 nt are never written)
+    for (int e = tid; e < (int)(4 * by_bytes / 16); e += TC_THREADS) reinterpret_cast<uint4*>(BY)[e] = make_uint4(0, 0, 0, 0);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+
+    const uint32_t taddr = tslot;
+    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+    const uint32_t idd = F16 ? tc::idesc_f16_f32(128, NBY) : tc::idesc_bf16_f32(128, NBY);
+    const uint32_t dyc = F16 ? (uint32_t)NBY : 0u;                  // correction columns of D_Y
+    const uint32_t dm0 = F16 ? 2u * NBY : (uint32_t)NBY;            // D_M of matrix 0
+    const uint32_t dms = F16 ? 2u * NBY : (uint32_t)NBY;            // stride to matrix 1
+    const int Lrow = 32 * quarter + lane;
+    uint32_t y_ph = 0, m_ph = 0;
+    bool failed = false;
+
+    auto refill_upto = [&](int last_consumed) -> bool {
+        while (loaded < n_units && loaded - S <= last_consumed) {
+            const int v = loaded - S, st = loaded % S;
+            if (v >= 0 && !tc::mbar_wait(&empty_bar[st], (uint32_t)((v / S) & 1))) return false;
+            tc::mbar_arrive_expect_tx(&full_bar[st], TC_UNIT);
+            tc::bulk_g2s(XR + (size_t)st * TC_UNIT, image + (size_t)loaded * TC_UNIT, TC_UNIT, &full_bar[st]);
+            ++loaded;
+        }
+        return true;
+    };
+    // GEMM-Y of unit u (thread 0): D_Y = X(unit) PW^T
+    auto issue_Y = [&](int u) -> bool {
+        const int st = u % S;
+        if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) return false;
+        tc::fence_after_sync();
+        const uint32_t sa = tc::smem_u32(XR + (size_t)st * TC_UNIT);
+#pragma unroll
+        for (int ss = 0; ss < 4; ++ss) {
+            const uint64_t ah = tc::desc_sw128(sa + ss * 32), al = tc::desc_sw128(sa + 16384 + ss * 32);
+            const uint64_t bh = tc::desc_sw128(tc::smem_u32(PWh) + ss * 32), bl = tc::desc_sw128(tc::smem_u32(PWl) + ss * 32);
+            const uint32_t acc = ss > 0 ? 1u : 0u;
+            tc::mma_f16(taddr, ah, bh, idd, acc);
+            if (F16) {
+                tc::mma_f16(taddr + dyc, ah, bl, idd, acc);
+                tc::mma_f16(taddr + dyc, al, bh, idd, 1u);
+                tc::mma_f16(taddr + dyc, al, bl, idd, 1u);
+            } else {
+                tc::mma_f16(taddr, ah, bl, idd, 1u);
+                tc::mma_f16(taddr, al, bh, idd, 1u);
+            }
+        }
+        tc::mma_commit(&empty_bar[st]);
+        tc::mma_commit(&ybar);
+        ++consumed;
+        return refill_upto(u - 1);
+    };
+    if (tid == 0 && !issue_Y(0)) fail_flag = 1;
+
+    const int gi = Lrow / 64, jrow = Lrow % 64;      // D_Y row: matrix in unit, j
+    const int ch = (nt + 1) / 2;                      // walker columns per half
+    const int cl = half * ch, cn = min(nt, cl + ch) - cl;
+    for (int u = 0; u < n_units && !failed; ++u) {
+        __syncwarp();
+        {
+            bool ok = fail_flag == 0 && tc::mbar_wait(&ybar, y_ph);
+            y_ph ^= 1;
+            if (__syncthreads_or(!ok || fail_flag)) { failed = true; break; }
+            tc::fence_after_sync();
+        }
+        if (tid == 0) ymax[(u + 1) & 1][0] = ymax[(u + 1) & 1][1] = 0u;
+        // ---- epilogue Y: Y_g[j, col] for this thread's columns (two passes over
+        // tensor memory: the matrix maximum, then scaled, split and stored in BY_g)
+        {
+            const int g = 2 * u + gi;
+            const int le = (F16 && g < G1) ? lexp[g] : 0;
+            uint8_t* byh = BY + (size_t)gi * 2 * by_bytes;
+            uint8_t* byl = byh + by_bytes;
+            // K position jrow of a BY row: within a 128-byte row, chunk (jrow / 8) xor (row % 8)
+            const uint32_t kb1 = (uint32_t)NBY * 128u;          // second K block (k = 64 + jrow)
+            float mul = pow2f(-le);
+            for (int pass = F16 ? 0 : 1; pass < 2; ++pass) {
+                float mx = 0.f;
+                for (int c0 = 0; c0 < ch; c0 += 16) {   // uniform across the block
+                    float v[16], vi[16];
+                    tc::tmem_ld16(taddr + lane_base + (uint32_t)(cl + c0), v);
+                    tc::tmem_ld16(taddr + lane_base + (uint32_t)(nt + cl + c0), vi);
+                    if (F16) {
+                        float vc[16], vic[16];
+                        tc::tmem_ld16(taddr + lane_base + dyc + (uint32_t)(cl + c0), vc);
+                        tc::tmem_ld16(taddr + lane_base + dyc + (uint32_t)(nt + cl + c0), vic);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) { v[q] += vc[q]; vi[q] += vic[q]; }
+                    } else {
+                        tc::tmem_ld_wait();
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int idx = c0 + q, col = cl + idx;
+                        if (idx < cn) {
+                            const float a = v[q] * (mul * cmul_pw[col]);
+                            const float b = vi[q] * (mul * cmul_pw[nt + col]);
+                            if (pass == 0) {
+                                mx = fmaxf(mx, fmaxf(fabsf(a), fabsf(b)));
+                            } else {
+                                uint16_t xh, xl, yh, yl;
+                                split_bits<F16>(a, xh, xl);
+                                split_bits<F16>(b, yh, yl);
+                                const int n0 = 2 * col, n1 = n0 + 1;   // rows (col, re), (col, im)
+                                const uint32_t o0 = (uint32_t)(n0 >> 3) * 1024u + (uint32_t)(n0 & 7) * 128u +
+                                                    (uint32_t)(((jrow >> 3) ^ (n0 & 7)) * 16 + (jrow & 7) * 2);
+                                const uint32_t o1 = (uint32_t)(n1 >> 3) * 1024u + (uint32_t)(n1 & 7) * 128u +
+                                                    (uint32_t)(((jrow >> 3) ^ (n1 & 7)) * 16 + (jrow & 7) * 2);
+                                // row (col, re) = [Re Y | -Im Y], row (col, im) = [Im Y | Re Y]
+                                *reinterpret_cast<uint16_t*>(byh + o0) = xh;
+                                *reinterpret_cast<uint16_t*>(byl + o0) = xl;
+                                *reinterpret_cast<uint16_t*>(byh + o0 + kb1) = yh ^ 0x8000u;
+                                *reinterpret_cast<uint16_t*>(byl + o0 + kb1) = yl ^ 0x8000u;
+                                *reinterpret_cast<uint16_t*>(byh + o1) = yh;
+                                *reinterpret_cast<uint16_t*>(byl + o1) = yl;
+                                *reinterpret_cast<uint16_t*>(byh + o1 + kb1) = xh;
+                                *reinterpret_cast<uint16_t*>(byl + o1 + kb1) = xl;
+                            }
+                        }
+                    }
+                }
+                if (pass == 0) {
+                    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+                    if (lane == 0) atomicMax(&ymax[u & 1][gi], m);
+                    __syncthreads();
+                    mul *= pow2f(row_exp(ymax[u & 1][gi]));
+                }
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // ---- GEMM-M for both matrices of the unit, then the next unit's GEMM-Y
+        if (tid == 0) {
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const uint32_t d = taddr + dm0 + (uint32_t)h2 * dms;
+                const uint8_t* byh = BY + (size_t)h2 * 2 * by_bytes;
+                const uint8_t* byl = byh + by_bytes;
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const uint32_t ka = (uint32_t)((s >> 2) * 128 * 128 + (s & 3) * 32);
+                    const uint32_t kbo = (uint32_t)((s >> 2) * NBY * 128 + (s & 3) * 32);
+                    const uint64_t ah = tc::desc_sw128(tc::smem_u32(AMh) + ka), al = tc::desc_sw128(tc::smem_u32(AMl) + ka);
+                    const uint64_t bh = tc::desc_sw128(tc::smem_u32(byh) + kbo), bl = tc::desc_sw128(tc::smem_u32(byl) + kbo);
+                    const uint32_t acc = s > 0 ? 1u : 0u;
+                    tc::mma_f16(d, ah, bh, idd, acc);
+                    if (F16) {
+                        tc::mma_f16(d + NBY, ah, bl, idd, acc);
+                        tc::mma_f16(d + NBY, al, bh, idd, 1u);
+                        tc::mma_f16(d + NBY, al, bl, idd, 1u);
+                    } else {
+                        tc::mma_f16(d, ah, bl, idd, 1u);
+                        tc::mma_f16(d, al, bh, idd, 1u);
+                    }
+                }
+            }
+            tc::mma_commit(&mbar);
+            if (u + 1 < n_units && !issue_Y(u + 1)) fail_flag = 1;
+        }
+        __syncwarp();
+        {
+            bool ok = tc::mbar_wait(&mbar, m_ph);
+            m_ph ^= 1;
+            if (__syncthreads_or(!ok || fail_flag)) { failed = true; break; }
+            tc::fence_after_sync();
+        }
+        // ---- epilogue M: half h takes matrix 2u + h; thread lane r = (p, col)
+        {
+            const int r = Lrow;
+            const int p = r / nt, col = r % nt;
+            const int spin = col < nu ? 0 : 1;
+            const int a = spin ? col - nu : col;
+            const int off = spin ? nu : 0, ns = spin ? nd : nu;
+            const bool row_ok = p < np;
+            const float sc = F16 ? pow2f(-(sA[r] + row_exp(ymax[u & 1][half]))) : 1.f;
+            const uint32_t dcol = dm0 + (uint32_t)half * dms;
+            float* Mg = Ms + (size_t)half * PG * S2 * 2;
+            float* Mrow = Mg + 2 * ((size_t)p * S2 + (spin ? nu * nu : 0));
+            for (int c0 = 0; c0 < 2 * nt; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(taddr + lane_base + dcol + (uint32_t)c0, v);
+                if (F16) {
+                    float vc[16];
+                    tc::tmem_ld16(taddr + lane_base + dcol + (uint32_t)NBY + (uint32_t)c0, vc);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] += vc[q];
+                } else {
+                    tc::tmem_ld_wait();
+                }
+                if (row_ok) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int n = c0 + q, cp = n >> 1;
+                        if (cp >= off && cp < off + ns) Mrow[2 * (a * ns + (cp - off)) + (n & 1)] = v[q] * sc;
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            float2 tr = make_float2(0.f, 0.f), ex = make_float2(0.f, 0.f);
+            if (row_ok) {
+                tr = make_float2(Mrow[2 * (a * ns + a)], Mrow[2 * (a * ns + a) + 1]);
+                float exx = 0.f, exy = 0.f;
+                for (int b = 0; b < ns; ++b) {
+                    const float x1 = Mrow[2 * (a * ns + b)], y1 = Mrow[2 * (a * ns + b) + 1];
+                    const float x2 = Mrow[2 * (b * ns + a)], y2 = Mrow[2 * (b * ns + a) + 1];
+                    exx = fmaf(x1, x2, fmaf(-y1, y2, exx));
+                    exy = fmaf(x1, y2, fmaf(y1, x2, exy));
+                }
+                ex = make_float2(exx, exy);
+            }
+            red_tr[half][r] = tr;
+            red_ex[half][r] = ex;
+            __syncthreads();
+            // per pair: sums over its rows in FP32 (FP64 is slow on this part), the
+            // energy term of the matrix, then one FP64 accumulation per pair and unit
+            if (tid < 2 * PG) {
+                const int hh = tid / PG, pp = tid % PG;
+                float2 c = make_float2(0.f, 0.f);
+                if (pp < np) {
+                    float trx = 0.f, tryy = 0.f, exx = 0.f, exy = 0.f;
+                    const float2* rt = &red_tr[hh][pp * nt];
+                    const float2* re = &red_ex[hh][pp * nt];
+                    for (int cc = 0; cc < nt; ++cc) {
+                        const float2 x = rt[cc], y = re[cc];
+                        trx += x.x; tryy += x.y;
+                        exx += y.x; exy += y.y;
+                    }
+                    const int ge = 2 * u + hh;    // index into (h, L_0, L_1, ...)
+                    if (ge == 0) {
+                        c = make_float2(trx, tryy);
+                    } else if (ge <= G) {
+                        vpair[(pairbase + pp) * (long long)G + (ge - 1)] = cmk((double)trx, (double)tryy);
+                        c = make_float2(0.5f * (trx * trx - tryy * tryy - exx), 0.5f * (2.f * trx * tryy - exy));
+                    }
+                }
+                red_c2[hh][pp] = c;
+            }
+            __syncthreads();
+            if (tid < np) {
+                const float2 a = red_c2[0][tid], b = red_c2[1][tid];
+                eacc[0][tid] = cadd(eacc[0][tid], cmk((double)(a.x + b.x), (double)(a.y + b.y)));
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+        }
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(status, STATUS_TIMEOUT);
+            for (int v = max(consumed, loaded - S); v < loaded; ++v)
+                if (v >= 0) tc::mbar_wait(&full_bar[v % S], (uint32_t)((v / S) & 1), 1u << 22);
+            tc::mma_commit(&drain_bar);
+            tc::mbar_wait(&drain_bar, 0, 1u << 22);
+        }
+    } else if (tid < np) {
+        epair[pairbase + tid] = eacc[0][tid];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 512);
+}
+
+struct TcyShape {
+    int PG, NBY, S;
+    size_t smem;
+};
+
+static size_t tcy_smem_bytes(int nu, int nd, int PG, int NBY, int S) {
+    return 1024 + (size_t)S * TC_UNIT + 2 * (size_t)128 * 128 * 2 + 2 * (size_t)NBY * 64 * 2 + 4 * (size_t)NBY * 128 * 2 +
+           2 * (size_t)PG * (nu * nu + nd * nd) * 8;
+}
+
+// Shape of the walker-side form: N <= 64, n_up + n_dn <= 40 (tensor memory:
+// D_Y and two D_M, each NBY columns plus as many for the corrections), PG pairs
+// per block with PG (n_up + n_dn) <= 128 rows of AM.
+static bool tcy_shape(int N, int nu, int nd, bool f16, int pg_override, TcyShape& s) {
+    const int nt = nu + nd;
+    if (N < 1 || N > 64 || nu < 1 || nd < 0 || nd > nu || nt > 40) return false;
+    s.NBY = ((2 * nt + 15) / 16) * 16;
+    if ((f16 ? 6 : 3) * s.NBY + 16 > 512) return false;
+    s.PG = min(TCY_MAXPG, 128 / nt);
+    if (pg_override > 0 && pg_override < s.PG) s.PG = pg_override;
+    for (s.S = TC_MAXSTAGES; s.S >= 2; --s.S) {
+        s.smem = tcy_smem_bytes(nu, nd, s.PG, s.NBY, s.S);
+        if (s.smem <= TC_SMEM_MAX) return true;
+    }
+    return false;
+}
+
+bool contract_tc_walker_side(int N, int nu, int nd, bool f16) {
+    TcyShape s;
+    return tcy_shape(N, nu, nd, f16, 0, s);
+}
+
+template <bool F16>
+static cudaError_t launch_tcy(cudaStream_t st, const Dims& d, const TcyShape& s, const void* image, const int* lexp,
+                              const double2* Bm, const double2* phi, double2* vpair, double2* epair, int* status) {
+    cudaError_t e = raise_smem_limit((const void*)contract_tcy_kernel<F16>, s.smem);
+    if (e != cudaSuccess) return e;
+    const long long W = d.pairs / d.P;
+    const long long blocks = W * ((d.P + s.PG - 1) / s.PG);
+    contract_tcy_kernel<F16><<<(unsigned)blocks, TC_THREADS, s.smem, st>>>(d.N, d.nu, d.nd, d.G, d.P, s.PG, s.NBY, s.S,
+                                                                         (const uint8_t*)image, lexp, Bm, phi, vpair,
+                                                                         epair, status); count_launches(1);
+    return cudaGetLastError();
+}
+
+static size_t tc_smem_bytes(int NPAD, int NB1, int NB2, int TP, int S) {
+    return 1024 + (size_t)S * TC_UNIT + 2 * (size_t)128 * NPAD * 2 + 2 * (size_t)NB1 * NPAD * 2 +
+           2 * (size_t)TP * NB2 * NPAD * 2;
+}
+
+// Fill in TP-dependent fields; false if they do not fit.
+static bool tc_fit(TcShape& s, int nu, int tp, bool f16) {
+    const int nb1 = ((tp * nu + 15) / 16) * 16;
+    if (nb1 > 256) return false;
+    const int c1 = s.T * nb1;
+    const int d2 = f16 ? 2 * c1 : c1;
+    const int end = d2 + (f16 ? 2 * s.NB2 : s.NB2);
+    if (end > 512) return false;
+    if (tp * s.NB2 > TC_MAXSCALE_B2) return false;
+    int S = TC_MAXSTAGES;
+    while (S >= 2 && tc_smem_bytes(s.NPAD, nb1, s.NB2, tp, S) > TC_SMEM_MAX) --S;
+    if (S < 2) return false;
+    s.TP = tp;
+    s.NB1 = nb1;
+    s.c1col = c1;
+    s.d2col = d2;
+    s.S = S;
+    s.smem = tc_smem_bytes(s.NPAD, nb1, s.NB2, tp, S);
+    return true;
+}
+
+// Tile shape for (N, n_up, n_dn): the deepest stack of matrices in GEMM2
+// (GT * n_up <= 128 rows) and then the most pairs per block (TP) that fit
+// tensor memory and shared memory.  Tensor-memory columns, in order: T = GT/GPT
+// D1 tiles of NB1, (FP16 mode) their T correction tiles, D2 of NB2, (FP16 mode)
+// its correction of NB2.  Shared memory: S >= 2 ring stages of one 32 KB unit,
+// A2 (also the epilogue-2 staging), B1, and B2 of the TP pairs.
 static bool tc_shape(int N, int nu, int nd, bool f16, TcShape& s) {
     s.NPAD = N <= 64 ? 64 : (N <= 128 ? 128 : 0);
-    if (!s.NPAD || nu < 1 || nu > 32 || nd > nu) return false;
+    if (!s.NPAD || nu < 1 || nu > 32 || nd > nu || nd < 0) return false;
     s.GPT = 128 / s.NPAD;
     s.NKB = s.NPAD / 64;
     s.NB2 = ((2 * (nu + nd) + 15) / 16) * 16;
     for (int gt = (128 / nu) / s.GPT * s.GPT; gt >= s.GPT; gt -= s.GPT) {
-        const int tiles = gt / s.GPT;
-        const size_t ms = (size_t)gt * (nu * nu + nd * nd) * 8;
-        if (ms > 32768 + 2 * (size_t)128 * s.NPAD * 2) continue;
-        for (int tp = TC_MAXTP; tp >= 1; --tp) {
-            int nb1 = ((tp * nu + 15) / 16) * 16;
-            if (nb1 > 256) continue;
-            int c1 = tiles * nb1;
-            int d2 = f16 ? c1 + nb1 : c1;
-            int end = d2 + (f16 ? 2 * s.NB2 : s.NB2);
-            if (end > 512 || d2 + 32 > 512) continue;   // the D1 reads of a pair run up to 31 columns past its start
-            if (tp * s.NB2 > TC_MAXSCALE_B2) continue;
-            size_t smem = 1024 + 2 * (size_t)nb1 * s.NPAD * 2 + 2 * (size_t)tp * s.NB2 * s.NPAD * 2 + 32768 +
-                          2 * (size_t)128 * s.NPAD * 2;
-            if (smem > 223000) continue;   // plus about 8.6 KB of static shared memory <= 227 KB
-            s.GT = gt;
-            s.TP = tp;
-            s.NB1 = nb1;
-            s.c1col = c1;
-            s.d2col = d2;
-            s.smem = smem < 120 * 1024 ? 120 * 1024 : smem;   // one block per SM (it holds all 512 columns)
-            return true;
-        }
+        const size_t ms = (size_t)gt * 2 * nu * nu * 8;
+        if (ms > 2 * (size_t)128 * s.NPAD * 2) continue;
+        s.GT = gt;
+        s.T = gt / s.GPT;
+        for (int tp = TC_MAXTP; tp >= 1; --tp)
+            if (tc_fit(s, nu, tp, f16)) return true;
     }
     return false;
 }
@@ -544,7 +1075,7 @@ size_t contract_tc_image_bytes(int N, int nu, int nd, int G, bool f16) {
     if (!tc_shape(N, nu, nd, f16, s)) return 0;
     long long G1p = (long long)((G + 1 + s.GT - 1) / s.GT) * s.GT;
     long long tiles = G1p / s.GPT;
-    return (size_t)tiles * s.NKB * 32768 + (size_t)G1p * sizeof(int);
+    return (size_t)tiles * s.NKB * TC_UNIT + (size_t)G1p * sizeof(int);
 }
 
 // The split image of (h, L_g) and, after it, the per-matrix exponents.
@@ -554,7 +1085,7 @@ cudaError_t contract_tc_prepare(cudaStream_t st, int N, int nu, int nd, int G, c
     if (!tc_shape(N, nu, nd, f16, s)) return cudaErrorInvalidValue;
     long long G1p = (long long)((G + 1 + s.GT - 1) / s.GT) * s.GT;
     int tiles = (int)(G1p / s.GPT);
-    int* lexp = reinterpret_cast<int*>(static_cast<uint8_t*>(image) + (size_t)tiles * s.NKB * 32768);
+    int* lexp = reinterpret_cast<int*>(static_cast<uint8_t*>(image) + (size_t)tiles * s.NKB * TC_UNIT);
     if (f16) {
         lt_scale_kernel<true><<<(unsigned)G1p, 256, 0, st>>>(N, G + 1, h, L, lexp); count_launches(1);
         prepare_lt_kernel<true><<<1024, 256, 0, st>>>(N, s.NPAD, G + 1, tiles, h, L, lexp, (uint8_t*)image); count_launches(1);
@@ -572,27 +1103,26 @@ static cudaError_t launch_tc(cudaStream_t st, const Dims& d, const TcShape& s, c
     if (e != cudaSuccess) return e;
     long long blocks = (d.pairs + s.TP - 1) / s.TP;
     contract_tc_kernel<NPAD, F16><<<(unsigned)blocks, TC_THREADS, s.smem, st>>>(
-        d.N, d.nu, d.nd, d.G, s.TP, s.GT, s.NB1, s.NB2, s.c1col, s.d2col, d.pairs, (const uint4*)image, lexp, Phi, Theta, vpair,
-        epair, status); count_launches(1);
+        d.N, d.nu, d.nd, d.G, s.TP, s.GT, s.NB1, s.NB2, s.S, s.c1col, s.d2col, d.pairs, (const uint8_t*)image, lexp, Phi,
+        Theta, vpair, epair, status); count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const double* Phi, const double2* Theta,
-                        double2* vpair, double2* epair, int* status, bool f16) {
+                        const double2* phi, double2* vpair, double2* epair, int* status, bool f16) {
     TcShape s;
     if (!tc_shape(d.N, d.nu, d.nd, f16, s)) return cudaErrorInvalidValue;
-    if (d.tc_tp > 0 && d.tc_tp < s.TP) {   // fewer pairs per block: same tensor-memory layout rules, less shared memory
-        s.TP = d.tc_tp;
-        s.NB1 = ((s.TP * d.nu + 15) / 16) * 16;
-        s.c1col = (s.GT / s.GPT) * s.NB1;
-        s.d2col = f16 ? s.c1col + s.NB1 : s.c1col;
-        size_t smem = 1024 + 2 * (size_t)s.NB1 * s.NPAD * 2 + 2 * (size_t)s.TP * s.NB2 * s.NPAD * 2 + 32768 +
-                      2 * (size_t)128 * s.NPAD * 2;
-        s.smem = smem < 120 * 1024 ? 120 * 1024 : smem;
-    }
+    if (d.pairs <= 0) return cudaSuccess;
     long long G1p = (long long)((d.G + 1 + s.GT - 1) / s.GT) * s.GT;
     const int* lexp = reinterpret_cast<const int*>(static_cast<const uint8_t*>(image) +
-                                                   (size_t)(G1p / s.GPT) * s.NKB * 32768);
+                                                   (size_t)(G1p / s.GPT) * s.NKB * TC_UNIT);
+    TcyShape sy;
+    if (tcy_shape(d.N, d.nu, d.nd, f16, d.tc_tp, sy)) {   // Theta holds B = Phi A^-T here
+        if (d.P < 1 || d.pairs % d.P != 0) return cudaErrorInvalidValue;
+        return f16 ? launch_tcy<true>(st, d, sy, image, lexp, Theta, phi, vpair, epair, status)
+                   : launch_tcy<false>(st, d, sy, image, lexp, Theta, phi, vpair, epair, status);
+    }
+    if (d.tc_tp > 0 && d.tc_tp < s.TP && !tc_fit(s, d.nu, d.tc_tp, f16)) return cudaErrorInvalidValue;
     if (s.NPAD == 64)
         return f16 ? launch_tc<64, true>(st, d, s, image, lexp, Phi, Theta, vpair, epair, status)
                    : launch_tc<64, false>(st, d, s, image, lexp, Phi, Theta, vpair, epair, status);

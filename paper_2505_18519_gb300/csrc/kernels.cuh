@@ -12,7 +12,7 @@ void gemm_nn_f64(cudaStream_t s, int M, int Nc, int K, double alpha, const doubl
                  long long ldb, double beta, double* C, long long ldc);
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                       long long pairs, int P);
+                       long long pairs, int P, bool trial_side = false);
 cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, double2* dst, const int* alive,
                              int* status, int n_walkers);
 cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,
@@ -30,8 +30,11 @@ bool contract_tc_supported(int N, int nu, int nd, bool f16);
 size_t contract_tc_image_bytes(int N, int nu, int nd, int G, bool f16);
 cudaError_t contract_tc_prepare(cudaStream_t st, int N, int nu, int nd, int G, const double* h, const double* L,
                                 void* image, bool f16);
+// With contract_tc_walker_side(...) true the contraction takes B = Phi A^-T per
+// pair (overlap_lu with trial_side = true) in place of Theta, plus the walkers.
+bool contract_tc_walker_side(int N, int nu, int nd, bool f16);
 cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const double* Phi, const double2* Theta,
-                        double2* vpair, double2* epair, int* status, bool f16);
+                        const double2* phi, double2* vpair, double2* epair, int* status, bool f16);
 
 // walker.cu
 struct StepParams {

@@ -70,13 +70,16 @@ void gemm_nn_f64(cudaStream_t s, int M, int Nc, int K, double alpha, const doubl
 // LU with partial pivoting (largest |re|+|im|, lowest row on ties),
 // log det A = sum log|u_kk| + i Arg(prod u_kk / |u_kk| * (-1)^swaps).
 // With Theta != nullptr also A^-1 (from the LU) and Theta_s = phi_s A^-1,
-// written to columns col0..col0+n-1 of Theta[pair] (N x nt).
+// written to columns col0..col0+n-1 of Theta[pair] (N x nt); with trial_side
+// the trial-side factor B_s = Phi_s A^-T is written there instead (then
+// Theta_s = phi_s A^-1 and Phi_s^T X Theta_s = A B_s^T X phi_s A^-1 share traces).
 // Dynamic shared memory per warp: n*n double2 (A), n*n double2 (A^-1) when
 // Theta is requested, n ints (row permutation).
 __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int spin, long long pairs, int P,
                                   const double* __restrict__ Phi, long long Phi_stride,
                                   const double2* __restrict__ phi, double2* __restrict__ logdet,
-                                  double2* __restrict__ Theta, const int* __restrict__ alive, int* status) {
+                                  double2* __restrict__ Theta, const int* __restrict__ alive, int* status,
+                                  int trial_side) {
     extern __shared__ double2 sm[];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
@@ -189,6 +192,21 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
     }
     __syncwarp();
     double2* Th = Theta + pair * (long long)N * nt + col0;
+    if (trial_side) {
+        // B = Phi A^-T (trial side): B[i][b] = sum_a Phi[i][a] (A^-1)[b][a]
+        for (int e = lane; e < N * n; e += 32) {
+            int i = e / n, b = e - i * n;
+            double2 s = cmk(0.0, 0.0);
+            const double* row = Ph + (long long)i * nu;
+            for (int a = 0; a < n; ++a) {
+                const double2 t = Ainv[b * n + a];
+                s.x = fma(row[a], t.x, s.x);
+                s.y = fma(row[a], t.y, s.y);
+            }
+            Th[(long long)i * nt + b] = s;
+        }
+        return;
+    }
     for (int e = lane; e < N * n; e += 32) {
         int i = e / n, b = e - i * n;
         double2 s = cmk(0.0, 0.0);
@@ -204,7 +222,7 @@ static size_t overlap_smem_per_warp(int n, bool theta) {
 
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                       long long pairs, int P) {
+                       long long pairs, int P, bool trial_side) {
     int n = spin == 0 ? d.nu : d.nd;
     int col0 = spin == 0 ? 0 : d.nu;
     size_t per = overlap_smem_per_warp(n, Theta != nullptr);
@@ -216,7 +234,7 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
     if (e != cudaSuccess) return e;
     long long blocks = (pairs + wpb - 1) / wpb;
     overlap_lu_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nt, n, col0, spin, pairs, P, Phi, Phi_stride,
-                                                               phi, logdet, Theta, alive, status); count_launches(1);
+                                                               phi, logdet, Theta, alive, status, trial_side ? 1 : 0); count_launches(1);
     return cudaGetLastError();
 }
 

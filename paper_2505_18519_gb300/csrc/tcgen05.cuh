@@ -73,6 +73,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     return false;
 }
 
+// One arrival on `bar` that also expects `bytes` more bytes of asynchronous
+// copies to land before its phase can complete.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// ---------------------------------------------------------------- bulk copies
+// Contiguous global -> shared copy by the tensor memory accelerator (both
+// addresses 16-byte aligned, `bytes` a multiple of 16); completion is counted
+// in bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // ---------------------------------------------------------------- MMA
 // Instruction descriptor for kind::f16 with BF16 A and B, FP32 accumulator,
 // both operands K-major, shape M x N.
