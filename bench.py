@@ -213,13 +213,15 @@ def kernel_digest(kernel_source: str, end_marker: str = "size_t contract_fp64_sm
     return hashlib.sha256(text[:cut + 1] if cut >= 0 else text).hexdigest()[:16]
 
 
-def recorded_traffic(kernel_source: str):
-    """DRAM bytes per launch of the contraction from the committed ncu summary,
-    or None if the kernel's device code changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "contract_fp64_c1_n50.md")
+def recorded_traffic(kernel_source: str, summary: str = "contract_fp64_c1_n50.md",
+                     end_marker: str = "size_t contract_fp64_smem"):
+    """DRAM bytes per launch of a contraction kernel from its committed ncu
+    summary, or None if the kernel's device code changed since the counters
+    were taken."""
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
-    digest = kernel_digest(kernel_source)
+    digest = kernel_digest(kernel_source, end_marker)
     fields = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
@@ -259,6 +261,11 @@ def _timed(step, sync, stream, steps, world, local):
     return max_over_ranks(e0.elapsed_time(e1)), clk.summary(), int(l1 - l0)
 
 
+TC_TRAFFIC = {   # kernel -> (committed summary, end of its device code), for the medium workload
+    "contract_tcy_kernel": ("contract_tcy_c1_n50.md", "static size_t tcy_smem_bytes"),
+}
+
+
 def tensor_roofline(spec, W, P, prof, kernel):
     """Algorithmic FLOP rate of the tensor-core contraction against the
     measured sustained BF16 peak (FP16 has the same nominal rate)."""
@@ -271,8 +278,13 @@ def tensor_roofline(spec, W, P, prof, kernel):
     ms = prof["ms"]["contract"] / max(1, prof["launches"]["contract"])
     flops = contract_flops_per_pair(spec) * W * P
     achieved = flops / (ms / 1e3) / 1e12
+    traffic = None
+    if kernel in TC_TRAFFIC and (W, P) == (512, 32):
+        summary, marker = TC_TRAFFIC[kernel]
+        traffic = recorded_traffic(os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "contract_tc.cu"), summary,
+                                   marker)
     return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "peak_source": source, "traffic": None, "flops_per_launch": flops,
+            "frac": achieved / peak, "peak_source": source, "traffic": traffic, "flops_per_launch": flops,
             "ms_per_launch": ms,
             "note": "algorithmic FLOPs of the real contraction; the split-FP16 scheme issues 4 MMA products per "
                     "real product and pads N and n to MMA tile sizes"}
@@ -309,7 +321,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
              "(force bias + local energy) on the tensor cores in split FP16 with FP32 accumulation, everything "
              "else FP64", "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
              "gpu_launches": launches, "clocks": clocks,
-             "roofline": tensor_roofline(spec, W, P, prof, "contract_tc_kernel"),
+             "roofline": tensor_roofline(spec, W, P, prof, lib.contract_kernel(cfg)),
              "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
         if ew64 is not None:
             dw = np.abs(ew.real - ew64.real)
@@ -339,7 +351,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
              "what": f"same workload; {n_train} untimed training steps, then the timed steps (training continues)",
              "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
              "gpu_launches": launches, "clocks": clocks, "acceptance": acc,
-             "roofline": tensor_roofline(spec, W, P, prof, "contract_tc_kernel"),
+             "roofline": tensor_roofline(spec, W, P, prof, lib.contract_kernel(cfg)),
              "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
         if hist64 is not None and len(hist64):
             d["acceptance_prior_proposal"] = float(hist64[-steps:, 3].sum() / (min(steps, len(hist64)) * W * P))

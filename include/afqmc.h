@@ -204,6 +204,14 @@ afqmc_status afqmc_profile_read(afqmc_ctx* ctx, double* out, int len);
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t afqmc_launch_count(void);
 
+/* Which kernel computes the fused contraction of Eq. (15) and (27) for `cfg`:
+ * 0 contract_fp64_kernel (precision FP64), 1 contract_tc_kernel (tensor cores,
+ * per-pair form, N <= 128, n_up <= 32), 2 contract_tcy_kernel (tensor cores,
+ * walker-side form B_p^T (L_g phi_w) with B_p = Phi_p A_p^-T, N <= 64 and
+ * n_up + n_dn <= 40); -1 if `cfg` is NULL or no kernel supports its sizes.
+ * Host only. */
+int afqmc_contract_kernel(const afqmc_config* cfg);
+
 /* Local energies, force-bias values and overlaps of a batch of (walker, trial
  * sample) pairs that allocates nothing.  The paper has no counterpart: this is
  * for callers that cannot call cudaMalloc or give the library a workspace (code

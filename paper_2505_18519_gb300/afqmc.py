@@ -42,7 +42,7 @@ _lib = None
 EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc_step", "afqmc_energy",
            "afqmc_observables", "afqmc_history", "afqmc_stats", "afqmc_state_save", "afqmc_state_load",
            "afqmc_destroy", "afqmc_last_error", "afqmc_philox_fill", "afqmc_profile", "afqmc_profile_read",
-           "afqmc_launch_count", "afqmc_autotune", "afqmc_batch_create", "afqmc_batch_step", "afqmc_batch_sync",
+           "afqmc_launch_count", "afqmc_contract_kernel", "afqmc_autotune", "afqmc_batch_create", "afqmc_batch_step", "afqmc_batch_sync",
            "afqmc_batch_destroy", "afqmc_mlp_n_params", "afqmc_mlp_params", "afqmc_mlp_eval", "afqmc_mlp_state")
 
 PHASES = ("overlap", "contract", "average", "fields", "propagate", "ratio", "propose", "trial_orbitals",
@@ -92,6 +92,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.afqmc_profile_read.restype = I
     lib.afqmc_launch_count.argtypes = []
     lib.afqmc_launch_count.restype = ctypes.c_int64
+    lib.afqmc_contract_kernel.argtypes = [ctypes.c_void_p]
+    lib.afqmc_contract_kernel.restype = ctypes.c_int
     lib.afqmc_autotune.argtypes = [P, P]
     lib.afqmc_autotune.restype = I
     lib.afqmc_batch_create.argtypes = [I, P, P, ctypes.POINTER(P)]
@@ -350,6 +352,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+CONTRACT_KERNELS = {0: "contract_fp64_kernel", 1: "contract_tc_kernel", 2: "contract_tcy_kernel"}
+
+
+def contract_kernel(cfg: AfqmcConfig) -> str:
+    """Name of the kernel that runs the fused contraction for ``cfg``."""
+    k = int(load_library().afqmc_contract_kernel(ctypes.byref(cfg)))
+    if k not in CONTRACT_KERNELS:
+        raise AfqmcError(1, "no contraction kernel supports these sizes")
+    return CONTRACT_KERNELS[k]
 
 
 def launch_count() -> int:

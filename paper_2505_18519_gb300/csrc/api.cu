@@ -44,6 +44,14 @@ void afq::count_launches(long long n) { g_launches.fetch_add(n, std::memory_orde
 
 extern "C" int64_t afqmc_launch_count(void) { return g_launches.load(); }
 
+extern "C" int afqmc_contract_kernel(const afqmc_config* cfg) {
+    if (!cfg) return -1;
+    if (cfg->precision == AFQMC_PRECISION_FP64) return contract_fp64_supported(cfg->N, cfg->n_up, cfg->n_dn) ? 0 : -1;
+    const bool f16 = cfg->precision == AFQMC_PRECISION_FP16X3;
+    if (contract_tc_walker_side(cfg->N, cfg->n_up, cfg->n_dn, f16)) return 2;
+    return contract_tc_supported(cfg->N, cfg->n_up, cfg->n_dn, f16) ? 1 : -1;
+}
+
 static std::mutex g_smem_mu;
 static std::map<std::pair<const void*, int>, size_t> g_smem_limit;   // (kernel, device) -> bytes allowed
 
