@@ -49,11 +49,22 @@ def workload_desc(spec, run):
 
 
 def contract_flops_per_pair(spec):
-    """Algorithmic FLOPs of the fused contraction for one (walker, path) pair:
-    R = Phi^T X (X = h and every L_g): 2 n_up N^2 each; M_s = R Theta_s
-    (real x complex): 4 N n_s^2 each; exchange traces Tr(M M): 8 n_s^2 per g."""
+    """Algorithmic FLOPs of the fused contraction for one (walker, path) pair in
+    the per-pair association order: R = Phi^T X (X = h and every L_g): 2 n_up N^2
+    each; M_s = R Theta_s (real x complex): 4 N n_s^2 each; exchange traces
+    Tr(M M): 8 n_s^2 per g."""
     N, nu, nd, G = spec.N, spec.n_up, spec.n_dn, spec.n_chol
     return (G + 1) * 2 * nu * N * N + (G + 1) * 4 * N * (nu * nu + nd * nd) + G * 8 * (nu * nu + nd * nd)
+
+
+def contract_flops_walker_side(spec, P):
+    """Algorithmic FLOPs per pair of the walker-side FP64 form: Y_g = X_g phi_w
+    (real x complex, 4 N^2 (n_up + n_dn) per matrix, once per walker, shared by
+    its P pairs), Z = Phi_s^T Y_s (4 N n_s^2), M = Z A_s^-1 (complex, 8 n_s^3),
+    exchange traces (8 n_s^2 per g)."""
+    N, nu, nd, G = spec.N, spec.n_up, spec.n_dn, spec.n_chol
+    s2, s3 = nu * nu + nd * nd, nu ** 3 + nd ** 3
+    return (G + 1) * (4 * N * s2 + 8 * s3) + G * 8 * s2 + (G + 1) * 4 * N * N * (nu + nd) / P
 
 
 def step_working_set_bytes(spec, run):
@@ -261,6 +272,10 @@ def _timed(step, sync, stream, steps, world, local):
     return max_over_ranks(e0.elapsed_time(e1)), clk.summary(), int(l1 - l0)
 
 
+FP64_TRAFFIC = {   # kernel -> (committed summary, end of its device code), for the medium workload
+    "contract_fp64_kernel": ("contract_fp64_c1_n50.md",
+                             "// ---------------------------------------------------------------- walker-side form"),
+}
 TC_TRAFFIC = {   # kernel -> (committed summary, end of its device code), for the medium workload
     "contract_tcy_kernel": ("contract_tcy_c1_n50.md", "static size_t tcy_smem_bytes"),
 }
@@ -490,9 +505,12 @@ def our_arm(args):
     value = pairs_total * args.steps / (ms_max / 1e3)
     e2e_value = pairs_total * args.steps / e2e_s if e2e_s else None
     contract_ms = prof["ms"]["contract"] / max(1, prof["launches"]["contract"])
-    flops = contract_flops_per_pair(spec) * W * P
+    kernel = lib.contract_kernel(cfg)
+    flops_pair_order = contract_flops_per_pair(spec) * W * P
+    flops = contract_flops_walker_side(spec, P) * W * P if kernel == "contract_fp64z_kernel" else flops_pair_order
     achieved = flops / (contract_ms / 1e3) / 1e12
-    traffic = recorded_traffic(os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "contract_fp64.cu"))
+    traffic = recorded_traffic(os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "contract_fp64.cu"),
+                               *FP64_TRAFFIC[kernel]) if kernel in FP64_TRAFFIC and (W, P) == (512, 32) else None
     phases = {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}
 
     if world > 1:
@@ -509,10 +527,13 @@ def our_arm(args):
         "config": {"workload": workload_desc(spec, run), "walkers_total": W * world, "paths": P,
                    "system_seed": spec.seed, "philox_seed": seed,
                    "l2": f"working set {step_working_set_bytes(spec, run) / 1e9:.2f} GB per step > 129 MB L2; no flush"},
-        "roofline": {"bound": "alu", "kernel": "contract_fp64_kernel", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                      "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (no FP64 figure measured by the driver)",
-                     "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": contract_ms},
+                     "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": contract_ms,
+                     "flops_per_launch_pair_order": flops_pair_order,
+                     "note": "flops_per_launch counts the kernel's own association order; the per-pair order "
+                             "(R = Phi^T L_g first) needs flops_per_launch_pair_order"},
         "cpu_baseline": cpu,
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 32,

@@ -208,8 +208,10 @@ int64_t afqmc_launch_count(void);
  * 0 contract_fp64_kernel (precision FP64), 1 contract_tc_kernel (tensor cores,
  * per-pair form, N <= 128, n_up <= 32), 2 contract_tcy_kernel (tensor cores,
  * walker-side form B_p^T (L_g phi_w) with B_p = Phi_p A_p^-T, N <= 64 and
- * n_up + n_dn <= 40); -1 if `cfg` is NULL or no kernel supports its sizes.
- * Host only. */
+ * n_up + n_dn <= 40), 3 contract_fp64z_kernel (precision FP64, walker-side form
+ * Phi_p^T (L_g phi_w) A_p^-1 for blocks of 8 or 16 pairs of a walker: when
+ * n_paths >= 8 and the block's operands fit in shared memory, e.g. N <= 64);
+ * -1 if `cfg` is NULL or no kernel supports its sizes.  Host only. */
 int afqmc_contract_kernel(const afqmc_config* cfg);
 
 /* Local energies, force-bias values and overlaps of a batch of (walker, trial

@@ -354,7 +354,8 @@ class Batch:
             pass
 
 
-CONTRACT_KERNELS = {0: "contract_fp64_kernel", 1: "contract_tc_kernel", 2: "contract_tcy_kernel"}
+CONTRACT_KERNELS = {0: "contract_fp64_kernel", 1: "contract_tc_kernel", 2: "contract_tcy_kernel",
+                    3: "contract_fp64z_kernel"}
 
 
 def contract_kernel(cfg: AfqmcConfig) -> str:

@@ -46,7 +46,10 @@ extern "C" int64_t afqmc_launch_count(void) { return g_launches.load(); }
 
 extern "C" int afqmc_contract_kernel(const afqmc_config* cfg) {
     if (!cfg) return -1;
-    if (cfg->precision == AFQMC_PRECISION_FP64) return contract_fp64_supported(cfg->N, cfg->n_up, cfg->n_dn) ? 0 : -1;
+    if (cfg->precision == AFQMC_PRECISION_FP64) {
+        if (contract_fp64_walker_side(cfg->N, cfg->n_up, cfg->n_dn, cfg->n_paths)) return 3;
+        return contract_fp64_supported(cfg->N, cfg->n_up, cfg->n_dn) ? 0 : -1;
+    }
     const bool f16 = cfg->precision == AFQMC_PRECISION_FP16X3;
     if (contract_tc_walker_side(cfg->N, cfg->n_up, cfg->n_dn, f16)) return 2;
     return contract_tc_supported(cfg->N, cfg->n_up, cfg->n_dn, f16) ? 1 : -1;
@@ -348,13 +351,17 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     afqmc_status st;
     const bool f16 = ctx->cfg.precision == AFQMC_PRECISION_FP16X3;
-    const bool walker_side = ctx->cfg.precision != AFQMC_PRECISION_FP64 && contract_tc_walker_side(d.N, d.nu, d.nd, f16);
+    const bool fp64 = ctx->cfg.precision == AFQMC_PRECISION_FP64;
+    const int ovl = fp64 ? (contract_fp64_walker_side(d.N, d.nu, d.nd, d.P) ? OVL_INVERSE : OVL_THETA)
+                         : (contract_tc_walker_side(d.N, d.nu, d.nd, f16) ? OVL_TRIAL : OVL_THETA);
     for (int spin = 0; spin < 2; ++spin)
         CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
-                      walker_side));
+                      ovl));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64)
         CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.vpair, w.epair, w.status, f16));
+    else if (ovl == OVL_INVERSE)
+        CK(contract_fp64_walker(s, d, w.h, w.L, w.Phi, w.Theta, w.phi, w.vpair, w.epair));
     else
         CK(contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
     if ((st = prof_mark(ctx, PH_CONTRACT)) != AFQMC_OK) return st;

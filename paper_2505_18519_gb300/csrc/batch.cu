@@ -95,10 +95,10 @@ extern "C" afqmc_status afqmc_autotune(afqmc_ctx* ctx, int* chosen) {
     int best_tp = 0;
     if (c.precision != AFQMC_PRECISION_FP64) {
         const bool f16 = c.precision == AFQMC_PRECISION_FP16X3;
-        const bool ws = contract_tc_walker_side(d.N, d.nu, d.nd, f16);
+        const int ovl = contract_tc_walker_side(d.N, d.nu, d.nd, f16) ? OVL_TRIAL : OVL_THETA;
         for (int spin = 0; spin < 2; ++spin)
             BK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs,
-                          d.P, ws));
+                          d.P, ovl));
         best = 1e30f;
         for (int tp : {0, 4, 2, 1}) {
             Dims t = d;

@@ -146,6 +146,187 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
     if (tid == 0) epair[pair] = e_acc;
 }
 
+// ---------------------------------------------------------------- walker-side form
+// With Theta_s = phi_s A_s^-1 (A_s = Phi_s^T phi_s) the matrix of the contraction is
+//   M_g,s = Phi_s^T X_g Theta_s = Z_g,s A_s^-1,   Z_g,s = Phi_s^T Y_g,s,   Y_g = X_g phi_w,
+// and Y_g is the same for every pair of walker w.  A block takes PG = 8 PPW pairs
+// of one walker (warp k owns pairs k PPW .. k PPW + PPW - 1): per matrix X_g it
+// forms Y_g once (all threads), then each warp forms Z (real x complex), M = Z A^-1
+// and the traces for its own pairs.  FP64 multiply-adds per pair and matrix:
+//   2 N (n_up^2 + n_dn^2) + 4 (n_up^3 + n_dn^3) + 4 (n_up^2 + n_dn^2) + 2 N^2 (n_up + n_dn) / PG
+// against n_up N^2 + 2 N (n_up^2 + n_dn^2) + 4 (n_up^2 + n_dn^2) for the per-pair form above.
+constexpr int CZ_T = 256;
+constexpr int CZ_WARPS = CZ_T / 32;
+constexpr int CZ_MAXPPW = 2;
+
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(CZ_T, 1)
+    contract_fp64z_kernel(int N, int nu, int nd, int G, int P, int PPW, const double* __restrict__ h,
+                          const double* __restrict__ L, const double* __restrict__ Phi, const double2* __restrict__ Ainv,
+                          const double2* __restrict__ phi, double2* __restrict__ vpair, double2* __restrict__ epair) {
+    extern __shared__ double smz[];
+    const int nt = nu + nd, PG = CZ_WARPS * PPW;
+    const int S2 = nu * nu + nd * nd;
+    const int bpw = (P + PG - 1) / PG;
+    const long long w = blockIdx.x / bpw;
+    const int p0 = (int)(blockIdx.x % bpw) * PG;
+    const int np = min(PG, P - p0);
+    const long long pairbase = w * P + p0;
+    double* sX = smz;                                                        // N x N
+    double2* sphi = reinterpret_cast<double2*>(sX + r2((size_t)N * N));      // N x nt
+    double2* sY = sphi + (size_t)N * nt;                                     // N x nt
+    double* sPh = reinterpret_cast<double*>(sY + (size_t)N * nt);            // PG x N x nu
+    double2* sW = reinterpret_cast<double2*>(sPh + r2((size_t)PG * N * nu));  // PG x S2
+    double2* sZ = sW + (size_t)PG * S2;                                      // PG x nu^2
+    double2* sQ = sZ + (size_t)PG * nu * nu;                                 // PG x nu^2
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int e = tid; e < N * nt; e += CZ_T) sphi[e] = phi[w * (long long)N * nt + e];
+    for (int e = tid; e < PG * N * nu; e += CZ_T) {
+        const int q = e / (N * nu);
+        sPh[e] = q < np ? Phi[(pairbase + q) * (long long)N * nu + (e - q * N * nu)] : 0.0;
+    }
+    for (int e = tid; e < PG * S2; e += CZ_T) {
+        const int q = e / S2;
+        sW[e] = q < np ? Ainv[(pairbase + q) * (long long)N * nt + (e - q * S2)] : cmk(0.0, 0.0);
+    }
+    double2 eacc[CZ_MAXPPW];
+#pragma unroll
+    for (int q = 0; q < CZ_MAXPPW; ++q) eacc[q] = cmk(0.0, 0.0);
+    __syncthreads();
+    for (int g = -1; g < G; ++g) {
+        const double* X = (g < 0) ? h : L + (long long)g * N * N;
+        for (int e = tid; e < N * N; e += CZ_T) sX[e] = X[e];
+        __syncthreads();
+        // Y = X phi_w
+        for (int e = tid; e < N * nt; e += CZ_T) {
+            const int i = e / nt, c = e - i * nt;
+            const double* Xi = sX + (size_t)i * N;
+            double2 acc = cmk(0.0, 0.0);
+            for (int k = 0; k < N; ++k) {
+                const double x = Xi[k];
+                const double2 f = sphi[(size_t)k * nt + c];
+                acc.x = fma(x, f.x, acc.x);
+                acc.y = fma(x, f.y, acc.y);
+            }
+            sY[e] = acc;
+        }
+        __syncthreads();
+        double2 tr[CZ_MAXPPW], ex[CZ_MAXPPW];
+#pragma unroll
+        for (int q = 0; q < CZ_MAXPPW; ++q) { tr[q] = cmk(0.0, 0.0); ex[q] = cmk(0.0, 0.0); }
+        for (int spin = 0; spin < 2; ++spin) {
+            const int n = spin ? nd : nu;
+            if (n == 0) continue;
+            const int off = spin ? nu : 0, woff = spin ? nu * nu : 0, nn = n * n, nout = PPW * nn;
+            // Z = Phi_s^T Y_s for this warp's pairs
+            for (int o = lane; o < nout; o += 32) {
+                const int q = o / nn, r = o - q * nn, a = r / n, b = r - a * n;
+                const int p = warp * PPW + q;
+                const double* Ph = sPh + (size_t)p * N * nu + a;
+                const double2* Yb = sY + off + b;
+                double2 acc = cmk(0.0, 0.0);
+                for (int i = 0; i < N; ++i) {
+                    const double f = Ph[(size_t)i * nu];
+                    const double2 y = Yb[(size_t)i * nt];
+                    acc.x = fma(f, y.x, acc.x);
+                    acc.y = fma(f, y.y, acc.y);
+                }
+                sZ[(size_t)p * nu * nu + r] = acc;
+            }
+            __syncwarp();
+            // M = Z A^-1
+            for (int o = lane; o < nout; o += 32) {
+                const int q = o / nn, r = o - q * nn, a = r / n, b = r - a * n;
+                const int p = warp * PPW + q;
+                const double2* Zr = sZ + (size_t)p * nu * nu + (size_t)a * n;
+                const double2* Wc = sW + (size_t)p * S2 + woff + b;
+                double2 acc = cmk(0.0, 0.0);
+                for (int c = 0; c < n; ++c) cfma(acc, Zr[c], Wc[(size_t)c * n]);
+                sQ[(size_t)p * nu * nu + r] = acc;
+            }
+            __syncwarp();
+            // Tr M and Tr M^2 of this spin
+            for (int o = lane; o < nout; o += 32) {
+                const int q = o / nn, r = o - q * nn, a = r / n, b = r - a * n;
+                const int p = warp * PPW + q;
+                const double2* Mp = sQ + (size_t)p * nu * nu;
+                const double2 mab = Mp[r];
+#pragma unroll
+                for (int qq = 0; qq < CZ_MAXPPW; ++qq) {
+                    if (qq == q) {
+                        cfma(ex[qq], mab, Mp[(size_t)b * n + a]);
+                        if (a == b) tr[qq] = cadd(tr[qq], mab);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int q = 0; q < CZ_MAXPPW; ++q) {
+            if (q >= PPW) break;
+            const double2 v = warp_sum2(tr[q]);
+            const double2 x = warp_sum2(ex[q]);
+            const int p = warp * PPW + q;
+            if (lane == 0 && p < np) {
+                if (g < 0) {
+                    eacc[q] = cadd(eacc[q], v);            // one-body term sum_s Tr(Phi_s^T h Theta_s)
+                } else {
+                    vpair[(pairbase + p) * G + g] = v;
+                    const double2 v2 = cmul(v, v);
+                    eacc[q].x += 0.5 * (v2.x - x.x);
+                    eacc[q].y += 0.5 * (v2.y - x.y);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < CZ_MAXPPW; ++q) {
+        const int p = warp * PPW + q;
+        if (q < PPW && lane == 0 && p < np) epair[pairbase + p] = eacc[q];
+    }
+}
+
+static size_t contract_fp64z_smem(int N, int nu, int nd, int PPW) {
+    const size_t PG = (size_t)CZ_WARPS * PPW, nt = nu + nd, S2 = (size_t)nu * nu + (size_t)nd * nd;
+    return (r2((size_t)N * N) + 4 * (size_t)N * nt + r2(PG * N * nu) + 2 * PG * S2 + 4 * PG * nu * nu) * sizeof(double);
+}
+
+// Pairs per warp for the walker-side form: 2 if it fits in shared memory and the
+// walker has at least 16 pairs, 1 with at least 8; 0 = use the per-pair form.
+static int contract_fp64z_ppw(int N, int nu, int nd, int P) {
+    if (N < 1 || nu < 1 || nd < 0 || nd > nu) return 0;
+    for (int ppw = CZ_MAXPPW; ppw >= 1; --ppw)
+        if (P >= CZ_WARPS * ppw && contract_fp64z_smem(N, nu, nd, ppw) <= 220 * 1024) return ppw;
+    return 0;
+}
+
+bool contract_fp64_walker_side(int N, int nu, int nd, int P) { return contract_fp64z_ppw(N, nu, nd, P) > 0; }
+
+cudaError_t contract_fp64_walker(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
+                                 const double2* Ainv, const double2* phi, double2* vpair, double2* epair) {
+    const int ppw = contract_fp64z_ppw(d.N, d.nu, d.nd, d.P);
+    if (ppw == 0 || d.P < 1 || d.pairs % d.P != 0) return cudaErrorInvalidValue;
+    if (d.pairs == 0) return cudaSuccess;
+    const size_t smem = contract_fp64z_smem(d.N, d.nu, d.nd, ppw);
+    cudaError_t e = raise_smem_limit((const void*)contract_fp64z_kernel, smem);
+    if (e != cudaSuccess) return e;
+    const int PG = CZ_WARPS * ppw;
+    const long long blocks = (d.pairs / d.P) * ((d.P + PG - 1) / PG);
+    contract_fp64z_kernel<<<(unsigned)blocks, CZ_T, smem, s>>>(d.N, d.nu, d.nd, d.G, d.P, ppw, h, L, Phi, Ainv, phi, vpair,
+                                                             epair); count_launches(1);
+    return cudaGetLastError();
+}
+
 size_t contract_fp64_smem(int N, int nu, int nd, int JB) {
     int nt = nu + nd;
     size_t oTh = r2((size_t)N * nu), oL = oTh + 2 * (size_t)N * nt, oR = oL + (size_t)N * JB;

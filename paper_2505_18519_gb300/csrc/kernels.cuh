@@ -10,9 +10,10 @@ namespace afq {
 // linalg_fp64.cu
 void gemm_nn_f64(cudaStream_t s, int M, int Nc, int K, double alpha, const double* A, long long lda, const double* B,
                  long long ldb, double beta, double* C, long long ldc);
+enum OverlapOutput { OVL_THETA = 0, OVL_TRIAL = 1, OVL_INVERSE = 2 };
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                       long long pairs, int P, bool trial_side = false);
+                       long long pairs, int P, int trial_side = OVL_THETA);
 cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, double2* dst, const int* alive,
                              int* status, int n_walkers);
 cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,
@@ -24,6 +25,12 @@ cudaError_t one_body_propagator(cudaStream_t s, int N, int G, double dtau, const
 cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                           const double2* Theta, double2* vpair, double2* epair, long long pairs);
 bool contract_fp64_supported(int N, int nu, int nd);
+// Walker-side FP64 form (Y_g = X_g phi_w once per block of a walker's pairs,
+// Z = Phi_p^T Y_g, Q = Z A_p^-1; Tr Q and Tr Q^2 are those of M_g): needs A^-1
+// per pair and spin (overlap_lu with OVL_INVERSE) and the walkers.
+bool contract_fp64_walker_side(int N, int nu, int nd, int P);
+cudaError_t contract_fp64_walker(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
+                                 const double2* Ainv, const double2* phi, double2* vpair, double2* epair);
 
 // contract_tc.cu
 bool contract_tc_supported(int N, int nu, int nd, bool f16);

@@ -69,10 +69,11 @@ void gemm_nn_f64(cudaStream_t s, int M, int Nc, int K, double alpha, const doubl
 // One warp per (pair, spin).  A = Phi_s^T phi_s (n x n complex; Phi real),
 // LU with partial pivoting (largest |re|+|im|, lowest row on ties),
 // log det A = sum log|u_kk| + i Arg(prod u_kk / |u_kk| * (-1)^swaps).
-// With Theta != nullptr also A^-1 (from the LU) and Theta_s = phi_s A^-1,
-// written to columns col0..col0+n-1 of Theta[pair] (N x nt); with trial_side
-// the trial-side factor B_s = Phi_s A^-T is written there instead (then
-// Theta_s = phi_s A^-1 and Phi_s^T X Theta_s = A B_s^T X phi_s A^-1 share traces).
+// With Theta != nullptr also A^-1 (from the LU) and, by `trial_side`:
+//   OVL_THETA (0): Theta_s = phi_s A^-1 in columns col0..col0+n-1 of Theta[pair] (N x nt);
+//   OVL_TRIAL (1): the trial-side factor B_s = Phi_s A^-T there instead (then
+//                  Phi_s^T X Theta_s = A B_s^T X phi_s A^-1 has the same traces);
+//   OVL_INVERSE (2): A^-1 itself, at offset (spin ? nu^2 : 0) of the pair's block.
 // Dynamic shared memory per warp: n*n double2 (A), n*n double2 (A^-1) when
 // Theta is requested, n ints (row permutation).
 __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int spin, long long pairs, int P,
@@ -161,7 +162,10 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
             logdet[pair * 2 + spin] = cmk(-INFINITY, 0.0);
             atomicOr(status, STATUS_SINGULAR);
         }
-        if (Theta) {
+        if (Theta && trial_side == 2) {
+            double2* Wp = Theta + pair * (long long)N * nt + (spin ? (long long)nu * nu : 0);
+            for (int e = lane; e < n * n; e += 32) Wp[e] = cmk(0.0, 0.0);
+        } else if (Theta) {
             double2* Th = Theta + pair * (long long)N * nt + col0;
             for (int e = lane; e < N * n; e += 32) Th[(long long)(e / n) * nt + e % n] = cmk(0.0, 0.0);
         }
@@ -191,6 +195,12 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
         }
     }
     __syncwarp();
+    if (trial_side == 2) {
+        // A^-1 itself: pair block [A_up^-1 (nu x nu) | A_dn^-1 (nd x nd)], row-major
+        double2* Wp = Theta + pair * (long long)N * nt + (spin ? (long long)nu * nu : 0);
+        for (int e = lane; e < n * n; e += 32) Wp[e] = Ainv[e];
+        return;
+    }
     double2* Th = Theta + pair * (long long)N * nt + col0;
     if (trial_side) {
         // B = Phi A^-T (trial side): B[i][b] = sum_a Phi[i][a] (A^-1)[b][a]
@@ -222,7 +232,7 @@ static size_t overlap_smem_per_warp(int n, bool theta) {
 
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                       long long pairs, int P, bool trial_side) {
+                       long long pairs, int P, int trial_side) {
     int n = spin == 0 ? d.nu : d.nd;
     int col0 = spin == 0 ? 0 : d.nu;
     size_t per = overlap_smem_per_warp(n, Theta != nullptr);
@@ -234,7 +244,7 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
     if (e != cudaSuccess) return e;
     long long blocks = (pairs + wpb - 1) / wpb;
     overlap_lu_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nt, n, col0, spin, pairs, P, Phi, Phi_stride,
-                                                               phi, logdet, Theta, alive, status, trial_side ? 1 : 0); count_launches(1);
+                                                               phi, logdet, Theta, alive, status, trial_side); count_launches(1);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,11 @@ SYSTEMS = {
     "one_electron_each": (ai.SystemSpec(9, 1, 1, 11, 3, False, 79), 4, 3, 0.02),
     "single_path": (ai.SystemSpec(10, 4, 3, 16, 5, False, 80), 7, 1, 0.01),
     "medium": (ai.SystemSpec(50, 10, 10, 250, 50, True, 1001), 4, 32, 0.005),
+    # the walker-side FP64 contraction (blocks of 8 or 16 pairs of a walker): a ragged
+    # last block, one spin only, and 16 pairs per block
+    "ragged_walker_side": (ai.SystemSpec(37, 7, 5, 40, 9, True, 77), 3, 11, 0.01),
+    "one_spin_walker_side": (ai.SystemSpec(12, 3, 0, 20, 6, True, 78), 3, 9, 0.01),
+    "two_blocks_walker_side": (ai.SystemSpec(20, 5, 4, 60, 7, True, 82), 2, 35, 0.01),
 }
 
 
@@ -303,4 +308,36 @@ def test_bad_state_buffer_is_rejected():
     with pytest.raises(lib.AfqmcError) as ei:
         ctx.load_state(blob[:-8])
     assert ei.value.status == 5
+    ctx.close()
+
+
+def test_fp64_contraction_forms_agree():
+    """The per-pair FP64 contraction (R_g = Phi^T L_g first; used by the entry
+    point that allocates nothing) and the walker-side one (Y_g = L_g phi_w once
+    per block of a walker's pairs, then Phi^T Y A^-1; used by contexts with at
+    least 8 paths) on the same walker and path states."""
+    spec = ai.SystemSpec(50, 10, 10, 250, 50, True, 1001)
+    s = ai.make_system(spec)
+    W, P = 3, 16
+    cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, 0.005, 77, n_burn=3)
+    assert lib.contract_kernel(cfg) == "contract_fp64z_kernel"
+    ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U)
+    ctx.step(2)
+    ctx.energy()
+    ref = ctx.observables()
+    st = ctx.state_arrays()
+    dev = torch.device("cuda")
+    pairs = W * P
+    h = torch.from_numpy(s.h).to(dev)
+    L = torch.from_numpy(s.L).to(dev)
+    Phi = torch.from_numpy(np.ascontiguousarray(st["Phi"])).to(dev)
+    phi = np.ascontiguousarray(np.concatenate([st["phi_up"], st["phi_dn"]], axis=2))
+    phi_d = torch.from_numpy(phi.view(np.float64)).to(dev)
+    logov = torch.empty(2 * pairs, dtype=torch.float64, device=dev)
+    e_local = torch.empty(2 * pairs, dtype=torch.float64, device=dev)
+    fb = torch.empty(2 * pairs * spec.n_chol, dtype=torch.float64, device=dev)
+    lib.local_energy_noalloc(spec.N, spec.n_up, spec.n_dn, spec.n_chol, pairs, P, h, L, Phi, phi_d, logov, e_local, fb)
+    torch.cuda.synchronize()
+    el = e_local.cpu().numpy().view(np.complex128).reshape(W, P)
+    assert np.max(np.abs(el - ref["e_local"])) < 1e-9
     ctx.close()
