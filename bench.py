@@ -275,6 +275,7 @@ def _timed(step, sync, stream, steps, world, local):
 FP64_TRAFFIC = {   # kernel -> (committed summary, end of its device code), for the medium workload
     "contract_fp64_kernel": ("contract_fp64_c1_n50.md",
                              "// ---------------------------------------------------------------- walker-side form"),
+    "contract_fp64z_kernel": ("contract_fp64z_c1_n50.md", "size_t contract_fp64_smem"),
 }
 TC_TRAFFIC = {   # kernel -> (committed summary, end of its device code), for the medium workload
     "contract_tcy_kernel": ("contract_tcy_c1_n50.md", "static size_t tcy_smem_bytes"),
@@ -310,7 +311,7 @@ def _emix(hist):
     return np.where(hist[:, 1] > 0, hist[:, 0] / np.where(hist[:, 1] > 0, hist[:, 1], 1.0), np.nan)
 
 
-def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, local, only=None):
+def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, local, only=None, state0=None):
     """The mixed-precision contraction, the learned proposal and the batch of
     uneven systems, each timed like the headline on this GPU's walker block."""
     import numpy as np
@@ -324,6 +325,8 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
                               walker_offset=rank * W, e_shift=28.5, precision="fp16x3")
         ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
+        if state0 is not None:
+            ctx.load_state(state0)   # the FP64 run's initial state: the differences below are the contraction's
         ew = ctx.energy(walkers=True)["e_walker"]
         for _ in range(warmup):
             ctx.step(1)
@@ -332,9 +335,9 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         prof = ctx.profile_read()
         hist = ctx.history(warmup + steps)
         ctx.close()
-        d = {"precision": "fp16x3", "what": "same workload and Philox streams as the headline; the contraction "
-             "(force bias + local energy) on the tensor cores in split FP16 with FP32 accumulation, everything "
-             "else FP64", "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+        d = {"precision": "fp16x3", "what": "same workload, Philox streams and initial state as the headline; the "
+             "contraction (force bias + local energy) on the tensor cores in split FP16 with FP32 accumulation, the "
+             "trial orbitals in double-float (FP32 pairs), everything else FP64", "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
              "gpu_launches": launches, "clocks": clocks,
              "roofline": tensor_roofline(spec, W, P, prof, lib.contract_kernel(cfg)),
              "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
@@ -448,7 +451,8 @@ def our_arm(args):
     with torch.cuda.device(dev):
         ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
         stream = ctx.stream
-        ew64 = ctx.energy(walkers=True)["e_walker"]     # initial state, identical for every precision
+        state0 = ctx.save_state()                        # the mixed-precision run starts from this state
+        ew64 = ctx.energy(walkers=True)["e_walker"]
         for _ in range(args.warmup):
             ctx.step(1)
         torch.cuda.synchronize(dev)
@@ -499,7 +503,8 @@ def our_arm(args):
             ctx2.close()
         variants = None
         if not args.no_variants:
-            variants = run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist_all, local)
+            variants = run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist_all, local,
+                                    state0=state0)
 
     pairs_total = W * P * world
     value = pairs_total * args.steps / (ms_max / 1e3)

@@ -317,6 +317,16 @@ static StepParams params_of(const afqmc_config* c) {
     return p;
 }
 
+// Trial orbitals exp(S) Phi0 for `problems` matrices S in ws.Sprop: FP64 on the
+// FP64 path, double-float arithmetic on the mixed-precision path.
+static cudaError_t trial_orbitals_of(afqmc_ctx* ctx, long long problems, double* Out, const int* alive, int P) {
+    const Dims& d = ctx->d;
+    Workspace& w = ctx->ws;
+    if (ctx->cfg.precision == AFQMC_PRECISION_FP64)
+        return trial_orbitals(ctx->stream, d.N, d.nu, problems, w.Sprop, w.Phi0, Out, alive, P, w.status, d.cheb_threads);
+    return trial_orbitals_df(ctx->stream, d.N, d.nu, problems, w.Sprop, w.Phi0, Out, alive, P, w.status, d.cheb_threads);
+}
+
 // One Metropolis sweep of every path against the walker orbitals `orbitals`
 // (phi' during a step, phi during burn-in).
 static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t tag_prop, uint32_t tag_acc,
@@ -332,7 +342,7 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
                 (long long)d.N * d.N);
     CK(cudaGetLastError());
     if ((st = prof_mark(ctx, PH_PROPOSE)) != AFQMC_OK) return st;
-    CK(trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phiprop, w.alive, d.P, w.status, d.cheb_threads));
+    CK(trial_orbitals_of(ctx, d.pairs, w.Phiprop, w.alive, d.P));
     if ((st = prof_mark(ctx, PH_TRIAL)) != AFQMC_OK) return st;
     for (int spin = 0; spin < 2; ++spin)
         CK(overlap_lu(s, d, spin, w.Phiprop, (long long)d.N * d.nu, orbitals, w.logdet_prop, nullptr, w.alive, w.status,
@@ -422,13 +432,19 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         // initial walkers phi_w = Phi(x_w), x_w ~ N(0, I), orthonormalised
         fill_normals(s, w.xprop, d.W, d.K, p.woff, p.seed, TAG_INIT_WALKER, w.counters, 0);
         gemm_nn_f64(s, d.W, (int)NN, d.K, 1.0, w.xprop, d.K, w.U, NN, 0.0, w.Sprop, NN);
-        trial_orbitals(s, d.N, d.nu, d.W, w.Sprop, w.Phi0, w.Phiprop, nullptr, 1, w.status);
+        if ((e = trial_orbitals_of(ctx, d.W, w.Phiprop, nullptr, 1)) != cudaSuccess) {
+            st = fail(AFQMC_ERR_CUDA, "initial walkers: %s", cudaGetErrorString(e));
+            break;
+        }
         walkers_from_trial(s, d, w.Phiprop, w.phi_new);
         reorthonormalise(s, d, w.phi_new, w.phi, nullptr, w.status, d.W);
         // paths x_wp ~ N(0, I) and their orbitals
         fill_normals(s, w.x, d.pairs, d.K, p.woff * d.P, p.seed, TAG_INIT_PATH, w.counters, 0);
         gemm_nn_f64(s, (int)d.pairs, (int)NN, d.K, 1.0, w.x, d.K, w.U, NN, 0.0, w.Sprop, NN);
-        trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phi, nullptr, d.P, w.status);
+        if ((e = trial_orbitals_of(ctx, d.pairs, w.Phi, nullptr, d.P)) != cudaSuccess) {
+            st = fail(AFQMC_ERR_CUDA, "initial paths: %s", cudaGetErrorString(e));
+            break;
+        }
         set_value(s, w.weight, d.W, 1.0);
         set_int(s, w.alive, d.W, 1);
         for (int spin = 0; spin < 2; ++spin)

@@ -116,8 +116,11 @@ extern "C" afqmc_status afqmc_autotune(afqmc_ctx* ctx, int* chosen) {
     best = 1e30f;
     for (int th : {128, 256}) {
         float ms;
-        st = time_ms(s, [&] { return trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phiprop, w.alive, d.P,
-                                                    w.status, th); }, 1, &ms);
+        st = time_ms(s, [&] {
+            return c.precision == AFQMC_PRECISION_FP64
+                       ? trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phiprop, w.alive, d.P, w.status, th)
+                       : trial_orbitals_df(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phiprop, w.alive, d.P, w.status, th);
+        }, 1, &ms);
         if (st != AFQMC_OK) return st;
         if (ms < best) { best = ms; best_th = th; }
     }

@@ -18,6 +18,10 @@ cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, 
                              int* status, int n_walkers);
 cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,
                            double* Out, const int* alive, int P, int* status, int threads = 256);
+// trial_df.cu: the same in double-float arithmetic (mixed-precision path); S_all
+// is scratch (converted in place when S does not fit in shared memory)
+cudaError_t trial_orbitals_df(cudaStream_t s, int N, int nu, long long problems, double* S_all, const double* Phi0,
+                              double* Out, const int* alive, int P, int* status, int threads = 256);
 cudaError_t one_body_propagator(cudaStream_t s, int N, int G, double dtau, const double* h, const double* L, double* T,
                                 double* scratch3, double* expT);
 

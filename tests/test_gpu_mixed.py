@@ -101,10 +101,18 @@ def test_large_workload_against_fp64_gpu_path():
     s = ai.make_system(spec)
     W, P = 32, run.n_paths
     res = {}
+    state = None
     for prec in ("fp64", "fp16x3"):
         cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, ai.philox_run_seed(2),
                               n_burn=8, precision=prec)
         ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U)
+        # both measure the FP64 context's state: the mixed path also forms its trial
+        # orbitals differently (double-float), and nearly singular overlaps this early
+        # in the burn-in amplify even 1e-12 differences of the state
+        if state is None:
+            state = ctx.save_state()
+        else:
+            ctx.load_state(state)
         res[prec] = ctx.energy(walkers=True)
         ctx.close()
     d_walker = np.abs(res["fp16x3"]["e_walker"] - res["fp64"]["e_walker"])
@@ -112,3 +120,23 @@ def test_large_workload_against_fp64_gpu_path():
     assert abs(res["fp16x3"]["e_mix"] - res["fp64"]["e_mix"]) < E_MIX_TOL
     print("large workload: median walker dE %.2e, max %.2e, dE_mix %.2e" % (
         np.median(d_walker), d_walker.max(), abs(res["fp16x3"]["e_mix"] - res["fp64"]["e_mix"])))
+
+
+@pytest.mark.parametrize("name", ["c0", "ragged", "n70_two_k_blocks", "medium"])
+def test_double_float_trial_orbitals_against_exact_exponential(name):
+    """The mixed path forms Phi(x) = exp(sum_k x_k U_k) Phi0 in double-float
+    arithmetic: after burn-in every stored path orbital must equal the exact
+    exponential (the oracle's, by eigendecomposition) of its own x to 1e-11
+    relative, and the paths' x must match the FP64 path's (same Metropolis
+    decisions)."""
+    spec, W, P, dtau = SYSTEMS[name]
+    s, ctx = _ctx(spec, W, P, dtau, 91, "fp16x3", n_burn=4)
+    st = ctx.state_arrays()
+    ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, dtau)
+    exact = oa.trial_orbitals(ham, st["x"])
+    scale = np.max(np.abs(exact), axis=(-2, -1), keepdims=True)
+    assert np.max(np.abs(st["Phi"] - exact) / scale) < 1e-11
+    s64, ctx64 = _ctx(spec, W, P, dtau, 91, "fp64", n_burn=4)
+    assert np.array_equal(ctx64.state_arrays()["x"], st["x"])
+    ctx.close()
+    ctx64.close()
