@@ -9,16 +9,15 @@
 // instruction rates: FP64 arithmetic is about 64 times slower than FP32 on
 // this part, and the FP64 version of this kernel is FP64-pipe bound.
 //
-// The series is the same Chebyshev expansion as the FP64 kernel: exp(c + rho t)
-// = e^c [I_0(rho) + 2 sum_k I_k(rho) T_k(t)] on the Gershgorin interval
-// [c - rho, c + rho] of S (bounds formed in FP32 and widened by a relative
-// 1e-5 so they stay bounds), modified Bessel I_k by Miller's backward
-// recurrence in FP64 (one thread, scalar), truncated once the coefficients
-// fall below 1e-18 of e^rho.  The partial sums cancel by about e^(rho - rho_true)
-// when the Gershgorin half-width rho overestimates the spectral one, which
-// multiplies the rounding error; a problem whose rho exceeds RHO_DF (the
-// large workload's S have rho ~ 13) runs the same recurrence in FP64 instead,
-// so the result stays within ~1e-9 relative of exp(S) Phi0 either way.
+// The series is the Chebyshev expansion exp(c + rho t) = e^c [I_0(rho) +
+// 2 sum_k I_k(rho) T_k(t)] on an interval [c - rho, c + rho] holding the
+// spectrum of S, modified Bessel I_k by Miller's backward recurrence in FP64
+// (one thread, scalar), truncated once the coefficients fall below 1e-18 of
+// e^rho.  The partial sums cancel by about e^(rho - rho_true) when rho
+// overestimates the spectral half-width, which multiplies the rounding error
+// and the number of terms; the Gershgorin half-width of the sampled S is
+// 3 to 4 times the spectral one.  So the interval comes from a short Lanczos
+// run, checked a posteriori (see chebyshev_expm_df_kernel).
 #include "kernels.cuh"
 
 namespace afq {
@@ -56,8 +55,66 @@ __device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a
 
 constexpr int CHEB_DF_MAX = 320;
 constexpr double RHO_DF = 6.5;   // largest Gershgorin half-width run in double-float
+constexpr int LZ_STEPS = 12;     // Lanczos steps of the spectral estimate
+constexpr int LZ_NMAX = 256;
 
-template <bool S_SMEM>
+// Sum over the block (256 threads); every thread gets the result.
+__device__ __forceinline__ float block_sum_f(float v, float* red8) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    __syncthreads();   // red8 may still be read from the previous call
+    if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red8[w];
+    return t;
+}
+
+// Chebyshev coefficients of exp on [c - rho, c + rho] (Miller's backward
+// recurrence for I_k(rho), normalised by sum = e^rho), scaled by e^(c + rho);
+// returns the number of terms m.  One thread.
+__device__ int cheb_coefs(double c, double rho, double* coef, int* status) {
+    int start = (int)ceil(rho) + 48;
+    if (!isfinite(rho) || start > CHEB_DF_MAX) {
+        atomicOr(status, STATUS_NONFINITE);
+        start = CHEB_DF_MAX;
+    }
+    const double r2 = 2.0 / rho;
+    double ip1 = 0.0, ik = 1e-280;
+    for (int k = start; k >= 1; --k) {
+        coef[k] = ik;
+        const double im1 = fma((double)k * r2, ik, ip1);
+        ip1 = ik;
+        ik = im1;
+        if (ik > 1e250) {   // rescale everything computed so far
+            for (int j = k; j <= start; ++j) coef[j] *= 1e-250;
+            ip1 *= 1e-250;
+            ik *= 1e-250;
+        }
+    }
+    coef[0] = ik;
+    double norm = coef[0];
+    for (int k = 1; k <= start; ++k) norm += 2.0 * coef[k];   // = e^rho in Miller's units
+    int m = start;
+    for (int k = 1; k <= start; ++k) {
+        if (coef[k] < 1e-18 * norm) { m = k; break; }
+    }
+    const double scale = exp(c + rho) / norm;
+    coef[0] *= scale;
+    for (int k = 1; k <= m; ++k) coef[k] *= 2.0 * scale;
+    return m;
+}
+
+// Interval of the expansion: first an estimate from LZ_STEPS Lanczos steps on S
+// (FP32; the Gershgorin disks of the Lanczos tridiagonal, which includes the
+// last residual, widened by 2 %, intersected with those of S), which is near
+// the spectral interval where the Gershgorin one of S can be several times
+// wider.  Estimates are not bounds, so the recurrence checks that the
+// Chebyshev vectors do not grow (|T_k(t)| <= 1 on the spectrum keeps
+// ||V_k||_F <= ||Phi0||_F); if they do, the problem is done again on the
+// Gershgorin interval of S, in double-float if its half-width is at most
+// RHO_DF and in FP64 otherwise.
 __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, long long problems,
                                                                 const double* __restrict__ S_all,
                                                                 const double* __restrict__ Phi0, double* __restrict__ Out,
@@ -65,29 +122,29 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
     extern __shared__ dfl smf[];
     __shared__ double coef[CHEB_DF_MAX + 2];
     __shared__ dfl coefd[CHEB_DF_MAX + 2];
-    __shared__ float red_lo[256], red_hi[256];
-    __shared__ int nterms, use_df;
+    __shared__ float red_lo[256], red_hi[256], red8[8];
+    __shared__ float lz_v[3][LZ_NMAX], lz_a[LZ_STEPS], lz_b[LZ_STEPS];
+    __shared__ int nterms, mode;
     __shared__ dfl cshift_d, irho_d;
-    __shared__ double cshift, irho;
+    __shared__ double cshift, irho, gers_c, gers_rho, est_c, est_rho;
     const long long prob = blockIdx.x;
     if (alive && !alive[prob / P]) return;
     const double* Sg = S_all + prob * (long long)N * N;
-    dfl* S = S_SMEM ? smf : nullptr;
-    dfl* Vp = S_SMEM ? smf + (size_t)N * N : smf;
+    dfl* S = smf;
+    dfl* Vp = smf + (size_t)N * N;
     dfl* Vc = Vp + (size_t)N * nu;
     dfl* acc = Vc + (size_t)N * nu;
-    dfl* Sd = reinterpret_cast<dfl*>(const_cast<double*>(Sg));   // in place when S is not in shared memory
     const int tid = threadIdx.x, nth = blockDim.x;
-    // Gershgorin interval in FP32 (row sums of |S_ij|), S to double-float
+    const int nn = N * nu;
+    // S to double-float; Gershgorin interval of S in FP32 (widened so it stays a bound)
+    for (int e = tid; e < N * N; e += nth) S[e] = df_from(Sg[e]);
+    __syncthreads();
     float lo = INFINITY, hi = -INFINITY;
     for (int i = tid; i < N; i += nth) {
-        float r = 0.f, dgi = 0.f;
-        for (int j = 0; j < N; ++j) {
-            const double x = Sg[(long long)i * N + j];
-            const float xf = __double2float_rn(x);
-            if (j == i) dgi = xf;
-            else r += fabsf(xf);
-        }
+        float r = 0.f;
+        const float dgi = S[(size_t)i * N + i].hi;
+        for (int j = 0; j < N; ++j)
+            if (j != i) r += fabsf(S[(size_t)i * N + j].hi);
         const float slack = 1e-5f * (r + fabsf(dgi)) + 1e-30f;
         lo = fminf(lo, dgi - r - slack);
         hi = fmaxf(hi, dgi + r + slack);
@@ -102,163 +159,193 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
         }
         __syncthreads();
     }
-    if (tid == 0) {
-        const double c = 0.5 * ((double)red_lo[0] + (double)red_hi[0]);
-        const double rho = fmax(0.5 * ((double)red_hi[0] - (double)red_lo[0]), 1e-3);
-        int start = (int)ceil(rho) + 48;
-        if (!isfinite(rho) || start > CHEB_DF_MAX) {
-            atomicOr(status, STATUS_NONFINITE);
-            start = CHEB_DF_MAX;
+    const float g_lo = red_lo[0], g_hi = red_hi[0];
+    // Lanczos on S from a fixed start vector
+    for (int i = tid; i < N; i += nth) {
+        lz_v[0][i] = 0.f;
+        lz_v[1][i] = 1.f + 0.5f * __sinf(1.3f * (float)i + 0.7f);
+    }
+    float nrm = 0.f;
+    for (int i = tid; i < N; i += nth) nrm += lz_v[1][i] * lz_v[1][i];
+    nrm = block_sum_f(nrm, red8);
+    for (int i = tid; i < N; i += nth) lz_v[1][i] *= rsqrtf(nrm);
+    int ksteps = 0;
+    float beta_prev = 0.f;
+    for (int j = 0; j < LZ_STEPS && j < N; ++j) {
+        __syncthreads();
+        float part = 0.f;
+        for (int i = tid; i < N; i += nth) {
+            float wsum = 0.f;
+            for (int q = 0; q < N; ++q) wsum = fmaf(S[(size_t)i * N + q].hi, lz_v[1][q], wsum);
+            lz_v[2][i] = wsum;
+            part = fmaf(wsum, lz_v[1][i], part);
         }
-        // Miller: I_{k-1} = (2k / rho) I_k + I_{k+1}, started at order `start` with I = 0, 1.
-        const double r2 = 2.0 / rho;
-        double ip1 = 0.0, ik = 1e-280;
-        for (int k = start; k >= 1; --k) {
-            coef[k] = ik;
-            const double im1 = fma((double)k * r2, ik, ip1);
-            ip1 = ik;
-            ik = im1;
-            if (ik > 1e250) {   // rescale everything computed so far
-                for (int j = k; j <= start; ++j) coef[j] *= 1e-250;
-                ip1 *= 1e-250;
-                ik *= 1e-250;
-            }
+        const float alpha = block_sum_f(part, red8);
+        float part2 = 0.f;
+        for (int i = tid; i < N; i += nth) {
+            const float wv = lz_v[2][i] - alpha * lz_v[1][i] - beta_prev * lz_v[0][i];
+            lz_v[2][i] = wv;
+            part2 = fmaf(wv, wv, part2);
         }
-        coef[0] = ik;
-        double norm = coef[0];
-        for (int k = 1; k <= start; ++k) norm += 2.0 * coef[k];   // = e^rho in Miller's units
-        int m = start;
-        for (int k = 1; k <= start; ++k) {
-            if (coef[k] < 1e-18 * norm) { m = k; break; }
+        const float beta = sqrtf(block_sum_f(part2, red8));
+        if (tid == 0) { lz_a[j] = alpha; lz_b[j] = beta; }
+        ksteps = j + 1;
+        if (!(beta > 1e-6f * (fabsf(alpha) + 1e-30f))) break;   // invariant subspace found
+        const float ib = 1.f / beta;
+        for (int i = tid; i < N; i += nth) {
+            lz_v[0][i] = lz_v[1][i];
+            lz_v[1][i] = lz_v[2][i] * ib;
         }
-        const double scale = exp(c + rho) / norm;
-        coef[0] *= scale;
-        for (int k = 1; k <= m; ++k) coef[k] *= 2.0 * scale;
-        for (int k = 0; k <= m; ++k) coefd[k] = df_from(coef[k]);
-        nterms = m;
-        cshift = c;
-        irho = 1.0 / rho;
-        cshift_d = df_from(c);
-        irho_d = df_from(1.0 / rho);
-        use_df = rho <= RHO_DF;
+        beta_prev = beta;
     }
     __syncthreads();
-    const int m = nterms;
-    const int nn = N * nu;
-    if (!use_df) {
-        // FP64 recurrence (same storage: 8 bytes per element)
-        double* S64 = S_SMEM ? reinterpret_cast<double*>(smf) : nullptr;
-        double* Vp64 = reinterpret_cast<double*>(Vp);
-        double* Vc64 = reinterpret_cast<double*>(Vc);
-        double* acc64 = reinterpret_cast<double*>(acc);
-        if (S_SMEM)
-            for (int e = tid; e < N * N; e += nth) S64[e] = Sg[e];
-        __syncthreads();
-        const double* Sr = S_SMEM ? S64 : Sg;
-        const double c = cshift, ir = irho;
-        for (int e = tid; e < nn; e += nth) {
-            Vp64[e] = Phi0[e];
-            acc64[e] = coef[0] * Phi0[e];
+    if (tid == 0) {
+        float tl = INFINITY, th = -INFINITY;
+        for (int j = 0; j < ksteps; ++j) {
+            const float r = (j > 0 ? fabsf(lz_b[j - 1]) : 0.f) + fabsf(lz_b[j]);
+            tl = fminf(tl, lz_a[j] - r);
+            th = fmaxf(th, lz_a[j] + r);
+        }
+        const float margin = 0.02f * (th - tl) + 1e-6f;
+        const double elo = fmax((double)g_lo, (double)(tl - margin)), ehi = fmin((double)g_hi, (double)(th + margin));
+        gers_c = 0.5 * ((double)g_lo + (double)g_hi);
+        gers_rho = fmax(0.5 * ((double)g_hi - (double)g_lo), 1e-3);
+        if (ehi > elo && isfinite(elo) && isfinite(ehi)) {
+            est_c = 0.5 * (elo + ehi);
+            est_rho = fmax(0.5 * (ehi - elo), 1e-3);
+        } else {
+            est_c = gers_c;
+            est_rho = gers_rho;
+        }
+    }
+    float phi_ss = 0.f;   // ||Phi0||_F^2
+    for (int e = tid; e < nn; e += nth) phi_ss = fmaf((float)Phi0[e], (float)Phi0[e], phi_ss);
+    phi_ss = block_sum_f(phi_ss, red8);
+    const float grow_limit = 1.5625f * phi_ss + 1e-30f;   // ||V_k||_F <= 1.25 ||Phi0||_F
+
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (tid == 0) {
+            const double c = attempt == 0 ? est_c : gers_c, rho = attempt == 0 ? est_rho : gers_rho;
+            const int m = cheb_coefs(c, rho, coef, status);
+            for (int k = 0; k <= m; ++k) coefd[k] = df_from(coef[k]);
+            nterms = m;
+            cshift = c;
+            irho = 1.0 / rho;
+            cshift_d = df_from(c);
+            irho_d = df_from(1.0 / rho);
+            // 0 double-float with the growth check, 1 double-float, 2 FP64
+            mode = attempt == 0 ? 0 : (rho <= RHO_DF ? 1 : 2);
         }
         __syncthreads();
-        for (int k = 1; k <= m; ++k) {
-            const double* Vsrc = k == 1 ? Vp64 : Vc64;
+        const int m = nterms;
+        if (mode == 2) {
+            // FP64 recurrence; S, V and the sum in FP64 (8 bytes per element, same storage)
+            double* S64 = reinterpret_cast<double*>(smf);
+            double* Vp64 = reinterpret_cast<double*>(Vp);
+            double* Vc64 = reinterpret_cast<double*>(Vc);
+            double* acc64 = reinterpret_cast<double*>(acc);
+            for (int e = tid; e < N * N; e += nth) S64[e] = Sg[e];
+            __syncthreads();
+            const double c = cshift, ir = irho;
             for (int e = tid; e < nn; e += nth) {
-                const int i = e / nu, a = e - i * nu;
-                double sum = 0.0;
-                for (int j = 0; j < N; ++j) sum = fma(Sr[(long long)i * N + j], Vsrc[j * nu + a], sum);
-                sum = (sum - c * Vsrc[e]) * ir;
-                if (k == 1) {
-                    Vc64[e] = sum;
-                    acc64[e] = fma(coef[1], sum, acc64[e]);
-                } else {
-                    const double v = 2.0 * sum - Vp64[e];
-                    Vp64[e] = v;
-                    acc64[e] = fma(coef[k], v, acc64[e]);
-                }
+                Vp64[e] = Phi0[e];
+                acc64[e] = coef[0] * Phi0[e];
             }
             __syncthreads();
-            if (k >= 2) { double* t = Vp64; Vp64 = Vc64; Vc64 = t; }
+            for (int k = 1; k <= m; ++k) {
+                const double* Vsrc = k == 1 ? Vp64 : Vc64;
+                for (int e = tid; e < nn; e += nth) {
+                    const int i = e / nu, a = e - i * nu;
+                    double sum = 0.0;
+                    for (int j = 0; j < N; ++j) sum = fma(S64[(size_t)i * N + j], Vsrc[j * nu + a], sum);
+                    sum = (sum - c * Vsrc[e]) * ir;
+                    if (k == 1) {
+                        Vc64[e] = sum;
+                        acc64[e] = fma(coef[1], sum, acc64[e]);
+                    } else {
+                        const double v = 2.0 * sum - Vp64[e];
+                        Vp64[e] = v;
+                        acc64[e] = fma(coef[k], v, acc64[e]);
+                    }
+                }
+                __syncthreads();
+                if (k >= 2) { double* t = Vp64; Vp64 = Vc64; Vc64 = t; }
+            }
+            double* o = Out + prob * (long long)nn;
+            for (int e = tid; e < nn; e += nth) o[e] = acc64[e];
+            return;
         }
-        double* o = Out + prob * (long long)nn;
-        for (int e = tid; e < nn; e += nth) o[e] = acc64[e];
-        return;
-    }
-    if (S_SMEM) {
-        for (int e = tid; e < N * N; e += nth) S[e] = df_from(Sg[e]);
-    } else {
-        // convert in place: each element is read and written by the same thread
-        for (int e = tid; e < N * N; e += nth) Sd[e] = df_from(Sg[e]);
-    }
-    __syncthreads();
-    const dfl* Sr = S_SMEM ? S : Sd;
-    const dfl cs = cshift_d, ir = irho_d;
-    // t V for one element: ((S V)_e - c V_e) / rho, the product by Dot2
-    auto tv = [&](const dfl* V, int e) -> dfl {
-        const int i = e / nu, a = e - i * nu;
-        const dfl* Srow = Sr + (size_t)i * N;
-        float s = 0.f, cc = 0.f;
-        for (int j = 0; j < N; ++j) {
-            const dfl x = Srow[j], y = V[(size_t)j * nu + a];
-            const float p = x.hi * y.hi;
-            float q = fmaf(x.hi, y.hi, -p);
-            q = fmaf(x.hi, y.lo, q);
-            q = fmaf(x.lo, y.hi, q);
-            const float t = s + p, z = t - s;
-            cc += q + ((s - (t - z)) + (p - z));
-            s = t;
-        }
-        const dfl sv = df_two_sum(s, cc);
-        return df_mul(df_add(sv, df_neg(df_mul(cs, V[e]))), ir);
-    };
-    for (int e = tid; e < nn; e += nth) {
-        const dfl f = df_from(Phi0[e]);
-        Vp[e] = f;
-        acc[e] = df_mul(coefd[0], f);
-    }
-    __syncthreads();
-    for (int e = tid; e < nn; e += nth) {
-        const dfl s = tv(Vp, e);
-        Vc[e] = s;
-        acc[e] = df_add(acc[e], df_mul(coefd[1], s));
-    }
-    __syncthreads();
-    for (int k = 2; k <= m; ++k) {
-        // V_k = 2 t V_{k-1} - V_{k-2}, written over V_{k-2} element by element
+        const dfl cs = cshift_d, ir = irho_d;
+        const bool check = mode == 0;
+        // t V for one element: ((S V)_e - c V_e) / rho, the product by Dot2
+        auto tv = [&](const dfl* V, int e) -> dfl {
+            const int i = e / nu, a = e - i * nu;
+            const dfl* Srow = S + (size_t)i * N;
+            float s = 0.f, cc = 0.f;
+            for (int j = 0; j < N; ++j) {
+                const dfl x = Srow[j], y = V[(size_t)j * nu + a];
+                const float p = x.hi * y.hi;
+                float q = fmaf(x.hi, y.hi, -p);
+                q = fmaf(x.hi, y.lo, q);
+                q = fmaf(x.lo, y.hi, q);
+                const float t = s + p, z = t - s;
+                cc += q + ((s - (t - z)) + (p - z));
+                s = t;
+            }
+            const dfl sv = df_two_sum(s, cc);
+            return df_mul(df_add(sv, df_neg(df_mul(cs, V[e]))), ir);
+        };
         for (int e = tid; e < nn; e += nth) {
-            const dfl s = tv(Vc, e);
-            const dfl v = df_add(dfl{2.f * s.hi, 2.f * s.lo}, df_neg(Vp[e]));
-            Vp[e] = v;
-            acc[e] = df_add(acc[e], df_mul(coefd[k], v));
+            const dfl f = df_from(Phi0[e]);
+            Vp[e] = f;
+            acc[e] = df_mul(coefd[0], f);
         }
         __syncthreads();
-        dfl* t = Vp; Vp = Vc; Vc = t;
+        float ss = 0.f;
+        for (int e = tid; e < nn; e += nth) {
+            const dfl sv = tv(Vp, e);
+            Vc[e] = sv;
+            acc[e] = df_add(acc[e], df_mul(coefd[1], sv));
+            ss = fmaf(sv.hi, sv.hi, ss);
+        }
+        bool grew = check && block_sum_f(ss, red8) > grow_limit;
+        for (int k = 2; k <= m && !grew; ++k) {
+            // V_k = 2 t V_{k-1} - V_{k-2}, written over V_{k-2} element by element
+            __syncthreads();
+            ss = 0.f;
+            for (int e = tid; e < nn; e += nth) {
+                const dfl sv = tv(Vc, e);
+                const dfl v = df_add(dfl{2.f * sv.hi, 2.f * sv.lo}, df_neg(Vp[e]));
+                Vp[e] = v;
+                acc[e] = df_add(acc[e], df_mul(coefd[k], v));
+                ss = fmaf(v.hi, v.hi, ss);
+            }
+            if (check) grew = block_sum_f(ss, red8) > grow_limit;   // uniform across the block
+            else __syncthreads();
+            dfl* t = Vp; Vp = Vc; Vc = t;
+        }
+        if (grew) {           // the estimate missed part of the spectrum: start again
+            __syncthreads();
+            continue;
+        }
+        __syncthreads();
+        double* o = Out + prob * (long long)nn;
+        for (int e = tid; e < nn; e += nth) o[e] = df_to(acc[e]);
+        return;
     }
-    double* o = Out + prob * (long long)nn;
-    for (int e = tid; e < nn; e += nth) o[e] = df_to(acc[e]);
 }
 
-// Same contract as trial_orbitals; S_all is overwritten (converted in place)
-// when S does not fit in shared memory.
+// Same contract as trial_orbitals (S_all is only read).
 cudaError_t trial_orbitals_df(cudaStream_t s, int N, int nu, long long problems, double* S_all, const double* Phi0,
                               double* Out, const int* alive, int P, int* status, int threads) {
     if (problems <= 0) return cudaSuccess;
-    if (threads != 128 && threads != 256) threads = 256;
-    const size_t vec = 3 * (size_t)N * nu * sizeof(dfl);
-    const size_t full = vec + (size_t)N * N * sizeof(dfl);
-    cudaError_t e;
-    if (full <= 200 * 1024) {
-        e = raise_smem_limit((const void*)chebyshev_expm_df_kernel<true>, full);
-        if (e != cudaSuccess) return e;
-        chebyshev_expm_df_kernel<true><<<(unsigned)problems, threads, full, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P,
-                                                                                 status); count_launches(1);
-    } else {
-        if (vec > 200 * 1024) return cudaErrorInvalidValue;
-        e = raise_smem_limit((const void*)chebyshev_expm_df_kernel<false>, vec);
-        if (e != cudaSuccess) return e;
-        chebyshev_expm_df_kernel<false><<<(unsigned)problems, threads, vec, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P,
-                                                                                 status); count_launches(1);
-    }
+    const size_t bytes = (3 * (size_t)N * nu + (size_t)N * N) * sizeof(dfl);
+    if (bytes > 200 * 1024 || N > LZ_NMAX)   // S does not fit in shared memory: the FP64 kernel
+        return trial_orbitals(s, N, nu, problems, S_all, Phi0, Out, alive, P, status, threads);
+    cudaError_t e = raise_smem_limit((const void*)chebyshev_expm_df_kernel, bytes);
+    if (e != cudaSuccess) return e;
+    chebyshev_expm_df_kernel<<<(unsigned)problems, 256, bytes, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status);
+    count_launches(1);
     return cudaGetLastError();
 }
 
