@@ -75,7 +75,7 @@ void gemm_nn_f64(cudaStream_t s, int M, int Nc, int K, double alpha, const doubl
 //                  Phi_s^T X Theta_s = A B_s^T X phi_s A^-1 has the same traces);
 //   OVL_INVERSE (2): A^-1 itself, at offset (spin ? nu^2 : 0) of the pair's block.
 // Dynamic shared memory per warp: n*n double2 (A), n*n double2 (A^-1) when
-// Theta is requested, n ints (row permutation).
+// Theta is requested, n double2 (pivot reciprocals), n ints (row permutation).
 __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int spin, long long pairs, int P,
                                   const double* __restrict__ Phi, long long Phi_stride,
                                   const double2* __restrict__ phi, double2* __restrict__ logdet,
@@ -89,9 +89,10 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
     long long w = pair / P;
     if (alive && !alive[w]) return;
     size_t per_warp = (size_t)n * n * (Theta ? 2 : 1);
-    double2* A = sm + warp * (per_warp + (n + 1) / 2 + 1);
+    double2* A = sm + warp * (per_warp + n + (n + 1) / 2 + 1);
     double2* Ainv = A + (size_t)n * n;
-    int* perm = reinterpret_cast<int*>(A + per_warp);
+    double2* dinv = A + per_warp;                       // 1 / u_kk
+    int* perm = reinterpret_cast<int*>(dinv + n);
     const double* Ph = Phi + pair * Phi_stride;         // N x nu, spin uses the first n columns
     const double2* ph = phi + w * (long long)N * nt + col0;  // N x nt
     if (n == 0) {
@@ -111,8 +112,12 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
     }
     for (int r = lane; r < n; r += 32) perm[r] = r;
     __syncwarp();
-    double logabs = 0.0;
-    double2 phase = cmk(1.0, 0.0);
+    // The product of the pivots is carried as z * 2^zexp (z rescaled by an exact
+    // power of two after every pivot), so log|det| and arg det need one log and
+    // one atan2 in all: scalar FP64 work occupies a whole warp instruction.
+    double2 z = cmk(1.0, 0.0);
+    int zexp = 0;
+    bool odd = false;   // odd number of row swaps
     bool singular = false;
     for (int k = 0; k < n; ++k) {
         double best = -1.0;
@@ -137,14 +142,23 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
                 A[bi * n + c] = t;
             }
             if (lane == 0) { int t = perm[k]; perm[k] = perm[bi]; perm[bi] = t; }
-            phase = cmk(-phase.x, -phase.y);
+            odd = !odd;
         }
         __syncwarp();
-        double2 piv = A[k * n + k];
-        double ap = cabs_(piv);
-        logabs += log(ap);
-        phase = cmul(phase, cmk(piv.x / ap, piv.y / ap));
-        for (int r = k + 1 + lane; r < n; r += 32) A[r * n + k] = cdiv(A[r * n + k], piv);
+        const double2 piv = A[k * n + k];
+        const double q = 1.0 / fma(piv.x, piv.x, piv.y * piv.y);
+        const double2 rinv = cmk(piv.x * q, -piv.y * q);   // 1 / piv
+        if (lane == 0) dinv[k] = rinv;
+        z = cmul(z, piv);
+        {
+            const double mz = fmax(fabs(z.x), fabs(z.y));
+            int ex = (int)((__double_as_longlong(mz) >> 52) & 0x7FF) - 1023;
+            ex = max(-1000, min(1000, ex));
+            const double f = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex, exact
+            z = cmk(z.x * f, z.y * f);
+            zexp += ex;
+        }
+        for (int r = k + 1 + lane; r < n; r += 32) A[r * n + k] = cmul(A[r * n + k], rinv);
         __syncwarp();
         int m = n - k - 1;
         for (int e = lane; e < m * m; e += 32) {
@@ -171,7 +185,10 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
         }
         return;
     }
-    if (lane == 0) logdet[pair * 2 + spin] = cmk(logabs, atan2(phase.y, phase.x));
+    if (lane == 0) {
+        const double logabs = 0.5 * log(fma(z.x, z.x, z.y * z.y)) + zexp * 0.69314718055994530942;
+        logdet[pair * 2 + spin] = odd ? cmk(logabs, atan2(-z.y, -z.x)) : cmk(logabs, atan2(z.y, z.x));
+    }
     if (!Theta) return;
     // A^-1 column c: solve L y = P e_c (unit lower), then U x = y.
     for (int c = lane; c < n; c += 32) {
@@ -191,7 +208,7 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
                 s.x -= u.x * xj.x - u.y * xj.y;
                 s.y -= u.x * xj.y + u.y * xj.x;
             }
-            Ainv[r * n + c] = cdiv(s, A[r * n + r]);
+            Ainv[r * n + c] = cmul(s, dinv[r]);
         }
     }
     __syncwarp();
@@ -227,7 +244,7 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
 }
 
 static size_t overlap_smem_per_warp(int n, bool theta) {
-    return ((size_t)n * n * (theta ? 2 : 1) + (n + 1) / 2 + 1) * sizeof(double2);
+    return ((size_t)n * n * (theta ? 2 : 1) + n + (n + 1) / 2 + 1) * sizeof(double2);
 }
 
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
