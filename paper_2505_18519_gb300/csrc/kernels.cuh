@@ -16,8 +16,15 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
                        long long pairs, int P, int trial_side = OVL_THETA);
 cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, double2* dst, const int* alive,
                              int* status, int n_walkers);
+// Phi = exp(S) Phi0 for `problems` symmetric S (FP64).  trial_orbitals runs the
+// Chebyshev series on a Lanczos-estimated spectral interval with an a-posteriori
+// check (trial_df.cu); trial_orbitals_gershgorin on the Gershgorin interval of S
+// (linalg_fp64.cu), also the fallback when S does not fit in shared memory.
 cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,
                            double* Out, const int* alive, int P, int* status, int threads = 256);
+cudaError_t trial_orbitals_gershgorin(cudaStream_t s, int N, int nu, long long problems, const double* S_all,
+                                      const double* Phi0, double* Out, const int* alive, int P, int* status,
+                                      int threads = 256);
 // trial_df.cu: the same in double-float arithmetic (mixed-precision path); S_all
 // is scratch (converted in place when S does not fit in shared memory)
 cudaError_t trial_orbitals_df(cudaStream_t s, int N, int nu, long long problems, double* S_all, const double* Phi0,

@@ -445,8 +445,8 @@ __global__ void __launch_bounds__(256) chebyshev_expm_kernel(int N, int nu, long
     for (int e = tid; e < nn; e += nth) o[e] = acc[e];
 }
 
-cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,
-                           double* Out, const int* alive, int P, int* status, int threads) {
+cudaError_t trial_orbitals_gershgorin(cudaStream_t s, int N, int nu, long long problems, const double* S_all,
+                                      const double* Phi0, double* Out, const int* alive, int P, int* status, int threads) {
     if (problems <= 0) return cudaSuccess;
     if (threads != 128 && threads != 256) threads = 256;
     size_t vec = 3 * (size_t)N * nu * sizeof(double);

@@ -118,7 +118,8 @@ __device__ int cheb_coefs(double c, double rho, double* coef, int* status) {
 __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, long long problems,
                                                                 const double* __restrict__ S_all,
                                                                 const double* __restrict__ Phi0, double* __restrict__ Out,
-                                                                const int* __restrict__ alive, int P, int* status) {
+                                                                const int* __restrict__ alive, int P, int* status,
+                                                                int allow_df) {
     extern __shared__ dfl smf[];
     __shared__ double coef[CHEB_DF_MAX + 2];
     __shared__ dfl coefd[CHEB_DF_MAX + 2];
@@ -233,13 +234,16 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
             irho = 1.0 / rho;
             cshift_d = df_from(c);
             irho_d = df_from(1.0 / rho);
-            // 0 double-float with the growth check, 1 double-float, 2 FP64
-            mode = attempt == 0 ? 0 : (rho <= RHO_DF ? 1 : 2);
+            // 0 double-float with the growth check, 1 double-float, 2 FP64 with the
+            // growth check, 3 FP64
+            if (allow_df) mode = attempt == 0 ? 0 : (rho <= RHO_DF ? 1 : 3);
+            else mode = attempt == 0 ? 2 : 3;
         }
         __syncthreads();
         const int m = nterms;
-        if (mode == 2) {
+        if (mode >= 2) {
             // FP64 recurrence; S, V and the sum in FP64 (8 bytes per element, same storage)
+            const bool check64 = mode == 2;
             double* S64 = reinterpret_cast<double*>(smf);
             double* Vp64 = reinterpret_cast<double*>(Vp);
             double* Vc64 = reinterpret_cast<double*>(Vc);
@@ -252,25 +256,38 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
                 acc64[e] = coef[0] * Phi0[e];
             }
             __syncthreads();
-            for (int k = 1; k <= m; ++k) {
+            bool grew64 = false;
+            for (int k = 1; k <= m && !grew64; ++k) {
                 const double* Vsrc = k == 1 ? Vp64 : Vc64;
+                float ss64 = 0.f;
                 for (int e = tid; e < nn; e += nth) {
                     const int i = e / nu, a = e - i * nu;
                     double sum = 0.0;
                     for (int j = 0; j < N; ++j) sum = fma(S64[(size_t)i * N + j], Vsrc[j * nu + a], sum);
                     sum = (sum - c * Vsrc[e]) * ir;
+                    double v;
                     if (k == 1) {
-                        Vc64[e] = sum;
-                        acc64[e] = fma(coef[1], sum, acc64[e]);
+                        v = sum;
+                        Vc64[e] = v;
                     } else {
-                        const double v = 2.0 * sum - Vp64[e];
+                        v = 2.0 * sum - Vp64[e];
                         Vp64[e] = v;
-                        acc64[e] = fma(coef[k], v, acc64[e]);
+                    }
+                    acc64[e] = fma(coef[k], v, acc64[e]);
+                    if (check64) {
+                        const float vf = __double2float_rn(v);
+                        ss64 = fmaf(vf, vf, ss64);
                     }
                 }
-                __syncthreads();
+                if (check64) grew64 = block_sum_f(ss64, red8) > grow_limit;   // uniform across the block
+                else __syncthreads();
                 if (k >= 2) { double* t = Vp64; Vp64 = Vc64; Vc64 = t; }
             }
+            if (grew64) {       // the estimate missed part of the spectrum: start again
+                __syncthreads();
+                continue;
+            }
+            __syncthreads();
             double* o = Out + prob * (long long)nn;
             for (int e = tid; e < nn; e += nth) o[e] = acc64[e];
             return;
@@ -336,17 +353,30 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
 }
 
 // Same contract as trial_orbitals (S_all is only read).
-cudaError_t trial_orbitals_df(cudaStream_t s, int N, int nu, long long problems, double* S_all, const double* Phi0,
-                              double* Out, const int* alive, int P, int* status, int threads) {
+static cudaError_t trial_orbitals_lanczos(cudaStream_t s, int N, int nu, long long problems, double* S_all,
+                                          const double* Phi0, double* Out, const int* alive, int P, int* status,
+                                          int threads, bool allow_df) {
     if (problems <= 0) return cudaSuccess;
     const size_t bytes = (3 * (size_t)N * nu + (size_t)N * N) * sizeof(dfl);
-    if (bytes > 200 * 1024 || N > LZ_NMAX)   // S does not fit in shared memory: the FP64 kernel
-        return trial_orbitals(s, N, nu, problems, S_all, Phi0, Out, alive, P, status, threads);
+    if (bytes > 200 * 1024 || N > LZ_NMAX)   // S does not fit in shared memory: the Gershgorin FP64 kernel
+        return trial_orbitals_gershgorin(s, N, nu, problems, S_all, Phi0, Out, alive, P, status, threads);
     cudaError_t e = raise_smem_limit((const void*)chebyshev_expm_df_kernel, bytes);
     if (e != cudaSuccess) return e;
-    chebyshev_expm_df_kernel<<<(unsigned)problems, 256, bytes, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status);
+    chebyshev_expm_df_kernel<<<(unsigned)problems, 256, bytes, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status,
+                                                                   allow_df ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t trial_orbitals_df(cudaStream_t s, int N, int nu, long long problems, double* S_all, const double* Phi0,
+                              double* Out, const int* alive, int P, int* status, int threads) {
+    return trial_orbitals_lanczos(s, N, nu, problems, S_all, Phi0, Out, alive, P, status, threads, true);
+}
+
+cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,
+                           double* Out, const int* alive, int P, int* status, int threads) {
+    return trial_orbitals_lanczos(s, N, nu, problems, const_cast<double*>(S_all), Phi0, Out, alive, P, status, threads,
+                                  false);
 }
 
 }  // namespace afq
