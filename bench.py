@@ -306,6 +306,23 @@ def tensor_roofline(spec, W, P, prof, kernel):
                     "real product and pads N and n to MMA tile sizes"}
 
 
+def tau_int(series):
+    """Integrated autocorrelation time of a series, Sokal's self-consistent window (c = 5)."""
+    import numpy as np
+    x = np.asarray(series, dtype=np.float64)
+    x = x - x.mean()
+    n = x.size
+    var = float(np.dot(x, x)) / n
+    if var == 0.0:
+        return 1.0
+    tau = 1.0
+    for t in range(1, n // 2):
+        tau += 2.0 * float(np.dot(x[:-t], x[t:])) / (n * var)
+        if t >= 5 * tau:
+            break
+    return max(tau, 1.0)
+
+
 def _emix(hist):
     import numpy as np
     return np.where(hist[:, 1] > 0, hist[:, 0] / np.where(hist[:, 1] > 0, hist[:, 1], 1.0), np.nan)
@@ -363,8 +380,34 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         ms, clocks, launches = _timed(ctx.step, lambda: torch.cuda.synchronize(dev), ctx.stream, steps, world, local)
         prof = ctx.profile_read()
         hist = ctx.history(steps)
+        theta = ctx.mlp_params()
         ctx.close()
         acc = float(hist[:, 3].sum() / (steps * W * P))
+        # mixing: the trained network frozen against the prior proposal, from one common
+        # state, on a block of walkers: acceptance and integrated autocorrelation time of
+        # every path's first hidden variable (Sokal window), averaged over paths
+        Wt, T = min(64, W), 40
+        mixing, start = {}, None
+        for prop in ("prior", "mlp"):
+            c = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, Wt, P, run.dtau, seed, n_burn=20,
+                                walker_offset=rank * Wt, e_shift=28.5, precision="fp16x3", proposal=prop,
+                                mlp_train=False)
+            cx = lib.Context(c, s.h, s.L, s.Phi0, s.U, device=dev)
+            if prop == "mlp":
+                cx.mlp_params(theta)
+            if start is None:
+                start = cx.save_state()
+            else:
+                cx.load_state(start)
+            xs, acc_t = [], []
+            for _ in range(T):
+                cx.step(1)
+                xs.append(cx.state_arrays()["x"][:, :, 0].ravel().copy())
+                acc_t.append(cx.history(1)[0][3] / (Wt * P))
+            cx.close()
+            X = np.array(xs)
+            mixing[prop] = {"acceptance": float(np.mean(acc_t)),
+                            "tau_int_x": float(np.mean([tau_int(X[:, j]) for j in range(X.shape[1])]))}
         d = {"precision": "fp16x3", "proposal": "mlp (K->256->256->2K, BF16 GEMMs, trained online every step)",
              "what": f"same workload; {n_train} untimed training steps, then the timed steps (training continues)",
              "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
@@ -373,6 +416,9 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
              "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
         if hist64 is not None and len(hist64):
             d["acceptance_prior_proposal"] = float(hist64[-steps:, 3].sum() / (min(steps, len(hist64)) * W * P))
+        d["mixing"] = dict(mixing, what=f"{Wt} walkers x {P} paths from one common state, {T} steps each, the "
+                                        "trained network frozen (mlp_mix 0.1) vs the prior proposal; tau_int of each "
+                                        "path's x_1 in steps, averaged over paths")
         out["learned_proposal"] = d
 
     if only in (None, "batched"):

@@ -221,6 +221,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.L = (double*)take(G * NN * 8);
     w.Phi0 = (double*)take(N * nu * 8);
     w.U = (double*)take(K * NN * 8);
+    w.Udf = c->precision != AFQMC_PRECISION_FP64 ? take(K * NN * 8) : nullptr;
     w.T = (double*)take(NN * 8);
     w.expT = (double*)take(NN * 8);
     w.scratchNN = (double*)take(3 * NN * 8);
@@ -317,6 +318,23 @@ static StepParams params_of(const afqmc_config* c) {
     return p;
 }
 
+// The mixed-precision path forms S and the trial orbitals in double-float
+// arithmetic (S stored as double-float pairs) when S fits the trial kernel's
+// shared memory; the FP64 path in FP64.
+static bool s_in_df(const afqmc_ctx* ctx) {
+    return ctx->cfg.precision != AFQMC_PRECISION_FP64 && trial_orbitals_df_supported(ctx->d.N, ctx->d.nu);
+}
+
+// S_m = sum_k X[m, k] U_k into ws.Sprop for `M` rows of X.
+static cudaError_t form_S(afqmc_ctx* ctx, const double* X, long long M) {
+    const Dims& d = ctx->d;
+    Workspace& w = ctx->ws;
+    const long long NN = (long long)d.N * d.N;
+    if (s_in_df(ctx)) return gemm_df(ctx->stream, (int)M, (int)NN, d.K, X, w.Udf, w.Sprop);
+    gemm_nn_f64(ctx->stream, (int)M, (int)NN, d.K, 1.0, X, d.K, w.U, NN, 0.0, w.Sprop, NN);
+    return cudaGetLastError();
+}
+
 // Trial orbitals exp(S) Phi0 for `problems` matrices S in ws.Sprop: FP64 on the
 // FP64 path, double-float arithmetic on the mixed-precision path.
 static cudaError_t trial_orbitals_of(afqmc_ctx* ctx, long long problems, double* Out, const int* alive, int P) {
@@ -324,7 +342,8 @@ static cudaError_t trial_orbitals_of(afqmc_ctx* ctx, long long problems, double*
     Workspace& w = ctx->ws;
     if (ctx->cfg.precision == AFQMC_PRECISION_FP64)
         return trial_orbitals(ctx->stream, d.N, d.nu, problems, w.Sprop, w.Phi0, Out, alive, P, w.status, d.cheb_threads);
-    return trial_orbitals_df(ctx->stream, d.N, d.nu, problems, w.Sprop, w.Phi0, Out, alive, P, w.status, d.cheb_threads);
+    return trial_orbitals_df(ctx->stream, d.N, d.nu, problems, w.Sprop, w.Phi0, Out, alive, P, w.status, d.cheb_threads,
+                             s_in_df(ctx));
 }
 
 // One Metropolis sweep of every path against the walker orbitals `orbitals`
@@ -338,9 +357,7 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
     if (burn_in && p.proposal == AFQMC_PROPOSAL_MLP) p.proposal = AFQMC_PROPOSAL_PRIOR;   // no network output yet
     afqmc_status st;
     CK(propose(s, d, p, w.counters, tag_prop, tag_acc, sweep, w.x, w.alive, w.mlp.mu, w.mlp.logv, w.xprop));
-    gemm_nn_f64(s, (int)d.pairs, d.N * d.N, d.K, 1.0, w.xprop, d.K, w.U, (long long)d.N * d.N, 0.0, w.Sprop,
-                (long long)d.N * d.N);
-    CK(cudaGetLastError());
+    CK(form_S(ctx, w.xprop, d.pairs));
     if ((st = prof_mark(ctx, PH_PROPOSE)) != AFQMC_OK) return st;
     CK(trial_orbitals_of(ctx, d.pairs, w.Phiprop, w.alive, d.P));
     if ((st = prof_mark(ctx, PH_TRIAL)) != AFQMC_OK) return st;
@@ -431,8 +448,11 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         }
         // initial walkers phi_w = Phi(x_w), x_w ~ N(0, I), orthonormalised
         fill_normals(s, w.xprop, d.W, d.K, p.woff, p.seed, TAG_INIT_WALKER, w.counters, 0);
-        gemm_nn_f64(s, d.W, (int)NN, d.K, 1.0, w.xprop, d.K, w.U, NN, 0.0, w.Sprop, NN);
-        if ((e = trial_orbitals_of(ctx, d.W, w.Phiprop, nullptr, 1)) != cudaSuccess) {
+        if (w.Udf && (e = u_to_df(s, (long long)d.K * NN, w.U, w.Udf)) != cudaSuccess) {
+            st = fail(AFQMC_ERR_CUDA, "double-float copy of U: %s", cudaGetErrorString(e));
+            break;
+        }
+        if ((e = form_S(ctx, w.xprop, d.W)) != cudaSuccess || (e = trial_orbitals_of(ctx, d.W, w.Phiprop, nullptr, 1)) != cudaSuccess) {
             st = fail(AFQMC_ERR_CUDA, "initial walkers: %s", cudaGetErrorString(e));
             break;
         }
@@ -440,8 +460,7 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         reorthonormalise(s, d, w.phi_new, w.phi, nullptr, w.status, d.W);
         // paths x_wp ~ N(0, I) and their orbitals
         fill_normals(s, w.x, d.pairs, d.K, p.woff * d.P, p.seed, TAG_INIT_PATH, w.counters, 0);
-        gemm_nn_f64(s, (int)d.pairs, (int)NN, d.K, 1.0, w.x, d.K, w.U, NN, 0.0, w.Sprop, NN);
-        if ((e = trial_orbitals_of(ctx, d.pairs, w.Phi, nullptr, d.P)) != cudaSuccess) {
+        if ((e = form_S(ctx, w.x, d.pairs)) != cudaSuccess || (e = trial_orbitals_of(ctx, d.pairs, w.Phi, nullptr, d.P)) != cudaSuccess) {
             st = fail(AFQMC_ERR_CUDA, "initial paths: %s", cudaGetErrorString(e));
             break;
         }

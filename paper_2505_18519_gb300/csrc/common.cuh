@@ -147,6 +147,7 @@ struct Workspace {
     double* L;        // G*N*N
     double* Phi0;     // N*n_up
     double* U;        // K*N*N
+    void* Udf;        // K*N*N double-float copy of U (mixed-precision path)
     double* T;        // N*N, h - 1/2 sum_g L_g L_g
     double* expT;     // N*N, exp(-tau T / 2)
     double* scratchNN;  // 3*N*N for the matrix exponential at init

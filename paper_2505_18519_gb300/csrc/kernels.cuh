@@ -28,7 +28,13 @@ cudaError_t trial_orbitals_gershgorin(cudaStream_t s, int N, int nu, long long p
 // trial_df.cu: the same in double-float arithmetic (mixed-precision path); S_all
 // is scratch (converted in place when S does not fit in shared memory)
 cudaError_t trial_orbitals_df(cudaStream_t s, int N, int nu, long long problems, double* S_all, const double* Phi0,
-                              double* Out, const int* alive, int P, int* status, int threads = 256);
+                              double* Out, const int* alive, int P, int* status, int threads = 256,
+                              bool s_is_df = false);
+bool trial_orbitals_df_supported(int N, int nu);
+// S = X U in double-float (X FP64 M x K, U as double-float K x Nc from u_to_df);
+// S is written as double-float pairs, 8 bytes per element
+cudaError_t u_to_df(cudaStream_t s, long long n, const double* U, void* Ud);
+cudaError_t gemm_df(cudaStream_t s, int M, int Nc, int K, const double* X, const void* Ud, double* S);
 cudaError_t one_body_propagator(cudaStream_t s, int N, int G, double dtau, const double* h, const double* L, double* T,
                                 double* scratch3, double* expT);
 

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
                                                                 const double* __restrict__ S_all,
                                                                 const double* __restrict__ Phi0, double* __restrict__ Out,
                                                                 const int* __restrict__ alive, int P, int* status,
-                                                                int allow_df) {
+                                                                int allow_df, int s_is_df) {
     extern __shared__ dfl smf[];
     __shared__ double coef[CHEB_DF_MAX + 2];
     __shared__ dfl coefd[CHEB_DF_MAX + 2];
@@ -137,8 +137,10 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
     dfl* acc = Vc + (size_t)N * nu;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int nn = N * nu;
-    // S to double-float; Gershgorin interval of S in FP32 (widened so it stays a bound)
-    for (int e = tid; e < N * N; e += nth) S[e] = df_from(Sg[e]);
+    // S to double-float (or as given, when the caller formed it in double-float);
+    // Gershgorin interval of S in FP32 (widened so it stays a bound)
+    const dfl* Sgd = reinterpret_cast<const dfl*>(Sg);
+    for (int e = tid; e < N * N; e += nth) S[e] = s_is_df ? Sgd[e] : df_from(Sg[e]);
     __syncthreads();
     float lo = INFINITY, hi = -INFINITY;
     for (int i = tid; i < N; i += nth) {
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
             double* Vp64 = reinterpret_cast<double*>(Vp);
             double* Vc64 = reinterpret_cast<double*>(Vc);
             double* acc64 = reinterpret_cast<double*>(acc);
-            for (int e = tid; e < N * N; e += nth) S64[e] = Sg[e];
+            for (int e = tid; e < N * N; e += nth) S64[e] = s_is_df ? df_to(Sgd[e]) : Sg[e];
             __syncthreads();
             const double c = cshift, ir = irho;
             for (int e = tid; e < nn; e += nth) {
@@ -353,30 +355,121 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
 }
 
 // Same contract as trial_orbitals (S_all is only read).
+bool trial_orbitals_df_supported(int N, int nu) {
+    return (3 * (size_t)N * nu + (size_t)N * N) * sizeof(dfl) <= 200 * 1024 && N <= LZ_NMAX;
+}
+
 static cudaError_t trial_orbitals_lanczos(cudaStream_t s, int N, int nu, long long problems, double* S_all,
                                           const double* Phi0, double* Out, const int* alive, int P, int* status,
-                                          int threads, bool allow_df) {
+                                          int threads, bool allow_df, bool s_is_df) {
     if (problems <= 0) return cudaSuccess;
     const size_t bytes = (3 * (size_t)N * nu + (size_t)N * N) * sizeof(dfl);
-    if (bytes > 200 * 1024 || N > LZ_NMAX)   // S does not fit in shared memory: the Gershgorin FP64 kernel
+    if (!trial_orbitals_df_supported(N, nu)) {   // S does not fit in shared memory: the Gershgorin FP64 kernel
+        if (s_is_df) return cudaErrorInvalidValue;
         return trial_orbitals_gershgorin(s, N, nu, problems, S_all, Phi0, Out, alive, P, status, threads);
+    }
     cudaError_t e = raise_smem_limit((const void*)chebyshev_expm_df_kernel, bytes);
     if (e != cudaSuccess) return e;
     chebyshev_expm_df_kernel<<<(unsigned)problems, 256, bytes, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status,
-                                                                   allow_df ? 1 : 0);
+                                                                   allow_df ? 1 : 0, s_is_df ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t trial_orbitals_df(cudaStream_t s, int N, int nu, long long problems, double* S_all, const double* Phi0,
-                              double* Out, const int* alive, int P, int* status, int threads) {
-    return trial_orbitals_lanczos(s, N, nu, problems, S_all, Phi0, Out, alive, P, status, threads, true);
+                              double* Out, const int* alive, int P, int* status, int threads, bool s_is_df) {
+    return trial_orbitals_lanczos(s, N, nu, problems, S_all, Phi0, Out, alive, P, status, threads, true, s_is_df);
 }
 
 cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,
                            double* Out, const int* alive, int P, int* status, int threads) {
     return trial_orbitals_lanczos(s, N, nu, problems, const_cast<double*>(S_all), Phi0, Out, alive, P, status, threads,
-                                  false);
+                                  false, false);
+}
+
+// ---------------------------------------------------------------- S = X U in double-float
+// S[p, e] = sum_k X[p, k] U[k, e] for the proposal matrices S_p = sum_k x'_k U_k
+// (the mixed-precision path): X (M x K, FP64) is rounded to double-float as its
+// tiles are loaded, U comes in double-float from init, each product is
+// accumulated by Dot2, and S is stored as double-float pairs (8 bytes per
+// element, the layout chebyshev_expm_df_kernel reads with s_is_df).
+constexpr int DG_T = 64, DG_K = 16;
+
+__global__ void u_to_df_kernel(long long n, const double* __restrict__ U, dfl* __restrict__ Ud) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        Ud[e] = df_from(U[e]);
+}
+
+__global__ void __launch_bounds__(256) gemm_df_kernel(int M, int Nc, int K, const double* __restrict__ X,
+                                                      const dfl* __restrict__ Ud, dfl* __restrict__ S) {
+    __shared__ dfl Xs[DG_K][DG_T + 1];
+    __shared__ dfl Us[DG_K][DG_T];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const long long row0 = (long long)blockIdx.y * DG_T, col0 = (long long)blockIdx.x * DG_T;
+    float sh[4][4], sl[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
+    for (int k0 = 0; k0 < K; k0 += DG_K) {
+        for (int e = threadIdx.x; e < DG_K * DG_T; e += 256) {
+            const int r = e / DG_K, kk = e % DG_K;        // X tile: 64 rows x 16 k
+            const long long gr = row0 + r;
+            const int gk = k0 + kk;
+            Xs[kk][r] = (gr < M && gk < K) ? df_from(X[gr * K + gk]) : dfl{0.f, 0.f};
+            const int kb = e / DG_T, c = e % DG_T;        // U tile: 16 k x 64 cols
+            const long long gc = col0 + c;
+            const int gkb = k0 + kb;
+            Us[kb][c] = (gkb < K && gc < Nc) ? Ud[(long long)gkb * Nc + gc] : dfl{0.f, 0.f};
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < DG_K; ++kk) {
+            dfl a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Xs[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Us[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float p = a[i].hi * b[j].hi;
+                    float q = fmaf(a[i].hi, b[j].hi, -p);
+                    q = fmaf(a[i].hi, b[j].lo, q);
+                    q = fmaf(a[i].lo, b[j].hi, q);
+                    const float t = sh[i][j] + p, z = t - sh[i][j];
+                    sl[i][j] += q + ((sh[i][j] - (t - z)) + (p - z));
+                    sh[i][j] = t;
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long r = row0 + ty + 16 * i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long c = col0 + tx + 16 * j;
+            if (c < Nc) S[r * Nc + c] = df_two_sum(sh[i][j], sl[i][j]);
+        }
+    }
+}
+
+cudaError_t u_to_df(cudaStream_t s, long long n, const double* U, void* Ud) {
+    if (n <= 0) return cudaSuccess;
+    u_to_df_kernel<<<(unsigned)min((n + 255) / 256, 4096LL), 256, 0, s>>>(n, U, reinterpret_cast<dfl*>(Ud));
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_df(cudaStream_t s, int M, int Nc, int K, const double* X, const void* Ud, double* S) {
+    if (M <= 0 || Nc <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((Nc + DG_T - 1) / DG_T), (unsigned)((M + DG_T - 1) / DG_T));
+    gemm_df_kernel<<<grid, 256, 0, s>>>(M, Nc, K, X, reinterpret_cast<const dfl*>(Ud), reinterpret_cast<dfl*>(S));
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace afq
