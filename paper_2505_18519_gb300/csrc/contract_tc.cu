@@ -182,9 +182,10 @@ __device__ __forceinline__ int row_exp(unsigned maxbits) {
 // warps run the epilogues, warp w on tensor-memory lanes 32 (w % 4) .. +31.
 //   GEMM1 of a block of GT matrices: T = GT / GPT tiles of 128 rows (g, j),
 //     each accumulated in its own columns (F16 mode: hi*hi in one set, the
-//     corrections in a second set), streamed unit by unit from the ring; the
-//     ring is refilled as soon as the MMAs reading a stage have completed, so
-//     the next block's operands load while the per-pair epilogues run.
+//     corrections in a second set), streamed unit by unit from the ring; a
+//     stage is refilled as soon as the MMAs reading it have completed (so S
+//     copies stay in flight), and the next block's first units load while the
+//     per-pair epilogues run.
 //   per pair: epilogue 1 (row maxima of R_g,p over j, then R scaled to
 //     [128, 256) per row, split, stored as the A operand of GEMM2), GEMM2
 //     against Theta_p, epilogue 2 (M to shared memory, traces, sums over a and g).
@@ -359,7 +360,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     tc::mma_commit(&empty_bar[st]);
                     ++consumed;
-                    if (u >= 1 && !refill_upto(u - 1)) ok = false;
+                    // refill this stage as soon as its MMAs (a fraction of a load's latency)
+                    // are done, so S copies stay in flight
+                    if (!refill_upto(u)) ok = false;
                 }
             }
             if (ok) {
