@@ -48,7 +48,7 @@ typedef struct afqmc_ctx afqmc_ctx;
 
 typedef enum {
     AFQMC_OK = 0,
-    AFQMC_ERR_ARG = 1,        /* invalid argument, or a size this build does not support */
+    AFQMC_ERR_ARG = 1,        /* invalid argument, or a size the library does not support */
     AFQMC_ERR_CUDA = 2,       /* a CUDA runtime call failed (the message says which) */
     AFQMC_ERR_WORKSPACE = 3,  /* workspace missing, too small, or not 256-byte aligned */
     AFQMC_ERR_NUMERIC = 4,    /* the device flagged a singular overlap or a non-finite value */
