@@ -224,6 +224,8 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.Udf = c->precision != AFQMC_PRECISION_FP64 ? take(K * NN * 8) : nullptr;
     w.T = (double*)take(NN * 8);
     w.expT = (double*)take(NN * 8);
+    w.Ldf = c->precision != AFQMC_PRECISION_FP64 ? take(G * NN * 8) : nullptr;
+    w.expTdf = c->precision != AFQMC_PRECISION_FP64 ? take(NN * 8) : nullptr;
     w.scratchNN = (double*)take(3 * NN * 8);
     w.Lt = c->precision != AFQMC_PRECISION_FP64
                ? take(contract_tc_image_bytes(d.N, d.nu, d.nd, d.G, c->precision == AFQMC_PRECISION_FP16X3))
@@ -448,8 +450,10 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         }
         // initial walkers phi_w = Phi(x_w), x_w ~ N(0, I), orthonormalised
         fill_normals(s, w.xprop, d.W, d.K, p.woff, p.seed, TAG_INIT_WALKER, w.counters, 0);
-        if (w.Udf && (e = u_to_df(s, (long long)d.K * NN, w.U, w.Udf)) != cudaSuccess) {
-            st = fail(AFQMC_ERR_CUDA, "double-float copy of U: %s", cudaGetErrorString(e));
+        if (w.Udf && ((e = u_to_df(s, (long long)d.K * NN, w.U, w.Udf)) != cudaSuccess ||
+                      (e = u_to_df(s, (long long)d.G * NN, w.L, w.Ldf)) != cudaSuccess ||
+                      (e = u_to_df(s, (long long)NN, w.expT, w.expTdf)) != cudaSuccess)) {
+            st = fail(AFQMC_ERR_CUDA, "double-float copies of U, L and exp(-tau T/2): %s", cudaGetErrorString(e));
             break;
         }
         if ((e = form_S(ctx, w.xprop, d.W)) != cudaSuccess || (e = trial_orbitals_of(ctx, d.W, w.Phiprop, nullptr, 1)) != cudaSuccess) {
@@ -506,11 +510,18 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         if (st != AFQMC_OK) return st;
         if ((st = measure(ctx)) != AFQMC_OK) return st;      // Eq. (25)-(27), (16) at phi
         CK(fields(s, d, p, w.counters, w.vbar, w.sumS, w.weight, w.alive, (double*)w.y, w.logshift));
-        gemm_nn_f64(s, 2 * d.W, d.N * d.N, d.G, 1.0, (const double*)w.y, d.G, w.L, (long long)d.N * d.N, 0.0,
-                    w.Aplanes, (long long)d.N * d.N);
-        CK(cudaGetLastError());
+        if (w.Ldf) {   // mixed precision: field planes and propagation in double-float
+            CK(gemm_df(s, 2 * d.W, d.N * d.N, d.G, (const double*)w.y, w.Ldf, w.Aplanes));
+        } else {
+            gemm_nn_f64(s, 2 * d.W, d.N * d.N, d.G, 1.0, (const double*)w.y, d.G, w.L, (long long)d.N * d.N, 0.0,
+                        w.Aplanes, (long long)d.N * d.N);
+            CK(cudaGetLastError());
+        }
         if ((st = prof_mark(ctx, PH_FIELDS)) != AFQMC_OK) return st;
-        CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive));          // Eq. (12)
+        if (w.Ldf)
+            CK(propagate_df(s, d, p, w.expTdf, w.Aplanes, w.phi, w.phi_new, w.alive));  // Eq. (12)
+        else
+            CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive));       // Eq. (12)
         if ((st = prof_mark(ctx, PH_PROPAGATE)) != AFQMC_OK) return st;
         for (int spin = 0; spin < 2; ++spin)
             CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi_new, w.logdet_new, nullptr, w.alive, w.status,

@@ -150,6 +150,8 @@ struct Workspace {
     void* Udf;        // K*N*N double-float copy of U (mixed-precision path)
     double* T;        // N*N, h - 1/2 sum_g L_g L_g
     double* expT;     // N*N, exp(-tau T / 2)
+    void* Ldf;        // G*N*N double-float copy of L (mixed-precision path)
+    void* expTdf;     // N*N double-float copy of expT (mixed-precision path)
     double* scratchNN;  // 3*N*N for the matrix exponential at init
     void* Lt;           // split-BF16 image of (h, L_g) for the tensor-core contraction
     // composite walkers
@@ -172,6 +174,7 @@ struct Workspace {
     double2* y;       // W*G   x - xbar
     double2* logshift;  // W  sum_g (xi xbar - xbar^2/2)
     double* Aplanes;  // 2W*N*N  rows 2w: sum_g Re(y) L_g ; 2w+1: sum_g Im(y) L_g
+                      //         (double-float pairs, 8 bytes each, on the mixed-precision path)
     double2* phi_new; // W*N*nt
     double2* old_sum; // W   sum_p S_p ov'/ov
     double2* ratio;   // W

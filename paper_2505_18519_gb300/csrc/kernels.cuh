@@ -79,6 +79,10 @@ cudaError_t fields(cudaStream_t s, const Dims& d, const StepParams& p, const uns
                    double2* logshift);
 cudaError_t propagate(cudaStream_t s, const Dims& d, const StepParams& p, const double* expT, const double* Aplanes,
                       const double2* phi, double2* phi_new, const int* alive);
+// The same propagation with expT and the field planes as double-float (from
+// u_to_df and gemm_df), for the mixed-precision path.
+cudaError_t propagate_df(cudaStream_t s, const Dims& d, const StepParams& p, const void* expTdf, const void* Aplanes_df,
+                         const double2* phi, double2* phi_new, const int* alive);
 cudaError_t ratios(cudaStream_t s, const Dims& d, const double2* logov, const double2* logdet_new,
                    const double2* sumS, const double2* logshift, const int* alive, double2* logov_cur,
                    double2* old_sum, double2* ratio, double* Iabs);

@@ -18,40 +18,10 @@
 // and the number of terms; the Gershgorin half-width of the sampled S is
 // 3 to 4 times the spectral one.  So the interval comes from a short Lanczos
 // run, checked a posteriori (see chebyshev_expm_df_kernel).
+#include "df.cuh"
 #include "kernels.cuh"
 
 namespace afq {
-
-struct dfl {
-    float hi, lo;
-};
-
-__device__ __forceinline__ dfl df_two_sum(float a, float b) {
-    const float s = a + b, bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ dfl df_quick(float a, float b) {   // |a| >= |b|
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-    const dfl s = df_two_sum(a.hi, b.hi), t = df_two_sum(a.lo, b.lo);
-    const dfl u = df_quick(s.hi, s.lo + t.hi);
-    return df_quick(u.hi, u.lo + t.lo);
-}
-__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-    const float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return df_quick(p, e);
-}
-__device__ __forceinline__ dfl df_from(double x) {
-    const float h = __double2float_rn(x);
-    return {h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
 
 constexpr int CHEB_DF_MAX = 320;
 constexpr double RHO_DF = 6.5;   // largest Gershgorin half-width run in double-float

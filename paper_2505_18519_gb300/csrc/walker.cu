@@ -3,6 +3,7 @@
 // and force bias (Eq. (4), (15)), propagation B(x - xbar) (Eq. (5), (12)), the
 // importance function (Eq. (14)), Metropolis proposals and acceptance of the
 // paths (Eq. (23)), and the hand-off constraint (Eq. (17), (28)-(29)).
+#include "df.cuh"
 #include "kernels.cuh"
 
 namespace afq {
@@ -279,6 +280,108 @@ cudaError_t propagate(cudaStream_t s, const Dims& d, const StepParams& p, const 
     cudaError_t e = raise_smem_limit((const void*)propagate_kernel, smem);
     if (e != cudaSuccess) return e;
     propagate_kernel<<<d.W, 256, smem, s>>>(d.N, d.nt, p.taylor_order, p.dtau, expT, Aplanes, phi, phi_new, alive); count_launches(1);
+    return cudaGetLastError();
+}
+
+// Mixed-precision form of the same propagation (Eq. (12)): E and the planes
+// P, Q arrive as double-float pairs, the vectors V are held as double-float in
+// shared memory, every matrix-vector product is a Dot2 sum, and the series
+// acc = sum_m (A^m / m!) E phi is summed in FP64.  FP32 instructions issue at
+// 64 times the FP64 rate here, and the double-float products carry about 44
+// significant bits, far below the tensor-core contraction's error.
+__device__ __forceinline__ float4 df_pack(dfl re, dfl im) { return make_float4(re.hi, re.lo, im.hi, im.lo); }
+
+__global__ void __launch_bounds__(256) propagate_df_kernel(int N, int nt, int order, double dtau,
+                                                           const dfl* __restrict__ E, const dfl* __restrict__ Aplanes,
+                                                           const double2* __restrict__ phi, double2* phi_new,
+                                                           const int* __restrict__ alive) {
+    extern __shared__ float4 sdf[];
+    float4* V = sdf;                          // N x nt, (Re hi, Re lo, Im hi, Im lo)
+    float4* Wt = sdf + (size_t)N * nt;        // N x nt
+    const long long w = blockIdx.x;
+    const double2* in = phi + w * (long long)N * nt;
+    double2* acc = phi_new + w * (long long)N * nt;
+    const int nn = N * nt;
+    if (!alive[w]) {
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) acc[e] = in[e];
+        return;
+    }
+    const dfl* Pm = Aplanes + (2 * w) * (long long)N * N;
+    const dfl* Qm = Pm + (long long)N * N;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const double2 v = in[e];
+        V[e] = df_pack(df_from(v.x), df_from(v.y));
+    }
+    __syncthreads();
+    // acc <- E phi
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int i = e / nt, c = e - i * nt;
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        for (int j = 0; j < N; ++j) {
+            const dfl ev = E[(long long)i * N + j];
+            const float4 v = V[j * nt + c];
+            dot2_fma(rh, rl, ev, dfl{v.x, v.y});
+            dot2_fma(ih, il, ev, dfl{v.z, v.w});
+        }
+        const dfl re = df_two_sum(rh, rl), im = df_two_sum(ih, il);
+        Wt[e] = df_pack(re, im);
+        acc[e] = make_double2(df_to(re), df_to(im));
+    }
+    __syncthreads();
+    float4* cur = Wt;
+    float4* nxt = V;
+    const double st = sqrt(dtau);
+    for (int m = 1; m <= order; ++m) {
+        const dfl scale = df_from(st / m);
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int i = e / nt, c = e - i * nt;
+            // A V = (-st Q + i st P) V: Re = -(Q Re V) - (P Im V), Im = (P Re V) - (Q Im V)
+            float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+            for (int j = 0; j < N; ++j) {
+                const dfl pv = Pm[(long long)i * N + j], qv = Qm[(long long)i * N + j];
+                const float4 v = cur[j * nt + c];
+                const dfl vr{v.x, v.y}, vi{v.z, v.w};
+                dot2_fma(rh, rl, df_neg(qv), vr);
+                dot2_fma(rh, rl, df_neg(pv), vi);
+                dot2_fma(ih, il, pv, vr);
+                dot2_fma(ih, il, df_neg(qv), vi);
+            }
+            const dfl re = df_mul(df_two_sum(rh, rl), scale), im = df_mul(df_two_sum(ih, il), scale);
+            nxt[e] = df_pack(re, im);
+            const double2 a = acc[e];
+            acc[e] = make_double2(a.x + df_to(re), a.y + df_to(im));
+        }
+        __syncthreads();   // every read of cur is done before it is overwritten as nxt
+        float4* t = cur; cur = nxt; nxt = t;
+    }
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const double2 a = acc[e];
+        V[e] = df_pack(df_from(a.x), df_from(a.y));
+    }
+    __syncthreads();
+    // phi' <- E acc
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int i = e / nt, c = e - i * nt;
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        for (int j = 0; j < N; ++j) {
+            const dfl ev = E[(long long)i * N + j];
+            const float4 v = V[j * nt + c];
+            dot2_fma(rh, rl, ev, dfl{v.x, v.y});
+            dot2_fma(ih, il, ev, dfl{v.z, v.w});
+        }
+        acc[e] = make_double2(df_to(df_two_sum(rh, rl)), df_to(df_two_sum(ih, il)));
+    }
+}
+
+cudaError_t propagate_df(cudaStream_t s, const Dims& d, const StepParams& p, const void* expTdf, const void* Aplanes_df,
+                         const double2* phi, double2* phi_new, const int* alive) {
+    size_t smem = 2 * (size_t)d.N * d.nt * sizeof(float4);
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = raise_smem_limit((const void*)propagate_df_kernel, smem);
+    if (e != cudaSuccess) return e;
+    propagate_df_kernel<<<d.W, 256, smem, s>>>(d.N, d.nt, p.taylor_order, p.dtau, reinterpret_cast<const dfl*>(expTdf),
+                                               reinterpret_cast<const dfl*>(Aplanes_df), phi, phi_new, alive);
+    count_launches(1);
     return cudaGetLastError();
 }
 

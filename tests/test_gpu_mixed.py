@@ -74,6 +74,51 @@ def test_mixed_measure_against_oracle(name, precision):
     ctx.close()
 
 
+@pytest.mark.parametrize("name", ["c0", "ragged", "one_spin", "one_electron_each", "n70_two_k_blocks", "medium"])
+def test_mixed_step_matches_oracle_given_its_force_bias(name):
+    """One step of the mixed path against the oracle's step fed the mixed
+    path's own force-bias averages: the rest of the step (fields, the field
+    planes sum_g y_g L_g and the Taylor propagation of Eq. (12) in double-float,
+    overlap ratios, Metropolis sweeps with double-float trial orbitals,
+    constraint, reorthonormalisation) must then agree to 1e-9, so an error in
+    the double-float propagation is not hidden behind the contraction's 1e-6."""
+    spec, W, P, dtau = SYSTEMS[name]
+    seed = 640 + len(name)
+    s, ctx = _ctx(spec, W, P, dtau, seed, "fp16x3", n_burn=2, n_sweeps=2)
+    ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, dtau)
+    ocfg = oa.OracleConfig(dtau=dtau, n_walkers=W, n_paths=P, seed=seed, n_burn=2, n_sweeps=2)
+    ost = oa.init(ham, ocfg)
+    ost, _ = oa.step(ham, ocfg, ost)
+    ctx.load_state_arrays(dict(step=ost.step, phi_up=ost.phi_up, phi_dn=ost.phi_dn, weight=ost.weight, x=ost.x,
+                               Phi=ost.Phi))
+    ctx.energy()                          # measures at the loaded state
+    vbar_gpu = ctx.observables()["force_bias"]
+    ctx.step(1)
+    g = ctx.state_arrays()
+    measure = oa.measure
+
+    def measure_with_gpu_force_bias(ham_, st_):
+        m = measure(ham_, st_)
+        assert np.max(np.abs(m["v_bar"] - vbar_gpu)) < 1e-4      # the contraction's accuracy
+        m["v_bar"] = vbar_gpu.copy()
+        return m
+
+    oa.measure = measure_with_gpu_force_bias
+    try:
+        ost2, _ = oa.step(ham, ocfg, ost)
+    finally:
+        oa.measure = measure
+    assert g["step"] == ost2.step
+    assert np.array_equal(g["weight"] == 0, ost2.weight == 0)
+    assert np.allclose(g["weight"], ost2.weight, rtol=1e-9, atol=0)
+    assert np.max(np.abs(g["phi_up"] - ost2.phi_up)) < 1e-9
+    if ost2.phi_dn.size:
+        assert np.max(np.abs(g["phi_dn"] - ost2.phi_dn)) < 1e-9
+    assert np.max(np.abs(g["x"] - ost2.x)) < 1e-9
+    assert np.max(np.abs(g["Phi"] - ost2.Phi)) < 1e-9
+    ctx.close()
+
+
 def test_mixed_trajectory_tracks_fp64_gpu_path():
     """Same seed and inputs, 10 steps of the medium system (64 walkers x 32
     paths) on both paths: the per-step mixed energies stay within 0.1 mHa."""
