@@ -216,23 +216,29 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ traffic of the dominant kernel
-def kernel_digest(kernel_source: str, end_marker: str = "size_t contract_fp64_smem") -> str:
-    """sha256 (16 hex digits) of the device code of the contraction file: its
-    text up to the first host function, so that launcher-only edits keep it."""
+def kernel_digest(kernel_source: str, end_marker: str = "size_t contract_fp64_smem", start_marker: str = None) -> str:
+    """sha256 (16 hex digits) of a kernel's device code: the text of its
+    source file from the line starting with ``start_marker`` (the file's start
+    if None) up to the line starting with ``end_marker`` (the first host
+    function), so that edits of launchers or of other kernels keep it."""
     text = open(kernel_source, "rb").read()
-    cut = text.find(b"\n" + end_marker.encode())
-    return hashlib.sha256(text[:cut + 1] if cut >= 0 else text).hexdigest()[:16]
+    begin = 0
+    if start_marker is not None:
+        b = text.find(b"\n" + start_marker.encode())
+        begin = b + 1 if b >= 0 else 0
+    cut = text.find(b"\n" + end_marker.encode(), begin)
+    return hashlib.sha256(text[begin:cut + 1] if cut >= 0 else text[begin:]).hexdigest()[:16]
 
 
 def recorded_traffic(kernel_source: str, summary: str = "contract_fp64_c1_n50.md",
-                     end_marker: str = "size_t contract_fp64_smem"):
+                     end_marker: str = "size_t contract_fp64_smem", start_marker: str = None):
     """DRAM bytes per launch of a contraction kernel from its committed ncu
     summary, or None if the kernel's device code changed since the counters
     were taken."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
-    digest = kernel_digest(kernel_source, end_marker)
+    digest = kernel_digest(kernel_source, end_marker, start_marker)
     fields = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
@@ -272,10 +278,10 @@ def _timed(step, sync, stream, steps, world, local):
     return max_over_ranks(e0.elapsed_time(e1)), clk.summary(), int(l1 - l0)
 
 
-FP64_TRAFFIC = {   # kernel -> (committed summary, end of its device code), for the medium workload
-    "contract_fp64_kernel": ("contract_fp64_c1_n50.md",
-                             "// ---------------------------------------------------------------- walker-side form"),
-    "contract_fp64z_kernel": ("contract_fp64z_c1_n50.md", "size_t contract_fp64_smem"),
+FP64_WALKER_SIDE = "// ---------------------------------------------------------------- walker-side form"
+FP64_TRAFFIC = {   # kernel -> (committed summary, end of its device code, start of it), for the medium workload
+    "contract_fp64_kernel": ("contract_fp64_c1_n50.md", FP64_WALKER_SIDE, None),
+    "contract_fp64z_kernel": ("contract_fp64z_c1_n50.md", "size_t contract_fp64_smem", FP64_WALKER_SIDE),
 }
 TC_TRAFFIC = {   # kernel -> (committed summary, end of its device code), for the medium workload
     "contract_tcy_kernel": ("contract_tcy_c1_n50.md", "static size_t tcy_smem_bytes"),
