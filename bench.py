@@ -360,7 +360,8 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         ctx.close()
         d = {"precision": "fp16x3", "what": "same workload, Philox streams and initial state as the headline; the "
              "contraction (force bias + local energy) on the tensor cores in split FP16 with FP32 accumulation, the "
-             "trial orbitals in double-float (FP32 pairs), everything else FP64", "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+             "trial orbitals, proposal and field matrices and the propagation in double-float (FP32 pairs), "
+             "everything else FP64", "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
              "gpu_launches": launches, "clocks": clocks,
              "roofline": tensor_roofline(spec, W, P, prof, lib.contract_kernel(cfg)),
              "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
@@ -456,6 +457,37 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             "live_walkers_frac": sum(st["live_walkers"] for st in stats) / (len(specs) * Wb),
             "device_status_words": [int(st["status"]) for st in stats],
             "status_bits": "1 singular overlap, 2 non-finite value (the walker is removed), 4 tensor-core wait timed out"}
+
+    if only in (None, "largest"):
+        # the largest system (N = 200, 40 + 40 electrons, 1000 Cholesky vectors) in FP64 on a
+        # bounded sample: 19 walkers x 16 paths = 304 pairs, two full waves of the per-pair
+        # kernel (one block per SM), 1 warm-up and 2 timed steps
+        spec4, run4 = ai.CONFIGS["c4_n200"]
+        sy = ai.make_system(spec4)
+        W4, P4, st4 = 19, run4.n_paths, 2
+        c = lib.make_config(spec4.N, spec4.n_up, spec4.n_dn, spec4.n_chol, spec4.K, W4, P4, run4.dtau,
+                            ai.philox_run_seed(4), n_burn=2, walker_offset=rank * W4)
+        ctx = lib.Context(c, sy.h, sy.L, sy.Phi0, sy.U, device=dev)
+        ctx.step(1)
+        ctx.profile(True)
+        ms, clocks, launches = _timed(ctx.step, lambda: torch.cuda.synchronize(dev), ctx.stream, st4, world, local)
+        prof = ctx.profile_read()
+        kernel = lib.contract_kernel(c)
+        ctx.close()
+        cms = prof["ms"]["contract"] / max(1, prof["launches"]["contract"])
+        flops = contract_flops_per_pair(spec4) * W4 * P4
+        achieved = flops / (cms / 1e3) / 1e12
+        out["largest_fp64_sample"] = {
+            "precision": "fp64", "what": f"system of the largest workload (N = {spec4.N}, {spec4.n_up} + {spec4.n_dn} "
+            f"electrons, n_chol = {spec4.n_chol}, K = {spec4.K}), {W4} walkers x {P4} paths (304 pairs = 2 x 152 "
+            f"blocks of the per-pair kernel, Theta streamed in row slabs), 1 warm-up and {st4} timed steps",
+            "value": W4 * P4 * world * st4 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / st4,
+            "full_workload_step_s_extrapolated": ms / st4 / 1e3 * (run4.n_walkers * run4.n_paths) / (W4 * P4),
+            "gpu_launches": launches, "clocks": clocks,
+            "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3,
+                         "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
+                         "flops_per_launch": flops, "ms_per_launch": cms},
+            "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
     return out
 
 
@@ -616,7 +648,7 @@ def main():
     ap.add_argument("--walkers", type=int, default=0, help="walkers per GPU (profiling runs on a small case)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision, learned-proposal and batched measurements")
-    ap.add_argument("--only", choices=("mixed", "learned", "batched"), default=None,
+    ap.add_argument("--only", choices=("mixed", "learned", "batched", "largest"), default=None,
                     help="time one variant alone (profiling); skips the FP64 headline's extras")
     args = ap.parse_args()
     if args.impl == "reference":

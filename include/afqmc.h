@@ -73,9 +73,13 @@ enum {
 
 /* arithmetic of the two big contractions (R = Phi^T L_g and M = R Theta) */
 enum {
-    AFQMC_PRECISION_FP64 = 0,  /* FP64 everywhere */
+    AFQMC_PRECISION_FP64 = 0,  /* FP64 everywhere.  N <= 256, n_up <= 64, n_up^2 + n_dn^2 <= 4096, and
+                                  3 N n_up <= 25600 (e.g. N = 200 with 40 + 40 electrons) */
     AFQMC_PRECISION_BF16X3 = 1, /* the fused contraction on the tensor cores in split BF16 (hi*hi + hi*lo +
-                                   lo*hi, FP32 accumulation, traces summed in FP64); everything else FP64.
+                                   lo*hi, FP32 accumulation, traces summed in FP64); trial orbitals, proposal
+                                   and field matrices and the propagation in double-float (pairs of FP32
+                                   numbers, about 44 bits; the propagation in FP64 when its 2 N (n_up + n_dn)
+                                   complex work values exceed shared memory); everything else FP64.
                                    N <= 128, n_up <= 32 */
     AFQMC_PRECISION_FP16X3 = 2  /* the same with each operand row/column scaled by a power of two and split
                                    into an integer FP16 part (|x| <= 256) and an FP16 remainder (about 20 bits
@@ -205,7 +209,8 @@ afqmc_status afqmc_profile_read(afqmc_ctx* ctx, double* out, int len);
 int64_t afqmc_launch_count(void);
 
 /* Which kernel computes the fused contraction of Eq. (15) and (27) for `cfg`:
- * 0 contract_fp64_kernel (precision FP64), 1 contract_tc_kernel (tensor cores,
+ * 0 contract_fp64_kernel (precision FP64; when Theta does not fit in shared
+ * memory, e.g. N = 200, it streams row slabs of Theta), 1 contract_tc_kernel (tensor cores,
  * per-pair form, N <= 128, n_up <= 32), 2 contract_tcy_kernel (tensor cores,
  * walker-side form B_p^T (L_g phi_w) with B_p = Phi_p A_p^-T, N <= 64 and
  * n_up + n_dn <= 40), 3 contract_fp64z_kernel (precision FP64, walker-side form

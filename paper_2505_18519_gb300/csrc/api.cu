@@ -189,7 +189,8 @@ static const char* check_config(const afqmc_config* c) {
     if (c->precision != AFQMC_PRECISION_FP64 &&
         !contract_tc_supported(c->N, c->n_up, c->n_dn, c->precision == AFQMC_PRECISION_FP16X3))
         return "sizes not supported by the tensor-core contraction (N <= 128, n_up <= 32)";
-    if (2ull * c->N * (c->n_up + c->n_dn) * 16 > 220 * 1024) return "sizes too large for the propagation kernel";
+    if (3ull * c->N * c->n_up * 8 > 200 * 1024)
+        return "sizes too large for the trial-orbital kernel (3 N n_up doubles of shared memory)";
     return nullptr;
 }
 
@@ -224,8 +225,10 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.Udf = c->precision != AFQMC_PRECISION_FP64 ? take(K * NN * 8) : nullptr;
     w.T = (double*)take(NN * 8);
     w.expT = (double*)take(NN * 8);
-    w.Ldf = c->precision != AFQMC_PRECISION_FP64 ? take(G * NN * 8) : nullptr;
-    w.expTdf = c->precision != AFQMC_PRECISION_FP64 ? take(NN * 8) : nullptr;
+    // the double-float propagation needs its work arrays in shared memory
+    const bool prop_df = c->precision != AFQMC_PRECISION_FP64 && propagate_in_smem(d.N, d.nt);
+    w.Ldf = prop_df ? take(G * NN * 8) : nullptr;
+    w.expTdf = prop_df ? take(NN * 8) : nullptr;
     w.scratchNN = (double*)take(3 * NN * 8);
     w.Lt = c->precision != AFQMC_PRECISION_FP64
                ? take(contract_tc_image_bytes(d.N, d.nu, d.nd, d.G, c->precision == AFQMC_PRECISION_FP16X3))
@@ -248,6 +251,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.logshift = (double2*)take(W * 16);
     w.Aplanes = (double*)take(2 * W * NN * 8);
     w.phi_new = (double2*)take(W * N * nt * 16);
+    w.propbuf = propagate_in_smem(d.N, d.nt) ? nullptr : (double2*)take(W * 2 * N * nt * 16);
     w.old_sum = (double2*)take(W * 16);
     w.ratio = (double2*)take(W * 16);
     w.Iabs = (double*)take(W * 8);
@@ -451,8 +455,8 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         // initial walkers phi_w = Phi(x_w), x_w ~ N(0, I), orthonormalised
         fill_normals(s, w.xprop, d.W, d.K, p.woff, p.seed, TAG_INIT_WALKER, w.counters, 0);
         if (w.Udf && ((e = u_to_df(s, (long long)d.K * NN, w.U, w.Udf)) != cudaSuccess ||
-                      (e = u_to_df(s, (long long)d.G * NN, w.L, w.Ldf)) != cudaSuccess ||
-                      (e = u_to_df(s, (long long)NN, w.expT, w.expTdf)) != cudaSuccess)) {
+                      (w.Ldf && (e = u_to_df(s, (long long)d.G * NN, w.L, w.Ldf)) != cudaSuccess) ||
+                      (w.expTdf && (e = u_to_df(s, (long long)NN, w.expT, w.expTdf)) != cudaSuccess))) {
             st = fail(AFQMC_ERR_CUDA, "double-float copies of U, L and exp(-tau T/2): %s", cudaGetErrorString(e));
             break;
         }
@@ -521,7 +525,7 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         if (w.Ldf)
             CK(propagate_df(s, d, p, w.expTdf, w.Aplanes, w.phi, w.phi_new, w.alive));  // Eq. (12)
         else
-            CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive));       // Eq. (12)
+            CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive, w.propbuf));   // Eq. (12)
         if ((st = prof_mark(ctx, PH_PROPAGATE)) != AFQMC_OK) return st;
         for (int spin = 0; spin < 2; ++spin)
             CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi_new, w.logdet_new, nullptr, w.alive, w.status,

@@ -176,6 +176,7 @@ struct Workspace {
     double* Aplanes;  // 2W*N*N  rows 2w: sum_g Re(y) L_g ; 2w+1: sum_g Im(y) L_g
                       //         (double-float pairs, 8 bytes each, on the mixed-precision path)
     double2* phi_new; // W*N*nt
+    double2* propbuf; // W*2*N*nt work space of the propagation when it does not fit in shared memory (else null)
     double2* old_sum; // W   sum_p S_p ov'/ov
     double2* ratio;   // W
     double* Iabs;     // W

@@ -7,7 +7,10 @@
 // energy (Eq. (1), (3), (16) by Wick's theorem) is
 //   E_L = sum_s Tr(Phi_s^T h Theta_s) + 1/2 sum_g [ v_g^2 - sum_s Tr(M_g,s M_g,s) ].
 // No matrix of the contraction goes to global memory: one block per pair keeps
-// Phi and Theta in shared memory and streams column blocks of each L_g.
+// Phi and Theta in shared memory and streams column blocks of each L_g.  When
+// Theta does not fit (N = 200 with 40 + 40 electrons needs 256 KB), the SLAB
+// form keeps only the JB rows of Theta that the current column block of L_g
+// multiplies, loaded beside it (the pair's Theta stays in L2 across matrices).
 #include "kernels.cuh"
 
 namespace afq {
@@ -39,6 +42,27 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* red) {
     return t;   // valid in thread 0
 }
 
+// Offsets (in doubles) of the shared-memory arrays: Phi, Theta (all N rows, or
+// the JB-row slab), the L_g column block, R, and the M entries (which in the
+// SLAB form reuse the slab/L/R region: they are written after the last column
+// block of a matrix and read before the next matrix's first block is loaded).
+struct Fp64Layout {
+    size_t oTh, oL, oR, oM, total;
+};
+
+__host__ __device__ __forceinline__ Fp64Layout fp64_layout(int N, int nu, int nd, int JB, bool slab) {
+    const size_t nt = nu + nd, throws = slab ? (size_t)JB : (size_t)N;
+    Fp64Layout l;
+    l.oTh = r2((size_t)N * nu);
+    l.oL = l.oTh + 2 * throws * nt;
+    l.oR = l.oL + (size_t)N * JB;
+    const size_t endR = r2(l.oR + (size_t)nu * JB), nM = 2 * (size_t)(nu * nu + nd * nd);
+    l.oM = slab ? l.oTh : endR;
+    l.total = slab ? (endR > l.oTh + nM ? endR : l.oTh + nM) : endR + nM;
+    return l;
+}
+
+template <bool SLAB>
 __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd, int G, int JB,
                                                            const double* __restrict__ h, const double* __restrict__ L,
                                                            const double* __restrict__ Phi, const double2* __restrict__ Theta,
@@ -47,18 +71,18 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
     __shared__ double2 red[CT / 32];
     const int nt = nu + nd;
     const long long pair = blockIdx.x;
-    const size_t oTh = r2((size_t)N * nu), oL = oTh + 2 * (size_t)N * nt, oR = oL + (size_t)N * JB;
-    const size_t oM = r2(oR + (size_t)nu * JB);
+    const Fp64Layout lay = fp64_layout(N, nu, nd, JB, SLAB);
     double* sPhi = smc;                                             // N x nu
-    double2* sTh = reinterpret_cast<double2*>(smc + oTh);           // N x nt
-    double* sL = smc + oL;                                          // N x JB
-    double* sR = smc + oR;                                          // nu x JB
-    double2* sM = reinterpret_cast<double2*>(smc + oM);             // nu^2 + nd^2
+    double2* sTh = reinterpret_cast<double2*>(smc + lay.oTh);       // N x nt (SLAB: JB x nt)
+    double* sL = smc + lay.oL;                                      // N x JB
+    double* sR = smc + lay.oR;                                      // nu x JB
+    double2* sM = reinterpret_cast<double2*>(smc + lay.oM);         // nu^2 + nd^2
     const int tid = threadIdx.x;
     const double* gPhi = Phi + pair * (long long)N * nu;
     const double2* gTh = Theta + pair * (long long)N * nt;
     for (int e = tid; e < N * nu; e += CT) sPhi[e] = gPhi[e];
-    for (int e = tid; e < N * nt; e += CT) sTh[e] = gTh[e];
+    if (!SLAB)
+        for (int e = tid; e < N * nt; e += CT) sTh[e] = gTh[e];
     const int nM = nu * nu + nd * nd;
     // decode owned M entries: o < nu^2 -> spin up (a, b); else spin down
     int own_a[MAXOWN], own_b[MAXOWN], own_c[MAXOWN];
@@ -85,6 +109,8 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
                 int i = e / jb, j = e - i * jb;
                 sL[i * JB + j] = Lg[(long long)i * N + j0 + j];
             }
+            if (SLAB)   // rows j0 .. j0 + jb - 1 of Theta, contiguous in global memory
+                for (int e = tid; e < jb * nt; e += CT) sTh[e] = gTh[(size_t)j0 * nt + e];
             __syncthreads();
             for (int e = tid; e < nu * jb; e += CT) {
                 int a = e / jb, j = e - a * jb;
@@ -97,7 +123,7 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
             for (int r = 0; r < MAXOWN; ++r) {
                 if (r >= nown) break;
                 const double* Ra = sR + own_a[r] * JB;
-                const double2* Tc = sTh + (size_t)j0 * nt + own_c[r];
+                const double2* Tc = sTh + (SLAB ? 0 : (size_t)j0 * nt) + own_c[r];
                 double2 s = acc[r];
                 for (int j = 0; j < jb; ++j) {
                     double rv = Ra[j];
@@ -328,27 +354,39 @@ cudaError_t contract_fp64_walker(cudaStream_t s, const Dims& d, const double* h,
 }
 
 size_t contract_fp64_smem(int N, int nu, int nd, int JB) {
-    int nt = nu + nd;
-    size_t oTh = r2((size_t)N * nu), oL = oTh + 2 * (size_t)N * nt, oR = oL + (size_t)N * JB;
-    size_t oM = r2(oR + (size_t)nu * JB);
-    return (oM + 2 * (size_t)(nu * nu + nd * nd)) * sizeof(double);
+    return fp64_layout(N, nu, nd, JB, false).total * sizeof(double);
+}
+
+static size_t contract_fp64_slab_smem(int N, int nu, int nd, int JB) {
+    return fp64_layout(N, nu, nd, JB, true).total * sizeof(double);
 }
 
 int contract_fp64_jb(int N) { return N <= 64 ? N : 32; }
 
 bool contract_fp64_supported(int N, int nu, int nd) {
     if (nu * nu + nd * nd > MAXOWN * CT) return false;
-    return contract_fp64_smem(N, nu, nd, contract_fp64_jb(N)) <= 220 * 1024;
+    const int JB = contract_fp64_jb(N);
+    return contract_fp64_smem(N, nu, nd, JB) <= 220 * 1024 || contract_fp64_slab_smem(N, nu, nd, JB) <= 220 * 1024;
 }
 
 cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                           const double2* Theta, double2* vpair, double2* epair, long long pairs) {
-    int JB = contract_fp64_jb(d.N);
-    size_t smem = contract_fp64_smem(d.N, d.nu, d.nd, JB);
     if (!contract_fp64_supported(d.N, d.nu, d.nd)) return cudaErrorInvalidValue;
-    cudaError_t e = raise_smem_limit((const void*)contract_fp64_kernel, smem);
+    if (pairs <= 0) return cudaSuccess;
+    const int JB = contract_fp64_jb(d.N);
+    size_t smem = contract_fp64_smem(d.N, d.nu, d.nd, JB);
+    const bool slab = smem > 220 * 1024;
+    if (slab) smem = contract_fp64_slab_smem(d.N, d.nu, d.nd, JB);
+    const void* k = slab ? (const void*)contract_fp64_kernel<true> : (const void*)contract_fp64_kernel<false>;
+    cudaError_t e = raise_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
-    contract_fp64_kernel<<<(unsigned)pairs, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair, epair); count_launches(1);
+    if (slab)
+        contract_fp64_kernel<true><<<(unsigned)pairs, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair,
+                                                                      epair);
+    else
+        contract_fp64_kernel<false><<<(unsigned)pairs, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair,
+                                                                       epair);
+    count_launches(1);
     return cudaGetLastError();
 }
 

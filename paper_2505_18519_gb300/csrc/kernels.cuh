@@ -77,10 +77,13 @@ cudaError_t energy_reduce(cudaStream_t s, const Dims& d, const double* weight, c
 cudaError_t fields(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr,
                    const double2* vbar, const double2* sumS, double* weight, int* alive, double* yplanes,
                    double2* logshift);
+// scratch: W * 2 * N * nt complex work space, used (and then required) only when
+// propagate_in_smem(N, nt) is false.
+bool propagate_in_smem(int N, int nt);
 cudaError_t propagate(cudaStream_t s, const Dims& d, const StepParams& p, const double* expT, const double* Aplanes,
-                      const double2* phi, double2* phi_new, const int* alive);
+                      const double2* phi, double2* phi_new, const int* alive, double2* scratch);
 // The same propagation with expT and the field planes as double-float (from
-// u_to_df and gemm_df), for the mixed-precision path.
+// u_to_df and gemm_df), for the mixed-precision path; needs propagate_in_smem.
 cudaError_t propagate_df(cudaStream_t s, const Dims& d, const StepParams& p, const void* expTdf, const void* Aplanes_df,
                          const double2* phi, double2* phi_new, const int* alive);
 cudaError_t ratios(cudaStream_t s, const Dims& d, const double2* logov, const double2* logdet_new,

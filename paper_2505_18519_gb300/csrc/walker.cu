@@ -202,14 +202,19 @@ cudaError_t fields(cudaStream_t s, const Dims& d, const StepParams& p, const uns
 // A = i sqrt(tau) sum_g y_g L_g = -sqrt(tau) Q + i sqrt(tau) P, where
 // P = sum_g Re(y_g) L_g, Q = sum_g Im(y_g) L_g (rows 2w, 2w+1 of Aplanes).
 // One block per walker, both spins at once (N x nt complex); the running sum
-// is kept in phi_new (global) and the current term in shared memory.
+// is kept in phi_new (global) and the current term in shared memory, or, when
+// the two N x nt work arrays do not fit there (N = 200 with 40 + 40 electrons
+// needs 512 KB), in the walker's slice of a global scratch buffer (L1/L2).
+template <bool SMEM>
 __global__ void __launch_bounds__(256) propagate_kernel(int N, int nt, int order, double dtau, const double* __restrict__ E,
                                                         const double* __restrict__ Aplanes, const double2* __restrict__ phi,
-                                                        double2* phi_new, const int* __restrict__ alive) {
+                                                        double2* phi_new, const int* __restrict__ alive,
+                                                        double2* scratch) {
     extern __shared__ double2 sv[];
-    double2* V = sv;                       // N x nt
-    double2* Wt = sv + (size_t)N * nt;     // N x nt
     long long w = blockIdx.x;
+    double2* work = SMEM ? sv : scratch + w * 2 * (long long)N * nt;
+    double2* V = work;                     // N x nt
+    double2* Wt = work + (size_t)N * nt;   // N x nt
     const double2* in = phi + w * (long long)N * nt;
     double2* acc = phi_new + w * (long long)N * nt;
     int nn = N * nt;
@@ -273,13 +278,22 @@ __global__ void __launch_bounds__(256) propagate_kernel(int N, int nt, int order
     }
 }
 
+bool propagate_in_smem(int N, int nt) { return 2 * (size_t)N * nt * 16 <= 220 * 1024; }
+
 cudaError_t propagate(cudaStream_t s, const Dims& d, const StepParams& p, const double* expT, const double* Aplanes,
-                      const double2* phi, double2* phi_new, const int* alive) {
-    size_t smem = 2 * (size_t)d.N * d.nt * sizeof(double2);
-    if (smem > 220 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = raise_smem_limit((const void*)propagate_kernel, smem);
-    if (e != cudaSuccess) return e;
-    propagate_kernel<<<d.W, 256, smem, s>>>(d.N, d.nt, p.taylor_order, p.dtau, expT, Aplanes, phi, phi_new, alive); count_launches(1);
+                      const double2* phi, double2* phi_new, const int* alive, double2* scratch) {
+    if (propagate_in_smem(d.N, d.nt)) {
+        const size_t smem = 2 * (size_t)d.N * d.nt * sizeof(double2);
+        cudaError_t e = raise_smem_limit((const void*)propagate_kernel<true>, smem);
+        if (e != cudaSuccess) return e;
+        propagate_kernel<true><<<d.W, 256, smem, s>>>(d.N, d.nt, p.taylor_order, p.dtau, expT, Aplanes, phi, phi_new,
+                                                      alive, nullptr);
+    } else {
+        if (!scratch) return cudaErrorInvalidValue;
+        propagate_kernel<false><<<d.W, 256, 0, s>>>(d.N, d.nt, p.taylor_order, p.dtau, expT, Aplanes, phi, phi_new,
+                                                    alive, scratch);
+    }
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -376,7 +390,7 @@ __global__ void __launch_bounds__(256) propagate_df_kernel(int N, int nt, int or
 cudaError_t propagate_df(cudaStream_t s, const Dims& d, const StepParams& p, const void* expTdf, const void* Aplanes_df,
                          const double2* phi, double2* phi_new, const int* alive) {
     size_t smem = 2 * (size_t)d.N * d.nt * sizeof(float4);
-    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    if (!propagate_in_smem(d.N, d.nt)) return cudaErrorInvalidValue;
     cudaError_t e = raise_smem_limit((const void*)propagate_df_kernel, smem);
     if (e != cudaSuccess) return e;
     propagate_df_kernel<<<d.W, 256, smem, s>>>(d.N, d.nt, p.taylor_order, p.dtau, reinterpret_cast<const dfl*>(expTdf),

@@ -41,6 +41,9 @@ SYSTEMS = {
     "single_path": (ai.SystemSpec(10, 4, 3, 16, 5, False, 80), 7, 1, 0.01),
     "n70_two_k_blocks": (ai.SystemSpec(70, 14, 13, 90, 10, True, 81), 3, 7, 0.005),
     "medium": (ai.SystemSpec(50, 10, 10, 250, 50, True, 1001), 4, 32, 0.005),
+    # 32 + 32 electrons at N = 128: the propagation's work arrays exceed shared memory, so
+    # this context propagates in FP64 from global memory
+    "n128_fp64_propagation": (ai.SystemSpec(128, 32, 32, 160, 16, True, 84), 2, 3, 0.005),
 }
 
 
@@ -74,7 +77,8 @@ def test_mixed_measure_against_oracle(name, precision):
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["c0", "ragged", "one_spin", "one_electron_each", "n70_two_k_blocks", "medium"])
+@pytest.mark.parametrize("name", ["c0", "ragged", "one_spin", "one_electron_each", "n70_two_k_blocks", "medium",
+                                  "n128_fp64_propagation"])
 def test_mixed_step_matches_oracle_given_its_force_bias(name):
     """One step of the mixed path against the oracle's step fed the mixed
     path's own force-bias averages: the rest of the step (fields, the field

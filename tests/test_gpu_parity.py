@@ -98,6 +98,13 @@ SYSTEMS = {
     "ragged_walker_side": (ai.SystemSpec(37, 7, 5, 40, 9, True, 77), 3, 11, 0.01),
     "one_spin_walker_side": (ai.SystemSpec(12, 3, 0, 20, 6, True, 78), 3, 9, 0.01),
     "two_blocks_walker_side": (ai.SystemSpec(20, 5, 4, 60, 7, True, 82), 2, 35, 0.01),
+    # N = 200 with 40 + 40 electrons and 1000 Cholesky vectors (the largest workload's
+    # system, few walkers): Theta streamed in row slabs through the contraction, the
+    # propagation's work arrays in global memory, a ragged last column block (200 = 6 x 32 + 8).
+    # Two walkers, as the phaseless constraint kills one of them in the first step here
+    "c4_shape": (ai.CONFIGS["c4_n200"][0], 2, 2, 0.005),
+    # one spin, Theta slabs with the propagation still in shared memory
+    "one_spin_slab": (ai.SystemSpec(150, 45, 0, 300, 20, True, 83), 2, 3, 0.005),
 }
 
 
@@ -175,6 +182,7 @@ def test_one_step_matches_oracle(name):
     ost2, d = oa.step(ham, ocfg, ost)
     g = ctx.state_arrays()
     _compare_state(g, ost2)
+    assert np.any(ost.weight > 0)                     # the step is not vacuous
     rec = ctx.history(1)[0]
     num, den = d["mixed"]
     assert abs(rec[0] / rec[1] - num / den) < E_TOL
