@@ -113,10 +113,18 @@ typedef struct {
     double mlp_mix;     /* probability of a random-walk move under AFQMC_PROPOSAL_MLP */
     double mlp_lr;      /* Adam learning rate of the proposal network */
     int mlp_train;      /* 1: after every step, one Adam step on the paths' states (online training) */
+    double refine_tol;  /* mixed precision, per-pair tensor-core form: per-walker energy tolerance (Ha) of
+                           the error-controlled refinement.  Each measurement estimates every pair's
+                           contraction error as (2/N) 2^-20 sum_g ||L_g||_2^2 ||Theta_p||_F^2 and recomputes
+                           in FP64 the pairs with the largest ||Theta_p||_F until the estimated error of the
+                           walker's average, 2 sqrt(sum of the kept pairs' squared errors) / |sum_p S_p|,
+                           is at most refine_tol / 2.  0 turns it off.  Default 1e-4.  Not used by the
+                           walker-side tensor-core form (N <= 64, n_up + n_dn <= 40), which keeps no Theta */
 } afqmc_config;
 
 /* Fill *cfg with defaults (combined constraint, prior proposal, FP64, Taylor
- * order 6, one sweep, 20 burn-in sweeps, kill threshold 1e-10) and zero sizes. */
+ * order 6, one sweep, 20 burn-in sweeps, kill threshold 1e-10, refine_tol 1e-4)
+ * and zero sizes. */
 void afqmc_config_default(afqmc_config* cfg);
 
 /* Bytes of device workspace the configuration needs (0 if cfg is invalid). */
@@ -169,7 +177,8 @@ afqmc_status afqmc_history(afqmc_ctx* ctx, double* out, int n, int* n_out);
 
 /* Statistics since init (synchronises); out[0..len) receives, as available:
  *   0 steps taken, 1 accepted moves, 2 proposed moves, 3 live walkers,
- *   4 device status word (0 = fine), 5 min weight, 6 max weight, 7 sum weight */
+ *   4 device status word (0 = fine), 5 min weight, 6 max weight, 7 sum weight,
+ *   8 pairs recomputed in FP64 by the refinement (see refine_tol) since init */
 afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len);
 
 /* Checkpoint.  The state buffer (host memory) is, in order, with no padding:

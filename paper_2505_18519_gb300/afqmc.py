@@ -33,7 +33,7 @@ class AfqmcConfig(ctypes.Structure):
         ("dtau", ctypes.c_double), ("pcn_beta", ctypes.c_double), ("e_shift", ctypes.c_double),
         ("kill_threshold", ctypes.c_double), ("seed", ctypes.c_uint64), ("walker_offset", ctypes.c_int64),
         ("rw_step", ctypes.c_double), ("mlp_mix", ctypes.c_double), ("mlp_lr", ctypes.c_double),
-        ("mlp_train", ctypes.c_int),
+        ("mlp_train", ctypes.c_int), ("refine_tol", ctypes.c_double),
     ]
 
 
@@ -136,7 +136,7 @@ def _check(st: int):
 def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_sweeps=1, n_burn=20,
                 constraint="combined", proposal="prior", precision="fp64", taylor_order=6, history_capacity=1024,
                 pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10, walker_offset=0, rw_step=0.3, mlp_mix=0.1,
-                mlp_lr=1e-3, mlp_train=False) -> AfqmcConfig:
+                mlp_lr=1e-3, mlp_train=False, refine_tol=1e-4) -> AfqmcConfig:
     lib = load_library()
     c = AfqmcConfig()
     lib.afqmc_config_default(ctypes.byref(c))
@@ -147,6 +147,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
     c.dtau, c.pcn_beta, c.e_shift, c.kill_threshold, c.seed = dtau, pcn_beta, e_shift, kill_threshold, seed
     c.walker_offset = walker_offset
     c.rw_step, c.mlp_mix, c.mlp_lr, c.mlp_train = rw_step, mlp_mix, mlp_lr, int(bool(mlp_train))
+    c.refine_tol = refine_tol
     return c
 
 
@@ -226,9 +227,10 @@ class Context:
         return out[: 4 * k.value].reshape(k.value, 4)
 
     def stats(self):
-        out = np.empty(8)
-        _check(load_library().afqmc_stats(self._ctx, out.ctypes.data, 8))
-        keys = ("steps", "accepted", "proposed", "live_walkers", "status", "min_weight", "max_weight", "sum_weight")
+        out = np.empty(9)
+        _check(load_library().afqmc_stats(self._ctx, out.ctypes.data, 9))
+        keys = ("steps", "accepted", "proposed", "live_walkers", "status", "min_weight", "max_weight", "sum_weight",
+                "refined_pairs")
         return dict(zip(keys, out.tolist()))
 
     def autotune(self):

@@ -159,6 +159,16 @@ extern "C" void afqmc_config_default(afqmc_config* c) {
     c->mlp_mix = 0.1;
     c->mlp_lr = 1e-3;
     c->mlp_train = 0;
+    c->refine_tol = 1e-4;
+}
+
+// The tensor-core contraction's pairs with the largest error get recomputed in
+// FP64 (refine.cu): mixed precision, the per-pair form (it keeps Theta), and a
+// positive per-walker tolerance.
+static bool refine_enabled(const afqmc_config* c) {
+    if (c->precision == AFQMC_PRECISION_FP64 || !(c->refine_tol > 0.0)) return false;
+    const bool f16 = c->precision == AFQMC_PRECISION_FP16X3;
+    return !contract_tc_walker_side(c->N, c->n_up, c->n_dn, f16) && contract_fp64_supported(c->N, c->n_up, c->n_dn);
 }
 
 static const char* check_config(const afqmc_config* c) {
@@ -182,6 +192,7 @@ static const char* check_config(const afqmc_config* c) {
     if (!(c->dtau > 0.0)) return "dtau must be > 0";
     if (c->proposal == AFQMC_PROPOSAL_PCN && !(c->pcn_beta > 0.0 && c->pcn_beta <= 1.0)) return "pcn_beta in (0, 1]";
     if (!(c->kill_threshold >= 0.0)) return "kill_threshold must be >= 0";
+    if (!(c->refine_tol >= 0.0)) return "refine_tol must be >= 0";
     if (c->walker_offset < 0 || (c->walker_offset + c->n_walkers) * (long long)c->n_paths > (1ll << 32))
         return "walker_offset out of range of the 32-bit stream entity";
     if (c->precision == AFQMC_PRECISION_FP64 && !contract_fp64_supported(c->N, c->n_up, c->n_dn))
@@ -249,6 +260,11 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.ebar = (double2*)take(W * 16);
     w.y = (double2*)take(W * G * 16);
     w.logshift = (double2*)take(W * 16);
+    const bool refine = refine_enabled(c);
+    w.refine_th2 = refine ? (double*)take(pairs * 8) : nullptr;
+    w.refine_items = refine ? (int*)take(pairs * 4) : nullptr;
+    w.refine_n = refine ? (int*)take(4) : nullptr;
+    w.refine_lam = refine ? (double*)take((G + 1) * 8) : nullptr;
     w.Aplanes = (double*)take(2 * W * NN * 8);
     w.phi_new = (double2*)take(W * N * nt * 16);
     w.propbuf = propagate_in_smem(d.N, d.nt) ? nullptr : (double2*)take(W * 2 * N * nt * 16);
@@ -391,9 +407,15 @@ static afqmc_status measure(afqmc_ctx* ctx) {
         CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
                       ovl));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
-    if (ctx->cfg.precision != AFQMC_PRECISION_FP64)
+    if (ctx->cfg.precision != AFQMC_PRECISION_FP64) {
         CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.vpair, w.epair, w.status, f16));
-    else if (ovl == OVL_INVERSE)
+        if (w.refine_items) {   // the pairs whose error would put their walker above refine_tol, in FP64
+            CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2, w.alive,
+                             w.refine_items, w.refine_n, w.counters));
+            CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n,
+                                    d.pairs));
+        }
+    } else if (ovl == OVL_INVERSE)
         CK(contract_fp64_walker(s, d, w.h, w.L, w.Phi, w.Theta, w.phi, w.vpair, w.epair));
     else
         CK(contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
@@ -446,6 +468,10 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
             (e = contract_tc_prepare(s, d.N, d.nu, d.nd, d.G, w.h, w.L, w.Lt,
                                      cfg->precision == AFQMC_PRECISION_FP16X3)) != cudaSuccess) {
             st = fail(AFQMC_ERR_CUDA, "tensor-core operand image: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (w.refine_lam && (e = refine_scale(s, d.N, d.G, w.L, w.refine_lam, w.refine_lam + d.G)) != cudaSuccess) {
+            st = fail(AFQMC_ERR_CUDA, "refinement scale: %s", cudaGetErrorString(e));
             break;
         }
         if ((e = one_body_propagator(s, d.N, d.G, cfg->dtau, w.h, w.L, w.T, w.scratchNN, w.expT)) != cudaSuccess) {
@@ -640,8 +666,9 @@ extern "C" afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len) {
     CK(cudaMemcpyAsync(ws4, ctx->ws.reduce + 4, sizeof ws4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(&status, ctx->ws.status, sizeof status, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    double v[8] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3]};
-    for (int i = 0; i < len && i < 8; ++i) out[i] = v[i];
+    double v[9] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3],
+                   (double)c[5]};
+    for (int i = 0; i < len && i < 9; ++i) out[i] = v[i];
     return AFQMC_OK;
 }
 

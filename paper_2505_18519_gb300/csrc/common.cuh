@@ -173,6 +173,11 @@ struct Workspace {
     double2* ebar;    // W
     double2* y;       // W*G   x - xbar
     double2* logshift;  // W  sum_g (xi xbar - xbar^2/2)
+    // error-controlled FP64 refinement of the tensor-core contraction (null when off)
+    double* refine_th2;   // W*P   ||Theta_p||_F^2
+    int* refine_items;    // W*P   pairs to recompute in FP64
+    int* refine_n;        // 1     their number
+    double* refine_lam;   // G+1   ||L_g||_2^2, then their sum at [G]
     double* Aplanes;  // 2W*N*N  rows 2w: sum_g Re(y) L_g ; 2w+1: sum_g Im(y) L_g
                       //         (double-float pairs, 8 bytes each, on the mixed-precision path)
     double2* phi_new; // W*N*nt

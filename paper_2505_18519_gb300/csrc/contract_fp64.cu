@@ -62,15 +62,17 @@ __host__ __device__ __forceinline__ Fp64Layout fp64_layout(int N, int nu, int nd
     return l;
 }
 
+// Block b computes pair b (items == nullptr, one block per pair), or, with a
+// device list items[0 .. *n_items), the listed pairs items[b], items[b + gridDim.x], ...
 template <bool SLAB>
 __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd, int G, int JB,
                                                            const double* __restrict__ h, const double* __restrict__ L,
                                                            const double* __restrict__ Phi, const double2* __restrict__ Theta,
-                                                           double2* __restrict__ vpair, double2* __restrict__ epair) {
+                                                           double2* __restrict__ vpair, double2* __restrict__ epair,
+                                                           const int* __restrict__ items, const int* __restrict__ n_items) {
     extern __shared__ double smc[];
     __shared__ double2 red[CT / 32];
     const int nt = nu + nd;
-    const long long pair = blockIdx.x;
     const Fp64Layout lay = fp64_layout(N, nu, nd, JB, SLAB);
     double* sPhi = smc;                                             // N x nu
     double2* sTh = reinterpret_cast<double2*>(smc + lay.oTh);       // N x nt (SLAB: JB x nt)
@@ -78,11 +80,6 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
     double* sR = smc + lay.oR;                                      // nu x JB
     double2* sM = reinterpret_cast<double2*>(smc + lay.oM);         // nu^2 + nd^2
     const int tid = threadIdx.x;
-    const double* gPhi = Phi + pair * (long long)N * nu;
-    const double2* gTh = Theta + pair * (long long)N * nt;
-    for (int e = tid; e < N * nu; e += CT) sPhi[e] = gPhi[e];
-    if (!SLAB)
-        for (int e = tid; e < N * nt; e += CT) sTh[e] = gTh[e];
     const int nM = nu * nu + nd * nd;
     // decode owned M entries: o < nu^2 -> spin up (a, b); else spin down
     int own_a[MAXOWN], own_b[MAXOWN], own_c[MAXOWN];
@@ -96,6 +93,14 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
         if (o < nu * nu) { own_a[r] = o / nu; own_b[r] = o % nu; own_c[r] = o % nu; }
         else { int q = o - nu * nu; own_a[r] = q / nd; own_b[r] = q % nd; own_c[r] = nu + q % nd; }
     }
+    const long long n_work = items ? (long long)*n_items : (long long)gridDim.x;
+    for (long long item = blockIdx.x; item < n_work; item += gridDim.x) {
+    const long long pair = items ? (long long)items[item] : item;
+    const double* gPhi = Phi + pair * (long long)N * nu;
+    const double2* gTh = Theta + pair * (long long)N * nt;
+    for (int e = tid; e < N * nu; e += CT) sPhi[e] = gPhi[e];
+    if (!SLAB)
+        for (int e = tid; e < N * nt; e += CT) sTh[e] = gTh[e];
     double2 e_acc = cmk(0.0, 0.0);   // thread 0 accumulates E_L
     __syncthreads();
     for (int g = -1; g < G; ++g) {
@@ -170,6 +175,8 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
         }
     }
     if (tid == 0) epair[pair] = e_acc;
+    __syncthreads();   // the next item overwrites shared memory
+    }
 }
 
 // ---------------------------------------------------------------- walker-side form
@@ -369,10 +376,13 @@ bool contract_fp64_supported(int N, int nu, int nd) {
     return contract_fp64_smem(N, nu, nd, JB) <= 220 * 1024 || contract_fp64_slab_smem(N, nu, nd, JB) <= 220 * 1024;
 }
 
-cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
-                          const double2* Theta, double2* vpair, double2* epair, long long pairs) {
+// blocks: one per pair without a list; with a list, at most that many items (the
+// grid is then the resident capacity of the GPU and each block loops over items).
+static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
+                               const double2* Theta, double2* vpair, double2* epair, long long blocks, const int* items,
+                               const int* n_items) {
     if (!contract_fp64_supported(d.N, d.nu, d.nd)) return cudaErrorInvalidValue;
-    if (pairs <= 0) return cudaSuccess;
+    if (blocks <= 0) return cudaSuccess;
     const int JB = contract_fp64_jb(d.N);
     size_t smem = contract_fp64_smem(d.N, d.nu, d.nd, JB);
     const bool slab = smem > 220 * 1024;
@@ -380,14 +390,35 @@ cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const 
     const void* k = slab ? (const void*)contract_fp64_kernel<true> : (const void*)contract_fp64_kernel<false>;
     cudaError_t e = raise_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
+    if (items) {
+        int dev = 0, sms = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, CT, smem);
+        if (e != cudaSuccess) return e;
+        const long long cap = (long long)sms * (per_sm > 0 ? per_sm : 1);
+        if (blocks > cap) blocks = cap;
+    }
     if (slab)
-        contract_fp64_kernel<true><<<(unsigned)pairs, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair,
-                                                                      epair);
+        contract_fp64_kernel<true><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair,
+                                                                      epair, items, n_items);
     else
-        contract_fp64_kernel<false><<<(unsigned)pairs, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair,
-                                                                       epair);
+        contract_fp64_kernel<false><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair,
+                                                                       epair, items, n_items);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
+                          const double2* Theta, double2* vpair, double2* epair, long long pairs) {
+    return launch_fp64(s, d, h, L, Phi, Theta, vpair, epair, pairs, nullptr, nullptr);
+}
+
+cudaError_t contract_fp64_listed(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
+                                 const double2* Theta, double2* vpair, double2* epair, const int* items,
+                                 const int* n_items, long long max_items) {
+    if (!items || !n_items) return cudaErrorInvalidValue;
+    return launch_fp64(s, d, h, L, Phi, Theta, vpair, epair, max_items, items, n_items);
 }
 
 }  // namespace afq

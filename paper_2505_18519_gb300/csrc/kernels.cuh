@@ -42,6 +42,20 @@ cudaError_t one_body_propagator(cudaStream_t s, int N, int G, double dtau, const
 cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                           const double2* Theta, double2* vpair, double2* epair, long long pairs);
 bool contract_fp64_supported(int N, int nu, int nd);
+// Error-controlled refinement of the tensor-core contraction (per-pair form):
+// lam = sum_g ||L_g||_2^2 (lam_g: G scratch values), once at init; per
+// measurement, the pairs each walker must recompute in FP64 so that its
+// estimated error stays below tol, appended to items (count in *n_items,
+// cumulative count in counters[5]).
+cudaError_t refine_scale(cudaStream_t s, int N, int G, const double* L, double* lam_g, double* lam);
+cudaError_t refine_select(cudaStream_t s, const Dims& d, double tol, const double* lam, const double2* logdet,
+                          const double2* Theta, double* th2, const int* alive, int* items, int* n_items,
+                          unsigned long long* counters);
+// The same contraction for the pairs items[0 .. *n_items) only (a device list of
+// pair indices, *n_items <= max_items), the others' vpair/epair left as they are.
+cudaError_t contract_fp64_listed(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
+                                 const double2* Theta, double2* vpair, double2* epair, const int* items,
+                                 const int* n_items, long long max_items);
 // Walker-side FP64 form (Y_g = X_g phi_w once per block of a walker's pairs,
 // Z = Phi_p^T Y_g, Q = Z A_p^-1; Tr Q and Tr Q^2 are those of M_g): needs A^-1
 // per pair and spin (overlap_lu with OVL_INVERSE) and the walkers.
