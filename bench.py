@@ -488,6 +488,51 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
                          "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
                          "flops_per_launch": flops, "ms_per_launch": cms},
             "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
+
+    if only in (None, "large_mixed"):
+        # the mixed-precision workload's system (N = 120, 24 + 24 electrons, 600 Cholesky
+        # vectors, 64 paths) on 128 walkers: per-walker error against the FP64 path from
+        # one state, with and without the error-controlled FP64 refinement, and step times
+        spec2, run2 = ai.CONFIGS["c2_n120"]
+        sy = ai.make_system(spec2)
+        W2, P2, st2 = 128, run2.n_paths, 2
+        res, state = {}, None
+        for key, prec, tol in (("fp64", "fp64", 1e-4), ("refined", "fp16x3", 1e-4), ("tensor_only", "fp16x3", 0.0)):
+            c = lib.make_config(spec2.N, spec2.n_up, spec2.n_dn, spec2.n_chol, spec2.K, W2, P2, run2.dtau,
+                                ai.philox_run_seed(2), n_burn=20, walker_offset=rank * W2, precision=prec,
+                                refine_tol=tol)
+            ctx = lib.Context(c, sy.h, sy.L, sy.Phi0, sy.U, device=dev)
+            if state is None:
+                state = ctx.save_state()
+            else:
+                ctx.load_state(state)
+            ew = ctx.energy(walkers=True)["e_walker"]
+            refined0 = ctx.stats()["refined_pairs"]
+            k = 1 if prec == "fp64" else st2
+            ctx.step(1)
+            ms, clocks, launches = _timed(ctx.step, lambda: torch.cuda.synchronize(dev), ctx.stream, k, world, local)
+            refined = ctx.stats()["refined_pairs"]
+            res[key] = dict(ew=ew, ms=ms / k, clocks=clocks, refined0=refined0,
+                            refined_per_step=(refined - refined0) / (k + 1), kernel=lib.contract_kernel(c))
+            ctx.close()
+        d = {"what": f"system of the mixed-precision workload (N = {spec2.N}, {spec2.n_up} + {spec2.n_dn} electrons, "
+                     f"n_chol = {spec2.n_chol}, K = {spec2.K}), {W2} walkers x {P2} paths after 20 burn-in sweeps; "
+                     "per-walker energy differences against the FP64 path at one common state; "
+                     f"{st2} timed steps per mixed context (1 for FP64) after 1 untimed step",
+             "unit": UNIT, "clocks": res["refined"]["clocks"], "kernel": res["refined"]["kernel"]}
+        for key in ("refined", "tensor_only", "fp64"):
+            r = res[key]
+            e = {"value": W2 * P2 * world / (r["ms"] / 1e3), "ms_per_step": r["ms"]}
+            if key != "fp64":
+                dw = np.abs(r["ew"] - res["fp64"]["ew"])
+                e["dE_walker_ha"] = {"max": float(dw.max()), "median": float(np.median(dw)),
+                                     "frac_above_1e-4": float(np.mean(dw > 1e-4))}
+            if key == "refined":
+                e["refined_pairs_at_common_state"] = int(r["refined0"])
+                e["refined_pairs_per_step"] = float(r["refined_per_step"])
+                e["refine_tol_ha"] = 1e-4
+            d[key] = e
+        out["large_mixed_sample"] = d
     return out
 
 
@@ -648,7 +693,7 @@ def main():
     ap.add_argument("--walkers", type=int, default=0, help="walkers per GPU (profiling runs on a small case)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision, learned-proposal and batched measurements")
-    ap.add_argument("--only", choices=("mixed", "learned", "batched", "largest"), default=None,
+    ap.add_argument("--only", choices=("mixed", "learned", "batched", "largest", "large_mixed"), default=None,
                     help="time one variant alone (profiling); skips the FP64 headline's extras")
     args = ap.parse_args()
     if args.impl == "reference":
