@@ -116,7 +116,8 @@ typedef struct {
     double refine_tol;  /* mixed precision, per-pair tensor-core form: per-walker energy tolerance (Ha) of
                            the error-controlled refinement.  Each measurement estimates every pair's
                            contraction error as (2/N) 2^-20 sum_g ||L_g||_2^2 ||Theta_p||_F^2 and recomputes
-                           in FP64 the pairs with the largest ||Theta_p||_F until the estimated error of the
+                           in double-float (FP32 pairs, about 44 bits) the pairs with the largest ||Theta_p||_F
+                           until the estimated error of the
                            walker's average, 2 sqrt(sum of the kept pairs' squared errors) / |sum_p S_p|,
                            is at most refine_tol / 2.  0 turns it off.  Default 1e-4.  Not used by the
                            walker-side tensor-core form (N <= 64, n_up + n_dn <= 40), which keeps no Theta */
@@ -178,7 +179,7 @@ afqmc_status afqmc_history(afqmc_ctx* ctx, double* out, int n, int* n_out);
 /* Statistics since init (synchronises); out[0..len) receives, as available:
  *   0 steps taken, 1 accepted moves, 2 proposed moves, 3 live walkers,
  *   4 device status word (0 = fine), 5 min weight, 6 max weight, 7 sum weight,
- *   8 pairs recomputed in FP64 by the refinement (see refine_tol) since init */
+ *   8 pairs recomputed by the refinement (see refine_tol) since init */
 afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len);
 
 /* Checkpoint.  The state buffer (host memory) is, in order, with no padding:

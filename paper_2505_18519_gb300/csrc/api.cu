@@ -409,11 +409,11 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64) {
         CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.vpair, w.epair, w.status, f16));
-        if (w.refine_items) {   // the pairs whose error would put their walker above refine_tol, in FP64
+        if (w.refine_items) {   // the pairs whose error would put their walker above refine_tol, again
             CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2, w.alive,
                              w.refine_items, w.refine_n, w.counters));
             CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n,
-                                    d.pairs));
+                                    d.pairs, /*df=*/true));
         }
     } else if (ovl == OVL_INVERSE)
         CK(contract_fp64_walker(s, d, w.h, w.L, w.Phi, w.Theta, w.phi, w.vpair, w.epair));

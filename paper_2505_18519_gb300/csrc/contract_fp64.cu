@@ -11,6 +11,7 @@
 // Theta does not fit (N = 200 with 40 + 40 electrons needs 256 KB), the SLAB
 // form keeps only the JB rows of Theta that the current column block of L_g
 // multiplies, loaded beside it (the pair's Theta stays in L2 across matrices).
+#include "df.cuh"
 #include "kernels.cuh"
 
 namespace afq {
@@ -64,7 +65,10 @@ __host__ __device__ __forceinline__ Fp64Layout fp64_layout(int N, int nu, int nd
 
 // Block b computes pair b (items == nullptr, one block per pair), or, with a
 // device list items[0 .. *n_items), the listed pairs items[b], items[b + gridDim.x], ...
-template <bool SLAB>
+// DF: R and M in double-float (FP32 pairs, Dot2 sums; about 44 significant
+// bits at FP32 instruction rates), the traces in FP64; shared memory holds the
+// same bytes (a double-float value takes 8 bytes like a double).
+template <bool SLAB, bool DF>
 __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd, int G, int JB,
                                                            const double* __restrict__ h, const double* __restrict__ L,
                                                            const double* __restrict__ Phi, const double2* __restrict__ Theta,
@@ -98,47 +102,99 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
     const long long pair = items ? (long long)items[item] : item;
     const double* gPhi = Phi + pair * (long long)N * nu;
     const double2* gTh = Theta + pair * (long long)N * nt;
-    for (int e = tid; e < N * nu; e += CT) sPhi[e] = gPhi[e];
+    dfl* const sPhiD = reinterpret_cast<dfl*>(sPhi);
+    float4* const sThD = reinterpret_cast<float4*>(sTh);   // (Re hi, Re lo, Im hi, Im lo)
+    dfl* const sLD = reinterpret_cast<dfl*>(sL);
+    dfl* const sRD = reinterpret_cast<dfl*>(sR);
+    for (int e = tid; e < N * nu; e += CT) {
+        if constexpr (DF) sPhiD[e] = df_from(gPhi[e]);
+        else sPhi[e] = gPhi[e];
+    }
     if (!SLAB)
-        for (int e = tid; e < N * nt; e += CT) sTh[e] = gTh[e];
+        for (int e = tid; e < N * nt; e += CT) {
+            if constexpr (DF) {
+                const double2 t = gTh[e];
+                const dfl re = df_from(t.x), im = df_from(t.y);
+                sThD[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            } else {
+                sTh[e] = gTh[e];
+            }
+        }
     double2 e_acc = cmk(0.0, 0.0);   // thread 0 accumulates E_L
     __syncthreads();
     for (int g = -1; g < G; ++g) {
         const double* Lg = (g < 0) ? h : L + (long long)g * N * N;
         double2 acc[MAXOWN];
+        float4 accd[MAXOWN];   // DF: (Re hi, Re lo, Im hi, Im lo)
 #pragma unroll
-        for (int r = 0; r < MAXOWN; ++r) acc[r] = cmk(0.0, 0.0);
+        for (int r = 0; r < MAXOWN; ++r) {
+            acc[r] = cmk(0.0, 0.0);
+            accd[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         for (int j0 = 0; j0 < N; j0 += JB) {
             int jb = min(JB, N - j0);
             for (int e = tid; e < N * jb; e += CT) {
                 int i = e / jb, j = e - i * jb;
-                sL[i * JB + j] = Lg[(long long)i * N + j0 + j];
+                if constexpr (DF) sLD[i * JB + j] = df_from(Lg[(long long)i * N + j0 + j]);
+                else sL[i * JB + j] = Lg[(long long)i * N + j0 + j];
             }
             if (SLAB)   // rows j0 .. j0 + jb - 1 of Theta, contiguous in global memory
-                for (int e = tid; e < jb * nt; e += CT) sTh[e] = gTh[(size_t)j0 * nt + e];
+                for (int e = tid; e < jb * nt; e += CT) {
+                    if constexpr (DF) {
+                        const double2 t = gTh[(size_t)j0 * nt + e];
+                        const dfl re = df_from(t.x), im = df_from(t.y);
+                        sThD[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+                    } else {
+                        sTh[e] = gTh[(size_t)j0 * nt + e];
+                    }
+                }
             __syncthreads();
             for (int e = tid; e < nu * jb; e += CT) {
                 int a = e / jb, j = e - a * jb;
-                double s = 0.0;
-                for (int i = 0; i < N; ++i) s = fma(sPhi[i * nu + a], sL[i * JB + j], s);
-                sR[a * JB + j] = s;
+                if constexpr (DF) {
+                    float sh = 0.f, sl = 0.f;
+                    for (int i = 0; i < N; ++i) dot2_fma(sh, sl, sPhiD[i * nu + a], sLD[i * JB + j]);
+                    sRD[a * JB + j] = df_two_sum(sh, sl);
+                } else {
+                    double s = 0.0;
+                    for (int i = 0; i < N; ++i) s = fma(sPhi[i * nu + a], sL[i * JB + j], s);
+                    sR[a * JB + j] = s;
+                }
             }
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < MAXOWN; ++r) {
                 if (r >= nown) break;
-                const double* Ra = sR + own_a[r] * JB;
-                const double2* Tc = sTh + (SLAB ? 0 : (size_t)j0 * nt) + own_c[r];
-                double2 s = acc[r];
-                for (int j = 0; j < jb; ++j) {
-                    double rv = Ra[j];
-                    double2 t = Tc[(size_t)j * nt];
-                    s.x = fma(rv, t.x, s.x);
-                    s.y = fma(rv, t.y, s.y);
+                if constexpr (DF) {
+                    const dfl* Ra = sRD + own_a[r] * JB;
+                    const float4* Tc = sThD + (SLAB ? 0 : (size_t)j0 * nt) + own_c[r];
+                    float4 s = accd[r];
+                    for (int j = 0; j < jb; ++j) {
+                        const dfl rv = Ra[j];
+                        const float4 t = Tc[(size_t)j * nt];
+                        dot2_fma(s.x, s.y, rv, dfl{t.x, t.y});
+                        dot2_fma(s.z, s.w, rv, dfl{t.z, t.w});
+                    }
+                    accd[r] = s;
+                } else {
+                    const double* Ra = sR + own_a[r] * JB;
+                    const double2* Tc = sTh + (SLAB ? 0 : (size_t)j0 * nt) + own_c[r];
+                    double2 s = acc[r];
+                    for (int j = 0; j < jb; ++j) {
+                        double rv = Ra[j];
+                        double2 t = Tc[(size_t)j * nt];
+                        s.x = fma(rv, t.x, s.x);
+                        s.y = fma(rv, t.y, s.y);
+                    }
+                    acc[r] = s;
                 }
-                acc[r] = s;
             }
             __syncthreads();
+        }
+        if constexpr (DF) {
+#pragma unroll
+            for (int r = 0; r < MAXOWN; ++r)
+                acc[r] = cmk((double)accd[r].x + (double)accd[r].y, (double)accd[r].z + (double)accd[r].w);
         }
         // traces
         double2 tr = cmk(0.0, 0.0);
@@ -378,6 +434,7 @@ bool contract_fp64_supported(int N, int nu, int nd) {
 
 // blocks: one per pair without a list; with a list, at most that many items (the
 // grid is then the resident capacity of the GPU and each block loops over items).
+template <bool DF>
 static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                                const double2* Theta, double2* vpair, double2* epair, long long blocks, const int* items,
                                const int* n_items) {
@@ -387,7 +444,7 @@ static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, c
     size_t smem = contract_fp64_smem(d.N, d.nu, d.nd, JB);
     const bool slab = smem > 220 * 1024;
     if (slab) smem = contract_fp64_slab_smem(d.N, d.nu, d.nd, JB);
-    const void* k = slab ? (const void*)contract_fp64_kernel<true> : (const void*)contract_fp64_kernel<false>;
+    const void* k = slab ? (const void*)contract_fp64_kernel<true, DF> : (const void*)contract_fp64_kernel<false, DF>;
     cudaError_t e = raise_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
     if (items) {
@@ -400,25 +457,26 @@ static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, c
         if (blocks > cap) blocks = cap;
     }
     if (slab)
-        contract_fp64_kernel<true><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair,
-                                                                      epair, items, n_items);
+        contract_fp64_kernel<true, DF><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta,
+                                                                          vpair, epair, items, n_items);
     else
-        contract_fp64_kernel<false><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta, vpair,
-                                                                       epair, items, n_items);
+        contract_fp64_kernel<false, DF><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta,
+                                                                           vpair, epair, items, n_items);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                           const double2* Theta, double2* vpair, double2* epair, long long pairs) {
-    return launch_fp64(s, d, h, L, Phi, Theta, vpair, epair, pairs, nullptr, nullptr);
+    return launch_fp64<false>(s, d, h, L, Phi, Theta, vpair, epair, pairs, nullptr, nullptr);
 }
 
 cudaError_t contract_fp64_listed(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                                  const double2* Theta, double2* vpair, double2* epair, const int* items,
-                                 const int* n_items, long long max_items) {
+                                 const int* n_items, long long max_items, bool df) {
     if (!items || !n_items) return cudaErrorInvalidValue;
-    return launch_fp64(s, d, h, L, Phi, Theta, vpair, epair, max_items, items, n_items);
+    return df ? launch_fp64<true>(s, d, h, L, Phi, Theta, vpair, epair, max_items, items, n_items)
+              : launch_fp64<false>(s, d, h, L, Phi, Theta, vpair, epair, max_items, items, n_items);
 }
 
 }  // namespace afq

@@ -1,5 +1,8 @@
-// Error-controlled FP64 refinement of the tensor-core contraction (mixed
-// precision, per-pair form).
+// Error-controlled refinement of the tensor-core contraction (mixed precision,
+// per-pair form): the pairs that would put their walker's energy outside the
+// tolerance are recomputed by the per-pair contraction kernel in double-float
+// arithmetic (FP32 pairs, about 44 significant bits: some 2^24 times below the
+// split-FP16 error, at FP32 instruction rates).
 //
 // The split-FP16 contraction carries about 20 significant bits per operand.
 // Its local-energy error grows with the conditioning of the overlap: for pair p
@@ -10,7 +13,7 @@
 // sign-weighted average (Eq. (27)) is estimated as
 //   eps_w = 2 sqrt(sum_p sigma_p^2) / |sum_p S_p|
 // over the pairs whose tensor-core values it keeps.  Per walker, the pairs are
-// taken in decreasing ||Theta_p||_F and recomputed in FP64 until eps_w <= tol / 2,
+// taken in decreasing ||Theta_p||_F and recomputed until eps_w <= tol / 2,
 // so the walker's error stays below tol.  The model and its constant 2 / N were
 // fitted to the measured per-pair errors of systems with N = 50 .. 120.
 #include "kernels.cuh"

@@ -144,8 +144,8 @@ def test_large_workload_against_fp64_gpu_path(n_burn):
     120 Metropolis sweeps, mixed path against the FP64 GPU path (which the
     other tests pin to the oracle) from the same state.  The split-FP16
     contraction's error grows with ||Theta_p||_F (nearly singular overlaps make
-    the Coulomb and exchange sums cancel); with the error-controlled FP64
-    refinement every walker meets the 1e-4 Ha target, which the tensor-core
+    the Coulomb and exchange sums cancel); with the error-controlled refinement
+    every walker meets the 1e-4 Ha target, which the tensor-core
     values alone miss for the worst walkers (printed for the record)."""
     spec, run = ai.CONFIGS["c2_n120"]
     s = ai.make_system(spec)
@@ -178,10 +178,11 @@ def test_large_workload_against_fp64_gpu_path(n_burn):
     assert 0 < refined < 0.25 * W * P            # a small share of the pairs
 
 
-def test_refining_every_pair_gives_the_fp64_contraction():
-    """With a vanishing tolerance every pair is recomputed in FP64 (the listed
-    form of the per-pair FP64 kernel), so the mixed path's per-pair energies and
-    force biases match the oracle to the FP64 path's 1e-9."""
+def test_refining_every_pair_matches_the_oracle():
+    """With a vanishing tolerance every pair is recomputed by the refinement
+    (the per-pair contraction kernel in double-float, walking a device list of
+    pairs), so the mixed path's per-pair energies and force biases match the
+    oracle to the FP64 path's 1e-9."""
     spec, W, P, dtau = SYSTEMS["n70_two_k_blocks"]
     s, ctx = _ctx(spec, W, P, dtau, 650, "fp16x3", n_burn=2, refine_tol=1e-300)
     assert lib.contract_kernel(ctx.cfg) == "contract_tc_kernel"
