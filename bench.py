@@ -444,6 +444,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         b.sync()
         ms, clocks, launches = _timed(b.step, b.sync, b.stream, steps, world, local)
         stats = [c.stats() for c in ctxs]
+        refined = sum(st["refined_pairs"] for st in stats) / (warmup + steps)
         b.close()
         for c in ctxs:
             c.close()
@@ -455,6 +456,9 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             "value": units * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "gpu_launches": launches, "clocks": clocks,
             "live_walkers_frac": sum(st["live_walkers"] for st in stats) / (len(specs) * Wb),
+            "refined_pairs_per_step": refined, "refined_frac": refined / (len(specs) * Wb * Pb),
+            "refine_tol_ha": 1e-4,
+            "tensor_core_forms": sorted({lib.contract_kernel(c.cfg) for c in ctxs}),
             "device_status_words": [int(st["status"]) for st in stats],
             "status_bits": "1 singular overlap, 2 non-finite value (the walker is removed), 4 tensor-core wait timed out"}
 

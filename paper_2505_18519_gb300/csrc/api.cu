@@ -238,7 +238,8 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.expT = (double*)take(NN * 8);
     // the double-float propagation needs its work arrays in shared memory
     const bool prop_df = c->precision != AFQMC_PRECISION_FP64 && propagate_in_smem(d.N, d.nt);
-    w.Ldf = prop_df ? take(G * NN * 8) : nullptr;
+    w.Ldf = prop_df || refine_enabled(c) ? take(G * NN * 8) : nullptr;
+    w.hdf = refine_enabled(c) ? take(NN * 8) : nullptr;
     w.expTdf = prop_df ? take(NN * 8) : nullptr;
     w.scratchNN = (double*)take(3 * NN * 8);
     w.Lt = c->precision != AFQMC_PRECISION_FP64
@@ -413,7 +414,7 @@ static afqmc_status measure(afqmc_ctx* ctx) {
             CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2, w.alive,
                              w.refine_items, w.refine_n, w.counters));
             CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n,
-                                    d.pairs, /*df=*/true));
+                                    d.pairs, w.hdf, w.Ldf));
         }
     } else if (ovl == OVL_INVERSE)
         CK(contract_fp64_walker(s, d, w.h, w.L, w.Phi, w.Theta, w.phi, w.vpair, w.epair));
@@ -482,6 +483,7 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         fill_normals(s, w.xprop, d.W, d.K, p.woff, p.seed, TAG_INIT_WALKER, w.counters, 0);
         if (w.Udf && ((e = u_to_df(s, (long long)d.K * NN, w.U, w.Udf)) != cudaSuccess ||
                       (w.Ldf && (e = u_to_df(s, (long long)d.G * NN, w.L, w.Ldf)) != cudaSuccess) ||
+                      (w.hdf && (e = u_to_df(s, (long long)NN, w.h, w.hdf)) != cudaSuccess) ||
                       (w.expTdf && (e = u_to_df(s, (long long)NN, w.expT, w.expTdf)) != cudaSuccess))) {
             st = fail(AFQMC_ERR_CUDA, "double-float copies of U, L and exp(-tau T/2): %s", cudaGetErrorString(e));
             break;
@@ -540,7 +542,7 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         if (st != AFQMC_OK) return st;
         if ((st = measure(ctx)) != AFQMC_OK) return st;      // Eq. (25)-(27), (16) at phi
         CK(fields(s, d, p, w.counters, w.vbar, w.sumS, w.weight, w.alive, (double*)w.y, w.logshift));
-        if (w.Ldf) {   // mixed precision: field planes and propagation in double-float
+        if (w.expTdf) {   // mixed precision: field planes and propagation in double-float
             CK(gemm_df(s, 2 * d.W, d.N * d.N, d.G, (const double*)w.y, w.Ldf, w.Aplanes));
         } else {
             gemm_nn_f64(s, 2 * d.W, d.N * d.N, d.G, 1.0, (const double*)w.y, d.G, w.L, (long long)d.N * d.N, 0.0,
@@ -548,7 +550,7 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
             CK(cudaGetLastError());
         }
         if ((st = prof_mark(ctx, PH_FIELDS)) != AFQMC_OK) return st;
-        if (w.Ldf)
+        if (w.expTdf)
             CK(propagate_df(s, d, p, w.expTdf, w.Aplanes, w.phi, w.phi_new, w.alive));  // Eq. (12)
         else
             CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive, w.propbuf));   // Eq. (12)

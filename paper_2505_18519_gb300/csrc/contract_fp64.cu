@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
                                                            const double* __restrict__ h, const double* __restrict__ L,
                                                            const double* __restrict__ Phi, const double2* __restrict__ Theta,
                                                            double2* __restrict__ vpair, double2* __restrict__ epair,
-                                                           const int* __restrict__ items, const int* __restrict__ n_items) {
+                                                           const int* __restrict__ items, const int* __restrict__ n_items,
+                                                           const dfl* __restrict__ hdf, const dfl* __restrict__ Ldf) {
     extern __shared__ double smc[];
     __shared__ double2 red[CT / 32];
     const int nt = nu + nd;
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
     __syncthreads();
     for (int g = -1; g < G; ++g) {
         const double* Lg = (g < 0) ? h : L + (long long)g * N * N;
+        const dfl* LgD = DF ? ((g < 0) ? hdf : Ldf + (long long)g * N * N) : nullptr;
         double2 acc[MAXOWN];
         float4 accd[MAXOWN];   // DF: (Re hi, Re lo, Im hi, Im lo)
 #pragma unroll
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
             int jb = min(JB, N - j0);
             for (int e = tid; e < N * jb; e += CT) {
                 int i = e / jb, j = e - i * jb;
-                if constexpr (DF) sLD[i * JB + j] = df_from(Lg[(long long)i * N + j0 + j]);
+                if constexpr (DF) sLD[i * JB + j] = LgD[(long long)i * N + j0 + j];
                 else sL[i * JB + j] = Lg[(long long)i * N + j0 + j];
             }
             if (SLAB)   // rows j0 .. j0 + jb - 1 of Theta, contiguous in global memory
@@ -437,7 +439,8 @@ bool contract_fp64_supported(int N, int nu, int nd) {
 template <bool DF>
 static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                                const double2* Theta, double2* vpair, double2* epair, long long blocks, const int* items,
-                               const int* n_items) {
+                               const int* n_items, const dfl* hdf = nullptr, const dfl* Ldf = nullptr) {
+    if (DF && (!hdf || !Ldf)) return cudaErrorInvalidValue;
     if (!contract_fp64_supported(d.N, d.nu, d.nd)) return cudaErrorInvalidValue;
     if (blocks <= 0) return cudaSuccess;
     const int JB = contract_fp64_jb(d.N);
@@ -458,10 +461,10 @@ static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, c
     }
     if (slab)
         contract_fp64_kernel<true, DF><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta,
-                                                                          vpair, epair, items, n_items);
+                                                                          vpair, epair, items, n_items, hdf, Ldf);
     else
         contract_fp64_kernel<false, DF><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta,
-                                                                           vpair, epair, items, n_items);
+                                                                           vpair, epair, items, n_items, hdf, Ldf);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -473,10 +476,12 @@ cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const 
 
 cudaError_t contract_fp64_listed(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                                  const double2* Theta, double2* vpair, double2* epair, const int* items,
-                                 const int* n_items, long long max_items, bool df) {
+                                 const int* n_items, long long max_items, const void* hdf, const void* Ldf) {
     if (!items || !n_items) return cudaErrorInvalidValue;
-    return df ? launch_fp64<true>(s, d, h, L, Phi, Theta, vpair, epair, max_items, items, n_items)
-              : launch_fp64<false>(s, d, h, L, Phi, Theta, vpair, epair, max_items, items, n_items);
+    if (hdf || Ldf)
+        return launch_fp64<true>(s, d, h, L, Phi, Theta, vpair, epair, max_items, items, n_items,
+                                 static_cast<const dfl*>(hdf), static_cast<const dfl*>(Ldf));
+    return launch_fp64<false>(s, d, h, L, Phi, Theta, vpair, epair, max_items, items, n_items);
 }
 
 }  // namespace afq

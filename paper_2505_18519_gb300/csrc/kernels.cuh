@@ -53,10 +53,12 @@ cudaError_t refine_select(cudaStream_t s, const Dims& d, double tol, const doubl
                           unsigned long long* counters);
 // The same contraction for the pairs items[0 .. *n_items) only (a device list of
 // pair indices, *n_items <= max_items), the others' vpair/epair left as they are;
-// df: R and M in double-float arithmetic instead of FP64 (about 44 bits).
+// with hdf and Ldf (double-float copies of h and L from u_to_df) R and M run in
+// double-float arithmetic instead of FP64 (about 44 bits).
 cudaError_t contract_fp64_listed(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                                  const double2* Theta, double2* vpair, double2* epair, const int* items,
-                                 const int* n_items, long long max_items, bool df);
+                                 const int* n_items, long long max_items, const void* hdf = nullptr,
+                                 const void* Ldf = nullptr);
 // Walker-side FP64 form (Y_g = X_g phi_w once per block of a walker's pairs,
 // Z = Phi_p^T Y_g, Q = Z A_p^-1; Tr Q and Tr Q^2 are those of M_g): needs A^-1
 // per pair and spin (overlap_lu with OVL_INVERSE) and the walkers.
