@@ -68,8 +68,11 @@ __host__ __device__ __forceinline__ Fp64Layout fp64_layout(int N, int nu, int nd
 // DF: R and M in double-float (FP32 pairs, Dot2 sums; about 44 significant
 // bits at FP32 instruction rates), the traces in FP64; shared memory holds the
 // same bytes (a double-float value takes 8 bytes like a double).
-template <bool SLAB, bool DF>
-__global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd, int G, int JB,
+// OWN: M entries owned per thread (n_up^2 + n_dn^2 <= OWN * CT); the double-float
+// mode with OWN = 8 fits two blocks per SM (slab layout, at most 128 registers;
+// the FP64 instances keep the same 128-register budget).
+template <bool SLAB, bool DF, int OWN>
+__global__ void __launch_bounds__(CT, (DF && OWN > 8) ? 1 : 2) contract_fp64_kernel(int N, int nu, int nd, int G, int JB,
                                                            const double* __restrict__ h, const double* __restrict__ L,
                                                            const double* __restrict__ Phi, const double2* __restrict__ Theta,
                                                            double2* __restrict__ vpair, double2* __restrict__ epair,
@@ -87,10 +90,10 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
     const int tid = threadIdx.x;
     const int nM = nu * nu + nd * nd;
     // decode owned M entries: o < nu^2 -> spin up (a, b); else spin down
-    int own_a[MAXOWN], own_b[MAXOWN], own_c[MAXOWN];
+    int own_a[OWN], own_b[OWN], own_c[OWN];
     int nown = 0;
 #pragma unroll
-    for (int r = 0; r < MAXOWN; ++r) {
+    for (int r = 0; r < OWN; ++r) {
         int o = tid + r * CT;
         own_a[r] = own_b[r] = own_c[r] = 0;
         if (o >= nM) continue;
@@ -111,25 +114,21 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
         if constexpr (DF) sPhiD[e] = df_from(gPhi[e]);
         else sPhi[e] = gPhi[e];
     }
+    const float4* gThD = reinterpret_cast<const float4*>(gTh);   // DF: Theta already as FP32 pairs
     if (!SLAB)
         for (int e = tid; e < N * nt; e += CT) {
-            if constexpr (DF) {
-                const double2 t = gTh[e];
-                const dfl re = df_from(t.x), im = df_from(t.y);
-                sThD[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
-            } else {
-                sTh[e] = gTh[e];
-            }
+            if constexpr (DF) sThD[e] = gThD[e];
+            else sTh[e] = gTh[e];
         }
     double2 e_acc = cmk(0.0, 0.0);   // thread 0 accumulates E_L
     __syncthreads();
     for (int g = -1; g < G; ++g) {
         const double* Lg = (g < 0) ? h : L + (long long)g * N * N;
         const dfl* LgD = DF ? ((g < 0) ? hdf : Ldf + (long long)g * N * N) : nullptr;
-        double2 acc[MAXOWN];
-        float4 accd[MAXOWN];   // DF: (Re hi, Re lo, Im hi, Im lo)
+        double2 acc[OWN];
+        float4 accd[OWN];   // DF: (Re hi, Re lo, Im hi, Im lo)
 #pragma unroll
-        for (int r = 0; r < MAXOWN; ++r) {
+        for (int r = 0; r < OWN; ++r) {
             acc[r] = cmk(0.0, 0.0);
             accd[r] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -142,13 +141,8 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
             }
             if (SLAB)   // rows j0 .. j0 + jb - 1 of Theta, contiguous in global memory
                 for (int e = tid; e < jb * nt; e += CT) {
-                    if constexpr (DF) {
-                        const double2 t = gTh[(size_t)j0 * nt + e];
-                        const dfl re = df_from(t.x), im = df_from(t.y);
-                        sThD[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
-                    } else {
-                        sTh[e] = gTh[(size_t)j0 * nt + e];
-                    }
+                    if constexpr (DF) sThD[e] = gThD[(size_t)j0 * nt + e];
+                    else sTh[e] = gTh[(size_t)j0 * nt + e];
                 }
             __syncthreads();
             for (int e = tid; e < nu * jb; e += CT) {
@@ -165,7 +159,7 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
             }
             __syncthreads();
 #pragma unroll
-            for (int r = 0; r < MAXOWN; ++r) {
+            for (int r = 0; r < OWN; ++r) {
                 if (r >= nown) break;
                 if constexpr (DF) {
                     const dfl* Ra = sRD + own_a[r] * JB;
@@ -195,13 +189,13 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
         }
         if constexpr (DF) {
 #pragma unroll
-            for (int r = 0; r < MAXOWN; ++r)
+            for (int r = 0; r < OWN; ++r)
                 acc[r] = cmk((double)accd[r].x + (double)accd[r].y, (double)accd[r].z + (double)accd[r].w);
         }
         // traces
         double2 tr = cmk(0.0, 0.0);
 #pragma unroll
-        for (int r = 0; r < MAXOWN; ++r) {
+        for (int r = 0; r < OWN; ++r) {
             if (r >= nown) break;
             int o = tid + r * CT;
             sM[o] = acc[r];
@@ -211,7 +205,7 @@ __global__ void __launch_bounds__(CT) contract_fp64_kernel(int N, int nu, int nd
         double2 ex = cmk(0.0, 0.0);
         if (g >= 0) {
 #pragma unroll
-            for (int r = 0; r < MAXOWN; ++r) {
+            for (int r = 0; r < OWN; ++r) {
                 if (r >= nown) break;
                 int o = tid + r * CT;
                 int a = own_a[r], b = own_b[r];
@@ -434,20 +428,29 @@ bool contract_fp64_supported(int N, int nu, int nd) {
     return contract_fp64_smem(N, nu, nd, JB) <= 220 * 1024 || contract_fp64_slab_smem(N, nu, nd, JB) <= 220 * 1024;
 }
 
+// Theta of the listed pairs to double-float pairs (Re hi, Re lo, Im hi, Im lo), in
+// place: the listed pairs' Theta is read again only by the double-float launch.
+__global__ void theta_to_df_kernel(int nn, const int* __restrict__ items, const int* __restrict__ n_items,
+                                   double2* Theta) {
+    const long long n = *n_items;
+    for (long long it = blockIdx.x; it < n; it += gridDim.x) {
+        double2* T = Theta + (long long)items[it] * nn;
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const double2 t = T[e];
+            const dfl re = df_from(t.x), im = df_from(t.y);
+            reinterpret_cast<float4*>(T)[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+    }
+}
+
 // blocks: one per pair without a list; with a list, at most that many items (the
 // grid is then the resident capacity of the GPU and each block loops over items).
-template <bool DF>
-static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
-                               const double2* Theta, double2* vpair, double2* epair, long long blocks, const int* items,
-                               const int* n_items, const dfl* hdf = nullptr, const dfl* Ldf = nullptr) {
-    if (DF && (!hdf || !Ldf)) return cudaErrorInvalidValue;
-    if (!contract_fp64_supported(d.N, d.nu, d.nd)) return cudaErrorInvalidValue;
-    if (blocks <= 0) return cudaSuccess;
-    const int JB = contract_fp64_jb(d.N);
-    size_t smem = contract_fp64_smem(d.N, d.nu, d.nd, JB);
-    const bool slab = smem > 220 * 1024;
-    if (slab) smem = contract_fp64_slab_smem(d.N, d.nu, d.nd, JB);
-    const void* k = slab ? (const void*)contract_fp64_kernel<true, DF> : (const void*)contract_fp64_kernel<false, DF>;
+template <bool SLAB, bool DF, int OWN>
+static cudaError_t launch_fp64_shape(cudaStream_t s, const Dims& d, int JB, size_t smem, const double* h,
+                                     const double* L, const double* Phi, const double2* Theta, double2* vpair,
+                                     double2* epair, long long blocks, const int* items, const int* n_items,
+                                     const dfl* hdf, const dfl* Ldf) {
+    const void* k = (const void*)contract_fp64_kernel<SLAB, DF, OWN>;
     cudaError_t e = raise_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
     if (items) {
@@ -459,14 +462,38 @@ static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, c
         const long long cap = (long long)sms * (per_sm > 0 ? per_sm : 1);
         if (blocks > cap) blocks = cap;
     }
-    if (slab)
-        contract_fp64_kernel<true, DF><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta,
-                                                                          vpair, epair, items, n_items, hdf, Ldf);
-    else
-        contract_fp64_kernel<false, DF><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta,
+    contract_fp64_kernel<SLAB, DF, OWN><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta,
                                                                            vpair, epair, items, n_items, hdf, Ldf);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <bool DF>
+static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
+                               const double2* Theta, double2* vpair, double2* epair, long long blocks, const int* items,
+                               const int* n_items, const dfl* hdf = nullptr, const dfl* Ldf = nullptr) {
+    if (DF && (!hdf || !Ldf || !items)) return cudaErrorInvalidValue;
+    if (!contract_fp64_supported(d.N, d.nu, d.nd)) return cudaErrorInvalidValue;
+    if (blocks <= 0) return cudaSuccess;
+    const int JB = contract_fp64_jb(d.N);
+    if (DF) {   // always the slab layout (half the shared memory); Theta converted first
+        theta_to_df_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, s>>>(
+            d.N * d.nt, items, n_items, const_cast<double2*>(Theta));
+        count_launches(1);
+        const size_t smem = contract_fp64_slab_smem(d.N, d.nu, d.nd, JB);
+        if (d.nu * d.nu + d.nd * d.nd <= 8 * CT)
+            return launch_fp64_shape<true, true, 8>(s, d, JB, smem, h, L, Phi, Theta, vpair, epair, blocks, items,
+                                                    n_items, hdf, Ldf);
+        return launch_fp64_shape<true, true, MAXOWN>(s, d, JB, smem, h, L, Phi, Theta, vpair, epair, blocks, items,
+                                                     n_items, hdf, Ldf);
+    }
+    const size_t smem = contract_fp64_smem(d.N, d.nu, d.nd, JB);
+    if (smem > 220 * 1024)
+        return launch_fp64_shape<true, false, MAXOWN>(s, d, JB, contract_fp64_slab_smem(d.N, d.nu, d.nd, JB), h, L,
+                                                      Phi, Theta, vpair, epair, blocks, items, n_items, nullptr,
+                                                      nullptr);
+    return launch_fp64_shape<false, false, MAXOWN>(s, d, JB, smem, h, L, Phi, Theta, vpair, epair, blocks, items,
+                                                   n_items, nullptr, nullptr);
 }
 
 cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
