@@ -94,18 +94,18 @@ def make_system(spec: SystemSpec) -> System:
     return System(spec, h, L, np.ascontiguousarray(Phi0), U)
 
 
-def philox_run_seed(config_index: int) -> int:
+def philox_run_seed(workload_index: int) -> int:
     """64-bit key of the counter-based random streams for a named workload."""
-    return 0x5EED0000 + config_index
+    return 0x5EED0000 + workload_index
 
 
 # The five workloads (small FP64, medium FP64, mixed precision, batched uneven,
 # learned proposal).  Walker counts, path counts, time step and step counts.
 CONFIGS = {
-    "c0_n8": (SystemSpec(8, 4, 4, 32, 8, False, 1000), RunSpec(64, 16, 0.01, 200)),
-    "c1_n50": (SystemSpec(50, 10, 10, 250, 50, True, 1001), RunSpec(512, 32, 0.005, 500)),
-    "c2_n120": (SystemSpec(120, 24, 24, 600, 120, True, 1002), RunSpec(1024, 64, 0.005, 500)),
-    "c4_n200": (SystemSpec(200, 40, 40, 1000, 200, True, 1004), RunSpec(2048, 16, 0.005, 500)),
+    "small_n8": (SystemSpec(8, 4, 4, 32, 8, False, 1000), RunSpec(64, 16, 0.01, 200)),
+    "medium_n50": (SystemSpec(50, 10, 10, 250, 50, True, 1001), RunSpec(512, 32, 0.005, 500)),
+    "large_n120": (SystemSpec(120, 24, 24, 600, 120, True, 1002), RunSpec(1024, 64, 0.005, 500)),
+    "largest_n200": (SystemSpec(200, 40, 40, 1000, 200, True, 1004), RunSpec(2048, 16, 0.005, 500)),
 }
 
 

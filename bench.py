@@ -33,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "c1_n50"
+WORKLOAD = "medium_n50"
 METRIC = "walker-sample steps/s incl. local energy"
 UNIT = "walker-sample steps/s"
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 4 FP64 flop/clk
@@ -230,7 +230,7 @@ def kernel_digest(kernel_source: str, end_marker: str = "size_t contract_fp64_sm
     return hashlib.sha256(text[begin:cut + 1] if cut >= 0 else text[begin:]).hexdigest()[:16]
 
 
-def recorded_traffic(kernel_source: str, summary: str = "contract_fp64_c1_n50.md",
+def recorded_traffic(kernel_source: str, summary: str = "contract_fp64_medium_n50.md",
                      end_marker: str = "size_t contract_fp64_smem", start_marker: str = None):
     """DRAM bytes per launch of a contraction kernel from its committed ncu
     summary, or None if the kernel's device code changed since the counters
@@ -280,11 +280,11 @@ def _timed(step, sync, stream, steps, world, local):
 
 FP64_WALKER_SIDE = "// ---------------------------------------------------------------- walker-side form"
 FP64_TRAFFIC = {   # kernel -> (committed summary, end of its device code, start of it), for the medium workload
-    "contract_fp64_kernel": ("contract_fp64_c1_n50.md", FP64_WALKER_SIDE, None),
-    "contract_fp64z_kernel": ("contract_fp64z_c1_n50.md", "size_t contract_fp64_smem", FP64_WALKER_SIDE),
+    "contract_fp64_kernel": ("contract_fp64_medium_n50.md", FP64_WALKER_SIDE, None),
+    "contract_fp64z_kernel": ("contract_fp64z_medium_n50.md", "size_t contract_fp64_smem", FP64_WALKER_SIDE),
 }
 TC_TRAFFIC = {   # kernel -> (committed summary, end of its device code), for the medium workload
-    "contract_tcy_kernel": ("contract_tcy_c1_n50.md", "static size_t tcy_smem_bytes"),
+    "contract_tcy_kernel": ("contract_tcy_medium_n50.md", "static size_t tcy_smem_bytes"),
 }
 
 
@@ -466,7 +466,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         # the largest system (N = 200, 40 + 40 electrons, 1000 Cholesky vectors) in FP64 on a
         # bounded sample: 19 walkers x 16 paths = 304 pairs, two full waves of the per-pair
         # kernel (one block per SM), 1 warm-up and 2 timed steps
-        spec4, run4 = ai.CONFIGS["c4_n200"]
+        spec4, run4 = ai.CONFIGS["largest_n200"]
         sy = ai.make_system(spec4)
         W4, P4, st4 = 19, run4.n_paths, 2
         c = lib.make_config(spec4.N, spec4.n_up, spec4.n_dn, spec4.n_chol, spec4.K, W4, P4, run4.dtau,
@@ -497,7 +497,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         # the mixed-precision workload's system (N = 120, 24 + 24 electrons, 600 Cholesky
         # vectors, 64 paths) on 128 walkers: per-walker error against the FP64 path from
         # one state, with and without the error-controlled FP64 refinement, and step times
-        spec2, run2 = ai.CONFIGS["c2_n120"]
+        spec2, run2 = ai.CONFIGS["large_n120"]
         sy = ai.make_system(spec2)
         W2, P2, st2 = 128, run2.n_paths, 2
         res, state = {}, None

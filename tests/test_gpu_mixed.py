@@ -126,7 +126,7 @@ def test_mixed_step_matches_oracle_given_its_force_bias(name):
 def test_mixed_trajectory_tracks_fp64_gpu_path():
     """Same seed and inputs, 10 steps of the medium system (64 walkers x 32
     paths) on both paths: the per-step mixed energies stay within 0.1 mHa."""
-    spec = ai.CONFIGS["c1_n50"][0]
+    spec = ai.CONFIGS["medium_n50"][0]
     hist = {}
     for prec in ("fp64", "fp16x3"):
         s, ctx = _ctx(spec, 64, 32, 0.005, 4321, prec, n_burn=5, e_shift=28.5)
@@ -147,7 +147,7 @@ def test_large_workload_against_fp64_gpu_path(n_burn):
     the Coulomb and exchange sums cancel); with the error-controlled refinement
     every walker meets the 1e-4 Ha target, which the tensor-core
     values alone miss for the worst walkers (printed for the record)."""
-    spec, run = ai.CONFIGS["c2_n120"]
+    spec, run = ai.CONFIGS["large_n120"]
     s = ai.make_system(spec)
     W, P = 32, run.n_paths
     res, refined = {}, None
@@ -208,7 +208,7 @@ def test_refinement_selects_the_pairs_of_its_rule():
     ||Theta_p||_F^2 until 2 sqrt(sum_kept sigma_p^2) / |sum_p S_p| <= tol / 2 with
     sigma_p = (2/N) 2^-20 sum_g ||L_g||_2^2 ||Theta_p||_F^2 (spectral norms from
     numpy here, power iteration on the GPU)."""
-    spec, run = ai.CONFIGS["c2_n120"]
+    spec, run = ai.CONFIGS["large_n120"]
     s = ai.make_system(spec)
     W, P, tol = 8, run.n_paths, 1e-4
     cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, ai.philox_run_seed(3),

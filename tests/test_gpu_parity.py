@@ -102,7 +102,7 @@ SYSTEMS = {
     # system, few walkers): Theta streamed in row slabs through the contraction, the
     # propagation's work arrays in global memory, a ragged last column block (200 = 6 x 32 + 8).
     # Two walkers, as the phaseless constraint kills one of them in the first step here
-    "c4_shape": (ai.CONFIGS["c4_n200"][0], 2, 2, 0.005),
+    "c4_shape": (ai.CONFIGS["largest_n200"][0], 2, 2, 0.005),
     # one spin, Theta slabs with the propagation still in shared memory
     "one_spin_slab": (ai.SystemSpec(150, 45, 0, 300, 20, True, 83), 2, 3, 0.005),
 }
@@ -233,7 +233,7 @@ def test_init_matches_oracle():
 def test_trajectory_c0_matches_oracle():
     """The small FP64 workload (8 orbitals, 4+4 electrons, 32 Cholesky vectors,
     8 hidden variables, tau = 0.01), 64 walkers x 16 paths, 12 steps from init."""
-    spec, run = ai.CONFIGS["c0_n8"]
+    spec, run = ai.CONFIGS["small_n8"]
     s, ham, ocfg, ctx = _setup(spec, run.n_walkers, run.n_paths, run.dtau, seed=ai.philox_run_seed(0), n_burn=20,
                                e_shift=11.5)
     ost = oa.init(ham, ocfg)
@@ -254,7 +254,7 @@ def test_full_size_medium_workload_sampled_walkers():
     250 Cholesky vectors, 50 hidden variables, 512 walkers x 32 paths, as
     timed by the benchmark): sampled walkers recomputed one by one by the
     oracle, for the measurement and for one whole step."""
-    spec, run = ai.CONFIGS["c1_n50"]
+    spec, run = ai.CONFIGS["medium_n50"]
     s = ai.make_system(spec)
     W, P = run.n_walkers, run.n_paths
     seed = ai.philox_run_seed(1)

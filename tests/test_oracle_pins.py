@@ -43,7 +43,7 @@ def _commuting_U(h, K, n_up, rng, scale=0.3):
 
 @pytest.fixture(scope="module")
 def c0():
-    s, run = ai.make_config("c0_n8")
+    s, run = ai.make_config("small_n8")
     fs = FockSpace(8, 4, 4)
     H = fs.hamiltonian(s.h, s.L)
     return s, run, fs, H
@@ -244,7 +244,7 @@ def test_no_hidden_variables_reduces_to_single_determinant():
 
 def test_combined_angle_identity():
     """Delta theta + Delta theta_T = Arg sum_p S'_p - Arg sum_p S_p (mod 2 pi)."""
-    s, run = ai.make_config("c0_n8")
+    s, run = ai.make_config("small_n8")
     ham = _ham(s, 4, 4, run.dtau)
     cfg = oa.OracleConfig(dtau=run.dtau, n_walkers=8, n_paths=6, seed=5, n_burn=3)
     st0 = oa.init(ham, cfg)
@@ -327,7 +327,7 @@ def test_force_bias_cancels_first_order_weight_fluctuation():
     """With the optimal shift of Eq. (15) the O(sqrt(tau)) field dependence of
     the importance function Eq. (14) cancels; at tau = 1e-6 every |log|I||
     stays O(tau), while a shift with the wrong sign or scale leaves O(sqrt(tau))."""
-    s, run = ai.make_config("c0_n8")
+    s, run = ai.make_config("small_n8")
     tau = 1e-6
     ham = _ham(s, 4, 4, tau)
     cfg = oa.OracleConfig(dtau=tau, n_walkers=12, n_paths=4, seed=31, n_burn=2)
