@@ -283,8 +283,9 @@ FP64_TRAFFIC = {   # kernel -> (committed summary, end of its device code, start
     "contract_fp64_kernel": ("contract_fp64_medium_n50.md", FP64_WALKER_SIDE, None),
     "contract_fp64z_kernel": ("contract_fp64z_medium_n50.md", "size_t contract_fp64_smem", FP64_WALKER_SIDE),
 }
-TC_TRAFFIC = {   # kernel -> (committed summary, end of its device code), for the medium workload
-    "contract_tcy_kernel": ("contract_tcy_medium_n50.md", "static size_t tcy_smem_bytes"),
+TC_TRAFFIC = {   # kernel -> (committed summary, end of its device code, start of it), for the medium workload
+    "contract_tcy_kernel": ("contract_tcy_medium_n50.md", "struct TcyShape",
+                            "// ---------------------------------------------------------------- walker-side form"),
 }
 
 
@@ -297,19 +298,24 @@ def tensor_roofline(spec, W, P, prof, kernel):
     source = "measured bf16 sustained (fp16 nominal ratio 1)"
     if peak is None:
         peak, source = 1700.0, "fallback sustained bf16 (fp16 nominal ratio 1)"
-    ms = prof["ms"]["contract"] / max(1, prof["launches"]["contract"])
+    # the contraction of one step: for the walker-side form, the Y-image kernel and
+    # the pair kernel (plus, for the per-pair form, the refinement's launches)
+    steps = max(1, prof["steps"])
+    ms = prof["ms"]["contract"] / steps
     flops = contract_flops_per_pair(spec) * W * P
     achieved = flops / (ms / 1e3) / 1e12
     traffic = None
     if kernel in TC_TRAFFIC and (W, P) == (512, 32):
-        summary, marker = TC_TRAFFIC[kernel]
+        summary, marker, start = TC_TRAFFIC[kernel]
         traffic = recorded_traffic(os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "contract_tc.cu"), summary,
-                                   marker)
+                                   marker, start)
     return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "peak_source": source, "traffic": traffic, "flops_per_launch": flops,
-            "ms_per_launch": ms,
-            "note": "algorithmic FLOPs of the real contraction; the split-FP16 scheme issues 4 MMA products per "
-                    "real product and pads N and n to MMA tile sizes"}
+            "ms_per_launch": ms, "launches_per_contraction": prof["launches"]["contract"] / steps,
+            "note": "one contraction per step (for the walker-side form its two kernels, tcy_y_kernel and "
+                    "contract_tcy_kernel; flops, time and DRAM traffic are theirs together); algorithmic FLOPs of "
+                    "the real contraction; the split-FP16 scheme issues 4 MMA products per real product and pads N "
+                    "and n to MMA tile sizes"}
 
 
 def tau_int(series):

@@ -245,6 +245,9 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.Lt = c->precision != AFQMC_PRECISION_FP64
                ? take(contract_tc_image_bytes(d.N, d.nu, d.nd, d.G, c->precision == AFQMC_PRECISION_FP16X3))
                : nullptr;
+    w.Yimg = c->precision != AFQMC_PRECISION_FP64
+                 ? take(contract_tcy_yimage_bytes(d.N, d.nu, d.nd, d.G, d.W, c->precision == AFQMC_PRECISION_FP16X3))
+                 : nullptr;
     w.phi = (double2*)take(W * N * nt * 16);
     w.weight = (double*)take(W * 8);
     w.x = (double*)take(pairs * K * 8);
@@ -409,7 +412,7 @@ static afqmc_status measure(afqmc_ctx* ctx) {
                       ovl));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64) {
-        CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.vpair, w.epair, w.status, f16));
+        CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.Yimg, w.vpair, w.epair, w.status, f16));
         if (w.refine_items) {   // the pairs whose error would put their walker above refine_tol, again
             CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2, w.alive,
                              w.refine_items, w.refine_n, w.counters));

@@ -104,7 +104,7 @@ extern "C" afqmc_status afqmc_autotune(afqmc_ctx* ctx, int* chosen) {
             Dims t = d;
             t.tc_tp = tp;
             float ms;
-            st = time_ms(s, [&] { return contract_tc(s, t, w.Lt, w.Phi, w.Theta, w.phi, w.vpair, w.epair, w.status, f16); }, 1,
+            st = time_ms(s, [&] { return contract_tc(s, t, w.Lt, w.Phi, w.Theta, w.phi, w.Yimg, w.vpair, w.epair, w.status, f16); }, 1,
                          &ms);
             if (st != AFQMC_OK) return st;
             if (ms < best) { best = ms; best_tp = tp; }

@@ -155,6 +155,7 @@ struct Workspace {
     void* expTdf;     // N*N double-float copy of expT (mixed-precision path)
     double* scratchNN;  // 3*N*N for the matrix exponential at init
     void* Lt;           // split-BF16 image of (h, L_g) for the tensor-core contraction
+    void* Yimg;         // split images of Y_g = X_g phi_w per walker (walker-side tensor-core form)
     // composite walkers
     double2* phi;     // W*N*nt (nt = n_up + n_dn)
     double* weight;   // W

@@ -581,61 +581,61 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ---------------------------------------------------------------- walker-side form (N <= 64)
 // With Theta_p = phi_w A_p^-1 and B_p = Phi_p A_p^-T, the matrix
 // M'_g = B_p^T (X_g phi_w) = A_p^-1 M_g A_p has the traces of M_g = Phi_p^T X_g Theta_p,
-// and Y_g = X_g phi_w depends on the walker only.  A block takes PG pairs of one
-// walker, so Y_g is formed once for all of them:
-//   GEMM-Y  D_Y[(g, j), c] = sum_i X_g[j, i] PW[c, i],  PW rows c = [Re phi | Im phi]
-//   GEMM-M  D_M[(p, col), (col', ri)] = sum_k AM[(p, col), k] BY_g[(col', ri), k] with
-//           AM row (p, col)  = [Re B_p[:, col] | Im B_p[:, col]]   (K = 2 x 64),
-//           BY row (col', re) = [Re Y_g[:, col'] | -Im Y_g[:, col']],
-//           BY row (col', im) = [Im Y_g[:, col'] |  Re Y_g[:, col']],
-//   so D_M[(p, col), (col', re/im)] = Re/Im (B_p^T Y_g)[col, col'] (same-spin blocks used).
-// One operand unit of the image holds two matrices (rows (g, j), N <= 64); each
-// iteration runs GEMM-Y on it, builds both BY (per-matrix power-of-two scale),
-// issues both GEMM-M and the next unit's GEMM-Y, and the two halves of the
-// block run epilogue M (shared-memory transpose, traces, sums) for one matrix each.
+// and Y_g = X_g phi_w depends on the walker only.  Two kernels:
+//   tcy_y_kernel (one block per walker) forms, per operand unit of two matrices,
+//     GEMM-Y  D_Y[(g, j), c] = sum_i X_g[j, i] PW[c, i],  PW rows c = [Re phi | Im phi],
+//     and its epilogue: the split image BY_g with rows
+//       BY row (col', re) = [Re Y_g[:, col'] | -Im Y_g[:, col']],
+//       BY row (col', im) = [Im Y_g[:, col'] |  Re Y_g[:, col']]   (K = 2 x 64),
+//     per-matrix power-of-two scale, written to global memory in the swizzled
+//     layout the MMAs read, plus the scale exponents;
+//   contract_tcy_kernel (one block per PG pairs of a walker) streams those
+//     images through a ring of bulk copies and runs
+//     GEMM-M  D_M[(p, col), (col', ri)] = sum_k AM[(p, col), k] BY_g[(col', ri), k],
+//     AM row (p, col) = [Re B_p[:, col] | Im B_p[:, col]], so
+//     D_M[(p, col), (col', re/im)] = Re/Im (B_p^T Y_g)[col, col'] (same-spin blocks used),
+//     and epilogue M (shared-memory transpose, traces, sums) with the two halves
+//     of the block on the two matrices of a unit.  With two tensor-memory buffers
+//     the next unit's GEMM-M runs while the block works on this unit's epilogue.
+// So the image of Y_g, whose epilogue dominated the fused kernel, is formed once
+// per walker instead of once per block of pairs.
 constexpr int TCY_MAXPG = 64;
+
+__host__ __device__ __forceinline__ size_t tcy_unit_bytes(int NBY) { return 4 * (size_t)NBY * 128 * 2; }
 
 template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    contract_tcy_kernel(int N, int nu, int nd, int G, int P, int PG, int NBY, int S, const uint8_t* __restrict__ image,
-                        const int* __restrict__ lexp, const double2* __restrict__ Bm, const double2* __restrict__ phi,
-                        double2* __restrict__ vpair, double2* __restrict__ epair, int* status) {
+    tcy_y_kernel(int N, int nu, int nd, int G, int NBY, int S, const uint8_t* __restrict__ image,
+                 const int* __restrict__ lexp, const double2* __restrict__ phi, uint8_t* __restrict__ yimg,
+                 int* __restrict__ yexp, int* status) {
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const int nt = nu + nd;
-    const int S2 = nu * nu + nd * nd;
-    uint8_t* XR = sm;                                          // S units
-    uint8_t* AMh = XR + (size_t)S * TC_UNIT;                   // 128 rows x 128 K
-    uint8_t* AMl = AMh + 128 * 128 * 2;
-    uint8_t* PWh = AMl + 128 * 128 * 2;                        // NBY rows x 64 K
+    uint8_t* XR = sm;                                          // S units of the (h, L_g) image
+    uint8_t* PWh = XR + (size_t)S * TC_UNIT;                   // NBY rows x 64 K
     const size_t pw_bytes = (size_t)NBY * 64 * 2;
     uint8_t* PWl = PWh + pw_bytes;
-    uint8_t* BY = PWl + pw_bytes;                              // matrix h: hi at 2h*by, lo at (2h+1)*by
+    uint8_t* BY = PWl + pw_bytes;                              // staging: matrix h hi at 2h*by, lo at (2h+1)*by
     const size_t by_bytes = (size_t)NBY * 128 * 2;
-    float* Ms = reinterpret_cast<float*>(BY + 4 * by_bytes);   // matrix h: PG x S2 complex
-    __shared__ uint64_t full_bar[TC_MAXSTAGES], empty_bar[TC_MAXSTAGES], ybar, mbar, drain_bar;
+    const size_t unit_bytes = 4 * by_bytes;
+    __shared__ uint64_t full_bar[TC_MAXSTAGES], empty_bar[TC_MAXSTAGES], ybar, drain_bar;
     __shared__ uint32_t tslot;
     __shared__ int fail_flag;
     __shared__ unsigned ymax[2][2];
-    __shared__ float2 red_tr[2][128], red_ex[2][128];
-    __shared__ double2 eacc[2][TCY_MAXPG];
-    __shared__ float2 red_c2[2][TCY_MAXPG];
-    __shared__ int sPW[128], sA[128];
+    __shared__ int sPW[128];
     __shared__ float cmul_pw[128];          // 2^-sPW: removes the PW row scales from D_Y
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, half = warp >> 2;
-    const int bpw = (P + PG - 1) / PG;
-    const long long w = blockIdx.x / bpw;
-    const int p0 = (int)(blockIdx.x % bpw) * PG;
-    const int np = min(PG, P - p0);
-    const long long pairbase = w * P + p0;
+    const long long w = blockIdx.x;
     const int G1 = G + 1;
     const int n_units = (G1 + 1) / 2;
     const double2* phw = phi + w * (long long)N * nt;
+    uint8_t* yout = yimg + (size_t)w * n_units * unit_bytes;
+    int* yex = yexp + (size_t)w * 2 * n_units;
 
     if (warp == 0) {
-        tc::tmem_alloc(&tslot, 512);
+        tc::tmem_alloc(&tslot, 256);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
@@ -644,14 +644,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc::mbar_init(&empty_bar[q], 1);
         }
         tc::mbar_init(&ybar, 1);
-        tc::mbar_init(&mbar, 1);
         tc::mbar_init(&drain_bar, 1);
         tc::mbar_fence_init();
         fail_flag = 0;
         ymax[0][0] = ymax[0][1] = ymax[1][0] = ymax[1][1] = 0u;
     }
-    if (tid < 2 * TCY_MAXPG) eacc[tid / TCY_MAXPG][tid % TCY_MAXPG] = cmk(0.0, 0.0);
-    // exponents of the PW rows (walker columns) and of the AM rows (B columns)
+    // exponents of the PW rows (walker columns)
     for (int c = tid; c < 128; c += TC_THREADS) {
         float m = 0.f;
         if (F16 && c < 2 * nt) {
@@ -663,18 +661,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         sPW[c] = scale_exp<F16>(m);
         cmul_pw[c] = pow2f(-sPW[c]);
-    }
-    for (int r = tid; r < 128; r += TC_THREADS) {
-        const int p = r / nt, col = r % nt;
-        float m = 0.f;
-        if (F16 && p < np) {
-            const double2* Bp = Bm + (pairbase + p) * (long long)N * nt;
-            for (int j = 0; j < N; ++j) {
-                const double2 t = Bp[(long long)j * nt + col];
-                m = fmaxf(m, fmaxf((float)fabs(t.x), (float)fabs(t.y)));
-            }
-        }
-        sA[r] = scale_exp<F16>(m);
     }
     __syncthreads();
     int loaded = 0, consumed = 0;   // meaningful in thread 0
@@ -694,20 +680,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         split16<F16>(x, PWh, PWl, tc::sw128_offset(NBY, c, i));
     }
-    // AM: row (p, col) = [Re B_p[:, col] | Im B_p[:, col]]
-    for (int e = tid; e < 128 * 128; e += TC_THREADS) {
-        const int r = e / 128, k = e % 128;
-        const int j = k & 63, ri = k >> 6;
-        const int p = r / nt, col = r % nt;
-        float x = 0.f;
-        if (p < np && j < N) {
-            const double2 t = Bm[(pairbase + p) * (long long)N * nt + (long long)j * nt + col];
-            x = (float)(ri ? t.y : t.x) * pow2f(sA[r]);
-        }
-        split16<F16>(x, AMh, AMl, tc::sw128_offset(128, r, k));
-    }
     // BY starts zero (rows past 2 nt are never written)
-    for (int e = tid; e < (int)(4 * by_bytes / 16); e += TC_THREADS) reinterpret_cast<uint4*>(BY)[e] = make_uint4(0, 0, 0, 0);
+    for (int e = tid; e < (int)(unit_bytes / 16); e += TC_THREADS) reinterpret_cast<uint4*>(BY)[e] = make_uint4(0, 0, 0, 0);
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -717,10 +691,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
     const uint32_t idd = F16 ? tc::idesc_f16_f32(128, NBY) : tc::idesc_bf16_f32(128, NBY);
     const uint32_t dyc = F16 ? (uint32_t)NBY : 0u;                  // correction columns of D_Y
-    const uint32_t dm0 = F16 ? 2u * NBY : (uint32_t)NBY;            // D_M of matrix 0
-    const uint32_t dms = F16 ? 2u * NBY : (uint32_t)NBY;            // stride to matrix 1
     const int Lrow = 32 * quarter + lane;
-    uint32_t y_ph = 0, m_ph = 0;
+    uint32_t y_ph = 0;
     bool failed = false;
 
     auto refill_upto = [&](int last_consumed) -> bool {
@@ -837,43 +809,183 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
         }
-        tc::fence_proxy_async();
+        // D_Y is read; the next unit's GEMM-Y overlaps the copy of this unit's image
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-        // ---- GEMM-M for both matrices of the unit, then the next unit's GEMM-Y
         if (tid == 0) {
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const uint32_t d = taddr + dm0 + (uint32_t)h2 * dms;
-                const uint8_t* byh = BY + (size_t)h2 * 2 * by_bytes;
-                const uint8_t* byl = byh + by_bytes;
-#pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    const uint32_t ka = (uint32_t)((s >> 2) * 128 * 128 + (s & 3) * 32);
-                    const uint32_t kbo = (uint32_t)((s >> 2) * NBY * 128 + (s & 3) * 32);
-                    const uint64_t ah = tc::desc_sw128(tc::smem_u32(AMh) + ka), al = tc::desc_sw128(tc::smem_u32(AMl) + ka);
-                    const uint64_t bh = tc::desc_sw128(tc::smem_u32(byh) + kbo), bl = tc::desc_sw128(tc::smem_u32(byl) + kbo);
-                    const uint32_t acc = s > 0 ? 1u : 0u;
-                    tc::mma_f16(d, ah, bh, idd, acc);
-                    if (F16) {
-                        tc::mma_f16(d + NBY, ah, bl, idd, acc);
-                        tc::mma_f16(d + NBY, al, bh, idd, 1u);
-                        tc::mma_f16(d + NBY, al, bl, idd, 1u);
-                    } else {
-                        tc::mma_f16(d, ah, bl, idd, 1u);
-                        tc::mma_f16(d, al, bh, idd, 1u);
-                    }
-                }
-            }
-            tc::mma_commit(&mbar);
+            yex[2 * u] = F16 ? row_exp(ymax[u & 1][0]) : 0;
+            yex[2 * u + 1] = F16 ? row_exp(ymax[u & 1][1]) : 0;
             if (u + 1 < n_units && !issue_Y(u + 1)) fail_flag = 1;
         }
+        const uint4* src = reinterpret_cast<const uint4*>(BY);
+        uint4* dst = reinterpret_cast<uint4*>(yout + (size_t)u * unit_bytes);
+        for (int e = tid; e < (int)(unit_bytes / 16); e += TC_THREADS) dst[e] = src[e];
+        __syncthreads();   // the staging area is free for the next epilogue
+    }
+    if (failed && tid == 0) {
+        // drain: every issued copy and MMA completes before the block releases its memory
+        atomicOr(status, STATUS_TIMEOUT);
+        for (int v = max(consumed, loaded - S); v < loaded; ++v)
+            if (v >= 0) tc::mbar_wait(&full_bar[v % S], (uint32_t)((v / S) & 1), 1u << 22);
+        tc::mma_commit(&drain_bar);
+        tc::mbar_wait(&drain_bar, 0, 1u << 22);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 256);
+}
+
+// nbuf: tensor-memory buffers of D_M (2: the next unit's GEMM-M is issued before
+// this unit's epilogue; 1: after it).
+template <bool F16>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    contract_tcy_kernel(int N, int nu, int nd, int G, int P, int PG, int NBY, int S, int nbuf,
+                        const uint8_t* __restrict__ yimg, const int* __restrict__ yexp,
+                        const double2* __restrict__ Bm, double2* __restrict__ vpair, double2* __restrict__ epair,
+                        int* status) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    const int nt = nu + nd;
+    const int S2 = nu * nu + nd * nd;
+    const size_t by_bytes = (size_t)NBY * 128 * 2;
+    const uint32_t unit_bytes = (uint32_t)(4 * by_bytes);
+    uint8_t* YR = sm;                                          // S units of the Y images
+    uint8_t* AMh = YR + (size_t)S * unit_bytes;                // 128 rows x 128 K
+    uint8_t* AMl = AMh + 128 * 128 * 2;
+    float* Ms = reinterpret_cast<float*>(AMl + 128 * 128 * 2);  // matrix h: PG x S2 complex
+    __shared__ uint64_t full_bar[TC_MAXSTAGES], mbar[2], drain_bar;
+    __shared__ uint32_t tslot;
+    __shared__ int fail_flag;
+    __shared__ float2 red_tr[2][128], red_ex[2][128];
+    __shared__ double2 eacc[2][TCY_MAXPG];
+    __shared__ float2 red_c2[2][TCY_MAXPG];
+    __shared__ int sA[128];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int bpw = (P + PG - 1) / PG;
+    const long long w = blockIdx.x / bpw;
+    const int p0 = (int)(blockIdx.x % bpw) * PG;
+    const int np = min(PG, P - p0);
+    const long long pairbase = w * P + p0;
+    const int G1 = G + 1;
+    const int n_units = (G1 + 1) / 2;
+    const uint8_t* ysrc = yimg + (size_t)w * n_units * unit_bytes;
+    const int* yex = yexp + (size_t)w * 2 * n_units;
+
+    if (warp == 0) {
+        tc::tmem_alloc(&tslot, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) tc::mbar_init(&full_bar[q], 1);
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        tc::mbar_init(&drain_bar, 1);
+        tc::mbar_fence_init();
+        fail_flag = 0;
+    }
+    if (tid < 2 * TCY_MAXPG) eacc[tid / TCY_MAXPG][tid % TCY_MAXPG] = cmk(0.0, 0.0);
+    // exponents of the AM rows (B columns)
+    for (int r = tid; r < 128; r += TC_THREADS) {
+        const int p = r / nt, col = r % nt;
+        float m = 0.f;
+        if (F16 && p < np) {
+            const double2* Bp = Bm + (pairbase + p) * (long long)N * nt;
+            for (int j = 0; j < N; ++j) {
+                const double2 t = Bp[(long long)j * nt + col];
+                m = fmaxf(m, fmaxf((float)fabs(t.x), (float)fabs(t.y)));
+            }
+        }
+        sA[r] = scale_exp<F16>(m);
+    }
+    __syncthreads();
+    int loaded = 0, consumed = 0;   // meaningful in thread 0
+    if (tid == 0) {
+        for (; loaded < S && loaded < n_units; ++loaded) {
+            tc::mbar_arrive_expect_tx(&full_bar[loaded], unit_bytes);
+            tc::bulk_g2s(YR + (size_t)loaded * unit_bytes, ysrc + (size_t)loaded * unit_bytes, unit_bytes,
+                         &full_bar[loaded]);
+        }
+    }
+    // AM: row (p, col) = [Re B_p[:, col] | Im B_p[:, col]]
+    for (int e = tid; e < 128 * 128; e += TC_THREADS) {
+        const int r = e / 128, k = e % 128;
+        const int j = k & 63, ri = k >> 6;
+        const int p = r / nt, col = r % nt;
+        float x = 0.f;
+        if (p < np && j < N) {
+            const double2 t = Bm[(pairbase + p) * (long long)N * nt + (long long)j * nt + col];
+            x = (float)(ri ? t.y : t.x) * pow2f(sA[r]);
+        }
+        split16<F16>(x, AMh, AMl, tc::sw128_offset(128, r, k));
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+
+    const uint32_t taddr = tslot;
+    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+    const uint32_t idd = F16 ? tc::idesc_f16_f32(128, NBY) : tc::idesc_bf16_f32(128, NBY);
+    const uint32_t dms = F16 ? 2u * NBY : (uint32_t)NBY;            // columns of one matrix's D_M
+    const int Lrow = 32 * quarter + lane;
+    uint32_t m_ph0 = 0, m_ph1 = 0;
+    bool failed = false;
+
+    // GEMM-M of unit u (thread 0) into buffer u % nbuf, both matrices
+    auto issue_M = [&](int u) -> bool {
+        const int st = u % S;
+        if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) return false;
+        tc::fence_after_sync();
+        ++consumed;
+        const uint8_t* unit = YR + (size_t)st * unit_bytes;
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const uint32_t d = taddr + (uint32_t)(u % nbuf) * 2u * dms + (uint32_t)h2 * dms;
+            const uint8_t* byh = unit + (size_t)h2 * 2 * by_bytes;
+            const uint8_t* byl = byh + by_bytes;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const uint32_t ka = (uint32_t)((s >> 2) * 128 * 128 + (s & 3) * 32);
+                const uint32_t kbo = (uint32_t)((s >> 2) * NBY * 128 + (s & 3) * 32);
+                const uint64_t ah = tc::desc_sw128(tc::smem_u32(AMh) + ka), al = tc::desc_sw128(tc::smem_u32(AMl) + ka);
+                const uint64_t bh = tc::desc_sw128(tc::smem_u32(byh) + kbo), bl = tc::desc_sw128(tc::smem_u32(byl) + kbo);
+                const uint32_t acc = s > 0 ? 1u : 0u;
+                tc::mma_f16(d, ah, bh, idd, acc);
+                if (F16) {
+                    tc::mma_f16(d + NBY, ah, bl, idd, acc);
+                    tc::mma_f16(d + NBY, al, bh, idd, 1u);
+                    tc::mma_f16(d + NBY, al, bl, idd, 1u);
+                } else {
+                    tc::mma_f16(d, ah, bl, idd, 1u);
+                    tc::mma_f16(d, al, bh, idd, 1u);
+                }
+            }
+        }
+        tc::mma_commit(&mbar[u % nbuf]);
+        return true;
+    };
+    if (tid == 0 && !issue_M(0)) fail_flag = 1;
+
+    for (int u = 0; u < n_units && !failed; ++u) {
         __syncwarp();
         {
-            bool ok = tc::mbar_wait(&mbar, m_ph);
-            m_ph ^= 1;
+            const int b = u % nbuf;
+            bool ok = fail_flag == 0 && tc::mbar_wait(&mbar[b], b ? m_ph1 : m_ph0);
+            if (b) m_ph1 ^= 1; else m_ph0 ^= 1;
             if (__syncthreads_or(!ok || fail_flag)) { failed = true; break; }
             tc::fence_after_sync();
+        }
+        if (tid == 0) {
+            // the MMAs that read stage u % S have completed: refill it with unit u + S
+            if (loaded < n_units) {
+                const int st = loaded % S;
+                tc::mbar_arrive_expect_tx(&full_bar[st], unit_bytes);
+                tc::bulk_g2s(YR + (size_t)st * unit_bytes, ysrc + (size_t)loaded * unit_bytes, unit_bytes, &full_bar[st]);
+                ++loaded;
+            }
+            if (nbuf == 2 && u + 1 < n_units && !issue_M(u + 1)) fail_flag = 1;
         }
         // ---- epilogue M: half h takes matrix 2u + h; thread lane r = (p, col)
         {
@@ -883,8 +995,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int a = spin ? col - nu : col;
             const int off = spin ? nu : 0, ns = spin ? nd : nu;
             const bool row_ok = p < np;
-            const float sc = F16 ? pow2f(-(sA[r] + row_exp(ymax[u & 1][half]))) : 1.f;
-            const uint32_t dcol = dm0 + (uint32_t)half * dms;
+            const float sc = F16 ? pow2f(-(sA[r] + yex[2 * u + half])) : 1.f;
+            const uint32_t dcol = (uint32_t)(u % nbuf) * 2u * dms + (uint32_t)half * dms;
             float* Mg = Ms + (size_t)half * PG * S2 * 2;
             float* Mrow = Mg + 2 * ((size_t)p * S2 + (spin ? nu * nu : 0));
             for (int c0 = 0; c0 < 2 * nt; c0 += 16) {
@@ -957,8 +1069,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             __syncthreads();
             tc::fence_after_sync();
         }
+        if (nbuf == 1 && tid == 0 && u + 1 < n_units && !issue_M(u + 1)) fail_flag = 1;
     }
     if (failed) {
+        // drain: every issued copy and MMA completes before the block releases its memory
         if (tid == 0) {
             atomicOr(status, STATUS_TIMEOUT);
             for (int v = max(consumed, loaded - S); v < loaded; ++v)
@@ -975,28 +1089,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 struct TcyShape {
-    int PG, NBY, S;
-    size_t smem;
+    int PG, NBY, S, SY, nbuf;
+    size_t smem, smem_y;
 };
 
 static size_t tcy_smem_bytes(int nu, int nd, int PG, int NBY, int S) {
-    return 1024 + (size_t)S * TC_UNIT + 2 * (size_t)128 * 128 * 2 + 2 * (size_t)NBY * 64 * 2 + 4 * (size_t)NBY * 128 * 2 +
+    return 1024 + (size_t)S * tcy_unit_bytes(NBY) + 2 * (size_t)128 * 128 * 2 +
            2 * (size_t)PG * (nu * nu + nd * nd) * 8;
 }
 
-// Shape of the walker-side form: N <= 64, n_up + n_dn <= 40 (tensor memory:
-// D_Y and two D_M, each NBY columns plus as many for the corrections), PG pairs
-// per block with PG (n_up + n_dn) <= 128 rows of AM.
+static size_t tcy_y_smem_bytes(int NBY, int S) {
+    return 1024 + (size_t)S * TC_UNIT + 2 * (size_t)NBY * 64 * 2 + tcy_unit_bytes(NBY);
+}
+
+// Shape of the walker-side form: N <= 64, n_up + n_dn <= 40, PG pairs per block
+// with PG (n_up + n_dn) <= 128 rows of AM.  Tensor memory: D_Y of the image
+// kernel (NBY columns, doubled for the FP16 corrections) in 256 columns; D_M of
+// the pair kernel (two matrices, NBY columns each plus as many corrections) once
+// or, when it fits the 512 columns, twice.
 static bool tcy_shape(int N, int nu, int nd, bool f16, int pg_override, TcyShape& s) {
     const int nt = nu + nd;
     if (N < 1 || N > 64 || nu < 1 || nd < 0 || nd > nu || nt > 40) return false;
     s.NBY = ((2 * nt + 15) / 16) * 16;
-    if ((f16 ? 6 : 3) * s.NBY + 16 > 512) return false;
+    const int dm = (f16 ? 2 : 1) * s.NBY;          // D_M columns of one matrix
+    if ((f16 ? 2 : 1) * s.NBY > 256 || 2 * dm > 512) return false;
+    s.nbuf = 4 * dm <= 512 ? 2 : 1;
     s.PG = min(TCY_MAXPG, 128 / nt);
     if (pg_override > 0 && pg_override < s.PG) s.PG = pg_override;
-    for (s.S = TC_MAXSTAGES; s.S >= 2; --s.S) {
+    for (s.S = TC_MAXSTAGES; s.S >= 1; --s.S) {
         s.smem = tcy_smem_bytes(nu, nd, s.PG, s.NBY, s.S);
-        if (s.smem <= TC_SMEM_MAX) return true;
+        if (s.smem <= TC_SMEM_MAX) break;
+    }
+    if (s.S < 1) return false;
+    for (s.SY = TC_MAXSTAGES; s.SY >= 2; --s.SY) {
+        s.smem_y = tcy_y_smem_bytes(s.NBY, s.SY);
+        if (s.smem_y <= TC_SMEM_MAX) return true;
     }
     return false;
 }
@@ -1006,16 +1133,34 @@ bool contract_tc_walker_side(int N, int nu, int nd, bool f16) {
     return tcy_shape(N, nu, nd, f16, 0, s);
 }
 
+size_t contract_tcy_yimage_bytes(int N, int nu, int nd, int G, long long W, bool f16) {
+    TcyShape s;
+    if (!tcy_shape(N, nu, nd, f16, 0, s)) return 0;
+    const long long n_units = (G + 2) / 2;
+    const size_t img = (size_t)W * n_units * tcy_unit_bytes(s.NBY);
+    return img + (size_t)W * 2 * n_units * sizeof(int);
+}
+
 template <bool F16>
 static cudaError_t launch_tcy(cudaStream_t st, const Dims& d, const TcyShape& s, const void* image, const int* lexp,
-                              const double2* Bm, const double2* phi, double2* vpair, double2* epair, int* status) {
-    cudaError_t e = raise_smem_limit((const void*)contract_tcy_kernel<F16>, s.smem);
-    if (e != cudaSuccess) return e;
+                              const double2* Bm, const double2* phi, void* ywork, double2* vpair, double2* epair,
+                              int* status) {
     const long long W = d.pairs / d.P;
+    const long long n_units = (d.G + 2) / 2;
+    uint8_t* yimg = static_cast<uint8_t*>(ywork);
+    int* yexp = reinterpret_cast<int*>(yimg + (size_t)W * n_units * tcy_unit_bytes(s.NBY));
+    cudaError_t e = raise_smem_limit((const void*)tcy_y_kernel<F16>, s.smem_y);
+    if (e != cudaSuccess) return e;
+    tcy_y_kernel<F16><<<(unsigned)W, TC_THREADS, s.smem_y, st>>>(d.N, d.nu, d.nd, d.G, s.NBY, s.SY,
+                                                                 (const uint8_t*)image, lexp, phi, yimg, yexp, status);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = raise_smem_limit((const void*)contract_tcy_kernel<F16>, s.smem);
+    if (e != cudaSuccess) return e;
     const long long blocks = W * ((d.P + s.PG - 1) / s.PG);
     contract_tcy_kernel<F16><<<(unsigned)blocks, TC_THREADS, s.smem, st>>>(d.N, d.nu, d.nd, d.G, d.P, s.PG, s.NBY, s.S,
-                                                                         (const uint8_t*)image, lexp, Bm, phi, vpair,
-                                                                         epair, status); count_launches(1);
+                                                                         s.nbuf, yimg, yexp, Bm, vpair, epair, status);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -1112,7 +1257,7 @@ static cudaError_t launch_tc(cudaStream_t st, const Dims& d, const TcShape& s, c
 }
 
 cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const double* Phi, const double2* Theta,
-                        const double2* phi, double2* vpair, double2* epair, int* status, bool f16) {
+                        const double2* phi, void* ywork, double2* vpair, double2* epair, int* status, bool f16) {
     TcShape s;
     if (!tc_shape(d.N, d.nu, d.nd, f16, s)) return cudaErrorInvalidValue;
     if (d.pairs <= 0) return cudaSuccess;
@@ -1121,9 +1266,9 @@ cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const
                                                    (size_t)(G1p / s.GPT) * s.NKB * TC_UNIT);
     TcyShape sy;
     if (tcy_shape(d.N, d.nu, d.nd, f16, d.tc_tp, sy)) {   // Theta holds B = Phi A^-T here
-        if (d.P < 1 || d.pairs % d.P != 0) return cudaErrorInvalidValue;
-        return f16 ? launch_tcy<true>(st, d, sy, image, lexp, Theta, phi, vpair, epair, status)
-                   : launch_tcy<false>(st, d, sy, image, lexp, Theta, phi, vpair, epair, status);
+        if (d.P < 1 || d.pairs % d.P != 0 || !ywork) return cudaErrorInvalidValue;
+        return f16 ? launch_tcy<true>(st, d, sy, image, lexp, Theta, phi, ywork, vpair, epair, status)
+                   : launch_tcy<false>(st, d, sy, image, lexp, Theta, phi, ywork, vpair, epair, status);
     }
     if (d.tc_tp > 0 && d.tc_tp < s.TP && !tc_fit(s, d.nu, d.tc_tp, f16)) return cudaErrorInvalidValue;
     if (s.NPAD == 64)

@@ -74,8 +74,11 @@ cudaError_t contract_tc_prepare(cudaStream_t st, int N, int nu, int nd, int G, c
 // With contract_tc_walker_side(...) true the contraction takes B = Phi A^-T per
 // pair (overlap_lu with trial_side = true) in place of Theta, plus the walkers.
 bool contract_tc_walker_side(int N, int nu, int nd, bool f16);
+// Work space of the walker-side form: the split images of Y_g = X_g phi_w of
+// every walker and their scale exponents (0 when the form does not apply).
+size_t contract_tcy_yimage_bytes(int N, int nu, int nd, int G, long long W, bool f16);
 cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const double* Phi, const double2* Theta,
-                        const double2* phi, double2* vpair, double2* epair, int* status, bool f16);
+                        const double2* phi, void* ywork, double2* vpair, double2* epair, int* status, bool f16);
 
 // walker.cu
 struct StepParams {
