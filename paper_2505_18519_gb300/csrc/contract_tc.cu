@@ -836,10 +836,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) tc::tmem_dealloc(taddr, 256);
 }
 
-// nbuf: tensor-memory buffers of D_M (2: the next unit's GEMM-M is issued before
-// this unit's epilogue; 1: after it).
+// Pair kernel: warps 0-7 run epilogue M (two halves, one matrix of the unit
+// each; they synchronise on named barrier 1), warp 8 is the producer: it streams
+// the Y images into the ring, waits for a D_M buffer to be free, and issues
+// GEMM-M.  mbarriers: full_bar (a unit's image has landed), empty_bar (the MMAs
+// reading a ring stage have completed), mfull (GEMM-M of a unit has completed),
+// mempty (the epilogue has read a D_M buffer).  nbuf: D_M buffers (2 when both
+// fit in tensor memory).  Every wait is bounded; on a timeout the warps stop,
+// the producer drains its copies and MMAs, and the block returns.
+constexpr int TCY_THREADS = TC_THREADS + 32;
+
 template <bool F16>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TCY_THREADS, 1)
     contract_tcy_kernel(int N, int nu, int nd, int G, int P, int PG, int NBY, int S, int nbuf,
                         const uint8_t* __restrict__ yimg, const int* __restrict__ yexp,
                         const double2* __restrict__ Bm, double2* __restrict__ vpair, double2* __restrict__ epair,
@@ -854,16 +862,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint8_t* AMh = YR + (size_t)S * unit_bytes;                // 128 rows x 128 K
     uint8_t* AMl = AMh + 128 * 128 * 2;
     float* Ms = reinterpret_cast<float*>(AMl + 128 * 128 * 2);  // matrix h: PG x S2 complex
-    __shared__ uint64_t full_bar[TC_MAXSTAGES], mbar[2], drain_bar;
+    __shared__ uint64_t full_bar[TC_MAXSTAGES], empty_bar[TC_MAXSTAGES], mfull[2], mempty[2], drain_bar;
     __shared__ uint32_t tslot;
-    __shared__ int fail_flag;
     __shared__ float2 red_tr[2][128], red_ex[2][128];
     __shared__ double2 eacc[2][TCY_MAXPG];
     __shared__ float2 red_c2[2][TCY_MAXPG];
     __shared__ int sA[128];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, half = (warp >> 2) & 1;
     const int bpw = (P + PG - 1) / PG;
     const long long w = blockIdx.x / bpw;
     const int p0 = (int)(blockIdx.x % bpw) * PG;
@@ -879,16 +886,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int q = 0; q < S; ++q) tc::mbar_init(&full_bar[q], 1);
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        for (int q = 0; q < S; ++q) {
+            tc::mbar_init(&full_bar[q], 1);
+            tc::mbar_init(&empty_bar[q], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&mfull[b], 1);
+            tc::mbar_init(&mempty[b], 1);
+        }
         tc::mbar_init(&drain_bar, 1);
         tc::mbar_fence_init();
-        fail_flag = 0;
     }
     if (tid < 2 * TCY_MAXPG) eacc[tid / TCY_MAXPG][tid % TCY_MAXPG] = cmk(0.0, 0.0);
     // exponents of the AM rows (B columns)
-    for (int r = tid; r < 128; r += TC_THREADS) {
+    for (int r = tid; r < 128; r += TCY_THREADS) {
         const int p = r / nt, col = r % nt;
         float m = 0.f;
         if (F16 && p < np) {
@@ -901,16 +912,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         sA[r] = scale_exp<F16>(m);
     }
     __syncthreads();
-    int loaded = 0, consumed = 0;   // meaningful in thread 0
-    if (tid == 0) {
-        for (; loaded < S && loaded < n_units; ++loaded) {
-            tc::mbar_arrive_expect_tx(&full_bar[loaded], unit_bytes);
-            tc::bulk_g2s(YR + (size_t)loaded * unit_bytes, ysrc + (size_t)loaded * unit_bytes, unit_bytes,
-                         &full_bar[loaded]);
-        }
-    }
     // AM: row (p, col) = [Re B_p[:, col] | Im B_p[:, col]]
-    for (int e = tid; e < 128 * 128; e += TC_THREADS) {
+    for (int e = tid; e < 128 * 128; e += TCY_THREADS) {
         const int r = e / 128, k = e % 128;
         const int j = k & 63, ri = k >> 6;
         const int p = r / nt, col = r % nt;
@@ -927,66 +930,82 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc::fence_after_sync();
 
     const uint32_t taddr = tslot;
-    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
     const uint32_t idd = F16 ? tc::idesc_f16_f32(128, NBY) : tc::idesc_bf16_f32(128, NBY);
     const uint32_t dms = F16 ? 2u * NBY : (uint32_t)NBY;            // columns of one matrix's D_M
-    const int Lrow = 32 * quarter + lane;
-    uint32_t m_ph0 = 0, m_ph1 = 0;
     bool failed = false;
 
-    // GEMM-M of unit u (thread 0) into buffer u % nbuf, both matrices
-    auto issue_M = [&](int u) -> bool {
-        const int st = u % S;
-        if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) return false;
-        tc::fence_after_sync();
-        ++consumed;
-        const uint8_t* unit = YR + (size_t)st * unit_bytes;
-        for (int h2 = 0; h2 < 2; ++h2) {
-            const uint32_t d = taddr + (uint32_t)(u % nbuf) * 2u * dms + (uint32_t)h2 * dms;
-            const uint8_t* byh = unit + (size_t)h2 * 2 * by_bytes;
-            const uint8_t* byl = byh + by_bytes;
+    if (warp == 8) {
+        // ---- producer (one thread)
+        if (lane == 0) {
+            int loaded = 0, consumed = 0;
+            auto load = [&](int st, int v) {
+                tc::mbar_arrive_expect_tx(&full_bar[st], unit_bytes);
+                tc::bulk_g2s(YR + (size_t)st * unit_bytes, ysrc + (size_t)v * unit_bytes, unit_bytes, &full_bar[st]);
+            };
+            for (; loaded < S && loaded < n_units; ++loaded) load(loaded, loaded);
+            for (int u = 0; u < n_units && !failed; ++u) {
+                const int b = u % nbuf, st = u % S;
+                // D_M buffer b is free once the epilogue of unit u - nbuf has read it
+                if (u >= nbuf && !tc::mbar_wait(&mempty[b], (uint32_t)((u / nbuf - 1) & 1))) { failed = true; break; }
+                if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) { failed = true; break; }
+                tc::fence_after_sync();
+                ++consumed;
+                const uint8_t* unit = YR + (size_t)st * unit_bytes;
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const uint32_t d = taddr + (uint32_t)b * 2u * dms + (uint32_t)h2 * dms;
+                    const uint8_t* byh = unit + (size_t)h2 * 2 * by_bytes;
+                    const uint8_t* byl = byh + by_bytes;
 #pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const uint32_t ka = (uint32_t)((s >> 2) * 128 * 128 + (s & 3) * 32);
-                const uint32_t kbo = (uint32_t)((s >> 2) * NBY * 128 + (s & 3) * 32);
-                const uint64_t ah = tc::desc_sw128(tc::smem_u32(AMh) + ka), al = tc::desc_sw128(tc::smem_u32(AMl) + ka);
-                const uint64_t bh = tc::desc_sw128(tc::smem_u32(byh) + kbo), bl = tc::desc_sw128(tc::smem_u32(byl) + kbo);
-                const uint32_t acc = s > 0 ? 1u : 0u;
-                tc::mma_f16(d, ah, bh, idd, acc);
-                if (F16) {
-                    tc::mma_f16(d + NBY, ah, bl, idd, acc);
-                    tc::mma_f16(d + NBY, al, bh, idd, 1u);
-                    tc::mma_f16(d + NBY, al, bl, idd, 1u);
-                } else {
-                    tc::mma_f16(d, ah, bl, idd, 1u);
-                    tc::mma_f16(d, al, bh, idd, 1u);
+                    for (int s = 0; s < 8; ++s) {
+                        const uint32_t ka = (uint32_t)((s >> 2) * 128 * 128 + (s & 3) * 32);
+                        const uint32_t kbo = (uint32_t)((s >> 2) * NBY * 128 + (s & 3) * 32);
+                        const uint64_t ah = tc::desc_sw128(tc::smem_u32(AMh) + ka),
+                                       al = tc::desc_sw128(tc::smem_u32(AMl) + ka);
+                        const uint64_t bh = tc::desc_sw128(tc::smem_u32(byh) + kbo),
+                                       bl = tc::desc_sw128(tc::smem_u32(byl) + kbo);
+                        const uint32_t acc = s > 0 ? 1u : 0u;
+                        tc::mma_f16(d, ah, bh, idd, acc);
+                        if (F16) {
+                            tc::mma_f16(d + NBY, ah, bl, idd, acc);
+                            tc::mma_f16(d + NBY, al, bh, idd, 1u);
+                            tc::mma_f16(d + NBY, al, bl, idd, 1u);
+                        } else {
+                            tc::mma_f16(d, ah, bl, idd, 1u);
+                            tc::mma_f16(d, al, bh, idd, 1u);
+                        }
+                    }
+                }
+                tc::mma_commit(&empty_bar[st]);
+                tc::mma_commit(&mfull[b]);
+                // refill the stages whose MMAs (units up to u - 1) have completed
+                while (loaded < n_units && loaded - S <= u - 1) {
+                    const int v = loaded - S, sv = loaded % S;
+                    if (!tc::mbar_wait(&empty_bar[sv], (uint32_t)((v / S) & 1))) { failed = true; break; }
+                    load(sv, loaded);
+                    ++loaded;
                 }
             }
-        }
-        tc::mma_commit(&mbar[u % nbuf]);
-        return true;
-    };
-    if (tid == 0 && !issue_M(0)) fail_flag = 1;
-
-    for (int u = 0; u < n_units && !failed; ++u) {
-        __syncwarp();
-        {
-            const int b = u % nbuf;
-            bool ok = fail_flag == 0 && tc::mbar_wait(&mbar[b], b ? m_ph1 : m_ph0);
-            if (b) m_ph1 ^= 1; else m_ph0 ^= 1;
-            if (__syncthreads_or(!ok || fail_flag)) { failed = true; break; }
-            tc::fence_after_sync();
-        }
-        if (tid == 0) {
-            // the MMAs that read stage u % S have completed: refill it with unit u + S
-            if (loaded < n_units) {
-                const int st = loaded % S;
-                tc::mbar_arrive_expect_tx(&full_bar[st], unit_bytes);
-                tc::bulk_g2s(YR + (size_t)st * unit_bytes, ysrc + (size_t)loaded * unit_bytes, unit_bytes, &full_bar[st]);
-                ++loaded;
+            if (failed) {
+                atomicOr(status, STATUS_TIMEOUT);
             }
-            if (nbuf == 2 && u + 1 < n_units && !issue_M(u + 1)) fail_flag = 1;
+            // drain: every issued copy and MMA completes before the block releases its memory
+            for (int v = max(consumed, loaded - S); v < loaded; ++v)
+                if (v >= 0) tc::mbar_wait(&full_bar[v % S], (uint32_t)((v / S) & 1), 1u << 22);
+            tc::mma_commit(&drain_bar);
+            tc::mbar_wait(&drain_bar, 0, 1u << 22);
         }
+        __syncwarp();
+    } else {
+        // ---- epilogue warps 0-7
+        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+        const int Lrow = 32 * quarter + lane;
+        uint32_t m_ph0 = 0, m_ph1 = 0;
+        for (int u = 0; u < n_units; ++u) {
+            const int b = u % nbuf;
+            const bool ok = tc::mbar_wait(&mfull[b], b ? m_ph1 : m_ph0);
+            if (b) m_ph1 ^= 1; else m_ph0 ^= 1;
+            if (tc::named_sync_or<TC_THREADS>(!ok)) { failed = true; break; }
+            tc::fence_after_sync();
         // ---- epilogue M: half h takes matrix 2u + h; thread lane r = (p, col)
         {
             const int r = Lrow;
@@ -1020,7 +1039,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
             tc::fence_before_sync();
-            __syncthreads();
+            tc::named_sync<TC_THREADS>();
             float2 tr = make_float2(0.f, 0.f), ex = make_float2(0.f, 0.f);
             if (row_ok) {
                 tr = make_float2(Mrow[2 * (a * ns + a)], Mrow[2 * (a * ns + a) + 1]);
@@ -1035,7 +1054,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             red_tr[half][r] = tr;
             red_ex[half][r] = ex;
-            __syncthreads();
+            tc::named_sync<TC_THREADS>();
             // per pair: sums over its rows in FP32 (FP64 is slow on this part), the
             // energy term of the matrix, then one FP64 accumulation per pair and unit
             if (tid < 2 * PG) {
@@ -1060,28 +1079,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 red_c2[hh][pp] = c;
             }
-            __syncthreads();
+            tc::named_sync<TC_THREADS>();
             if (tid < np) {
                 const float2 a = red_c2[0][tid], b = red_c2[1][tid];
                 eacc[0][tid] = cadd(eacc[0][tid], cmk((double)(a.x + b.x), (double)(a.y + b.y)));
             }
             tc::fence_before_sync();
-            __syncthreads();
+            tc::named_sync<TC_THREADS>();
             tc::fence_after_sync();
         }
-        if (nbuf == 1 && tid == 0 && u + 1 < n_units && !issue_M(u + 1)) fail_flag = 1;
-    }
-    if (failed) {
-        // drain: every issued copy and MMA completes before the block releases its memory
-        if (tid == 0) {
-            atomicOr(status, STATUS_TIMEOUT);
-            for (int v = max(consumed, loaded - S); v < loaded; ++v)
-                if (v >= 0) tc::mbar_wait(&full_bar[v % S], (uint32_t)((v / S) & 1), 1u << 22);
-            tc::mma_commit(&drain_bar);
-            tc::mbar_wait(&drain_bar, 0, 1u << 22);
+            if (tid == 0) tc::mbar_arrive(&mempty[b]);   // D_M buffer b has been read
         }
-    } else if (tid < np) {
-        epair[pairbase + tid] = eacc[0][tid];
+        if (failed && tid == 0) atomicOr(status, STATUS_TIMEOUT);
+        if (!failed && tid < np) epair[pairbase + tid] = eacc[0][tid];
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -1158,7 +1168,7 @@ static cudaError_t launch_tcy(cudaStream_t st, const Dims& d, const TcyShape& s,
     e = raise_smem_limit((const void*)contract_tcy_kernel<F16>, s.smem);
     if (e != cudaSuccess) return e;
     const long long blocks = W * ((d.P + s.PG - 1) / s.PG);
-    contract_tcy_kernel<F16><<<(unsigned)blocks, TC_THREADS, s.smem, st>>>(d.N, d.nu, d.nd, d.G, d.P, s.PG, s.NBY, s.S,
+    contract_tcy_kernel<F16><<<(unsigned)blocks, TCY_THREADS, s.smem, st>>>(d.N, d.nu, d.nd, d.G, d.P, s.PG, s.NBY, s.S,
                                                                          s.nbuf, yimg, yexp, Bm, vpair, epair, status);
     count_launches(1);
     return cudaGetLastError();

@@ -79,6 +79,28 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// One arrival on `bar` (its phase completes once all expected arrivals are in).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Named barrier 1 over the first `count` threads of the block (a multiple of
+// 32), for warps that synchronise among themselves while another warp of the
+// block runs its own loop; the _or form returns the OR of `v` over them.
+template <int COUNT>
+__device__ __forceinline__ void named_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(COUNT) : "memory");
+}
+template <int COUNT>
+__device__ __forceinline__ bool named_sync_or(bool v) {
+    uint32_t r;
+    asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(r)
+                 : "r"((uint32_t)v), "n"(COUNT)
+                 : "memory");
+    return r != 0;
+}
+
 // ---------------------------------------------------------------- bulk copies
 // Contiguous global -> shared copy by the tensor memory accelerator (both
 // addresses 16-byte aligned, `bytes` a multiple of 16); completion is counted
