@@ -648,7 +648,9 @@ def our_arm(args):
     pairs_total = W * P * world
     value = pairs_total * args.steps / (ms_max / 1e3)
     e2e_value = pairs_total * args.steps / e2e_s if e2e_s else None
-    contract_ms = prof["ms"]["contract"] / max(1, prof["launches"]["contract"])
+    # the contraction of one step (for the walker-side form: the orbital layout, the
+    # GEMM forming Y_g = X_g phi_w for all walkers, and the pair kernel)
+    contract_ms = prof["ms"]["contract"] / max(1, prof["steps"])
     kernel = lib.contract_kernel(cfg)
     flops_pair_order = contract_flops_per_pair(spec) * W * P
     flops = contract_flops_walker_side(spec, P) * W * P if kernel == "contract_fp64z_kernel" else flops_pair_order
@@ -676,8 +678,11 @@ def our_arm(args):
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (no FP64 figure measured by the driver)",
                      "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": contract_ms,
                      "flops_per_launch_pair_order": flops_pair_order,
-                     "note": "flops_per_launch counts the kernel's own association order; the per-pair order "
-                             "(R = Phi^T L_g first) needs flops_per_launch_pair_order"},
+                     "launches_per_contraction": prof["launches"]["contract"] / max(1, prof["steps"]),
+                     "note": "one contraction per step (for the walker-side form: phi_columns_kernel, the FP64 GEMM "
+                             "forming Y_g = X_g phi_w of every walker, and contract_fp64z_kernel; flops, time and "
+                             "traffic are theirs together); flops_per_launch counts the walker-side association "
+                             "order; the per-pair order (R = Phi^T L_g first) needs flops_per_launch_pair_order"},
         "cpu_baseline": cpu,
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 32,

@@ -229,8 +229,9 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     };
     size_t N = d.N, NN = N * N, nt = d.nt, nu = d.nu, G = d.G, K = d.K, W = d.W, pairs = d.pairs;
     Workspace w{};
-    w.h = (double*)take(NN * 8);
-    w.L = (double*)take(G * NN * 8);
+    // h and the L_g back to back: [h; L_1; ...; L_G] is one (G+1) N x N matrix
+    w.h = (double*)take((G + 1) * NN * 8);
+    w.L = w.h + NN;
     w.Phi0 = (double*)take(N * nu * 8);
     w.U = (double*)take(K * NN * 8);
     w.Udf = c->precision != AFQMC_PRECISION_FP64 ? take(K * NN * 8) : nullptr;
@@ -248,6 +249,9 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.Yimg = c->precision != AFQMC_PRECISION_FP64
                  ? take(contract_tcy_yimage_bytes(d.N, d.nu, d.nd, d.G, d.W, c->precision == AFQMC_PRECISION_FP16X3))
                  : nullptr;
+    const size_t ywalk = c->precision == AFQMC_PRECISION_FP64 ? contract_fp64_walker_bytes(d.N, d.nu, d.nd, d.G, d.W, d.P)
+                                                              : 0;
+    w.ywalk = ywalk ? take(ywalk) : nullptr;
     w.phi = (double2*)take(W * N * nt * 16);
     w.weight = (double*)take(W * 8);
     w.x = (double*)take(pairs * K * 8);
@@ -420,7 +424,7 @@ static afqmc_status measure(afqmc_ctx* ctx) {
                                     d.pairs, w.hdf, w.Ldf));
         }
     } else if (ovl == OVL_INVERSE)
-        CK(contract_fp64_walker(s, d, w.h, w.L, w.Phi, w.Theta, w.phi, w.vpair, w.epair));
+        CK(contract_fp64_walker(s, d, w.h, w.L, w.Phi, w.Theta, w.phi, w.ywalk, w.vpair, w.epair));
     else
         CK(contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
     if ((st = prof_mark(ctx, PH_CONTRACT)) != AFQMC_OK) return st;

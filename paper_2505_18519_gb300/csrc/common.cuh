@@ -156,6 +156,7 @@ struct Workspace {
     double* scratchNN;  // 3*N*N for the matrix exponential at init
     void* Lt;           // split-BF16 image of (h, L_g) for the tensor-core contraction
     void* Yimg;         // split images of Y_g = X_g phi_w per walker (walker-side tensor-core form)
+    void* ywalk;        // Y_g = X_g phi_w of every walker, and the walkers' orbitals as columns (walker-side FP64 form)
     // composite walkers
     double2* phi;     // W*N*nt (nt = n_up + n_dn)
     double* weight;   // W

@@ -234,12 +234,15 @@ __global__ void __launch_bounds__(CT, (DF && OWN > 8) ? 1 : 2) contract_fp64_ker
 // ---------------------------------------------------------------- walker-side form
 // With Theta_s = phi_s A_s^-1 (A_s = Phi_s^T phi_s) the matrix of the contraction is
 //   M_g,s = Phi_s^T X_g Theta_s = Z_g,s A_s^-1,   Z_g,s = Phi_s^T Y_g,s,   Y_g = X_g phi_w,
-// and Y_g is the same for every pair of walker w.  A block takes PG = 8 PPW pairs
-// of one walker (warp k owns pairs k PPW .. k PPW + PPW - 1): per matrix X_g it
-// forms Y_g once (all threads), then each warp forms Z (real x complex), M = Z A^-1
-// and the traces for its own pairs.  FP64 multiply-adds per pair and matrix:
-//   2 N (n_up^2 + n_dn^2) + 4 (n_up^3 + n_dn^3) + 4 (n_up^2 + n_dn^2) + 2 N^2 (n_up + n_dn) / PG
-// against n_up N^2 + 2 N (n_up^2 + n_dn^2) + 4 (n_up^2 + n_dn^2) for the per-pair form above.
+// and Y_g is the same for every pair of walker w.  One FP64 GEMM forms Y_g for
+// every matrix and walker at once ([h; L_1; ...] times the walkers' orbitals laid
+// side by side), then a block takes PG = 8 PPW pairs of one walker (warp k owns
+// pairs k PPW .. k PPW + PPW - 1): per matrix X_g it loads Y_g, and each warp
+// forms Z (real x complex), M = Z A^-1 and the traces for its own pairs.  FP64
+// multiply-adds per pair and matrix:
+//   2 N (n_up^2 + n_dn^2) + 4 (n_up^3 + n_dn^3) + 4 (n_up^2 + n_dn^2) + 2 N^2 (n_up + n_dn) / P
+// (the last term in the GEMM) against n_up N^2 + 2 N (n_up^2 + n_dn^2) + 4 (n_up^2 + n_dn^2)
+// for the per-pair form above.
 constexpr int CZ_T = 256;
 constexpr int CZ_WARPS = CZ_T / 32;
 constexpr int CZ_MAXPPW = 2;
@@ -253,10 +256,12 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
     return v;
 }
 
+// Y: row g1 N + i, columns w 2nt + 2c, 2c + 1 hold Y_{g1}[i, c] of walker w
+// (g1 = 0 for h, g + 1 for L_g), leading dimension ldy = W 2nt.
 __global__ void __launch_bounds__(CZ_T, 1)
-    contract_fp64z_kernel(int N, int nu, int nd, int G, int P, int PPW, const double* __restrict__ h,
-                          const double* __restrict__ L, const double* __restrict__ Phi, const double2* __restrict__ Ainv,
-                          const double2* __restrict__ phi, double2* __restrict__ vpair, double2* __restrict__ epair) {
+    contract_fp64z_kernel(int N, int nu, int nd, int G, int P, int PPW, const double* __restrict__ Y, long long ldy,
+                          const double* __restrict__ Phi, const double2* __restrict__ Ainv,
+                          double2* __restrict__ vpair, double2* __restrict__ epair) {
     extern __shared__ double smz[];
     const int nt = nu + nd, PG = CZ_WARPS * PPW;
     const int S2 = nu * nu + nd * nd;
@@ -265,16 +270,13 @@ __global__ void __launch_bounds__(CZ_T, 1)
     const int p0 = (int)(blockIdx.x % bpw) * PG;
     const int np = min(PG, P - p0);
     const long long pairbase = w * P + p0;
-    double* sX = smz;                                                        // N x N
-    double2* sphi = reinterpret_cast<double2*>(sX + r2((size_t)N * N));      // N x nt
-    double2* sY = sphi + (size_t)N * nt;                                     // N x nt
+    double2* sY = reinterpret_cast<double2*>(smz);                           // N x nt
     double* sPh = reinterpret_cast<double*>(sY + (size_t)N * nt);            // PG x N x nu
     double2* sW = reinterpret_cast<double2*>(sPh + r2((size_t)PG * N * nu));  // PG x S2
     double2* sZ = sW + (size_t)PG * S2;                                      // PG x nu^2
     double2* sQ = sZ + (size_t)PG * nu * nu;                                 // PG x nu^2
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    for (int e = tid; e < N * nt; e += CZ_T) sphi[e] = phi[w * (long long)N * nt + e];
     for (int e = tid; e < PG * N * nu; e += CZ_T) {
         const int q = e / (N * nu);
         sPh[e] = q < np ? Phi[(pairbase + q) * (long long)N * nu + (e - q * N * nu)] : 0.0;
@@ -288,21 +290,11 @@ __global__ void __launch_bounds__(CZ_T, 1)
     for (int q = 0; q < CZ_MAXPPW; ++q) eacc[q] = cmk(0.0, 0.0);
     __syncthreads();
     for (int g = -1; g < G; ++g) {
-        const double* X = (g < 0) ? h : L + (long long)g * N * N;
-        for (int e = tid; e < N * N; e += CZ_T) sX[e] = X[e];
-        __syncthreads();
-        // Y = X phi_w
+        // Y_g of this walker (16-byte aligned: ldy and the column offsets are even)
+        const double* Yg = Y + (long long)(g + 1) * N * ldy + w * 2 * nt;
         for (int e = tid; e < N * nt; e += CZ_T) {
             const int i = e / nt, c = e - i * nt;
-            const double* Xi = sX + (size_t)i * N;
-            double2 acc = cmk(0.0, 0.0);
-            for (int k = 0; k < N; ++k) {
-                const double x = Xi[k];
-                const double2 f = sphi[(size_t)k * nt + c];
-                acc.x = fma(x, f.x, acc.x);
-                acc.y = fma(x, f.y, acc.y);
-            }
-            sY[e] = acc;
+            sY[e] = *reinterpret_cast<const double2*>(Yg + (long long)i * ldy + 2 * c);
         }
         __syncthreads();
         double2 tr[CZ_MAXPPW], ex[CZ_MAXPPW];
@@ -383,7 +375,7 @@ __global__ void __launch_bounds__(CZ_T, 1)
 
 static size_t contract_fp64z_smem(int N, int nu, int nd, int PPW) {
     const size_t PG = (size_t)CZ_WARPS * PPW, nt = nu + nd, S2 = (size_t)nu * nu + (size_t)nd * nd;
-    return (r2((size_t)N * N) + 4 * (size_t)N * nt + r2(PG * N * nu) + 2 * PG * S2 + 4 * PG * nu * nu) * sizeof(double);
+    return (2 * (size_t)N * nt + r2(PG * N * nu) + 2 * PG * S2 + 4 * PG * nu * nu) * sizeof(double);
 }
 
 // Pairs per warp for the walker-side form: 2 if it fits in shared memory and the
@@ -397,18 +389,50 @@ static int contract_fp64z_ppw(int N, int nu, int nd, int P) {
 
 bool contract_fp64_walker_side(int N, int nu, int nd, int P) { return contract_fp64z_ppw(N, nu, nd, P) > 0; }
 
+size_t contract_fp64_walker_bytes(int N, int nu, int nd, int G, long long W, int P) {
+    if (!contract_fp64_walker_side(N, nu, nd, P)) return 0;
+    const size_t cols = (size_t)W * 2 * (nu + nd);
+    return ((size_t)(G + 1) * N * cols + (size_t)N * cols) * sizeof(double);
+}
+
+// cols[i][w][c] = phi[w][i][c] (complex): the real N x (W 2nt) matrix of the
+// walkers' orbitals side by side.
+__global__ void phi_columns_kernel(int N, int nt, long long W, const double2* __restrict__ phi, double2* cols) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= W * N * nt) return;
+    const int c = (int)(e % nt);
+    const long long r = e / nt;
+    const int i = (int)(r % N);
+    const long long w = r / N;
+    cols[((long long)i * W + w) * nt + c] = phi[e];
+}
+
 cudaError_t contract_fp64_walker(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
-                                 const double2* Ainv, const double2* phi, double2* vpair, double2* epair) {
+                                 const double2* Ainv, const double2* phi, void* work, double2* vpair, double2* epair) {
     const int ppw = contract_fp64z_ppw(d.N, d.nu, d.nd, d.P);
     if (ppw == 0 || d.P < 1 || d.pairs % d.P != 0) return cudaErrorInvalidValue;
+    if (L != h + (size_t)d.N * d.N || !work) return cudaErrorInvalidValue;
     if (d.pairs == 0) return cudaSuccess;
+    const long long W = d.pairs / d.P;
+    const long long cols = W * 2 * d.nt;
+    const long long rows = (long long)(d.G + 1) * d.N;
+    if (cols > INT32_MAX || rows > INT32_MAX) return cudaErrorInvalidValue;
+    double* Y = static_cast<double*>(work);
+    double* C = Y + rows * cols;
+    const long long n = W * d.N * d.nt;
+    phi_columns_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d.N, d.nt, W, phi, reinterpret_cast<double2*>(C));
+    count_launches(1);
+    gemm_nn_f64(s, (int)rows, (int)cols, d.N, 1.0, h, d.N, C, cols, 0.0, Y, cols);   // Y_g = X_g phi_w, all g and w
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const size_t smem = contract_fp64z_smem(d.N, d.nu, d.nd, ppw);
-    cudaError_t e = raise_smem_limit((const void*)contract_fp64z_kernel, smem);
+    e = raise_smem_limit((const void*)contract_fp64z_kernel, smem);
     if (e != cudaSuccess) return e;
     const int PG = CZ_WARPS * ppw;
-    const long long blocks = (d.pairs / d.P) * ((d.P + PG - 1) / PG);
-    contract_fp64z_kernel<<<(unsigned)blocks, CZ_T, smem, s>>>(d.N, d.nu, d.nd, d.G, d.P, ppw, h, L, Phi, Ainv, phi, vpair,
-                                                             epair); count_launches(1);
+    const long long blocks = W * ((d.P + PG - 1) / PG);
+    contract_fp64z_kernel<<<(unsigned)blocks, CZ_T, smem, s>>>(d.N, d.nu, d.nd, d.G, d.P, ppw, Y, cols, Phi, Ainv, vpair,
+                                                             epair);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -63,8 +63,12 @@ cudaError_t contract_fp64_listed(cudaStream_t s, const Dims& d, const double* h,
 // Z = Phi_p^T Y_g, Q = Z A_p^-1; Tr Q and Tr Q^2 are those of M_g): needs A^-1
 // per pair and spin (overlap_lu with OVL_INVERSE) and the walkers.
 bool contract_fp64_walker_side(int N, int nu, int nd, int P);
+// L must follow h directly ([h; L] one (G+1) N x N matrix); work: W (G+1) N 2nt
+// + N W 2nt doubles (contract_fp64_walker_bytes), where Y_g = X_g phi_w of every
+// walker is formed by one GEMM before the contraction reads it.
+size_t contract_fp64_walker_bytes(int N, int nu, int nd, int G, long long W, int P);
 cudaError_t contract_fp64_walker(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
-                                 const double2* Ainv, const double2* phi, double2* vpair, double2* epair);
+                                 const double2* Ainv, const double2* phi, void* work, double2* vpair, double2* epair);
 
 // contract_tc.cu
 bool contract_tc_supported(int N, int nu, int nd, bool f16);
