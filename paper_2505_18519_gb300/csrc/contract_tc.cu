@@ -945,6 +945,14 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
             for (; loaded < S && loaded < n_units; ++loaded) load(loaded, loaded);
             for (int u = 0; u < n_units && !failed; ++u) {
                 const int b = u % nbuf, st = u % S;
+                // unit u not loaded yet (a one-stage ring): its stage frees when GEMM-M of unit u - S completes
+                while (loaded <= u) {
+                    const int v = loaded - S, sv = loaded % S;
+                    if (v >= 0 && !tc::mbar_wait(&empty_bar[sv], (uint32_t)((v / S) & 1))) { failed = true; break; }
+                    load(sv, loaded);
+                    ++loaded;
+                }
+                if (failed) break;
                 // D_M buffer b is free once the epilogue of unit u - nbuf has read it
                 if (u >= nbuf && !tc::mbar_wait(&mempty[b], (uint32_t)((u / nbuf - 1) & 1))) { failed = true; break; }
                 if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) { failed = true; break; }
