@@ -284,6 +284,22 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
             const dfl sv = df_two_sum(s, cc);
             return df_mul(df_add(sv, df_neg(df_mul(cs, V[e]))), ir);
         };
+        // the same for elements e0 and e0 + 1 of one row (n_up even, e0 even): one load
+        // of S per term serves both, each element's Dot2 sequence is unchanged
+        auto tv2 = [&](const dfl* V, int e0, dfl& r0, dfl& r1) {
+            const int i = e0 / nu, a = e0 - i * nu;
+            const dfl* Srow = S + (size_t)i * N;
+            const dfl* Va = V + a;
+            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+            for (int j = 0; j < N; ++j) {
+                const dfl x = Srow[j], y0 = Va[(size_t)j * nu], y1 = Va[(size_t)j * nu + 1];
+                dot2_fma(s0, c0, x, y0);
+                dot2_fma(s1, c1, x, y1);
+            }
+            r0 = df_mul(df_add(df_two_sum(s0, c0), df_neg(df_mul(cs, V[e0]))), ir);
+            r1 = df_mul(df_add(df_two_sum(s1, c1), df_neg(df_mul(cs, V[e0 + 1]))), ir);
+        };
+        const bool pairs2 = (nu & 1) == 0;
         for (int e = tid; e < nn; e += nth) {
             const dfl f = df_from(Phi0[e]);
             Vp[e] = f;
@@ -291,23 +307,50 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
         }
         __syncthreads();
         float ss = 0.f;
-        for (int e = tid; e < nn; e += nth) {
-            const dfl sv = tv(Vp, e);
-            Vc[e] = sv;
-            acc[e] = df_add(acc[e], df_mul(coefd[1], sv));
-            ss = fmaf(sv.hi, sv.hi, ss);
+        if (pairs2) {
+            for (int e = 2 * tid; e < nn; e += 2 * nth) {
+                dfl sv[2];
+                tv2(Vp, e, sv[0], sv[1]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    Vc[e + h] = sv[h];
+                    acc[e + h] = df_add(acc[e + h], df_mul(coefd[1], sv[h]));
+                    ss = fmaf(sv[h].hi, sv[h].hi, ss);
+                }
+            }
+        } else {
+            for (int e = tid; e < nn; e += nth) {
+                const dfl sv = tv(Vp, e);
+                Vc[e] = sv;
+                acc[e] = df_add(acc[e], df_mul(coefd[1], sv));
+                ss = fmaf(sv.hi, sv.hi, ss);
+            }
         }
         bool grew = check && block_sum_f(ss, red8) > grow_limit;
         for (int k = 2; k <= m && !grew; ++k) {
             // V_k = 2 t V_{k-1} - V_{k-2}, written over V_{k-2} element by element
             __syncthreads();
             ss = 0.f;
-            for (int e = tid; e < nn; e += nth) {
-                const dfl sv = tv(Vc, e);
-                const dfl v = df_add(dfl{2.f * sv.hi, 2.f * sv.lo}, df_neg(Vp[e]));
-                Vp[e] = v;
-                acc[e] = df_add(acc[e], df_mul(coefd[k], v));
-                ss = fmaf(v.hi, v.hi, ss);
+            if (pairs2) {
+                for (int e = 2 * tid; e < nn; e += 2 * nth) {
+                    dfl sv[2];
+                    tv2(Vc, e, sv[0], sv[1]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const dfl v = df_add(dfl{2.f * sv[h].hi, 2.f * sv[h].lo}, df_neg(Vp[e + h]));
+                        Vp[e + h] = v;
+                        acc[e + h] = df_add(acc[e + h], df_mul(coefd[k], v));
+                        ss = fmaf(v.hi, v.hi, ss);
+                    }
+                }
+            } else {
+                for (int e = tid; e < nn; e += nth) {
+                    const dfl sv = tv(Vc, e);
+                    const dfl v = df_add(dfl{2.f * sv.hi, 2.f * sv.lo}, df_neg(Vp[e]));
+                    Vp[e] = v;
+                    acc[e] = df_add(acc[e], df_mul(coefd[k], v));
+                    ss = fmaf(v.hi, v.hi, ss);
+                }
             }
             if (check) grew = block_sum_f(ss, red8) > grow_limit;   // uniform across the block
             else __syncthreads();
