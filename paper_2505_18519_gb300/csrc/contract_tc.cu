@@ -750,10 +750,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         {
             const int g = 2 * u + gi;
             const int le = (F16 && g < G1) ? lexp[g] : 0;
-            uint8_t* byh = BY + (size_t)gi * 2 * by_bytes;
-            uint8_t* byl = byh + by_bytes;
+            // one image of 2 NBY rows for the unit's two matrices (matrix gi from row gi NBY),
+            // so the pair kernel multiplies both with one MMA per K step and product
+            uint8_t* byh = BY + (size_t)gi * NBY * 128;
+            uint8_t* byl = BY + 2 * by_bytes + (size_t)gi * NBY * 128;
             // K position jrow of a BY row: within a 128-byte row, chunk (jrow / 8) xor (row % 8)
-            const uint32_t kb1 = (uint32_t)NBY * 128u;          // second K block (k = 64 + jrow)
+            const uint32_t kb1 = 2u * (uint32_t)NBY * 128u;     // second K block (k = 64 + jrow)
             float mul = pow2f(-le);
             for (int pass = F16 ? 0 : 1; pass < 2; ++pass) {
                 float mx = 0.f;
@@ -930,7 +932,7 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
     tc::fence_after_sync();
 
     const uint32_t taddr = tslot;
-    const uint32_t idd = F16 ? tc::idesc_f16_f32(128, NBY) : tc::idesc_bf16_f32(128, NBY);
+    const uint32_t idd = F16 ? tc::idesc_f16_f32(128, 2 * NBY) : tc::idesc_bf16_f32(128, 2 * NBY);
     const uint32_t dms = F16 ? 2u * NBY : (uint32_t)NBY;            // columns of one matrix's D_M
     bool failed = false;
 
@@ -958,29 +960,28 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
                 if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) { failed = true; break; }
                 tc::fence_after_sync();
                 ++consumed;
-                const uint8_t* unit = YR + (size_t)st * unit_bytes;
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    const uint32_t d = taddr + (uint32_t)b * 2u * dms + (uint32_t)h2 * dms;
-                    const uint8_t* byh = unit + (size_t)h2 * 2 * by_bytes;
-                    const uint8_t* byl = byh + by_bytes;
+                // both matrices of the unit in one operand of 2 NBY rows; D columns of buffer b:
+                // [matrix 0 | matrix 1] then (FP16) their corrections
+                const uint8_t* byh = YR + (size_t)st * unit_bytes;
+                const uint8_t* byl = byh + 2 * by_bytes;
+                const uint32_t d = taddr + (uint32_t)b * 2u * dms;
 #pragma unroll
-                    for (int s = 0; s < 8; ++s) {
-                        const uint32_t ka = (uint32_t)((s >> 2) * 128 * 128 + (s & 3) * 32);
-                        const uint32_t kbo = (uint32_t)((s >> 2) * NBY * 128 + (s & 3) * 32);
-                        const uint64_t ah = tc::desc_sw128(tc::smem_u32(AMh) + ka),
-                                       al = tc::desc_sw128(tc::smem_u32(AMl) + ka);
-                        const uint64_t bh = tc::desc_sw128(tc::smem_u32(byh) + kbo),
-                                       bl = tc::desc_sw128(tc::smem_u32(byl) + kbo);
-                        const uint32_t acc = s > 0 ? 1u : 0u;
-                        tc::mma_f16(d, ah, bh, idd, acc);
-                        if (F16) {
-                            tc::mma_f16(d + NBY, ah, bl, idd, acc);
-                            tc::mma_f16(d + NBY, al, bh, idd, 1u);
-                            tc::mma_f16(d + NBY, al, bl, idd, 1u);
-                        } else {
-                            tc::mma_f16(d, ah, bl, idd, 1u);
-                            tc::mma_f16(d, al, bh, idd, 1u);
-                        }
+                for (int s = 0; s < 8; ++s) {
+                    const uint32_t ka = (uint32_t)((s >> 2) * 128 * 128 + (s & 3) * 32);
+                    const uint32_t kbo = (uint32_t)((s >> 2) * 2 * NBY * 128 + (s & 3) * 32);
+                    const uint64_t ah = tc::desc_sw128(tc::smem_u32(AMh) + ka),
+                                   al = tc::desc_sw128(tc::smem_u32(AMl) + ka);
+                    const uint64_t bh = tc::desc_sw128(tc::smem_u32(byh) + kbo),
+                                   bl = tc::desc_sw128(tc::smem_u32(byl) + kbo);
+                    const uint32_t acc = s > 0 ? 1u : 0u;
+                    tc::mma_f16(d, ah, bh, idd, acc);
+                    if (F16) {
+                        tc::mma_f16(d + 2u * NBY, ah, bl, idd, acc);
+                        tc::mma_f16(d + 2u * NBY, al, bh, idd, 1u);
+                        tc::mma_f16(d + 2u * NBY, al, bl, idd, 1u);
+                    } else {
+                        tc::mma_f16(d, ah, bl, idd, 1u);
+                        tc::mma_f16(d, al, bh, idd, 1u);
                     }
                 }
                 tc::mma_commit(&empty_bar[st]);
@@ -1023,7 +1024,7 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
             const int off = spin ? nu : 0, ns = spin ? nd : nu;
             const bool row_ok = p < np;
             const float sc = F16 ? pow2f(-(sA[r] + yex[2 * u + half])) : 1.f;
-            const uint32_t dcol = (uint32_t)(u % nbuf) * 2u * dms + (uint32_t)half * dms;
+            const uint32_t dcol = (uint32_t)(u % nbuf) * 2u * dms + (uint32_t)half * NBY;
             float* Mg = Ms + (size_t)half * PG * S2 * 2;
             float* Mrow = Mg + 2 * ((size_t)p * S2 + (spin ? nu * nu : 0));
             for (int c0 = 0; c0 < 2 * nt; c0 += 16) {
@@ -1031,7 +1032,7 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
                 tc::tmem_ld16(taddr + lane_base + dcol + (uint32_t)c0, v);
                 if (F16) {
                     float vc[16];
-                    tc::tmem_ld16(taddr + lane_base + dcol + (uint32_t)NBY + (uint32_t)c0, vc);
+                    tc::tmem_ld16(taddr + lane_base + dcol + 2u * (uint32_t)NBY + (uint32_t)c0, vc);
                     tc::tmem_ld_wait();
 #pragma unroll
                     for (int q = 0; q < 16; ++q) v[q] += vc[q];
