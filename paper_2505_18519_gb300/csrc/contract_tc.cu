@@ -1066,18 +1066,30 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
             tc::named_sync<TC_THREADS>();
             // per pair: sums over its rows in FP32 (FP64 is slow on this part), the
             // energy term of the matrix, then one FP64 accumulation per pair and unit
-            if (tid < 2 * PG) {
-                const int hh = tid / PG, pp = tid % PG;
-                float2 c = make_float2(0.f, 0.f);
-                if (pp < np) {
-                    float trx = 0.f, tryy = 0.f, exx = 0.f, exy = 0.f;
+            // lpp consecutive threads (one warp) share the rows of a pair, then combine by shuffles
+            {
+                const int lpp = 8 * PG <= TC_THREADS ? 4 : (4 * PG <= TC_THREADS ? 2 : 1);
+                const int slot = tid / lpp, q = tid % lpp;
+                const int hh = slot / PG, pp = slot % PG;
+                const bool mine = slot < 2 * PG && pp < np;
+                float trx = 0.f, tryy = 0.f, exx = 0.f, exy = 0.f;
+                if (mine) {
                     const float2* rt = &red_tr[hh][pp * nt];
                     const float2* re = &red_ex[hh][pp * nt];
-                    for (int cc = 0; cc < nt; ++cc) {
+                    for (int cc = q; cc < nt; cc += lpp) {
                         const float2 x = rt[cc], y = re[cc];
                         trx += x.x; tryy += x.y;
                         exx += y.x; exy += y.y;
                     }
+                }
+                for (int o = 1; o < lpp; o <<= 1) {   // every epilogue thread takes part
+                    trx += __shfl_xor_sync(0xffffffffu, trx, o);
+                    tryy += __shfl_xor_sync(0xffffffffu, tryy, o);
+                    exx += __shfl_xor_sync(0xffffffffu, exx, o);
+                    exy += __shfl_xor_sync(0xffffffffu, exy, o);
+                }
+                if (mine && q == 0) {
+                    float2 c = make_float2(0.f, 0.f);
                     const int ge = 2 * u + hh;    // index into (h, L_0, L_1, ...)
                     if (ge == 0) {
                         c = make_float2(trx, tryy);
@@ -1085,8 +1097,8 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
                         vpair[(pairbase + pp) * (long long)G + (ge - 1)] = cmk((double)trx, (double)tryy);
                         c = make_float2(0.5f * (trx * trx - tryy * tryy - exx), 0.5f * (2.f * trx * tryy - exy));
                     }
+                    red_c2[hh][pp] = c;
                 }
-                red_c2[hh][pp] = c;
             }
             tc::named_sync<TC_THREADS>();
             if (tid < np) {
