@@ -868,7 +868,6 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
     __shared__ uint32_t tslot;
     __shared__ float2 red_tr[2][128], red_ex[2][128];
     __shared__ double2 eacc[2][TCY_MAXPG];
-    __shared__ float2 red_c2[2][TCY_MAXPG];
     __shared__ int sA[128];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1097,13 +1096,8 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
                         vpair[(pairbase + pp) * (long long)G + (ge - 1)] = cmk((double)trx, (double)tryy);
                         c = make_float2(0.5f * (trx * trx - tryy * tryy - exx), 0.5f * (2.f * trx * tryy - exy));
                     }
-                    red_c2[hh][pp] = c;
+                    eacc[hh][pp] = cadd(eacc[hh][pp], cmk((double)c.x, (double)c.y));   // one thread per slot
                 }
-            }
-            tc::named_sync<TC_THREADS>();
-            if (tid < np) {
-                const float2 a = red_c2[0][tid], b = red_c2[1][tid];
-                eacc[0][tid] = cadd(eacc[0][tid], cmk((double)(a.x + b.x), (double)(a.y + b.y)));
             }
             tc::fence_before_sync();
             tc::named_sync<TC_THREADS>();
@@ -1112,7 +1106,7 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
             if (tid == 0) tc::mbar_arrive(&mempty[b]);   // D_M buffer b has been read
         }
         if (failed && tid == 0) atomicOr(status, STATUS_TIMEOUT);
-        if (!failed && tid < np) epair[pairbase + tid] = eacc[0][tid];
+        if (!failed && tid < np) epair[pairbase + tid] = cadd(eacc[0][tid], eacc[1][tid]);
     }
     tc::fence_before_sync();
     __syncthreads();
