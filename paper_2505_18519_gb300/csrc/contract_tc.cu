@@ -605,7 +605,7 @@ __host__ __device__ __forceinline__ size_t tcy_unit_bytes(int NBY) { return 4 * 
 
 template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tcy_y_kernel(int N, int nu, int nd, int G, int NBY, int S, const uint8_t* __restrict__ image,
+    tcy_y_kernel(int N, int nu, int nd, int G, int NBY, int S, int parts, const uint8_t* __restrict__ image,
                  const int* __restrict__ lexp, const double2* __restrict__ phi, uint8_t* __restrict__ yimg,
                  int* __restrict__ yexp, int* status) {
     extern __shared__ uint8_t smraw[];
@@ -627,9 +627,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, half = warp >> 2;
-    const long long w = blockIdx.x;
+    const long long w = blockIdx.x / parts;   // walker; its units are split over `parts` blocks
     const int G1 = G + 1;
     const int n_units = (G1 + 1) / 2;
+    const int upp = (n_units + parts - 1) / parts;
+    const int u0 = (int)(blockIdx.x % parts) * upp;
+    const int nloc = max(0, min(n_units, u0 + upp) - u0);   // units of this block: u0 .. u0 + nloc - 1
     const double2* phw = phi + w * (long long)N * nt;
     uint8_t* yout = yimg + (size_t)w * n_units * unit_bytes;
     int* yex = yexp + (size_t)w * 2 * n_units;
@@ -665,9 +668,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     int loaded = 0, consumed = 0;   // meaningful in thread 0
     if (tid == 0) {
-        for (; loaded < S && loaded < n_units; ++loaded) {
+        for (; loaded < S && loaded < nloc; ++loaded) {
             tc::mbar_arrive_expect_tx(&full_bar[loaded], TC_UNIT);
-            tc::bulk_g2s(XR + (size_t)loaded * TC_UNIT, image + (size_t)loaded * TC_UNIT, TC_UNIT, &full_bar[loaded]);
+            tc::bulk_g2s(XR + (size_t)loaded * TC_UNIT, image + (size_t)(u0 + loaded) * TC_UNIT, TC_UNIT,
+                         &full_bar[loaded]);
         }
     }
     // PW: rows c = [Re phi_w | Im phi_w] (column c), K = i
@@ -696,16 +700,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool failed = false;
 
     auto refill_upto = [&](int last_consumed) -> bool {
-        while (loaded < n_units && loaded - S <= last_consumed) {
+        while (loaded < nloc && loaded - S <= last_consumed) {
             const int v = loaded - S, st = loaded % S;
             if (v >= 0 && !tc::mbar_wait(&empty_bar[st], (uint32_t)((v / S) & 1))) return false;
             tc::mbar_arrive_expect_tx(&full_bar[st], TC_UNIT);
-            tc::bulk_g2s(XR + (size_t)st * TC_UNIT, image + (size_t)loaded * TC_UNIT, TC_UNIT, &full_bar[st]);
+            tc::bulk_g2s(XR + (size_t)st * TC_UNIT, image + (size_t)(u0 + loaded) * TC_UNIT, TC_UNIT, &full_bar[st]);
             ++loaded;
         }
         return true;
     };
-    // GEMM-Y of unit u (thread 0): D_Y = X(unit) PW^T
+    // GEMM-Y of this block's unit u (local index; thread 0): D_Y = X(unit) PW^T
     auto issue_Y = [&](int u) -> bool {
         const int st = u % S;
         if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) return false;
@@ -731,12 +735,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ++consumed;
         return refill_upto(u - 1);
     };
-    if (tid == 0 && !issue_Y(0)) fail_flag = 1;
+    if (tid == 0 && nloc > 0 && !issue_Y(0)) fail_flag = 1;
 
     const int gi = Lrow / 64, jrow = Lrow % 64;      // D_Y row: matrix in unit, j
     const int ch = (nt + 1) / 2;                      // walker columns per half
     const int cl = half * ch, cn = min(nt, cl + ch) - cl;
-    for (int u = 0; u < n_units && !failed; ++u) {
+    for (int v = 0; v < nloc && !failed; ++v) {
+        const int u = u0 + v;   // unit of the walker's image
         __syncwarp();
         {
             bool ok = fail_flag == 0 && tc::mbar_wait(&ybar, y_ph);
@@ -818,7 +823,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (tid == 0) {
             yex[2 * u] = F16 ? row_exp(ymax[u & 1][0]) : 0;
             yex[2 * u + 1] = F16 ? row_exp(ymax[u & 1][1]) : 0;
-            if (u + 1 < n_units && !issue_Y(u + 1)) fail_flag = 1;
+            if (v + 1 < nloc && !issue_Y(v + 1)) fail_flag = 1;
         }
         const uint4* src = reinterpret_cast<const uint4*>(BY);
         uint4* dst = reinterpret_cast<uint4*>(yout + (size_t)u * unit_bytes);
@@ -1176,8 +1181,11 @@ static cudaError_t launch_tcy(cudaStream_t st, const Dims& d, const TcyShape& s,
     int* yexp = reinterpret_cast<int*>(yimg + (size_t)W * n_units * tcy_unit_bytes(s.NBY));
     cudaError_t e = raise_smem_limit((const void*)tcy_y_kernel<F16>, s.smem_y);
     if (e != cudaSuccess) return e;
-    tcy_y_kernel<F16><<<(unsigned)W, TC_THREADS, s.smem_y, st>>>(d.N, d.nu, d.nd, d.G, s.NBY, s.SY,
-                                                                 (const uint8_t*)image, lexp, phi, yimg, yexp, status);
+    // each walker's units over two blocks: twice the blocks fill the last wave better
+    const int parts = n_units >= 2 ? 2 : 1;
+    tcy_y_kernel<F16><<<(unsigned)(W * parts), TC_THREADS, s.smem_y, st>>>(d.N, d.nu, d.nd, d.G, s.NBY, s.SY, parts,
+                                                                           (const uint8_t*)image, lexp, phi, yimg,
+                                                                           yexp, status);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = raise_smem_limit((const void*)contract_tcy_kernel<F16>, s.smem);
