@@ -128,7 +128,11 @@ typedef struct {
  * and zero sizes. */
 void afqmc_config_default(afqmc_config* cfg);
 
-/* Bytes of device workspace the configuration needs (0 if cfg is invalid). */
+/* Bytes of device workspace the configuration needs (0 if cfg is invalid).  Besides
+ * the state and per-pair buffers it holds, for the walker-side contraction forms,
+ * Y_g = L_g phi_w of every walker: (n_chol + 1) N 2 (n_up + n_dn) doubles per walker
+ * in FP64 (4 MB per walker on the 50-orbital system), or the split-FP16 images
+ * of it (6.2 MB per walker there). */
 size_t afqmc_workspace_bytes(const afqmc_config* cfg);
 
 /* Create a context.
