@@ -13,7 +13,7 @@
 // 2 sum_k I_k(rho) T_k(t)] on an interval [c - rho, c + rho] holding the
 // spectrum of S, modified Bessel I_k by Miller's backward recurrence in FP64
 // (one thread, scalar), truncated once the coefficients fall below 1e-18 of
-// e^rho.  The partial sums cancel by about e^(rho - rho_true) when rho
+// e^rho (1e-15 when the recurrence runs in double-float, about 2^-44).  The partial sums cancel by about e^(rho - rho_true) when rho
 // overestimates the spectral half-width, which multiplies the rounding error
 // and the number of terms; the Gershgorin half-width of the sampled S is
 // 3 to 4 times the spectral one.  So the interval comes from a short Lanczos
@@ -44,7 +44,7 @@ __device__ __forceinline__ float block_sum_f(float v, float* red8) {
 // Chebyshev coefficients of exp on [c - rho, c + rho] (Miller's backward
 // recurrence for I_k(rho), normalised by sum = e^rho), scaled by e^(c + rho);
 // returns the number of terms m.  One thread.
-__device__ int cheb_coefs(double c, double rho, double* coef, int* status) {
+__device__ int cheb_coefs(double c, double rho, double tol, double* coef, int* status) {
     int start = (int)ceil(rho) + 48;
     if (!isfinite(rho) || start > CHEB_DF_MAX) {
         atomicOr(status, STATUS_NONFINITE);
@@ -68,7 +68,7 @@ __device__ int cheb_coefs(double c, double rho, double* coef, int* status) {
     for (int k = 1; k <= start; ++k) norm += 2.0 * coef[k];   // = e^rho in Miller's units
     int m = start;
     for (int k = 1; k <= start; ++k) {
-        if (coef[k] < 1e-18 * norm) { m = k; break; }
+        if (coef[k] < tol * norm) { m = k; break; }
     }
     const double scale = exp(c + rho) / norm;
     coef[0] *= scale;
@@ -199,17 +199,19 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (tid == 0) {
             const double c = attempt == 0 ? est_c : gers_c, rho = attempt == 0 ? est_rho : gers_rho;
-            const int m = cheb_coefs(c, rho, coef, status);
+            // 0 double-float with the growth check, 1 double-float, 2 FP64 with the
+            // growth check, 3 FP64
+            if (allow_df) mode = attempt == 0 ? 0 : (rho <= RHO_DF ? 1 : 3);
+            else mode = attempt == 0 ? 2 : 3;
+            // truncation below the arithmetic's own resolution: about 2^-44 in double-float
+            // (1e-15 of e^rho), FP64 rounding (1e-18)
+            const int m = cheb_coefs(c, rho, mode < 2 ? 1e-15 : 1e-18, coef, status);
             for (int k = 0; k <= m; ++k) coefd[k] = df_from(coef[k]);
             nterms = m;
             cshift = c;
             irho = 1.0 / rho;
             cshift_d = df_from(c);
             irho_d = df_from(1.0 / rho);
-            // 0 double-float with the growth check, 1 double-float, 2 FP64 with the
-            // growth check, 3 FP64
-            if (allow_df) mode = attempt == 0 ? 0 : (rho <= RHO_DF ? 1 : 3);
-            else mode = attempt == 0 ? 2 : 3;
         }
         __syncthreads();
         const int m = nterms;
