@@ -391,9 +391,8 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
     if ((st = prof_mark(ctx, PH_PROPOSE)) != AFQMC_OK) return st;
     CK(trial_orbitals_of(ctx, d.pairs, w.Phiprop, w.alive, d.P));
     if ((st = prof_mark(ctx, PH_TRIAL)) != AFQMC_OK) return st;
-    for (int spin = 0; spin < 2; ++spin)
-        CK(overlap_lu(s, d, spin, w.Phiprop, (long long)d.N * d.nu, orbitals, w.logdet_prop, nullptr, w.alive, w.status,
-                      d.pairs, d.P));
+    CK(overlap_lu_both(s, d, w.Phiprop, (long long)d.N * d.nu, orbitals, w.logdet_prop, nullptr, w.alive, w.status,
+                       d.pairs, d.P));
     if ((st = prof_mark(ctx, PH_MCMC_OVERLAP)) != AFQMC_OK) return st;
     CK(accept(s, d, p, w.counters, tag_acc, sweep, w.logdet_prop, w.xprop, w.Phiprop, w.alive, w.mlp.mu, w.mlp.logv,
               w.logov_cur, w.x, w.Phi, w.counters));
@@ -411,9 +410,8 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     const bool fp64 = ctx->cfg.precision == AFQMC_PRECISION_FP64;
     const int ovl = fp64 ? (contract_fp64_walker_side(d.N, d.nu, d.nd, d.P) ? OVL_INVERSE : OVL_THETA)
                          : (contract_tc_walker_side(d.N, d.nu, d.nd, f16) ? OVL_TRIAL : OVL_THETA);
-    for (int spin = 0; spin < 2; ++spin)
-        CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
-                      ovl));
+    CK(overlap_lu_both(s, d, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
+                       ovl));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64) {
         CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.Yimg, w.vpair, w.epair, w.status, f16));
@@ -562,9 +560,8 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         else
             CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive, w.propbuf));   // Eq. (12)
         if ((st = prof_mark(ctx, PH_PROPAGATE)) != AFQMC_OK) return st;
-        for (int spin = 0; spin < 2; ++spin)
-            CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi_new, w.logdet_new, nullptr, w.alive, w.status,
-                          d.pairs, d.P));
+        CK(overlap_lu_both(s, d, w.Phi, (long long)d.N * d.nu, w.phi_new, w.logdet_new, nullptr, w.alive, w.status,
+                           d.pairs, d.P));
         CK(ratios(s, d, w.logov, w.logdet_new, w.sumS, w.logshift, w.alive, w.logov_cur, w.old_sum, w.ratio, w.Iabs));
         if ((st = prof_mark(ctx, PH_RATIO)) != AFQMC_OK) return st;
         if (ctx->cfg.proposal == AFQMC_PROPOSAL_MLP) {       // proposal conditioned on the new walkers

@@ -14,6 +14,11 @@ enum OverlapOutput { OVL_THETA = 0, OVL_TRIAL = 1, OVL_INVERSE = 2 };
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
                        long long pairs, int P, int trial_side = OVL_THETA);
+// Both spins: one warp per pair (half a warp per spin) when n_up <= 16, else
+// overlap_lu for each spin.  Same results.
+cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, long long Phi_stride,
+                            const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
+                            long long pairs, int P, int trial_side = OVL_THETA);
 cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, double2* dst, const int* alive,
                              int* status, int n_walkers);
 // Phi = exp(S) Phi0 for `problems` symmetric S (FP64).  trial_orbitals runs the

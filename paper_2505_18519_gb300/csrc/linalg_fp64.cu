@@ -265,6 +265,206 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
     return cudaGetLastError();
 }
 
+// Both spins of a pair in one warp, lanes 0-15 on spin up and 16-31 on spin
+// down, for n_up <= 16: the same arithmetic as overlap_lu_kernel per spin, but the
+// pivot search, the scalar work on each pivot and the column-wise inverse run for
+// the two spins at once instead of on 10-odd lanes of a warp each.  Every lane
+// reaches every warp synchronisation: a spin with fewer (or no) electrons, or a
+// singular overlap, only skips the work of its half.
+__global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long pairs, int P,
+                                       const double* __restrict__ Phi, long long Phi_stride,
+                                       const double2* __restrict__ phi, double2* __restrict__ logdet,
+                                       double2* __restrict__ Theta, const int* __restrict__ alive, int* status,
+                                       int trial_side) {
+    extern __shared__ double2 sm[];
+    const unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const long long pair = (long long)blockIdx.x * wpb + warp;
+    if (pair >= pairs) return;                   // uniform across the warp
+    const long long w = pair / P;
+    if (alive && !alive[w]) return;              // uniform across the warp
+    const int h = lane >> 4, hl = lane & 15;     // half = spin, lane within the half
+    const int n = h ? nd : nu, col0 = h ? nu : 0;
+    const size_t mats = (size_t)nu * nu * (Theta ? 2 : 1);
+    double2* A = sm + (size_t)(warp * 2 + h) * (mats + nu + (nu + 1) / 2 + 1);
+    double2* Ainv = A + (size_t)n * n;
+    double2* dinv = A + mats;                    // 1 / u_kk
+    int* perm = reinterpret_cast<int*>(dinv + nu);
+    const double* Ph = Phi + pair * Phi_stride;         // N x nu, spin uses the first n columns
+    const double2* ph = phi + w * (long long)N * nt + col0;  // N x nt
+    for (int e = hl; e < n * n; e += 16) {
+        const int a = e / n, b = e - a * n;
+        double2 s = cmk(0.0, 0.0);
+        for (int i = 0; i < N; ++i) {
+            const double f = Ph[(long long)i * nu + a];
+            const double2 g = ph[(long long)i * nt + b];
+            s.x = fma(f, g.x, s.x);
+            s.y = fma(f, g.y, s.y);
+        }
+        A[e] = s;
+    }
+    for (int r = hl; r < n; r += 16) perm[r] = r;
+    __syncwarp();
+    double2 z = cmk(1.0, 0.0);
+    int zexp = 0;
+    bool odd = false;
+    bool singular = false;
+    for (int k = 0; k < nu; ++k) {               // nu >= nd: the same trip count in both halves
+        const bool act = k < n && !singular;     // uniform within a half
+        double best = -1.0;
+        int bi = k;
+        if (act)
+            for (int r = k + hl; r < n; r += 16) {
+                const double m = fabs(A[r * n + k].x) + fabs(A[r * n + k].y);
+                if (m > best) { best = m; bi = r; }
+            }
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) {
+            const double ob = __shfl_down_sync(FULL, best, off, 16);
+            const int oi = __shfl_down_sync(FULL, bi, off, 16);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        best = __shfl_sync(FULL, best, 0, 16);
+        bi = __shfl_sync(FULL, bi, 0, 16);
+        if (act && !(best > 0.0)) singular = true;
+        const bool go = act && !singular;
+        if (go && bi != k) {
+            for (int c = hl; c < n; c += 16) {
+                const double2 t = A[k * n + c];
+                A[k * n + c] = A[bi * n + c];
+                A[bi * n + c] = t;
+            }
+            if (hl == 0) { const int t = perm[k]; perm[k] = perm[bi]; perm[bi] = t; }
+            odd = !odd;
+        }
+        __syncwarp();
+        if (go) {
+            const double2 piv = A[k * n + k];
+            const double q = 1.0 / fma(piv.x, piv.x, piv.y * piv.y);
+            const double2 rinv = cmk(piv.x * q, -piv.y * q);   // 1 / piv
+            if (hl == 0) dinv[k] = rinv;
+            z = cmul(z, piv);
+            const double mz = fmax(fabs(z.x), fabs(z.y));
+            int ex = (int)((__double_as_longlong(mz) >> 52) & 0x7FF) - 1023;
+            ex = max(-1000, min(1000, ex));
+            const double f = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex, exact
+            z = cmk(z.x * f, z.y * f);
+            zexp += ex;
+            for (int r = k + 1 + hl; r < n; r += 16) A[r * n + k] = cmul(A[r * n + k], rinv);
+        }
+        __syncwarp();
+        if (go) {
+            const int m = n - k - 1;
+            for (int e = hl; e < m * m; e += 16) {
+                const int r = k + 1 + e / m, c = k + 1 + e % m;
+                double2 t = A[r * n + c];
+                const double2 l = A[r * n + k], u = A[k * n + c];
+                t.x -= l.x * u.x - l.y * u.y;
+                t.y -= l.x * u.y + l.y * u.x;
+                A[r * n + c] = t;
+            }
+        }
+        __syncwarp();
+    }
+    if (n == 0) {
+        if (hl == 0) logdet[pair * 2 + h] = cmk(0.0, 0.0);
+    } else if (singular) {
+        if (hl == 0) {
+            logdet[pair * 2 + h] = cmk(-INFINITY, 0.0);
+            atomicOr(status, STATUS_SINGULAR);
+        }
+        if (Theta && trial_side == 2) {
+            double2* Wp = Theta + pair * (long long)N * nt + (h ? (long long)nu * nu : 0);
+            for (int e = hl; e < n * n; e += 16) Wp[e] = cmk(0.0, 0.0);
+        } else if (Theta) {
+            double2* Th = Theta + pair * (long long)N * nt + col0;
+            for (int e = hl; e < N * n; e += 16) Th[(long long)(e / n) * nt + e % n] = cmk(0.0, 0.0);
+        }
+    } else if (hl == 0) {
+        const double logabs = 0.5 * log(fma(z.x, z.x, z.y * z.y)) + zexp * 0.69314718055994530942;
+        logdet[pair * 2 + h] = odd ? cmk(logabs, atan2(-z.y, -z.x)) : cmk(logabs, atan2(z.y, z.x));
+    }
+    if (!Theta) return;                          // uniform: a kernel argument
+    const bool inv = n > 0 && !singular;
+    // A^-1 column c: solve L y = P e_c (unit lower), then U x = y.
+    if (inv)
+        for (int c = hl; c < n; c += 16) {
+            for (int r = 0; r < n; ++r) {
+                double2 s = cmk(perm[r] == c ? 1.0 : 0.0, 0.0);
+                for (int j = 0; j < r; ++j) {
+                    const double2 l = A[r * n + j], yj = Ainv[j * n + c];
+                    s.x -= l.x * yj.x - l.y * yj.y;
+                    s.y -= l.x * yj.y + l.y * yj.x;
+                }
+                Ainv[r * n + c] = s;
+            }
+            for (int r = n - 1; r >= 0; --r) {
+                double2 s = Ainv[r * n + c];
+                for (int j = r + 1; j < n; ++j) {
+                    const double2 u = A[r * n + j], xj = Ainv[j * n + c];
+                    s.x -= u.x * xj.x - u.y * xj.y;
+                    s.y -= u.x * xj.y + u.y * xj.x;
+                }
+                Ainv[r * n + c] = cmul(s, dinv[r]);
+            }
+        }
+    __syncwarp();
+    if (!inv) return;                            // nothing below synchronises the warp
+    if (trial_side == 2) {
+        double2* Wp = Theta + pair * (long long)N * nt + (h ? (long long)nu * nu : 0);
+        for (int e = hl; e < n * n; e += 16) Wp[e] = Ainv[e];
+        return;
+    }
+    double2* Th = Theta + pair * (long long)N * nt + col0;
+    if (trial_side) {
+        for (int e = hl; e < N * n; e += 16) {
+            const int i = e / n, b = e - i * n;
+            double2 s = cmk(0.0, 0.0);
+            const double* row = Ph + (long long)i * nu;
+            for (int a = 0; a < n; ++a) {
+                const double2 t = Ainv[b * n + a];
+                s.x = fma(row[a], t.x, s.x);
+                s.y = fma(row[a], t.y, s.y);
+            }
+            Th[(long long)i * nt + b] = s;
+        }
+        return;
+    }
+    for (int e = hl; e < N * n; e += 16) {
+        const int i = e / n, b = e - i * n;
+        double2 s = cmk(0.0, 0.0);
+        const double2* row = ph + (long long)i * nt;
+        for (int a = 0; a < n; ++a) cfma(s, row[a], Ainv[a * n + b]);
+        Th[(long long)i * nt + b] = s;
+    }
+}
+
+cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, long long Phi_stride,
+                            const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
+                            long long pairs, int P, int trial_side) {
+    if (d.nu > 16) {   // a half-warp per spin would leave the larger matrices short of lanes
+        for (int spin = 0; spin < 2; ++spin) {
+            const cudaError_t e = overlap_lu(s, d, spin, Phi, Phi_stride, phi, logdet, Theta, alive, status, pairs, P,
+                                             trial_side);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    if (pairs <= 0) return cudaSuccess;
+    const size_t per = 2 * ((size_t)d.nu * d.nu * (Theta ? 2 : 1) + d.nu + (d.nu + 1) / 2 + 1) * sizeof(double2);
+    int wpb = d.ov_wpb > 0 ? d.ov_wpb : 4;
+    while (wpb > 1 && per * wpb > 200 * 1024) wpb >>= 1;
+    const size_t smem = per * wpb;
+    cudaError_t e = raise_smem_limit((const void*)overlap_lu_both_kernel, smem);
+    if (e != cudaSuccess) return e;
+    const long long blocks = (pairs + wpb - 1) / wpb;
+    overlap_lu_both_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nd, d.nt, pairs, P, Phi, Phi_stride,
+                                                                    phi, logdet, Theta, alive, status, trial_side);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- re-orthonormalisation
 // One warp per (walker, spin): modified Gram-Schmidt on the N x n complex
 // block (columns col0..), q_j = (v_j - sum_k<j (q_k^H v_j) q_k) / norm, so
