@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <map>
+#include <algorithm>
 #include <mutex>
 #include <utility>
 
@@ -241,6 +242,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     const bool prop_df = c->precision != AFQMC_PRECISION_FP64 && propagate_in_smem(d.N, d.nt);
     w.Ldf = prop_df || refine_enabled(c) ? take(G * NN * 8) : nullptr;
     w.hdf = refine_enabled(c) ? take(NN * 8) : nullptr;
+    w.xdf = c->precision != AFQMC_PRECISION_FP64 ? take(std::max(pairs * K, 2 * W * G) * 8) : nullptr;
     w.expTdf = prop_df ? take(NN * 8) : nullptr;
     w.scratchNN = (double*)take(3 * NN * 8);
     w.Lt = c->precision != AFQMC_PRECISION_FP64
@@ -360,7 +362,7 @@ static cudaError_t form_S(afqmc_ctx* ctx, const double* X, long long M) {
     const Dims& d = ctx->d;
     Workspace& w = ctx->ws;
     const long long NN = (long long)d.N * d.N;
-    if (s_in_df(ctx)) return gemm_df(ctx->stream, (int)M, (int)NN, d.K, X, w.Udf, w.Sprop);
+    if (s_in_df(ctx)) return gemm_df(ctx->stream, (int)M, (int)NN, d.K, X, w.Udf, w.Sprop, w.xdf);
     gemm_nn_f64(ctx->stream, (int)M, (int)NN, d.K, 1.0, X, d.K, w.U, NN, 0.0, w.Sprop, NN);
     return cudaGetLastError();
 }
@@ -548,7 +550,7 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         if ((st = measure(ctx)) != AFQMC_OK) return st;      // Eq. (25)-(27), (16) at phi
         CK(fields(s, d, p, w.counters, w.vbar, w.sumS, w.weight, w.alive, (double*)w.y, w.logshift));
         if (w.expTdf) {   // mixed precision: field planes and propagation in double-float
-            CK(gemm_df(s, 2 * d.W, d.N * d.N, d.G, (const double*)w.y, w.Ldf, w.Aplanes));
+            CK(gemm_df(s, 2 * d.W, d.N * d.N, d.G, (const double*)w.y, w.Ldf, w.Aplanes, w.xdf));
         } else {
             gemm_nn_f64(s, 2 * d.W, d.N * d.N, d.G, 1.0, (const double*)w.y, d.G, w.L, (long long)d.N * d.N, 0.0,
                         w.Aplanes, (long long)d.N * d.N);

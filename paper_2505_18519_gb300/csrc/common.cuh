@@ -152,6 +152,7 @@ struct Workspace {
     double* expT;     // N*N, exp(-tau T / 2)
     void* Ldf;        // G*N*N double-float copy of L (mixed-precision path)
     void* hdf;        // N*N double-float copy of h (refinement of the mixed path)
+    void* xdf;        // max(W*P*K, 2W*G) double-float coefficients of the double-float GEMMs (mixed path)
     void* expTdf;     // N*N double-float copy of expT (mixed-precision path)
     double* scratchNN;  // 3*N*N for the matrix exponential at init
     void* Lt;           // split-BF16 image of (h, L_g) for the tensor-core contraction

@@ -39,7 +39,10 @@ bool trial_orbitals_df_supported(int N, int nu);
 // S = X U in double-float (X FP64 M x K, U as double-float K x Nc from u_to_df);
 // S is written as double-float pairs, 8 bytes per element
 cudaError_t u_to_df(cudaStream_t s, long long n, const double* U, void* Ud);
-cudaError_t gemm_df(cudaStream_t s, int M, int Nc, int K, const double* X, const void* Ud, double* S);
+// Xdf (optional): M*K*8 bytes of work space to hold X in double-float, formed
+// once instead of once per column tile of S.
+cudaError_t gemm_df(cudaStream_t s, int M, int Nc, int K, const double* X, const void* Ud, double* S,
+                    void* Xdf = nullptr);
 cudaError_t one_body_propagator(cudaStream_t s, int N, int G, double dtau, const double* h, const double* L, double* T,
                                 double* scratch3, double* expT);
 

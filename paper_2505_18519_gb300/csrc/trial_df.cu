@@ -415,8 +415,11 @@ __global__ void u_to_df_kernel(long long n, const double* __restrict__ U, dfl* _
         Ud[e] = df_from(U[e]);
 }
 
+// XDF: X already in double-float (Xd); else rounded from FP64 as its tiles load.
+template <bool XDF>
 __global__ void __launch_bounds__(256) gemm_df_kernel(int M, int Nc, int K, const double* __restrict__ X,
-                                                      const dfl* __restrict__ Ud, dfl* __restrict__ S) {
+                                                      const dfl* __restrict__ Xd, const dfl* __restrict__ Ud,
+                                                      dfl* __restrict__ S) {
     __shared__ dfl Xs[DG_K][DG_T + 1];
     __shared__ dfl Us[DG_K][DG_T];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -431,7 +434,8 @@ __global__ void __launch_bounds__(256) gemm_df_kernel(int M, int Nc, int K, cons
             const int r = e / DG_K, kk = e % DG_K;        // X tile: 64 rows x 16 k
             const long long gr = row0 + r;
             const int gk = k0 + kk;
-            Xs[kk][r] = (gr < M && gk < K) ? df_from(X[gr * K + gk]) : dfl{0.f, 0.f};
+            if constexpr (XDF) Xs[kk][r] = (gr < M && gk < K) ? Xd[gr * K + gk] : dfl{0.f, 0.f};
+            else Xs[kk][r] = (gr < M && gk < K) ? df_from(X[gr * K + gk]) : dfl{0.f, 0.f};
             const int kb = e / DG_T, c = e % DG_T;        // U tile: 16 k x 64 cols
             const long long gc = col0 + c;
             const int gkb = k0 + kb;
@@ -479,10 +483,18 @@ cudaError_t u_to_df(cudaStream_t s, long long n, const double* U, void* Ud) {
     return cudaGetLastError();
 }
 
-cudaError_t gemm_df(cudaStream_t s, int M, int Nc, int K, const double* X, const void* Ud, double* S) {
+cudaError_t gemm_df(cudaStream_t s, int M, int Nc, int K, const double* X, const void* Ud, double* S, void* Xdf) {
     if (M <= 0 || Nc <= 0) return cudaSuccess;
     dim3 grid((unsigned)((Nc + DG_T - 1) / DG_T), (unsigned)((M + DG_T - 1) / DG_T));
-    gemm_df_kernel<<<grid, 256, 0, s>>>(M, Nc, K, X, reinterpret_cast<const dfl*>(Ud), reinterpret_cast<dfl*>(S));
+    if (Xdf) {   // X to double-float once (its FP64 rounding would otherwise run once per column tile)
+        const cudaError_t e = u_to_df(s, (long long)M * K, X, Xdf);
+        if (e != cudaSuccess) return e;
+        gemm_df_kernel<true><<<grid, 256, 0, s>>>(M, Nc, K, X, reinterpret_cast<const dfl*>(Xdf),
+                                                  reinterpret_cast<const dfl*>(Ud), reinterpret_cast<dfl*>(S));
+    } else {
+        gemm_df_kernel<false><<<grid, 256, 0, s>>>(M, Nc, K, X, nullptr, reinterpret_cast<const dfl*>(Ud),
+                                                   reinterpret_cast<dfl*>(S));
+    }
     count_launches(1);
     return cudaGetLastError();
 }
