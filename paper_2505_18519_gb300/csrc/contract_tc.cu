@@ -582,21 +582,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // With Theta_p = phi_w A_p^-1 and B_p = Phi_p A_p^-T, the matrix
 // M'_g = B_p^T (X_g phi_w) = A_p^-1 M_g A_p has the traces of M_g = Phi_p^T X_g Theta_p,
 // and Y_g = X_g phi_w depends on the walker only.  Two kernels:
-//   tcy_y_kernel (one block per walker) forms, per operand unit of two matrices,
+//   tcy_y_kernel (two blocks per walker, half of its units each) forms, per
+//     operand unit of two matrices,
 //     GEMM-Y  D_Y[(g, j), c] = sum_i X_g[j, i] PW[c, i],  PW rows c = [Re phi | Im phi],
 //     and its epilogue: the split image BY_g with rows
 //       BY row (col', re) = [Re Y_g[:, col'] | -Im Y_g[:, col']],
 //       BY row (col', im) = [Im Y_g[:, col'] |  Re Y_g[:, col']]   (K = 2 x 64),
-//     per-matrix power-of-two scale, written to global memory in the swizzled
-//     layout the MMAs read, plus the scale exponents;
+//     per-matrix power-of-two scale, the two matrices' images as one operand of
+//     2 NBY rows, written to global memory in the swizzled layout the MMAs read,
+//     plus the scale exponents;
 //   contract_tcy_kernel (one block per PG pairs of a walker) streams those
 //     images through a ring of bulk copies and runs
-//     GEMM-M  D_M[(p, col), (col', ri)] = sum_k AM[(p, col), k] BY_g[(col', ri), k],
+//     GEMM-M  D_M[(p, col), (h, col', ri)] = sum_k AM[(p, col), k] BY_g+h[(col', ri), k],
 //     AM row (p, col) = [Re B_p[:, col] | Im B_p[:, col]], so
-//     D_M[(p, col), (col', re/im)] = Re/Im (B_p^T Y_g)[col, col'] (same-spin blocks used),
-//     and epilogue M (shared-memory transpose, traces, sums) with the two halves
-//     of the block on the two matrices of a unit.  With two tensor-memory buffers
-//     the next unit's GEMM-M runs while the block works on this unit's epilogue.
+//     D_M[(p, col), (h, col', re/im)] = Re/Im (B_p^T Y_g+h)[col, col'] (same-spin blocks
+//     used), one MMA per K step and product for both matrices; a producer warp
+//     issues copies and MMAs into two tensor-memory buffers while the other eight
+//     warps run epilogue M (shared-memory transpose, traces, sums) on the other,
+//     the two halves of them on the two matrices of a unit.
 // So the image of Y_g, whose epilogue dominated the fused kernel, is formed once
 // per walker instead of once per block of pairs.
 constexpr int TCY_MAXPG = 64;
