@@ -289,6 +289,13 @@ TC_TRAFFIC = {   # kernel -> (committed summary, end of its device code, start o
 }
 
 
+def hbm_peak():
+    """Measured copy bandwidth of this GPU type (GB/s) and where it came from."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = json.load(open(path)).get("hbm_gbs") if os.path.exists(path) else None
+    return (peak, "measured copy") if peak else (6800.0, "fallback copy")
+
+
 def tensor_roofline(spec, W, P, prof, kernel):
     """Algorithmic FLOP rate of the tensor-core contraction against the
     measured sustained BF16 peak (FP16 has the same nominal rate)."""
@@ -467,6 +474,46 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             "tensor_core_forms": sorted({lib.contract_kernel(c.cfg) for c in ctxs}),
             "device_status_words": [int(st["status"]) for st in stats],
             "status_bits": "1 singular overlap, 2 non-finite value (the walker is removed), 4 tensor-core wait timed out"}
+
+    if only in (None, "popctl"):
+        # the local-energy importance function and a comb after every step, on the
+        # mixed-precision step of the same workload
+        cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
+                              walker_offset=rank * W, e_shift=28.5, precision="fp16x3", importance="local_energy",
+                              pop_period=1)
+        ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
+        for _ in range(warmup):
+            ctx.step(1)
+        ctx.profile(True)
+        ms, clocks, launches = _timed(ctx.step, lambda: torch.cuda.synchronize(dev), ctx.stream, steps, world, local)
+        prof = ctx.profile_read()
+        stats = ctx.stats()
+        hist = ctx.history(steps)
+        ctx.close()
+        comb_ms = prof["ms"]["comb"] / max(1, prof["steps"])
+        # bytes a comb must move: the state (phi, x, Phi(x)) of every replaced walker read
+        # from its source and written to its slot, plus the weights
+        row = spec.N * (spec.n_up + spec.n_dn) * 16 + P * spec.K * 8 + P * spec.N * spec.n_up * 8
+        replaced = stats["comb_replaced"] / max(1, stats["combs"])
+        moved = 2 * replaced * row + 2 * W * 8
+        gbs = moved / (comb_ms / 1e3) / 1e9
+        hbm, hbm_source = hbm_peak()
+        out["population_control"] = {
+            "precision": "fp16x3", "importance": "local_energy: |I| = exp(-tau (Re E_w - E_T))",
+            "what": "same workload and mixed-precision step; a comb resamples the walkers (phi, paths x and Phi(x)) "
+                    "after every step",
+            "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "gpu_launches": launches, "clocks": clocks, "combs": int(stats["combs"]),
+            "walkers_replaced_per_comb": replaced,
+            "live_walkers_frac": stats["live_walkers"] / W,
+            "e_mix_last_step": float(hist[-1, 0] / hist[-1, 1]),
+            "comb_ms_per_step": comb_ms,
+            "roofline": {"bound": "hbm", "kernel": "comb_select_kernel + comb_gather_kernel",
+                         "achieved": gbs, "peak": hbm, "peak_source": hbm_source, "unit": "GB/s",
+                         "frac": gbs / hbm, "traffic": None, "algorithmic_bytes": moved,
+                         "note": "walkers with a copy keep their slot, so only the replaced walkers' rows move; "
+                                 "the selection (running sum of the weights, block scans) is latency-bound"},
+            "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
 
     if only in (None, "largest"):
         # the largest system (N = 200, 40 + 40 electrons, 1000 Cholesky vectors) in FP64 on a
@@ -708,7 +755,7 @@ def main():
     ap.add_argument("--walkers", type=int, default=0, help="walkers per GPU (profiling runs on a small case)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision, learned-proposal and batched measurements")
-    ap.add_argument("--only", choices=("mixed", "learned", "batched", "largest", "large_mixed"), default=None,
+    ap.add_argument("--only", choices=("mixed", "learned", "batched", "popctl", "largest", "large_mixed"), default=None,
                     help="time one variant alone (profiling); skips the FP64 headline's extras")
     args = ap.parse_args()
     if args.impl == "reference":

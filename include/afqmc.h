@@ -62,6 +62,13 @@ enum {
     AFQMC_CONSTRAINT_HALF_PLANE = 2  /* W *= |I| max(0, cos dtheta), and W = 0 if |dtheta_T| > pi/2 */
 };
 
+/* importance function |I| of the weight update (Sec. III A); the phase dtheta of
+ * the constraint comes from the overlap ratio Eq. (25) in both */
+enum {
+    AFQMC_IMPORTANCE_HYBRID = 0,       /* |I| of Eq. (14): |p(x - xbar)/p(x)| times the ratio Eq. (25) (default) */
+    AFQMC_IMPORTANCE_LOCAL_ENERGY = 1  /* |I| = exp(-tau Re E_w), E_w of Eq. (27) at the start of the step */
+};
+
 /* Metropolis proposal for the paths (Sec. III A; Appendix B.2) */
 enum {
     AFQMC_PROPOSAL_PRIOR = 0,  /* independent draw x' ~ N(0, I) (the paper's sampler) */
@@ -121,6 +128,13 @@ typedef struct {
                            walker's average, 2 sqrt(sum of the kept pairs' squared errors) / |sum_p S_p|,
                            is at most refine_tol / 2.  0 turns it off.  Default 1e-4.  Not used by the
                            walker-side tensor-core form (N <= 64, n_up + n_dn <= 40), which keeps no Theta */
+    int importance;     /* AFQMC_IMPORTANCE_* (default hybrid) */
+    int pop_period;     /* population control of the branching random walk (Sec. II B, II D): after every
+                           pop_period-th step a comb resamples the W walkers (phi, paths x and Phi(x)) in
+                           proportion to their weights and gives each the mean weight; teeth spaced sum W / W
+                           apart from u sum W / W, u a Philox uniform (tag 10, entity walker_offset, the
+                           step's index).  0 (default) turns it off; on, n_walkers <= 65535.  Each GPU of a
+                           sharded run combs its own walkers */
 } afqmc_config;
 
 /* Fill *cfg with defaults (combined constraint, prior proposal, FP64, Taylor
@@ -183,7 +197,9 @@ afqmc_status afqmc_history(afqmc_ctx* ctx, double* out, int n, int* n_out);
 /* Statistics since init (synchronises); out[0..len) receives, as available:
  *   0 steps taken, 1 accepted moves, 2 proposed moves, 3 live walkers,
  *   4 device status word (0 = fine), 5 min weight, 6 max weight, 7 sum weight,
- *   8 pairs recomputed by the refinement (see refine_tol) since init */
+ *   8 pairs recomputed by the refinement (see refine_tol) since init,
+ *   9 population-control combs applied since init (see pop_period),
+ *   10 walkers those combs replaced by copies of others */
 afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len);
 
 /* Checkpoint.  The state buffer (host memory) is, in order, with no padding:
@@ -214,8 +230,9 @@ void afqmc_destroy(afqmc_ctx* ctx);
  * mixed-estimator sums; 3 fields and the auxiliary-field matrices;
  * 4 propagation; 5 overlaps at phi' and ratios; 6 proposals and sum_k x_k U_k;
  * 7 trial orbitals exp(S) Phi0; 8 proposal overlaps; 9 acceptance;
- * 10 hand-off, re-orthonormalisation and bookkeeping. */
-#define AFQMC_PHASES 11
+ * 10 hand-off, re-orthonormalisation and bookkeeping; 11 population-control
+ * comb (see pop_period). */
+#define AFQMC_PHASES 12
 afqmc_status afqmc_profile(afqmc_ctx* ctx, int enable);
 afqmc_status afqmc_profile_read(afqmc_ctx* ctx, double* out, int len);
 

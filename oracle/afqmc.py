@@ -30,7 +30,15 @@ Readings of points where the paper is silent or ambiguous (R1-R14):
       Gaussian random walk x' = x + s xi, or the learned proposal (oracle.mlp)
       mixed with the random walk; Metropolis-Hastings with the proposal ratio.
   R9  walkers are re-orthonormalised every step (QR, diag(R) > 0).
-  R10 no population control; weights carried, optional constant E_T.
+  R10 population control (the branching random walk of Sec. II B and II D
+      leaves the scheme open): optional comb every pop_period steps, at the
+      end of the step, drawn with one Philox uniform; otherwise weights are
+      carried.  Optional constant E_T.
+  R15 importance function of the weight update (Sec. III A): "hybrid", |I| of
+      Eq. (14) with the sampled-trial ratio Eq. (25) (default), or
+      "local_energy", |I| = exp(-tau Re E_w(phi)) with E_w the path-averaged
+      local energy Eq. (27) at the start of the step; the phase dtheta comes
+      from the overlap ratio in both.
   R11 initial walkers phi_w = Phi(x_w), x_w ~ p; paths x_wp ~ p; W = 1;
       n_burn Metropolis sweeps at fixed phi before the first step.
   R14 the local energy is measured every step at the start of the step.
@@ -47,9 +55,10 @@ from . import philox as px
 
 __all__ = ["OracleConfig", "Hamiltonian", "State", "prepare", "trial_orbitals", "log_overlap",
            "green", "local_energy_force_bias", "measure", "init", "step", "reorthonormalise",
-           "propagate_walker", "mcmc_sweep", "CONSTRAINTS"]
+           "propagate_walker", "mcmc_sweep", "comb", "CONSTRAINTS", "IMPORTANCE"]
 
 CONSTRAINTS = ("combined", "separate", "half_plane")
+IMPORTANCE = ("hybrid", "local_energy")
 
 
 @dataclasses.dataclass
@@ -70,6 +79,8 @@ class OracleConfig:
     mlp_mix: float = 0.1         # probability of a random-walk move under proposal "mlp"
     mlp_params: object = None    # flat parameters of the learned proposal (oracle.mlp layout)
     mlp_hidden: int = 256
+    importance: str = "hybrid"   # R15: "hybrid" or "local_energy"
+    pop_period: int = 0          # R10: comb after every pop_period-th step (0: never)
 
 
 @dataclasses.dataclass
@@ -322,6 +333,42 @@ def _wrap(a):
     return np.angle(np.exp(1j * a))
 
 
+def comb(weight: np.ndarray, u: float):
+    """Comb population control (R10).
+
+    The W walkers' weights are laid end to end on [0, sum W); W teeth spaced
+    sum W / W apart, the first at u sum W / W with u in [0, 1), each pick the
+    walker whose interval holds them, so walker w gets c_w copies, and every
+    new walker has weight sum W / W.  Slots: a walker with c_w >= 1 keeps its
+    own slot; the c_w - 1 extra copies of each walker, in increasing w, fill the
+    slots of the walkers with c_w = 0, in increasing slot order.  Returns
+    (source walker of every slot, new weights); with no positive total weight
+    the population is left as it is.  Tooth positions are (j + u) * (sum W / W)
+    in FP64, which for u within an ulp of 1 can round onto the next interval's
+    boundary (a valid comb still, at probability ~2^-53).
+    """
+    W = weight.shape[0]
+    cum = np.empty(W)
+    acc = 0.0
+    for w in range(W):                 # running sum, left to right
+        acc += weight[w]
+        cum[w] = acc
+    total = cum[-1]
+    if not (total > 0.0 and math.isfinite(total)):
+        return np.arange(W), weight.copy()
+    width = total / W
+    teeth = (np.arange(W) + u) * width
+    # tooth j picks the first walker whose running sum exceeds it; rounding can put
+    # the last tooth at the total, which then goes to the last walker of positive weight
+    picked = np.minimum(np.searchsorted(cum, teeth, side="right"), int(np.nonzero(weight > 0.0)[0][-1]))
+    copies = np.bincount(picked, minlength=W)
+    extras = [w for w in range(W) for _ in range(copies[w] - 1)]
+    free = [j for j in range(W) if copies[j] == 0]
+    src = np.arange(W)
+    src[free] = extras
+    return src, np.full(W, width)
+
+
 def step(ham: Hamiltonian, cfg: OracleConfig, st: State, mlp_mu_logv=None):
     """One leapfrog step (Sec. III A and the propagation outline of Appendix B.2).
 
@@ -363,7 +410,12 @@ def step(ham: Hamiltonian, cfg: OracleConfig, st: State, mlp_mu_logv=None):
         # Importance function Eq. (14): p(x - xbar)/p(x) times the ratio.
         log_shift = np.sum(xi[w] * xbar[w] - 0.5 * xbar[w] * xbar[w])
         I_full[w] = np.exp(log_shift) * ratio[w]
-        I_abs[w] = abs(I_full[w])
+        if cfg.importance == "hybrid":
+            I_abs[w] = abs(I_full[w])
+        elif cfg.importance == "local_energy":   # R15: exp(-tau E_L(phi)), Sec. III A
+            I_abs[w] = math.exp(-tau * m["e_bar"][w].real)
+        else:
+            raise ValueError(cfg.importance)
 
     # Leapfrog step 2: Metropolis update of the paths at phi' (Sec. III A).
     if cfg.proposal == "mlp" and mlp_mu_logv is None:
@@ -399,8 +451,18 @@ def step(ham: Hamiltonian, cfg: OracleConfig, st: State, mlp_mu_logv=None):
             new.phi_up[w] = reorthonormalise(new.phi_up[w])
             new.phi_dn[w] = reorthonormalise(new.phi_dn[w])
     new.step = i + 1
+
+    # Population control (R10): comb at the end of every pop_period-th step.
+    comb_src = None
+    if cfg.pop_period > 0 and (i + 1) % cfg.pop_period == 0:
+        u = px.uniforms(cfg.seed, px.TAG_COMB, i, st.walker_index[:1], 0, 1)[0, 0]
+        comb_src, new.weight = comb(new.weight, u)
+        new.phi_up = new.phi_up[comb_src]
+        new.phi_dn = new.phi_dn[comb_src]
+        new.x = new.x[comb_src]
+        new.Phi = new.Phi[comb_src]
     diag = dict(mixed=mixed, n_accept=n_acc, n_proposed=int(alive.sum()) * P * cfg.n_sweeps,
                 alive=alive, e_bar=m["e_bar"], v_bar=m["v_bar"], ratio=ratio, measure=m,
                 old_sum=old_sum, new_sum=np.exp(1j * logov_new.imag).sum(axis=1), logov_new=logov_new,
-                xi=xi, I_abs=I_abs, I=I_full)
+                xi=xi, I_abs=I_abs, I=I_full, comb_src=comb_src)
     return new, diag

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libafqmc.so")
 CONSTRAINTS = {"combined": 0, "separate": 1, "half_plane": 2}
 PROPOSALS = {"prior": 0, "pcn": 1, "rw": 2, "mlp": 3}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "fp16x3": 2}
+IMPORTANCE = {"hybrid": 0, "local_energy": 1}
 STATE_MAGIC = 0x4146514D43535431
 
 
@@ -34,6 +35,7 @@ class AfqmcConfig(ctypes.Structure):
         ("kill_threshold", ctypes.c_double), ("seed", ctypes.c_uint64), ("walker_offset", ctypes.c_int64),
         ("rw_step", ctypes.c_double), ("mlp_mix", ctypes.c_double), ("mlp_lr", ctypes.c_double),
         ("mlp_train", ctypes.c_int), ("refine_tol", ctypes.c_double),
+        ("importance", ctypes.c_int), ("pop_period", ctypes.c_int),
     ]
 
 
@@ -46,7 +48,7 @@ EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc
            "afqmc_batch_destroy", "afqmc_mlp_n_params", "afqmc_mlp_params", "afqmc_mlp_eval", "afqmc_mlp_state")
 
 PHASES = ("overlap", "contract", "average", "fields", "propagate", "ratio", "propose", "trial_orbitals",
-          "mcmc_overlap", "accept", "finish")
+          "mcmc_overlap", "accept", "finish", "comb")
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -136,7 +138,8 @@ def _check(st: int):
 def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_sweeps=1, n_burn=20,
                 constraint="combined", proposal="prior", precision="fp64", taylor_order=6, history_capacity=1024,
                 pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10, walker_offset=0, rw_step=0.3, mlp_mix=0.1,
-                mlp_lr=1e-3, mlp_train=False, refine_tol=1e-4) -> AfqmcConfig:
+                mlp_lr=1e-3, mlp_train=False, refine_tol=1e-4, importance="hybrid",
+                pop_period=0) -> AfqmcConfig:
     lib = load_library()
     c = AfqmcConfig()
     lib.afqmc_config_default(ctypes.byref(c))
@@ -148,6 +151,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
     c.walker_offset = walker_offset
     c.rw_step, c.mlp_mix, c.mlp_lr, c.mlp_train = rw_step, mlp_mix, mlp_lr, int(bool(mlp_train))
     c.refine_tol = refine_tol
+    c.importance, c.pop_period = IMPORTANCE[importance], pop_period
     return c
 
 
@@ -227,10 +231,10 @@ class Context:
         return out[: 4 * k.value].reshape(k.value, 4)
 
     def stats(self):
-        out = np.empty(9)
-        _check(load_library().afqmc_stats(self._ctx, out.ctypes.data, 9))
+        out = np.empty(11)
+        _check(load_library().afqmc_stats(self._ctx, out.ctypes.data, 11))
         keys = ("steps", "accepted", "proposed", "live_walkers", "status", "min_weight", "max_weight", "sum_weight",
-                "refined_pairs")
+                "refined_pairs", "combs", "comb_replaced")
         return dict(zip(keys, out.tolist()))
 
     def autotune(self):

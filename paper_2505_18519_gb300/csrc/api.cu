@@ -194,6 +194,10 @@ static const char* check_config(const afqmc_config* c) {
     if (c->proposal == AFQMC_PROPOSAL_PCN && !(c->pcn_beta > 0.0 && c->pcn_beta <= 1.0)) return "pcn_beta in (0, 1]";
     if (!(c->kill_threshold >= 0.0)) return "kill_threshold must be >= 0";
     if (!(c->refine_tol >= 0.0)) return "refine_tol must be >= 0";
+    if (c->importance < AFQMC_IMPORTANCE_HYBRID || c->importance > AFQMC_IMPORTANCE_LOCAL_ENERGY)
+        return "unknown importance function";
+    if (c->pop_period < 0) return "pop_period must be >= 0";
+    if (c->pop_period > 0 && c->n_walkers > 65535) return "population control supports at most 65535 walkers";
     if (c->walker_offset < 0 || (c->walker_offset + c->n_walkers) * (long long)c->n_paths > (1ll << 32))
         return "walker_offset out of range of the 32-bit stream entity";
     if (c->precision == AFQMC_PRECISION_FP64 && !contract_fp64_supported(c->N, c->n_up, c->n_dn))
@@ -282,6 +286,13 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.ratio = (double2*)take(W * 16);
     w.Iabs = (double*)take(W * 8);
     w.alive = (int*)take(W * 4);
+    if (c->pop_period > 0) {
+        w.comb_cum = (double*)take(W * 8);
+        w.comb_hit = (int*)take(W * 4);
+        w.comb_slot = (int*)take(W * 4);
+        w.comb_from = (int*)take(W * 4);
+        w.comb_flag = (int*)take(2 * 4);
+    }
     w.xprop = (double*)take(pairs * K * 8);
     w.Sprop = (double*)take(pairs * NN * 8);
     w.Phiprop = (double*)take(pairs * N * nu * 8);
@@ -347,6 +358,7 @@ static StepParams params_of(const afqmc_config* c) {
     p.rw_step = c->rw_step; p.mlp_mix = c->mlp_mix;
     p.kill_threshold = c->kill_threshold; p.constraint = c->constraint; p.proposal = c->proposal;
     p.taylor_order = c->taylor_order; p.history_capacity = c->history_capacity;
+    p.importance = c->importance; p.pop_period = c->pop_period;
     return p;
 }
 
@@ -576,10 +588,14 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         }
         if (ctx->cfg.proposal == AFQMC_PROPOSAL_MLP && ctx->cfg.mlp_train)   // one Adam step on the new states
             CK(mlp_backward(s, d, w.mlp, d.W, w.x, (float)ctx->cfg.mlp_lr, true));
-        CK(handoff(s, d, p, w.logov_cur, w.old_sum, w.ratio, w.Iabs, w.alive, w.weight, w.status));  // Eq. (28)-(29)
+        CK(handoff(s, d, p, w.logov_cur, w.old_sum, w.ratio, w.Iabs, w.ebar, w.alive, w.weight,
+                   w.status));  // Eq. (28)-(29)
         CK(reorthonormalise(s, d, w.phi_new, w.phi, w.alive, w.status, d.W));
         CK(step_end(s, p, w.reduce, w.history, w.counters));
         if ((st = prof_mark(ctx, PH_FINISH)) != AFQMC_OK) return st;
+        CK(population_control(s, d, p, w.counters, w.weight, w.phi, w.x, w.Phi, w.comb_cum, w.comb_hit,
+                              w.comb_slot, w.comb_from, w.comb_flag));
+        if ((st = prof_mark(ctx, PH_COMB)) != AFQMC_OK) return st;
         if (ctx->profiling) ctx->prof_steps++;
         ctx->steps_taken++;
     }
@@ -674,9 +690,9 @@ extern "C" afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len) {
     CK(cudaMemcpyAsync(ws4, ctx->ws.reduce + 4, sizeof ws4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(&status, ctx->ws.status, sizeof status, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    double v[9] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3],
-                   (double)c[5]};
-    for (int i = 0; i < len && i < 9; ++i) out[i] = v[i];
+    double v[11] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3],
+                    (double)c[5], (double)c[6], (double)c[7]};
+    for (int i = 0; i < len && i < 11; ++i) out[i] = v[i];
     return AFQMC_OK;
 }
 

@@ -78,7 +78,7 @@ __host__ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t 
 // Random-stream tags (counter word 3 = tag << 24 | sweep).
 enum : uint32_t {
     TAG_INIT_WALKER = 1, TAG_INIT_PATH = 2, TAG_FIELD = 3, TAG_PROPOSE = 4,
-    TAG_ACCEPT = 5, TAG_BURN_PROPOSE = 6, TAG_BURN_ACCEPT = 7, TAG_MLP_INIT = 9
+    TAG_ACCEPT = 5, TAG_BURN_PROPOSE = 6, TAG_BURN_ACCEPT = 7, TAG_MLP_INIT = 9, TAG_COMB = 10
 };
 
 __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
@@ -190,6 +190,12 @@ struct Workspace {
     double2* ratio;   // W
     double* Iabs;     // W
     int* alive;       // W
+    // population control (null when off)
+    double* comb_cum; // W   running sums of the weights
+    int* comb_hit;    // W   whether a tooth picked the walker
+    int* comb_slot;   // W   walker of every tooth, then the replaced slots
+    int* comb_from;   // W   walker each replaced slot copies
+    int* comb_flag;   // 2   whether this step combed, replaced walkers
     // Metropolis
     double* xprop;    // W*P*K
     double* Sprop;    // W*P*N*N   sum_k x'_k U_k
@@ -227,7 +233,7 @@ cudaError_t raise_smem_limit(const void* kernel, size_t bytes);
 // Phases of a step timed by afqmc_profile (CUDA events on the context's stream).
 enum Phase : int {
     PH_OVERLAP = 0, PH_CONTRACT, PH_AVERAGE, PH_FIELDS, PH_PROPAGATE, PH_RATIO, PH_PROPOSE, PH_TRIAL,
-    PH_MCMC_OVERLAP, PH_ACCEPT, PH_FINISH, PH_COUNT
+    PH_MCMC_OVERLAP, PH_ACCEPT, PH_FINISH, PH_COMB, PH_COUNT
 };
 }  // namespace afq
 

@@ -98,6 +98,7 @@ struct StepParams {
     long long woff;   // global index of walker 0
     double dtau, pcn_beta, e_shift, kill_threshold, rw_step, mlp_mix;
     int constraint, proposal, taylor_order, history_capacity;
+    int importance, pop_period;
 };
 cudaError_t fill_normals(cudaStream_t s, double* out, long long rows, int cols, long long entity0, uint64_t seed,
                          uint32_t tag, const unsigned long long* step_ctr, uint32_t sweep);
@@ -130,8 +131,14 @@ cudaError_t accept(cudaStream_t s, const Dims& d, const StepParams& p, const uns
                    unsigned long long* counters);
 cudaError_t combine_logdet(cudaStream_t s, long long pairs, const double2* logdet, double2* logov);
 cudaError_t handoff(cudaStream_t s, const Dims& d, const StepParams& p, const double2* logov_cur,
-                    const double2* old_sum, const double2* ratio, const double* Iabs, const int* alive,
-                    double* weight, int* status);
+                    const double2* old_sum, const double2* ratio, const double* Iabs, const double2* ebar,
+                    const int* alive, double* weight, int* status);
+// Comb population control after every p.pop_period-th step (decided on the
+// device from counters[0]), gathering the walker state in place; cum, hit,
+// slot and from are W entries of scratch each, flag two ints.
+cudaError_t population_control(cudaStream_t s, const Dims& d, const StepParams& p, unsigned long long* counters,
+                               double* weight, double2* phi, double* x, double* Phi, double* cum, int* hit,
+                               int* slot, int* from, int* flag);
 cudaError_t step_end(cudaStream_t s, const StepParams& p, const double* measured3, double* history,
                      unsigned long long* counters);
 cudaError_t set_value(cudaStream_t s, double* out, long long n, double v);

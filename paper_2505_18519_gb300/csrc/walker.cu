@@ -4,6 +4,8 @@
 // importance function (Eq. (14)), Metropolis proposals and acceptance of the
 // paths (Eq. (23)), and the hand-off constraint (Eq. (17), (28)-(29)).
 #include "df.cuh"
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace afq {
@@ -586,10 +588,11 @@ cudaError_t accept(cudaStream_t s, const Dims& d, const StepParams& p, const uns
 // separate:   W *= |I| max(0, cos dtheta) max(0, cos dtheta_T)
 // half-plane: W *= |I| max(0, cos dtheta) [|wrap(dtheta_T)| <= pi/2]
 // and W *= exp(tau E_T).  Non-finite weights become 0.  One warp per walker.
-__global__ void handoff_kernel(int W, int P, int constraint, double dtau, double e_shift,
+__global__ void handoff_kernel(int W, int P, int constraint, int importance, double dtau, double e_shift,
                                const double2* __restrict__ logov_cur, const double2* __restrict__ old_sum,
                                const double2* __restrict__ ratio, const double* __restrict__ Iabs,
-                               const int* __restrict__ alive, double* weight, int* status) {
+                               const double2* __restrict__ ebar, const int* __restrict__ alive, double* weight,
+                               int* status) {
     long long w = blockIdx.x;
     if (!alive[w]) return;
     int lane = threadIdx.x;
@@ -612,7 +615,10 @@ __global__ void handoff_kernel(int W, int P, int constraint, double dtau, double
         double wr = atan2(sin(dthT), cos(dthT));
         f = fmax(0.0, cos(dth)) * (fabs(wr) <= 0.5 * M_PI ? 1.0 : 0.0);
     }
-    double wn = weight[w] * Iabs[w] * f * exp(dtau * e_shift);
+    // |I|: hybrid form (Eq. (14) with the ratio of Eq. (25)), or the local-energy
+    // form exp(-tau Re E_w) with E_w of Eq. (27) at the start of the step (Sec. III A)
+    const double ia = importance == AFQMC_IMPORTANCE_LOCAL_ENERGY ? exp(-dtau * ebar[w].x) : Iabs[w];
+    double wn = weight[w] * ia * f * exp(dtau * e_shift);
     if (!isfinite(wn)) {
         wn = 0.0;
         atomicOr(status, STATUS_NONFINITE);
@@ -621,10 +627,174 @@ __global__ void handoff_kernel(int W, int P, int constraint, double dtau, double
 }
 
 cudaError_t handoff(cudaStream_t s, const Dims& d, const StepParams& p, const double2* logov_cur,
-                    const double2* old_sum, const double2* ratio, const double* Iabs, const int* alive,
-                    double* weight, int* status) {
-    handoff_kernel<<<d.W, 32, 0, s>>>(d.W, d.P, p.constraint, p.dtau, p.e_shift, logov_cur, old_sum, ratio, Iabs, alive,
-                                      weight, status); count_launches(1);
+                    const double2* old_sum, const double2* ratio, const double* Iabs, const double2* ebar,
+                    const int* alive, double* weight, int* status) {
+    handoff_kernel<<<d.W, 32, 0, s>>>(d.W, d.P, p.constraint, p.importance, p.dtau, p.e_shift, logov_cur, old_sum,
+                                      ratio, Iabs, ebar, alive, weight, status); count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- population control
+// Comb (branching random walk, Sec. II B and II D; the scheme is this code's
+// reading): after every `period`-th step the W weights are laid end to end on
+// [0, sum W), W teeth spaced sum W / W apart starting at u sum W / W each pick
+// the walker whose interval holds them (walker w gets c_w copies), and every
+// new walker gets weight sum W / W.  A walker with c_w >= 1 keeps its slot; the
+// extra copies, in increasing walker order, fill the slots of the walkers with
+// c_w = 0, in increasing order, so the state is gathered in place and only the
+// replaced slots move.  u is one Philox uniform (tag COMB, entity = global index
+// of walker 0, the step's index).  Whether a step combs is decided here from the
+// device step counter, so the same launches serve every step of a captured
+// graph; the gather does nothing on the other steps.
+constexpr int COMB_T = 1024;
+constexpr int COMB_STAGE = 4096;    // weights staged in shared memory per pass of the running sum
+constexpr int COMB_CHUNK = 2048;    // doubles per work item of the gather
+
+// Exclusive prefix sum of one int per thread over the block; *total gets the sum.
+__device__ int comb_block_scan(int v, int* sh, int* total) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < COMB_T; off <<= 1) {
+        const int t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    const int incl = sh[threadIdx.x];
+    *total = sh[COMB_T - 1];
+    __syncthreads();
+    return incl - v;
+}
+
+// One block.  Writes flag[0] (whether this step combs), flag[1] (replaced
+// walkers n), slot[0..n) the replaced slots in increasing order and from[0..n)
+// the walker each one copies.
+__global__ void __launch_bounds__(COMB_T) comb_select_kernel(int W, int period, uint64_t seed, uint32_t entity,
+                                                             unsigned long long* counters, double* weight,
+                                                             double* cum, int* hit, int* slot, int* from,
+                                                             int* flag) {
+    __shared__ double s_w[COMB_STAGE];
+    __shared__ double s_width, s_u, s_acc;
+    __shared__ int s_last, s_do;
+    __shared__ int sh[COMB_T];
+    if (threadIdx.x == 0) {
+        const unsigned long long done = counters[0];   // steps taken, this one included
+        s_do = period > 0 && done > 0 && done % (unsigned long long)period == 0;
+        s_u = s_do ? uniform_at0(seed, TAG_COMB, (uint32_t)(done - 1), entity, 0) : 0.0;
+        s_acc = 0.0;
+        s_last = -1;
+    }
+    __syncthreads();
+    if (!s_do) {
+        if (threadIdx.x == 0) flag[0] = 0;
+        return;
+    }
+    // running sum, left to right, by one thread over weights staged in shared memory
+    for (int base = 0; base < W; base += COMB_STAGE) {
+        const int n = min(COMB_STAGE, W - base);
+        for (int i = threadIdx.x; i < n; i += COMB_T) s_w[i] = weight[base + i];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double acc = s_acc;
+            int last = s_last;
+            for (int i = 0; i < n; ++i) {
+                const double x = s_w[i];
+                if (x > 0.0) last = base + i;
+                acc += x;
+                cum[base + i] = acc;
+            }
+            s_acc = acc;
+            s_last = last;
+        }
+        __syncthreads();
+    }
+    const double total = s_acc;
+    if (!(total > 0.0 && isfinite(total)) || s_last < 0) {   // nothing to resample from (uniform)
+        if (threadIdx.x == 0) flag[0] = 0;
+        return;
+    }
+    const double width = total / W, u = s_u;
+    // tooth j -> walker (nondecreasing in j): `cum` is reused for the teeth's walkers
+    // only after every search is done, so they go to `slot` first
+    for (int j = threadIdx.x; j < W; j += COMB_T) {
+        const double pos = ((double)j + u) * width;
+        int lo = 0, hi = W;   // first w with cum[w] > pos, W if none
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cum[mid] > pos) hi = mid; else lo = mid + 1;
+        }
+        slot[j] = min(lo, s_last);
+        hit[j] = 0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < W; j += COMB_T) hit[slot[j]] = 1;   // same value from every writer
+    __syncthreads();
+    // each thread takes a contiguous range of indices; free slots (walkers not hit)
+    // and extra teeth (a tooth on the same walker as the one before) are ranked in
+    // increasing index order by block scans
+    const int per = (W + COMB_T - 1) / COMB_T;
+    const int j0 = min(W, (int)threadIdx.x * per), j1 = min(W, j0 + per);
+    int n_free = 0, n_extra = 0;
+    for (int j = j0; j < j1; ++j) {
+        n_free += hit[j] == 0;
+        n_extra += j > 0 && slot[j] == slot[j - 1];
+    }
+    int total_free, total_extra;
+    int r_free = comb_block_scan(n_free, sh, &total_free);
+    int r_extra = comb_block_scan(n_extra, sh, &total_extra);
+    for (int j = j0; j < j1; ++j)
+        if (j > 0 && slot[j] == slot[j - 1]) from[r_extra++] = slot[j];
+    __syncthreads();   // every tooth was read; `slot` now takes the replaced slots
+    for (int j = j0; j < j1; ++j)
+        if (!hit[j]) slot[r_free++] = j;
+    for (int j = threadIdx.x; j < W; j += COMB_T) weight[j] = width;   // every read of weight came before
+    if (threadIdx.x == 0) {
+        flag[0] = 1;
+        flag[1] = total_free;
+        counters[6] += 1;
+        counters[7] += (unsigned long long)total_free;
+    }
+}
+
+// The three walker-state arrays, rows of len[b] doubles per walker.
+struct CombRows {
+    double* a[3];
+    long long len[3];
+};
+
+// Replaced slot slot[r] of every state array gets the row of walker from[r];
+// those sources keep their own slots, so the copy is in place.  Work items are
+// chunks of COMB_CHUNK doubles of one row of one array.
+__global__ void __launch_bounds__(256) comb_gather_kernel(CombRows r, const int* __restrict__ slot,
+                                                          const int* __restrict__ from, const int* __restrict__ flag) {
+    if (!flag[0]) return;
+    const long long n = flag[1];
+    const long long c0 = (r.len[0] + COMB_CHUNK - 1) / COMB_CHUNK, c1 = (r.len[1] + COMB_CHUNK - 1) / COMB_CHUNK,
+                    c2 = (r.len[2] + COMB_CHUNK - 1) / COMB_CHUNK;
+    const long long per_slot = c0 + c1 + c2;
+    for (long long it = blockIdx.x; it < n * per_slot; it += gridDim.x) {
+        const long long q = it / per_slot;
+        long long k = it - q * per_slot;
+        int b = 0;
+        if (k >= c0) { k -= c0; b = 1; if (k >= c1) { k -= c1; b = 2; } }
+        const long long len = b == 0 ? r.len[0] : b == 1 ? r.len[1] : r.len[2];
+        double* base = b == 0 ? r.a[0] : b == 1 ? r.a[1] : r.a[2];
+        const double* in = base + (long long)from[q] * len;
+        double* o = base + (long long)slot[q] * len;
+        const long long e1 = min(len, (k + 1) * COMB_CHUNK);
+        for (long long e = k * COMB_CHUNK + threadIdx.x; e < e1; e += 256) o[e] = in[e];
+    }
+}
+
+cudaError_t population_control(cudaStream_t s, const Dims& d, const StepParams& p, unsigned long long* counters,
+                               double* weight, double2* phi, double* x, double* Phi, double* cum, int* hit,
+                               int* slot, int* from, int* flag) {
+    if (p.pop_period <= 0) return cudaSuccess;
+    comb_select_kernel<<<1, COMB_T, 0, s>>>(d.W, p.pop_period, p.seed, (uint32_t)p.woff, counters, weight, cum, hit,
+                                            slot, from, flag);
+    CombRows rows{{(double*)phi, x, Phi}, {(long long)d.N * d.nt * 2, (long long)d.P * d.K, (long long)d.P * d.N * d.nu}};
+    comb_gather_kernel<<<2 * 152, 256, 0, s>>>(rows, slot, from, flag);
+    count_launches(2);
     return cudaGetLastError();
 }
 

@@ -65,6 +65,30 @@ def test_batch_graph_equals_individual_steps():
         c.close()
 
 
+def test_batch_graph_combs_like_individual_steps():
+    """Whether a step combs is decided on the device, so the one captured graph
+    serves the steps that comb and those that do not."""
+    def mk(i, spec, W, P, prec):
+        s = ai.make_system(spec)
+        cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, 0.01, 70 + i, n_burn=2,
+                              precision=prec, pop_period=2, importance="local_energy")
+        return lib.Context(cfg, s.h, s.L, s.Phi0, s.U, stream=torch.cuda.Stream())
+    batched = [mk(i, *sy) for i, sy in enumerate(SYSTEMS[:2])]
+    single = [mk(i, *sy) for i, sy in enumerate(SYSTEMS[:2])]
+    b = lib.Batch(batched)
+    b.step(4)
+    b.sync()
+    for c in single:
+        c.step(4)
+    torch.cuda.synchronize()
+    for cb, cs in zip(batched, single):
+        assert cb.save_state() == cs.save_state()
+        assert cb.stats()["combs"] == cs.stats()["combs"] == 2
+    b.close()
+    for c in batched + single:
+        c.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp16x3"])
 def test_autotune_changes_no_result(prec):
     spec = ai.SystemSpec(50, 10, 10, 250, 50, True, 1001)

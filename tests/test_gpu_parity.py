@@ -14,6 +14,7 @@ would be reported as such).
 """
 
 import ctypes
+import dataclasses
 import os
 import subprocess
 import tempfile
@@ -46,7 +47,8 @@ def built():
 def _setup(spec, W, P, dtau, seed, **kw):
     s = ai.make_system(spec)
     ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, dtau)
-    okw = {k: v for k, v in kw.items() if k in ("n_sweeps", "n_burn", "constraint", "proposal", "pcn_beta", "e_shift")}
+    okw = {k: v for k, v in kw.items() if k in ("n_sweeps", "n_burn", "constraint", "proposal", "pcn_beta", "e_shift",
+                                                 "importance", "pop_period")}
     ocfg = oa.OracleConfig(dtau=dtau, n_walkers=W, n_paths=P, seed=seed, **okw)
     cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, dtau, seed, **kw)
     ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U)
@@ -202,6 +204,54 @@ def test_variants_match_oracle(constraint, proposal):
         ctx.step(1)
         ost, _ = oa.step(ham, ocfg, ost)
         _compare_state(ctx.state_arrays(), ost)
+    ctx.close()
+
+
+def test_local_energy_importance_matches_oracle():
+    """Weights with |I| = exp(-tau Re E_w) (the local-energy form of Sec. III A)."""
+    spec, W, P, dtau = SYSTEMS["c0"]
+    kw = dict(n_burn=3, importance="local_energy", e_shift=11.0)
+    s, ham, ocfg, ctx = _setup(spec, W, P, 0.05, seed=37, **kw)
+    ost = oa.init(ham, ocfg)
+    hyb = ost.copy()
+    ctx.load_state_arrays(_as_dict(ost))
+    for _ in range(3):
+        ctx.step(1)
+        ost, _ = oa.step(ham, ocfg, ost)
+        hyb, _ = oa.step(ham, dataclasses.replace(ocfg, importance="hybrid"), hyb)
+        _compare_state(ctx.state_arrays(), ost)
+    live = (ost.weight > 0) & (hyb.weight > 0)
+    assert live.sum() >= W // 2
+    assert np.max(np.abs(ost.weight[live] / hyb.weight[live] - 1.0)) > 1e-4   # the two forms differ
+    ctx.close()
+
+
+@pytest.mark.parametrize("importance,period", [("hybrid", 1), ("local_energy", 2)])
+def test_comb_matches_oracle(importance, period):
+    """Population control: the comb after every period-th step picks the same
+    walkers (bit-equal selection, then the gathered state within 1e-9) and
+    gives every walker the mean weight."""
+    spec, W, P, dtau = SYSTEMS["c0"]
+    kw = dict(n_burn=3, importance=importance, pop_period=period)
+    s, ham, ocfg, ctx = _setup(spec, W, P, 0.05, seed=41 + period, **kw)
+    ost = oa.init(ham, ocfg)
+    ost.weight = np.random.default_rng(period).exponential(size=W)
+    ost.weight[[2, 7, 8]] = 0.0
+    ctx.load_state_arrays(_as_dict(ost))
+    n_steps, combs, replaced = 4, 0, 0
+    for k in range(n_steps):
+        ctx.step(1)
+        ost, d = oa.step(ham, ocfg, ost)
+        if d["comb_src"] is not None:
+            combs += 1
+            replaced += int(np.sum(d["comb_src"] != np.arange(W)))
+            if combs == 1:
+                assert len(set(d["comb_src"].tolist())) < W      # the first comb duplicates walkers
+            assert np.all(ost.weight == ost.weight[0]) and ost.weight[0] > 0
+        _compare_state(ctx.state_arrays(), ost)
+    assert combs == n_steps // period
+    st = ctx.stats()
+    assert st["combs"] == combs and st["comb_replaced"] == replaced >= 3
     ctx.close()
 
 

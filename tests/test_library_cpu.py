@@ -34,7 +34,8 @@ def test_config_validation(L):
     good = lib.make_config(8, 4, 4, 32, 8, 64, 16, 0.01, 1)
     assert lib.workspace_bytes(good) > 0
     for field, bad in (("N", 0), ("n_up", 0), ("n_dn", 5), ("n_paths", 0), ("dtau", 0.0), ("taylor_order", 0),
-                       ("constraint", 7), ("precision", 9), ("n_chol", 0)):
+                       ("constraint", 7), ("precision", 9), ("n_chol", 0), ("importance", 2), ("importance", -1),
+                       ("pop_period", -1)):
         c = lib.make_config(8, 4, 4, 32, 8, 64, 16, 0.01, 1)
         setattr(c, field, bad)
         assert lib.workspace_bytes(c) == 0, field
@@ -49,6 +50,23 @@ def test_init_rejects_bad_workspace_without_touching_a_gpu(L):
     assert st == 3 and out.value is None                     # AFQMC_ERR_WORKSPACE
     st = L.afqmc_init(None, None, None, None, None, None, 0, None, ctypes.byref(out))
     assert st == 1 and b"NULL" in L.afqmc_last_error()      # AFQMC_ERR_ARG
+
+
+def test_population_control_fields_reach_the_library(L):
+    """The two fields appended to the config are read at their offsets: the comb's
+    buffers appear in the workspace only with pop_period > 0, and its walker limit
+    and the importance functions are checked."""
+    base = lib.make_config(8, 4, 4, 32, 8, 64, 16, 0.01, 1)
+    le = lib.make_config(8, 4, 4, 32, 8, 64, 16, 0.01, 1, importance="local_energy")
+    comb = lib.make_config(8, 4, 4, 32, 8, 64, 16, 0.01, 1, pop_period=5)
+    assert lib.workspace_bytes(le) == lib.workspace_bytes(base) > 0
+    assert lib.workspace_bytes(comb) > lib.workspace_bytes(base)
+    assert lib.workspace_bytes(lib.make_config(8, 4, 4, 32, 8, 65535, 1, 0.01, 1, pop_period=1)) > 0
+    assert lib.workspace_bytes(lib.make_config(8, 4, 4, 32, 8, 65536, 1, 0.01, 1, pop_period=1)) == 0
+    assert lib.workspace_bytes(lib.make_config(8, 4, 4, 32, 8, 65536, 1, 0.01, 1)) > 0
+    d = lib.AfqmcConfig()
+    L.afqmc_config_default(ctypes.byref(d))
+    assert d.importance == 0 and d.pop_period == 0 and d.refine_tol == 1e-4
 
 
 def test_workspace_grows_with_walkers(L):

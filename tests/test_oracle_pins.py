@@ -7,6 +7,7 @@ operand anywhere in the oracle's local energy, force bias, overlaps,
 propagator, Metropolis step or weight update fails at least one of them.
 """
 
+import dataclasses
 import math
 
 import numpy as np
@@ -409,3 +410,127 @@ def test_importance_function_averages_to_exact_projection(c0):
     shift = abs(exact - 1.0)
     assert shift > 0.03                                  # the projection is resolved
     assert abs(mean - exact) < 5 * err + 5e-4
+
+
+# ---------------------------------------------------------------- importance function and population control
+def test_local_energy_weights_of_an_exact_eigenstate():
+    """L = 0 and U commuting with h make every trial sample an eigenstate of
+    H = h: the hybrid |I| (the overlap ratio) and the local-energy |I| =
+    exp(-tau E_L) both equal exp(-tau E0), the constraint factor is 1, and after
+    k steps every weight is exp(-k tau (E0 - E_T)) under either form."""
+    s = _small_system(8, 3, 3, K=4, seed=21)
+    rng = np.random.default_rng(4)
+    U, _ = _commuting_U(s.h, 4, 3, rng)
+    tau = 0.02
+    ham = _ham(s, 3, 3, dtau=tau, U=U, L=np.zeros((2, 8, 8)))
+    e0 = 2.0 * np.sum(np.linalg.eigvalsh(s.h)[:3])
+    e_t = e0 + 0.7
+    for imp in oa.IMPORTANCE:
+        cfg = oa.OracleConfig(dtau=tau, n_walkers=4, n_paths=3, seed=11, n_burn=2, importance=imp, e_shift=e_t)
+        st = oa.init(ham, cfg)
+        for k in range(1, 4):
+            st, d = oa.step(ham, cfg, st)
+            assert np.allclose(d["I_abs"], math.exp(-tau * e0), rtol=1e-12, atol=0), imp
+            assert np.allclose(st.weight, math.exp(-k * tau * (e0 - e_t)), rtol=1e-11, atol=0), imp
+
+
+def test_local_energy_importance_of_one_electron():
+    """One electron with L != 0: the two-body term has nothing to act on, so
+    E_L = eps_0 and the local-energy |I| is exp(-tau eps_0) for every live walker
+    while the fields act (the hybrid |I| differs from walker to walker); the
+    constraint factor W'/(W |I|) stays in [0, 1]."""
+    s = _small_system(7, 1, 1, G=6, K=3, seed=5)
+    rng = np.random.default_rng(1)
+    U, _ = _commuting_U(s.h, 3, 1, rng)
+    tau = 0.02
+    ham = _ham(s, 1, 0, dtau=tau, U=U)
+    eps0 = np.linalg.eigvalsh(s.h)[0]
+    cfg = oa.OracleConfig(dtau=tau, n_walkers=5, n_paths=2, seed=3, n_burn=1, importance="local_energy")
+    st = oa.init(ham, cfg)
+    for _ in range(3):
+        w0 = st.weight.copy()
+        st, d = oa.step(ham, cfg, st)
+        live = d["alive"]
+        assert live.sum() >= 3
+        assert np.allclose(d["I_abs"][live], math.exp(-tau * eps0), rtol=1e-11, atol=0)
+        assert np.ptp(np.abs(d["I"][live])) > 1e-6
+        f = st.weight[live] / (w0[live] * d["I_abs"][live])
+        assert np.all((f >= 0.0) & (f <= 1.0 + 1e-12))
+
+
+def test_comb_keeps_the_total_weight_and_copies_in_proportion():
+    """A comb keeps the total weight, gives every new walker the mean weight,
+    never copies a dead walker, gives walker w floor or ceil of W w_w / sum w
+    copies, and leaves every walker that has a copy in its own slot."""
+    rng = np.random.default_rng(12)
+    W = 37
+    weight = rng.exponential(size=W) * (rng.random(W) > 0.25)
+    total = math.fsum(weight)
+    expect = W * weight / total
+    for u in (0.0, 0.31, 0.5, 1.0 - 2.0 ** -53):
+        src, wn = oa.comb(weight, u)
+        assert src.shape == (W,)
+        assert np.all(weight[src] > 0.0)
+        assert np.allclose(wn, total / W, rtol=1e-14, atol=0)
+        assert abs(math.fsum(wn) - total) <= 1e-13 * total
+        n = np.bincount(src, minlength=W)
+        assert np.all(n >= np.floor(expect - 1e-9)) and np.all(n <= np.ceil(expect + 1e-9))
+        moved = src != np.arange(W)
+        assert np.all(src[n > 0] == np.arange(W)[n > 0]) and np.all(n[moved] == 0)
+        assert np.all(~moved[src[moved]])      # every source is a walker that stays in place
+
+
+def test_comb_of_equal_weights_is_the_identity():
+    """Equal weights: tooth j falls in walker j's interval.  (With u within an
+    ulp of 1, j + u rounds to j + 1 and the tooth lands on the next boundary;
+    1 - 2^-40 stays clear of that.)"""
+    weight = np.full(29, 2.5)
+    for u in (0.0, 0.2, 0.75, 1.0 - 2.0 ** -40):
+        src, wn = oa.comb(weight, u)
+        np.testing.assert_array_equal(src, np.arange(29))
+        assert np.all(wn == 2.5)
+
+
+def test_comb_is_unbiased_over_its_uniform():
+    """Averaged over u in [0, 1) (midpoint rule), walker w gets W w_w / sum w
+    copies and the weighted sum of any per-walker quantity is unchanged: each
+    walker's copy count jumps at most twice in u, so the rule errs by at most
+    2 / M per walker."""
+    rng = np.random.default_rng(3)
+    W, M = 23, 20000
+    weight = rng.gamma(0.5, size=W)
+    weight[[4, 17]] = 0.0
+    energy = rng.normal(size=W)
+    copies = np.zeros(W)
+    est = 0.0
+    for u in (np.arange(M) + 0.5) / M:
+        src, wn = oa.comb(weight, u)
+        copies += np.bincount(src, minlength=W)
+        est += np.sum(wn * energy[src])
+    copies /= M
+    est /= M
+    assert np.allclose(copies, W * weight / weight.sum(), rtol=0, atol=2.5 / M)
+    assert abs(est - np.sum(weight * energy)) <= 2.5 / M * np.sum(np.abs(energy)) * weight.sum() / W
+
+
+def test_comb_step_resamples_the_walkers_of_the_plain_step():
+    """With pop_period = 2 the first step leaves the population alone and the
+    second combs, after the weight update and reorthonormalisation, with the
+    uniform of its own Philox stream; every state array is gathered alike."""
+    s, run = ai.make_config("small_n8")
+    ham = _ham(s, 4, 4, run.dtau)
+    base = oa.OracleConfig(dtau=run.dtau, n_walkers=8, n_paths=4, seed=9, n_burn=2)
+    combing = dataclasses.replace(base, pop_period=2)
+    st = oa.init(ham, base)
+    st.weight = np.array([0.0, 3.0, 0.2, 1.0, 0.0, 0.5, 2.0, 0.3])
+    st1, d1 = oa.step(ham, combing, st)
+    assert d1["comb_src"] is None
+    plain, _ = oa.step(ham, base, st1)
+    combed, d2 = oa.step(ham, combing, st1)
+    u = px.uniforms(base.seed, px.TAG_COMB, st1.step, [0], 0, 1)[0, 0]
+    ref_src, ref_w = oa.comb(plain.weight, u)
+    np.testing.assert_array_equal(d2["comb_src"], ref_src)
+    assert np.array_equal(combed.weight, ref_w)
+    for name in ("phi_up", "phi_dn", "x", "Phi"):
+        np.testing.assert_array_equal(getattr(combed, name), getattr(plain, name)[ref_src])
+    assert len(set(ref_src.tolist())) < 8 and plain.weight[0] == 0.0 and combed.weight[0] > 0.0
