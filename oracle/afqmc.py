@@ -13,7 +13,8 @@ reordering.  Notation: N orbitals, n_up/n_dn electrons, Gamma Cholesky vectors
 L_g, K hidden variables, W walkers, P paths (trial samples) per walker, tau the
 time step.  A "pair" is one (walker, path).
 
-Readings of points where the paper is silent or ambiguous (R1-R14):
+Readings of points where the paper is silent or ambiguous (those of R1-R17 that
+concern the oracle):
   R1  H = sum_ij h_ij c+_i c_j + 1/2 sum_ijkl V_ijkl c+_i c+_k c_l c_j with
       V_ijkl = sum_g L_g,ij L_g,kl; so H = T + 1/2 sum_g L_g^2 (Eq. (3)) with
       T = h - 1/2 sum_g L_g L_g.
@@ -34,7 +35,7 @@ Readings of points where the paper is silent or ambiguous (R1-R14):
       leaves the scheme open): optional comb every pop_period steps, at the
       end of the step, drawn with one Philox uniform; otherwise weights are
       carried.  Optional constant E_T.
-  R15 importance function of the weight update (Sec. III A): "hybrid", |I| of
+  R17 importance function of the weight update (Sec. III A): "hybrid", |I| of
       Eq. (14) with the sampled-trial ratio Eq. (25) (default), or
       "local_energy", |I| = exp(-tau Re E_w(phi)) with E_w the path-averaged
       local energy Eq. (27) at the start of the step; the phase dtheta comes
@@ -79,7 +80,7 @@ class OracleConfig:
     mlp_mix: float = 0.1         # probability of a random-walk move under proposal "mlp"
     mlp_params: object = None    # flat parameters of the learned proposal (oracle.mlp layout)
     mlp_hidden: int = 256
-    importance: str = "hybrid"   # R15: "hybrid" or "local_energy"
+    importance: str = "hybrid"   # R17: "hybrid" or "local_energy"
     pop_period: int = 0          # R10: comb after every pop_period-th step (0: never)
 
 
@@ -412,7 +413,7 @@ def step(ham: Hamiltonian, cfg: OracleConfig, st: State, mlp_mu_logv=None):
         I_full[w] = np.exp(log_shift) * ratio[w]
         if cfg.importance == "hybrid":
             I_abs[w] = abs(I_full[w])
-        elif cfg.importance == "local_energy":   # R15: exp(-tau E_L(phi)), Sec. III A
+        elif cfg.importance == "local_energy":   # R17: exp(-tau E_L(phi)), Sec. III A
             I_abs[w] = math.exp(-tau * m["e_bar"][w].real)
         else:
             raise ValueError(cfg.importance)
