@@ -67,10 +67,28 @@ def contract_flops_walker_side(spec, P):
     return (G + 1) * (4 * N * s2 + 8 * s3) + G * 8 * s2 + (G + 1) * 4 * N * N * (nu + nd) / P
 
 
-def step_working_set_bytes(spec, run):
+def contract_flops_cached(spec):
+    """Algorithmic FLOPs per pair of the FP64 form with the half-rotated matrices
+    R_g = Phi^T X_g cached per pair: M_s = R Theta_s (4 N n_s^2 per matrix) and the
+    exchange traces (8 n_s^2 per g); the refresh of a pair whose path moved costs
+    contract_flops_refresh more."""
+    N, nu, nd, G = spec.N, spec.n_up, spec.n_dn, spec.n_chol
+    s2 = nu * nu + nd * nd
+    return (G + 1) * 4 * N * s2 + G * 8 * s2
+
+
+def contract_flops_refresh(spec):
+    """FLOPs of forming one pair's cached matrices X_g Phi_p (2 n_up N^2 each)."""
+    return (spec.n_chol + 1) * 2 * spec.n_up * spec.N * spec.N
+
+
+def step_working_set_bytes(spec, run, rcache=False):
+    """Bytes a step touches per GPU: per-pair state and buffers, plus the cached
+    half-rotated matrices (read in full by every contraction) when they are on."""
     N, nt, nu, G, K = spec.N, spec.n_up + spec.n_dn, spec.n_up, spec.n_chol, spec.K
     pairs = run.n_walkers * run.n_paths
-    return pairs * (N * nt * 16 + N * nu * 8 * 3 + N * N * 8 + G * 16 + K * 16)
+    cached = pairs * (G + 1) * N * nu * 8 if rcache else 0
+    return pairs * (N * nt * 16 + N * nu * 8 * 3 + N * N * 8 + G * 16 + K * 16) + cached
 
 
 # ------------------------------------------------------------------ clocks
@@ -633,7 +651,7 @@ def our_arm(args):
             dist.destroy_process_group()
         return
     cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
-                          walker_offset=rank * W, e_shift=28.5)
+                          walker_offset=rank * W, e_shift=28.5, rcache=not args.no_rcache)
     with torch.cuda.device(dev):
         ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
         stream = ctx.stream
@@ -650,12 +668,15 @@ def our_arm(args):
             if world > 1:
                 dist.barrier()
             torch.cuda.synchronize(dev)
+            formed0 = ctx.stats()["rcache_formed"]
+            torch.cuda.synchronize(dev)
             l0 = lib.launch_count()
             e0.record(stream)
             ctx.step(args.steps)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             l1 = lib.launch_count()
+            refreshed = (ctx.stats()["rcache_formed"] - formed0) / args.steps
             if world > 1:
                 dist.barrier()
         prof = ctx.profile_read()
@@ -700,7 +721,12 @@ def our_arm(args):
     contract_ms = prof["ms"]["contract"] / max(1, prof["steps"])
     kernel = lib.contract_kernel(cfg)
     flops_pair_order = contract_flops_per_pair(spec) * W * P
-    flops = contract_flops_walker_side(spec, P) * W * P if kernel == "contract_fp64z_kernel" else flops_pair_order
+    if kernel == "contract_fp64r_kernel":
+        flops = contract_flops_cached(spec) * W * P + contract_flops_refresh(spec) * refreshed
+    elif kernel == "contract_fp64z_kernel":
+        flops = contract_flops_walker_side(spec, P) * W * P
+    else:
+        flops = flops_pair_order
     achieved = flops / (contract_ms / 1e3) / 1e12
     traffic = recorded_traffic(os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "contract_fp64.cu"),
                                *FP64_TRAFFIC[kernel]) if kernel in FP64_TRAFFIC and (W, P) == (512, 32) else None
@@ -719,17 +745,21 @@ def our_arm(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_desc(spec, run), "walkers_total": W * world, "paths": P,
                    "system_seed": spec.seed, "philox_seed": seed,
-                   "l2": f"working set {step_working_set_bytes(spec, run) / 1e9:.2f} GB per step > 129 MB L2; no flush"},
+                   "l2": f"working set {step_working_set_bytes(spec, run, not args.no_rcache) / 1e9:.2f} GB per step "
+                         "> 129 MB L2; no flush"},
         "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                      "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (no FP64 figure measured by the driver)",
                      "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": contract_ms,
                      "flops_per_launch_pair_order": flops_pair_order,
                      "launches_per_contraction": prof["launches"]["contract"] / max(1, prof["steps"]),
-                     "note": "one contraction per step (for the walker-side form: phi_columns_kernel, the FP64 GEMM "
-                             "forming Y_g = X_g phi_w of every walker, and contract_fp64z_kernel; flops, time and "
-                             "traffic are theirs together); flops_per_launch counts the walker-side association "
-                             "order; the per-pair order (R = Phi^T L_g first) needs flops_per_launch_pair_order"},
+                     "refreshed_pairs_per_step": refreshed if kernel == "contract_fp64r_kernel" else None,
+                     "note": "one contraction per step: with the cached half-rotated matrices (contract_fp64r_kernel) "
+                             "the refresh of the pairs whose path moved (rcache_collect/fill) and the pair kernel; "
+                             "for the walker-side form phi_columns_kernel, the FP64 GEMM forming Y_g = X_g phi_w and "
+                             "contract_fp64z_kernel; flops, time and traffic are theirs together; flops_per_launch "
+                             "counts the executed association order (cached: M = R Theta plus the refreshes); the "
+                             "per-pair order (R = Phi^T L_g formed every step) needs flops_per_launch_pair_order"},
         "cpu_baseline": cpu,
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 32,
@@ -753,6 +783,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--walkers", type=int, default=0, help="walkers per GPU (profiling runs on a small case)")
+    ap.add_argument("--no-rcache", action="store_true",
+                    help="FP64 headline without the cached half-rotated matrices (the walker-side form)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision, learned-proposal and batched measurements")
     ap.add_argument("--only", choices=("mixed", "learned", "batched", "popctl", "largest", "large_mixed"), default=None,

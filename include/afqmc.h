@@ -135,6 +135,13 @@ typedef struct {
                            apart from u sum W / W, u a Philox uniform (tag 10, entity walker_offset, the
                            step's index).  0 (default) turns it off; on, n_walkers <= 65535.  Each GPU of a
                            sharded run combs its own walkers */
+    int rcache;         /* 1: precision FP64 with the half-rotated matrices X_g Phi(x_wp) (g = h, L_1 ..)
+                           cached per pair and refreshed only for the paths whose Metropolis move was accepted
+                           since the last measurement; the contraction is then M = R Theta (2 N (n_up^2 +
+                           n_dn^2) multiply-adds per pair and matrix).  Costs (n_chol + 1) N n_up doubles of
+                           workspace per pair (16.4 GB for 512 x 32 pairs of the 50-orbital system) and needs
+                           4 warps' shares of Theta (N x (n_up + n_dn) complex) and one matrix (N x n_up) in
+                           220 KB of shared memory (e.g. N <= 64 with 10 + 10 electrons).  0 (default): off */
 } afqmc_config;
 
 /* Fill *cfg with defaults (combined constraint, prior proposal, FP64, Taylor
@@ -199,7 +206,8 @@ afqmc_status afqmc_history(afqmc_ctx* ctx, double* out, int n, int* n_out);
  *   4 device status word (0 = fine), 5 min weight, 6 max weight, 7 sum weight,
  *   8 pairs recomputed by the refinement (see refine_tol) since init,
  *   9 population-control combs applied since init (see pop_period),
- *   10 walkers those combs replaced by copies of others */
+ *   10 walkers those combs replaced by copies of others,
+ *   11 pairs whose cached half-rotated matrices were formed since init (see rcache) */
 afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len);
 
 /* Checkpoint.  The state buffer (host memory) is, in order, with no padding:
@@ -246,7 +254,8 @@ int64_t afqmc_launch_count(void);
  * walker-side form B_p^T (L_g phi_w) with B_p = Phi_p A_p^-T, N <= 64 and
  * n_up + n_dn <= 40), 3 contract_fp64z_kernel (precision FP64, walker-side form
  * Phi_p^T (L_g phi_w) A_p^-1 for blocks of 8 or 16 pairs of a walker: when
- * n_paths >= 8 and the block's operands fit in shared memory, e.g. N <= 64);
+ * n_paths >= 8 and the block's operands fit in shared memory, e.g. N <= 64),
+ * 4 contract_fp64r_kernel (precision FP64 with rcache = 1: cached R_g,p Theta);
  * -1 if `cfg` is NULL or no kernel supports its sizes.  Host only. */
 int afqmc_contract_kernel(const afqmc_config* cfg);
 

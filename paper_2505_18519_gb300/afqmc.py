@@ -35,7 +35,7 @@ class AfqmcConfig(ctypes.Structure):
         ("kill_threshold", ctypes.c_double), ("seed", ctypes.c_uint64), ("walker_offset", ctypes.c_int64),
         ("rw_step", ctypes.c_double), ("mlp_mix", ctypes.c_double), ("mlp_lr", ctypes.c_double),
         ("mlp_train", ctypes.c_int), ("refine_tol", ctypes.c_double),
-        ("importance", ctypes.c_int), ("pop_period", ctypes.c_int),
+        ("importance", ctypes.c_int), ("pop_period", ctypes.c_int), ("rcache", ctypes.c_int),
     ]
 
 
@@ -139,7 +139,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
                 constraint="combined", proposal="prior", precision="fp64", taylor_order=6, history_capacity=1024,
                 pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10, walker_offset=0, rw_step=0.3, mlp_mix=0.1,
                 mlp_lr=1e-3, mlp_train=False, refine_tol=1e-4, importance="hybrid",
-                pop_period=0) -> AfqmcConfig:
+                pop_period=0, rcache=False) -> AfqmcConfig:
     lib = load_library()
     c = AfqmcConfig()
     lib.afqmc_config_default(ctypes.byref(c))
@@ -152,6 +152,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
     c.rw_step, c.mlp_mix, c.mlp_lr, c.mlp_train = rw_step, mlp_mix, mlp_lr, int(bool(mlp_train))
     c.refine_tol = refine_tol
     c.importance, c.pop_period = IMPORTANCE[importance], pop_period
+    c.rcache = int(bool(rcache))
     return c
 
 
@@ -231,10 +232,10 @@ class Context:
         return out[: 4 * k.value].reshape(k.value, 4)
 
     def stats(self):
-        out = np.empty(11)
-        _check(load_library().afqmc_stats(self._ctx, out.ctypes.data, 11))
+        out = np.empty(12)
+        _check(load_library().afqmc_stats(self._ctx, out.ctypes.data, 12))
         keys = ("steps", "accepted", "proposed", "live_walkers", "status", "min_weight", "max_weight", "sum_weight",
-                "refined_pairs", "combs", "comb_replaced")
+                "refined_pairs", "combs", "comb_replaced", "rcache_formed")
         return dict(zip(keys, out.tolist()))
 
     def autotune(self):
@@ -361,7 +362,7 @@ class Batch:
 
 
 CONTRACT_KERNELS = {0: "contract_fp64_kernel", 1: "contract_tc_kernel", 2: "contract_tcy_kernel",
-                    3: "contract_fp64z_kernel"}
+                    3: "contract_fp64z_kernel", 4: "contract_fp64r_kernel"}
 
 
 def contract_kernel(cfg: AfqmcConfig) -> str:

@@ -48,6 +48,7 @@ extern "C" int64_t afqmc_launch_count(void) { return g_launches.load(); }
 extern "C" int afqmc_contract_kernel(const afqmc_config* cfg) {
     if (!cfg) return -1;
     if (cfg->precision == AFQMC_PRECISION_FP64) {
+        if (cfg->rcache) return contract_fp64r_supported(cfg->N, cfg->n_up, cfg->n_dn) ? 4 : -1;
         if (contract_fp64_walker_side(cfg->N, cfg->n_up, cfg->n_dn, cfg->n_paths)) return 3;
         return contract_fp64_supported(cfg->N, cfg->n_up, cfg->n_dn) ? 0 : -1;
     }
@@ -198,6 +199,10 @@ static const char* check_config(const afqmc_config* c) {
         return "unknown importance function";
     if (c->pop_period < 0) return "pop_period must be >= 0";
     if (c->pop_period > 0 && c->n_walkers > 65535) return "population control supports at most 65535 walkers";
+    if (c->rcache != 0 && c->rcache != 1) return "rcache must be 0 or 1";
+    if (c->rcache && c->precision != AFQMC_PRECISION_FP64) return "rcache needs precision FP64";
+    if (c->rcache && !contract_fp64r_supported(c->N, c->n_up, c->n_dn))
+        return "sizes too large for the cached half-rotation form (Theta and one matrix per warp, 4 warps per block)";
     if (c->walker_offset < 0 || (c->walker_offset + c->n_walkers) * (long long)c->n_paths > (1ll << 32))
         return "walker_offset out of range of the 32-bit stream entity";
     if (c->precision == AFQMC_PRECISION_FP64 && !contract_fp64_supported(c->N, c->n_up, c->n_dn))
@@ -293,13 +298,19 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
         w.comb_from = (int*)take(W * 4);
         w.comb_flag = (int*)take(2 * 4);
     }
+    if (c->rcache) {
+        w.rc = (double*)take(rcache_bytes(c->N, c->n_up, c->n_chol, (long long)c->n_walkers * c->n_paths));
+        w.rdirty = (int*)take(pairs * 4);
+        w.rlist = (int*)take(pairs * 4);
+        w.rcount = (int*)take(4);
+    }
     w.xprop = (double*)take(pairs * K * 8);
     w.Sprop = (double*)take(pairs * NN * 8);
     w.Phiprop = (double*)take(pairs * N * nu * 8);
     w.logdet_prop = (double2*)take(pairs * 2 * 16);
     w.history = (double*)take((size_t)c->history_capacity * 4 * 8);
     w.reduce = (double*)take(8 * 8);
-    w.counters = (unsigned long long*)take(8 * 8);
+    w.counters = (unsigned long long*)take(16 * 8);
     w.status = (int*)take(4);
     if (c->proposal == AFQMC_PROPOSAL_MLP) {
         MlpBuffers& m = w.mlp;
@@ -409,7 +420,7 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
                        d.pairs, d.P));
     if ((st = prof_mark(ctx, PH_MCMC_OVERLAP)) != AFQMC_OK) return st;
     CK(accept(s, d, p, w.counters, tag_acc, sweep, w.logdet_prop, w.xprop, w.Phiprop, w.alive, w.mlp.mu, w.mlp.logv,
-              w.logov_cur, w.x, w.Phi, w.counters));
+              w.logov_cur, w.x, w.Phi, w.counters, w.rdirty));
     return prof_mark(ctx, PH_ACCEPT);
 }
 
@@ -422,7 +433,7 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     afqmc_status st;
     const bool f16 = ctx->cfg.precision == AFQMC_PRECISION_FP16X3;
     const bool fp64 = ctx->cfg.precision == AFQMC_PRECISION_FP64;
-    const int ovl = fp64 ? (contract_fp64_walker_side(d.N, d.nu, d.nd, d.P) ? OVL_INVERSE : OVL_THETA)
+    const int ovl = fp64 ? (!w.rc && contract_fp64_walker_side(d.N, d.nu, d.nd, d.P) ? OVL_INVERSE : OVL_THETA)
                          : (contract_tc_walker_side(d.N, d.nu, d.nd, f16) ? OVL_TRIAL : OVL_THETA);
     CK(overlap_lu_both(s, d, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
                        ovl));
@@ -435,6 +446,9 @@ static afqmc_status measure(afqmc_ctx* ctx) {
             CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n,
                                     d.pairs, w.hdf, w.Ldf));
         }
+    } else if (w.rc) {   // cached half-rotated matrices, refreshed for the paths that moved
+        CK(rcache_refresh(s, d, w.h, w.Phi, w.rdirty, w.rlist, w.rcount, w.rc, w.counters));
+        CK(contract_fp64r(s, d, w.rc, w.Theta, w.vpair, w.epair));
     } else if (ovl == OVL_INVERSE)
         CK(contract_fp64_walker(s, d, w.h, w.L, w.Phi, w.Theta, w.phi, w.ywalk, w.vpair, w.epair));
     else
@@ -480,7 +494,7 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         if (e == cudaSuccess) e = copy_in(w.L, L, (size_t)d.G * NN * 8);
         if (e == cudaSuccess) e = copy_in(w.Phi0, Phi0, (size_t)d.N * d.nu * 8);
         if (e == cudaSuccess) e = copy_in(w.U, U, (size_t)d.K * NN * 8);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 8 * 8, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 16 * 8, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, 4, s);
         if (e != cudaSuccess) { st = fail(AFQMC_ERR_CUDA, "copying inputs: %s", cudaGetErrorString(e)); break; }
         StepParams p = params_of(cfg);
@@ -521,6 +535,7 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         }
         set_value(s, w.weight, d.W, 1.0);
         set_int(s, w.alive, d.W, 1);
+        if (w.rdirty) set_int(s, w.rdirty, d.pairs, 1);   // nothing cached yet
         for (int spin = 0; spin < 2; ++spin)
             overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet_new, nullptr, nullptr, w.status,
                        d.pairs, d.P);
@@ -535,7 +550,7 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
             st = mcmc_sweep(ctx, w.phi, TAG_BURN_PROPOSE, TAG_BURN_ACCEPT, b, true);
         if (st != AFQMC_OK) break;
         // the burn-in acceptances are not counted in the run statistics
-        if ((e = cudaMemsetAsync(w.counters, 0, 8 * 8, s)) != cudaSuccess ||
+        if ((e = cudaMemsetAsync(w.counters, 0, 16 * 8, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess) {
             st = fail(AFQMC_ERR_CUDA, "init: %s", cudaGetErrorString(e));
             break;
@@ -593,7 +608,7 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         CK(reorthonormalise(s, d, w.phi_new, w.phi, w.alive, w.status, d.W));
         CK(step_end(s, p, w.reduce, w.history, w.counters));
         if ((st = prof_mark(ctx, PH_FINISH)) != AFQMC_OK) return st;
-        CK(population_control(s, d, p, w.counters, w.weight, w.phi, w.x, w.Phi, w.comb_cum, w.comb_hit,
+        CK(population_control(s, d, p, w.counters, w.weight, w.phi, w.x, w.Phi, w.rc, w.rdirty, w.comb_cum, w.comb_hit,
                               w.comb_slot, w.comb_from, w.comb_flag));
         if ((st = prof_mark(ctx, PH_COMB)) != AFQMC_OK) return st;
         if (ctx->profiling) ctx->prof_steps++;
@@ -681,7 +696,7 @@ __global__ void weight_stats_kernel(int W, const double* __restrict__ weight, do
 
 extern "C" afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len) {
     if (!ctx || !out || len < 0) return fail(AFQMC_ERR_ARG, "bad arguments");
-    unsigned long long c[8];
+    unsigned long long c[16];
     double ws4[4];
     int status = 0;
     weight_stats_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d.W, ctx->ws.weight, ctx->ws.reduce + 4); count_launches(1);
@@ -690,9 +705,9 @@ extern "C" afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len) {
     CK(cudaMemcpyAsync(ws4, ctx->ws.reduce + 4, sizeof ws4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(&status, ctx->ws.status, sizeof status, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    double v[11] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3],
-                    (double)c[5], (double)c[6], (double)c[7]};
-    for (int i = 0; i < len && i < 11; ++i) out[i] = v[i];
+    double v[12] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3],
+                    (double)c[5], (double)c[6], (double)c[7], (double)c[8]};
+    for (int i = 0; i < len && i < 12; ++i) out[i] = v[i];
     return AFQMC_OK;
 }
 
@@ -742,8 +757,9 @@ extern "C" afqmc_status afqmc_state_load(afqmc_ctx* ctx, const void* buf, size_t
     CK(cudaMemcpyAsync(ctx->ws.weight, p, b = (size_t)d.W * 8, cudaMemcpyHostToDevice, ctx->stream)); p += b;
     CK(cudaMemcpyAsync(ctx->ws.x, p, b = (size_t)d.pairs * d.K * 8, cudaMemcpyHostToDevice, ctx->stream)); p += b;
     CK(cudaMemcpyAsync(ctx->ws.Phi, p, b = (size_t)d.pairs * d.N * d.nu * 8, cudaMemcpyHostToDevice, ctx->stream));
-    unsigned long long c[8] = {hdr[7], 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long c[16] = {hdr[7]};
     CK(cudaMemcpyAsync(ctx->ws.counters, c, sizeof c, cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->ws.rdirty) CK(set_int(ctx->stream, ctx->ws.rdirty, d.pairs, 1));   // every cached matrix is stale
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->steps_taken = (long long)hdr[7];
     ctx->measured = false;

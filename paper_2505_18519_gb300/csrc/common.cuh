@@ -196,6 +196,11 @@ struct Workspace {
     int* comb_slot;   // W   walker of every tooth, then the replaced slots
     int* comb_from;   // W   walker each replaced slot copies
     int* comb_flag;   // 2   whether this step combed, replaced walkers
+    // cached half-rotated matrices X_g Phi_p (FP64 path, null when off)
+    double* rc;       // W*P*(G+1)*N*n_up
+    int* rdirty;      // W*P  1: the pair's path moved since its matrices were formed
+    int* rlist;       // W*P  pairs to refresh
+    int* rcount;      // 1
     // Metropolis
     double* xprop;    // W*P*K
     double* Sprop;    // W*P*N*N   sum_k x'_k U_k
@@ -204,7 +209,7 @@ struct Workspace {
     // accounting
     double* history;  // capacity*4
     double* reduce;   // 8 doubles of scratch for reductions
-    unsigned long long* counters;  // [0] step, [1] accepted (total), [2] proposed (total), [3] accepted this step
+    unsigned long long* counters;  // 16: [0] step, [1] accepted (total), [2] proposed (total), [3] accepted this step
     int* status;      // 1 int
     MlpBuffers mlp;   // learned proposal (only with AFQMC_PROPOSAL_MLP)
     size_t total;

@@ -128,17 +128,27 @@ cudaError_t propose(cudaStream_t s, const Dims& d, const StepParams& p, const un
 cudaError_t accept(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
                    uint32_t sweep, const double2* logdet_prop, const double* xprop, const double* Phiprop,
                    const int* alive, const float* mu, const float* logv, double2* logov_cur, double* x, double* Phi,
-                   unsigned long long* counters);
+                   unsigned long long* counters, int* rdirty = nullptr);
 cudaError_t combine_logdet(cudaStream_t s, long long pairs, const double2* logdet, double2* logov);
 cudaError_t handoff(cudaStream_t s, const Dims& d, const StepParams& p, const double2* logov_cur,
                     const double2* old_sum, const double2* ratio, const double* Iabs, const double2* ebar,
                     const int* alive, double* weight, int* status);
+// rcache.cu: half-rotated matrices (X_g Phi_p) cached per pair, refreshed for the
+// pairs flagged dirty, and the FP64 contraction that reads them.
+bool contract_fp64r_supported(int N, int nu, int nd);
+size_t rcache_bytes(int N, int nu, int G, long long pairs);
+cudaError_t rcache_refresh(cudaStream_t s, const Dims& d, const double* X, const double* Phi, int* dirty, int* list,
+                           int* count, double* Rc, unsigned long long* counters);
+cudaError_t contract_fp64r(cudaStream_t s, const Dims& d, const double* Rc, const double2* Theta, double2* vpair,
+                           double2* epair);
 // Comb population control after every p.pop_period-th step (decided on the
 // device from counters[0]), gathering the walker state in place; cum, hit,
 // slot and from are W entries of scratch each, flag two ints.
+// The cached half-rotated matrices Rc and their dirty flags (both nullable) move
+// with the walkers.
 cudaError_t population_control(cudaStream_t s, const Dims& d, const StepParams& p, unsigned long long* counters,
-                               double* weight, double2* phi, double* x, double* Phi, double* cum, int* hit,
-                               int* slot, int* from, int* flag);
+                               double* weight, double2* phi, double* x, double* Phi, double* Rc, int* rdirty,
+                               double* cum, int* hit, int* slot, int* from, int* flag);
 cudaError_t step_end(cudaStream_t s, const StepParams& p, const double* measured3, double* history,
                      unsigned long long* counters);
 cudaError_t set_value(cudaStream_t s, double* out, long long n, double v);

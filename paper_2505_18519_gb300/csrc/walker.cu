@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(128) accept_kernel(int N, int nu, int K, int P
                                                      const double* __restrict__ xprop, const double* __restrict__ Phiprop,
                                                      const int* __restrict__ alive, const float* __restrict__ mu,
                                                      const float* __restrict__ logv, double2* logov_cur, double* x,
-                                                     double* Phi, unsigned long long* counters) {
+                                                     double* Phi, unsigned long long* counters, int* rdirty) {
     long long q = blockIdx.x;
     if (!alive[q / P]) return;
     __shared__ int acc;
@@ -562,6 +562,7 @@ __global__ void __launch_bounds__(128) accept_kernel(int N, int nu, int K, int P
         if (a) {
             logov_cur[q] = ln;
             atomicAdd(&counters[3], 1ull);
+            if (rdirty) rdirty[q] = 1;   // the pair's cached half-rotated matrices are stale
         }
         atomicAdd(&counters[4], 1ull);
     }
@@ -575,10 +576,10 @@ __global__ void __launch_bounds__(128) accept_kernel(int N, int nu, int K, int P
 cudaError_t accept(cudaStream_t s, const Dims& d, const StepParams& p, const unsigned long long* ctr, uint32_t tag,
                    uint32_t sweep, const double2* logdet_prop, const double* xprop, const double* Phiprop,
                    const int* alive, const float* mu, const float* logv, double2* logov_cur, double* x, double* Phi,
-                   unsigned long long* counters) {
+                   unsigned long long* counters, int* rdirty) {
     accept_kernel<<<(unsigned)d.pairs, 128, 0, s>>>(d.N, d.nu, d.K, d.P, p.woff, p.seed, tag, sweep, ctr, p.proposal,
                                                     p.mlp_mix, logdet_prop, xprop, Phiprop, alive, mu, logv, logov_cur, x,
-                                                    Phi, counters); count_launches(1);
+                                                    Phi, counters, rdirty); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -756,43 +757,61 @@ __global__ void __launch_bounds__(COMB_T) comb_select_kernel(int W, int period, 
     }
 }
 
-// The three walker-state arrays, rows of len[b] doubles per walker.
+// The walker-state arrays, rows of len[b] doubles per walker (a[3]: the cached
+// half-rotated matrices, len[3] = 0 without them), and the per-walker rows of
+// flen ints of their dirty flags (nullable).
 struct CombRows {
-    double* a[3];
-    long long len[3];
+    double* a[4];
+    long long len[4];
+    int* flags;
+    int flen;
 };
 
 // Replaced slot slot[r] of every state array gets the row of walker from[r];
 // those sources keep their own slots, so the copy is in place.  Work items are
-// chunks of COMB_CHUNK doubles of one row of one array.
+// chunks of COMB_CHUNK doubles of one row of one array; the item that copies the
+// first chunk of a slot's phi also copies its flags.
 __global__ void __launch_bounds__(256) comb_gather_kernel(CombRows r, const int* __restrict__ slot,
                                                           const int* __restrict__ from, const int* __restrict__ flag) {
     if (!flag[0]) return;
     const long long n = flag[1];
-    const long long c0 = (r.len[0] + COMB_CHUNK - 1) / COMB_CHUNK, c1 = (r.len[1] + COMB_CHUNK - 1) / COMB_CHUNK,
-                    c2 = (r.len[2] + COMB_CHUNK - 1) / COMB_CHUNK;
-    const long long per_slot = c0 + c1 + c2;
+    long long c[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) c[b] = (r.len[b] + COMB_CHUNK - 1) / COMB_CHUNK;
+    const long long per_slot = c[0] + c[1] + c[2] + c[3];
     for (long long it = blockIdx.x; it < n * per_slot; it += gridDim.x) {
         const long long q = it / per_slot;
         long long k = it - q * per_slot;
         int b = 0;
-        if (k >= c0) { k -= c0; b = 1; if (k >= c1) { k -= c1; b = 2; } }
-        const long long len = b == 0 ? r.len[0] : b == 1 ? r.len[1] : r.len[2];
-        double* base = b == 0 ? r.a[0] : b == 1 ? r.a[1] : r.a[2];
-        const double* in = base + (long long)from[q] * len;
-        double* o = base + (long long)slot[q] * len;
+        if (k >= c[0]) {
+            k -= c[0]; b = 1;
+            if (k >= c[1]) {
+                k -= c[1]; b = 2;
+                if (k >= c[2]) { k -= c[2]; b = 3; }
+            }
+        }
+        const long long len = b == 0 ? r.len[0] : b == 1 ? r.len[1] : b == 2 ? r.len[2] : r.len[3];
+        double* base = b == 0 ? r.a[0] : b == 1 ? r.a[1] : b == 2 ? r.a[2] : r.a[3];
+        const long long src = from[q], dst = slot[q];
+        const double* in = base + src * len;
+        double* o = base + dst * len;
         const long long e1 = min(len, (k + 1) * COMB_CHUNK);
         for (long long e = k * COMB_CHUNK + threadIdx.x; e < e1; e += 256) o[e] = in[e];
+        if (b == 0 && k == 0 && r.flags)
+            for (int e = threadIdx.x; e < r.flen; e += 256) r.flags[dst * r.flen + e] = r.flags[src * r.flen + e];
     }
 }
 
 cudaError_t population_control(cudaStream_t s, const Dims& d, const StepParams& p, unsigned long long* counters,
-                               double* weight, double2* phi, double* x, double* Phi, double* cum, int* hit,
-                               int* slot, int* from, int* flag) {
+                               double* weight, double2* phi, double* x, double* Phi, double* Rc, int* rdirty,
+                               double* cum, int* hit, int* slot, int* from, int* flag) {
     if (p.pop_period <= 0) return cudaSuccess;
     comb_select_kernel<<<1, COMB_T, 0, s>>>(d.W, p.pop_period, p.seed, (uint32_t)p.woff, counters, weight, cum, hit,
                                             slot, from, flag);
-    CombRows rows{{(double*)phi, x, Phi}, {(long long)d.N * d.nt * 2, (long long)d.P * d.K, (long long)d.P * d.N * d.nu}};
+    const long long rlen = Rc ? (long long)d.P * (d.G + 1) * d.N * d.nu : 0;
+    CombRows rows{{(double*)phi, x, Phi, Rc},
+                  {(long long)d.N * d.nt * 2, (long long)d.P * d.K, (long long)d.P * d.N * d.nu, rlen},
+                  Rc ? rdirty : nullptr, d.P};
     comb_gather_kernel<<<2 * 152, 256, 0, s>>>(rows, slot, from, flag);
     count_launches(2);
     return cudaGetLastError();

@@ -67,11 +67,12 @@ def test_batch_graph_equals_individual_steps():
 
 def test_batch_graph_combs_like_individual_steps():
     """Whether a step combs is decided on the device, so the one captured graph
-    serves the steps that comb and those that do not."""
+    serves the steps that comb and those that do not (the FP64 system with the
+    cached half-rotated matrices, whose refresh is sized on the device too)."""
     def mk(i, spec, W, P, prec):
         s = ai.make_system(spec)
         cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, 0.01, 70 + i, n_burn=2,
-                              precision=prec, pop_period=2, importance="local_energy")
+                              precision=prec, pop_period=2, importance="local_energy", rcache=prec == "fp64")
         return lib.Context(cfg, s.h, s.L, s.Phi0, s.U, stream=torch.cuda.Stream())
     batched = [mk(i, *sy) for i, sy in enumerate(SYSTEMS[:2])]
     single = [mk(i, *sy) for i, sy in enumerate(SYSTEMS[:2])]

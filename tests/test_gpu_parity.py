@@ -255,6 +255,64 @@ def test_comb_matches_oracle(importance, period):
     ctx.close()
 
 
+@pytest.mark.parametrize("name", ["c0", "ragged", "one_spin", "one_electron_each", "single_path", "medium",
+                                  "two_blocks_walker_side"])
+def test_half_rotation_cache_matches_oracle(name):
+    """FP64 with the cached half-rotated matrices X_g Phi_p: the measurement after a
+    state load (every pair formed) and three steps whose accepted moves leave pairs
+    to refresh match the oracle; the refresh count is every pair once plus the
+    pairs whose path moved."""
+    spec, W, P, dtau = SYSTEMS[name]
+    s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=700 + len(name), n_burn=2, n_sweeps=2, rcache=True)
+    assert lib.contract_kernel(ctx.cfg) == "contract_fp64r_kernel"
+    ost = oa.init(ham, ocfg)
+    ost, _ = oa.step(ham, ocfg, ost)
+    ctx.load_state_arrays(_as_dict(ost))
+    _compare_measure(ctx, ham, ost)
+    accepted = 0
+    for _ in range(3):
+        ctx.step(1)
+        ost, d = oa.step(ham, ocfg, ost)
+        accepted += d["n_accept"]
+        _compare_state(ctx.state_arrays(), ost)
+    _compare_measure(ctx, ham, ost)
+    formed = ctx.stats()["rcache_formed"]
+    assert W * P < formed <= W * P + accepted
+    ctx.close()
+
+
+def test_half_rotation_cache_follows_the_comb():
+    """The comb copies the cached matrices and their refresh flags with the walkers."""
+    spec, W, P, dtau = SYSTEMS["c0"]
+    s, ham, ocfg, ctx = _setup(spec, W, P, 0.05, seed=43, n_burn=3, pop_period=1, rcache=True)
+    ost = oa.init(ham, ocfg)
+    ost.weight = np.random.default_rng(5).exponential(size=W)
+    ost.weight[[1, 6]] = 0.0
+    ctx.load_state_arrays(_as_dict(ost))
+    for _ in range(3):
+        ctx.step(1)
+        ost, d = oa.step(ham, ocfg, ost)
+        _compare_state(ctx.state_arrays(), ost)
+        _compare_measure(ctx, ham, ost)
+    assert ctx.stats()["comb_replaced"] > 0
+    ctx.close()
+
+
+def test_half_rotation_cache_checkpoint_resume_is_bitwise():
+    spec, W, P, dtau = SYSTEMS["c0"]
+    s, ham, ocfg, a = _setup(spec, W, P, dtau, seed=91, n_burn=2, rcache=True)
+    _, _, _, b = _setup(spec, W, P, dtau, seed=91, n_burn=2, rcache=True)
+    a.step(2)
+    blob = a.save_state()
+    a.step(2)
+    b.load_state(blob)
+    b.step(2)
+    assert a.save_state() == b.save_state()
+    assert np.array_equal(a.history(2), b.history(2))
+    a.close()
+    b.close()
+
+
 def test_dead_walkers_stay_frozen():
     spec, W, P, dtau = SYSTEMS["c0"]
     s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=3, n_burn=1)

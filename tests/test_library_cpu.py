@@ -69,6 +69,23 @@ def test_population_control_fields_reach_the_library(L):
     assert d.importance == 0 and d.pop_period == 0 and d.refine_tol == 1e-4
 
 
+def test_half_rotation_cache_configuration(L):
+    """rcache = 1 needs FP64 and sizes whose Theta fits four warps' shared memory;
+    its workspace holds (n_chol + 1) N n_up doubles per pair more."""
+    base = lib.make_config(50, 10, 10, 250, 50, 16, 32, 0.005, 1)
+    rc = lib.make_config(50, 10, 10, 250, 50, 16, 32, 0.005, 1, rcache=True)
+    extra = lib.workspace_bytes(rc) - lib.workspace_bytes(base)
+    assert extra >= 16 * 32 * 251 * 50 * 10 * 8
+    assert extra < 16 * 32 * 251 * 50 * 10 * 8 + 16 * 32 * 8 + 4096
+    assert lib.workspace_bytes(lib.make_config(50, 10, 10, 250, 50, 16, 32, 0.005, 1, rcache=True,
+                                               precision="fp16x3")) == 0
+    assert lib.workspace_bytes(lib.make_config(120, 24, 24, 600, 120, 4, 8, 0.005, 1, rcache=True)) == 0
+    c = lib.make_config(8, 4, 4, 32, 8, 64, 16, 0.01, 1)
+    c.rcache = 2
+    assert lib.workspace_bytes(c) == 0
+    assert lib.contract_kernel(rc) == "contract_fp64r_kernel"
+
+
 def test_workspace_grows_with_walkers(L):
     a = lib.workspace_bytes(lib.make_config(50, 10, 10, 250, 50, 16, 32, 0.005, 1))
     b = lib.workspace_bytes(lib.make_config(50, 10, 10, 250, 50, 32, 32, 0.005, 1))
