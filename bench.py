@@ -300,7 +300,10 @@ FP64_WALKER_SIDE = "// ---------------------------------------------------------
 FP64_TRAFFIC = {   # kernel -> (committed summary, end of its device code, start of it), for the medium workload
     "contract_fp64_kernel": ("contract_fp64_medium_n50.md", FP64_WALKER_SIDE, None),
     "contract_fp64z_kernel": ("contract_fp64z_medium_n50.md", "size_t contract_fp64_smem", FP64_WALKER_SIDE),
+    "contract_fp64r_kernel": ("contract_fp64r_medium_n50.md", "// Running count of refreshed pairs",
+                              "// One warp per pair: Theta stays"),
 }
+FP64_SOURCE = {"contract_fp64r_kernel": "rcache.cu"}   # else contract_fp64.cu
 TC_TRAFFIC = {   # kernel -> (committed summary, end of its device code, start of it), for the medium workload
     "contract_tcy_kernel": ("contract_tcy_medium_n50.md", "struct TcyShape",
                             "// ---------------------------------------------------------------- walker-side form"),
@@ -728,7 +731,8 @@ def our_arm(args):
     else:
         flops = flops_pair_order
     achieved = flops / (contract_ms / 1e3) / 1e12
-    traffic = recorded_traffic(os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "contract_fp64.cu"),
+    traffic = recorded_traffic(os.path.join(ROOT, "paper_2505_18519_gb300", "csrc",
+                                            FP64_SOURCE.get(kernel, "contract_fp64.cu")),
                                *FP64_TRAFFIC[kernel]) if kernel in FP64_TRAFFIC and (W, P) == (512, 32) else None
     phases = {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}
 
@@ -759,7 +763,8 @@ def our_arm(args):
                              "for the walker-side form phi_columns_kernel, the FP64 GEMM forming Y_g = X_g phi_w and "
                              "contract_fp64z_kernel; flops, time and traffic are theirs together; flops_per_launch "
                              "counts the executed association order (cached: M = R Theta plus the refreshes); the "
-                             "per-pair order (R = Phi^T L_g formed every step) needs flops_per_launch_pair_order"},
+                             "per-pair order (R = Phi^T L_g formed every step) needs flops_per_launch_pair_order; "
+                             "with the cache, traffic is the pair kernel's (it reads every pair's matrices, 16.4 GB)"},
         "cpu_baseline": cpu,
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 32,
