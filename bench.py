@@ -536,6 +536,34 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
                                  "the selection (running sum of the weights, block scans) is latency-bound"},
             "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
 
+    if only in (None, "measpaths"):
+        # extra measurement-only paths on the mixed-precision step of the same workload:
+        # P' = 4 P paths from one sweep per round, against the plain estimate
+        cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
+                              walker_offset=rank * W, e_shift=28.5, precision="fp16x3")
+        ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
+        for _ in range(warmup):
+            ctx.step(1)
+        plain = ctx.energy()["e_mix"]
+        rounds, sweeps = 4, 1
+        ctx.energy_paths(rounds, sweeps)   # untimed first call
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        r = ctx.energy_paths(rounds, sweeps)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        ratio = r["ratio"][np.abs(r["ratio"]) > 0]
+        ctx.close()
+        out["measurement_paths"] = {
+            "precision": "fp16x3", "what": f"afqmc_energy_paths after {warmup} steps: {rounds} rounds x {sweeps} "
+            f"measurement-only sweep(s), P' = {rounds * P} paths per walker, against afqmc_energy's {P}",
+            "ms_per_call": ms, "ms_per_round": ms / rounds, "e_mix_plain": plain, "e_mix_paths": r["e_mix"],
+            "ratio_abs_median": float(np.median(np.abs(ratio))) if len(ratio) else None,
+            "ratio_abs_range": [float(np.min(np.abs(ratio))), float(np.max(np.abs(ratio)))] if len(ratio) else None}
+
     if only in (None, "largest"):
         # the largest system (N = 200, 40 + 40 electrons, 1000 Cholesky vectors) in FP64 on a
         # bounded sample: 19 walkers x 16 paths = 304 pairs, two full waves of the per-pair
@@ -792,7 +820,8 @@ def main():
                     help="FP64 headline without the cached half-rotated matrices (the walker-side form)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision, learned-proposal and batched measurements")
-    ap.add_argument("--only", choices=("mixed", "learned", "batched", "popctl", "largest", "large_mixed"), default=None,
+    ap.add_argument("--only", choices=("mixed", "learned", "batched", "popctl", "measpaths", "largest", "large_mixed"),
+                    default=None,
                     help="time one variant alone (profiling); skips the FP64 headline's extras")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -189,6 +189,24 @@ afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps);
 afqmc_status afqmc_energy(afqmc_ctx* ctx, double* e_mix, double* sum_w, double* mean_sign,
                           double* e_walker);
 
+/* Mixed energy from extra, measurement-only paths (Sec. III A, last paragraph;
+ * Appendix B.3).  From the current paths, `rounds` times `sweeps` Metropolis
+ * sweeps at the current walkers (Philox tags 11 and 12 with the current step's
+ * index, the sweep numbered r sweeps + m; the learned proposal gives way to the
+ * prior); the paths after every round count as P more samples, P' = rounds P.
+ * For every walker with W > 0 and |sum_p S_p| above the kill threshold:
+ *   E'_w = sum_p' S'_p' E_L,p' / sum_p' S'_p',
+ *   R_w  = (sum_p' S'_p' / P') / (sum_p S_p / P),
+ *   e_mix = Re( sum_w W_w R_w E'_w / sum_w W_w R_w ).
+ * e_walker and ratio (nullable) receive E'_w and R_w, 2*W doubles each (re, im;
+ * zero for walkers that do not count).  The propagation's paths, weights and
+ * statistics are left as they were.  Synchronises.  rounds >= 1, sweeps >= 0
+ * (one round without sweeps is afqmc_energy's estimate); not available with
+ * rcache = 1 (AFQMC_ERR_ARG).  Returns AFQMC_ERR_NUMERIC if the device status
+ * word is set. */
+afqmc_status afqmc_energy_paths(afqmc_ctx* ctx, int rounds, int sweeps, double* e_mix, double* e_walker,
+                                double* ratio);
+
 /* After afqmc_energy: copy per-pair and per-walker measurements to host arrays
  * (each nullable):
  *   logov       2*W*P       log <Phi(x_wp)|phi_w> = log|det| + i Arg det (both spins)

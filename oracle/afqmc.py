@@ -35,14 +35,24 @@ concern the oracle):
       leaves the scheme open): optional comb every pop_period steps, at the
       end of the step, drawn with one Philox uniform; otherwise weights are
       carried.  Optional constant E_T.
+  R11 initial walkers phi_w = Phi(x_w), x_w ~ p; paths x_wp ~ p; W = 1;
+      n_burn Metropolis sweeps at fixed phi before the first step.
+  R14 the local energy is measured every step at the start of the step.
   R17 importance function of the weight update (Sec. III A): "hybrid", |I| of
       Eq. (14) with the sampled-trial ratio Eq. (25) (default), or
       "local_energy", |I| = exp(-tau Re E_w(phi)) with E_w the path-averaged
       local energy Eq. (27) at the start of the step; the phase dtheta comes
       from the overlap ratio in both.
-  R11 initial walkers phi_w = Phi(x_w), x_w ~ p; paths x_wp ~ p; W = 1;
-      n_burn Metropolis sweeps at fixed phi before the first step.
-  R14 the local energy is measured every step at the start of the step.
+  R18 extra measurement paths (Sec. III A, last paragraph; Appendix B.3): from
+      the current paths, `rounds` times `sweeps` measurement-only Metropolis
+      sweeps at the current walker (own Philox tags; the learned proposal is
+      replaced by the prior, as in burn-in), the paths after every round
+      counting as P more samples; the walker's estimate is the sign-weighted
+      average over all P' = rounds P of them, and its weight gets the factor
+      R = (sum_p' S'_p' / P') / (sum_p S_p / P) in the numerator and the
+      denominator of Eq. (16) (the normalisation by P' and P is a constant
+      that cancels there).  Reported: Re of the complex ratio of the sums.
+      The propagation's own paths are left as they were.
 """
 
 from __future__ import annotations
@@ -56,7 +66,7 @@ from . import philox as px
 
 __all__ = ["OracleConfig", "Hamiltonian", "State", "prepare", "trial_orbitals", "log_overlap",
            "green", "local_energy_force_bias", "measure", "init", "step", "reorthonormalise",
-           "propagate_walker", "mcmc_sweep", "comb", "CONSTRAINTS", "IMPORTANCE"]
+           "propagate_walker", "mcmc_sweep", "comb", "measure_paths", "CONSTRAINTS", "IMPORTANCE"]
 
 CONSTRAINTS = ("combined", "separate", "half_plane")
 IMPORTANCE = ("hybrid", "local_energy")
@@ -301,6 +311,36 @@ def mcmc_sweep(ham: Hamiltonian, cfg: OracleConfig, st: State, logov_cur: np.nda
                 logov_cur[w, p] = lo_new
                 n_acc += 1
     return n_acc
+
+
+def measure_paths(ham: Hamiltonian, cfg: OracleConfig, st: State, rounds: int, sweeps: int):
+    """Mixed energy from extra, measurement-only paths (R18; Sec. III A and
+    Appendix B.3).  ``st`` is not modified.
+
+    Returns e_mix (Re of sum_w W_w R_w E'_w / sum_w W_w R_w over the live
+    walkers), the per-walker estimates E'_w, the factors R_w and the live mask.
+    """
+    W, P = st.x.shape[:2]
+    m = measure(ham, st)
+    alive = (st.weight > 0) & (np.abs(m["sumS"]) > cfg.kill_threshold)
+    work = st.copy()
+    logov = m["logov"].copy()
+    mcfg = dataclasses.replace(cfg, proposal="prior") if cfg.proposal == "mlp" else cfg
+    num = np.zeros(W, dtype=np.complex128)       # sum over the P' paths of S' E_L
+    den = np.zeros(W, dtype=np.complex128)       # sum over the P' paths of S'
+    for r in range(rounds):
+        for s in range(sweeps):
+            mcmc_sweep(ham, mcfg, work, logov, alive, st.step, r * sweeps + s, px.TAG_MEAS_PROPOSE,
+                       px.TAG_MEAS_ACCEPT)
+        mr = measure(ham, work)
+        num += (mr["S"] * mr["e_pair"]).sum(axis=1)
+        den += mr["S"].sum(axis=1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        e_walker = num / den
+        R = (den / (rounds * P)) / (m["sumS"] / P)
+    wr = np.where(alive, st.weight * R, 0.0)
+    e_mix = complex(np.sum(wr[alive] * e_walker[alive]) / np.sum(wr[alive])).real
+    return dict(e_mix=e_mix, e_walker=e_walker, R=R, alive=alive, num=num, den=den)
 
 
 def init(ham: Hamiltonian, cfg: OracleConfig, walker_index=None) -> State:

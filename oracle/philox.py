@@ -30,7 +30,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["philox4x32_10", "uniforms", "normals", "TAG_INIT_WALKER", "TAG_INIT_PATH",
-           "TAG_FIELD", "TAG_PROPOSE", "TAG_ACCEPT", "TAG_BURN_PROPOSE", "TAG_BURN_ACCEPT", "TAG_COMB"]
+           "TAG_FIELD", "TAG_PROPOSE", "TAG_ACCEPT", "TAG_BURN_PROPOSE", "TAG_BURN_ACCEPT", "TAG_COMB",
+           "TAG_MEAS_PROPOSE", "TAG_MEAS_ACCEPT"]
 
 TAG_INIT_WALKER = 1
 TAG_INIT_PATH = 2
@@ -40,6 +41,8 @@ TAG_ACCEPT = 5
 TAG_BURN_PROPOSE = 6
 TAG_BURN_ACCEPT = 7
 TAG_COMB = 10          # one uniform per population-control comb, entity = first walker's index
+TAG_MEAS_PROPOSE = 11  # measurement-only Metropolis sweeps (extra paths of the mixed estimate)
+TAG_MEAS_ACCEPT = 12
 
 _M0 = np.uint64(0xD2511F53)
 _M1 = np.uint64(0xCD9E8D57)

@@ -42,7 +42,7 @@ class AfqmcConfig(ctypes.Structure):
 _lib = None
 
 EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc_step", "afqmc_energy",
-           "afqmc_observables", "afqmc_history", "afqmc_stats", "afqmc_state_save", "afqmc_state_load",
+           "afqmc_energy_paths", "afqmc_observables", "afqmc_history", "afqmc_stats", "afqmc_state_save", "afqmc_state_load",
            "afqmc_destroy", "afqmc_last_error", "afqmc_philox_fill", "afqmc_profile", "afqmc_profile_read",
            "afqmc_launch_count", "afqmc_contract_kernel", "afqmc_autotune", "afqmc_batch_create", "afqmc_batch_step", "afqmc_batch_sync",
            "afqmc_batch_destroy", "afqmc_mlp_n_params", "afqmc_mlp_params", "afqmc_mlp_eval", "afqmc_mlp_state")
@@ -71,6 +71,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.afqmc_step.restype = I
     lib.afqmc_energy.argtypes = [P, D, D, D, P]
     lib.afqmc_energy.restype = I
+    lib.afqmc_energy_paths.argtypes = [P, I, I, D, P, P]
+    lib.afqmc_energy_paths.restype = I
     lib.afqmc_observables.argtypes = [P, P, P, P]
     lib.afqmc_observables.restype = I
     lib.afqmc_history.argtypes = [P, P, I, ctypes.POINTER(I)]
@@ -215,6 +217,15 @@ class Context:
         if walkers:
             out["e_walker"] = ew.view(np.complex128)
         return out
+
+    def energy_paths(self, rounds: int, sweeps: int):
+        """Mixed energy from extra measurement-only paths (see afqmc_energy_paths)."""
+        e = ctypes.c_double()
+        ew = np.empty(2 * self.W)
+        R = np.empty(2 * self.W)
+        _check(load_library().afqmc_energy_paths(self._ctx, int(rounds), int(sweeps), ctypes.byref(e),
+                                                 ew.ctypes.data, R.ctypes.data))
+        return dict(e_mix=e.value, e_walker=ew.view(np.complex128), ratio=R.view(np.complex128))
 
     def observables(self):
         lo = np.empty(2 * self.W * self.P)

@@ -298,6 +298,11 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
         w.comb_from = (int*)take(W * 4);
         w.comb_flag = (int*)take(2 * 4);
     }
+    w.xsave = (double*)take(pairs * K * 8);
+    w.Phisave = (double*)take(pairs * N * nu * 8);
+    w.msum0 = (double2*)take(W * 16);
+    w.macc = (double2*)take(2 * W * 16);
+    w.mout = (double2*)take((2 * W + 2) * 16);
     if (c->rcache) {
         w.rc = (double*)take(rcache_bytes(c->N, c->n_up, c->n_chol, (long long)c->n_walkers * c->n_paths));
         w.rdirty = (int*)take(pairs * 4);
@@ -708,6 +713,49 @@ extern "C" afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len) {
     double v[12] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3],
                     (double)c[5], (double)c[6], (double)c[7], (double)c[8]};
     for (int i = 0; i < len && i < 12; ++i) out[i] = v[i];
+    return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_energy_paths(afqmc_ctx* ctx, int rounds, int sweeps, double* e_mix, double* e_walker,
+                                           double* ratio) {
+    if (!ctx || !e_mix) return fail(AFQMC_ERR_ARG, "ctx and e_mix must not be NULL");
+    if (rounds < 1 || sweeps < 0) return fail(AFQMC_ERR_ARG, "rounds must be >= 1 and sweeps >= 0");
+    if (ctx->ws.rc) return fail(AFQMC_ERR_ARG, "measurement paths are not available with rcache = 1");
+    const Dims& d = ctx->d;
+    Workspace& w = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    afqmc_status st = measure(ctx);   // at the propagation's paths
+    if (st != AFQMC_OK) return st;
+    CK(cudaMemcpyAsync(w.xsave, w.x, (size_t)d.pairs * d.K * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(w.Phisave, w.Phi, (size_t)d.pairs * d.N * d.nu * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(w.msum0, w.sumS, (size_t)d.W * 16, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(w.logov_cur, w.logov, (size_t)d.pairs * 16, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(w.macc, 0, (size_t)d.W * 2 * 16, s));
+    CK(meas_alive(s, d, ctx->cfg.kill_threshold, w.weight, w.msum0, w.alive));
+    for (int r = 0; r < rounds && st == AFQMC_OK; ++r) {
+        for (int m = 0; m < sweeps && st == AFQMC_OK; ++m)   // the learned proposal gives way to the prior
+            st = mcmc_sweep(ctx, w.phi, TAG_MEAS_PROPOSE, TAG_MEAS_ACCEPT, (uint32_t)(r * sweeps + m), true);
+        if (st == AFQMC_OK) st = measure(ctx);
+        if (st == AFQMC_OK) CK(meas_accumulate(s, d, w.logov, w.epair, w.alive, w.macc));
+    }
+    // the propagation's paths back; the measurement's acceptances are not the step's
+    CK(cudaMemcpyAsync(w.x, w.xsave, (size_t)d.pairs * d.K * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(w.Phi, w.Phisave, (size_t)d.pairs * d.N * d.nu * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(w.counters + 3, 0, 2 * 8, s));
+    ctx->measured = false;
+    if (st != AFQMC_OK) return st;
+    CK(meas_finish(s, d, rounds, w.weight, w.msum0, w.alive, w.macc, w.mout));
+    double2 AB[2];
+    CK(cudaMemcpyAsync(AB, w.mout + 2 * d.W, sizeof AB, cudaMemcpyDeviceToHost, s));
+    if (e_walker) CK(cudaMemcpyAsync(e_walker, w.mout, (size_t)d.W * 16, cudaMemcpyDeviceToHost, s));
+    if (ratio) CK(cudaMemcpyAsync(ratio, w.mout + d.W, (size_t)d.W * 16, cudaMemcpyDeviceToHost, s));
+    int status = 0;
+    if ((st = read_status(ctx, &status)) != AFQMC_OK) return st;
+    const double bb = AB[1].x * AB[1].x + AB[1].y * AB[1].y;
+    *e_mix = bb > 0.0 ? (AB[0].x * AB[1].x + AB[0].y * AB[1].y) / bb : 0.0;   // Re(A / B)
+    if (status)
+        return fail(AFQMC_ERR_NUMERIC, "device status word 0x%x (1 singular overlap, 2 non-finite value, 4 tensor-core wait timed out)",
+                    status);
     return AFQMC_OK;
 }
 

@@ -78,7 +78,8 @@ __host__ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t 
 // Random-stream tags (counter word 3 = tag << 24 | sweep).
 enum : uint32_t {
     TAG_INIT_WALKER = 1, TAG_INIT_PATH = 2, TAG_FIELD = 3, TAG_PROPOSE = 4,
-    TAG_ACCEPT = 5, TAG_BURN_PROPOSE = 6, TAG_BURN_ACCEPT = 7, TAG_MLP_INIT = 9, TAG_COMB = 10
+    TAG_ACCEPT = 5, TAG_BURN_PROPOSE = 6, TAG_BURN_ACCEPT = 7, TAG_MLP_INIT = 9, TAG_COMB = 10,
+    TAG_MEAS_PROPOSE = 11, TAG_MEAS_ACCEPT = 12
 };
 
 __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
@@ -196,6 +197,12 @@ struct Workspace {
     int* comb_slot;   // W   walker of every tooth, then the replaced slots
     int* comb_from;   // W   walker each replaced slot copies
     int* comb_flag;   // 2   whether this step combed, replaced walkers
+    // extra measurement paths: the propagation's paths while the measurement's move
+    double* xsave;    // W*P*K
+    double* Phisave;  // W*P*N*n_up
+    double2* msum0;   // W    sum_p S_p of the propagation's paths
+    double2* macc;    // 2W   sum S' E_L, sum S' over the measurement paths
+    double2* mout;    // 2W+2 E'_w, R_w, sum W R E', sum W R
     // cached half-rotated matrices X_g Phi_p (FP64 path, null when off)
     double* rc;       // W*P*(G+1)*N*n_up
     int* rdirty;      // W*P  1: the pair's path moved since its matrices were formed

@@ -133,6 +133,14 @@ cudaError_t combine_logdet(cudaStream_t s, long long pairs, const double2* logde
 cudaError_t handoff(cudaStream_t s, const Dims& d, const StepParams& p, const double2* logov_cur,
                     const double2* old_sum, const double2* ratio, const double* Iabs, const double2* ebar,
                     const int* alive, double* weight, int* status);
+// Extra measurement paths: the walkers that count, the per-walker sums over a
+// round's paths (acc: 2W), and the estimate (out: 2W + 2, see walker.cu).
+cudaError_t meas_alive(cudaStream_t s, const Dims& d, double thr, const double* weight, const double2* sumS,
+                       int* alive);
+cudaError_t meas_accumulate(cudaStream_t s, const Dims& d, const double2* logov, const double2* epair,
+                            const int* alive, double2* acc);
+cudaError_t meas_finish(cudaStream_t s, const Dims& d, int rounds, const double* weight, const double2* sumS0,
+                        const int* alive, const double2* acc, double2* out);
 // rcache.cu: half-rotated matrices (X_g Phi_p) cached per pair, refreshed for the
 // pairs flagged dirty, and the FP64 contraction that reads them.
 bool contract_fp64r_supported(int N, int nu, int nd);

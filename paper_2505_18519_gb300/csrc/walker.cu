@@ -817,6 +817,93 @@ cudaError_t population_control(cudaStream_t s, const Dims& d, const StepParams& 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- extra measurement paths
+// Measurement-only paths (Sec. III A, last paragraph; Appendix B.3): the walkers
+// that count (W > 0, |sum_p S_p| above the kill threshold at the propagation's
+// paths), the sums over every round's paths, and the estimate with the factor
+// R_w = (sum' S' / P') / (sum S / P) in numerator and denominator.
+__global__ void meas_alive_kernel(int W, double thr, const double* __restrict__ weight,
+                                  const double2* __restrict__ sumS, int* alive) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < W) alive[w] = weight[w] > 0.0 && cabs_(sumS[w]) > thr;
+}
+
+// acc[2w] += sum_p S_p E_L,p and acc[2w + 1] += sum_p S_p (in path order), S_p = exp(i Im log ov_p).
+__global__ void meas_accumulate_kernel(int W, int P, const double2* __restrict__ logov,
+                                       const double2* __restrict__ epair, const int* __restrict__ alive,
+                                       double2* acc) {
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W || !alive[w]) return;
+    double2 num = acc[2 * w], den = acc[2 * w + 1];
+    for (int p = 0; p < P; ++p) {
+        double sn, cs;
+        sincos(logov[w * P + p].y, &sn, &cs);
+        const double2 S = cmk(cs, sn);
+        num = cadd(num, cmul(S, epair[w * P + p]));
+        den = cadd(den, S);
+    }
+    acc[2 * w] = num;
+    acc[2 * w + 1] = den;
+}
+
+// out[w] = E'_w, out[W + w] = R_w (zero for the walkers that do not count),
+// out[2W] = sum_w W_w R_w E'_w, out[2W + 1] = sum_w W_w R_w; one block, fixed-order tree.
+__global__ void __launch_bounds__(1024) meas_finish_kernel(int W, int rounds, const double* __restrict__ weight,
+                                                           const double2* __restrict__ sumS0,
+                                                           const int* __restrict__ alive,
+                                                           const double2* __restrict__ acc, double2* out) {
+    __shared__ double2 ra[1024], rb[1024];
+    double2 A = cmk(0.0, 0.0), B = cmk(0.0, 0.0);
+    for (int w = threadIdx.x; w < W; w += 1024) {
+        double2 e = cmk(0.0, 0.0), R = cmk(0.0, 0.0);
+        if (alive[w]) {
+            const double2 den = acc[2 * w + 1];
+            e = cdiv(acc[2 * w], den);
+            R = cdiv(den, cmk(rounds * sumS0[w].x, rounds * sumS0[w].y));
+            const double2 wr = cmk(weight[w] * R.x, weight[w] * R.y);
+            A = cadd(A, cmul(wr, e));
+            B = cadd(B, wr);
+        }
+        out[w] = e;
+        out[W + w] = R;
+    }
+    ra[threadIdx.x] = A;
+    rb[threadIdx.x] = B;
+    __syncthreads();
+    for (int off = 512; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            ra[threadIdx.x] = cadd(ra[threadIdx.x], ra[threadIdx.x + off]);
+            rb[threadIdx.x] = cadd(rb[threadIdx.x], rb[threadIdx.x + off]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * W] = ra[0];
+        out[2 * W + 1] = rb[0];
+    }
+}
+
+cudaError_t meas_alive(cudaStream_t s, const Dims& d, double thr, const double* weight, const double2* sumS,
+                       int* alive) {
+    meas_alive_kernel<<<(d.W + 255) / 256, 256, 0, s>>>(d.W, thr, weight, sumS, alive);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t meas_accumulate(cudaStream_t s, const Dims& d, const double2* logov, const double2* epair,
+                            const int* alive, double2* acc) {
+    meas_accumulate_kernel<<<(d.W + 127) / 128, 128, 0, s>>>(d.W, d.P, logov, epair, alive, acc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t meas_finish(cudaStream_t s, const Dims& d, int rounds, const double* weight, const double2* sumS0,
+                        const int* alive, const double2* acc, double2* out) {
+    meas_finish_kernel<<<1, 1024, 0, s>>>(d.W, rounds, weight, sumS0, alive, acc, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- step bookkeeping
 // counters: [0] steps taken, [1] accepted total, [2] proposed total,
 // [3] accepted this step, [4] proposed this step.

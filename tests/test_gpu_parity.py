@@ -313,6 +313,43 @@ def test_half_rotation_cache_checkpoint_resume_is_bitwise():
     b.close()
 
 
+@pytest.mark.parametrize("name,proposal", [("c0", "prior"), ("ragged", "pcn")])
+def test_measurement_paths_match_oracle(name, proposal):
+    """Extra measurement-only paths: the estimate, every walker's E'_w and R_w
+    against the oracle; the propagation's state is left as it was (the next
+    step still matches); one round without sweeps is the plain estimate."""
+    spec, W, P, dtau = SYSTEMS[name]
+    s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=801, n_burn=2, proposal=proposal, pcn_beta=0.5)
+    ost = oa.init(ham, ocfg)
+    ost, _ = oa.step(ham, ocfg, ost)
+    ost.weight[1] = 0.0
+    ctx.load_state_arrays(_as_dict(ost))
+    g = ctx.energy_paths(3, 2)
+    o = oa.measure_paths(ham, ocfg, ost, 3, 2)
+    live = o["alive"]
+    assert live.sum() >= W // 2 and not live[1]
+    assert abs(g["e_mix"] - o["e_mix"]) < E_TOL
+    assert np.max(np.abs(g["e_walker"][live] - o["e_walker"][live])) < E_TOL
+    assert np.max(np.abs(g["ratio"][live] - o["R"][live])) < 1e-9
+    assert np.all(g["ratio"][~live] == 0)
+    assert np.max(np.abs(o["R"][live] - 1.0)) > 1e-6        # the measurement paths moved
+    _compare_state(ctx.state_arrays(), ost)
+    ctx.step(1)
+    ost2, _ = oa.step(ham, ocfg, ost)
+    _compare_state(ctx.state_arrays(), ost2)
+    g1 = ctx.energy_paths(1, 0)
+    assert abs(g1["e_mix"] - ctx.energy()["e_mix"]) < 1e-11
+    ctx.close()
+
+
+def test_measurement_paths_are_refused_with_the_cache():
+    spec, W, P, dtau = SYSTEMS["c0"]
+    s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=5, n_burn=1, rcache=True)
+    with pytest.raises(lib.AfqmcError):
+        ctx.energy_paths(1, 0)
+    ctx.close()
+
+
 def test_dead_walkers_stay_frozen():
     spec, W, P, dtau = SYSTEMS["c0"]
     s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=3, n_burn=1)

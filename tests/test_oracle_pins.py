@@ -534,3 +534,82 @@ def test_comb_step_resamples_the_walkers_of_the_plain_step():
     for name in ("phi_up", "phi_dn", "x", "Phi"):
         np.testing.assert_array_equal(getattr(combed, name), getattr(plain, name)[ref_src])
     assert len(set(ref_src.tolist())) < 8 and plain.weight[0] == 0.0 and combed.weight[0] > 0.0
+
+
+# ---------------------------------------------------------------- extra measurement paths
+def test_measurement_paths_without_sweeps_are_the_plain_estimate():
+    """One round and no sweep: the measurement paths are the propagation's, so
+    R = 1, E'_w = E_w and the estimate is Eq. (16)'s; the state is untouched."""
+    s, run = ai.make_config("small_n8")
+    ham = _ham(s, 4, 4, run.dtau)
+    cfg = oa.OracleConfig(dtau=run.dtau, n_walkers=6, n_paths=5, seed=14, n_burn=2)
+    st, _ = oa.step(ham, cfg, oa.init(ham, cfg))
+    st.weight[2] = 0.0
+    before = st.copy()
+    r = oa.measure_paths(ham, cfg, st, rounds=1, sweeps=0)
+    m = oa.measure(ham, st)
+    num, den = oa.mixed_energy(st.weight, m["e_bar"])
+    assert abs(r["e_mix"] - num / den) < 1e-12
+    assert np.allclose(r["R"][r["alive"]], 1.0, rtol=0, atol=1e-13)
+    assert np.allclose(r["e_walker"], m["e_bar"], rtol=0, atol=1e-12)
+    for name in ("x", "Phi", "weight", "phi_up"):
+        assert np.array_equal(getattr(st, name), getattr(before, name))
+    # with sweeps the paths move and the estimate changes
+    r2 = oa.measure_paths(ham, cfg, st, rounds=2, sweeps=1)
+    assert abs(r2["e_mix"] - r["e_mix"]) > 1e-8
+
+
+def test_measurement_paths_in_the_exact_limits():
+    """U = 0 (every path gives Phi0): R = 1 and the same estimate for any number
+    of rounds; an exact-eigenstate trial (L = 0, [U_k, h] = 0): E' = E0."""
+    s = _small_system(8, 3, 3, K=4, seed=8)
+    ham0 = _ham(s, 3, 3, dtau=0.02, U=np.zeros_like(s.U[:4]))
+    cfg = oa.OracleConfig(dtau=0.02, n_walkers=5, n_paths=3, seed=19, n_burn=1)
+    st, _ = oa.step(ham0, cfg, oa.init(ham0, cfg))
+    plain = oa.measure_paths(ham0, cfg, st, rounds=1, sweeps=0)
+    more = oa.measure_paths(ham0, cfg, st, rounds=3, sweeps=2)
+    assert np.allclose(more["R"], 1.0, rtol=0, atol=1e-12)
+    assert abs(more["e_mix"] - plain["e_mix"]) < 1e-11
+    rng = np.random.default_rng(3)
+    U, _ = _commuting_U(s.h, 4, 3, rng)
+    hame = _ham(s, 3, 3, dtau=0.02, U=U, L=np.zeros((2, 8, 8)))
+    e0 = 2.0 * np.sum(np.linalg.eigvalsh(s.h)[:3])
+    st, _ = oa.step(hame, cfg, oa.init(hame, cfg))
+    r = oa.measure_paths(hame, cfg, st, rounds=3, sweeps=2)
+    assert abs(r["e_mix"] - e0) < 1e-11 and np.allclose(r["e_walker"], e0, atol=1e-11)
+
+
+def test_measurement_paths_converge_to_the_quadrature():
+    """K = 1: with many measurement rounds at one walker, the sign-weighted
+    average over the measurement paths, and the estimate weighted by R, tend
+    to <Psi_T|H|phi>/<Psi_T|phi> given by Gauss-Hermite quadrature."""
+    N, n = 4, 2
+    s = _small_system(N, n, n, G=3, K=1, seed=43)
+    rng = np.random.default_rng(8)
+    ham = _ham(s, n, n, U=2.0 * s.U[:1])
+    phu, phd = _rand_walker(rng, N, n), _rand_walker(rng, N, n)
+    xq, wq = np.polynomial.hermite_e.hermegauss(80)
+    num = den = dabs = 0.0
+    for xj, wj in zip(xq, wq):
+        Phi = oa.trial_orbitals(ham, np.array([xj]))
+        ov = np.exp(oa.log_overlap(ham, Phi, phu, phd))
+        e, _ = oa.local_energy_force_bias(ham, Phi, phu, phd)
+        num, den, dabs = num + wj * ov * e, den + wj * ov, dabs + wj * abs(ov)
+    e_exact = num / den
+    sign_exact = den / dabs          # mean path sign under |ov| p(x)
+    W, P = 8, 32
+    cfg = oa.OracleConfig(dtau=0.01, n_walkers=W, n_paths=P, seed=78, n_burn=10)
+    st = oa.init(ham, cfg)
+    st.phi_up[:] = phu
+    st.phi_dn[:] = phd
+    logov = np.array([[oa.log_overlap(ham, st.Phi[w, p], phu, phd) for p in range(P)] for w in range(W)])
+    for b in range(10):   # equilibrate the paths at this walker
+        oa.mcmc_sweep(ham, cfg, st, logov, np.ones(W, dtype=bool), 0, b, px.TAG_BURN_PROPOSE, px.TAG_BURN_ACCEPT)
+    sumS = oa.measure(ham, st)["sumS"]
+    r = oa.measure_paths(ham, cfg, st, rounds=60, sweeps=1)
+    pooled = r["num"].sum() / r["den"].sum()
+    assert abs(pooled - e_exact) < 0.02 * abs(e_exact)
+    assert abs(r["e_mix"] - e_exact.real) < 0.03 * abs(e_exact)
+    # R_w (sum_p S_p / P) is the measurement paths' mean sign, which tends to the exact one
+    assert 0.05 < abs(sign_exact) < 0.95
+    assert abs(np.mean(r["R"] * sumS / P) - sign_exact) < 0.05
