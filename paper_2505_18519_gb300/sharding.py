@@ -5,7 +5,11 @@ random draw is addressed by the walker's global index (the library's
 ``walker_offset``), so splitting one population into contiguous blocks of
 walkers reproduces the single-GPU run exactly.  The only exchange is the
 mixed-estimator sums {sum W Re E, sum W, sum W |sum S|/P} of each measured step,
-three doubles, summed over ranks.
+three doubles, summed over ranks; for the estimate from extra measurement paths
+(afqmc_energy_paths), the complex sums {sum W R E', sum W R}.  With population
+control on (pop_period > 0) every GPU combs its own walkers, with no walker
+exchange, so a sharded run is a different (equally valid) population from the
+single-GPU one from the first comb on.
 """
 
 from __future__ import annotations
@@ -35,6 +39,28 @@ def combine_mixed(sums, group=None):
         dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     num, den, sgn = t.tolist()
     return (num / den if den > 0 else 0.0), den, (sgn / den if den > 0 else 0.0)
+
+
+def combine_paths(weight, e_walker, ratio, group=None) -> float:
+    """Global estimate from extra measurement paths: each rank passes its
+    walkers' weights W_w and the E'_w and R_w that afqmc_energy_paths returned
+    (R_w = 0 for walkers that do not count); returns
+    Re(sum W R E' / sum W R) over all ranks."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    wr = np.asarray(weight, dtype=np.float64) * np.asarray(ratio, dtype=np.complex128)
+    num = np.sum(wr * np.asarray(e_walker, dtype=np.complex128))
+    den = np.sum(wr)
+    dev = "cpu"
+    if dist.is_initialized() and dist.get_backend(group) == "nccl":
+        dev = torch.device("cuda", torch.cuda.current_device())
+    t = torch.tensor([num.real, num.imag, den.real, den.imag], dtype=torch.float64, device=dev)
+    if dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    nr, ni, dr, di = t.tolist()
+    q = complex(nr, ni) / complex(dr, di) if (dr, di) != (0.0, 0.0) else 0.0
+    return float(np.real(q))
 
 
 def max_over_ranks(value: float, group=None) -> float:

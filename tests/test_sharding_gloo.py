@@ -12,7 +12,7 @@ import torch.multiprocessing as mp
 
 import afqmc_inputs as ai
 from oracle import afqmc as oa
-from paper_2505_18519_gb300.sharding import combine_mixed, max_over_ranks, shard
+from paper_2505_18519_gb300.sharding import combine_mixed, combine_paths, max_over_ranks, shard
 
 W, P, STEPS = 10, 4, 3
 
@@ -45,9 +45,14 @@ def _rank_main(rank, world, port, q):
         st, d = oa.step(ham, cfg, st)
         num, den = d["mixed"]
         out.append(combine_mixed((num, den, 0.0)))
+    # extra measurement paths on each rank's walkers: their chains are addressed by the
+    # global pair index too, so the combined estimate is the single process's
+    r = oa.measure_paths(ham, cfg, st, rounds=2, sweeps=1)
+    R = np.where(r["alive"], r["R"], 0.0)
+    e_paths = combine_paths(st.weight, np.where(r["alive"], r["e_walker"], 0.0), R)
     slowest = max_over_ranks(float(rank + 1))
     if rank == 0:
-        q.put((out, slowest))
+        q.put((out, e_paths, slowest))
     dist.destroy_process_group()
 
 
@@ -65,7 +70,7 @@ def test_two_gloo_ranks_reproduce_one_process():
     procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    out, slowest = q.get(timeout=300)
+    out, e_paths, slowest = q.get(timeout=300)
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
@@ -77,4 +82,6 @@ def test_two_gloo_ranks_reproduce_one_process():
         e_mix, sum_w, _ = out[k]
         assert abs(e_mix - num / den) < 1e-12 * abs(num / den)
         assert abs(sum_w - den) < 1e-12 * den
+    ref = oa.measure_paths(ham, cfg, st, rounds=2, sweeps=1)["e_mix"]
+    assert abs(e_paths - ref) < 1e-12 * abs(ref)
     assert slowest == 2.0
