@@ -1,0 +1,50 @@
+"""Host-side checks of the benchmark's bookkeeping (no GPU): the committed ncu
+summaries still describe the device code bench.py reports traffic for, and the
+FLOP counts behind its roofline figures have the values the summaries quote."""
+
+import importlib.util
+import os
+
+import pytest
+
+import afqmc_inputs as ai
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("kernel,bytes_per_launch", [("contract_fp64z_kernel", 3.89e9),
+                                                     ("contract_fp64r_kernel", 16.82e9)])
+def test_fp64_summaries_match_the_device_code(bench, kernel, bytes_per_launch):
+    src = os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", bench.FP64_SOURCE.get(kernel, "contract_fp64.cu"))
+    assert bench.recorded_traffic(src, *bench.FP64_TRAFFIC[kernel]) == pytest.approx(bytes_per_launch)
+
+
+def test_tensor_core_summary_matches_the_device_code(bench):
+    src = os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "contract_tc.cu")
+    assert bench.recorded_traffic(src, *bench.TC_TRAFFIC["contract_tcy_kernel"]) == pytest.approx(6.34e9)
+
+
+def test_a_changed_kernel_voids_its_traffic(bench, tmp_path):
+    src = os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "rcache.cu")
+    text = open(src).read().replace("acc.x = fma(r, t.x, acc.x);", "acc.x = fma(t.x, r, acc.x);", 1)
+    changed = tmp_path / "rcache.cu"
+    changed.write_text(text)
+    assert bench.recorded_traffic(str(changed), *bench.FP64_TRAFFIC["contract_fp64r_kernel"]) is None
+
+
+def test_flop_counts_of_the_medium_workload(bench):
+    spec, run = ai.CONFIGS["medium_n50"]
+    assert bench.contract_flops_per_pair(spec) == pytest.approx(22.99e6, rel=1e-3)      # per-pair order
+    assert bench.contract_flops_walker_side(spec, run.n_paths) == pytest.approx(16.02e6, rel=1e-3)
+    assert bench.contract_flops_cached(spec) == pytest.approx(10.44e6, rel=1e-3)
+    assert bench.contract_flops_refresh(spec) == pytest.approx(12.55e6, rel=1e-3)
+    # the cached form's share per refreshed pair: (G + 1) matrices of 2 n_up N^2
+    assert bench.contract_flops_refresh(spec) == (spec.n_chol + 1) * 2 * spec.n_up * spec.N ** 2
