@@ -53,6 +53,11 @@ concern the oracle):
       denominator of Eq. (16) (the normalisation by P' and P is a constant
       that cancels there).  Reported: Re of the complex ratio of the sums.
       The propagation's own paths are left as they were.
+  R19 complex trial samples (Eq. (30), single slice): Phi(x) = exp(alpha
+      sum_k x_k U_k) Phi0 with a complex alpha (-i sqrt(s) and U_k = L_k for
+      the VAFQMC form; Phi0 absorbs exp(-t T) exp(-t0 T0) phi_T), so every
+      overlap and Green's function takes Phi^dagger; the real form (alpha = 1)
+      is unchanged.  The multi-slice form is not covered.
 """
 
 from __future__ import annotations
@@ -104,6 +109,7 @@ class Hamiltonian:
     n_dn: int
     T: np.ndarray          # h - 1/2 sum_g L_g L_g
     expT_half: np.ndarray  # exp(-tau T / 2)
+    alpha: complex = 1.0   # R19: Phi(x) = exp(alpha sum_k x_k U_k) Phi0 (1: the real form)
 
 
 @dataclasses.dataclass
@@ -135,21 +141,28 @@ def _expm_sym(A: np.ndarray) -> np.ndarray:
     return (V * np.exp(lam)[..., None, :]) @ np.swapaxes(V, -1, -2)
 
 
-def prepare(h, L, Phi0, U, n_up: int, n_dn: int, dtau: float) -> Hamiltonian:
+def prepare(h, L, Phi0, U, n_up: int, n_dn: int, dtau: float, alpha: complex = 1.0) -> Hamiltonian:
     """One-body operator of the Monte Carlo form, Eq. (3) with reading R1, and
-    the exact half-step kinetic propagator exp(-tau T/2) of Eq. (5)."""
+    the exact half-step kinetic propagator exp(-tau T/2) of Eq. (5).  ``alpha``
+    is the factor of the hidden-variable exponent (R19): 1 for the real trial
+    samples, -i sqrt(s) for the single-slice VAFQMC form of Eq. (30) with
+    U_k = L_k and Phi0 = exp(-t T) exp(-t0 T0) phi_T."""
     h = np.asarray(h, dtype=np.float64)
     L = np.asarray(L, dtype=np.float64)
     T = h - 0.5 * np.einsum("gij,gjk->ik", L, L)
     return Hamiltonian(h, L, np.asarray(Phi0, dtype=np.float64), np.asarray(U, dtype=np.float64),
-                       n_up, n_dn, T, _expm_sym(-0.5 * dtau * T))
+                       n_up, n_dn, T, _expm_sym(-0.5 * dtau * T), complex(alpha) if alpha != 1.0 else 1.0)
 
 
 def trial_orbitals(ham: Hamiltonian, x: np.ndarray) -> np.ndarray:
-    """Phi(x) = exp(sum_k x_k U_k) Phi0, the determinant of one hidden-variable
-    sample of the trial, Eq. (20)-(21) with one slice; x has shape (..., K)."""
+    """Phi(x) = exp(alpha sum_k x_k U_k) Phi0, the determinant of one
+    hidden-variable sample of the trial, Eq. (20)-(21) with one slice (alpha = 1,
+    real), or the complex single-slice form of Eq. (30) (R19); x has shape (..., K)."""
     S = np.einsum("...k,kij->...ij", x, ham.U)
-    return _expm_sym(S) @ ham.Phi0
+    if ham.alpha == 1.0:
+        return _expm_sym(S) @ ham.Phi0
+    lam, V = np.linalg.eigh(S)        # exp(alpha S) = V exp(alpha lam) V^T for real symmetric S
+    return (V * np.exp(ham.alpha * lam)[..., None, :]) @ np.swapaxes(V, -1, -2) @ ham.Phi0
 
 
 # ---------------------------------------------------------------------------
@@ -164,19 +177,24 @@ def _slog(A: np.ndarray) -> np.ndarray:
     return logabs + 1j * np.angle(sign)
 
 
+def _adj(A: np.ndarray) -> np.ndarray:
+    """Conjugate transpose over the last two axes (the transpose for real A)."""
+    return np.swapaxes(np.conj(A), -1, -2)
+
+
 def log_overlap(ham: Hamiltonian, Phi: np.ndarray, phi_up: np.ndarray, phi_dn: np.ndarray) -> np.ndarray:
-    """log <Phi|phi> = sum over spins of log det(Phi_s^T phi_s) (Eq. (25), (26));
-    Phi is real so Phi^dagger = Phi^T.  Shapes broadcast over leading axes."""
+    """log <Phi|phi> = sum over spins of log det(Phi_s^dagger phi_s) (Eq. (25), (26));
+    Phi^dagger = Phi^T for the real trial samples.  Shapes broadcast over leading axes."""
     Pu = Phi
     Pd = Phi[..., : ham.n_dn]
-    return _slog(np.swapaxes(Pu, -1, -2) @ phi_up) + _slog(np.swapaxes(Pd, -1, -2) @ phi_dn)
+    return _slog(_adj(Pu) @ phi_up) + _slog(_adj(Pd) @ phi_dn)
 
 
 def green(Phi_s: np.ndarray, phi_s: np.ndarray) -> np.ndarray:
     """Mixed one-body Green's function of one spin, G_ij = <Phi|c+_i c_j|phi>/<Phi|phi>
-    = [phi (Phi^T phi)^-1 Phi^T]_ji."""
-    A = np.swapaxes(Phi_s, -1, -2) @ phi_s
-    M = phi_s @ np.linalg.inv(A) @ np.swapaxes(Phi_s, -1, -2)
+    = [phi (Phi^dagger phi)^-1 Phi^dagger]_ji."""
+    A = _adj(Phi_s) @ phi_s
+    M = phi_s @ np.linalg.inv(A) @ _adj(Phi_s)
     return np.swapaxes(M, -1, -2)
 
 

@@ -613,3 +613,98 @@ def test_measurement_paths_converge_to_the_quadrature():
     # R_w (sum_p S_p / P) is the measurement paths' mean sign, which tends to the exact one
     assert 0.05 < abs(sign_exact) < 0.95
     assert abs(np.mean(r["R"] * sumS / P) - sign_exact) < 0.05
+
+
+# ---------------------------------------------------------------- complex trial samples
+def test_complex_trial_local_energy_matches_determinant_space(c0):
+    """Complex trial samples (R19, alpha = -i sqrt(s)): the bra <Phi| has the
+    complex-conjugate determinant coefficients, so by brute force
+    E_L = conj(c_Phi) H c_phi / conj(c_Phi) c_phi; the oracle's Phi^dagger
+    formulas must agree, as must the overlap and every force-bias value."""
+    s, run, fs, H = c0
+    ham = oa.prepare(s.h, s.L, s.Phi0, s.U, 4, 4, run.dtau, alpha=-0.6j)
+    rng = np.random.default_rng(21)
+    for _ in range(3):
+        x = rng.normal(size=ham.U.shape[0])
+        Phi = oa.trial_orbitals(ham, x)
+        assert np.iscomplexobj(Phi) and np.max(np.abs(Phi.imag)) > 1e-3
+        phu, phd = _rand_walker(rng, 8, 4), _rand_walker(rng, 8, 4)
+        cP = fs.determinant(Phi, Phi).conj()
+        cp = fs.determinant(phu, phd)
+        ov = cP @ cp
+        e_fs = (cP @ (H @ cp)) / ov
+        e, v = oa.local_energy_force_bias(ham, Phi, phu, phd)
+        assert abs(e - e_fs) < 1e-10 * max(1.0, abs(e_fs))
+        assert abs(np.exp(oa.log_overlap(ham, Phi, phu, phd)) - ov) < 1e-10 * abs(ov)
+        for g in (0, 7, 30):
+            vg = (cP @ (fs.one_body(s.L[g], 4, 4) @ cp)) / ov
+            assert abs(v[g] - vg) < 1e-11 * max(1.0, abs(vg))
+
+
+def test_complex_trial_orbitals_are_a_unitary_rotation():
+    """exp(-i c S) with S real symmetric is unitary: Phi(x)^dagger Phi(x) =
+    Phi0^T Phi0 for every x, and alpha = 1 gives the real form unchanged."""
+    s = _small_system(9, 3, 3, K=4, seed=12)
+    hr = _ham(s, 3, 3, dtau=0.01, U=s.U[:4])
+    hc = oa.prepare(s.h, s.L, s.Phi0, s.U[:4], 3, 3, 0.01, alpha=-0.8j)
+    x = np.random.default_rng(2).normal(size=(5, 4))
+    Phi = oa.trial_orbitals(hc, x)
+    gram = np.swapaxes(Phi.conj(), -1, -2) @ Phi
+    assert np.allclose(gram, s.Phi0.T @ s.Phi0, atol=1e-12)
+    assert not np.iscomplexobj(oa.trial_orbitals(hr, x))
+
+
+def test_complex_trial_exact_eigenstate_walk():
+    """L = 0 and [U_k, h] = 0 with a complex alpha: every sample is the ground
+    determinant times a phase, so E_L = E0 for every pair while the path
+    signs vary, and the walk keeps the mixed energy at E0."""
+    s = _small_system(8, 3, 3, K=4, seed=21)
+    rng = np.random.default_rng(6)
+    U, _ = _commuting_U(s.h, 4, 3, rng, scale=0.8)
+    ham = oa.prepare(s.h, np.zeros((2, 8, 8)), s.Phi0, U, 3, 3, 0.02, alpha=-1.0j)
+    e0 = 2.0 * np.sum(np.linalg.eigvalsh(s.h)[:3])
+    cfg = oa.OracleConfig(dtau=0.02, n_walkers=4, n_paths=6, seed=29, n_burn=2)
+    st = oa.init(ham, cfg)
+    phases = []
+    for _ in range(3):
+        st, d = oa.step(ham, cfg, st)
+        assert np.allclose(d["measure"]["e_pair"], e0, atol=1e-10)
+        num, den = d["mixed"]
+        assert abs(num / den - e0) < 1e-10
+        phases.append(np.angle(d["measure"]["S"]))
+    assert np.ptp(np.concatenate([p.ravel() for p in phases])) > 0.1   # the samples' phases differ
+
+
+def test_complex_trial_sampled_estimator_matches_quadrature():
+    """K = 1 with a complex alpha: the path-sign-weighted average over paths
+    sampled from |<Phi(x)|phi>| p(x) tends to <Psi_T|H|phi>/<Psi_T|phi> by
+    Gauss-Hermite quadrature."""
+    N, n = 4, 2
+    s = _small_system(N, n, n, G=3, K=1, seed=43)
+    rng = np.random.default_rng(8)
+    ham = oa.prepare(s.h, s.L, s.Phi0, 10.0 * s.U[:1], n, n, 0.01, alpha=-1.0j)
+    phu, phd = _rand_walker(rng, N, n), _rand_walker(rng, N, n)
+    xq, wq = np.polynomial.hermite_e.hermegauss(80)
+    num = den = 0.0
+    for xj, wj in zip(xq, wq):
+        Phi = oa.trial_orbitals(ham, np.array([xj]))
+        ov = np.exp(oa.log_overlap(ham, Phi, phu, phd))
+        e, _ = oa.local_energy_force_bias(ham, Phi, phu, phd)
+        num, den = num + wj * ov * e, den + wj * ov
+    e_exact = num / den
+    W, P = 8, 32
+    cfg = oa.OracleConfig(dtau=0.01, n_walkers=W, n_paths=P, seed=79, n_burn=0)
+    st = oa.init(ham, cfg)
+    st.phi_up[:] = phu
+    st.phi_dn[:] = phd
+    logov = np.array([[oa.log_overlap(ham, st.Phi[w, p], phu, phd) for p in range(P)] for w in range(W)])
+    alive = np.ones(W, dtype=bool)
+    se = ss = 0.0
+    for sweep in range(50):
+        oa.mcmc_sweep(ham, cfg, st, logov, alive, 0, sweep, px.TAG_BURN_PROPOSE, px.TAG_BURN_ACCEPT)
+        if sweep >= 10:
+            m = oa.measure(ham, st)
+            se += np.sum(m["S"] * m["e_pair"])
+            ss += np.sum(m["S"])
+    assert 0.05 < abs(ss) / (40 * W * P) < 0.95
+    assert abs(se / ss - e_exact) < 0.02 * abs(e_exact)
