@@ -104,7 +104,7 @@ SYSTEMS = {
     # system, few walkers): Theta streamed in row slabs through the contraction, the
     # propagation's work arrays in global memory, a ragged last column block (200 = 6 x 32 + 8).
     # Two walkers, as the phaseless constraint kills one of them in the first step here
-    "c4_shape": (ai.CONFIGS["largest_n200"][0], 2, 2, 0.005),
+    "largest_shape": (ai.CONFIGS["largest_n200"][0], 2, 2, 0.005),
     # one spin, Theta slabs with the propagation still in shared memory
     "one_spin_slab": (ai.SystemSpec(150, 45, 0, 300, 20, True, 83), 2, 3, 0.005),
 }
