@@ -141,7 +141,8 @@ typedef struct {
                            n_dn^2) multiply-adds per pair and matrix).  Costs (n_chol + 1) N n_up doubles of
                            workspace per pair (16.4 GB for 512 x 32 pairs of the 50-orbital system) and needs
                            4 warps' shares of Theta (N x (n_up + n_dn) complex) and one matrix (N x n_up) in
-                           220 KB of shared memory (e.g. N <= 64 with 10 + 10 electrons).  0 (default): off */
+                           220 KB of shared memory, and the refresh N^2 + 8 N n_up doubles in 200 KB (with
+                           10 + 10 electrons N <= 124; not 120 orbitals with 24 + 24).  0 (default): off */
 } afqmc_config;
 
 /* Fill *cfg with defaults (combined constraint, prior proposal, FP64, Taylor
