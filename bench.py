@@ -429,26 +429,32 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         # every path's first hidden variable (Sokal window), averaged over paths
         Wt, T = min(64, W), 40
         mixing, start = {}, None
-        for prop in ("prior", "mlp"):
-            c = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, Wt, P, run.dtau, seed, n_burn=20,
-                                walker_offset=rank * Wt, e_shift=28.5, precision="fp16x3", proposal=prop,
-                                mlp_train=False)
-            cx = lib.Context(c, s.h, s.L, s.Phi0, s.U, device=dev)
-            if prop == "mlp":
-                cx.mlp_params(theta)
-            if start is None:
-                start = cx.save_state()
-            else:
-                cx.load_state(start)
-            xs, acc_t = [], []
-            for _ in range(T):
-                cx.step(1)
-                xs.append(cx.state_arrays()["x"][:, :, 0].ravel().copy())
-                acc_t.append(cx.history(1)[0][3] / (Wt * P))
-            cx.close()
-            X = np.array(xs)
-            mixing[prop] = {"acceptance": float(np.mean(acc_t)),
-                            "tau_int_x": float(np.mean([tau_int(X[:, j]) for j in range(X.shape[1])]))}
+        for prop in ("prior", "mlp", "pcn"):
+            try:
+                c = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, Wt, P, run.dtau, seed,
+                                    n_burn=20, walker_offset=rank * Wt, e_shift=28.5, precision="fp16x3",
+                                    proposal=prop, mlp_train=False, pcn_beta=0.5)
+                cx = lib.Context(c, s.h, s.L, s.Phi0, s.U, device=dev)
+                if prop == "mlp":
+                    cx.mlp_params(theta)
+                if start is None:
+                    start = cx.save_state()
+                else:
+                    cx.load_state(start)
+                xs, es, acc_t = [], [], []
+                for _ in range(T):
+                    cx.step(1)
+                    xs.append(cx.state_arrays()["x"][:, :, 0].ravel().copy())
+                    acc_t.append(cx.history(1)[0][3] / (Wt * P))
+                    es.append(cx.energy(walkers=True)["e_walker"].real.copy())
+                cx.close()
+                X, E = np.array(xs), np.array(es)
+                cols = [j for j in range(E.shape[1]) if np.all(np.isfinite(E[:, j]))]
+                mixing[prop] = {"acceptance": float(np.mean(acc_t)),
+                                "tau_int_x": float(np.mean([tau_int(X[:, j]) for j in range(X.shape[1])])),
+                                "tau_int_e_walker": float(np.mean([tau_int(E[:, j]) for j in cols])) if cols else None}
+            except Exception as exc:   # a failed comparison must not cost the variant
+                mixing[prop] = {"error": f"{type(exc).__name__}: {exc}"}
         d = {"precision": "fp16x3", "proposal": "mlp (K->256->256->2K, BF16 GEMMs, trained online every step)",
              "what": f"same workload; {n_train} untimed training steps, then the timed steps (training continues)",
              "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
@@ -458,8 +464,9 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         if hist64 is not None and len(hist64):
             d["acceptance_prior_proposal"] = float(hist64[-steps:, 3].sum() / (min(steps, len(hist64)) * W * P))
         d["mixing"] = dict(mixing, what=f"{Wt} walkers x {P} paths from one common state, {T} steps each, the "
-                                        "trained network frozen (mlp_mix 0.1) vs the prior proposal; tau_int of each "
-                                        "path's x_1 in steps, averaged over paths")
+                                        "trained network frozen (mlp_mix 0.1), the prior proposal and pCN (beta 0.5); "
+                                        "tau_int of each path's x_1 and of each walker's Re E_w, in steps, averaged "
+                                        "over paths and walkers")
         out["learned_proposal"] = d
 
     if only in (None, "batched"):
@@ -563,6 +570,32 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             "ms_per_call": ms, "ms_per_round": ms / rounds, "e_mix_plain": plain, "e_mix_paths": r["e_mix"],
             "ratio_abs_median": float(np.median(np.abs(ratio))) if len(ratio) else None,
             "ratio_abs_range": [float(np.min(np.abs(ratio))), float(np.max(np.abs(ratio)))] if len(ratio) else None}
+
+    if only in (None, "pscaling"):
+        # the cost of a step per walker-path pair against the paths per walker, at the
+        # medium workload's 16384 pairs (W = 16384 / P), FP64 with the cached half-rotation:
+        # the paper's cost model is linear in P at fixed walkers, i.e. flat per pair
+        try:
+            rows = []
+            for Pn in (4, 8, 16, 32, 64):
+                Wn = (W * P) // Pn
+                c = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, Wn, Pn, run.dtau, seed,
+                                    n_burn=20, walker_offset=rank * Wn, e_shift=28.5, rcache=True)
+                cx = lib.Context(c, s.h, s.L, s.Phi0, s.U, device=dev)
+                cx.step(1)
+                ms, clocks, launches = _timed(cx.step, lambda: torch.cuda.synchronize(dev), cx.stream, 2, world,
+                                              local)
+                cx.close()
+                del cx
+                torch.cuda.empty_cache()
+                rows.append({"paths": Pn, "walkers": Wn, "ms_per_step": ms / 2,
+                             "value": Wn * Pn * world * 2 / (ms / 1e3), "sm_mhz": clocks.get("sm_mhz")})
+            out["paths_scaling"] = {
+                "precision": "fp64", "unit": UNIT, "rows": rows,
+                "what": "medium workload system, W x P = 16384 pairs per GPU, rcache on, 1 warm-up and 2 timed "
+                        "steps per P; a flat value means a cost per step linear in P at fixed walkers"}
+        except Exception as exc:   # the measurement is optional; the line must still print
+            out["paths_scaling"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     if only in (None, "largest"):
         # the largest system (N = 200, 40 + 40 electrons, 1000 Cholesky vectors) in FP64 on a
@@ -820,7 +853,8 @@ def main():
                     help="FP64 headline without the cached half-rotated matrices (the walker-side form)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision, learned-proposal and batched measurements")
-    ap.add_argument("--only", choices=("mixed", "learned", "batched", "popctl", "measpaths", "largest", "large_mixed"),
+    ap.add_argument("--only", choices=("mixed", "learned", "batched", "popctl", "measpaths", "pscaling", "largest",
+                                       "large_mixed"),
                     default=None,
                     help="time one variant alone (profiling); skips the FP64 headline's extras")
     args = ap.parse_args()
