@@ -57,7 +57,9 @@ concern the oracle):
       sum_k x_k U_k) Phi0 with a complex alpha (-i sqrt(s) and U_k = L_k for
       the VAFQMC form; Phi0 absorbs exp(-t T) exp(-t0 T0) phi_T), so every
       overlap and Green's function takes Phi^dagger; the real form (alpha = 1)
-      is unchanged.  The multi-slice form is not covered.
+      is unchanged.  Several slices (Eq. (19), Eq. (32)): Phi(x) = exp(alpha S_m)
+      P ... P exp(alpha S_1) Phi0 with S_l = sum_k x_lk U_k and a fixed real
+      P between slices (exp(-t T) for the ansatz), K hidden variables per slice.
 """
 
 from __future__ import annotations
@@ -71,7 +73,7 @@ from . import philox as px
 
 __all__ = ["OracleConfig", "Hamiltonian", "State", "prepare", "trial_orbitals", "log_overlap",
            "green", "local_energy_force_bias", "measure", "init", "step", "reorthonormalise",
-           "propagate_walker", "mcmc_sweep", "comb", "measure_paths", "CONSTRAINTS", "IMPORTANCE"]
+           "propagate_walker", "mcmc_sweep", "comb", "measure_paths", "n_hidden", "CONSTRAINTS", "IMPORTANCE"]
 
 CONSTRAINTS = ("combined", "separate", "half_plane")
 IMPORTANCE = ("hybrid", "local_energy")
@@ -110,6 +112,8 @@ class Hamiltonian:
     T: np.ndarray          # h - 1/2 sum_g L_g L_g
     expT_half: np.ndarray  # exp(-tau T / 2)
     alpha: complex = 1.0   # R19: Phi(x) = exp(alpha sum_k x_k U_k) Phi0 (1: the real form)
+    slices: int = 1        # R19: hidden-variable slices of the trial (1: the one-slice form)
+    slice_prop: np.ndarray = None  # (N, N) real propagator between slices (slices > 1)
 
 
 @dataclasses.dataclass
@@ -141,28 +145,56 @@ def _expm_sym(A: np.ndarray) -> np.ndarray:
     return (V * np.exp(lam)[..., None, :]) @ np.swapaxes(V, -1, -2)
 
 
-def prepare(h, L, Phi0, U, n_up: int, n_dn: int, dtau: float, alpha: complex = 1.0) -> Hamiltonian:
+def prepare(h, L, Phi0, U, n_up: int, n_dn: int, dtau: float, alpha: complex = 1.0, slices: int = 1,
+            slice_prop=None) -> Hamiltonian:
     """One-body operator of the Monte Carlo form, Eq. (3) with reading R1, and
     the exact half-step kinetic propagator exp(-tau T/2) of Eq. (5).  ``alpha``
     is the factor of the hidden-variable exponent (R19): 1 for the real trial
     samples, -i sqrt(s) for the single-slice VAFQMC form of Eq. (30) with
-    U_k = L_k and Phi0 = exp(-t T) exp(-t0 T0) phi_T."""
+    U_k = L_k and Phi0 = exp(-t T) exp(-t0 T0) phi_T.  ``slices`` > 1 gives the
+    multi-slice trial of Eq. (19) and Eq. (32) with ``slice_prop`` (e.g.
+    exp(-t T)) between consecutive slices; each slice has its own K hidden
+    variables."""
+    if slices < 1 or (slices > 1 and slice_prop is None):
+        raise ValueError("slices >= 1, and slice_prop for slices > 1")
     h = np.asarray(h, dtype=np.float64)
     L = np.asarray(L, dtype=np.float64)
     T = h - 0.5 * np.einsum("gij,gjk->ik", L, L)
     return Hamiltonian(h, L, np.asarray(Phi0, dtype=np.float64), np.asarray(U, dtype=np.float64),
-                       n_up, n_dn, T, _expm_sym(-0.5 * dtau * T), complex(alpha) if alpha != 1.0 else 1.0)
+                       n_up, n_dn, T, _expm_sym(-0.5 * dtau * T), complex(alpha) if alpha != 1.0 else 1.0,
+                       int(slices), None if slice_prop is None else np.asarray(slice_prop, dtype=np.float64))
+
+
+def n_hidden(ham: Hamiltonian) -> int:
+    """Hidden variables of one trial sample: K per slice."""
+    return ham.slices * ham.U.shape[0]
 
 
 def trial_orbitals(ham: Hamiltonian, x: np.ndarray) -> np.ndarray:
     """Phi(x) = exp(alpha sum_k x_k U_k) Phi0, the determinant of one
     hidden-variable sample of the trial, Eq. (20)-(21) with one slice (alpha = 1,
     real), or the complex single-slice form of Eq. (30) (R19); x has shape (..., K)."""
+    if ham.slices > 1:   # Phi(x) = e^{alpha S_m} P ... P e^{alpha S_1} Phi0, slice l using x[..., l K:(l+1) K]
+        K = ham.U.shape[0]
+        one = dataclasses.replace(ham, slices=1)
+        Y = None
+        for l in range(ham.slices):
+            x_l = x[..., l * K:(l + 1) * K]
+            if Y is None:
+                Y = trial_orbitals(one, x_l)
+            else:
+                Y = _exp_hidden(ham, x_l) @ (ham.slice_prop @ Y)
+        return Y
+    return _exp_hidden(ham, x) @ ham.Phi0
+
+
+def _exp_hidden(ham: Hamiltonian, x: np.ndarray) -> np.ndarray:
+    """exp(alpha sum_k x_k U_k) (batched over the leading axes of x)."""
     S = np.einsum("...k,kij->...ij", x, ham.U)
     if ham.alpha == 1.0:
-        return _expm_sym(S) @ ham.Phi0
+        return _expm_sym(S)
     lam, V = np.linalg.eigh(S)        # exp(alpha S) = V exp(alpha lam) V^T for real symmetric S
-    return (V * np.exp(ham.alpha * lam)[..., None, :]) @ np.swapaxes(V, -1, -2) @ ham.Phi0
+    return (V * np.exp(ham.alpha * lam)[..., None, :]) @ np.swapaxes(V, -1, -2)
 
 
 # ---------------------------------------------------------------------------
@@ -366,7 +398,7 @@ def init(ham: Hamiltonian, cfg: OracleConfig, walker_index=None) -> State:
     (default 0..W-1) gives the global walker numbers used in the random streams,
     so a subset of a larger population can be rebuilt on its own."""
     W, P = cfg.n_walkers, cfg.n_paths
-    K = ham.U.shape[0]
+    K = n_hidden(ham)
     widx = np.arange(W) if walker_index is None else np.asarray(walker_index)
     W = widx.size
     xw = px.normals(cfg.seed, px.TAG_INIT_WALKER, 0, widx, 0, K)

@@ -708,3 +708,39 @@ def test_complex_trial_sampled_estimator_matches_quadrature():
             ss += np.sum(m["S"])
     assert 0.05 < abs(ss) / (40 * W * P) < 0.95
     assert abs(se / ss - e_exact) < 0.02 * abs(e_exact)
+
+
+@pytest.mark.parametrize("alpha", [1.0, -1j * math.sqrt(0.3)])
+def test_multi_slice_trial_averages_to_the_projected_bra(alpha):
+    """Two slices (Eq. (19), Eq. (32)) with one Cholesky vector as the hidden
+    operator: <Phi(x)| = <phi_T| e^{-tT} e^{a* x_1 L} e^{-tT} e^{a* x_2 L}
+    (a = alpha), so by the Gaussian identity E[e^{a* x L}] = e^{(a*)^2 L^2 / 2}
+    for the many-body one-body operator L, the bra averaged over the hidden
+    variables (2-D Gauss-Hermite) is <phi_T| e^{-tT} e^{(a*)^2 L^2/2} e^{-tT}
+    e^{(a*)^2 L^2/2}, built here from dense Fock-space exponentials."""
+    N, n = 4, 2
+    s = _small_system(N, n, n, G=1, K=1, seed=61)
+    fs = FockSpace(N, n, n)
+    t = 0.2
+    P = sla.expm(-t * s.h)
+    L1 = 0.8 * s.L[:1] / np.max(np.abs(s.L[0]))
+    ham = oa.prepare(s.h, L1, P @ s.Phi0, L1, n, n, 0.01, alpha=alpha, slices=2, slice_prop=P)
+    assert oa.n_hidden(ham) == 2
+    xq, wq = np.polynomial.hermite_e.hermegauss(40)
+    bra = 0.0
+    for x1, w1 in zip(xq, wq):
+        for x2, w2 in zip(xq, wq):
+            Phi = oa.trial_orbitals(ham, np.array([x1, x2]))
+            bra = bra + (w1 * w2 / (2 * np.pi)) * np.conj(fs.determinant(Phi, Phi))
+    Th = fs.one_body(s.h, n, n).toarray()
+    Lh = fs.one_body(L1[0], n, n).toarray()
+    a2 = np.conj(alpha) ** 2
+    E = sla.expm(-t * Th)
+    G = sla.expm(0.5 * a2 * (Lh @ Lh))
+    exact = fs.determinant(s.Phi0, s.Phi0) @ E @ G @ E @ G
+    assert np.max(np.abs(bra - exact)) < 1e-10 * np.max(np.abs(exact))
+    # one slice is the single-slice form unchanged
+    one = oa.prepare(s.h, L1, P @ s.Phi0, L1, n, n, 0.01, alpha=alpha)
+    x = np.array([0.37])
+    assert np.allclose(oa.trial_orbitals(one, x), oa.trial_orbitals(
+        oa.prepare(s.h, L1, P @ s.Phi0, L1, n, n, 0.01, alpha=alpha, slices=1), x), atol=0)
