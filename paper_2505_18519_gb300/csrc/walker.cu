@@ -715,8 +715,8 @@ __global__ void __launch_bounds__(COMB_T) comb_select_kernel(int W, int period, 
         return;
     }
     const double width = total / W, u = s_u;
-    // tooth j -> walker (nondecreasing in j): `cum` is reused for the teeth's walkers
-    // only after every search is done, so they go to `slot` first
+    // tooth j -> walker (nondecreasing in j), kept in `slot` until the ranking below
+    // has read it; `hit` marks the walkers some tooth picked
     for (int j = threadIdx.x; j < W; j += COMB_T) {
         const double pos = ((double)j + u) * width;
         int lo = 0, hi = W;   // first w with cum[w] > pos, W if none
