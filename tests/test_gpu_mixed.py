@@ -50,6 +50,10 @@ SYSTEMS = {
     "n128_fp64_propagation": (ai.SystemSpec(128, 32, 32, 160, 16, True, 84), 2, 3, 0.005),
 }
 
+# Per-case offsets of the Philox run seeds, fixed here so that renaming a case does not move its seed.
+CASE_SEED = {"c0": 2, "ragged": 6, "one_spin": 8, "one_electron_each": 17, "single_path": 11,
+             "n70_two_k_blocks": 16, "medium": 6, "walker_side_wide": 16, "n128_fp64_propagation": 21}
+
 
 def _ctx(spec, W, P, dtau, seed, precision, **kw):
     s = ai.make_system(spec)
@@ -61,9 +65,9 @@ def _ctx(spec, W, P, dtau, seed, precision, **kw):
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_mixed_measure_against_oracle(name, precision):
     spec, W, P, dtau = SYSTEMS[name]
-    s, ctx = _ctx(spec, W, P, dtau, 700 + len(name), precision, n_burn=2)
+    s, ctx = _ctx(spec, W, P, dtau, 700 + CASE_SEED[name], precision, n_burn=2)
     ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, dtau)
-    ocfg = oa.OracleConfig(dtau=dtau, n_walkers=W, n_paths=P, seed=700 + len(name), n_burn=2)
+    ocfg = oa.OracleConfig(dtau=dtau, n_walkers=W, n_paths=P, seed=700 + CASE_SEED[name], n_burn=2)
     ost = oa.init(ham, ocfg)
     ost, _ = oa.step(ham, ocfg, ost)
     ctx.load_state_arrays(dict(step=ost.step, phi_up=ost.phi_up, phi_dn=ost.phi_dn, weight=ost.weight, x=ost.x,
@@ -94,7 +98,7 @@ def test_mixed_step_matches_oracle_given_its_force_bias(name):
     constraint, reorthonormalisation) must then agree to 1e-9, so an error in
     the double-float propagation is not hidden behind the contraction's 1e-6."""
     spec, W, P, dtau = SYSTEMS[name]
-    seed = 640 + len(name)
+    seed = 640 + CASE_SEED[name]
     s, ctx = _ctx(spec, W, P, dtau, seed, "fp16x3", n_burn=2, n_sweeps=2)
     ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, dtau)
     ocfg = oa.OracleConfig(dtau=dtau, n_walkers=W, n_paths=P, seed=seed, n_burn=2, n_sweeps=2)

@@ -73,6 +73,7 @@ def _compare_measure(ctx, ham, ost, tol=E_TOL):
     assert np.max(np.abs(e["e_walker"] - m["e_bar"])) < tol
     assert np.max(np.abs(obs["force_bias"] - m["v_bar"])) < 1e-9
     num, den = oa.mixed_energy(ost.weight, m["e_bar"])
+    assert den > 0, "every walker of this state is dead: the mixed energy is undefined"
     assert abs(e["e_mix"] - num / den) < tol
     return e, m
 
@@ -108,6 +109,18 @@ SYSTEMS = {
     # one spin, Theta slabs with the propagation still in shared memory
     "one_spin_slab": (ai.SystemSpec(150, 45, 0, 300, 20, True, 83), 2, 3, 0.005),
 }
+
+# Per-case offsets of the Philox run seeds, fixed here so that renaming a case does
+# not move its seed.  With two walkers and two burn-in sweeps the first step can
+# kill every walker of the N = 200 case: offset 8 keeps walker 0 alive (checked on
+# the oracle); the tests assert a live walker before comparing mixed energies.
+CASE_SEED = {"c0": 2, "ragged": 6, "one_spin": 8, "one_electron_each": 17, "single_path": 11, "medium": 6,
+             "ragged_walker_side": 18, "one_spin_walker_side": 20, "two_blocks_walker_side": 22,
+             "largest_shape": 8, "one_spin_slab": 13}
+
+
+def _seed(base, name):
+    return base + CASE_SEED[name]
 
 
 # ---------------------------------------------------------------- generator
@@ -165,9 +178,10 @@ def test_philox_matches_an_independent_implementation():
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_measure_matches_oracle(name):
     spec, W, P, dtau = SYSTEMS[name]
-    s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=900 + len(name), n_burn=2)
+    s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=_seed(900, name), n_burn=2)
     ost = oa.init(ham, ocfg)
     ost, _ = oa.step(ham, ocfg, ost)                  # complex walkers
+    assert np.any(ost.weight > 0), "the oracle's first step killed every walker: choose another seed"
     ctx.load_state_arrays(_as_dict(ost))
     _compare_measure(ctx, ham, ost)
     ctx.close()
@@ -176,17 +190,18 @@ def test_measure_matches_oracle(name):
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_one_step_matches_oracle(name):
     spec, W, P, dtau = SYSTEMS[name]
-    s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=500 + len(name), n_burn=2, n_sweeps=2)
+    s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=_seed(500, name), n_burn=2, n_sweeps=2)
     ost = oa.init(ham, ocfg)
     ost, _ = oa.step(ham, ocfg, ost)
+    assert np.any(ost.weight > 0), "the oracle's first step killed every walker: choose another seed"
     ctx.load_state_arrays(_as_dict(ost))
     ctx.step(1)
     ost2, d = oa.step(ham, ocfg, ost)
     g = ctx.state_arrays()
     _compare_state(g, ost2)
-    assert np.any(ost.weight > 0)                     # the step is not vacuous
     rec = ctx.history(1)[0]
     num, den = d["mixed"]
+    assert den > 0
     assert abs(rec[0] / rec[1] - num / den) < E_TOL
     assert rec[3] == d["n_accept"]
     ctx.close()
@@ -263,7 +278,7 @@ def test_half_rotation_cache_matches_oracle(name):
     to refresh match the oracle; the refresh count is every pair once plus the
     pairs whose path moved."""
     spec, W, P, dtau = SYSTEMS[name]
-    s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=700 + len(name), n_burn=2, n_sweeps=2, rcache=True)
+    s, ham, ocfg, ctx = _setup(spec, W, P, dtau, seed=_seed(700, name), n_burn=2, n_sweeps=2, rcache=True)
     assert lib.contract_kernel(ctx.cfg) == "contract_fp64r_kernel"
     ost = oa.init(ham, ocfg)
     ost, _ = oa.step(ham, ocfg, ost)
