@@ -299,9 +299,13 @@ int afqmc_contract_kernel(const afqmc_config* cfg);
  * Returns AFQMC_ERR_ARG, without launching anything, when the batch needs more
  * than the fixed scratch (about n_pairs * (N*(n_up+n_dn)*16 + 32) bytes).
  * The first call on each device resolves the array's device address there
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and caches it for the process; make that first call
+ * before any stream capture.  The address is that of the device's primary
+ * context (the runtime API's): calls from another driver-API context, or after
+ * a cudaDeviceReset that follows the first call, are not supported.
  * Every call shares the array, so calls that overlap on the GPU race.  A
- * singular overlap gives log|ov| = -inf for that pair. */
+ * singular overlap gives log|ov| = -inf for that pair (its energy and force
+ * bias are then those of a zero Theta; the other pairs are unaffected). */
 size_t afqmc_noalloc_scratch_bytes(void);
 afqmc_status afqmc_local_energy_noalloc(int N, int n_up, int n_dn, int n_chol, int64_t n_pairs,
                                         int pairs_per_walker, const double* h, const double* L,

@@ -509,6 +509,9 @@ def step(ham: Hamiltonian, cfg: OracleConfig, st: State, mlp_mu_logv=None):
             raise ValueError(cfg.importance)
 
     # Leapfrog step 2: Metropolis update of the paths at phi' (Sec. III A).
+    if cfg.proposal == "mlp" and ham.slices > 1:
+        # the network's features and output are defined over the K variables of one slice
+        raise ValueError("the learned proposal is defined for one-slice trials only")
     if cfg.proposal == "mlp" and mlp_mu_logv is None:
         from . import mlp as _mlp
         f = _mlp.features(ham.Phi0, ham.U, new.phi_up, new.phi_dn)

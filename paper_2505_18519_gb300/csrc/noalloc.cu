@@ -55,17 +55,23 @@ extern "C" afqmc_status afqmc_local_energy_noalloc(int N, int n_up, int n_dn, in
     if (!contract_fp64_supported(N, n_up, n_dn))
         return noalloc_fail(AFQMC_ERR_ARG, "sizes too large for the FP64 contraction kernel");
     const int nt = n_up + n_dn;
+    // Bound n_pairs before any product with it, so that no size below can wrap: every
+    // pair takes N nt complex Theta entries and two complex log-determinants, and the
+    // layout adds at most 255 bytes of alignment and the status word.
+    const size_t per_pair = (size_t)N * nt * sizeof(double2) + 2 * sizeof(double2);
+    const size_t fixed = 256 + sizeof(int);
+    if (n_pairs > 0 && (uint64_t)n_pairs > (kNoallocScratchBytes - fixed) / per_pair) {
+        snprintf(g_noalloc_err, sizeof g_noalloc_err,
+                 "batch of %lld pairs needs more scratch than the fixed maximum of %zu bytes "
+                 "(about n_pairs * (N * (n_up + n_dn) * 16 + 32)); split the batch",
+                 (long long)n_pairs, kNoallocScratchBytes);
+        return AFQMC_ERR_ARG;
+    }
+    if ((n_pairs + pairs_per_walker - 1) / pairs_per_walker > INT32_MAX)
+        return noalloc_fail(AFQMC_ERR_ARG, "too many walkers in the batch");
     const size_t theta_bytes = (size_t)n_pairs * N * nt * sizeof(double2);
     const size_t logdet_off = (theta_bytes + 255) & ~(size_t)255;
     const size_t status_off = logdet_off + (size_t)n_pairs * 2 * sizeof(double2);
-    const size_t need = status_off + sizeof(int);
-    if (need > kNoallocScratchBytes) {
-        snprintf(g_noalloc_err, sizeof g_noalloc_err,
-                 "batch needs %zu bytes of scratch, above the fixed maximum of %zu bytes "
-                 "(about n_pairs * (N * (n_up + n_dn) * 16 + 32)); split the batch",
-                 need, kNoallocScratchBytes);
-        return AFQMC_ERR_ARG;
-    }
     if (n_pairs == 0) return AFQMC_OK;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -74,7 +80,11 @@ extern "C" afqmc_status afqmc_local_energy_noalloc(int N, int n_up, int n_dn, in
     void* base = nullptr;
     {
         // Set-up, once per device, with that device current: the host-side name
-        // of the array is not a device address, so ask the runtime for it.
+        // of the array is not a device address, so ask the runtime for it.  The
+        // address belongs to the device's primary context (the one the runtime
+        // API uses); it is cached for the life of the process, so neither another
+        // driver-API context made current nor a cudaDeviceReset after this first
+        // call is supported.
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
         if (!g_noalloc_addr[dev]) {
             void* p = nullptr;

@@ -744,3 +744,17 @@ def test_multi_slice_trial_averages_to_the_projected_bra(alpha):
     x = np.array([0.37])
     assert np.allclose(oa.trial_orbitals(one, x), oa.trial_orbitals(
         oa.prepare(s.h, L1, P @ s.Phi0, L1, n, n, 0.01, alpha=alpha, slices=1), x), atol=0)
+
+
+def test_learned_proposal_is_refused_for_multi_slice_trials():
+    """The proposal network's features and output live on the K variables of
+    one slice, so a multi-slice trial with the learned proposal is rejected
+    with a clear error (not a broadcasting failure deep in the sweep)."""
+    N, n = 4, 2
+    s = _small_system(N, n, n, G=2, K=1, seed=62)
+    P = sla.expm(-0.2 * s.h)
+    ham = oa.prepare(s.h, s.L, s.Phi0, s.U, n, n, 0.01, slices=2, slice_prop=P)
+    cfg = oa.OracleConfig(dtau=0.01, n_walkers=2, n_paths=2, seed=5, n_burn=1, proposal="mlp")
+    st = oa.init(ham, cfg)
+    with pytest.raises(ValueError, match="one-slice"):
+        oa.step(ham, cfg, st)
