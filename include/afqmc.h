@@ -52,7 +52,9 @@ typedef enum {
     AFQMC_ERR_CUDA = 2,       /* a CUDA runtime call failed (the message says which) */
     AFQMC_ERR_WORKSPACE = 3,  /* workspace missing, too small, or not 256-byte aligned */
     AFQMC_ERR_NUMERIC = 4,    /* the device flagged a singular overlap or a non-finite value */
-    AFQMC_ERR_STATE = 5       /* a state buffer of the wrong size or shape */
+    AFQMC_ERR_STATE = 5,      /* a state buffer of the wrong size or shape */
+    AFQMC_ERR_TIMEOUT = 6     /* a tensor-core kernel gave up a bounded wait (see wait_polls); its
+                                 results of that measurement are not valid, the context stays usable */
 } afqmc_status;
 
 /* weight update of the hand-off (Sec. III A, Eq. (17), (29)) */
@@ -143,7 +145,20 @@ typedef struct {
                            4 warps' shares of Theta (N x (n_up + n_dn) complex) and one matrix (N x n_up) in
                            220 KB of shared memory, and the refresh N^2 + 8 N n_up doubles in 200 KB (with
                            10 + 10 electrons N <= 124; not 120 orbitals with 24 + 24).  0 (default): off */
+    int64_t wait_polls; /* tensor-core kernels: polls of an mbarrier before a main wait (a copy landing,
+                           MMAs completing, an epilogue freeing a buffer) gives up; the block then sets
+                           bit 4 of the device status word, lets its own copies and MMAs complete (a
+                           fixed bound of 2^22 polls each) and returns, and afqmc_energy / afqmc_stats
+                           return AFQMC_ERR_TIMEOUT.  0 (default): 2^26 polls; at most 2^31 */
+    int tc_form;        /* mixed precision: which tensor-core form runs the contraction.
+                           AFQMC_TC_AUTO (0, default): the walker-side form of N <= 64 with
+                           n_up + n_dn <= 40, else the per-pair form (N <= 128, n_up <= 32; it has the
+                           error-controlled refinement), else the general walker-side form;
+                           AFQMC_TC_PER_PAIR (1); AFQMC_TC_WALKER (2): the general walker-side form
+                           (N <= 256, n_up <= 64; not refined) */
 } afqmc_config;
+
+enum { AFQMC_TC_AUTO = 0, AFQMC_TC_PER_PAIR = 1, AFQMC_TC_WALKER = 2 };
 
 /* Fill *cfg with defaults (combined constraint, prior proposal, FP64, Taylor
  * order 6, one sweep, 20 burn-in sweeps, kill threshold 1e-10, refine_tol 1e-4)
@@ -274,7 +289,9 @@ int64_t afqmc_launch_count(void);
  * n_up + n_dn <= 40), 3 contract_fp64z_kernel (precision FP64, walker-side form
  * Phi_p^T (L_g phi_w) A_p^-1 for blocks of 8 or 16 pairs of a walker: when
  * n_paths >= 8 and the block's operands fit in shared memory, e.g. N <= 64),
- * 4 contract_fp64r_kernel (precision FP64 with rcache = 1: cached R_g,p Theta);
+ * 4 contract_fp64r_kernel (precision FP64 with rcache = 1: cached R_g,p Theta),
+ * 5 contract_tcw_kernel (tensor cores, general walker-side form B_p^T (X_g phi_w),
+ * N <= 256, n_up <= 64: see tc_form);
  * -1 if `cfg` is NULL or no kernel supports its sizes.  Host only. */
 int afqmc_contract_kernel(const afqmc_config* cfg);
 

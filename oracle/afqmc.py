@@ -275,8 +275,10 @@ def measure(ham: Hamiltonian, st: State):
 
 
 def mixed_energy(weight: np.ndarray, e_bar: np.ndarray):
-    """Mixed estimator, Eq. (16), real part (R4); walkers with W = 0 do not enter."""
-    alive = weight > 0
+    """Mixed estimator, Eq. (16), real part (R4); walkers with W = 0 do not enter,
+    nor walkers without a finite estimate (non-finite orbitals, which the kill rule
+    R15 removes in the same step)."""
+    alive = (weight > 0) & np.isfinite(e_bar)
     num = float(np.sum(weight[alive] * e_bar[alive].real))
     den = float(np.sum(weight[alive]))
     return num, den

@@ -22,6 +22,7 @@ CONSTRAINTS = {"combined": 0, "separate": 1, "half_plane": 2}
 PROPOSALS = {"prior": 0, "pcn": 1, "rw": 2, "mlp": 3}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "fp16x3": 2}
 IMPORTANCE = {"hybrid": 0, "local_energy": 1}
+TC_FORMS = {"auto": 0, "per_pair": 1, "walker": 2}
 STATE_MAGIC = 0x4146514D43535431
 
 
@@ -36,6 +37,7 @@ class AfqmcConfig(ctypes.Structure):
         ("rw_step", ctypes.c_double), ("mlp_mix", ctypes.c_double), ("mlp_lr", ctypes.c_double),
         ("mlp_train", ctypes.c_int), ("refine_tol", ctypes.c_double),
         ("importance", ctypes.c_int), ("pop_period", ctypes.c_int), ("rcache", ctypes.c_int),
+        ("wait_polls", ctypes.c_int64), ("tc_form", ctypes.c_int),
     ]
 
 
@@ -141,7 +143,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
                 constraint="combined", proposal="prior", precision="fp64", taylor_order=6, history_capacity=1024,
                 pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10, walker_offset=0, rw_step=0.3, mlp_mix=0.1,
                 mlp_lr=1e-3, mlp_train=False, refine_tol=1e-4, importance="hybrid",
-                pop_period=0, rcache=False) -> AfqmcConfig:
+                pop_period=0, rcache=False, wait_polls=0, tc_form="auto") -> AfqmcConfig:
     lib = load_library()
     c = AfqmcConfig()
     lib.afqmc_config_default(ctypes.byref(c))
@@ -155,6 +157,8 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
     c.refine_tol = refine_tol
     c.importance, c.pop_period = IMPORTANCE[importance], pop_period
     c.rcache = int(bool(rcache))
+    c.wait_polls = int(wait_polls)
+    c.tc_form = TC_FORMS[tc_form]
     return c
 
 
@@ -373,7 +377,7 @@ class Batch:
 
 
 CONTRACT_KERNELS = {0: "contract_fp64_kernel", 1: "contract_tc_kernel", 2: "contract_tcy_kernel",
-                    3: "contract_fp64z_kernel", 4: "contract_fp64r_kernel"}
+                    3: "contract_fp64z_kernel", 4: "contract_fp64r_kernel", 5: "contract_tcw_kernel"}
 
 
 def contract_kernel(cfg: AfqmcConfig) -> str:

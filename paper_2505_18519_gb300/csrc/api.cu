@@ -200,6 +200,7 @@ static const char* check_config(const afqmc_config* c) {
     if (c->pop_period < 0) return "pop_period must be >= 0";
     if (c->pop_period > 0 && c->n_walkers > 65535) return "population control supports at most 65535 walkers";
     if (c->rcache != 0 && c->rcache != 1) return "rcache must be 0 or 1";
+    if (c->wait_polls < 0 || c->wait_polls > (1ll << 31)) return "wait_polls must be in [0, 2^31]";
     if (c->rcache && c->precision != AFQMC_PRECISION_FP64) return "rcache needs precision FP64";
     if (c->rcache && !contract_fp64r_supported(c->N, c->n_up, c->n_dn))
         return "sizes too large for the cached half-rotation form (Theta and one matrix per warp, 4 warps per block)";
@@ -223,6 +224,7 @@ static Dims dims_of(const afqmc_config* c) {
     d.ov_wpb = 0;
     d.tc_tp = 0;
     d.cheb_threads = 0;
+    if (c->wait_polls > 0) d.wait_polls = (uint32_t)c->wait_polls;
     return d;
 }
 
@@ -623,6 +625,17 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
     return AFQMC_OK;
 }
 
+// The device status word as a return value: a wait that timed out outranks the
+// numerical flags (that measurement is not valid at all).
+static afqmc_status status_result(int status) {
+    if (status & STATUS_TIMEOUT)
+        return fail(AFQMC_ERR_TIMEOUT, "device status word 0x%x: a tensor-core kernel gave up a bounded wait "
+                                       "(4 timeout; 1 singular overlap, 2 non-finite value)", status);
+    if (status)
+        return fail(AFQMC_ERR_NUMERIC, "device status word 0x%x (1 singular overlap, 2 non-finite value)", status);
+    return AFQMC_OK;
+}
+
 static afqmc_status read_status(afqmc_ctx* ctx, int* status) {
     CK(cudaMemcpyAsync(status, ctx->ws.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -644,10 +657,7 @@ extern "C" afqmc_status afqmc_energy(afqmc_ctx* ctx, double* e_mix, double* sum_
     if (e_mix) *e_mix = r[1] > 0 ? r[0] / r[1] : 0.0;
     if (sum_w) *sum_w = r[1];
     if (mean_sign) *mean_sign = r[1] > 0 ? r[2] / r[1] : 0.0;
-    if (status)
-        return fail(AFQMC_ERR_NUMERIC, "device status word 0x%x (1 singular overlap, 2 non-finite value, 4 tensor-core wait timed out)",
-                    status);
-    return AFQMC_OK;
+    return status_result(status);
 }
 
 extern "C" afqmc_status afqmc_observables(afqmc_ctx* ctx, double* logov, double* e_local, double* force_bias) {
@@ -713,7 +723,7 @@ extern "C" afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len) {
     double v[12] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3],
                     (double)c[5], (double)c[6], (double)c[7], (double)c[8]};
     for (int i = 0; i < len && i < 12; ++i) out[i] = v[i];
-    return AFQMC_OK;
+    return (status & STATUS_TIMEOUT) ? status_result(status) : AFQMC_OK;
 }
 
 extern "C" afqmc_status afqmc_energy_paths(afqmc_ctx* ctx, int rounds, int sweeps, double* e_mix, double* e_walker,
@@ -753,10 +763,7 @@ extern "C" afqmc_status afqmc_energy_paths(afqmc_ctx* ctx, int rounds, int sweep
     if ((st = read_status(ctx, &status)) != AFQMC_OK) return st;
     const double bb = AB[1].x * AB[1].x + AB[1].y * AB[1].y;
     *e_mix = bb > 0.0 ? (AB[0].x * AB[1].x + AB[0].y * AB[1].y) / bb : 0.0;   // Re(A / B)
-    if (status)
-        return fail(AFQMC_ERR_NUMERIC, "device status word 0x%x (1 singular overlap, 2 non-finite value, 4 tensor-core wait timed out)",
-                    status);
-    return AFQMC_OK;
+    return status_result(status);
 }
 
 static const uint64_t STATE_MAGIC = 0x4146514D43535431ull;

@@ -158,6 +158,7 @@ struct Workspace {
     double* scratchNN;  // 3*N*N for the matrix exponential at init
     void* Lt;           // split-BF16 image of (h, L_g) for the tensor-core contraction
     void* Yimg;         // split images of Y_g = X_g phi_w per walker (walker-side tensor-core form)
+    void* tcw;          // work of the general walker-side tensor-core form (contract_tcw.cu)
     void* ywalk;        // Y_g = X_g phi_w of every walker, and the walkers' orbitals as columns (walker-side FP64 form)
     // composite walkers
     double2* phi;     // W*N*nt (nt = n_up + n_dn)
@@ -229,6 +230,9 @@ struct Dims {
     int ov_wpb;        // warps (matrices) per block of the overlap kernel
     int tc_tp;         // pairs per block of the tensor-core contraction
     int cheb_threads;  // threads per block of the trial-orbital kernel
+    // polls of an mbarrier before a tensor-core kernel's main wait gives up (sets
+    // STATUS_TIMEOUT, drains its copies and MMAs with their own fixed bound, returns)
+    uint32_t wait_polls = 1u << 26;
 };
 
 }  // namespace afq

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     contract_tc_kernel(int N, int nu, int nd, int G, int TP, int GT, int NB1, int NB2, int S, int c1col, int d2col,
                        long long pairs, const uint8_t* __restrict__ image, const int* __restrict__ lexp,
                        const double* __restrict__ Phi, const double2* __restrict__ Theta, double2* __restrict__ vpair,
-                       double2* __restrict__ epair, int* status) {
+                       double2* __restrict__ epair, int* status, uint32_t lim) {
     constexpr int GPT = 128 / NPAD;
     constexpr int NKB = NPAD / 64;
     extern __shared__ uint8_t smraw[];
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     auto refill_upto = [&](int last_consumed) -> bool {
         while (loaded < total && loaded - S <= last_consumed) {
             const int v = loaded - S, st = loaded % S;
-            if (v >= 0 && !tc::mbar_wait(&empty_bar[st], (uint32_t)((v / S) & 1))) return false;
+            if (v >= 0 && !tc::mbar_wait(&empty_bar[st], (uint32_t)((v / S) & 1), lim)) return false;
             tc::mbar_arrive_expect_tx(&full_bar[st], TC_UNIT);
             tc::bulk_g2s(A1 + (size_t)st * TC_UNIT, image + (size_t)loaded * TC_UNIT, TC_UNIT, &full_bar[st]);
             ++loaded;
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int k = 0; k < T && ok; ++k) {
                 for (int kb = 0; kb < NKB && ok; ++kb) {
                     const int u = consumed, st = u % S;
-                    if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) { ok = false; break; }
+                    if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1), lim)) { ok = false; break; }
                     tc::fence_after_sync();
                     const uint32_t sa = tc::smem_u32(A1 + (size_t)st * TC_UNIT);
                     const uint32_t d = taddr + (uint32_t)(k * NB1);
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         __syncwarp();
         {
-            bool ok = fail_flag == 0 && tc::mbar_wait(&done_bar, done_phase);
+            bool ok = fail_flag == 0 && tc::mbar_wait(&done_bar, done_phase, lim);
             done_phase ^= 1;
             if (__syncthreads_or(!ok || fail_flag)) { failed = true; break; }
             tc::fence_after_sync();
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             __syncwarp();
             {
-                bool ok = tc::mbar_wait(&done_bar, done_phase);
+                bool ok = tc::mbar_wait(&done_bar, done_phase, lim);
                 done_phase ^= 1;
                 if (__syncthreads_or(!ok)) { failed = true; break; }
                 tc::fence_after_sync();
@@ -610,7 +610,7 @@ template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tcy_y_kernel(int N, int nu, int nd, int G, int NBY, int S, int parts, const uint8_t* __restrict__ image,
                  const int* __restrict__ lexp, const double2* __restrict__ phi, uint8_t* __restrict__ yimg,
-                 int* __restrict__ yexp, int* status) {
+                 int* __restrict__ yexp, int* status, uint32_t lim) {
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const int nt = nu + nd;
@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     auto refill_upto = [&](int last_consumed) -> bool {
         while (loaded < nloc && loaded - S <= last_consumed) {
             const int v = loaded - S, st = loaded % S;
-            if (v >= 0 && !tc::mbar_wait(&empty_bar[st], (uint32_t)((v / S) & 1))) return false;
+            if (v >= 0 && !tc::mbar_wait(&empty_bar[st], (uint32_t)((v / S) & 1), lim)) return false;
             tc::mbar_arrive_expect_tx(&full_bar[st], TC_UNIT);
             tc::bulk_g2s(XR + (size_t)st * TC_UNIT, image + (size_t)(u0 + loaded) * TC_UNIT, TC_UNIT, &full_bar[st]);
             ++loaded;
@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // GEMM-Y of this block's unit u (local index; thread 0): D_Y = X(unit) PW^T
     auto issue_Y = [&](int u) -> bool {
         const int st = u % S;
-        if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) return false;
+        if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1), lim)) return false;
         tc::fence_after_sync();
         const uint32_t sa = tc::smem_u32(XR + (size_t)st * TC_UNIT);
 #pragma unroll
@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int u = u0 + v;   // unit of the walker's image
         __syncwarp();
         {
-            bool ok = fail_flag == 0 && tc::mbar_wait(&ybar, y_ph);
+            bool ok = fail_flag == 0 && tc::mbar_wait(&ybar, y_ph, lim);
             y_ph ^= 1;
             if (__syncthreads_or(!ok || fail_flag)) { failed = true; break; }
             tc::fence_after_sync();
@@ -861,7 +861,7 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
     contract_tcy_kernel(int N, int nu, int nd, int G, int P, int PG, int NBY, int S, int nbuf,
                         const uint8_t* __restrict__ yimg, const int* __restrict__ yexp,
                         const double2* __restrict__ Bm, double2* __restrict__ vpair, double2* __restrict__ epair,
-                        int* status) {
+                        int* status, uint32_t lim) {
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const int nt = nu + nd;
@@ -957,14 +957,14 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
                 // unit u not loaded yet (a one-stage ring): its stage frees when GEMM-M of unit u - S completes
                 while (loaded <= u) {
                     const int v = loaded - S, sv = loaded % S;
-                    if (v >= 0 && !tc::mbar_wait(&empty_bar[sv], (uint32_t)((v / S) & 1))) { failed = true; break; }
+                    if (v >= 0 && !tc::mbar_wait(&empty_bar[sv], (uint32_t)((v / S) & 1), lim)) { failed = true; break; }
                     load(sv, loaded);
                     ++loaded;
                 }
                 if (failed) break;
                 // D_M buffer b is free once the epilogue of unit u - nbuf has read it
-                if (u >= nbuf && !tc::mbar_wait(&mempty[b], (uint32_t)((u / nbuf - 1) & 1))) { failed = true; break; }
-                if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1))) { failed = true; break; }
+                if (u >= nbuf && !tc::mbar_wait(&mempty[b], (uint32_t)((u / nbuf - 1) & 1), lim)) { failed = true; break; }
+                if (!tc::mbar_wait(&full_bar[st], (uint32_t)((u / S) & 1), lim)) { failed = true; break; }
                 tc::fence_after_sync();
                 ++consumed;
                 // both matrices of the unit in one operand of 2 NBY rows; D columns of buffer b:
@@ -996,7 +996,7 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
                 // refill the stages whose MMAs (units up to u - 1) have completed
                 while (loaded < n_units && loaded - S <= u - 1) {
                     const int v = loaded - S, sv = loaded % S;
-                    if (!tc::mbar_wait(&empty_bar[sv], (uint32_t)((v / S) & 1))) { failed = true; break; }
+                    if (!tc::mbar_wait(&empty_bar[sv], (uint32_t)((v / S) & 1), lim)) { failed = true; break; }
                     load(sv, loaded);
                     ++loaded;
                 }
@@ -1018,7 +1018,7 @@ __global__ void __launch_bounds__(TCY_THREADS, 1)
         uint32_t m_ph0 = 0, m_ph1 = 0;
         for (int u = 0; u < n_units; ++u) {
             const int b = u % nbuf;
-            const bool ok = tc::mbar_wait(&mfull[b], b ? m_ph1 : m_ph0);
+            const bool ok = tc::mbar_wait(&mfull[b], b ? m_ph1 : m_ph0, lim);
             if (b) m_ph1 ^= 1; else m_ph0 ^= 1;
             if (tc::named_sync_or<TC_THREADS>(!ok)) { failed = true; break; }
             tc::fence_after_sync();
@@ -1188,14 +1188,15 @@ static cudaError_t launch_tcy(cudaStream_t st, const Dims& d, const TcyShape& s,
     const int parts = n_units >= 2 ? 2 : 1;
     tcy_y_kernel<F16><<<(unsigned)(W * parts), TC_THREADS, s.smem_y, st>>>(d.N, d.nu, d.nd, d.G, s.NBY, s.SY, parts,
                                                                            (const uint8_t*)image, lexp, phi, yimg,
-                                                                           yexp, status);
+                                                                           yexp, status, d.wait_polls);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = raise_smem_limit((const void*)contract_tcy_kernel<F16>, s.smem);
     if (e != cudaSuccess) return e;
     const long long blocks = W * ((d.P + s.PG - 1) / s.PG);
     contract_tcy_kernel<F16><<<(unsigned)blocks, TCY_THREADS, s.smem, st>>>(d.N, d.nu, d.nd, d.G, d.P, s.PG, s.NBY, s.S,
-                                                                         s.nbuf, yimg, yexp, Bm, vpair, epair, status);
+                                                                         s.nbuf, yimg, yexp, Bm, vpair, epair, status,
+                                                                         d.wait_polls);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1288,7 +1289,7 @@ static cudaError_t launch_tc(cudaStream_t st, const Dims& d, const TcShape& s, c
     long long blocks = (d.pairs + s.TP - 1) / s.TP;
     contract_tc_kernel<NPAD, F16><<<(unsigned)blocks, TC_THREADS, s.smem, st>>>(
         d.N, d.nu, d.nd, d.G, s.TP, s.GT, s.NB1, s.NB2, s.S, s.c1col, s.d2col, d.pairs, (const uint8_t*)image, lexp, Phi,
-        Theta, vpair, epair, status); count_launches(1);
+        Theta, vpair, epair, status, d.wait_polls); count_launches(1);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,913 @@
+// Walker-side tensor-core contraction for any size the FP64 path supports
+// (N <= 256, n_up <= 64): the fused force-bias / local-energy contraction of
+// Eq. (15), (16), (27) as one batched GEMM per walker and spin.
+//
+// With B_p = Phi_p A_p^-T (written by the overlap kernel in place of Theta) and
+// Y_g = X_g phi_w (X_0 = h, X_g = L_g; it depends on the walker only),
+//     Z_{p,g} = B_p^T Y_g = A_p^-1 (Phi_p^T X_g phi_w)
+// is similar to M_{p,g} = Phi_p^T X_g Theta_p (Theta_p = phi_w A_p^-1), so it has
+// the traces the local energy needs: v_g = sum_s Tr Z, and sum_s Tr Z_s^2.
+// For one walker and spin (n = n_s electrons) the products of all P paths and
+// all G + 1 matrices are one real GEMM with the complex K dimension unrolled:
+//   D[(p, a), (g, b, ri)] = sum_k A[(p, a), k] Bop[(g, b, ri), k],  k < 2 N16,
+//   A row (p, a)      = [Re B_p[:, a] | Im B_p[:, a]],
+//   Bop row (g, b, re) = [Re Y_g[:, b] | -Im Y_g[:, b]],  row (g, b, im) = [Im Y_g[:, b] | Re Y_g[:, b]],
+// so D[(p, a), (g, b, re/im)] = Re/Im Z_{p,g}[a, b].
+//
+// Kernels (all tcgen05.mma.cta_group::1.kind::f16, 128-row tiles, K-major operands
+// in the 128-byte swizzled layout, accumulators in tensor memory):
+//   tcw_x_image_kernel  (init) the split image of every X_g, rows j, K = i;
+//   tcw_y_kernel        per (walker, spin, block of matrices): GEMM-Y
+//                       D_Y[(b, ri), j] = sum_i PW[(b, ri), i] X_g[j, i] (= Re/Im Y_g[j, b])
+//                       and its epilogue, which writes the Bop image of Y_g
+//                       (per-column power-of-two scale, split) to global memory;
+//   tcw_a_kernel        per (walker, spin, tile of pairs): the A image of B_p;
+//   contract_tcw_kernel per (walker, spin, tile of pairs): GEMM-Z over every block
+//                       of matrices, a producer warp streaming the Bop image
+//                       through a ring of bulk copies, an MMA warp filling two
+//                       tensor-memory buffers, four epilogue warps forming Tr Z and
+//                       Tr Z^2 through a shared-memory transpose;
+//   tcw_finish_kernel   per pair: v_g = sum over spins, E_L.
+//
+// Split 16-bit arithmetic (fp16x3): every operand row is scaled by a power of two
+// and split into an integer FP16 part hi (A rows into [64, 128), Bop and GEMM-Y
+// operand rows into [128, 256)) and an FP16 remainder lo; hi*hi products go to
+// their own accumulator, where every partial sum is an integer of magnitude at
+// most 2^24 (|hi_A hi_B| <= 2^15, K <= 512; GEMM-Y: 2^16, K <= 256) and therefore
+// exact in FP32 whatever the tensor cores' rounding, and hi*lo + lo*hi + lo*lo go
+// to a second accumulator about 2^-8 as large.  bf16x3: hi = bf16(x),
+// lo = bf16(x - hi), hi*hi + hi*lo + lo*hi in one accumulator.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "tcgen05.cuh"
+
+namespace afq {
+
+namespace {
+
+constexpr int TCW_THREADS = 192;        // warp 0 producer, warp 1 MMA issue, warps 2-5 epilogue
+constexpr int TCW_EPI = 128;            // epilogue threads (one per tensor-memory lane)
+constexpr int TCW_MAXSTAGES = 4;
+constexpr size_t TCW_SMEM_MAX = 216 * 1024;   // dynamic; static use is about 7 KB of 227 KB
+constexpr uint32_t TCW_CHUNK_A = 32768; // one K chunk of a 128-row operand: 16 KB hi, 16 KB lo
+
+__host__ __device__ __forceinline__ int tcw_round16(int x) { return (x + 15) / 16 * 16; }
+
+// Byte offset of the 16-byte unit u (K elements 8u .. 8u + 7) of row r in a
+// K-major 128-byte swizzled region (rows of 128 bytes, groups of 8 rows 1 KB apart).
+__host__ __device__ __forceinline__ uint32_t swz16(int r, int u) {
+    return (uint32_t)(r >> 3) * 1024u + (uint32_t)(r & 7) * 128u + (uint32_t)((u ^ (r & 7)) << 4);
+}
+
+// 2^e as a float, for |e| <= 126.
+__device__ __forceinline__ float p2f(int e) {
+    e = max(-126, min(126, e));
+    return __int_as_float((e + 127) << 23);
+}
+
+// Exponent e with m 2^e in [2^t, 2^(t+1)) (0 for m = 0 or not finite).
+__device__ __forceinline__ int exp_into(float m, int t) {
+    if (!(m > 0.f) || !isfinite(m)) return 0;
+    return max(-100, min(100, t - ilogbf(m)));
+}
+
+// x = hi + lo as two 16-bit patterns (FP16: hi integer; BF16: hi = bf16(x)).
+template <bool F16>
+__device__ __forceinline__ void split2(float x, uint16_t& hi, uint16_t& lo) {
+    if (F16) {
+        const float r = rintf(x);
+        const __half h = __float2half_rn(r), l = __float2half_rn(x - r);
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(l);
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(l);
+    }
+}
+
+__device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
+
+// Bounded wait that records a timeout (the caller breaks out of its loop).
+__device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, uint32_t lim, volatile int* fail) {
+    if (*fail) return false;
+    if (tc::mbar_wait(bar, parity, lim)) return true;
+    *fail = 1;
+    return false;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- X image (init)
+// Ximg[((g KCX + c) 2 + h) RX]: matrix g = (h, L_1, ...), K chunk c (i in
+// [64c, 64c + 64)), hi (h = 0) or lo part, N16 rows j x 128 bytes, values
+// X_g[j, i] 2^lexp[g] (zero outside N x N).
+template <bool F16>
+__global__ void tcw_x_image_kernel(int N, int N16, int KCX, int G1, const double* __restrict__ h,
+                                   const double* __restrict__ L, const int* __restrict__ lexp, uint8_t* __restrict__ out) {
+    const long long units = (long long)G1 * KCX * N16 * 8;   // (g, c, j, u)
+    const size_t RX = (size_t)N16 * 128;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < units;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(e % 8);
+        const int j = (int)((e / 8) % N16);
+        const long long gc = e / (8 * (long long)N16);
+        const int c = (int)(gc % KCX);
+        const int g = (int)(gc / KCX);
+        const double* X = g == 0 ? h : L + (long long)(g - 1) * N * N;
+        const int le = lexp[g];
+        uint16_t hi[8], lo[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = c * 64 + u * 8 + q;
+            const float x = (j < N && i < N) ? (float)ldexp(X[(long long)j * N + i], le) : 0.f;
+            split2<F16>(x, hi[q], lo[q]);
+        }
+        uint8_t* base = out + ((size_t)g * KCX + c) * 2 * RX + swz16(j, u);
+        *reinterpret_cast<uint4*>(base) = make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]),
+                                                     pack2(hi[6], hi[7]));
+        *reinterpret_cast<uint4*>(base + RX) = make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]), pack2(lo[4], lo[5]),
+                                                          pack2(lo[6], lo[7]));
+    }
+}
+
+// ---------------------------------------------------------------- GEMM-Y and the Bop image of Y_g
+// Block: walker w0 + blockIdx.x / n_gblk, matrices [gb GPB, (gb + 1) GPB) of one spin
+// (columns col0 .. col0 + n - 1 of phi).  Shared memory: PW (KCX chunks of 128
+// rows: row (b, ri) = Re/Im phi[:, col0 + b] times 2^sPW[b], K = i), then a ring
+// of S stages, each one half (hi or lo) of a K chunk of X_g (N16 rows).
+// Tensor memory: D_Y (N16 columns) and, FP16, its correction (N16 more).
+// Output: the Bop rows (g, b, ri) of matrix g in N-tile t = g / GB at row
+// (g % GB) 2n + 2b + ri; K chunk c of a tile is NT rows hi then NT rows lo; and
+// yexp[(wl G1 + g) n + b], the exponent of column b (image = Y 2^yexp).
+template <bool F16>
+__global__ void __launch_bounds__(TCW_THREADS, 1)
+    tcw_y_kernel(int N, int nt, int col0, int n, int G1, int N16, int KCX, int S, int GPB, int n_gblk, long long w0,
+                 const double2* __restrict__ phi, const uint8_t* __restrict__ Ximg, const int* __restrict__ lexp,
+                 int NT, int GB, int KC, int NTILES, uint8_t* __restrict__ Yimg, int* __restrict__ yexp, int* status,
+                 uint32_t lim) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    const uint32_t RX = (uint32_t)N16 * 128u;
+    uint8_t* PW = sm;                                         // KCX x 32 KB
+    uint8_t* ring = PW + (size_t)KCX * TCW_CHUNK_A;           // S x RX
+    __shared__ uint64_t full_bar[TCW_MAXSTAGES], empty_bar[TCW_MAXSTAGES], dfull, dempty, drain_bar;
+    __shared__ uint32_t tslot;
+    __shared__ volatile int fail;
+    __shared__ int sPW[64];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wl = blockIdx.x / n_gblk;
+    const int gb = blockIdx.x % n_gblk;
+    const int g0 = gb * GPB, g1 = min(G1, g0 + GPB);
+    const int ng = max(0, g1 - g0);
+    const int n_units = ng * KCX * 2;
+    const double2* ph = phi + (w0 + wl) * (long long)N * nt + col0;
+    const uint32_t tcols = F16 ? 2u * (uint32_t)N16 : (uint32_t)N16;
+    const uint32_t talloc = tcols <= 32 ? 32 : (tcols <= 64 ? 64 : (tcols <= 128 ? 128 : (tcols <= 256 ? 256 : 512)));
+
+    if (warp == 1) {
+        tc::tmem_alloc(&tslot, talloc);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            tc::mbar_init(&full_bar[q], 1);
+            tc::mbar_init(&empty_bar[q], 1);
+        }
+        tc::mbar_init(&dfull, 1);
+        tc::mbar_init(&dempty, 1);
+        tc::mbar_init(&drain_bar, 1);
+        tc::mbar_fence_init();
+        fail = 0;
+    }
+    // column exponents of PW: the larger of |Re|, |Im| of phi[:, b] into [128, 256)
+    for (int b = warp; b < n; b += TCW_THREADS / 32) {
+        float m = 0.f;
+        for (int i = lane; i < N; i += 32) {
+            const double2 t = ph[(long long)i * nt + b];
+            m = fmaxf(m, fmaxf((float)fabs(t.x), (float)fabs(t.y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) sPW[b] = F16 ? exp_into(m, 7) : 0;
+    }
+    __syncthreads();
+    // PW rows (b, ri), K = i, 16-byte units; rows >= 2n are zero
+    for (int e = tid; e < KCX * 128 * 8; e += TCW_THREADS) {
+        const int u = e % 8, r = (e / 8) % 128, c = e / (8 * 128);
+        const int b = r >> 1, ri = r & 1;
+        uint16_t hi[8], lo[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = c * 64 + u * 8 + q;
+            float x = 0.f;
+            if (r < 2 * n && i < N) {
+                const double2 t = ph[(long long)i * nt + b];
+                x = (float)(ri ? t.y : t.x) * p2f(sPW[b]);
+            }
+            split2<F16>(x, hi[q], lo[q]);
+        }
+        uint8_t* base = PW + (size_t)c * TCW_CHUNK_A + swz16(r, u);
+        *reinterpret_cast<uint4*>(base) = make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]),
+                                                     pack2(hi[6], hi[7]));
+        *reinterpret_cast<uint4*>(base + 16384) = make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]),
+                                                             pack2(lo[4], lo[5]), pack2(lo[6], lo[7]));
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tslot;
+    bool failed = false;
+
+    if (warp == 0) {
+        // ---- producer: unit v = (matrix g0 + v / (2 KCX), chunk (v / 2) % KCX, half v % 2)
+        if (lane == 0) {
+            int issued = 0;
+            for (int v = 0; v < n_units; ++v) {
+                const int st = v % S;
+                if (v >= S && !wait_or_fail(&empty_bar[st], (uint32_t)(((v / S) - 1) & 1), lim, &fail)) { failed = true; break; }
+                const int g = g0 + v / (2 * KCX), c = (v / 2) % KCX, hh = v % 2;
+                tc::mbar_arrive_expect_tx(&full_bar[st], RX);
+                tc::bulk_g2s(ring + (size_t)st * RX, Ximg + (((size_t)g * KCX + c) * 2 + hh) * RX, RX, &full_bar[st]);
+                ++issued;
+            }
+            // every issued copy lands before the block leaves
+            for (int v = max(0, issued - S); v < issued; ++v)
+                tc::mbar_wait(&full_bar[v % S], (uint32_t)((v / S) & 1), 1u << 22);
+            if (failed) atomicOr(status, STATUS_TIMEOUT);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- MMA issue (one thread): D_Y = PW X_g^T
+        if (lane == 0) {
+            const uint32_t idesc = F16 ? tc::idesc_f16_f32(128, N16) : tc::idesc_bf16_f32(128, N16);
+            const uint32_t dh = taddr, dl = taddr + (F16 ? (uint32_t)N16 : 0u);
+            int v = 0;
+            for (int gi = 0; gi < ng && !failed; ++gi) {
+                if (gi > 0 && !wait_or_fail(&dempty, (uint32_t)((gi - 1) & 1), lim, &fail)) { failed = true; break; }
+                tc::fence_after_sync();
+                for (int c = 0; c < KCX && !failed; ++c) {
+                    const int ks = min(4, (N16 - 64 * c) / 16);
+                    for (int hh = 0; hh < 2; ++hh, ++v) {
+                        const int st = v % S;
+                        if (!wait_or_fail(&full_bar[st], (uint32_t)((v / S) & 1), lim, &fail)) { failed = true; break; }
+                        tc::fence_after_sync();
+                        const uint32_t pa = tc::smem_u32(PW + (size_t)c * TCW_CHUNK_A);
+                        const uint32_t pb = tc::smem_u32(ring + (size_t)st * RX);
+                        for (int s = 0; s < ks; ++s) {
+                            const uint64_t ah = tc::desc_sw128(pa + s * 32), al = tc::desc_sw128(pa + 16384 + s * 32);
+                            const uint64_t bx = tc::desc_sw128(pb + s * 32);
+                            const uint32_t first = (c == 0 && s == 0) ? 0u : 1u;
+                            if (hh == 0) {
+                                tc::mma_f16(dh, ah, bx, idesc, first);
+                                tc::mma_f16(dl, al, bx, idesc, F16 ? first : 1u);
+                            } else {
+                                tc::mma_f16(dl, ah, bx, idesc, 1u);
+                                if (F16) tc::mma_f16(dl, al, bx, idesc, 1u);
+                            }
+                        }
+                        tc::mma_commit(&empty_bar[st]);
+                    }
+                }
+                if (!failed) tc::mma_commit(&dfull);
+            }
+            if (failed) atomicOr(status, STATUS_TIMEOUT);
+            tc::mma_commit(&drain_bar);                 // every issued MMA completes before the block leaves
+            tc::mbar_wait(&drain_bar, 0, 1u << 22);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue (warps 2-5): lane r = (b, ri) of D_Y holds Re/Im Y_g[:, b]
+        const int quarter = warp & 3;
+        const int r = 32 * quarter + lane;
+        const uint32_t lb = (uint32_t)(32 * quarter) << 16;
+        const int b = r >> 1, ri = r & 1;
+        const bool row_ok = r < 2 * n;
+        const int e_pw = row_ok ? sPW[b] : 0;
+        for (int gi = 0; gi < ng; ++gi) {
+            const int g = g0 + gi;
+            const bool ok = wait_or_fail(&dfull, (uint32_t)(gi & 1), lim, &fail);
+            if (tc::named_sync_or<TCW_EPI>(!ok)) { failed = true; break; }
+            tc::fence_after_sync();
+            // pass 1: the largest |Y| of column b (its Re and Im lanes)
+            float mx = 0.f;
+            for (int j0 = 0; j0 < N16; j0 += 16) {
+                float v[16];
+                tc::tmem_ld16(taddr + lb + (uint32_t)j0, v);
+                if (F16) {
+                    float w[16];
+                    tc::tmem_ld16(taddr + lb + (uint32_t)(N16 + j0), w);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] += w[q];
+                } else {
+                    tc::tmem_ld_wait();
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) mx = fmaxf(mx, fabsf(v[q]));
+            }
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+            const int et = F16 ? exp_into(mx, 7) : 0;   // image = D_Y 2^et
+            const int t = g / GB, gl = g % GB;
+            uint8_t* tile = Yimg + ((size_t)wl * NTILES + t) * KC * (size_t)NT * 256;
+            const int R1 = gl * 2 * n + 2 * b + ri;         // k = j: Re Y (re row), Im Y (im row)
+            const int R2 = gl * 2 * n + 2 * b + (1 - ri);   // k = N16 + j: Re Y (im row), -Im Y (re row)
+            const uint16_t neg = ri ? 0x8000u : 0u;
+            const float mul = p2f(et);
+            // pass 2: scale, split, and write 8 K elements (16 bytes) at a time
+            for (int j0 = 0; j0 < N16; j0 += 16) {
+                float v[16];
+                tc::tmem_ld16(taddr + lb + (uint32_t)j0, v);
+                if (F16) {
+                    float w[16];
+                    tc::tmem_ld16(taddr + lb + (uint32_t)(N16 + j0), w);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] += w[q];
+                } else {
+                    tc::tmem_ld_wait();
+                }
+                if (row_ok) {
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        uint16_t hi[8], lo[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) split2<F16>(v[8 * half + q] * mul, hi[q], lo[q]);
+                        const int j = j0 + 8 * half;
+                        const int k1 = j, k2 = N16 + j;
+                        const uint4 H1 = make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]),
+                                                    pack2(hi[6], hi[7]));
+                        const uint4 L1 = make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]), pack2(lo[4], lo[5]),
+                                                    pack2(lo[6], lo[7]));
+                        const uint32_t nn = (uint32_t)neg | ((uint32_t)neg << 16);
+                        const uint4 H2 = make_uint4(H1.x ^ nn, H1.y ^ nn, H1.z ^ nn, H1.w ^ nn);
+                        const uint4 L2 = make_uint4(L1.x ^ nn, L1.y ^ nn, L1.z ^ nn, L1.w ^ nn);
+                        uint8_t* c1 = tile + (size_t)(k1 >> 6) * NT * 256;
+                        uint8_t* c2 = tile + (size_t)(k2 >> 6) * NT * 256;
+                        *reinterpret_cast<uint4*>(c1 + swz16(R1, (k1 & 63) >> 3)) = H1;
+                        *reinterpret_cast<uint4*>(c1 + (size_t)NT * 128 + swz16(R1, (k1 & 63) >> 3)) = L1;
+                        *reinterpret_cast<uint4*>(c2 + swz16(R2, (k2 & 63) >> 3)) = H2;
+                        *reinterpret_cast<uint4*>(c2 + (size_t)NT * 128 + swz16(R2, (k2 & 63) >> 3)) = L2;
+                    }
+                }
+            }
+            if (row_ok && ri == 0) yexp[((size_t)wl * G1 + g) * n + b] = et + e_pw + lexp[g];
+            // D_Y has been read: the next matrix's MMAs may overwrite it
+            tc::fence_before_sync();
+            tc::named_sync<TCW_EPI>();
+            if (r == 0) tc::mbar_arrive(&dempty);
+        }
+        if (failed && r == 0) atomicOr(status, STATUS_TIMEOUT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(taddr, talloc);
+}
+
+// ---------------------------------------------------------------- A image of B_p
+// Block: walker w0 + blockIdx.x / MT, tile m = blockIdx.x % MT of its pairs
+// (pairs m PB .. m PB + PB - 1 of the walker), one spin.  Row r = p_l n + a:
+// [Re B_p[:, col0 + a] | Im B_p[:, col0 + a]] times 2^aexp[r] (largest entry in
+// [64, 128)), split; KC chunks of 32 KB (16 KB hi, 16 KB lo); rows past the
+// tile's pairs are zero.
+template <bool F16>
+__global__ void __launch_bounds__(256) tcw_a_kernel(int N, int nt, int col0, int n, int P, int PB, int MT, int N16,
+                                                    int KC, long long w0, const double2* __restrict__ Bm,
+                                                    uint8_t* __restrict__ Aimg, int* __restrict__ aexp) {
+    __shared__ int sA[128];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long wl = blockIdx.x / MT;
+    const int m = blockIdx.x % MT;
+    const int np = min(PB, P - m * PB);
+    const long long pair0 = (w0 + wl) * P + (long long)m * PB;
+    for (int r = warp; r < 128; r += 8) {
+        const int p = r / n, a = r % n;
+        float mx = 0.f;
+        if (r < np * n)
+            for (int i = lane; i < N; i += 32) {
+                const double2 t = Bm[(pair0 + p) * (long long)N * nt + (long long)i * nt + col0 + a];
+                mx = fmaxf(mx, fmaxf((float)fabs(t.x), (float)fabs(t.y)));
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) sA[r] = F16 ? exp_into(mx, 6) : 0;
+    }
+    __syncthreads();
+    uint8_t* out = Aimg + (size_t)blockIdx.x * KC * TCW_CHUNK_A;
+    for (int e = tid; e < KC * 128 * 8; e += 256) {
+        const int u = e % 8, r = (e / 8) % 128, c = e / (8 * 128);
+        const int p = r / n, a = r % n;
+        uint16_t hi[8], lo[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = c * 64 + u * 8 + q;
+            const int i = k < N16 ? k : k - N16;
+            float x = 0.f;
+            if (r < np * n && i < N && k < 2 * N16) {
+                const double2 t = Bm[(pair0 + p) * (long long)N * nt + (long long)i * nt + col0 + a];
+                x = (float)(k < N16 ? t.x : t.y) * p2f(sA[r]);
+            }
+            split2<F16>(x, hi[q], lo[q]);
+        }
+        uint8_t* base = out + (size_t)c * TCW_CHUNK_A + swz16(r, u);
+        *reinterpret_cast<uint4*>(base) = make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]),
+                                                     pack2(hi[6], hi[7]));
+        *reinterpret_cast<uint4*>(base + 16384) = make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]),
+                                                             pack2(lo[4], lo[5]), pack2(lo[6], lo[7]));
+    }
+    if (tid < 128) aexp[(size_t)blockIdx.x * 128 + tid] = sA[tid];
+}
+
+// ---------------------------------------------------------------- GEMM-Z and the traces
+// Block: walker w0 + blockIdx.x / MT, pair tile m, one spin with n electrons.
+// Shared memory: with a_res the tile's A image (KC x 32 KB) stays resident and the
+// ring streams only the Bop chunks (NT rows hi + lo); otherwise every ring stage
+// holds an A chunk (32 KB) and a Bop chunk.  Then Ms, the staging of one matrix's
+// Z blocks (128 rows x (n + 1) complex floats) for the transpose.
+// Tensor memory, buffer b of two: D (NT columns) and, FP16, its correction (NT).
+// Outputs: vpart[pair G1 + g] = Tr Z_{p,g} (float2; g = 0 is the one-body term),
+// exsum[pair] = sum_{g >= 1} Tr Z_{p,g}^2 (FP64 accumulation over the matrices).
+template <bool F16>
+__global__ void __launch_bounds__(TCW_THREADS, 1)
+    contract_tcw_kernel(int n, int G1, int KZ, int KC, int NT, int GB, int NTILES, int P, int PB, int MT, int S,
+                        int a_res, long long w0, const uint8_t* __restrict__ Aimg, const int* __restrict__ aexp,
+                        const uint8_t* __restrict__ Yimg, const int* __restrict__ yexp, float2* __restrict__ vpart,
+                        double2* __restrict__ exsum, int* status, uint32_t lim) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    const uint32_t bbytes = (uint32_t)NT * 256u;                      // one Bop chunk (hi + lo)
+    const uint32_t stage_bytes = (a_res ? 0u : TCW_CHUNK_A) + bbytes;
+    uint8_t* Ares = sm;
+    uint8_t* ring = sm + (a_res ? (size_t)KC * TCW_CHUNK_A : 0);
+    float2* Ms = reinterpret_cast<float2*>(ring + (size_t)S * stage_bytes);
+    const int ld = n + 1;                                             // row stride of Ms (complex)
+    __shared__ uint64_t full_bar[TCW_MAXSTAGES], empty_bar[TCW_MAXSTAGES], dfull[2], dempty[2], a_bar, drain_bar;
+    __shared__ uint32_t tslot;
+    __shared__ volatile int fail;
+    __shared__ float2 red_tr[2][128], red_ex[2][128];
+    __shared__ double2 exacc[128];
+    __shared__ int sA[128];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long wl = blockIdx.x / MT;
+    const int m = blockIdx.x % MT;
+    const int np = min(PB, P - m * PB);
+    const long long pair0 = (w0 + wl) * P + (long long)m * PB;
+    const uint8_t* Atile = Aimg + (size_t)blockIdx.x * KC * TCW_CHUNK_A;
+    const uint8_t* Ywalk = Yimg + (size_t)wl * NTILES * KC * bbytes;
+    const int* yex = yexp + (size_t)wl * G1 * n;
+    const uint32_t dcols = (F16 ? 2u : 1u) * (uint32_t)NT;              // one buffer
+    const uint32_t tneed = 2u * dcols;
+    const uint32_t talloc = tneed <= 32 ? 32 : (tneed <= 64 ? 64 : (tneed <= 128 ? 128 : (tneed <= 256 ? 256 : 512)));
+    const int n_units = NTILES * KC;
+
+    if (warp == 1) {
+        tc::tmem_alloc(&tslot, talloc);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            tc::mbar_init(&full_bar[q], 1);
+            tc::mbar_init(&empty_bar[q], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&dfull[b], 1);
+            tc::mbar_init(&dempty[b], 1);
+        }
+        tc::mbar_init(&a_bar, 1);
+        tc::mbar_init(&drain_bar, 1);
+        tc::mbar_fence_init();
+        fail = 0;
+    }
+    if (tid < 128) {
+        sA[tid] = aexp[(size_t)blockIdx.x * 128 + tid];
+        exacc[tid] = cmk(0.0, 0.0);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tslot;
+    bool failed = false;
+
+    if (warp == 0) {
+        // ---- producer: the A tile once (a_res), then unit v = (N-tile v / KC, chunk v % KC)
+        if (lane == 0) {
+            if (a_res) {
+                tc::mbar_arrive_expect_tx(&a_bar, (uint32_t)KC * TCW_CHUNK_A);
+                for (int c = 0; c < KC; ++c)
+                    tc::bulk_g2s(Ares + (size_t)c * TCW_CHUNK_A, Atile + (size_t)c * TCW_CHUNK_A, TCW_CHUNK_A, &a_bar);
+            }
+            int issued = 0;
+            for (int v = 0; v < n_units; ++v) {
+                const int st = v % S;
+                if (v >= S && !wait_or_fail(&empty_bar[st], (uint32_t)(((v / S) - 1) & 1), lim, &fail)) { failed = true; break; }
+                const int t = v / KC, c = v % KC;
+                uint8_t* dst = ring + (size_t)st * stage_bytes;
+                tc::mbar_arrive_expect_tx(&full_bar[st], stage_bytes);
+                if (!a_res) tc::bulk_g2s(dst, Atile + (size_t)c * TCW_CHUNK_A, TCW_CHUNK_A, &full_bar[st]);
+                tc::bulk_g2s(dst + (a_res ? 0 : TCW_CHUNK_A), Ywalk + ((size_t)t * KC + c) * bbytes, bbytes, &full_bar[st]);
+                ++issued;
+            }
+            for (int v = max(0, issued - S); v < issued; ++v)
+                tc::mbar_wait(&full_bar[v % S], (uint32_t)((v / S) & 1), 1u << 22);
+            if (a_res) tc::mbar_wait(&a_bar, 0, 1u << 22);
+            if (failed) atomicOr(status, STATUS_TIMEOUT);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- MMA issue (one thread)
+        if (lane == 0) {
+            const uint32_t idesc = F16 ? tc::idesc_f16_f32(128, NT) : tc::idesc_bf16_f32(128, NT);
+            if (a_res && !wait_or_fail(&a_bar, 0, lim, &fail)) failed = true;
+            for (int t = 0; t < NTILES && !failed; ++t) {
+                const int b = t & 1;
+                if (t >= 2 && !wait_or_fail(&dempty[b], (uint32_t)(((t >> 1) - 1) & 1), lim, &fail)) { failed = true; break; }
+                tc::fence_after_sync();
+                const uint32_t dh = taddr + (uint32_t)b * dcols, dl = dh + (F16 ? (uint32_t)NT : 0u);
+                for (int c = 0; c < KC; ++c) {
+                    const int v = t * KC + c, st = v % S;
+                    if (!wait_or_fail(&full_bar[st], (uint32_t)((v / S) & 1), lim, &fail)) { failed = true; break; }
+                    tc::fence_after_sync();
+                    const int ks = min(4, (KZ - 64 * c) / 16);
+                    const uint8_t* sbase = ring + (size_t)st * stage_bytes;
+                    const uint32_t pa = tc::smem_u32(a_res ? Ares + (size_t)c * TCW_CHUNK_A : sbase);
+                    const uint32_t pb = tc::smem_u32(sbase + (a_res ? 0 : TCW_CHUNK_A));
+                    for (int s = 0; s < ks; ++s) {
+                        const uint64_t ah = tc::desc_sw128(pa + s * 32), al = tc::desc_sw128(pa + 16384 + s * 32);
+                        const uint64_t bh = tc::desc_sw128(pb + s * 32),
+                                       bl = tc::desc_sw128(pb + (uint32_t)NT * 128 + s * 32);
+                        const uint32_t first = (c == 0 && s == 0) ? 0u : 1u;
+                        tc::mma_f16(dh, ah, bh, idesc, first);
+                        if (F16) {
+                            tc::mma_f16(dl, ah, bl, idesc, first);
+                            tc::mma_f16(dl, al, bh, idesc, 1u);
+                            tc::mma_f16(dl, al, bl, idesc, 1u);
+                        } else {
+                            tc::mma_f16(dh, ah, bl, idesc, 1u);
+                            tc::mma_f16(dh, al, bh, idesc, 1u);
+                        }
+                    }
+                    tc::mma_commit(&empty_bar[st]);
+                }
+                if (!failed) tc::mma_commit(&dfull[b]);
+            }
+            if (failed) atomicOr(status, STATUS_TIMEOUT);
+            tc::mma_commit(&drain_bar);
+            tc::mbar_wait(&drain_bar, 0, 1u << 22);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue (warps 2-5): lane r = (p_l, a) holds row a of Z_{p,g}
+        const int et = tid - 64;                         // 0 .. 127
+        const int quarter = warp & 3;
+        const int r = 32 * quarter + lane;
+        const uint32_t lb = (uint32_t)(32 * quarter) << 16;
+        const int pl = r / n, a = r % n;
+        const bool row_ok = r < np * n;
+        const int er = sA[r];
+        // per-pair sums: lpp consecutive threads share a pair's rows
+        int lpp = 32;
+        while (lpp > 1 && lpp * PB > TCW_EPI) lpp >>= 1;
+        const int slot = et / lpp, q = et % lpp;
+        const bool mine = slot < np;
+        for (int t = 0; t < NTILES; ++t) {
+            const int b = t & 1;
+            const bool ok = wait_or_fail(&dfull[b], (uint32_t)((t >> 1) & 1), lim, &fail);
+            if (tc::named_sync_or<TCW_EPI>(!ok)) { failed = true; break; }
+            tc::fence_after_sync();
+            const uint32_t dh = taddr + lb + (uint32_t)b * dcols, dl = dh + (F16 ? (uint32_t)NT : 0u);
+            for (int gl = 0; gl < GB; ++gl) {
+                const int g = t * GB + gl;
+                if (g >= G1) break;                              // uniform
+                const int c0 = gl * 2 * n, c1 = c0 + 2 * n;
+                for (int j0 = (c0 / 16) * 16; j0 < c1; j0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(dh + (uint32_t)j0, v);
+                    if (F16) {
+                        float w[16];
+                        tc::tmem_ld16(dl + (uint32_t)j0, w);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int qq = 0; qq < 16; ++qq) v[qq] += w[qq];
+                    } else {
+                        tc::tmem_ld_wait();
+                    }
+                    if (row_ok) {
+#pragma unroll
+                        for (int qq = 0; qq < 16; ++qq) {
+                            const int col = j0 + qq;
+                            if (col >= c0 && col < c1) {
+                                const int bb = (col - c0) >> 1;
+                                const float z = v[qq] * p2f(-(er + yex[g * n + bb]));
+                                float* dst = reinterpret_cast<float*>(&Ms[(size_t)r * ld + bb]);
+                                dst[(col - c0) & 1] = z;
+                            }
+                        }
+                    }
+                }
+                tc::named_sync<TCW_EPI>();                      // Ms holds Z_{p,g} of every pair of the tile
+                float2 tr = make_float2(0.f, 0.f), ex = make_float2(0.f, 0.f);
+                if (row_ok) {
+                    const float2* row = Ms + (size_t)r * ld;
+                    const float2* col = Ms + (size_t)(pl * n) * ld + a;
+                    tr = row[a];
+                    float ex_x = 0.f, ex_y = 0.f;
+                    for (int bb = 0; bb < n; ++bb) {
+                        const float2 x1 = row[bb], x2 = col[(size_t)bb * ld];
+                        ex_x = fmaf(x1.x, x2.x, fmaf(-x1.y, x2.y, ex_x));
+                        ex_y = fmaf(x1.x, x2.y, fmaf(x1.y, x2.x, ex_y));
+                    }
+                    ex = make_float2(ex_x, ex_y);
+                }
+                red_tr[gl & 1][r] = tr;
+                red_ex[gl & 1][r] = ex;
+                tc::named_sync<TCW_EPI>();                      // Ms free for the next matrix, sums ready
+                float tx = 0.f, ty = 0.f, xx = 0.f, xy = 0.f;
+                if (mine)
+                    for (int aa = q; aa < n; aa += lpp) {
+                        const float2 u = red_tr[gl & 1][slot * n + aa], w = red_ex[gl & 1][slot * n + aa];
+                        tx += u.x; ty += u.y; xx += w.x; xy += w.y;
+                    }
+                for (int o = 1; o < lpp; o <<= 1) {
+                    tx += __shfl_xor_sync(0xffffffffu, tx, o);
+                    ty += __shfl_xor_sync(0xffffffffu, ty, o);
+                    xx += __shfl_xor_sync(0xffffffffu, xx, o);
+                    xy += __shfl_xor_sync(0xffffffffu, xy, o);
+                }
+                if (mine && q == 0) {
+                    vpart[(pair0 + slot) * (long long)G1 + g] = make_float2(tx, ty);
+                    if (g > 0) exacc[slot] = cadd(exacc[slot], cmk((double)xx, (double)xy));
+                }
+            }
+            // buffer b has been read
+            tc::fence_before_sync();
+            tc::named_sync<TCW_EPI>();
+            if (et == 0) tc::mbar_arrive(&dempty[b]);
+        }
+        if (failed && et == 0) atomicOr(status, STATUS_TIMEOUT);
+        tc::named_sync<TCW_EPI>();
+        if (!failed && et < np) exsum[pair0 + et] = exacc[et];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(taddr, talloc);
+}
+
+// ---------------------------------------------------------------- per pair: v_g and E_L
+// One warp per pair: v_g = sum_s Tr Z_s (g >= 1), E_L = sum_s Tr Z_{s,0} +
+// 1/2 sum_g [v_g^2 - sum_s Tr Z_{s,g}^2] (Eq. (16) with Wick's theorem).
+__global__ void tcw_finish_kernel(long long pairs, int G, int two_spins, const float2* __restrict__ vp0,
+                                  const float2* __restrict__ vp1, const double2* __restrict__ ex0,
+                                  const double2* __restrict__ ex1, double2* __restrict__ vpair,
+                                  double2* __restrict__ epair) {
+    const long long pair = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (pair >= pairs) return;
+    const int G1 = G + 1;
+    const float2* a = vp0 + pair * G1;
+    const float2* b = vp1 + pair * G1;
+    double sx = 0.0, sy = 0.0;
+    for (int g = 1 + lane; g < G1; g += 32) {
+        double2 v = cmk((double)a[g].x, (double)a[g].y);
+        if (two_spins) v = cadd(v, cmk((double)b[g].x, (double)b[g].y));
+        vpair[pair * G + (g - 1)] = v;
+        sx += v.x * v.x - v.y * v.y;
+        sy += 2.0 * v.x * v.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) {
+        double2 e1 = cmk((double)a[0].x, (double)a[0].y);
+        double2 ex = ex0[pair];
+        if (two_spins) {
+            e1 = cadd(e1, cmk((double)b[0].x, (double)b[0].y));
+            ex = cadd(ex, ex1[pair]);
+        }
+        epair[pair] = cmk(e1.x + 0.5 * (sx - ex.x), e1.y + 0.5 * (sy - ex.y));
+    }
+}
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+struct TcwSpin {
+    int n, PB, MT, GB, NT, NTILES;
+    int a_res, S;
+    size_t smem;
+};
+
+struct TcwShape {
+    int N16, KZ, KC, KCX, G1;
+    int SY, GPB;
+    size_t smem_y;
+    TcwSpin sp[2];
+    long long WB;                 // walkers per chunk of the Y images
+    size_t ximg, yimg, aimg, yexp, aexp;
+};
+
+size_t tcw_z_smem(int KC, int NT, int n, int S, bool a_res) {
+    const size_t stage = (a_res ? 0 : TCW_CHUNK_A) + (size_t)NT * 256;
+    return 1024 + (a_res ? (size_t)KC * TCW_CHUNK_A : 0) + (size_t)S * stage + (size_t)128 * (n + 1) * 8;
+}
+
+bool tcw_spin(int n, int P, int KC, int G1, bool f16, TcwSpin& s) {
+    s.n = n;
+    if (n < 1 || n > 64) return false;
+    s.PB = 128 / n;
+    if (s.PB > P) s.PB = P;
+    s.MT = (P + s.PB - 1) / s.PB;
+    const int per = 2 * n;
+    const int maxcols = f16 ? 128 : 256;                 // two buffers of (1 or 2) x NT columns in 512
+    s.GB = 0;
+    for (int gb = maxcols / per; gb >= 1; --gb)
+        if (tcw_round16(gb * per) <= maxcols) { s.GB = gb; break; }
+    if (s.GB < 1) return false;
+    if (s.GB > G1) s.GB = G1;
+    s.NT = tcw_round16(s.GB * per);
+    s.NTILES = (G1 + s.GB - 1) / s.GB;
+    for (int a_res = 1; a_res >= 0; --a_res)
+        for (int S = TCW_MAXSTAGES; S >= 2; --S) {
+            const size_t sm = tcw_z_smem(KC, s.NT, n, S, a_res);
+            if (sm <= TCW_SMEM_MAX) {
+                s.a_res = a_res;
+                s.S = S;
+                s.smem = sm;
+                return true;
+            }
+        }
+    return false;
+}
+
+bool tcw_shape(int N, int nu, int nd, int G, long long W, int P, bool f16, TcwShape& s) {
+    if (N < 1 || N > 256 || nu < 1 || nu > 64 || nd < 0 || nd > nu) return false;
+    s.N16 = tcw_round16(N);
+    s.KZ = 2 * s.N16;
+    s.KC = (s.KZ + 63) / 64;
+    s.KCX = (s.N16 + 63) / 64;
+    s.G1 = G + 1;
+    if (!tcw_spin(nu, P, s.KC, s.G1, f16, s.sp[0])) return false;
+    if (nd > 0 && !tcw_spin(nd, P, s.KC, s.G1, f16, s.sp[1])) return false;
+    if (nd == 0) s.sp[1] = s.sp[0], s.sp[1].n = 0;
+    // GEMM-Y: PW (KCX x 32 KB) and a ring of at least two half-chunks of N16 rows
+    const size_t RX = (size_t)s.N16 * 128;
+    s.SY = 0;
+    for (int S = TCW_MAXSTAGES; S >= 2; --S)
+        if (1024 + (size_t)s.KCX * TCW_CHUNK_A + S * RX <= TCW_SMEM_MAX) { s.SY = S; break; }
+    if (!s.SY) return false;
+    s.smem_y = 1024 + (size_t)s.KCX * TCW_CHUNK_A + s.SY * RX;
+    if ((f16 ? 2 : 1) * s.N16 > 512) return false;
+    s.GPB = 64;
+    // Y images: per walker and spin NTILES x KC chunks of NT x 256 bytes; chunks of
+    // walkers sized to about 4 GB of images
+    size_t per_walker = 0, aper = 0;
+    for (int q = 0; q < 2; ++q) {
+        if (s.sp[q].n == 0) continue;
+        per_walker = std::max(per_walker, (size_t)s.sp[q].NTILES * s.KC * s.sp[q].NT * 256);
+        aper = std::max(aper, (size_t)s.sp[q].MT * s.KC * TCW_CHUNK_A);
+    }
+    // about 12 GB of Y images per chunk, and a chunk's GEMM-Z blocks (WB x MT per
+    // spin) a whole number of waves of 152 blocks when the population allows
+    const size_t budget = (size_t)12 << 30;
+    s.WB = std::max(1LL, std::min(W, (long long)(budget / per_walker)));
+    const int mt = std::max(s.sp[0].MT, s.sp[1].MT);
+    if (s.WB < W && s.WB * mt >= 152) s.WB = std::max(1LL, (s.WB * mt / 152) * 152 / mt);
+    s.ximg = (size_t)s.G1 * s.KCX * 2 * RX;
+    s.yimg = (size_t)s.WB * per_walker;
+    s.aimg = (size_t)s.WB * aper;
+    s.yexp = (size_t)s.WB * s.G1 * nu * sizeof(int);
+    s.aexp = (size_t)s.WB * std::max(s.sp[0].MT, s.sp[1].MT) * 128 * sizeof(int);
+    return true;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct TcwWork {
+    uint8_t *ximg, *yimg, *aimg;
+    int *lexp, *yexp, *aexp;
+    float2* vpart[2];
+    double2* exsum[2];
+};
+
+TcwWork tcw_carve(void* work, const TcwShape& s, int G, long long pairs) {
+    TcwWork w;
+    uint8_t* p = static_cast<uint8_t*>(work);
+    w.ximg = p; p += align256(s.ximg);
+    w.yimg = p; p += align256(s.yimg);
+    w.aimg = p; p += align256(s.aimg);
+    w.lexp = reinterpret_cast<int*>(p); p += align256((size_t)(G + 1) * sizeof(int));
+    w.yexp = reinterpret_cast<int*>(p); p += align256(s.yexp);
+    w.aexp = reinterpret_cast<int*>(p); p += align256(s.aexp);
+    for (int q = 0; q < 2; ++q) { w.vpart[q] = reinterpret_cast<float2*>(p); p += align256((size_t)pairs * (G + 1) * 8); }
+    for (int q = 0; q < 2; ++q) { w.exsum[q] = reinterpret_cast<double2*>(p); p += align256((size_t)pairs * 16); }
+    return w;
+}
+
+size_t tcw_total(const TcwShape& s, int G, long long pairs) {
+    return align256(s.ximg) + align256(s.yimg) + align256(s.aimg) + align256((size_t)(G + 1) * sizeof(int)) +
+           align256(s.yexp) + align256(s.aexp) + 2 * align256((size_t)pairs * (G + 1) * 8) + 2 * align256((size_t)pairs * 16);
+}
+
+// Per-matrix exponent (FP16 mode) putting max |X_g| into [128, 256).
+__global__ void tcw_lexp_kernel(int N, int G1, const double* __restrict__ h, const double* __restrict__ L, int f16,
+                                int* lexp) {
+    __shared__ float red[256];
+    const int g = blockIdx.x;
+    const double* X = g == 0 ? h : L + (long long)(g - 1) * N * N;
+    float m = 0.f;
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) m = fmaxf(m, (float)fabs(X[e]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + off]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) lexp[g] = f16 ? exp_into(red[0], 7) : 0;
+}
+
+template <bool F16>
+cudaError_t tcw_run(cudaStream_t st, const Dims& d, const TcwShape& s, const TcwWork& w, const double2* Bm,
+                    const double2* phi, double2* vpair, double2* epair, int* status) {
+    cudaError_t e;
+    if ((e = raise_smem_limit((const void*)tcw_y_kernel<F16>, s.smem_y)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void*)contract_tcw_kernel<F16>, std::max(s.sp[0].smem, s.sp[1].smem))) !=
+        cudaSuccess)
+        return e;
+    const long long W = d.pairs / d.P;
+    const int n_gblk = (s.G1 + s.GPB - 1) / s.GPB;
+    for (long long w0 = 0; w0 < W; w0 += s.WB) {
+        const long long wb = std::min(s.WB, W - w0);
+        for (int q = 0; q < 2; ++q) {
+            const TcwSpin& sp = s.sp[q];
+            if (sp.n == 0) continue;
+            const int col0 = q ? d.nu : 0;
+            tcw_y_kernel<F16><<<(unsigned)(wb * n_gblk), TCW_THREADS, s.smem_y, st>>>(
+                d.N, d.nt, col0, sp.n, s.G1, s.N16, s.KCX, s.SY, s.GPB, n_gblk, w0, phi, w.ximg, w.lexp, sp.NT, sp.GB,
+                s.KC, sp.NTILES, w.yimg, w.yexp, status, d.wait_polls);
+            tcw_a_kernel<F16><<<(unsigned)(wb * sp.MT), 256, 0, st>>>(d.N, d.nt, col0, sp.n, d.P, sp.PB, sp.MT, s.N16,
+                                                                      s.KC, w0, Bm, w.aimg, w.aexp);
+            contract_tcw_kernel<F16><<<(unsigned)(wb * sp.MT), TCW_THREADS, sp.smem, st>>>(
+                sp.n, s.G1, s.KZ, s.KC, sp.NT, sp.GB, sp.NTILES, d.P, sp.PB, sp.MT, sp.S, sp.a_res, w0, w.aimg, w.aexp,
+                w.yimg, w.yexp, w.vpart[q], w.exsum[q], status, d.wait_polls);
+            count_launches(3);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    const long long threads = d.pairs * 32;
+    tcw_finish_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(d.pairs, d.G, d.nd > 0 ? 1 : 0, w.vpart[0],
+                                                                        w.vpart[1], w.exsum[0], w.exsum[1], vpair, epair);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool contract_tcw_supported(int N, int nu, int nd, int G, long long W, int P, bool f16) {
+    TcwShape s;
+    return tcw_shape(N, nu, nd, G, W, P, f16, s);
+}
+
+size_t contract_tcw_work_bytes(int N, int nu, int nd, int G, long long W, int P, bool f16) {
+    TcwShape s;
+    if (!tcw_shape(N, nu, nd, G, W, P, f16, s)) return 0;
+    return tcw_total(s, G, W * (long long)P);
+}
+
+cudaError_t contract_tcw_prepare(cudaStream_t st, const Dims& d, const double* h, const double* L, void* work,
+                                 bool f16) {
+    TcwShape s;
+    if (!tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, f16, s)) return cudaErrorInvalidValue;
+    TcwWork w = tcw_carve(work, s, d.G, d.pairs);
+    tcw_lexp_kernel<<<(unsigned)s.G1, 256, 0, st>>>(d.N, s.G1, h, L, f16 ? 1 : 0, w.lexp);
+    if (f16)
+        tcw_x_image_kernel<true><<<1024, 256, 0, st>>>(d.N, s.N16, s.KCX, s.G1, h, L, w.lexp, w.ximg);
+    else
+        tcw_x_image_kernel<false><<<1024, 256, 0, st>>>(d.N, s.N16, s.KCX, s.G1, h, L, w.lexp, w.ximg);
+    count_launches(2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the Y images' padding rows (past the last matrix of a tile's block, and the
+    // rows of absent matrices in the last tile) are never written: zero them once
+    return cudaMemsetAsync(w.yimg, 0, s.yimg, st);
+}
+
+cudaError_t contract_tcw(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,
+                         double2* vpair, double2* epair, int* status, bool f16) {
+    TcwShape s;
+    if (!tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, f16, s)) return cudaErrorInvalidValue;
+    if (d.pairs <= 0) return cudaSuccess;
+    TcwWork w = tcw_carve(work, s, d.G, d.pairs);
+    return f16 ? tcw_run<true>(st, d, s, w, Bm, phi, vpair, epair, status)
+               : tcw_run<false>(st, d, s, w, Bm, phi, vpair, epair, status);
+}
+
+}  // namespace afq

@@ -92,6 +92,18 @@ size_t contract_tcy_yimage_bytes(int N, int nu, int nd, int G, long long W, bool
 cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const double* Phi, const double2* Theta,
                         const double2* phi, void* ywork, double2* vpair, double2* epair, int* status, bool f16);
 
+// contract_tcw.cu: the walker-side tensor-core form for any size of the FP64
+// path (N <= 256, n_up <= 64): Z_{p,g} = B_p^T (X_g phi_w), B_p = Phi_p A_p^-T from
+// overlap_lu with OVL_TRIAL.  work: contract_tcw_work_bytes bytes (the split
+// image of X_g, per chunk of walkers the images of Y_g and B_p, per-pair traces);
+// contract_tcw_prepare fills the X image once (h and L must not change after).
+bool contract_tcw_supported(int N, int nu, int nd, int G, long long W, int P, bool f16);
+size_t contract_tcw_work_bytes(int N, int nu, int nd, int G, long long W, int P, bool f16);
+cudaError_t contract_tcw_prepare(cudaStream_t st, const Dims& d, const double* h, const double* L, void* work,
+                                 bool f16);
+cudaError_t contract_tcw(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,
+                         double2* vpair, double2* epair, int* status, bool f16);
+
 // walker.cu
 struct StepParams {
     uint64_t seed;

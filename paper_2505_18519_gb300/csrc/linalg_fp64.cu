@@ -99,6 +99,7 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
         if (lane == 0) logdet[pair * 2 + spin] = cmk(0.0, 0.0);
         return;
     }
+    bool bad = false;
     for (int e = lane; e < n * n; e += 32) {
         int a = e / n, b = e - a * n;
         double2 s = cmk(0.0, 0.0);
@@ -109,9 +110,26 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
             s.y = fma(f, g.y, s.y);
         }
         A[e] = s;
+        bad |= !isfinite(s.x) || !isfinite(s.y);
     }
     for (int r = lane; r < n; r += 32) perm[r] = r;
     __syncwarp();
+    // orbitals with a non-finite entry have no overlap: NaN log-determinant, so the
+    // walker's path signs are NaN and the kill rule removes it
+    if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) {
+            logdet[pair * 2 + spin] = cmk(__longlong_as_double(0x7FF8000000000000LL), __longlong_as_double(0x7FF8000000000000LL));
+            atomicOr(status, STATUS_NONFINITE);
+        }
+        if (Theta && trial_side == 2) {
+            double2* Wp = Theta + pair * (long long)N * nt + (spin ? (long long)nu * nu : 0);
+            for (int e = lane; e < n * n; e += 32) Wp[e] = cmk(0.0, 0.0);
+        } else if (Theta) {
+            double2* Th = Theta + pair * (long long)N * nt + col0;
+            for (int e = lane; e < N * n; e += 32) Th[(long long)(e / n) * nt + e % n] = cmk(0.0, 0.0);
+        }
+        return;
+    }
     // The product of the pivots is carried as z * 2^zexp (z rescaled by an exact
     // power of two after every pivot), so log|det| and arg det need one log and
     // one atan2 in all: scalar FP64 work occupies a whole warp instruction.
@@ -293,6 +311,7 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
     int* perm = reinterpret_cast<int*>(dinv + nu);
     const double* Ph = Phi + pair * Phi_stride;         // N x nu, spin uses the first n columns
     const double2* ph = phi + w * (long long)N * nt + col0;  // N x nt
+    bool bad = false;
     for (int e = hl; e < n * n; e += 16) {
         const int a = e / n, b = e - a * n;
         double2 s = cmk(0.0, 0.0);
@@ -303,9 +322,26 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
             s.y = fma(f, g.y, s.y);
         }
         A[e] = s;
+        bad |= !isfinite(s.x) || !isfinite(s.y);
     }
     for (int r = hl; r < n; r += 16) perm[r] = r;
     __syncwarp();
+    // orbitals with a non-finite entry (either spin) have no overlap: NaN
+    // log-determinants, so the walker's path signs are NaN and the kill rule removes it
+    if (__any_sync(FULL, bad)) {
+        if (hl == 0) {
+            logdet[pair * 2 + h] = cmk(__longlong_as_double(0x7FF8000000000000LL), __longlong_as_double(0x7FF8000000000000LL));
+            atomicOr(status, STATUS_NONFINITE);
+        }
+        if (Theta && trial_side == 2) {
+            double2* Wp = Theta + pair * (long long)N * nt + (h ? (long long)nu * nu : 0);
+            for (int e = hl; e < n * n; e += 16) Wp[e] = cmk(0.0, 0.0);
+        } else if (Theta) {
+            double2* Th = Theta + pair * (long long)N * nt + col0;
+            for (int e = hl; e < N * n; e += 16) Th[(long long)(e / n) * nt + e % n] = cmk(0.0, 0.0);
+        }
+        return;
+    }
     double2 z = cmk(1.0, 0.0);
     int zexp = 0;
     bool odd = false;

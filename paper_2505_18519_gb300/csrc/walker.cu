@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(1024) energy_reduce_kernel(int W, int P, const
     double a = 0.0, b = 0.0, c = 0.0;
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
         double wt = weight[w];
-        if (wt > 0.0) {
+        // a walker without a finite estimate (non-finite orbitals) carries no weight
+        if (wt > 0.0 && isfinite(ebar[w].x) && isfinite(ebar[w].y)) {
             a += wt * ebar[w].x;
             b += wt;
             c += wt * cabs_(sumS[w]) / P;
