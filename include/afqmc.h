@@ -334,6 +334,12 @@ const char* afqmc_noalloc_last_error(void);
 /* Message of the last error in this thread (static storage). */
 const char* afqmc_last_error(void);
 
+/* Measured FP64 fused multiply-add rate of the current device (TFLOP/s, 2 flops
+ * per FMA): a loop of independent register FMA chains over every SM, timed with
+ * CUDA events on `stream`, best of three after a warm-up launch.  The peak the
+ * FP64 path's contraction is compared with.  Synchronises. */
+afqmc_status afqmc_fp64_fma_rate(double* tflops, void* stream);
+
 /* Launch-shape autotuner: times the candidate shapes of the overlap kernel
  * (matrices per block), the tensor-core contraction (pairs per block) and the
  * trial-orbital kernel (threads per block) on this context's own data, keeps

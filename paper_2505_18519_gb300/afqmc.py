@@ -47,7 +47,9 @@ EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc
            "afqmc_energy_paths", "afqmc_observables", "afqmc_history", "afqmc_stats", "afqmc_state_save", "afqmc_state_load",
            "afqmc_destroy", "afqmc_last_error", "afqmc_philox_fill", "afqmc_profile", "afqmc_profile_read",
            "afqmc_launch_count", "afqmc_contract_kernel", "afqmc_autotune", "afqmc_batch_create", "afqmc_batch_step", "afqmc_batch_sync",
-           "afqmc_batch_destroy", "afqmc_mlp_n_params", "afqmc_mlp_params", "afqmc_mlp_eval", "afqmc_mlp_state")
+           "afqmc_batch_destroy", "afqmc_mlp_n_params", "afqmc_mlp_params", "afqmc_mlp_eval", "afqmc_mlp_state",
+           "afqmc_fp64_fma_rate", "afqmc_local_energy_noalloc", "afqmc_noalloc_scratch_bytes",
+           "afqmc_noalloc_last_error")
 
 PHASES = ("overlap", "contract", "average", "fields", "propagate", "ratio", "propose", "trial_orbitals",
           "mcmc_overlap", "accept", "finish", "comb")
@@ -122,6 +124,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.afqmc_noalloc_scratch_bytes.restype = SZ
     lib.afqmc_local_energy_noalloc.argtypes = [I, I, I, I, ctypes.c_int64, I, P, P, P, P, P, P, P, P]
     lib.afqmc_local_energy_noalloc.restype = I
+    lib.afqmc_fp64_fma_rate.argtypes = [D, P]
+    lib.afqmc_fp64_fma_rate.restype = I
     lib.afqmc_noalloc_last_error.argtypes = []
     lib.afqmc_noalloc_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -386,6 +390,15 @@ def contract_kernel(cfg: AfqmcConfig) -> str:
     if k not in CONTRACT_KERNELS:
         raise AfqmcError(1, "no contraction kernel supports these sizes")
     return CONTRACT_KERNELS[k]
+
+
+def fp64_fma_rate(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current GPU in TFLOP/s."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    v = ctypes.c_double()
+    _check(load_library().afqmc_fp64_fma_rate(ctypes.byref(v), s.cuda_stream))
+    return v.value
 
 
 def launch_count() -> int:

@@ -52,9 +52,18 @@ extern "C" int afqmc_contract_kernel(const afqmc_config* cfg) {
         if (contract_fp64_walker_side(cfg->N, cfg->n_up, cfg->n_dn, cfg->n_paths)) return 3;
         return contract_fp64_supported(cfg->N, cfg->n_up, cfg->n_dn) ? 0 : -1;
     }
-    const bool f16 = cfg->precision == AFQMC_PRECISION_FP16X3;
-    if (contract_tc_walker_side(cfg->N, cfg->n_up, cfg->n_dn, f16)) return 2;
-    return contract_tc_supported(cfg->N, cfg->n_up, cfg->n_dn, f16) ? 1 : -1;
+    return tc_kind(cfg);
+}
+
+int tc_kind(const afqmc_config* c) {
+    const bool f16 = c->precision == AFQMC_PRECISION_FP16X3;
+    const bool tc = contract_tc_supported(c->N, c->n_up, c->n_dn, f16);
+    const bool tcw = contract_tcw_supported(c->N, c->n_up, c->n_dn, c->n_chol, c->n_walkers, c->n_paths, f16);
+    if (c->tc_form == AFQMC_TC_PER_PAIR) return tc ? 1 : -1;
+    if (c->tc_form == AFQMC_TC_WALKER) return tcw ? 5 : -1;
+    if (contract_tc_walker_side(c->N, c->n_up, c->n_dn, f16)) return 2;
+    if (tc) return 1;
+    return tcw ? 5 : -1;
 }
 
 static std::mutex g_smem_mu;
@@ -169,8 +178,8 @@ extern "C" void afqmc_config_default(afqmc_config* c) {
 // positive per-walker tolerance.
 static bool refine_enabled(const afqmc_config* c) {
     if (c->precision == AFQMC_PRECISION_FP64 || !(c->refine_tol > 0.0)) return false;
-    const bool f16 = c->precision == AFQMC_PRECISION_FP16X3;
-    return !contract_tc_walker_side(c->N, c->n_up, c->n_dn, f16) && contract_fp64_supported(c->N, c->n_up, c->n_dn);
+    const int k = tc_kind(c);
+    return (k == 1 || k == 5) && contract_fp64_supported(c->N, c->n_up, c->n_dn);
 }
 
 static const char* check_config(const afqmc_config* c) {
@@ -208,9 +217,10 @@ static const char* check_config(const afqmc_config* c) {
         return "walker_offset out of range of the 32-bit stream entity";
     if (c->precision == AFQMC_PRECISION_FP64 && !contract_fp64_supported(c->N, c->n_up, c->n_dn))
         return "sizes too large for the FP64 contraction kernel";
-    if (c->precision != AFQMC_PRECISION_FP64 &&
-        !contract_tc_supported(c->N, c->n_up, c->n_dn, c->precision == AFQMC_PRECISION_FP16X3))
-        return "sizes not supported by the tensor-core contraction (N <= 128, n_up <= 32)";
+    if (c->tc_form < AFQMC_TC_AUTO || c->tc_form > AFQMC_TC_WALKER) return "unknown tc_form";
+    if (c->precision != AFQMC_PRECISION_FP64 && tc_kind(c) < 0)
+        return "sizes not supported by the chosen tensor-core contraction (per-pair form: N <= 128, n_up <= 32; "
+               "walker-side form: N <= 256, n_up <= 64)";
     if (3ull * c->N * c->n_up * 8 > 200 * 1024)
         return "sizes too large for the trial-orbital kernel (3 N n_up doubles of shared memory)";
     return nullptr;
@@ -256,12 +266,11 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.xdf = c->precision != AFQMC_PRECISION_FP64 ? take(std::max(pairs * K, 2 * W * G) * 8) : nullptr;
     w.expTdf = prop_df ? take(NN * 8) : nullptr;
     w.scratchNN = (double*)take(3 * NN * 8);
-    w.Lt = c->precision != AFQMC_PRECISION_FP64
-               ? take(contract_tc_image_bytes(d.N, d.nu, d.nd, d.G, c->precision == AFQMC_PRECISION_FP16X3))
-               : nullptr;
-    w.Yimg = c->precision != AFQMC_PRECISION_FP64
-                 ? take(contract_tcy_yimage_bytes(d.N, d.nu, d.nd, d.G, d.W, c->precision == AFQMC_PRECISION_FP16X3))
-                 : nullptr;
+    const int tck = c->precision != AFQMC_PRECISION_FP64 ? tc_kind(c) : -1;
+    const bool f16c = c->precision == AFQMC_PRECISION_FP16X3;
+    w.Lt = (tck == 1 || tck == 2) ? take(contract_tc_image_bytes(d.N, d.nu, d.nd, d.G, f16c)) : nullptr;
+    w.Yimg = tck == 2 ? take(contract_tcy_yimage_bytes(d.N, d.nu, d.nd, d.G, d.W, f16c)) : nullptr;
+    w.tcw = tck == 5 ? take(contract_tcw_work_bytes(d.N, d.nu, d.nd, d.G, d.W, d.P, f16c)) : nullptr;
     const size_t ywalk = c->precision == AFQMC_PRECISION_FP64 ? contract_fp64_walker_bytes(d.N, d.nu, d.nd, d.G, d.W, d.P)
                                                               : 0;
     w.ywalk = ywalk ? take(ywalk) : nullptr;
@@ -282,7 +291,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.y = (double2*)take(W * G * 16);
     w.logshift = (double2*)take(W * 16);
     const bool refine = refine_enabled(c);
-    w.refine_th2 = refine ? (double*)take(pairs * 8) : nullptr;
+    w.refine_th2 = refine ? (double*)take(2 * pairs * 8) : nullptr;   // per pair (and spin)
     w.refine_items = refine ? (int*)take(pairs * 4) : nullptr;
     w.refine_n = refine ? (int*)take(4) : nullptr;
     w.refine_lam = refine ? (double*)take((G + 1) * 8) : nullptr;
@@ -440,14 +449,32 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     afqmc_status st;
     const bool f16 = ctx->cfg.precision == AFQMC_PRECISION_FP16X3;
     const bool fp64 = ctx->cfg.precision == AFQMC_PRECISION_FP64;
+    const int tck = fp64 ? -1 : tc_kind(&ctx->cfg);
     const int ovl = fp64 ? (!w.rc && contract_fp64_walker_side(d.N, d.nu, d.nd, d.P) ? OVL_INVERSE : OVL_THETA)
-                         : (contract_tc_walker_side(d.N, d.nu, d.nd, f16) ? OVL_TRIAL : OVL_THETA);
+                         : (tck == 2 || tck == 5 ? OVL_TRIAL : OVL_THETA);
     CK(overlap_lu_both(s, d, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
-                       ovl));
+                       ovl, tck == 5 && w.refine_items ? w.refine_th2 : nullptr));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64) {
-        CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.Yimg, w.vpair, w.epair, w.status, f16));
-        if (w.refine_items) {   // the pairs whose error would put their walker above refine_tol, again
+        if (tck == 5) {
+            CK(contract_tcw(s, d, w.tcw, w.Theta, w.phi, w.vpair, w.epair, w.status, f16));
+            if (w.refine_items) {
+                // the pairs whose error would put their walker above refine_tol, again: selected
+                // by ||A_p^-1||_F^2 from the overlap kernel (the walker-side operand carries
+                // about 19 bits, hence u = 2^-19), their Theta formed in place of B, then the
+                // double-float per-pair contraction; the log-overlaps go to scratch
+                CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2,
+                                 w.alive, w.refine_items, w.refine_n, w.counters, w.refine_th2, 0x1p-19));
+                for (int spin = 0; spin < 2; ++spin)
+                    CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet_new, w.Theta, nullptr,
+                                  w.status, d.pairs, d.P, OVL_THETA, nullptr, w.refine_items, w.refine_n));
+                CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n,
+                                        d.pairs, w.hdf, w.Ldf));
+            }
+        } else {
+            CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.Yimg, w.vpair, w.epair, w.status, f16));
+        }
+        if (tck != 5 && w.refine_items) {   // the pairs whose error would put their walker above refine_tol, again
             CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2, w.alive,
                              w.refine_items, w.refine_n, w.counters));
             CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n,
@@ -505,7 +532,12 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, 4, s);
         if (e != cudaSuccess) { st = fail(AFQMC_ERR_CUDA, "copying inputs: %s", cudaGetErrorString(e)); break; }
         StepParams p = params_of(cfg);
-        if (cfg->precision != AFQMC_PRECISION_FP64 &&
+        if (w.tcw && (e = contract_tcw_prepare(s, d, w.h, w.L, w.tcw, cfg->precision == AFQMC_PRECISION_FP16X3)) !=
+                         cudaSuccess) {
+            st = fail(AFQMC_ERR_CUDA, "tensor-core operand image: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (w.Lt &&
             (e = contract_tc_prepare(s, d.N, d.nu, d.nd, d.G, w.h, w.L, w.Lt,
                                      cfg->precision == AFQMC_PRECISION_FP16X3)) != cudaSuccess) {
             st = fail(AFQMC_ERR_CUDA, "tensor-core operand image: %s", cudaGetErrorString(e));

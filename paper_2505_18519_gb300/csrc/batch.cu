@@ -93,9 +93,9 @@ extern "C" afqmc_status afqmc_autotune(afqmc_ctx* ctx, int* chosen) {
     d.ov_wpb = best_wpb;
     // tensor-core contraction: pairs per block (largest that fits, and smaller)
     int best_tp = 0;
-    if (c.precision != AFQMC_PRECISION_FP64) {
+    if (c.precision != AFQMC_PRECISION_FP64 && tc_kind(&c) != 5) {   // the general walker-side form has no tuned shape
         const bool f16 = c.precision == AFQMC_PRECISION_FP16X3;
-        const int ovl = contract_tc_walker_side(d.N, d.nu, d.nd, f16) ? OVL_TRIAL : OVL_THETA;
+        const int ovl = tc_kind(&c) == 2 ? OVL_TRIAL : OVL_THETA;
         for (int spin = 0; spin < 2; ++spin)
             BK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs,
                           d.P, ovl));

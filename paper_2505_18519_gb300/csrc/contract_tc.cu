@@ -1302,8 +1302,8 @@ cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const
     const int* lexp = reinterpret_cast<const int*>(static_cast<const uint8_t*>(image) +
                                                    (size_t)(G1p / s.GPT) * s.NKB * TC_UNIT);
     TcyShape sy;
-    if (tcy_shape(d.N, d.nu, d.nd, f16, d.tc_tp, sy)) {   // Theta holds B = Phi A^-T here
-        if (d.P < 1 || d.pairs % d.P != 0 || !ywork) return cudaErrorInvalidValue;
+    if (ywork && tcy_shape(d.N, d.nu, d.nd, f16, d.tc_tp, sy)) {   // Theta holds B = Phi A^-T here
+        if (d.P < 1 || d.pairs % d.P != 0) return cudaErrorInvalidValue;
         return f16 ? launch_tcy<true>(st, d, sy, image, lexp, Theta, phi, ywork, vpair, epair, status)
                    : launch_tcy<false>(st, d, sy, image, lexp, Theta, phi, ywork, vpair, epair, status);
     }

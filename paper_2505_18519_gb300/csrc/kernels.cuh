@@ -4,6 +4,10 @@
 
 // api.cu: record an error message for afqmc_last_error and return `st`
 afqmc_status set_error(afqmc_status st, const char* fmt, ...);
+// api.cu: the tensor-core form of a mixed-precision configuration (the value
+// afqmc_contract_kernel reports: 1 per-pair, 2 walker-side for N <= 64,
+// 5 general walker-side), -1 if the chosen form does not support its sizes.
+int tc_kind(const afqmc_config* c);
 
 namespace afq {
 
@@ -11,14 +15,18 @@ namespace afq {
 void gemm_nn_f64(cudaStream_t s, int M, int Nc, int K, double alpha, const double* A, long long lda, const double* B,
                  long long ldb, double beta, double* C, long long ldc);
 enum OverlapOutput { OVL_THETA = 0, OVL_TRIAL = 1, OVL_INVERSE = 2 };
+// th2 (nullable, with Theta): ||A^-1||_F^2 per pair and spin at th2[2 pair + spin]
+// (infinite for a singular or non-finite overlap).  list, n_list (nullable): only
+// the pairs list[0 .. *n_list), a device list, with the grid sized for `pairs` of them.
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                       long long pairs, int P, int trial_side = OVL_THETA);
+                       long long pairs, int P, int trial_side = OVL_THETA, double* th2 = nullptr,
+                       const int* list = nullptr, const int* n_list = nullptr);
 // Both spins: one warp per pair (half a warp per spin) when n_up <= 16, else
 // overlap_lu for each spin.  Same results.
 cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, long long Phi_stride,
                             const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                            long long pairs, int P, int trial_side = OVL_THETA);
+                            long long pairs, int P, int trial_side = OVL_THETA, double* th2 = nullptr);
 cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, double2* dst, const int* alive,
                              int* status, int n_walkers);
 // Phi = exp(S) Phi0 for `problems` symmetric S (FP64).  trial_orbitals runs the
@@ -56,9 +64,12 @@ bool contract_fp64_supported(int N, int nu, int nd);
 // estimated error stays below tol, appended to items (count in *n_items,
 // cumulative count in counters[5]).
 cudaError_t refine_scale(cudaStream_t s, int N, int G, const double* L, double* lam_g, double* lam);
+// th2_spins (nullable): ||Theta_p||_F^2 per pair and spin from the overlap kernel,
+// used instead of forming ||Theta_p||_F^2 from Theta; u: the contraction's
+// resolution in the error model (2^-20 for the per-pair form).
 cudaError_t refine_select(cudaStream_t s, const Dims& d, double tol, const double* lam, const double2* logdet,
                           const double2* Theta, double* th2, const int* alive, int* items, int* n_items,
-                          unsigned long long* counters);
+                          unsigned long long* counters, const double* th2_spins = nullptr, double u = 0x1p-20);
 // The same contraction for the pairs items[0 .. *n_items) only (a device list of
 // pair indices, *n_items <= max_items), the others' vpair/epair left as they are;
 // with hdf and Ldf (double-float copies of h and L from u_to_df) R and M run in

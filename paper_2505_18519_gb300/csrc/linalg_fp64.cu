@@ -80,11 +80,16 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
                                   const double* __restrict__ Phi, long long Phi_stride,
                                   const double2* __restrict__ phi, double2* __restrict__ logdet,
                                   double2* __restrict__ Theta, const int* __restrict__ alive, int* status,
-                                  int trial_side) {
+                                  int trial_side, double* __restrict__ th2, const int* __restrict__ list,
+                                  const int* __restrict__ n_list) {
     extern __shared__ double2 sm[];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
     long long pair = (long long)blockIdx.x * wpb + warp;
+    if (list) {                                         // only the listed pairs (uniform per warp)
+        if (pair >= *n_list) return;
+        pair = list[pair];
+    }
     if (pair >= pairs) return;
     long long w = pair / P;
     if (alive && !alive[w]) return;
@@ -96,7 +101,10 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
     const double* Ph = Phi + pair * Phi_stride;         // N x nu, spin uses the first n columns
     const double2* ph = phi + w * (long long)N * nt + col0;  // N x nt
     if (n == 0) {
-        if (lane == 0) logdet[pair * 2 + spin] = cmk(0.0, 0.0);
+        if (lane == 0) {
+            logdet[pair * 2 + spin] = cmk(0.0, 0.0);
+            if (th2) th2[pair * 2 + spin] = 0.0;
+        }
         return;
     }
     bool bad = false;
@@ -120,6 +128,7 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
         if (lane == 0) {
             logdet[pair * 2 + spin] = cmk(__longlong_as_double(0x7FF8000000000000LL), __longlong_as_double(0x7FF8000000000000LL));
             atomicOr(status, STATUS_NONFINITE);
+            if (th2) th2[pair * 2 + spin] = INFINITY;
         }
         if (Theta && trial_side == 2) {
             double2* Wp = Theta + pair * (long long)N * nt + (spin ? (long long)nu * nu : 0);
@@ -193,6 +202,7 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
         if (lane == 0) {
             logdet[pair * 2 + spin] = cmk(-INFINITY, 0.0);
             atomicOr(status, STATUS_SINGULAR);
+            if (th2) th2[pair * 2 + spin] = INFINITY;
         }
         if (Theta && trial_side == 2) {
             double2* Wp = Theta + pair * (long long)N * nt + (spin ? (long long)nu * nu : 0);
@@ -230,6 +240,13 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
         }
     }
     __syncwarp();
+    if (th2) {   // ||A^-1||_F^2 (= ||Theta||_F^2 for orthonormal walkers), for the refinement
+        double t = 0.0;
+        for (int e = lane; e < n * n; e += 32) t = fma(Ainv[e].x, Ainv[e].x, fma(Ainv[e].y, Ainv[e].y, t));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) th2[pair * 2 + spin] = t;
+    }
     if (trial_side == 2) {
         // A^-1 itself: pair block [A_up^-1 (nu x nu) | A_dn^-1 (nd x nd)], row-major
         double2* Wp = Theta + pair * (long long)N * nt + (spin ? (long long)nu * nu : 0);
@@ -267,7 +284,7 @@ static size_t overlap_smem_per_warp(int n, bool theta) {
 
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                       long long pairs, int P, int trial_side) {
+                       long long pairs, int P, int trial_side, double* th2, const int* list, const int* n_list) {
     int n = spin == 0 ? d.nu : d.nd;
     int col0 = spin == 0 ? 0 : d.nu;
     size_t per = overlap_smem_per_warp(n, Theta != nullptr);
@@ -279,7 +296,8 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
     if (e != cudaSuccess) return e;
     long long blocks = (pairs + wpb - 1) / wpb;
     overlap_lu_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nt, n, col0, spin, pairs, P, Phi, Phi_stride,
-                                                               phi, logdet, Theta, alive, status, trial_side); count_launches(1);
+                                                               phi, logdet, Theta, alive, status, trial_side, th2, list,
+                                                               n_list); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -293,7 +311,7 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
                                        const double* __restrict__ Phi, long long Phi_stride,
                                        const double2* __restrict__ phi, double2* __restrict__ logdet,
                                        double2* __restrict__ Theta, const int* __restrict__ alive, int* status,
-                                       int trial_side) {
+                                       int trial_side, double* __restrict__ th2) {
     extern __shared__ double2 sm[];
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -332,6 +350,7 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
         if (hl == 0) {
             logdet[pair * 2 + h] = cmk(__longlong_as_double(0x7FF8000000000000LL), __longlong_as_double(0x7FF8000000000000LL));
             atomicOr(status, STATUS_NONFINITE);
+            if (th2) th2[pair * 2 + h] = INFINITY;
         }
         if (Theta && trial_side == 2) {
             double2* Wp = Theta + pair * (long long)N * nt + (h ? (long long)nu * nu : 0);
@@ -446,6 +465,14 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
             }
         }
     __syncwarp();
+    if (th2) {   // ||A^-1||_F^2 per spin (every lane takes part in the half-warp sums)
+        double t = 0.0;
+        if (inv)
+            for (int e = hl; e < n * n; e += 16) t = fma(Ainv[e].x, Ainv[e].x, fma(Ainv[e].y, Ainv[e].y, t));
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) t += __shfl_xor_sync(FULL, t, off);
+        if (hl == 0) th2[pair * 2 + h] = n == 0 ? 0.0 : (inv ? t : INFINITY);
+    }
     if (!inv) return;                            // nothing below synchronises the warp
     if (trial_side == 2) {
         double2* Wp = Theta + pair * (long long)N * nt + (h ? (long long)nu * nu : 0);
@@ -478,11 +505,11 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
 
 cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, long long Phi_stride,
                             const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                            long long pairs, int P, int trial_side) {
+                            long long pairs, int P, int trial_side, double* th2) {
     if (d.nu > 16) {   // a half-warp per spin would leave the larger matrices short of lanes
         for (int spin = 0; spin < 2; ++spin) {
             const cudaError_t e = overlap_lu(s, d, spin, Phi, Phi_stride, phi, logdet, Theta, alive, status, pairs, P,
-                                             trial_side);
+                                             trial_side, th2);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -496,7 +523,7 @@ cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, lo
     if (e != cudaSuccess) return e;
     const long long blocks = (pairs + wpb - 1) / wpb;
     overlap_lu_both_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nd, d.nt, pairs, P, Phi, Phi_stride,
-                                                                    phi, logdet, Theta, alive, status, trial_side);
+                                                                    phi, logdet, Theta, alive, status, trial_side, th2);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(RF_T) theta_norm_kernel(int nn, long long pair
 // append their indices to items (order of walkers in the list is arbitrary).
 __global__ void __launch_bounds__(RF_T) refine_select_kernel(int N, int P, double tol, const double* __restrict__ lam,
                                                              const double2* __restrict__ logdet,
-                                                             const double* __restrict__ th2,
+                                                             const double* __restrict__ th2, int spins, double u,
                                                              const int* __restrict__ alive, int* items, int* n_items,
                                                              unsigned long long* counters) {
     __shared__ double key[RF_MAXP];
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(RF_T) refine_select_kernel(int N, int P, doubl
     for (int i = threadIdx.x; i < P2; i += RF_T) {
         double k = -INFINITY;
         if (i < P) {
-            k = th2[w * P + i];
+            k = spins ? th2[2 * (w * P + i)] + th2[2 * (w * P + i) + 1] : th2[w * P + i];
             if (!isfinite(k)) k = INFINITY;   // a singular or overflowing pair is always refined
         }
         key[i] = k;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(RF_T) refine_select_kernel(int N, int P, doubl
     __syncthreads();
     if (threadIdx.x == 0) {
         const double absS = sqrt(sx * sx + sy * sy);
-        const double c = (2.0 / N) * 0x1p-20 * lam[0];
+        const double c = (2.0 / N) * u * lam[0];
         int k = P;   // pairs 0 .. k-1 (in sorted order) are refined
         if (absS > 0.0 && isfinite(absS)) {
             // keep the smallest pairs while their estimated error stays within tol / 2
@@ -192,15 +192,19 @@ __global__ void __launch_bounds__(RF_T) refine_select_kernel(int N, int P, doubl
 
 cudaError_t refine_select(cudaStream_t s, const Dims& d, double tol, const double* lam, const double2* logdet,
                           const double2* Theta, double* th2, const int* alive, int* items, int* n_items,
-                          unsigned long long* counters) {
+                          unsigned long long* counters, const double* th2_spins, double u) {
     if (d.P > RF_MAXP) return cudaErrorInvalidValue;
     if (d.pairs <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(n_items, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     const long long nb = (d.pairs + RF_T / 32 - 1) / (RF_T / 32);
-    theta_norm_kernel<<<(unsigned)nb, RF_T, 0, s>>>(d.N * d.nt, d.pairs, Theta, th2);
-    refine_select_kernel<<<d.W, RF_T, 0, s>>>(d.N, d.P, tol, lam, logdet, th2, alive, items, n_items, counters);
-    count_launches(2);
+    if (!th2_spins) {
+        theta_norm_kernel<<<(unsigned)nb, RF_T, 0, s>>>(d.N * d.nt, d.pairs, Theta, th2);
+        count_launches(1);
+    }
+    refine_select_kernel<<<d.W, RF_T, 0, s>>>(d.N, d.P, tol, lam, logdet, th2_spins ? th2_spins : th2, th2_spins ? 1 : 0,
+                                              u, alive, items, n_items, counters);
+    count_launches(1);
     return cudaGetLastError();
 }
 

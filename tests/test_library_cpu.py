@@ -102,3 +102,25 @@ def test_state_pack_roundtrip():
     assert back["step"] == 7
     for k in ("phi_up", "phi_dn", "weight", "x", "Phi"):
         assert np.array_equal(back[k], st[k]), k
+
+
+def test_tensor_core_form_and_wait_limit_fields_reach_the_library(L):
+    """tc_form selects the tensor-core form that afqmc_contract_kernel reports
+    (host only), and wait_polls / tc_form are validated at their offsets."""
+    kw = dict(precision="fp16x3")
+    assert lib.contract_kernel(lib.make_config(50, 10, 10, 250, 50, 8, 32, 0.005, 1, **kw)) == "contract_tcy_kernel"
+    assert lib.contract_kernel(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, **kw)) == "contract_tc_kernel"
+    assert lib.contract_kernel(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, tc_form="walker",
+                                               **kw)) == "contract_tcw_kernel"
+    # N = 200 with 40 + 40 electrons: only the general walker-side form takes it
+    assert lib.contract_kernel(lib.make_config(200, 40, 40, 1000, 200, 8, 16, 0.005, 1, **kw)) == "contract_tcw_kernel"
+    with pytest.raises(lib.AfqmcError):
+        lib.contract_kernel(lib.make_config(200, 40, 40, 1000, 200, 8, 16, 0.005, 1, tc_form="per_pair", **kw))
+    for field, bad in (("wait_polls", -1), ("wait_polls", (1 << 31) + 1), ("tc_form", 3), ("tc_form", -1)):
+        c = lib.make_config(8, 4, 4, 32, 8, 64, 16, 0.01, 1, **kw)
+        setattr(c, field, bad)
+        assert lib.workspace_bytes(c) == 0, field
+    # the general form's work space (its X image and per-chunk images) is in the total
+    a = lib.workspace_bytes(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, **kw))
+    b = lib.workspace_bytes(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, tc_form="walker", **kw))
+    assert a > 0 and b > 0 and a != b
