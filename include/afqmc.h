@@ -155,7 +155,16 @@ typedef struct {
                            n_up + n_dn <= 40, else the per-pair form (N <= 128, n_up <= 32; it has the
                            error-controlled refinement), else the general walker-side form;
                            AFQMC_TC_PER_PAIR (1); AFQMC_TC_WALKER (2): the general walker-side form
-                           (N <= 256, n_up <= 64; not refined) */
+                           (N <= 256, n_up <= 64; refined like the per-pair form) */
+    double trial_alpha_re, trial_alpha_im;   /* alpha of the trial samples (default 1 + 0i) */
+    int trial_slices;   /* hidden-variable slices of a trial sample (default 1).  The samples are
+                           Phi(x) = exp(alpha S_m) P ... P exp(alpha S_1) Phi0 with S_l = sum_k x_lk U_k
+                           and K hidden variables per slice (x has trial_slices K entries): the
+                           complex VAFQMC form of Eq. (30) (alpha = -i sqrt(s), U_k = L_k) and the
+                           multi-slice form of Eq. (19), (32) (P from afqmc_init_trial).  Any value other
+                           than alpha = 1, one slice needs precision FP64, a proposal other than the
+                           learned one, rcache = 0, and 48 N n_up bytes of shared memory at most
+                           200 KB; Phi is then stored and returned as complex (state buffer) */
 } afqmc_config;
 
 enum { AFQMC_TC_AUTO = 0, AFQMC_TC_PER_PAIR = 1, AFQMC_TC_WALKER = 2 };
@@ -189,6 +198,13 @@ size_t afqmc_workspace_bytes(const afqmc_config* cfg);
 afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, const double* L,
                         const double* Phi0, const double* U, void* workspace,
                         size_t workspace_bytes, void* stream, afqmc_ctx** out);
+
+/* afqmc_init for a multi-slice trial (trial_slices > 1): slice_prop (N*N, host or
+ * device, real) is the fixed propagator P between slices, e.g. exp(-t T) of the
+ * ansatz of Eq. (32); NULL is allowed only with one slice. */
+afqmc_status afqmc_init_trial(const afqmc_config* cfg, const double* h, const double* L, const double* Phi0,
+                              const double* U, const double* slice_prop, void* workspace, size_t workspace_bytes,
+                              void* stream, afqmc_ctx** out);
 
 /* Enqueue n_steps leapfrog steps (asynchronous).  Each step first measures the
  * walkers it starts from and appends {sum_w W_w Re E_w, sum_w W_w,
@@ -246,11 +262,13 @@ afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len);
 
 /* Checkpoint.  The state buffer (host memory) is, in order, with no padding:
  *   uint64  magic 0x4146514D43535431, N, n_up, n_dn, K, W, P, step
+ *           (K here counts the hidden variables of one sample: trial_slices x K)
  *   double  phi     W*N*(n_up+n_dn)*2  walker orbitals, column c < n_up spin up,
  *                                       column n_up + c spin down (re, im)
  *   double  weight  W
  *   double  x       W*P*K              hidden variables of the paths
  *   double  Phi     W*P*N*n_up         Phi(x_wp), kept so a resumed run is exact
+ *                                       (complex, re im, for a trial other than alpha = 1, one slice)
  * afqmc_state_save with buf NULL stores the size in *len; otherwise *len must
  * be at least that size.  afqmc_state_load validates magic and shape.  The
  * random streams are counter based, so save + load + k steps is bitwise equal
@@ -291,7 +309,8 @@ int64_t afqmc_launch_count(void);
  * n_paths >= 8 and the block's operands fit in shared memory, e.g. N <= 64),
  * 4 contract_fp64r_kernel (precision FP64 with rcache = 1: cached R_g,p Theta),
  * 5 contract_tcw_kernel (tensor cores, general walker-side form B_p^T (X_g phi_w),
- * N <= 256, n_up <= 64: see tc_form);
+ * N <= 256, n_up <= 64: see tc_form), 6 contract_fp64c_kernel (precision FP64 with
+ * complex trial samples: R_g = Phi^dagger X_g);
  * -1 if `cfg` is NULL or no kernel supports its sizes.  Host only. */
 int afqmc_contract_kernel(const afqmc_config* cfg);
 

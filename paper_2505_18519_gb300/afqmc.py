@@ -38,12 +38,14 @@ class AfqmcConfig(ctypes.Structure):
         ("mlp_train", ctypes.c_int), ("refine_tol", ctypes.c_double),
         ("importance", ctypes.c_int), ("pop_period", ctypes.c_int), ("rcache", ctypes.c_int),
         ("wait_polls", ctypes.c_int64), ("tc_form", ctypes.c_int),
+        ("trial_alpha_re", ctypes.c_double), ("trial_alpha_im", ctypes.c_double), ("trial_slices", ctypes.c_int),
     ]
 
 
 _lib = None
 
-EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc_step", "afqmc_energy",
+EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc_init_trial", "afqmc_step",
+           "afqmc_energy",
            "afqmc_energy_paths", "afqmc_observables", "afqmc_history", "afqmc_stats", "afqmc_state_save", "afqmc_state_load",
            "afqmc_destroy", "afqmc_last_error", "afqmc_philox_fill", "afqmc_profile", "afqmc_profile_read",
            "afqmc_launch_count", "afqmc_contract_kernel", "afqmc_autotune", "afqmc_batch_create", "afqmc_batch_step", "afqmc_batch_sync",
@@ -71,6 +73,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.afqmc_workspace_bytes.restype = SZ
     lib.afqmc_init.argtypes = [cfgp, P, P, P, P, P, SZ, P, ctypes.POINTER(P)]
     lib.afqmc_init.restype = I
+    lib.afqmc_init_trial.argtypes = [cfgp, P, P, P, P, P, P, SZ, P, ctypes.POINTER(P)]
+    lib.afqmc_init_trial.restype = I
     lib.afqmc_step.argtypes = [P, I]
     lib.afqmc_step.restype = I
     lib.afqmc_energy.argtypes = [P, D, D, D, P]
@@ -147,7 +151,8 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
                 constraint="combined", proposal="prior", precision="fp64", taylor_order=6, history_capacity=1024,
                 pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10, walker_offset=0, rw_step=0.3, mlp_mix=0.1,
                 mlp_lr=1e-3, mlp_train=False, refine_tol=1e-4, importance="hybrid",
-                pop_period=0, rcache=False, wait_polls=0, tc_form="auto") -> AfqmcConfig:
+                pop_period=0, rcache=False, wait_polls=0, tc_form="auto", trial_alpha=1.0,
+                trial_slices=1) -> AfqmcConfig:
     lib = load_library()
     c = AfqmcConfig()
     lib.afqmc_config_default(ctypes.byref(c))
@@ -163,6 +168,8 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
     c.rcache = int(bool(rcache))
     c.wait_polls = int(wait_polls)
     c.tc_form = TC_FORMS[tc_form]
+    c.trial_alpha_re, c.trial_alpha_im = complex(trial_alpha).real, complex(trial_alpha).imag
+    c.trial_slices = int(trial_slices)
     return c
 
 
@@ -187,7 +194,7 @@ def _ptr(a):
 class Context:
     """One AFQMC run: configuration, Hamiltonian, walkers and paths on one GPU."""
 
-    def __init__(self, cfg: AfqmcConfig, h, L, Phi0, U, device=None, stream=None):
+    def __init__(self, cfg: AfqmcConfig, h, L, Phi0, U, device=None, stream=None, slice_prop=None):
         import torch
         lib = load_library()
         if not torch.cuda.is_available():
@@ -204,10 +211,11 @@ class Context:
         self._ws_ptr = (base + 255) & ~255
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         keep = [_ptr(x) for x in (h, L, Phi0, U)]
+        sp = _ptr(slice_prop) if slice_prop is not None else (None, None)
         self._ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            _check(lib.afqmc_init(ctypes.byref(cfg), keep[0][0], keep[1][0], keep[2][0], keep[3][0], self._ws_ptr,
-                                  nbytes, self.stream.cuda_stream, ctypes.byref(self._ctx)))
+            _check(lib.afqmc_init_trial(ctypes.byref(cfg), keep[0][0], keep[1][0], keep[2][0], keep[3][0], sp[0],
+                                        self._ws_ptr, nbytes, self.stream.cuda_stream, ctypes.byref(self._ctx)))
         self.W, self.P, self.G, self.K = cfg.n_walkers, cfg.n_paths, cfg.n_chol, cfg.K
         self.N, self.nu, self.nd = cfg.N, cfg.n_up, cfg.n_dn
 
@@ -381,7 +389,8 @@ class Batch:
 
 
 CONTRACT_KERNELS = {0: "contract_fp64_kernel", 1: "contract_tc_kernel", 2: "contract_tcy_kernel",
-                    3: "contract_fp64z_kernel", 4: "contract_fp64r_kernel", 5: "contract_tcw_kernel"}
+                    3: "contract_fp64z_kernel", 4: "contract_fp64r_kernel", 5: "contract_tcw_kernel",
+                    6: "contract_fp64c_kernel"}
 
 
 def contract_kernel(cfg: AfqmcConfig) -> str:
@@ -422,7 +431,9 @@ def unpack_state(blob: bytes) -> dict:
     phi = take(W * N * nt, np.complex128).reshape(W, N, nt)
     weight = take(W, np.float64)
     x = take(W * P * K, np.float64).reshape(W, P, K)
-    Phi = take(W * P * N * nu, np.float64).reshape(W, P, N, nu)
+    # real trial orbitals, or complex ones (complex or multi-slice trials): the rest of the buffer says which
+    cplx = len(blob) - o == W * P * N * nu * 16
+    Phi = take(W * P * N * nu, np.complex128 if cplx else np.float64).reshape(W, P, N, nu)
     return dict(step=int(step), phi_up=phi[:, :, :nu].copy(), phi_dn=phi[:, :, nu:].copy(), weight=weight, x=x, Phi=Phi)
 
 
@@ -434,7 +445,8 @@ def pack_state(st: dict) -> bytes:
     hdr = struct.pack("<8Q", STATE_MAGIC, N, nu, nd, K, W, P, int(st["step"]))
     return b"".join([hdr, np.ascontiguousarray(phi).tobytes(), np.ascontiguousarray(st["weight"], np.float64).tobytes(),
                      np.ascontiguousarray(st["x"], np.float64).tobytes(),
-                     np.ascontiguousarray(st["Phi"], np.float64).tobytes()])
+                     np.ascontiguousarray(st["Phi"], np.complex128 if np.iscomplexobj(st["Phi"]) else np.float64)
+                     .tobytes()])
 
 
 def philox_fill(out, n: int, c0: int, c1: int, c2: int, c3: int, key: int, stream=None):

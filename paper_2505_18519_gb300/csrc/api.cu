@@ -45,9 +45,15 @@ void afq::count_launches(long long n) { g_launches.fetch_add(n, std::memory_orde
 
 extern "C" int64_t afqmc_launch_count(void) { return g_launches.load(); }
 
+// A trial other than the real one-slice form (complex alpha, or several slices).
+static bool general_trial(const afqmc_config* c) {
+    return c->trial_alpha_im != 0.0 || c->trial_alpha_re != 1.0 || c->trial_slices > 1;
+}
+
 extern "C" int afqmc_contract_kernel(const afqmc_config* cfg) {
     if (!cfg) return -1;
     if (cfg->precision == AFQMC_PRECISION_FP64) {
+        if (general_trial(cfg)) return contract_fp64c_supported(cfg->N, cfg->n_up, cfg->n_dn) ? 6 : -1;
         if (cfg->rcache) return contract_fp64r_supported(cfg->N, cfg->n_up, cfg->n_dn) ? 4 : -1;
         if (contract_fp64_walker_side(cfg->N, cfg->n_up, cfg->n_dn, cfg->n_paths)) return 3;
         return contract_fp64_supported(cfg->N, cfg->n_up, cfg->n_dn) ? 0 : -1;
@@ -171,6 +177,9 @@ extern "C" void afqmc_config_default(afqmc_config* c) {
     c->mlp_lr = 1e-3;
     c->mlp_train = 0;
     c->refine_tol = 1e-4;
+    c->trial_alpha_re = 1.0;
+    c->trial_alpha_im = 0.0;
+    c->trial_slices = 1;
 }
 
 // The tensor-core contraction's pairs with the largest error get recomputed in
@@ -218,6 +227,19 @@ static const char* check_config(const afqmc_config* c) {
     if (c->precision == AFQMC_PRECISION_FP64 && !contract_fp64_supported(c->N, c->n_up, c->n_dn))
         return "sizes too large for the FP64 contraction kernel";
     if (c->tc_form < AFQMC_TC_AUTO || c->tc_form > AFQMC_TC_WALKER) return "unknown tc_form";
+    if (c->trial_slices < 1 || c->trial_slices > 8) return "trial_slices must be in [1, 8]";
+    if (!isfinite(c->trial_alpha_re) || !isfinite(c->trial_alpha_im) ||
+        (c->trial_alpha_re == 0.0 && c->trial_alpha_im == 0.0))
+        return "trial alpha must be finite and non-zero";
+    if (general_trial(c)) {
+        if (c->precision != AFQMC_PRECISION_FP64) return "complex or multi-slice trials need precision FP64";
+        if (c->proposal == AFQMC_PROPOSAL_MLP)
+            return "the learned proposal is defined for the one-slice real trial only";
+        if (c->rcache) return "complex or multi-slice trials need rcache = 0";
+        if (!trial_orbitals_c_supported(c->N, c->n_up) || !contract_fp64c_supported(c->N, c->n_up, c->n_dn))
+            return "sizes too large for the complex trial-orbital or contraction kernels";
+        if ((long long)c->K * c->trial_slices > 4096) return "too many hidden variables per sample";
+    }
     if (c->precision != AFQMC_PRECISION_FP64 && tc_kind(c) < 0)
         return "sizes not supported by the chosen tensor-core contraction (per-pair form: N <= 128, n_up <= 32; "
                "walker-side form: N <= 256, n_up <= 64)";
@@ -235,6 +257,12 @@ static Dims dims_of(const afqmc_config* c) {
     d.tc_tp = 0;
     d.cheb_threads = 0;
     if (c->wait_polls > 0) d.wait_polls = (uint32_t)c->wait_polls;
+    d.KU = c->K;
+    if (general_trial(c)) {   // complex storage of Phi; K counts the variables of every slice
+        d.cphi = 1;
+        d.slices = c->trial_slices;
+        d.K = c->K * c->trial_slices;
+    }
     return d;
 }
 
@@ -255,7 +283,9 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.h = (double*)take((G + 1) * NN * 8);
     w.L = w.h + NN;
     w.Phi0 = (double*)take(N * nu * 8);
-    w.U = (double*)take(K * NN * 8);
+    w.U = (double*)take((size_t)d.KU * NN * 8);
+    w.Pslice = d.slices > 1 ? (double*)take(NN * 8) : nullptr;
+    w.Vtmp = d.slices > 1 ? (double2*)take(pairs * N * nu * 16) : nullptr;
     w.Udf = c->precision != AFQMC_PRECISION_FP64 ? take(K * NN * 8) : nullptr;
     w.T = (double*)take(NN * 8);
     w.expT = (double*)take(NN * 8);
@@ -277,7 +307,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.phi = (double2*)take(W * N * nt * 16);
     w.weight = (double*)take(W * 8);
     w.x = (double*)take(pairs * K * 8);
-    w.Phi = (double*)take(pairs * N * nu * 8);
+    w.Phi = (double*)take(pairs * phi_stride(d) * 8);
     w.logdet = (double2*)take(pairs * 2 * 16);
     w.logov = (double2*)take(pairs * 16);
     w.Theta = (double2*)take(pairs * N * nt * 16);
@@ -310,7 +340,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
         w.comb_flag = (int*)take(2 * 4);
     }
     w.xsave = (double*)take(pairs * K * 8);
-    w.Phisave = (double*)take(pairs * N * nu * 8);
+    w.Phisave = (double*)take(pairs * phi_stride(d) * 8);
     w.msum0 = (double2*)take(W * 16);
     w.macc = (double2*)take(2 * W * 16);
     w.mout = (double2*)take((2 * W + 2) * 16);
@@ -322,7 +352,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     }
     w.xprop = (double*)take(pairs * K * 8);
     w.Sprop = (double*)take(pairs * NN * 8);
-    w.Phiprop = (double*)take(pairs * N * nu * 8);
+    w.Phiprop = (double*)take(pairs * phi_stride(d) * 8);
     w.logdet_prop = (double2*)take(pairs * 2 * 16);
     w.history = (double*)take((size_t)c->history_capacity * 4 * 8);
     w.reduce = (double*)take(8 * 8);
@@ -417,6 +447,39 @@ static cudaError_t trial_orbitals_of(afqmc_ctx* ctx, long long problems, double*
                              s_in_df(ctx));
 }
 
+// Trial orbitals Phi(x) of `problems` rows of X (the proposal or path variables):
+// S = sum_k x_k U_k and exp(S) Phi0, or, for a complex or multi-slice trial, the
+// chain exp(alpha S_m) P ... P exp(alpha S_1) Phi0 with S_l from the l-th block of
+// K variables (complex output).
+static cudaError_t trial_samples(afqmc_ctx* ctx, const double* X, long long problems, double* Out, const int* alive,
+                                 int P) {
+    const Dims& d = ctx->d;
+    Workspace& w = ctx->ws;
+    if (!d.cphi) {
+        cudaError_t e = form_S(ctx, X, problems);
+        return e != cudaSuccess ? e : trial_orbitals_of(ctx, problems, Out, alive, P);
+    }
+    const long long NN = (long long)d.N * d.N;
+    const double2 alpha = cmk(ctx->cfg.trial_alpha_re, ctx->cfg.trial_alpha_im);
+    double2* O = reinterpret_cast<double2*>(Out);
+    for (int l = 0; l < d.slices; ++l) {
+        gemm_nn_f64(ctx->stream, (int)problems, (int)NN, d.KU, 1.0, X + (size_t)l * d.KU, d.K, w.U, NN, 0.0, w.Sprop,
+                    NN);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (l == 0) {
+            e = trial_orbitals_c(ctx->stream, d.N, d.nu, problems, w.Sprop, alpha, w.Phi0, nullptr, O, alive, P, w.status);
+        } else {
+            e = slice_propagate(ctx->stream, d.N, d.nu, problems, w.Pslice, O, w.Vtmp, alive, P);
+            if (e == cudaSuccess)
+                e = trial_orbitals_c(ctx->stream, d.N, d.nu, problems, w.Sprop, alpha, nullptr, w.Vtmp, O, alive, P,
+                                     w.status);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // One Metropolis sweep of every path against the walker orbitals `orbitals`
 // (phi' during a step, phi during burn-in).
 static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t tag_prop, uint32_t tag_acc,
@@ -428,11 +491,14 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
     if (burn_in && p.proposal == AFQMC_PROPOSAL_MLP) p.proposal = AFQMC_PROPOSAL_PRIOR;   // no network output yet
     afqmc_status st;
     CK(propose(s, d, p, w.counters, tag_prop, tag_acc, sweep, w.x, w.alive, w.mlp.mu, w.mlp.logv, w.xprop));
-    CK(form_S(ctx, w.xprop, d.pairs));
+    if (!d.cphi) CK(form_S(ctx, w.xprop, d.pairs));
     if ((st = prof_mark(ctx, PH_PROPOSE)) != AFQMC_OK) return st;
-    CK(trial_orbitals_of(ctx, d.pairs, w.Phiprop, w.alive, d.P));
+    if (d.cphi)
+        CK(trial_samples(ctx, w.xprop, d.pairs, w.Phiprop, w.alive, d.P));
+    else
+        CK(trial_orbitals_of(ctx, d.pairs, w.Phiprop, w.alive, d.P));
     if ((st = prof_mark(ctx, PH_TRIAL)) != AFQMC_OK) return st;
-    CK(overlap_lu_both(s, d, w.Phiprop, (long long)d.N * d.nu, orbitals, w.logdet_prop, nullptr, w.alive, w.status,
+    CK(overlap_lu_both(s, d, w.Phiprop, phi_stride(d), orbitals, w.logdet_prop, nullptr, w.alive, w.status,
                        d.pairs, d.P));
     if ((st = prof_mark(ctx, PH_MCMC_OVERLAP)) != AFQMC_OK) return st;
     CK(accept(s, d, p, w.counters, tag_acc, sweep, w.logdet_prop, w.xprop, w.Phiprop, w.alive, w.mlp.mu, w.mlp.logv,
@@ -450,9 +516,9 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     const bool f16 = ctx->cfg.precision == AFQMC_PRECISION_FP16X3;
     const bool fp64 = ctx->cfg.precision == AFQMC_PRECISION_FP64;
     const int tck = fp64 ? -1 : tc_kind(&ctx->cfg);
-    const int ovl = fp64 ? (!w.rc && contract_fp64_walker_side(d.N, d.nu, d.nd, d.P) ? OVL_INVERSE : OVL_THETA)
+    const int ovl = fp64 ? (!w.rc && !d.cphi && contract_fp64_walker_side(d.N, d.nu, d.nd, d.P) ? OVL_INVERSE : OVL_THETA)
                          : (tck == 2 || tck == 5 ? OVL_TRIAL : OVL_THETA);
-    CK(overlap_lu_both(s, d, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
+    CK(overlap_lu_both(s, d, w.Phi, phi_stride(d), w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
                        ovl, tck == 5 && w.refine_items ? w.refine_th2 : nullptr));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64) {
@@ -460,13 +526,14 @@ static afqmc_status measure(afqmc_ctx* ctx) {
             CK(contract_tcw(s, d, w.tcw, w.Theta, w.phi, w.vpair, w.epair, w.status, f16));
             if (w.refine_items) {
                 // the pairs whose error would put their walker above refine_tol, again: selected
-                // by ||A_p^-1||_F^2 from the overlap kernel (the walker-side operand carries
-                // about 19 bits, hence u = 2^-19), their Theta formed in place of B, then the
-                // double-float per-pair contraction; the log-overlaps go to scratch
+                // by ||A_p^-1||_F^2 from the overlap kernel with the per-pair form's error model
+                // (measured per-pair errors of this form sit at 0.3-0.5 of it for N = 120 and 200),
+                // their Theta formed in place of B, then the double-float per-pair contraction;
+                // the log-overlaps go to scratch
                 CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2,
-                                 w.alive, w.refine_items, w.refine_n, w.counters, w.refine_th2, 0x1p-19));
+                                 w.alive, w.refine_items, w.refine_n, w.counters, w.refine_th2, 0x1p-20));
                 for (int spin = 0; spin < 2; ++spin)
-                    CK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet_new, w.Theta, nullptr,
+                    CK(overlap_lu(s, d, spin, w.Phi, phi_stride(d), w.phi, w.logdet_new, w.Theta, nullptr,
                                   w.status, d.pairs, d.P, OVL_THETA, nullptr, w.refine_items, w.refine_n));
                 CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n,
                                         d.pairs, w.hdf, w.Ldf));
@@ -486,7 +553,8 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     } else if (ovl == OVL_INVERSE)
         CK(contract_fp64_walker(s, d, w.h, w.L, w.Phi, w.Theta, w.phi, w.ywalk, w.vpair, w.epair));
     else
-        CK(contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
+        CK(d.cphi ? contract_fp64c(s, d, w.h, w.L, reinterpret_cast<const double2*>(w.Phi), w.Theta, w.vpair, w.epair)
+                  : contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
     if ((st = prof_mark(ctx, PH_CONTRACT)) != AFQMC_OK) return st;
     CK(walker_average(s, d, w.logdet, w.vpair, w.epair, w.logov, w.sumS, w.vbar, w.ebar));
     CK(energy_reduce(s, d, w.weight, w.ebar, w.sumS, w.reduce));
@@ -496,10 +564,18 @@ static afqmc_status measure(afqmc_ctx* ctx) {
 extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, const double* L, const double* Phi0,
                                    const double* U, void* workspace, size_t workspace_bytes, void* stream,
                                    afqmc_ctx** out) {
+    return afqmc_init_trial(cfg, h, L, Phi0, U, nullptr, workspace, workspace_bytes, stream, out);
+}
+
+extern "C" afqmc_status afqmc_init_trial(const afqmc_config* cfg, const double* h, const double* L,
+                                         const double* Phi0, const double* U, const double* slice_prop,
+                                         void* workspace, size_t workspace_bytes, void* stream, afqmc_ctx** out) {
     if (!out) return fail(AFQMC_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (const char* m = check_config(cfg)) return fail(AFQMC_ERR_ARG, "%s", m);
     if (!h || !L || !Phi0 || !U) return fail(AFQMC_ERR_ARG, "h, L, Phi0 and U must not be NULL");
+    if (cfg->trial_slices > 1 && !slice_prop)
+        return fail(AFQMC_ERR_ARG, "a multi-slice trial needs the propagator between slices (afqmc_init_trial)");
     size_t need = layout(cfg, nullptr, nullptr);
     if (!workspace || workspace_bytes < need)
         return fail(AFQMC_ERR_WORKSPACE, "workspace needs %zu bytes, got %zu", need, workspace_bytes);
@@ -527,7 +603,8 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         cudaError_t e = copy_in(w.h, h, NN * 8);
         if (e == cudaSuccess) e = copy_in(w.L, L, (size_t)d.G * NN * 8);
         if (e == cudaSuccess) e = copy_in(w.Phi0, Phi0, (size_t)d.N * d.nu * 8);
-        if (e == cudaSuccess) e = copy_in(w.U, U, (size_t)d.K * NN * 8);
+        if (e == cudaSuccess) e = copy_in(w.U, U, (size_t)d.KU * NN * 8);
+        if (e == cudaSuccess && w.Pslice) e = copy_in(w.Pslice, slice_prop, NN * 8);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.counters, 0, 16 * 8, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, 4, s);
         if (e != cudaSuccess) { st = fail(AFQMC_ERR_CUDA, "copying inputs: %s", cudaGetErrorString(e)); break; }
@@ -560,15 +637,18 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
             st = fail(AFQMC_ERR_CUDA, "double-float copies of U, L and exp(-tau T/2): %s", cudaGetErrorString(e));
             break;
         }
-        if ((e = form_S(ctx, w.xprop, d.W)) != cudaSuccess || (e = trial_orbitals_of(ctx, d.W, w.Phiprop, nullptr, 1)) != cudaSuccess) {
+        if ((e = trial_samples(ctx, w.xprop, d.W, w.Phiprop, nullptr, 1)) != cudaSuccess) {
             st = fail(AFQMC_ERR_CUDA, "initial walkers: %s", cudaGetErrorString(e));
             break;
         }
-        walkers_from_trial(s, d, w.Phiprop, w.phi_new);
+        if (d.cphi)
+            walkers_from_trial_c(s, d, reinterpret_cast<const double2*>(w.Phiprop), w.phi_new);
+        else
+            walkers_from_trial(s, d, w.Phiprop, w.phi_new);
         reorthonormalise(s, d, w.phi_new, w.phi, nullptr, w.status, d.W);
         // paths x_wp ~ N(0, I) and their orbitals
         fill_normals(s, w.x, d.pairs, d.K, p.woff * d.P, p.seed, TAG_INIT_PATH, w.counters, 0);
-        if ((e = form_S(ctx, w.x, d.pairs)) != cudaSuccess || (e = trial_orbitals_of(ctx, d.pairs, w.Phi, nullptr, d.P)) != cudaSuccess) {
+        if ((e = trial_samples(ctx, w.x, d.pairs, w.Phi, nullptr, d.P)) != cudaSuccess) {
             st = fail(AFQMC_ERR_CUDA, "initial paths: %s", cudaGetErrorString(e));
             break;
         }
@@ -576,7 +656,7 @@ extern "C" afqmc_status afqmc_init(const afqmc_config* cfg, const double* h, con
         set_int(s, w.alive, d.W, 1);
         if (w.rdirty) set_int(s, w.rdirty, d.pairs, 1);   // nothing cached yet
         for (int spin = 0; spin < 2; ++spin)
-            overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet_new, nullptr, nullptr, w.status,
+            overlap_lu(s, d, spin, w.Phi, phi_stride(d), w.phi, w.logdet_new, nullptr, nullptr, w.status,
                        d.pairs, d.P);
         combine_logdet(s, d.pairs, w.logdet_new, w.logov_cur);
         if ((e = cudaGetLastError()) != cudaSuccess) { st = fail(AFQMC_ERR_CUDA, "init kernels: %s", cudaGetErrorString(e)); break; }
@@ -628,7 +708,7 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         else
             CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive, w.propbuf));   // Eq. (12)
         if ((st = prof_mark(ctx, PH_PROPAGATE)) != AFQMC_OK) return st;
-        CK(overlap_lu_both(s, d, w.Phi, (long long)d.N * d.nu, w.phi_new, w.logdet_new, nullptr, w.alive, w.status,
+        CK(overlap_lu_both(s, d, w.Phi, phi_stride(d), w.phi_new, w.logdet_new, nullptr, w.alive, w.status,
                            d.pairs, d.P));
         CK(ratios(s, d, w.logov, w.logdet_new, w.sumS, w.logshift, w.alive, w.logov_cur, w.old_sum, w.ratio, w.Iabs));
         if ((st = prof_mark(ctx, PH_RATIO)) != AFQMC_OK) return st;
@@ -769,7 +849,7 @@ extern "C" afqmc_status afqmc_energy_paths(afqmc_ctx* ctx, int rounds, int sweep
     afqmc_status st = measure(ctx);   // at the propagation's paths
     if (st != AFQMC_OK) return st;
     CK(cudaMemcpyAsync(w.xsave, w.x, (size_t)d.pairs * d.K * 8, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(w.Phisave, w.Phi, (size_t)d.pairs * d.N * d.nu * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(w.Phisave, w.Phi, (size_t)d.pairs * phi_stride(d) * 8, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(w.msum0, w.sumS, (size_t)d.W * 16, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(w.logov_cur, w.logov, (size_t)d.pairs * 16, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(w.macc, 0, (size_t)d.W * 2 * 16, s));
@@ -782,7 +862,7 @@ extern "C" afqmc_status afqmc_energy_paths(afqmc_ctx* ctx, int rounds, int sweep
     }
     // the propagation's paths back; the measurement's acceptances are not the step's
     CK(cudaMemcpyAsync(w.x, w.xsave, (size_t)d.pairs * d.K * 8, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(w.Phi, w.Phisave, (size_t)d.pairs * d.N * d.nu * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(w.Phi, w.Phisave, (size_t)d.pairs * phi_stride(d) * 8, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(w.counters + 3, 0, 2 * 8, s));
     ctx->measured = false;
     if (st != AFQMC_OK) return st;
@@ -802,7 +882,7 @@ static const uint64_t STATE_MAGIC = 0x4146514D43535431ull;
 
 static size_t state_bytes(const Dims& d) {
     return 8 * 8 + (size_t)d.W * d.N * d.nt * 16 + (size_t)d.W * 8 + (size_t)d.pairs * d.K * 8 +
-           (size_t)d.pairs * d.N * d.nu * 8;
+           (size_t)d.pairs * phi_stride(d) * 8;
 }
 
 extern "C" afqmc_status afqmc_state_save(afqmc_ctx* ctx, void* buf, size_t* len) {
@@ -823,7 +903,7 @@ extern "C" afqmc_status afqmc_state_save(afqmc_ctx* ctx, void* buf, size_t* len)
     CK(cudaMemcpyAsync(p, ctx->ws.phi, b = (size_t)d.W * d.N * d.nt * 16, cudaMemcpyDeviceToHost, ctx->stream)); p += b;
     CK(cudaMemcpyAsync(p, ctx->ws.weight, b = (size_t)d.W * 8, cudaMemcpyDeviceToHost, ctx->stream)); p += b;
     CK(cudaMemcpyAsync(p, ctx->ws.x, b = (size_t)d.pairs * d.K * 8, cudaMemcpyDeviceToHost, ctx->stream)); p += b;
-    CK(cudaMemcpyAsync(p, ctx->ws.Phi, b = (size_t)d.pairs * d.N * d.nu * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(p, ctx->ws.Phi, b = (size_t)d.pairs * phi_stride(d) * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     *len = need;
     return AFQMC_OK;
@@ -843,7 +923,7 @@ extern "C" afqmc_status afqmc_state_load(afqmc_ctx* ctx, const void* buf, size_t
     CK(cudaMemcpyAsync(ctx->ws.phi, p, b = (size_t)d.W * d.N * d.nt * 16, cudaMemcpyHostToDevice, ctx->stream)); p += b;
     CK(cudaMemcpyAsync(ctx->ws.weight, p, b = (size_t)d.W * 8, cudaMemcpyHostToDevice, ctx->stream)); p += b;
     CK(cudaMemcpyAsync(ctx->ws.x, p, b = (size_t)d.pairs * d.K * 8, cudaMemcpyHostToDevice, ctx->stream)); p += b;
-    CK(cudaMemcpyAsync(ctx->ws.Phi, p, b = (size_t)d.pairs * d.N * d.nu * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->ws.Phi, p, b = (size_t)d.pairs * phi_stride(d) * 8, cudaMemcpyHostToDevice, ctx->stream));
     unsigned long long c[16] = {hdr[7]};
     CK(cudaMemcpyAsync(ctx->ws.counters, c, sizeof c, cudaMemcpyHostToDevice, ctx->stream));
     if (ctx->ws.rdirty) CK(set_int(ctx->stream, ctx->ws.rdirty, d.pairs, 1));   // every cached matrix is stale

@@ -85,7 +85,7 @@ extern "C" afqmc_status afqmc_autotune(afqmc_ctx* ctx, int* chosen) {
         Dims t = d;
         t.ov_wpb = wpb;
         float ms;
-        st = time_ms(s, [&] { return overlap_lu(s, t, 0, w.Phi, (long long)t.N * t.nu, w.phi, w.logdet, w.Theta, nullptr,
+        st = time_ms(s, [&] { return overlap_lu(s, t, 0, w.Phi, phi_stride(t), w.phi, w.logdet, w.Theta, nullptr,
                                                 w.status, t.pairs, t.P); }, reps, &ms);
         if (st != AFQMC_OK) return st;
         if (ms < best) { best = ms; best_wpb = wpb; }
@@ -97,7 +97,7 @@ extern "C" afqmc_status afqmc_autotune(afqmc_ctx* ctx, int* chosen) {
         const bool f16 = c.precision == AFQMC_PRECISION_FP16X3;
         const int ovl = tc_kind(&c) == 2 ? OVL_TRIAL : OVL_THETA;
         for (int spin = 0; spin < 2; ++spin)
-            BK(overlap_lu(s, d, spin, w.Phi, (long long)d.N * d.nu, w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs,
+            BK(overlap_lu(s, d, spin, w.Phi, phi_stride(d), w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs,
                           d.P, ovl));
         best = 1e30f;
         for (int tp : {0, 4, 2, 1}) {

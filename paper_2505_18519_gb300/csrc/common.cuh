@@ -147,7 +147,9 @@ struct Workspace {
     double* h;        // N*N
     double* L;        // G*N*N
     double* Phi0;     // N*n_up
-    double* U;        // K*N*N
+    double* U;        // KU*N*N (the operators U_k of one slice)
+    double* Pslice;   // N*N propagator between slices of a multi-slice trial (or null)
+    double2* Vtmp;    // pairs*N*n_up complex work of the multi-slice chain (or null)
     void* Udf;        // K*N*N double-float copy of U (mixed-precision path)
     double* T;        // N*N, h - 1/2 sum_g L_g L_g
     double* expT;     // N*N, exp(-tau T / 2)
@@ -233,7 +235,16 @@ struct Dims {
     // polls of an mbarrier before a tensor-core kernel's main wait gives up (sets
     // STATUS_TIMEOUT, drains its copies and MMAs with their own fixed bound, returns)
     uint32_t wait_polls = 1u << 26;
+    // complex trial orbitals (the complex or multi-slice trial, FP64 path): Phi is
+    // stored as N x n_up complex values per pair; K then counts the hidden
+    // variables of one sample (slices x the operators' count KU)
+    int cphi = 0;
+    int KU = 0;        // operators U_k (0: K)
+    int slices = 1;
 };
+
+// Doubles per pair of the trial orbitals Phi (N x n_up, real or complex).
+inline long long phi_stride(const Dims& d) { return (long long)d.N * d.nu * (d.cphi ? 2 : 1); }
 
 }  // namespace afq
 

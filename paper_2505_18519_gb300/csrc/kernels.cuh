@@ -115,6 +115,23 @@ cudaError_t contract_tcw_prepare(cudaStream_t st, const Dims& d, const double* h
 cudaError_t contract_tcw(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,
                          double2* vpair, double2* epair, int* status, bool f16);
 
+// trial_complex.cu: complex and multi-slice trial samples (FP64 path).
+// Out = exp(alpha S) V0 per problem (S real symmetric in S_all; V0 = the real
+// Phi0 when Vin is NULL, else Vin[problem], complex); Chebyshev series of
+// complex coefficients on the Gershgorin interval.
+bool trial_orbitals_c_supported(int N, int nu);
+cudaError_t trial_orbitals_c(cudaStream_t s, int N, int nu, long long problems, const double* S_all, double2 alpha,
+                             const double* Phi0, const double2* Vin, double2* Out, const int* alive, int P,
+                             int* status);
+// Out[problem] = Pm V[problem] (the fixed propagator between slices).
+cudaError_t slice_propagate(cudaStream_t s, int N, int nu, long long problems, const double* Pm, const double2* V,
+                            double2* Out, const int* alive, int P);
+cudaError_t walkers_from_trial_c(cudaStream_t s, const Dims& d, const double2* Phi_w, double2* phi);
+// The per-pair FP64 contraction with complex Phi (R_g = Phi^dagger X_g).
+bool contract_fp64c_supported(int N, int nu, int nd);
+cudaError_t contract_fp64c(cudaStream_t s, const Dims& d, const double* h, const double* L, const double2* Phi,
+                           const double2* Theta, double2* vpair, double2* epair);
+
 // walker.cu
 struct StepParams {
     uint64_t seed;

@@ -81,7 +81,7 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
                                   const double2* __restrict__ phi, double2* __restrict__ logdet,
                                   double2* __restrict__ Theta, const int* __restrict__ alive, int* status,
                                   int trial_side, double* __restrict__ th2, const int* __restrict__ list,
-                                  const int* __restrict__ n_list) {
+                                  const int* __restrict__ n_list, int cphi) {
     extern __shared__ double2 sm[];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
@@ -111,11 +111,21 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
     for (int e = lane; e < n * n; e += 32) {
         int a = e / n, b = e - a * n;
         double2 s = cmk(0.0, 0.0);
-        for (int i = 0; i < N; ++i) {
-            double f = Ph[(long long)i * nu + a];
-            double2 g = ph[(long long)i * nt + b];
-            s.x = fma(f, g.x, s.x);
-            s.y = fma(f, g.y, s.y);
+        if (cphi) {   // complex trial orbitals: A = Phi^dagger phi
+            const double2* Pc = reinterpret_cast<const double2*>(Ph);
+            for (int i = 0; i < N; ++i) {
+                const double2 f = Pc[(long long)i * nu + a];
+                const double2 g = ph[(long long)i * nt + b];
+                s.x = fma(f.x, g.x, fma(f.y, g.y, s.x));
+                s.y = fma(f.x, g.y, fma(-f.y, g.x, s.y));
+            }
+        } else {
+            for (int i = 0; i < N; ++i) {
+                double f = Ph[(long long)i * nu + a];
+                double2 g = ph[(long long)i * nt + b];
+                s.x = fma(f, g.x, s.x);
+                s.y = fma(f, g.y, s.y);
+            }
         }
         A[e] = s;
         bad |= !isfinite(s.x) || !isfinite(s.y);
@@ -297,7 +307,7 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
     long long blocks = (pairs + wpb - 1) / wpb;
     overlap_lu_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nt, n, col0, spin, pairs, P, Phi, Phi_stride,
                                                                phi, logdet, Theta, alive, status, trial_side, th2, list,
-                                                               n_list); count_launches(1);
+                                                               n_list, d.cphi); count_launches(1);
     return cudaGetLastError();
 }
 
@@ -311,7 +321,7 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
                                        const double* __restrict__ Phi, long long Phi_stride,
                                        const double2* __restrict__ phi, double2* __restrict__ logdet,
                                        double2* __restrict__ Theta, const int* __restrict__ alive, int* status,
-                                       int trial_side, double* __restrict__ th2) {
+                                       int trial_side, double* __restrict__ th2, int cphi) {
     extern __shared__ double2 sm[];
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -333,11 +343,21 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
     for (int e = hl; e < n * n; e += 16) {
         const int a = e / n, b = e - a * n;
         double2 s = cmk(0.0, 0.0);
-        for (int i = 0; i < N; ++i) {
-            const double f = Ph[(long long)i * nu + a];
-            const double2 g = ph[(long long)i * nt + b];
-            s.x = fma(f, g.x, s.x);
-            s.y = fma(f, g.y, s.y);
+        if (cphi) {   // complex trial orbitals: A = Phi^dagger phi
+            const double2* Pc = reinterpret_cast<const double2*>(Ph);
+            for (int i = 0; i < N; ++i) {
+                const double2 f = Pc[(long long)i * nu + a];
+                const double2 g = ph[(long long)i * nt + b];
+                s.x = fma(f.x, g.x, fma(f.y, g.y, s.x));
+                s.y = fma(f.x, g.y, fma(-f.y, g.x, s.y));
+            }
+        } else {
+            for (int i = 0; i < N; ++i) {
+                const double f = Ph[(long long)i * nu + a];
+                const double2 g = ph[(long long)i * nt + b];
+                s.x = fma(f, g.x, s.x);
+                s.y = fma(f, g.y, s.y);
+            }
         }
         A[e] = s;
         bad |= !isfinite(s.x) || !isfinite(s.y);
@@ -523,7 +543,8 @@ cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, lo
     if (e != cudaSuccess) return e;
     const long long blocks = (pairs + wpb - 1) / wpb;
     overlap_lu_both_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nd, d.nt, pairs, P, Phi, Phi_stride,
-                                                                    phi, logdet, Theta, alive, status, trial_side, th2);
+                                                                    phi, logdet, Theta, alive, status, trial_side, th2,
+                                                                    d.cphi);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -578,7 +578,8 @@ cudaError_t accept(cudaStream_t s, const Dims& d, const StepParams& p, const uns
                    uint32_t sweep, const double2* logdet_prop, const double* xprop, const double* Phiprop,
                    const int* alive, const float* mu, const float* logv, double2* logov_cur, double* x, double* Phi,
                    unsigned long long* counters, int* rdirty) {
-    accept_kernel<<<(unsigned)d.pairs, 128, 0, s>>>(d.N, d.nu, d.K, d.P, p.woff, p.seed, tag, sweep, ctr, p.proposal,
+    // the kernel copies N x nu doubles of an accepted pair's Phi: complex orbitals take twice as many
+    accept_kernel<<<(unsigned)d.pairs, 128, 0, s>>>(d.N, d.cphi ? 2 * d.nu : d.nu, d.K, d.P, p.woff, p.seed, tag, sweep, ctr, p.proposal,
                                                     p.mlp_mix, logdet_prop, xprop, Phiprop, alive, mu, logv, logov_cur, x,
                                                     Phi, counters, rdirty); count_launches(1);
     return cudaGetLastError();
@@ -811,7 +812,7 @@ cudaError_t population_control(cudaStream_t s, const Dims& d, const StepParams& 
                                             slot, from, flag);
     const long long rlen = Rc ? (long long)d.P * (d.G + 1) * d.N * d.nu : 0;
     CombRows rows{{(double*)phi, x, Phi, Rc},
-                  {(long long)d.N * d.nt * 2, (long long)d.P * d.K, (long long)d.P * d.N * d.nu, rlen},
+                  {(long long)d.N * d.nt * 2, (long long)d.P * d.K, (long long)d.P * phi_stride(d), rlen},
                   Rc ? rdirty : nullptr, d.P};
     comb_gather_kernel<<<2 * 152, 256, 0, s>>>(rows, slot, from, flag);
     count_launches(2);

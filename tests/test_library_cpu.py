@@ -124,3 +124,16 @@ def test_tensor_core_form_and_wait_limit_fields_reach_the_library(L):
     a = lib.workspace_bytes(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, **kw))
     b = lib.workspace_bytes(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, tc_form="walker", **kw))
     assert a > 0 and b > 0 and a != b
+
+
+def test_trial_fields_reach_the_library(L):
+    """The trial's alpha and slice count select the complex-trial contraction, and
+    the combinations it does not support are refused (host only)."""
+    c = lib.make_config(8, 4, 4, 32, 8, 8, 4, 0.01, 1, trial_alpha=-0.5j, trial_slices=2)
+    assert lib.contract_kernel(c) == "contract_fp64c_kernel"
+    real = lib.make_config(8, 4, 4, 32, 8, 8, 4, 0.01, 1)
+    assert lib.workspace_bytes(c) > lib.workspace_bytes(real)        # complex Phi, slice buffers
+    for kw in (dict(precision="fp16x3"), dict(proposal="mlp"), dict(rcache=True), dict(trial_slices=9),
+               dict(trial_alpha=0.0)):
+        bad = lib.make_config(8, 4, 4, 32, 8, 8, 4, 0.01, 1, **{"trial_alpha": -0.5j, **kw})
+        assert lib.workspace_bytes(bad) == 0, kw
