@@ -291,8 +291,9 @@ void afqmc_destroy(afqmc_ctx* ctx);
  * 4 propagation; 5 overlaps at phi' and ratios; 6 proposals and sum_k x_k U_k;
  * 7 trial orbitals exp(S) Phi0; 8 proposal overlaps; 9 acceptance;
  * 10 hand-off, re-orthonormalisation and bookkeeping; 11 population-control
- * comb (see pop_period). */
-#define AFQMC_PHASES 12
+ * comb (see pop_period); 12 error-controlled refinement of the tensor-core
+ * contraction (see refine_tol; it runs right after phase 1). */
+#define AFQMC_PHASES 13
 afqmc_status afqmc_profile(afqmc_ctx* ctx, int enable);
 afqmc_status afqmc_profile_read(afqmc_ctx* ctx, double* out, int len);
 

@@ -54,7 +54,7 @@ EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc
            "afqmc_noalloc_last_error")
 
 PHASES = ("overlap", "contract", "average", "fields", "propagate", "ratio", "propose", "trial_orbitals",
-          "mcmc_overlap", "accept", "finish", "comb")
+          "mcmc_overlap", "accept", "finish", "comb", "refine")
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:

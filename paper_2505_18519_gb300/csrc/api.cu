@@ -522,31 +522,10 @@ static afqmc_status measure(afqmc_ctx* ctx) {
                        ovl, tck == 5 && w.refine_items ? w.refine_th2 : nullptr));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64) {
-        if (tck == 5) {
+        if (tck == 5)
             CK(contract_tcw(s, d, w.tcw, w.Theta, w.phi, w.vpair, w.epair, w.status, f16));
-            if (w.refine_items) {
-                // the pairs whose error would put their walker above refine_tol, again: selected
-                // by ||A_p^-1||_F^2 from the overlap kernel with the per-pair form's error model
-                // (measured per-pair errors of this form sit at 0.3-0.5 of it for N = 120 and 200),
-                // their Theta formed in place of B, then the double-float per-pair contraction;
-                // the log-overlaps go to scratch
-                CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2,
-                                 w.alive, w.refine_items, w.refine_n, w.counters, w.refine_th2, 0x1p-20));
-                for (int spin = 0; spin < 2; ++spin)
-                    CK(overlap_lu(s, d, spin, w.Phi, phi_stride(d), w.phi, w.logdet_new, w.Theta, nullptr,
-                                  w.status, d.pairs, d.P, OVL_THETA, nullptr, w.refine_items, w.refine_n));
-                CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n,
-                                        d.pairs, w.hdf, w.Ldf));
-            }
-        } else {
+        else
             CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.Yimg, w.vpair, w.epair, w.status, f16));
-        }
-        if (tck != 5 && w.refine_items) {   // the pairs whose error would put their walker above refine_tol, again
-            CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2, w.alive,
-                             w.refine_items, w.refine_n, w.counters));
-            CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n,
-                                    d.pairs, w.hdf, w.Ldf));
-        }
     } else if (w.rc) {   // cached half-rotated matrices, refreshed for the paths that moved
         CK(rcache_refresh(s, d, w.h, w.Phi, w.rdirty, w.rlist, w.rcount, w.rc, w.counters));
         CK(contract_fp64r(s, d, w.rc, w.Theta, w.vpair, w.epair));
@@ -556,6 +535,26 @@ static afqmc_status measure(afqmc_ctx* ctx) {
         CK(d.cphi ? contract_fp64c(s, d, w.h, w.L, reinterpret_cast<const double2*>(w.Phi), w.Theta, w.vpair, w.epair)
                   : contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
     if ((st = prof_mark(ctx, PH_CONTRACT)) != AFQMC_OK) return st;
+    if (w.refine_items && tck == 5) {
+        // the pairs whose error would put their walker above refine_tol, again: selected
+        // by ||A_p^-1||_F^2 from the overlap kernel with the per-pair form's error model
+        // (measured per-pair errors of this form sit at 0.3-0.5 of it for N = 120 and 200),
+        // their Theta formed in place of B, then the double-float per-pair contraction;
+        // the log-overlaps go to scratch
+        CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2, w.alive,
+                         w.refine_items, w.refine_n, w.counters, w.refine_th2, 0x1p-20));
+        for (int spin = 0; spin < 2; ++spin)
+            CK(overlap_lu(s, d, spin, w.Phi, phi_stride(d), w.phi, w.logdet_new, w.Theta, nullptr, w.status, d.pairs,
+                          d.P, OVL_THETA, nullptr, w.refine_items, w.refine_n));
+        CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n, d.pairs,
+                                w.hdf, w.Ldf));
+    } else if (w.refine_items) {   // per-pair form: Theta is at hand
+        CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2, w.alive,
+                         w.refine_items, w.refine_n, w.counters));
+        CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n, d.pairs,
+                                w.hdf, w.Ldf));
+    }
+    if ((st = prof_mark(ctx, PH_REFINE)) != AFQMC_OK) return st;
     CK(walker_average(s, d, w.logdet, w.vpair, w.epair, w.logov, w.sumS, w.vbar, w.ebar));
     CK(energy_reduce(s, d, w.weight, w.ebar, w.sumS, w.reduce));
     return prof_mark(ctx, PH_AVERAGE);

@@ -260,7 +260,7 @@ cudaError_t raise_smem_limit(const void* kernel, size_t bytes);
 // Phases of a step timed by afqmc_profile (CUDA events on the context's stream).
 enum Phase : int {
     PH_OVERLAP = 0, PH_CONTRACT, PH_AVERAGE, PH_FIELDS, PH_PROPAGATE, PH_RATIO, PH_PROPOSE, PH_TRIAL,
-    PH_MCMC_OVERLAP, PH_ACCEPT, PH_FINISH, PH_COMB, PH_COUNT
+    PH_MCMC_OVERLAP, PH_ACCEPT, PH_FINISH, PH_COMB, PH_REFINE, PH_COUNT
 };
 }  // namespace afq
 

@@ -51,8 +51,10 @@ namespace {
 
 constexpr int TCW_THREADS = 192;        // warp 0 producer, warp 1 MMA issue, warps 2-5 epilogue
 constexpr int TCW_EPI = 128;            // epilogue threads (one per tensor-memory lane)
+constexpr int TCWZ_THREADS = 320;       // GEMM-Z: warp 0 producer, warp 1 MMA issue, warps 2-9 epilogue
+constexpr int TCWZ_EPI = 256;           // two epilogue warps per tensor-memory lane quadrant
 constexpr int TCW_MAXSTAGES = 4;
-constexpr size_t TCW_SMEM_MAX = 216 * 1024;   // dynamic; static use is about 7 KB of 227 KB
+constexpr size_t TCW_SMEM_MAX = 212 * 1024;   // dynamic; static use is about 11 KB of 227 KB
 constexpr uint32_t TCW_CHUNK_A = 32768; // one K chunk of a 128-row operand: 16 KB hi, 16 KB lo
 
 __host__ __device__ __forceinline__ int tcw_round16(int x) { return (x + 15) / 16 * 16; }
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(256) tcw_a_kernel(int N, int nt, int col0, int
 // Outputs: vpart[pair G1 + g] = Tr Z_{p,g} (float2; g = 0 is the one-body term),
 // exsum[pair] = sum_{g >= 1} Tr Z_{p,g}^2 (FP64 accumulation over the matrices).
 template <bool F16>
-__global__ void __launch_bounds__(TCW_THREADS, 1)
+__global__ void __launch_bounds__(TCWZ_THREADS, 1)
     contract_tcw_kernel(int n, int G1, int KZ, int KC, int NT, int GB, int NTILES, int P, int PB, int MT, int S,
                         int a_res, long long w0, const uint8_t* __restrict__ Aimg, const int* __restrict__ aexp,
                         const uint8_t* __restrict__ Yimg, const int* __restrict__ yexp, float2* __restrict__ vpart,
@@ -451,9 +453,10 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
     __shared__ uint64_t full_bar[TCW_MAXSTAGES], empty_bar[TCW_MAXSTAGES], dfull[2], dempty[2], a_bar, drain_bar;
     __shared__ uint32_t tslot;
     __shared__ volatile int fail;
-    __shared__ float2 red_tr[2][128], red_ex[2][128];
+    __shared__ float2 red_tr[2][2][128], red_ex[2][2][128];   // [matrix parity][column half][row]
     __shared__ double2 exacc[128];
     __shared__ int sA[128];
+    __shared__ float scl[128];                                 // 2^-yexp of the tile's columns
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long wl = blockIdx.x / MT;
@@ -564,76 +567,93 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
         }
         __syncwarp();
     } else {
-        // ---- epilogue (warps 2-5): lane r = (p_l, a) holds row a of Z_{p,g}
-        const int et = tid - 64;                         // 0 .. 127
+        // ---- epilogue (warps 2-9, two per tensor-memory lane quadrant): lane r = (p_l, a)
+        // holds row a of Z_{p,g}; half h of the warps takes the columns b of its half
+        const int et = tid - 64;                         // 0 .. 255
+        const int half = et >> 7;
         const int quarter = warp & 3;
         const int r = 32 * quarter + lane;
         const uint32_t lb = (uint32_t)(32 * quarter) << 16;
         const int pl = r / n, a = r % n;
         const bool row_ok = r < np * n;
-        const int er = sA[r];
+        const float rowf = p2f(-sA[r]);
+        const int nbh = (n + 1) >> 1;
+        const int bh0 = half * nbh, bh1 = min(n, bh0 + nbh);
         // per-pair sums: lpp consecutive threads share a pair's rows
         int lpp = 32;
-        while (lpp > 1 && lpp * PB > TCW_EPI) lpp >>= 1;
+        while (lpp > 1 && lpp * PB > TCWZ_EPI) lpp >>= 1;
         const int slot = et / lpp, q = et % lpp;
         const bool mine = slot < np;
         for (int t = 0; t < NTILES; ++t) {
             const int b = t & 1;
             const bool ok = wait_or_fail(&dfull[b], (uint32_t)((t >> 1) & 1), lim, &fail);
-            if (tc::named_sync_or<TCW_EPI>(!ok)) { failed = true; break; }
+            // column factors 2^-yexp of the tile's matrices (visible after the barrier below)
+            for (int e = et; e < GB * n; e += TCWZ_EPI) {
+                const int g = t * GB + e / n;
+                scl[e] = g < G1 ? p2f(-yex[(size_t)g * n + e % n]) : 0.f;
+            }
+            if (tc::named_sync_or<TCWZ_EPI>(!ok)) { failed = true; break; }
             tc::fence_after_sync();
             const uint32_t dh = taddr + lb + (uint32_t)b * dcols, dl = dh + (F16 ? (uint32_t)NT : 0u);
             for (int gl = 0; gl < GB; ++gl) {
                 const int g = t * GB + gl;
                 if (g >= G1) break;                              // uniform
-                const int c0 = gl * 2 * n, c1 = c0 + 2 * n;
-                for (int j0 = (c0 / 16) * 16; j0 < c1; j0 += 16) {
-                    float v[16];
-                    tc::tmem_ld16(dh + (uint32_t)j0, v);
-                    if (F16) {
-                        float w[16];
-                        tc::tmem_ld16(dl + (uint32_t)j0, w);
-                        tc::tmem_ld_wait();
+                const int c0 = gl * 2 * n + 2 * bh0, c1 = gl * 2 * n + 2 * bh1;
+                const float* sc = scl + gl * n;
+                for (int j0 = (c0 / 16) * 16; j0 < c1; j0 += 32) {   // up to two 16-column chunks per wait
+                    // the second chunk only while it holds columns of this range: reads stay inside the
+                    // buffer's NT columns (uniform across the warp)
+                    const bool two = j0 + 16 < c1;
+                    float v[32], w[32];
 #pragma unroll
-                        for (int qq = 0; qq < 16; ++qq) v[qq] += w[qq];
-                    } else {
-                        tc::tmem_ld_wait();
+                    for (int qq = 0; qq < 32; ++qq) v[qq] = w[qq] = 0.f;
+                    tc::tmem_ld16(dh + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(v));
+                    if (two) tc::tmem_ld16(dh + (uint32_t)(j0 + 16), *reinterpret_cast<float(*)[16]>(v + 16));
+                    if (F16) {
+                        tc::tmem_ld16(dl + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(w));
+                        if (two) tc::tmem_ld16(dl + (uint32_t)(j0 + 16), *reinterpret_cast<float(*)[16]>(w + 16));
+                    }
+                    tc::tmem_ld_wait();
+                    if (F16) {
+#pragma unroll
+                        for (int qq = 0; qq < 32; ++qq) v[qq] += w[qq];
                     }
                     if (row_ok) {
 #pragma unroll
-                        for (int qq = 0; qq < 16; ++qq) {
+                        for (int qq = 0; qq < 32; ++qq) {
                             const int col = j0 + qq;
                             if (col >= c0 && col < c1) {
-                                const int bb = (col - c0) >> 1;
-                                const float z = v[qq] * p2f(-(er + yex[g * n + bb]));
+                                const int bb = (col - gl * 2 * n) >> 1;
                                 float* dst = reinterpret_cast<float*>(&Ms[(size_t)r * ld + bb]);
-                                dst[(col - c0) & 1] = z;
+                                dst[col & 1] = v[qq] * rowf * sc[bb];
                             }
                         }
                     }
                 }
-                tc::named_sync<TCW_EPI>();                      // Ms holds Z_{p,g} of every pair of the tile
-                float2 tr = make_float2(0.f, 0.f), ex = make_float2(0.f, 0.f);
+                tc::named_sync<TCWZ_EPI>();                     // Ms holds Z_{p,g} of every pair of the tile
+                float2 tr = make_float2(0.f, 0.f);
+                float ex_x = 0.f, ex_y = 0.f;
                 if (row_ok) {
                     const float2* row = Ms + (size_t)r * ld;
                     const float2* col = Ms + (size_t)(pl * n) * ld + a;
-                    tr = row[a];
-                    float ex_x = 0.f, ex_y = 0.f;
-                    for (int bb = 0; bb < n; ++bb) {
+                    if (a >= bh0 && a < bh1) tr = row[a];
+                    for (int bb = bh0; bb < bh1; ++bb) {
                         const float2 x1 = row[bb], x2 = col[(size_t)bb * ld];
                         ex_x = fmaf(x1.x, x2.x, fmaf(-x1.y, x2.y, ex_x));
                         ex_y = fmaf(x1.x, x2.y, fmaf(x1.y, x2.x, ex_y));
                     }
-                    ex = make_float2(ex_x, ex_y);
                 }
-                red_tr[gl & 1][r] = tr;
-                red_ex[gl & 1][r] = ex;
-                tc::named_sync<TCW_EPI>();                      // Ms free for the next matrix, sums ready
+                red_tr[gl & 1][half][r] = tr;
+                red_ex[gl & 1][half][r] = make_float2(ex_x, ex_y);
+                tc::named_sync<TCWZ_EPI>();                     // Ms free for the next matrix, sums ready
                 float tx = 0.f, ty = 0.f, xx = 0.f, xy = 0.f;
                 if (mine)
                     for (int aa = q; aa < n; aa += lpp) {
-                        const float2 u = red_tr[gl & 1][slot * n + aa], w = red_ex[gl & 1][slot * n + aa];
-                        tx += u.x; ty += u.y; xx += w.x; xy += w.y;
+                        const int rr = slot * n + aa;
+                        const float2 u0 = red_tr[gl & 1][0][rr], u1 = red_tr[gl & 1][1][rr];
+                        const float2 w0 = red_ex[gl & 1][0][rr], w1 = red_ex[gl & 1][1][rr];
+                        tx += u0.x + u1.x; ty += u0.y + u1.y;
+                        xx += w0.x + w1.x; xy += w0.y + w1.y;
                     }
                 for (int o = 1; o < lpp; o <<= 1) {
                     tx += __shfl_xor_sync(0xffffffffu, tx, o);
@@ -648,11 +668,11 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
             }
             // buffer b has been read
             tc::fence_before_sync();
-            tc::named_sync<TCW_EPI>();
+            tc::named_sync<TCWZ_EPI>();
             if (et == 0) tc::mbar_arrive(&dempty[b]);
         }
         if (failed && et == 0) atomicOr(status, STATUS_TIMEOUT);
-        tc::named_sync<TCW_EPI>();
+        tc::named_sync<TCWZ_EPI>();
         if (!failed && et < np) exsum[pair0 + et] = exacc[et];
     }
     tc::fence_before_sync();
@@ -855,7 +875,7 @@ cudaError_t tcw_run(cudaStream_t st, const Dims& d, const TcwShape& s, const Tcw
                 s.KC, sp.NTILES, w.yimg, w.yexp, status, d.wait_polls);
             tcw_a_kernel<F16><<<(unsigned)(wb * sp.MT), 256, 0, st>>>(d.N, d.nt, col0, sp.n, d.P, sp.PB, sp.MT, s.N16,
                                                                       s.KC, w0, Bm, w.aimg, w.aexp);
-            contract_tcw_kernel<F16><<<(unsigned)(wb * sp.MT), TCW_THREADS, sp.smem, st>>>(
+            contract_tcw_kernel<F16><<<(unsigned)(wb * sp.MT), TCWZ_THREADS, sp.smem, st>>>(
                 sp.n, s.G1, s.KZ, s.KC, sp.NT, sp.GB, sp.NTILES, d.P, sp.PB, sp.MT, sp.S, sp.a_res, w0, w.aimg, w.aexp,
                 w.yimg, w.yexp, w.vpart[q], w.exsum[q], status, d.wait_polls);
             count_launches(3);
