@@ -7,11 +7,18 @@ leapfrog (overlaps, contraction for force bias and local energy, path
 averages and mixed estimator, fields, propagation, ratios, Metropolis path
 updates, hand-off constraint, re-orthonormalisation).
 
-Workload: the medium FP64 synthetic molecule -- N = 50 orbitals, 10 + 10
-electrons, 250 Cholesky vectors, 50 hidden variables, 512 walkers x 32 paths,
-tau = 0.005, one Metropolis sweep per step, synthetic inputs from
-afqmc_inputs (seed 1001).  With --gpus N (torchrun) every rank runs its own
-block of 512 walkers of one population (weak scaling).
+Headline workload: the mixed-precision synthetic molecule -- N = 120 orbitals,
+24 + 24 electrons, 600 Cholesky vectors, 120 hidden variables, 1024 walkers x
+64 paths, tau = 0.005, one Metropolis sweep per step (afqmc_inputs seed 1002) --
+on the mixed-precision path: the contraction on the tensor cores (walker-side
+form, split FP16, FP32 accumulation), the error-controlled double-float
+refinement of the pairs whose error would put their walker above 1e-4 Ha, the
+trial orbitals and propagation in double-float, overlaps, LU, weights and
+energy sums in FP64.  Beside it: the plain FP64 path on the same workload (a
+sample of walkers, from the same state: its time and the per-walker and mixed
+energy differences), and the other workloads as variants.  With --gpus N
+(torchrun) every rank runs its own block of walkers of one population (weak
+scaling).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -33,7 +40,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "medium_n50"
+WORKLOAD = "large_n120"          # the headline: the mixed-precision workload
+MEDIUM = "medium_n50"            # the medium FP64 workload of the variants
+HEADLINE_PATH = dict(precision="fp16x3", tc_form="walker", refine_tol=1e-4)
 METRIC = "walker-sample steps/s incl. local energy"
 UNIT = "walker-sample steps/s"
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 4 FP64 flop/clk
@@ -42,8 +51,8 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 L2_BYTES = 129e6
 
 
-def workload_desc(spec, run):
-    return (f"{WORKLOAD}: medium FP64 synthetic molecule, N={spec.N} orbitals, {spec.n_up}+{spec.n_dn} electrons, "
+def workload_desc(spec, run, name=WORKLOAD):
+    return (f"{name}: synthetic molecule, N={spec.N} orbitals, {spec.n_up}+{spec.n_dn} electrons, "
             f"{spec.n_chol} Cholesky vectors, K={spec.K} hidden variables, {run.n_walkers} walkers x "
             f"{run.n_paths} paths per GPU, tau={run.dtau}, 1 Metropolis sweep/step")
 
@@ -145,24 +154,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU) legs
+ORACLE_PATHS = 4   # paths per walker of the CPU sample (the oracle's pair cost does not depend on P)
+
+
 def _oracle_walker_job(args):
-    """Run in a spawned process: the oracle's own step on one walker of the
-    workload.  With ``state`` given, one timed step from that state; otherwise
-    the walker is initialised by the oracle and ``n_warm`` + ``n_timed`` steps
-    run, the last ``n_timed`` timed.  Returns the list of timed step seconds."""
-    state, widx, n_warm, n_timed = args
+    """Run in a spawned process: the oracle, as it stands, on one walker of the
+    headline workload with ORACLE_PATHS paths: initialised by the oracle (two
+    burn-in sweeps), then ``n_warm`` + ``n_timed`` steps, the last ``n_timed``
+    timed.  Returns the list of timed step seconds."""
+    widx, n_warm, n_timed = args
     import numpy as np
     import afqmc_inputs as ai
     from oracle import afqmc as oa
     spec, run = ai.CONFIGS[WORKLOAD]
     s = ai.make_system(spec)
     ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, run.dtau)
-    cfg = oa.OracleConfig(dtau=run.dtau, n_walkers=1, n_paths=run.n_paths, seed=ai.philox_run_seed(1))
-    if state is None:
-        st = oa.init(ham, cfg, walker_index=np.array([widx]))
-    else:
-        st = oa.State(state["step"], state["phi_up"], state["phi_dn"], state["weight"], state["x"], state["Phi"],
-                      walker_index=np.array([widx]))
+    cfg = oa.OracleConfig(dtau=run.dtau, n_walkers=1, n_paths=ORACLE_PATHS, seed=ai.philox_run_seed(2), n_burn=2)
+    st = oa.init(ham, cfg, walker_index=np.array([widx]))
     times = []
     for k in range(n_warm + n_timed):
         t0 = time.perf_counter()
@@ -172,7 +180,7 @@ def _oracle_walker_job(args):
     return times
 
 
-def oracle_pool_steps(n_walkers, states, n_warm, n_timed, spread):
+def oracle_pool_steps(n_walkers, n_warm, n_timed):
     """Run the oracle on ``n_walkers`` walkers of the workload, one walker per
     spawned process, all at once; returns (per-step wall seconds, processes)."""
     import multiprocessing as mp
@@ -180,11 +188,7 @@ def oracle_pool_steps(n_walkers, states, n_warm, n_timed, spread):
     # one BLAS thread per process (set before the spawned children import numpy)
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
-    jobs = []
-    for i in range(n_walkers):
-        widx = i * spread
-        st = None if states is None else states[i]
-        jobs.append((st, widx, n_warm, n_timed))
+    jobs = [(i, n_warm, n_timed) for i in range(n_walkers)]
     with mp.get_context("spawn").Pool(procs) as pool:
         res = pool.map(_oracle_walker_job, jobs)
     # walkers run concurrently: a step's wall time is the slowest walker's, per round of `procs` walkers
@@ -193,23 +197,20 @@ def oracle_pool_steps(n_walkers, states, n_warm, n_timed, spread):
     return per_step, procs
 
 
-def cpu_baseline_leg(gpu_state, run):
-    """The oracle, as it stands, on a bounded sample: one step of 16 walkers of
-    the same workload from the GPU's state, one walker per process."""
-    import numpy as np
-    n = 16
-    spread = run.n_walkers // n
-    states = []
-    for i in range(n):
-        w = i * spread
-        states.append(dict(step=gpu_state["step"], phi_up=gpu_state["phi_up"][w:w + 1],
-                           phi_dn=gpu_state["phi_dn"][w:w + 1], weight=gpu_state["weight"][w:w + 1],
-                           x=gpu_state["x"][w:w + 1], Phi=gpu_state["Phi"][w:w + 1]))
-    per_step, procs = oracle_pool_steps(n, states, 0, 1, spread)
-    value = n * run.n_paths / per_step[0]
-    return {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
-            "sample": f"1 step of {n} of the {run.n_walkers} walkers (x{run.n_paths} paths each) of {WORKLOAD}, "
-                      f"from the GPU run's state, one walker per process, {procs} processes"}
+def _sample_desc(n, procs, run):
+    return (f"{n} walkers x {ORACLE_PATHS} paths (of the {run.n_walkers} x {run.n_paths} of {WORKLOAD}), "
+            f"oracle-initialised (2 burn-in sweeps), one walker per process, {procs} processes on "
+            f"{os.cpu_count()} host cores; the oracle's cost per walker-path pair does not depend on the "
+            f"paths per walker")
+
+
+def cpu_baseline_leg(run):
+    """The oracle, as it stands, on a bounded sample of the workload: one step
+    of every host core's walker."""
+    n = os.cpu_count() or 1
+    per_step, procs = oracle_pool_steps(n, 0, 1)
+    value = n * ORACLE_PATHS / per_step[0]
+    return {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": _sample_desc(n, procs, run)}
 
 
 def reference_arm(args):
@@ -218,17 +219,16 @@ def reference_arm(args):
     if rank != 0:
         return
     spec, run = ai.CONFIGS[WORKLOAD]
-    n = 16
-    per_step, procs = oracle_pool_steps(n, None, args.warmup, args.steps, run.n_walkers // n)
+    n = os.cpu_count() or 1
+    per_step, procs = oracle_pool_steps(n, args.warmup, args.steps)
     total = sum(per_step)
-    value = n * run.n_paths * args.steps / total
+    value = n * ORACLE_PATHS * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(spec, run)},
             "cpu_baseline": {"kind": "oracle", "cores": procs, "value": value, "unit": UNIT,
-                             "sample": f"each step: {n} of the {run.n_walkers} walkers (x{run.n_paths} paths), "
-                                       f"oracle-initialised, one walker per process, {procs} processes"},
+                             "sample": "each step: " + _sample_desc(n, procs, run)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -264,11 +264,41 @@ def recorded_traffic(kernel_source: str, summary: str = "contract_fp64_medium_n5
             fields[k.strip()] = v.strip().strip("`")
     if fields.get("source_sha256_16") != digest:
         return None
-    try:
-        return float(fields["dram_bytes_per_full_launch"])
-    except (KeyError, ValueError):
-        return None
+    for key in ("dram_bytes_per_full_launch", "dram_bytes_per_pair"):
+        try:
+            return float(fields[key])
+        except (KeyError, ValueError):
+            continue
+    return None
 
+
+
+TCW_TRAFFIC = ("contract_tcw_large_n120.md", "// ---------------------------------------------------------------- per pair: v_g and E_L",
+               "// ---------------------------------------------------------------- GEMM-Z and the traces")
+
+
+def tcw_traffic(W, P):
+    """DRAM bytes of the GEMM-Z kernel per contraction of the headline workload,
+    from its committed ncu summary (taken on a smaller population of the same
+    system and scaled by pairs, as the summary states), or None if the kernel's
+    device code changed since."""
+    per_pair = recorded_traffic(os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "contract_tcw.cu"),
+                                TCW_TRAFFIC[0], TCW_TRAFFIC[1], TCW_TRAFFIC[2])
+    return None if per_pair is None else per_pair * W * P
+
+
+_FP64_PEAK = {}
+
+
+def fp64_peak():
+    """Measured FP64 FMA rate of this GPU (TFLOP/s) and where it came from."""
+    if "v" not in _FP64_PEAK:
+        from paper_2505_18519_gb300 import afqmc as lib
+        try:
+            _FP64_PEAK["v"] = (lib.fp64_fma_rate(), "measured: FP64 FMA loop (afqmc_fp64_fma_rate)")
+        except Exception:
+            _FP64_PEAK["v"] = (FP64_PEAK_GFLOPS / 1e3, "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz")
+    return _FP64_PEAK["v"]
 
 
 # ------------------------------------------------------------------ the widened paths
@@ -378,6 +408,35 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
     out = {}
     steps, warmup = args.steps, args.warmup
 
+    if only in (None, "fp64", "mixed"):
+        # the medium workload on the plain FP64 path with the cached half-rotated matrices
+        cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
+                              walker_offset=rank * W, e_shift=28.5, rcache=True)
+        ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
+        state0 = ctx.save_state()
+        ew64 = ctx.energy(walkers=True)["e_walker"]
+        for _ in range(warmup):
+            ctx.step(1)
+        ctx.profile(True)
+        ms, clocks, launches = _timed(ctx.step, lambda: torch.cuda.synchronize(dev), ctx.stream, steps, world, local)
+        prof = ctx.profile_read()
+        hist64 = ctx.history(warmup + steps)
+        ctx.close()
+        cms = prof["ms"]["contract"] / max(1, prof["steps"])
+        flops_pp = contract_flops_per_pair(spec) * W * P
+        peak, psrc = fp64_peak()
+        out["fp64_medium"] = {
+            "precision": "fp64", "what": workload_desc(spec, run, MEDIUM) + "; FP64 with the cached half-rotated "
+            "matrices (rcache = 1), 20 burn-in sweeps",
+            "value": W * P * world * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "gpu_launches": launches, "clocks": clocks,
+            "roofline": {"bound": "alu", "kernel": lib.contract_kernel(cfg), "ms_per_launch": cms,
+                         "achieved_per_pair_count": flops_pp / (cms / 1e3) / 1e12, "peak": peak, "peak_source": psrc,
+                         "unit": "TFLOP/s", "frac_per_pair_count": flops_pp / (cms / 1e3) / 1e12 / peak,
+                         "note": "per-pair algorithmic count; the cached form executes fewer FP64 operations "
+                                 "(M = R Theta plus the refreshed pairs)"},
+            "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
+
     if only in (None, "mixed"):
         cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
                               walker_offset=rank * W, e_shift=28.5, precision="fp16x3")
@@ -470,7 +529,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         out["learned_proposal"] = d
 
     if only in (None, "batched"):
-        specs = ai.batched_system_specs(16, n_range=(40, 125))
+        specs = ai.batched_system_specs(16)
         Wb, Pb = 256, 16
         ctxs = []
         for i, sp in enumerate(specs):
@@ -491,7 +550,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             c.close()
         units = len(specs) * Wb * Pb * world
         out["batched_uneven"] = {
-            "precision": "fp16x3", "what": f"{len(specs)} synthetic molecules, N ~ U[40,125] (N = "
+            "precision": "fp16x3", "what": f"{len(specs)} synthetic molecules, N ~ U[40,200] (N = "
             f"{','.join(str(sp.N) for sp in specs)}), n = N/5 per spin, n_chol = 5N, K = N, {Wb} walkers x {Pb} "
             "paths each, autotuned launch shapes, one CUDA-graph launch per step for the whole batch",
             "value": units * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
@@ -623,12 +682,50 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             "value": W4 * P4 * world * st4 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / st4,
             "full_workload_step_s_extrapolated": ms / st4 / 1e3 * (run4.n_walkers * run4.n_paths) / (W4 * P4),
             "gpu_launches": launches, "clocks": clocks,
-            "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3,
-                         "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
-                         "flops_per_launch": flops, "ms_per_launch": cms},
+            "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": fp64_peak()[0],
+                         "peak_source": fp64_peak()[1], "unit": "TFLOP/s", "frac": achieved / fp64_peak()[0],
+                         "traffic": None, "flops_per_launch": flops, "ms_per_launch": cms},
             "phases_ms_per_step": {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}}
 
-    if only in (None, "large_mixed"):
+    if only in (None, "largest_mixed"):
+        # the learned-proposal workload's system (N = 200, 40 + 40 electrons, 1000 Cholesky vectors,
+        # K = 200, 16 paths) on a quarter of its 2048 walkers: the mixed-precision step with the general
+        # walker-side tensor-core form and its refinement, and the learned proposal trained online
+        try:
+            spec4, run4 = ai.CONFIGS["largest_n200"]
+            sy = ai.make_system(spec4)
+            W4, P4 = 512, run4.n_paths
+            c = lib.make_config(spec4.N, spec4.n_up, spec4.n_dn, spec4.n_chol, spec4.K, W4, P4, run4.dtau,
+                                ai.philox_run_seed(4), n_burn=40, walker_offset=rank * W4, precision="fp16x3",
+                                tc_form="walker", refine_tol=1e-4, proposal="mlp", mlp_train=True)
+            ctx = lib.Context(c, sy.h, sy.L, sy.Phi0, sy.U, device=dev)
+            ctx.step(2)
+            ctx.profile(True)
+            r0 = ctx.stats()["refined_pairs"]
+            ms, clocks, launches = _timed(ctx.step, lambda: torch.cuda.synchronize(dev), ctx.stream, 2, world, local)
+            prof = ctx.profile_read()
+            st4 = ctx.stats()
+            hist = ctx.history(2)
+            ctx.close()
+            del ctx
+            torch.cuda.empty_cache()
+            ph = {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}
+            flops = contract_flops_per_pair(spec4) * W4 * P4
+            out["largest_mixed_learned"] = {
+                "precision": "fp16x3", "proposal": "mlp (trained online)", "kernel": lib.contract_kernel(c),
+                "what": workload_desc(spec4, run4, "largest_n200") + f"; {W4} of its {run4.n_walkers} walkers, 40 "
+                        "burn-in sweeps, 2 untimed and 2 timed steps",
+                "value": W4 * P4 * world * 2 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / 2,
+                "gpu_launches": launches, "clocks": clocks,
+                "acceptance": float(hist[:, 3].sum() / (2 * W4 * P4)),
+                "refined_frac": (st4["refined_pairs"] - r0) / (2 * W4 * P4),
+                "live_walkers": int(st4["live_walkers"]), "device_status": int(st4["status"]),
+                "tensor_contraction_tflops": flops / (ph["contract"] / 1e3) / 1e12 if ph["contract"] > 0 else None,
+                "phases_ms_per_step": ph}
+        except Exception as exc:   # the measurement is optional; the line must still print
+            out["largest_mixed_learned"] = {"error": f"{type(exc).__name__}: {exc}"}
+
+    if only == "large_mixed":
         # the mixed-precision workload's system (N = 120, 24 + 24 electrons, 600 Cholesky
         # vectors, 64 paths) on 128 walkers: per-walker error against the FP64 path from
         # one state, with and without the error-controlled FP64 refinement, and step times
@@ -676,6 +773,50 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
 
 
 # ------------------------------------------------------------------ our arm
+def tcw_flops_per_pair(spec, P):
+    """MMA-free count of the walker-side association per pair: Z = B^T Y
+    (complex x complex, 8 N (n_up^2 + n_dn^2) per matrix) plus the pair's share of
+    Y_g = X_g phi_w (4 N^2 (n_up + n_dn) per matrix, once per walker) and the
+    traces (8 (n_up^2 + n_dn^2) per matrix)."""
+    N, nu, nd, G = spec.N, spec.n_up, spec.n_dn, spec.n_chol
+    s2 = nu * nu + nd * nd
+    return (G + 1) * (8 * N * s2 + 4 * N * N * (nu + nd) / P) + G * 8 * s2
+
+
+def fp64_sample_leg(lib, s, spec, run, seed, rank, W, dev, state0, ew_mixed, local, world, n_walk=64):
+    """The plain FP64 path on the headline workload from the mixed run's
+    initial state, on its first ``n_walk`` walkers: the per-walker energy
+    difference at that state, the mixed energy difference over the sample, and
+    two timed steps (the full-workload step time extrapolated by walkers)."""
+    import numpy as np
+    import torch
+    from paper_2505_18519_gb300 import afqmc as L
+    Ws, P = min(n_walk, W), run.n_paths
+    st = L.unpack_state(state0)
+    sub = dict(step=st["step"], phi_up=st["phi_up"][:Ws], phi_dn=st["phi_dn"][:Ws], weight=st["weight"][:Ws],
+               x=st["x"][:Ws], Phi=st["Phi"][:Ws])
+    cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, Ws, P, run.dtau, seed, n_burn=0,
+                          walker_offset=rank * W)
+    ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
+    ctx.load_state_arrays(sub)
+    e64 = ctx.energy(walkers=True)
+    dw = np.abs(e64["e_walker"] - ew_mixed[:Ws])
+    live = sub["weight"] > 0
+    wr = sub["weight"][live]
+    emix_mixed = float(np.sum(wr * ew_mixed[:Ws][live].real) / np.sum(wr))
+    ctx.step(1)
+    ms, clocks, _ = _timed(ctx.step, lambda: torch.cuda.synchronize(dev), ctx.stream, 2, world, local)
+    ctx.close()
+    return {"precision": "fp64", "kernel": lib.contract_kernel(cfg),
+            "what": f"the plain FP64 path on the first {Ws} walkers (x{P} paths) of the same workload, from the "
+                    "mixed run's initial state; 1 untimed and 2 timed steps",
+            "ms_per_step_sample": ms / 2, "value_sample": Ws * P * world * 2 / (ms / 1e3),
+            "full_workload_ms_per_step_extrapolated": ms / 2 * W / Ws,
+            "dE_walker_ha": {"max": float(dw[live].max()), "median": float(np.median(dw[live])),
+                             "frac_above_1e-4": float(np.mean(dw[live] > 1e-4)), "walkers": int(live.sum())},
+            "dE_mix_ha": abs(float(e64["e_mix"]) - emix_mixed), "clocks": clocks}
+
+
 def our_arm(args):
     import numpy as np
     import torch
@@ -683,7 +824,7 @@ def our_arm(args):
     import afqmc_inputs as ai
     from paper_2505_18519_gb300 import afqmc as lib
     from paper_2505_18519_gb300 import build
-    from paper_2505_18519_gb300.sharding import max_over_ranks
+    from paper_2505_18519_gb300.sharding import combine_mixed, max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -698,33 +839,37 @@ def our_arm(args):
         dist.barrier()
     lib.load_library()
 
+    # medium workload: the variants that predate the headline's workload
+    spec1, run1 = ai.CONFIGS[MEDIUM]
+    s1 = ai.make_system(spec1)
+    if args.only:
+        # one widened path alone (a profiling run): no headline, no baselines
+        with torch.cuda.device(dev):
+            v = run_variants(args, lib, s1, spec1, run1, ai.philox_run_seed(1), rank, world, dev, None, None, local,
+                             only=args.only)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "variants": v}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     spec, run = ai.CONFIGS[WORKLOAD]
     if args.walkers:
         import dataclasses
         run = dataclasses.replace(run, n_walkers=args.walkers)
     s = ai.make_system(spec)
     W, P = run.n_walkers, run.n_paths
-    seed = ai.philox_run_seed(1)
-    if args.only:
-        # one widened path alone (a profiling run): no headline, no baselines
-        with torch.cuda.device(dev):
-            v = run_variants(args, lib, s, spec, run, seed, rank, world, dev, None, None, local, only=args.only)
-        if rank == 0:
-            print(json.dumps({"only": args.only, "variants": v}), flush=True)
-        if world > 1:
-            dist.destroy_process_group()
-        return
+    seed = ai.philox_run_seed(2)
     cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau, seed, n_burn=20,
-                          walker_offset=rank * W, e_shift=28.5, rcache=not args.no_rcache)
+                          walker_offset=rank * W, **HEADLINE_PATH)
     with torch.cuda.device(dev):
         ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, device=dev)
         stream = ctx.stream
-        state0 = ctx.save_state()                        # the mixed-precision run starts from this state
-        ew64 = ctx.energy(walkers=True)["e_walker"]
+        state0 = ctx.save_state()
+        ew0 = ctx.energy(walkers=True)["e_walker"]
         for _ in range(args.warmup):
             ctx.step(1)
         torch.cuda.synchronize(dev)
-
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
@@ -732,7 +877,7 @@ def our_arm(args):
             if world > 1:
                 dist.barrier()
             torch.cuda.synchronize(dev)
-            formed0 = ctx.stats()["rcache_formed"]
+            refined0 = ctx.stats()["refined_pairs"]
             torch.cuda.synchronize(dev)
             l0 = lib.launch_count()
             e0.record(stream)
@@ -740,7 +885,7 @@ def our_arm(args):
             e1.record(stream)
             torch.cuda.synchronize(dev)
             l1 = lib.launch_count()
-            refreshed = (ctx.stats()["rcache_formed"] - formed0) / args.steps
+            stats = ctx.stats()
             if world > 1:
                 dist.barrier()
         prof = ctx.profile_read()
@@ -749,14 +894,15 @@ def our_arm(args):
         ms_max = max_over_ranks(ms)
         clocks = clk.summary()
         hist = ctx.history(args.steps)
-        hist_all = ctx.history(args.warmup + args.steps)
-        gpu_state = ctx.state_arrays() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
         ctx.close()
         del ctx
         torch.cuda.empty_cache()
+        # the global mixed estimate of the last timed step: every rank's sums, all-reduced
+        emix_global = combine_mixed((hist[-1, 0], hist[-1, 1], hist[-1, 2])) if len(hist) else None
 
-        # end to end through the public API: host (pinned) inputs uploaded by
-        # afqmc_init inside the timed region, every step's energy record read back
+        # end to end through the public API: host (pinned) inputs uploaded by afqmc_init
+        # (its 20 burn-in sweeps included) inside the timed region, then the K steps, each
+        # followed by a device-to-host read of its energy record
         host = [torch.from_numpy(a).pin_memory() for a in (s.h, s.L, s.Phi0, s.U)]
         h2d = sum(t.numel() * 8 for t in host)
         e2e_s = None
@@ -772,30 +918,51 @@ def our_arm(args):
             t1 = time.perf_counter()
             e2e_s = max_over_ranks(t1 - t0)
             ctx2.close()
+            del ctx2
+            torch.cuda.empty_cache()
+        fp64 = fp64_sample_leg(lib, s, spec, run, seed, rank, W, dev, state0, ew0, local, world)
         variants = None
         if not args.no_variants:
-            variants = run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist_all, local,
-                                    state0=state0)
+            variants = run_variants(args, lib, s1, spec1, run1, ai.philox_run_seed(1), rank, world, dev, None, None,
+                                    local)
 
     pairs_total = W * P * world
     value = pairs_total * args.steps / (ms_max / 1e3)
     e2e_value = pairs_total * args.steps / e2e_s if e2e_s else None
-    # the contraction of one step (for the walker-side form: the orbital layout, the
-    # GEMM forming Y_g = X_g phi_w for all walkers, and the pair kernel)
-    contract_ms = prof["ms"]["contract"] / max(1, prof["steps"])
-    kernel = lib.contract_kernel(cfg)
-    flops_pair_order = contract_flops_per_pair(spec) * W * P
-    if kernel == "contract_fp64r_kernel":
-        flops = contract_flops_cached(spec) * W * P + contract_flops_refresh(spec) * refreshed
-    elif kernel == "contract_fp64z_kernel":
-        flops = contract_flops_walker_side(spec, P) * W * P
-    else:
-        flops = flops_pair_order
-    achieved = flops / (contract_ms / 1e3) / 1e12
-    traffic = recorded_traffic(os.path.join(ROOT, "paper_2505_18519_gb300", "csrc",
-                                            FP64_SOURCE.get(kernel, "contract_fp64.cu")),
-                               *FP64_TRAFFIC[kernel]) if kernel in FP64_TRAFFIC and (W, P) == (512, 32) else None
-    phases = {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}
+    steps_p = max(1, prof["steps"])
+    phases = {k: round(v / steps_p, 3) for k, v in prof["ms"].items()}
+    # the tensor-core contraction (Y images, pair images, GEMM-Z, per-pair finish) against the
+    # measured sustained BF16 peak, on the paper's per-pair algorithmic count and on the
+    # walker-side association's own count; the refinement (double-float per-pair kernel on the
+    # CUDA cores) is reported beside it
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    peak_src = "measured bf16 sustained" if peaks.get("bf16_tflops_sustained") else "fallback sustained bf16"
+    c_ms, r_ms = phases["contract"], phases["refine"]
+    flops = contract_flops_per_pair(spec) * W * P
+    flops_ws = tcw_flops_per_pair(spec, P) * W * P
+    achieved = flops / (c_ms / 1e3) / 1e12
+    refined_per_step = (stats["refined_pairs"] - refined0) / args.steps
+    roof_tc = {"bound": "tensor", "kernel": "contract_tcw_kernel (+ tcw_y_kernel, tcw_a_kernel, tcw_finish_kernel)",
+               "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+               "peak_source": peak_src + " (fp16 nominal ratio 1)",
+               "traffic": tcw_traffic(W, P), "flops_per_launch": flops, "ms_per_launch": c_ms,
+               "flops_per_launch_walker_side": flops_ws, "frac_walker_side": flops_ws / (c_ms / 1e3) / 1e12 / peak,
+               "mma_products_per_real_product": 4,
+               "note": "one contraction per step; flops_per_launch is the per-pair algorithmic count (R = Phi^T X, "
+                       "M = R Theta: 2 n N^2 + 4 N (n_up^2 + n_dn^2) + traces per matrix); the walker-side "
+                       "association executes flops_per_launch_walker_side in 4 split-FP16 MMA products each; "
+                       "traffic is the GEMM-Z kernel's DRAM bytes per contraction"}
+    rf_flops = contract_flops_per_pair(spec) * refined_per_step
+    roof_rf = {"bound": "alu", "kernel": "contract_fp64_kernel<double-float> (refinement of the listed pairs)",
+               "ms_per_launch": r_ms, "pairs_per_launch": refined_per_step,
+               "refined_frac": refined_per_step / (W * P),
+               "achieved": rf_flops / (r_ms / 1e3) / 1e12 if r_ms > 0 else None, "unit": "TFLOP/s (double-float)",
+               "peak": None, "frac": None, "traffic": None,
+               "note": "recomputes in double-float (about 44 bits) the pairs whose estimated tensor-core error would "
+                       "put their walker above refine_tol; CUDA-core FP32 pipe"}
+    dominant = roof_tc if c_ms >= r_ms else dict(roof_rf, tensor_contraction=roof_tc)
 
     if world > 1:
         dist.barrier()
@@ -803,36 +970,30 @@ def our_arm(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    cpu = cpu_baseline_leg(gpu_state, run) if gpu_state is not None else None
+    cpu = cpu_baseline_leg(run) if (world == 1 and not args.no_cpu_baseline) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "fp16x3 contraction (split FP16 on tensor cores, FP32 accumulation) + double-float refinement; "
+                 "f64 overlaps, LU, weights, energy sums",
+        "data": "synthetic",
         "config": {"workload": workload_desc(spec, run), "walkers_total": W * world, "paths": P,
-                   "system_seed": spec.seed, "philox_seed": seed,
-                   "l2": f"working set {step_working_set_bytes(spec, run, not args.no_rcache) / 1e9:.2f} GB per step "
-                         "> 129 MB L2; no flush"},
-        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
-                     "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
-                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (no FP64 figure measured by the driver)",
-                     "traffic": traffic, "flops_per_launch": flops, "ms_per_launch": contract_ms,
-                     "flops_per_launch_pair_order": flops_pair_order,
-                     "launches_per_contraction": prof["launches"]["contract"] / max(1, prof["steps"]),
-                     "refreshed_pairs_per_step": refreshed if kernel == "contract_fp64r_kernel" else None,
-                     "note": "one contraction per step: with the cached half-rotated matrices (contract_fp64r_kernel) "
-                             "the refresh of the pairs whose path moved (rcache_collect/fill) and the pair kernel; "
-                             "for the walker-side form phi_columns_kernel, the FP64 GEMM forming Y_g = X_g phi_w and "
-                             "contract_fp64z_kernel; flops, time and traffic are theirs together; flops_per_launch "
-                             "counts the executed association order (cached: M = R Theta plus the refreshes); the "
-                             "per-pair order (R = Phi^T L_g formed every step) needs flops_per_launch_pair_order; "
-                             "with the cache, traffic is the pair kernel's (it reads every pair's matrices, 16.4 GB)"},
+                   "system_seed": spec.seed, "philox_seed": seed, "path": dict(HEADLINE_PATH),
+                   "l2": f"working set {step_working_set_bytes(spec, run) / 1e9:.1f} GB per step > 129 MB L2; no flush"},
+        "roofline": dominant,
+        "roofline_tensor_contraction": roof_tc,
+        "roofline_refinement": roof_rf,
+        "vs_fp64_same_config": dict(fp64, speedup=(fp64["full_workload_ms_per_step_extrapolated"] /
+                                                   (ms_max / args.steps))),
         "cpu_baseline": cpu,
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 32,
             "includes": "afqmc_init from pinned host arrays (incl. 20 burn-in sweeps) + K steps, each followed by "
                         "a device-to-host read of its energy record"},
         "clocks": clocks, "gpu_launches": int(l1 - l0), "phases_ms_per_step": phases,
+        "device_status": int(stats["status"]), "live_walkers": int(stats["live_walkers"]),
         "mixed_energy_last_step": float(hist[-1, 0] / hist[-1, 1]) if len(hist) else None,
+        "mixed_energy_last_step_all_ranks": emix_global[0] if emix_global else None,
         "variants": variants,
     }
     print(json.dumps(line), flush=True)
@@ -843,7 +1004,7 @@ def our_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -853,8 +1014,8 @@ def main():
                     help="FP64 headline without the cached half-rotated matrices (the walker-side form)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision, learned-proposal and batched measurements")
-    ap.add_argument("--only", choices=("mixed", "learned", "batched", "popctl", "measpaths", "pscaling", "largest",
-                                       "large_mixed"),
+    ap.add_argument("--only", choices=("fp64", "mixed", "learned", "batched", "popctl", "measpaths", "pscaling",
+                                       "largest", "largest_mixed", "large_mixed"),
                     default=None,
                     help="time one variant alone (profiling); skips the FP64 headline's extras")
     args = ap.parse_args()
