@@ -42,7 +42,7 @@ if ROOT not in sys.path:
 
 WORKLOAD = "large_n120"          # the headline: the mixed-precision workload
 MEDIUM = "medium_n50"            # the medium FP64 workload of the variants
-HEADLINE_PATH = dict(precision="fp16x3", tc_form="walker", refine_tol=1e-4)
+HEADLINE_PATH = dict(precision="fp16x6", tc_form="walker", refine_tol=1e-4)
 METRIC = "walker-sample steps/s incl. local energy"
 UNIT = "walker-sample steps/s"
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 4 FP64 flop/clk
@@ -733,7 +733,8 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         sy = ai.make_system(spec2)
         W2, P2, st2 = 128, run2.n_paths, 2
         res, state = {}, None
-        for key, prec, tol in (("fp64", "fp64", 1e-4), ("refined", "fp16x3", 1e-4), ("tensor_only", "fp16x3", 0.0)):
+        for key, prec, tol in (("fp64", "fp64", 1e-4), ("refined", "fp16x3", 1e-4), ("tensor_only", "fp16x3", 0.0),
+                               ("refined_fp16x6", "fp16x6", 1e-4), ("tensor_only_fp16x6", "fp16x6", 0.0)):
             c = lib.make_config(spec2.N, spec2.n_up, spec2.n_dn, spec2.n_chol, spec2.K, W2, P2, run2.dtau,
                                 ai.philox_run_seed(2), n_burn=20, walker_offset=rank * W2, precision=prec,
                                 refine_tol=tol)
@@ -756,14 +757,15 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
                      "per-walker energy differences against the FP64 path at one common state; "
                      f"{st2} timed steps per mixed context (1 for FP64) after 1 untimed step",
              "unit": UNIT, "clocks": res["refined"]["clocks"], "kernel": res["refined"]["kernel"]}
-        for key in ("refined", "tensor_only", "fp64"):
+        for key in ("refined", "tensor_only", "refined_fp16x6", "tensor_only_fp16x6", "fp64"):
             r = res[key]
             e = {"value": W2 * P2 * world / (r["ms"] / 1e3), "ms_per_step": r["ms"]}
             if key != "fp64":
                 dw = np.abs(r["ew"] - res["fp64"]["ew"])
                 e["dE_walker_ha"] = {"max": float(dw.max()), "median": float(np.median(dw)),
                                      "frac_above_1e-4": float(np.mean(dw > 1e-4))}
-            if key == "refined":
+            e["kernel"] = r["kernel"]
+            if key.startswith("refined"):
                 e["refined_pairs_at_common_state"] = int(r["refined0"])
                 e["refined_pairs_per_step"] = float(r["refined_per_step"])
                 e["refine_tol_ha"] = 1e-4
@@ -949,10 +951,11 @@ def our_arm(args):
                "peak_source": peak_src + " (fp16 nominal ratio 1)",
                "traffic": tcw_traffic(W, P), "flops_per_launch": flops, "ms_per_launch": c_ms,
                "flops_per_launch_walker_side": flops_ws, "frac_walker_side": flops_ws / (c_ms / 1e3) / 1e12 / peak,
-               "mma_products_per_real_product": 4,
+               "mma_products_per_real_product": 6 if HEADLINE_PATH["precision"] == "fp16x6" else 4,
                "note": "one contraction per step; flops_per_launch is the per-pair algorithmic count (R = Phi^T X, "
                        "M = R Theta: 2 n N^2 + 4 N (n_up^2 + n_dn^2) + traces per matrix); the walker-side "
-                       "association executes flops_per_launch_walker_side in 4 split-FP16 MMA products each; "
+                       "association executes flops_per_launch_walker_side in mma_products_per_real_product "
+                       "split-FP16 MMA products each; "
                        "traffic is the GEMM-Z kernel's DRAM bytes per contraction"}
     rf_flops = contract_flops_per_pair(spec) * refined_per_step
     roof_rf = {"bound": "alu", "kernel": "contract_fp64_kernel<double-float> (refinement of the listed pairs)",
@@ -974,8 +977,9 @@ def our_arm(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "fp16x3 contraction (split FP16 on tensor cores, FP32 accumulation) + double-float refinement; "
-                 "f64 overlaps, LU, weights, energy sums",
+        "dtype": HEADLINE_PATH["precision"] + " contraction (operands split into " +
+                 ("three" if HEADLINE_PATH["precision"] == "fp16x6" else "two") + " FP16 parts on the tensor cores, "
+                 "FP32 accumulation) + double-float refinement; f64 overlaps, LU, weights, energy sums",
         "data": "synthetic",
         "config": {"workload": workload_desc(spec, run), "walkers_total": W * world, "paths": P,
                    "system_seed": spec.seed, "philox_seed": seed, "path": dict(HEADLINE_PATH),

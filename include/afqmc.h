@@ -90,10 +90,16 @@ enum {
                                    numbers, about 44 bits; the propagation in FP64 when its 2 N (n_up + n_dn)
                                    complex work values exceed shared memory); everything else FP64.
                                    N <= 128, n_up <= 32 */
-    AFQMC_PRECISION_FP16X3 = 2  /* the same with each operand row/column scaled by a power of two and split
+    AFQMC_PRECISION_FP16X3 = 2, /* the same with each operand row/column scaled by a power of two and split
                                    into an integer FP16 part (|x| <= 256) and an FP16 remainder (about 20 bits
                                    relative to the row's largest entry); integer*integer products go to their
                                    own, exact accumulator, the three correction products to a second one */
+    AFQMC_PRECISION_FP16X6 = 3  /* the walker-side tensor-core form (tc_form AUTO or WALKER) only: each operand
+                                   split into the integer FP16 part and two FP16 remainders (about 31 bits),
+                                   six products per real product (every one above about 2^-28 of the
+                                   integer*integer term), the entries reaching the traces as FP32 numbers (about
+                                   24 bits).  N <= 192 (the GEMM-Y block keeps three parts of the walker's
+                                   orbitals in shared memory) */
 };
 
 typedef struct {
@@ -124,7 +130,8 @@ typedef struct {
     int mlp_train;      /* 1: after every step, one Adam step on the paths' states (online training) */
     double refine_tol;  /* mixed precision, per-pair tensor-core form: per-walker energy tolerance (Ha) of
                            the error-controlled refinement.  Each measurement estimates every pair's
-                           contraction error as (2/N) 2^-20 sum_g ||L_g||_2^2 ||Theta_p||_F^2 and recomputes
+                           contraction error as (2/N) u sum_g ||L_g||_2^2 ||Theta_p||_F^2 (u = 2^-20; fp16x6:
+                           2^-24) and recomputes
                            in double-float (FP32 pairs, about 44 bits) the pairs with the largest ||Theta_p||_F
                            until the estimated error of the
                            walker's average, 2 sqrt(sum of the kept pairs' squared errors) / |sum_p S_p|,
@@ -155,7 +162,8 @@ typedef struct {
                            n_up + n_dn <= 40, else the per-pair form (N <= 128, n_up <= 32; it has the
                            error-controlled refinement), else the general walker-side form;
                            AFQMC_TC_PER_PAIR (1); AFQMC_TC_WALKER (2): the general walker-side form
-                           (N <= 256, n_up <= 64; refined like the per-pair form) */
+                           (N <= 256, n_up <= 64; refined like the per-pair form).  Precision FP16X6
+                           always takes the general walker-side form */
     double trial_alpha_re, trial_alpha_im;   /* alpha of the trial samples (default 1 + 0i) */
     int trial_slices;   /* hidden-variable slices of a trial sample (default 1).  The samples are
                            Phi(x) = exp(alpha S_m) P ... P exp(alpha S_1) Phi0 with S_l = sum_k x_lk U_k

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libafqmc.so")
 
 CONSTRAINTS = {"combined": 0, "separate": 1, "half_plane": 2}
 PROPOSALS = {"prior": 0, "pcn": 1, "rw": 2, "mlp": 3}
-PRECISIONS = {"fp64": 0, "bf16x3": 1, "fp16x3": 2}
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "fp16x3": 2, "fp16x6": 3}
 IMPORTANCE = {"hybrid": 0, "local_energy": 1}
 TC_FORMS = {"auto": 0, "per_pair": 1, "walker": 2}
 STATE_MAGIC = 0x4146514D43535431

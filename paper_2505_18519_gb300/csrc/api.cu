@@ -61,10 +61,19 @@ extern "C" int afqmc_contract_kernel(const afqmc_config* cfg) {
     return tc_kind(cfg);
 }
 
+// operand arithmetic of the walker-side tensor-core form: 0 bf16x3, 1 fp16x3, 2 fp16x6
+static int tc_mode(const afqmc_config* c) {
+    return c->precision == AFQMC_PRECISION_FP16X6 ? 2 : (c->precision == AFQMC_PRECISION_FP16X3 ? 1 : 0);
+}
+
 int tc_kind(const afqmc_config* c) {
     const bool f16 = c->precision == AFQMC_PRECISION_FP16X3;
+    const bool tcw = contract_tcw_supported(c->N, c->n_up, c->n_dn, c->n_chol, c->n_walkers, c->n_paths, tc_mode(c));
+    if (c->precision == AFQMC_PRECISION_FP16X6) {   // the walker-side form only
+        if (c->tc_form == AFQMC_TC_PER_PAIR) return -1;
+        return tcw ? 5 : -1;
+    }
     const bool tc = contract_tc_supported(c->N, c->n_up, c->n_dn, f16);
-    const bool tcw = contract_tcw_supported(c->N, c->n_up, c->n_dn, c->n_chol, c->n_walkers, c->n_paths, f16);
     if (c->tc_form == AFQMC_TC_PER_PAIR) return tc ? 1 : -1;
     if (c->tc_form == AFQMC_TC_WALKER) return tcw ? 5 : -1;
     if (contract_tc_walker_side(c->N, c->n_up, c->n_dn, f16)) return 2;
@@ -206,7 +215,7 @@ static const char* check_config(const afqmc_config* c) {
         return "rw_step must be > 0";
     if (c->proposal == AFQMC_PROPOSAL_MLP && !(c->mlp_mix >= 0.0 && c->mlp_mix <= 1.0)) return "mlp_mix in [0, 1]";
     if (c->proposal == AFQMC_PROPOSAL_MLP && !(c->mlp_lr >= 0.0)) return "mlp_lr must be >= 0";
-    if (c->precision < AFQMC_PRECISION_FP64 || c->precision > AFQMC_PRECISION_FP16X3) return "unknown precision";
+    if (c->precision < AFQMC_PRECISION_FP64 || c->precision > AFQMC_PRECISION_FP16X6) return "unknown precision";
     if (c->taylor_order < 1 || c->taylor_order > 32) return "taylor_order must be in [1, 32]";
     if (c->history_capacity < 1) return "history_capacity must be >= 1";
     if (!(c->dtau > 0.0)) return "dtau must be > 0";
@@ -300,7 +309,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     const bool f16c = c->precision == AFQMC_PRECISION_FP16X3;
     w.Lt = (tck == 1 || tck == 2) ? take(contract_tc_image_bytes(d.N, d.nu, d.nd, d.G, f16c)) : nullptr;
     w.Yimg = tck == 2 ? take(contract_tcy_yimage_bytes(d.N, d.nu, d.nd, d.G, d.W, f16c)) : nullptr;
-    w.tcw = tck == 5 ? take(contract_tcw_work_bytes(d.N, d.nu, d.nd, d.G, d.W, d.P, f16c)) : nullptr;
+    w.tcw = tck == 5 ? take(contract_tcw_work_bytes(d.N, d.nu, d.nd, d.G, d.W, d.P, tc_mode(c))) : nullptr;
     const size_t ywalk = c->precision == AFQMC_PRECISION_FP64 ? contract_fp64_walker_bytes(d.N, d.nu, d.nd, d.G, d.W, d.P)
                                                               : 0;
     w.ywalk = ywalk ? take(ywalk) : nullptr;
@@ -523,7 +532,7 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64) {
         if (tck == 5)
-            CK(contract_tcw(s, d, w.tcw, w.Theta, w.phi, w.vpair, w.epair, w.status, f16));
+            CK(contract_tcw(s, d, w.tcw, w.Theta, w.phi, w.vpair, w.epair, w.status, tc_mode(&ctx->cfg)));
         else
             CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.Yimg, w.vpair, w.epair, w.status, f16));
     } else if (w.rc) {   // cached half-rotated matrices, refreshed for the paths that moved
@@ -541,8 +550,11 @@ static afqmc_status measure(afqmc_ctx* ctx) {
         // (measured per-pair errors of this form sit at 0.3-0.5 of it for N = 120 and 200),
         // their Theta formed in place of B, then the double-float per-pair contraction;
         // the log-overlaps go to scratch
+        // unit roundoff of the model: fp16x3 and bf16x3 operands about 20 bits; fp16x6 operands about
+        // 31 bits, the entries reaching the traces as FP32 numbers (24 bits)
+        const double u = tc_mode(&ctx->cfg) == 2 ? 0x1p-24 : 0x1p-20;
         CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2, w.alive,
-                         w.refine_items, w.refine_n, w.counters, w.refine_th2, 0x1p-20));
+                         w.refine_items, w.refine_n, w.counters, w.refine_th2, u));
         for (int spin = 0; spin < 2; ++spin)
             CK(overlap_lu(s, d, spin, w.Phi, phi_stride(d), w.phi, w.logdet_new, w.Theta, nullptr, w.status, d.pairs,
                           d.P, OVL_THETA, nullptr, w.refine_items, w.refine_n));
@@ -608,7 +620,7 @@ extern "C" afqmc_status afqmc_init_trial(const afqmc_config* cfg, const double* 
         if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, 4, s);
         if (e != cudaSuccess) { st = fail(AFQMC_ERR_CUDA, "copying inputs: %s", cudaGetErrorString(e)); break; }
         StepParams p = params_of(cfg);
-        if (w.tcw && (e = contract_tcw_prepare(s, d, w.h, w.L, w.tcw, cfg->precision == AFQMC_PRECISION_FP16X3)) !=
+        if (w.tcw && (e = contract_tcw_prepare(s, d, w.h, w.L, w.tcw, tc_mode(cfg))) !=
                          cudaSuccess) {
             st = fail(AFQMC_ERR_CUDA, "tensor-core operand image: %s", cudaGetErrorString(e));
             break;

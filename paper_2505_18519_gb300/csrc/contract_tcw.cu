@@ -35,8 +35,14 @@
 // their own accumulator, where every partial sum is an integer of magnitude at
 // most 2^24 (|hi_A hi_B| <= 2^15, K <= 512; GEMM-Y: 2^16, K <= 256) and therefore
 // exact in FP32 whatever the tensor cores' rounding, and hi*lo + lo*hi + lo*lo go
-// to a second accumulator about 2^-8 as large.  bf16x3: hi = bf16(x),
-// lo = bf16(x - hi), hi*hi + hi*lo + lo*hi in one accumulator.
+// to a second accumulator about 2^-8 as large.  About 20 significant bits per
+// operand (relative to its row's largest entry).
+// fp16x6: the same hi part and two FP16 remainders, mid = x - hi and
+// lo = x - hi - mid (about 31 bits per operand); hi*hi to the exact accumulator,
+// hi*mid + mid*hi + mid*mid + hi*lo + lo*hi (every product larger than about
+// 2^-28 of hi*hi) to the second.  The epilogues form each entry as one FP32
+// number, so about 24 significant bits reach the traces.
+// bf16x3: hi = bf16(x), lo = bf16(x - hi), hi*hi + hi*lo + lo*hi in one accumulator.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -55,7 +61,12 @@ constexpr int TCWZ_THREADS = 320;       // GEMM-Z: warp 0 producer, warp 1 MMA i
 constexpr int TCWZ_EPI = 256;           // two epilogue warps per tensor-memory lane quadrant
 constexpr int TCW_MAXSTAGES = 4;
 constexpr size_t TCW_SMEM_MAX = 212 * 1024;   // dynamic; static use is about 11 KB of 227 KB
-constexpr uint32_t TCW_CHUNK_A = 32768; // one K chunk of a 128-row operand: 16 KB hi, 16 KB lo
+constexpr uint32_t TCW_PART = 16384;   // one part (hi, mid or lo) of a K chunk of a 128-row operand
+
+// Operand arithmetic: 0 bf16x3, 1 fp16x3, 2 fp16x6 (parts per operand: 2, 2, 3).
+__host__ __device__ constexpr int tcw_parts(int mode) { return mode == 2 ? 3 : 2; }
+// one K chunk (64 elements) of a 128-row operand, all parts
+__host__ __device__ constexpr uint32_t tcw_chunk(int mode) { return (uint32_t)tcw_parts(mode) * TCW_PART; }
 
 __host__ __device__ __forceinline__ int tcw_round16(int x) { return (x + 15) / 16 * 16; }
 
@@ -93,7 +104,40 @@ __device__ __forceinline__ void split2(float x, uint16_t& hi, uint16_t& lo) {
     }
 }
 
+// x = hi + mid + lo with hi an integer, from the unevaluated sum xh + xl (|xh| <= 256,
+// |xl| <= 2^-24 |xh|): xh - hi is exact, adding xl rounds at 2^-26, mid takes 11
+// bits of that remainder and lo, the exact difference, the next 11.
+__device__ __forceinline__ void split3(float xh, float xl, uint16_t& hi, uint16_t& mid, uint16_t& lo) {
+    const float r = rintf(xh);
+    const float r1 = (xh - r) + xl;
+    const __half m = __float2half_rn(r1);
+    const float r2 = r1 - __half2float(m);
+    hi = __half_as_ushort(__float2half_rn(r));
+    mid = __half_as_ushort(m);
+    lo = __half_as_ushort(__float2half_rn(r2));
+}
+
+// The parts of one operand value x (already scaled); MODE 0 and 1 round x to FP32
+// first, MODE 2 keeps it as a double-float pair.
+template <int MODE>
+__device__ __forceinline__ void split_parts(double x, uint16_t (&o)[tcw_parts(MODE)]) {
+    if constexpr (MODE == 2) {
+        const float xh = (float)x;
+        split3(xh, (float)(x - (double)xh), o[0], o[1], o[2]);
+    } else {
+        split2<MODE == 1>((float)x, o[0], o[1]);
+    }
+}
+template <int MODE>
+__device__ __forceinline__ void split_parts_f(float x, uint16_t (&o)[tcw_parts(MODE)]) {
+    if constexpr (MODE == 2) split3(x, 0.f, o[0], o[1], o[2]);
+    else split2<MODE == 1>(x, o[0], o[1]);
+}
+
 __device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
+__device__ __forceinline__ uint4 pack8(const uint16_t* v) {
+    return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+}
 
 // Bounded wait that records a timeout (the caller breaks out of its loop).
 __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, uint32_t lim, volatile int* fail) {
@@ -106,12 +150,13 @@ __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, uin
 }  // namespace
 
 // ---------------------------------------------------------------- X image (init)
-// Ximg[((g KCX + c) 2 + h) RX]: matrix g = (h, L_1, ...), K chunk c (i in
-// [64c, 64c + 64)), hi (h = 0) or lo part, N16 rows j x 128 bytes, values
+// Ximg[((g KCX + c) NP + h) RX]: matrix g = (h, L_1, ...), K chunk c (i in
+// [64c, 64c + 64)), part h (hi, [mid,] lo), N16 rows j x 128 bytes, values
 // X_g[j, i] 2^lexp[g] (zero outside N x N).
-template <bool F16>
+template <int MODE>
 __global__ void tcw_x_image_kernel(int N, int N16, int KCX, int G1, const double* __restrict__ h,
                                    const double* __restrict__ L, const int* __restrict__ lexp, uint8_t* __restrict__ out) {
+    constexpr int NP = tcw_parts(MODE);
     const long long units = (long long)G1 * KCX * N16 * 8;   // (g, c, j, u)
     const size_t RX = (size_t)N16 * 128;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < units;
@@ -123,41 +168,44 @@ __global__ void tcw_x_image_kernel(int N, int N16, int KCX, int G1, const double
         const int g = (int)(gc / KCX);
         const double* X = g == 0 ? h : L + (long long)(g - 1) * N * N;
         const int le = lexp[g];
-        uint16_t hi[8], lo[8];
+        uint16_t pt[NP][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int i = c * 64 + u * 8 + q;
-            const float x = (j < N && i < N) ? (float)ldexp(X[(long long)j * N + i], le) : 0.f;
-            split2<F16>(x, hi[q], lo[q]);
+            uint16_t o[NP];
+            split_parts<MODE>((j < N && i < N) ? ldexp(X[(long long)j * N + i], le) : 0.0, o);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) pt[p][q] = o[p];
         }
-        uint8_t* base = out + ((size_t)g * KCX + c) * 2 * RX + swz16(j, u);
-        *reinterpret_cast<uint4*>(base) = make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]),
-                                                     pack2(hi[6], hi[7]));
-        *reinterpret_cast<uint4*>(base + RX) = make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]), pack2(lo[4], lo[5]),
-                                                          pack2(lo[6], lo[7]));
+        uint8_t* base = out + ((size_t)g * KCX + c) * NP * RX + swz16(j, u);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) *reinterpret_cast<uint4*>(base + p * RX) = pack8(pt[p]);
     }
 }
 
 // ---------------------------------------------------------------- GEMM-Y and the Bop image of Y_g
 // Block: walker w0 + blockIdx.x / n_gblk, matrices [gb GPB, (gb + 1) GPB) of one spin
 // (columns col0 .. col0 + n - 1 of phi).  Shared memory: PW (KCX chunks of 128
-// rows: row (b, ri) = Re/Im phi[:, col0 + b] times 2^sPW[b], K = i), then a ring
-// of S stages, each one half (hi or lo) of a K chunk of X_g (N16 rows).
+// rows: row (b, ri) = Re/Im phi[:, col0 + b] times 2^sPW[b], K = i, NP parts each),
+// then a ring of S stages, each one part of a K chunk of X_g (N16 rows).
 // Tensor memory: D_Y (N16 columns) and, FP16, its correction (N16 more).
 // Output: the Bop rows (g, b, ri) of matrix g in N-tile t = g / GB at row
-// (g % GB) 2n + 2b + ri; K chunk c of a tile is NT rows hi then NT rows lo; and
+// (g % GB) 2n + 2b + ri; K chunk c of a tile is NT rows of each part in turn; and
 // yexp[(wl G1 + g) n + b], the exponent of column b (image = Y 2^yexp).
-template <bool F16>
+template <int MODE>
 __global__ void __launch_bounds__(TCW_THREADS, 1)
     tcw_y_kernel(int N, int nt, int col0, int n, int G1, int N16, int KCX, int S, int GPB, int n_gblk, long long w0,
                  const double2* __restrict__ phi, const uint8_t* __restrict__ Ximg, const int* __restrict__ lexp,
                  int NT, int GB, int KC, int NTILES, uint8_t* __restrict__ Yimg, int* __restrict__ yexp, int* status,
                  uint32_t lim) {
+    constexpr bool F16 = MODE != 0;
+    constexpr int NP = tcw_parts(MODE);
+    constexpr uint32_t CH = tcw_chunk(MODE);
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const uint32_t RX = (uint32_t)N16 * 128u;
-    uint8_t* PW = sm;                                         // KCX x 32 KB
-    uint8_t* ring = PW + (size_t)KCX * TCW_CHUNK_A;           // S x RX
+    uint8_t* PW = sm;                                         // KCX x CH
+    uint8_t* ring = PW + (size_t)KCX * CH;                    // S x RX
     __shared__ uint64_t full_bar[TCW_MAXSTAGES], empty_bar[TCW_MAXSTAGES], dfull, dempty, drain_bar;
     __shared__ uint32_t tslot;
     __shared__ volatile int fail;
@@ -168,7 +216,7 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
     const int gb = blockIdx.x % n_gblk;
     const int g0 = gb * GPB, g1 = min(G1, g0 + GPB);
     const int ng = max(0, g1 - g0);
-    const int n_units = ng * KCX * 2;
+    const int n_units = ng * KCX * NP;
     const double2* ph = phi + (w0 + wl) * (long long)N * nt + col0;
     const uint32_t tcols = F16 ? 2u * (uint32_t)N16 : (uint32_t)N16;
     const uint32_t talloc = tcols <= 32 ? 32 : (tcols <= 64 ? 64 : (tcols <= 128 ? 128 : (tcols <= 256 ? 256 : 512)));
@@ -204,22 +252,23 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
     for (int e = tid; e < KCX * 128 * 8; e += TCW_THREADS) {
         const int u = e % 8, r = (e / 8) % 128, c = e / (8 * 128);
         const int b = r >> 1, ri = r & 1;
-        uint16_t hi[8], lo[8];
+        uint16_t pt[NP][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int i = c * 64 + u * 8 + q;
-            float x = 0.f;
+            double x = 0.0;
             if (r < 2 * n && i < N) {
                 const double2 t = ph[(long long)i * nt + b];
-                x = (float)(ri ? t.y : t.x) * p2f(sPW[b]);
+                x = ldexp(ri ? t.y : t.x, sPW[b]);
             }
-            split2<F16>(x, hi[q], lo[q]);
+            uint16_t o[NP];
+            split_parts<MODE>(x, o);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) pt[p][q] = o[p];
         }
-        uint8_t* base = PW + (size_t)c * TCW_CHUNK_A + swz16(r, u);
-        *reinterpret_cast<uint4*>(base) = make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]),
-                                                     pack2(hi[6], hi[7]));
-        *reinterpret_cast<uint4*>(base + 16384) = make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]),
-                                                             pack2(lo[4], lo[5]), pack2(lo[6], lo[7]));
+        uint8_t* base = PW + (size_t)c * CH + swz16(r, u);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) *reinterpret_cast<uint4*>(base + p * TCW_PART) = pack8(pt[p]);
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -229,15 +278,15 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
     bool failed = false;
 
     if (warp == 0) {
-        // ---- producer: unit v = (matrix g0 + v / (2 KCX), chunk (v / 2) % KCX, half v % 2)
+        // ---- producer: unit v = (matrix g0 + v / (NP KCX), chunk (v / NP) % KCX, part v % NP)
         if (lane == 0) {
             int issued = 0;
             for (int v = 0; v < n_units; ++v) {
                 const int st = v % S;
                 if (v >= S && !wait_or_fail(&empty_bar[st], (uint32_t)(((v / S) - 1) & 1), lim, &fail)) { failed = true; break; }
-                const int g = g0 + v / (2 * KCX), c = (v / 2) % KCX, hh = v % 2;
+                const int g = g0 + v / (NP * KCX), c = (v / NP) % KCX, hh = v % NP;
                 tc::mbar_arrive_expect_tx(&full_bar[st], RX);
-                tc::bulk_g2s(ring + (size_t)st * RX, Ximg + (((size_t)g * KCX + c) * 2 + hh) * RX, RX, &full_bar[st]);
+                tc::bulk_g2s(ring + (size_t)st * RX, Ximg + (((size_t)g * KCX + c) * NP + hh) * RX, RX, &full_bar[st]);
                 ++issued;
             }
             // every issued copy lands before the block leaves
@@ -247,7 +296,7 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---- MMA issue (one thread): D_Y = PW X_g^T
+        // ---- MMA issue (one thread): D_Y = PW X_g^T, the part products of the header
         if (lane == 0) {
             const uint32_t idesc = F16 ? tc::idesc_f16_f32(128, N16) : tc::idesc_bf16_f32(128, N16);
             const uint32_t dh = taddr, dl = taddr + (F16 ? (uint32_t)N16 : 0u);
@@ -257,22 +306,34 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
                 tc::fence_after_sync();
                 for (int c = 0; c < KCX && !failed; ++c) {
                     const int ks = min(4, (N16 - 64 * c) / 16);
-                    for (int hh = 0; hh < 2; ++hh, ++v) {
+                    for (int hh = 0; hh < NP; ++hh, ++v) {
                         const int st = v % S;
                         if (!wait_or_fail(&full_bar[st], (uint32_t)((v / S) & 1), lim, &fail)) { failed = true; break; }
                         tc::fence_after_sync();
-                        const uint32_t pa = tc::smem_u32(PW + (size_t)c * TCW_CHUNK_A);
+                        const uint32_t pa = tc::smem_u32(PW + (size_t)c * CH);
                         const uint32_t pb = tc::smem_u32(ring + (size_t)st * RX);
                         for (int s = 0; s < ks; ++s) {
-                            const uint64_t ah = tc::desc_sw128(pa + s * 32), al = tc::desc_sw128(pa + 16384 + s * 32);
+                            const uint64_t a0 = tc::desc_sw128(pa + s * 32), a1 = tc::desc_sw128(pa + TCW_PART + s * 32);
                             const uint64_t bx = tc::desc_sw128(pb + s * 32);
                             const uint32_t first = (c == 0 && s == 0) ? 0u : 1u;
-                            if (hh == 0) {
-                                tc::mma_f16(dh, ah, bx, idesc, first);
-                                tc::mma_f16(dl, al, bx, idesc, F16 ? first : 1u);
+                            if constexpr (MODE == 2) {
+                                const uint64_t a2 = tc::desc_sw128(pa + 2 * TCW_PART + s * 32);
+                                if (hh == 0) {                 // X hi: hi*hi, mid*hi, lo*hi
+                                    tc::mma_f16(dh, a0, bx, idesc, first);
+                                    tc::mma_f16(dl, a1, bx, idesc, first);
+                                    tc::mma_f16(dl, a2, bx, idesc, 1u);
+                                } else if (hh == 1) {          // X mid: hi*mid, mid*mid
+                                    tc::mma_f16(dl, a0, bx, idesc, 1u);
+                                    tc::mma_f16(dl, a1, bx, idesc, 1u);
+                                } else {                       // X lo: hi*lo
+                                    tc::mma_f16(dl, a0, bx, idesc, 1u);
+                                }
+                            } else if (hh == 0) {
+                                tc::mma_f16(dh, a0, bx, idesc, first);
+                                tc::mma_f16(dl, a1, bx, idesc, F16 ? first : 1u);
                             } else {
-                                tc::mma_f16(dl, ah, bx, idesc, 1u);
-                                if (F16) tc::mma_f16(dl, al, bx, idesc, 1u);
+                                tc::mma_f16(dl, a0, bx, idesc, 1u);
+                                if (F16) tc::mma_f16(dl, a1, bx, idesc, 1u);
                             }
                         }
                         tc::mma_commit(&empty_bar[st]);
@@ -318,10 +379,11 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
             mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
             const int et = F16 ? exp_into(mx, 7) : 0;   // image = D_Y 2^et
             const int t = g / GB, gl = g % GB;
-            uint8_t* tile = Yimg + ((size_t)wl * NTILES + t) * KC * (size_t)NT * 256;
+            uint8_t* tile = Yimg + ((size_t)wl * NTILES + t) * KC * (size_t)NT * 128 * NP;
             const int R1 = gl * 2 * n + 2 * b + ri;         // k = j: Re Y (re row), Im Y (im row)
             const int R2 = gl * 2 * n + 2 * b + (1 - ri);   // k = N16 + j: Re Y (im row), -Im Y (re row)
-            const uint16_t neg = ri ? 0x8000u : 0u;
+            const uint32_t neg = ri ? 0x8000u : 0u;
+            const uint32_t nn = neg | (neg << 16);
             const float mul = p2f(et);
             // pass 2: scale, split, and write 8 K elements (16 bytes) at a time
             for (int j0 = 0; j0 < N16; j0 += 16) {
@@ -339,24 +401,25 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
                 if (row_ok) {
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
-                        uint16_t hi[8], lo[8];
+                        uint16_t pt[NP][8];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) split2<F16>(v[8 * half + q] * mul, hi[q], lo[q]);
+                        for (int q = 0; q < 8; ++q) {
+                            uint16_t o[NP];
+                            split_parts_f<MODE>(v[8 * half + q] * mul, o);
+#pragma unroll
+                            for (int p = 0; p < NP; ++p) pt[p][q] = o[p];
+                        }
                         const int j = j0 + 8 * half;
                         const int k1 = j, k2 = N16 + j;
-                        const uint4 H1 = make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]),
-                                                    pack2(hi[6], hi[7]));
-                        const uint4 L1 = make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]), pack2(lo[4], lo[5]),
-                                                    pack2(lo[6], lo[7]));
-                        const uint32_t nn = (uint32_t)neg | ((uint32_t)neg << 16);
-                        const uint4 H2 = make_uint4(H1.x ^ nn, H1.y ^ nn, H1.z ^ nn, H1.w ^ nn);
-                        const uint4 L2 = make_uint4(L1.x ^ nn, L1.y ^ nn, L1.z ^ nn, L1.w ^ nn);
-                        uint8_t* c1 = tile + (size_t)(k1 >> 6) * NT * 256;
-                        uint8_t* c2 = tile + (size_t)(k2 >> 6) * NT * 256;
-                        *reinterpret_cast<uint4*>(c1 + swz16(R1, (k1 & 63) >> 3)) = H1;
-                        *reinterpret_cast<uint4*>(c1 + (size_t)NT * 128 + swz16(R1, (k1 & 63) >> 3)) = L1;
-                        *reinterpret_cast<uint4*>(c2 + swz16(R2, (k2 & 63) >> 3)) = H2;
-                        *reinterpret_cast<uint4*>(c2 + (size_t)NT * 128 + swz16(R2, (k2 & 63) >> 3)) = L2;
+                        uint8_t* c1 = tile + (size_t)(k1 >> 6) * NT * 128 * NP;
+                        uint8_t* c2 = tile + (size_t)(k2 >> 6) * NT * 128 * NP;
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            const uint4 H1 = pack8(pt[p]);
+                            const uint4 H2 = make_uint4(H1.x ^ nn, H1.y ^ nn, H1.z ^ nn, H1.w ^ nn);
+                            *reinterpret_cast<uint4*>(c1 + (size_t)p * NT * 128 + swz16(R1, (k1 & 63) >> 3)) = H1;
+                            *reinterpret_cast<uint4*>(c2 + (size_t)p * NT * 128 + swz16(R2, (k2 & 63) >> 3)) = H2;
+                        }
                     }
                 }
             }
@@ -377,12 +440,14 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
 // Block: walker w0 + blockIdx.x / MT, tile m = blockIdx.x % MT of its pairs
 // (pairs m PB .. m PB + PB - 1 of the walker), one spin.  Row r = p_l n + a:
 // [Re B_p[:, col0 + a] | Im B_p[:, col0 + a]] times 2^aexp[r] (largest entry in
-// [64, 128)), split; KC chunks of 32 KB (16 KB hi, 16 KB lo); rows past the
-// tile's pairs are zero.
-template <bool F16>
+// [64, 128)), split; KC chunks of NP parts of 16 KB; rows past the tile's pairs
+// are zero.
+template <int MODE>
 __global__ void __launch_bounds__(256) tcw_a_kernel(int N, int nt, int col0, int n, int P, int PB, int MT, int N16,
                                                     int KC, long long w0, const double2* __restrict__ Bm,
                                                     uint8_t* __restrict__ Aimg, int* __restrict__ aexp) {
+    constexpr int NP = tcw_parts(MODE);
+    constexpr uint32_t CH = tcw_chunk(MODE);
     __shared__ int sA[128];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long wl = blockIdx.x / MT;
@@ -399,55 +464,59 @@ __global__ void __launch_bounds__(256) tcw_a_kernel(int N, int nt, int col0, int
             }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) sA[r] = F16 ? exp_into(mx, 6) : 0;
+        if (lane == 0) sA[r] = MODE != 0 ? exp_into(mx, 6) : 0;
     }
     __syncthreads();
-    uint8_t* out = Aimg + (size_t)blockIdx.x * KC * TCW_CHUNK_A;
+    uint8_t* out = Aimg + (size_t)blockIdx.x * KC * CH;
     for (int e = tid; e < KC * 128 * 8; e += 256) {
         const int u = e % 8, r = (e / 8) % 128, c = e / (8 * 128);
         const int p = r / n, a = r % n;
-        uint16_t hi[8], lo[8];
+        uint16_t pt[NP][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int k = c * 64 + u * 8 + q;
             const int i = k < N16 ? k : k - N16;
-            float x = 0.f;
+            double x = 0.0;
             if (r < np * n && i < N && k < 2 * N16) {
                 const double2 t = Bm[(pair0 + p) * (long long)N * nt + (long long)i * nt + col0 + a];
-                x = (float)(k < N16 ? t.x : t.y) * p2f(sA[r]);
+                x = ldexp(k < N16 ? t.x : t.y, sA[r]);
             }
-            split2<F16>(x, hi[q], lo[q]);
+            uint16_t o[NP];
+            split_parts<MODE>(x, o);
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) pt[pp][q] = o[pp];
         }
-        uint8_t* base = out + (size_t)c * TCW_CHUNK_A + swz16(r, u);
-        *reinterpret_cast<uint4*>(base) = make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]),
-                                                     pack2(hi[6], hi[7]));
-        *reinterpret_cast<uint4*>(base + 16384) = make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]),
-                                                             pack2(lo[4], lo[5]), pack2(lo[6], lo[7]));
+        uint8_t* base = out + (size_t)c * CH + swz16(r, u);
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) *reinterpret_cast<uint4*>(base + pp * TCW_PART) = pack8(pt[pp]);
     }
     if (tid < 128) aexp[(size_t)blockIdx.x * 128 + tid] = sA[tid];
 }
 
 // ---------------------------------------------------------------- GEMM-Z and the traces
 // Block: walker w0 + blockIdx.x / MT, pair tile m, one spin with n electrons.
-// Shared memory: with a_res the tile's A image (KC x 32 KB) stays resident and the
-// ring streams only the Bop chunks (NT rows hi + lo); otherwise every ring stage
-// holds an A chunk (32 KB) and a Bop chunk.  Then Ms, the staging of one matrix's
+// Shared memory: with a_res the tile's A image (KC chunks of NP x 16 KB) stays
+// resident and the ring streams only the Bop chunks (NT rows of each part);
+// otherwise every ring stage holds an A chunk and a Bop chunk.  Then Ms, the staging of one matrix's
 // Z blocks (128 rows x (n + 1) complex floats) for the transpose.
 // Tensor memory, buffer b of two: D (NT columns) and, FP16, its correction (NT).
 // Outputs: vpart[pair G1 + g] = Tr Z_{p,g} (float2; g = 0 is the one-body term),
 // exsum[pair] = sum_{g >= 1} Tr Z_{p,g}^2 (FP64 accumulation over the matrices).
-template <bool F16>
+template <int MODE>
 __global__ void __launch_bounds__(TCWZ_THREADS, 1)
     contract_tcw_kernel(int n, int G1, int KZ, int KC, int NT, int GB, int NTILES, int P, int PB, int MT, int S,
                         int a_res, long long w0, const uint8_t* __restrict__ Aimg, const int* __restrict__ aexp,
                         const uint8_t* __restrict__ Yimg, const int* __restrict__ yexp, float2* __restrict__ vpart,
                         double2* __restrict__ exsum, int* status, uint32_t lim) {
+    constexpr bool F16 = MODE != 0;
+    constexpr uint32_t CH = tcw_chunk(MODE);
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    const uint32_t bbytes = (uint32_t)NT * 256u;                      // one Bop chunk (hi + lo)
-    const uint32_t stage_bytes = (a_res ? 0u : TCW_CHUNK_A) + bbytes;
+    const uint32_t bpart = (uint32_t)NT * 128u;                       // one part of a Bop chunk
+    const uint32_t bbytes = bpart * (uint32_t)tcw_parts(MODE);       // one Bop chunk, all parts
+    const uint32_t stage_bytes = (a_res ? 0u : CH) + bbytes;
     uint8_t* Ares = sm;
-    uint8_t* ring = sm + (a_res ? (size_t)KC * TCW_CHUNK_A : 0);
+    uint8_t* ring = sm + (a_res ? (size_t)KC * CH : 0);
     float2* Ms = reinterpret_cast<float2*>(ring + (size_t)S * stage_bytes);
     const int ld = n + 1;                                             // row stride of Ms (complex)
     __shared__ uint64_t full_bar[TCW_MAXSTAGES], empty_bar[TCW_MAXSTAGES], dfull[2], dempty[2], a_bar, drain_bar;
@@ -463,7 +532,7 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
     const int m = blockIdx.x % MT;
     const int np = min(PB, P - m * PB);
     const long long pair0 = (w0 + wl) * P + (long long)m * PB;
-    const uint8_t* Atile = Aimg + (size_t)blockIdx.x * KC * TCW_CHUNK_A;
+    const uint8_t* Atile = Aimg + (size_t)blockIdx.x * KC * CH;
     const uint8_t* Ywalk = Yimg + (size_t)wl * NTILES * KC * bbytes;
     const int* yex = yexp + (size_t)wl * G1 * n;
     const uint32_t dcols = (F16 ? 2u : 1u) * (uint32_t)NT;              // one buffer
@@ -503,9 +572,9 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
         // ---- producer: the A tile once (a_res), then unit v = (N-tile v / KC, chunk v % KC)
         if (lane == 0) {
             if (a_res) {
-                tc::mbar_arrive_expect_tx(&a_bar, (uint32_t)KC * TCW_CHUNK_A);
+                tc::mbar_arrive_expect_tx(&a_bar, (uint32_t)KC * CH);
                 for (int c = 0; c < KC; ++c)
-                    tc::bulk_g2s(Ares + (size_t)c * TCW_CHUNK_A, Atile + (size_t)c * TCW_CHUNK_A, TCW_CHUNK_A, &a_bar);
+                    tc::bulk_g2s(Ares + (size_t)c * CH, Atile + (size_t)c * CH, CH, &a_bar);
             }
             int issued = 0;
             for (int v = 0; v < n_units; ++v) {
@@ -514,8 +583,8 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
                 const int t = v / KC, c = v % KC;
                 uint8_t* dst = ring + (size_t)st * stage_bytes;
                 tc::mbar_arrive_expect_tx(&full_bar[st], stage_bytes);
-                if (!a_res) tc::bulk_g2s(dst, Atile + (size_t)c * TCW_CHUNK_A, TCW_CHUNK_A, &full_bar[st]);
-                tc::bulk_g2s(dst + (a_res ? 0 : TCW_CHUNK_A), Ywalk + ((size_t)t * KC + c) * bbytes, bbytes, &full_bar[st]);
+                if (!a_res) tc::bulk_g2s(dst, Atile + (size_t)c * CH, CH, &full_bar[st]);
+                tc::bulk_g2s(dst + (a_res ? 0 : CH), Ywalk + ((size_t)t * KC + c) * bbytes, bbytes, &full_bar[st]);
                 ++issued;
             }
             for (int v = max(0, issued - S); v < issued; ++v)
@@ -540,21 +609,28 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
                     tc::fence_after_sync();
                     const int ks = min(4, (KZ - 64 * c) / 16);
                     const uint8_t* sbase = ring + (size_t)st * stage_bytes;
-                    const uint32_t pa = tc::smem_u32(a_res ? Ares + (size_t)c * TCW_CHUNK_A : sbase);
-                    const uint32_t pb = tc::smem_u32(sbase + (a_res ? 0 : TCW_CHUNK_A));
+                    const uint32_t pa = tc::smem_u32(a_res ? Ares + (size_t)c * CH : sbase);
+                    const uint32_t pb = tc::smem_u32(sbase + (a_res ? 0 : CH));
                     for (int s = 0; s < ks; ++s) {
-                        const uint64_t ah = tc::desc_sw128(pa + s * 32), al = tc::desc_sw128(pa + 16384 + s * 32);
-                        const uint64_t bh = tc::desc_sw128(pb + s * 32),
-                                       bl = tc::desc_sw128(pb + (uint32_t)NT * 128 + s * 32);
+                        const uint64_t a0 = tc::desc_sw128(pa + s * 32), a1 = tc::desc_sw128(pa + TCW_PART + s * 32);
+                        const uint64_t b0 = tc::desc_sw128(pb + s * 32), b1 = tc::desc_sw128(pb + bpart + s * 32);
                         const uint32_t first = (c == 0 && s == 0) ? 0u : 1u;
-                        tc::mma_f16(dh, ah, bh, idesc, first);
-                        if (F16) {
-                            tc::mma_f16(dl, ah, bl, idesc, first);
-                            tc::mma_f16(dl, al, bh, idesc, 1u);
-                            tc::mma_f16(dl, al, bl, idesc, 1u);
+                        tc::mma_f16(dh, a0, b0, idesc, first);
+                        if constexpr (MODE == 2) {
+                            const uint64_t a2 = tc::desc_sw128(pa + 2 * TCW_PART + s * 32),
+                                           b2 = tc::desc_sw128(pb + 2 * bpart + s * 32);
+                            tc::mma_f16(dl, a0, b1, idesc, first);
+                            tc::mma_f16(dl, a1, b0, idesc, 1u);
+                            tc::mma_f16(dl, a1, b1, idesc, 1u);
+                            tc::mma_f16(dl, a0, b2, idesc, 1u);
+                            tc::mma_f16(dl, a2, b0, idesc, 1u);
+                        } else if constexpr (MODE == 1) {
+                            tc::mma_f16(dl, a0, b1, idesc, first);
+                            tc::mma_f16(dl, a1, b0, idesc, 1u);
+                            tc::mma_f16(dl, a1, b1, idesc, 1u);
                         } else {
-                            tc::mma_f16(dh, ah, bl, idesc, 1u);
-                            tc::mma_f16(dh, al, bh, idesc, 1u);
+                            tc::mma_f16(dh, a0, b1, idesc, 1u);
+                            tc::mma_f16(dh, a1, b0, idesc, 1u);
                         }
                     }
                     tc::mma_commit(&empty_bar[st]);
@@ -735,12 +811,13 @@ struct TcwShape {
     size_t ximg, yimg, aimg, yexp, aexp;
 };
 
-size_t tcw_z_smem(int KC, int NT, int n, int S, bool a_res) {
-    const size_t stage = (a_res ? 0 : TCW_CHUNK_A) + (size_t)NT * 256;
-    return 1024 + (a_res ? (size_t)KC * TCW_CHUNK_A : 0) + (size_t)S * stage + (size_t)128 * (n + 1) * 8;
+size_t tcw_z_smem(int KC, int NT, int n, int S, bool a_res, int mode) {
+    const size_t stage = (a_res ? 0 : tcw_chunk(mode)) + (size_t)NT * 128 * tcw_parts(mode);
+    return 1024 + (a_res ? (size_t)KC * tcw_chunk(mode) : 0) + (size_t)S * stage + (size_t)128 * (n + 1) * 8;
 }
 
-bool tcw_spin(int n, int P, int KC, int G1, bool f16, TcwSpin& s) {
+bool tcw_spin(int n, int P, int KC, int G1, int mode, TcwSpin& s) {
+    const bool f16 = mode != 0;
     s.n = n;
     if (n < 1 || n > 64) return false;
     s.PB = 128 / n;
@@ -748,52 +825,55 @@ bool tcw_spin(int n, int P, int KC, int G1, bool f16, TcwSpin& s) {
     s.MT = (P + s.PB - 1) / s.PB;
     const int per = 2 * n;
     const int maxcols = f16 ? 128 : 256;                 // two buffers of (1 or 2) x NT columns in 512
-    s.GB = 0;
-    for (int gb = maxcols / per; gb >= 1; --gb)
-        if (tcw_round16(gb * per) <= maxcols) { s.GB = gb; break; }
-    if (s.GB < 1) return false;
-    if (s.GB > G1) s.GB = G1;
-    s.NT = tcw_round16(s.GB * per);
-    s.NTILES = (G1 + s.GB - 1) / s.GB;
-    for (int a_res = 1; a_res >= 0; --a_res)
-        for (int S = TCW_MAXSTAGES; S >= 2; --S) {
-            const size_t sm = tcw_z_smem(KC, s.NT, n, S, a_res);
-            if (sm <= TCW_SMEM_MAX) {
-                s.a_res = a_res;
-                s.S = S;
-                s.smem = sm;
-                return true;
+    // the widest block of matrices whose ring fits beside the staging area
+    for (int gb = maxcols / per; gb >= 1; --gb) {
+        if (tcw_round16(gb * per) > maxcols) continue;
+        s.GB = gb > G1 ? G1 : gb;
+        s.NT = tcw_round16(s.GB * per);
+        s.NTILES = (G1 + s.GB - 1) / s.GB;
+        for (int a_res = 1; a_res >= 0; --a_res)
+            for (int S = TCW_MAXSTAGES; S >= 2; --S) {
+                const size_t sm = tcw_z_smem(KC, s.NT, n, S, a_res, mode);
+                if (sm <= TCW_SMEM_MAX) {
+                    s.a_res = a_res;
+                    s.S = S;
+                    s.smem = sm;
+                    return true;
+                }
             }
-        }
+    }
     return false;
 }
 
-bool tcw_shape(int N, int nu, int nd, int G, long long W, int P, bool f16, TcwShape& s) {
+bool tcw_shape(int N, int nu, int nd, int G, long long W, int P, int mode, TcwShape& s) {
+    if (mode < 0 || mode > 2) return false;
+    const bool f16 = mode != 0;
+    const size_t CH = tcw_chunk(mode);
+    const int NP = tcw_parts(mode);
     if (N < 1 || N > 256 || nu < 1 || nu > 64 || nd < 0 || nd > nu) return false;
     s.N16 = tcw_round16(N);
     s.KZ = 2 * s.N16;
     s.KC = (s.KZ + 63) / 64;
     s.KCX = (s.N16 + 63) / 64;
     s.G1 = G + 1;
-    if (!tcw_spin(nu, P, s.KC, s.G1, f16, s.sp[0])) return false;
-    if (nd > 0 && !tcw_spin(nd, P, s.KC, s.G1, f16, s.sp[1])) return false;
+    if (!tcw_spin(nu, P, s.KC, s.G1, mode, s.sp[0])) return false;
+    if (nd > 0 && !tcw_spin(nd, P, s.KC, s.G1, mode, s.sp[1])) return false;
     if (nd == 0) s.sp[1] = s.sp[0], s.sp[1].n = 0;
-    // GEMM-Y: PW (KCX x 32 KB) and a ring of at least two half-chunks of N16 rows
+    // GEMM-Y: PW (KCX chunks) and a ring of at least two chunk parts of N16 rows
     const size_t RX = (size_t)s.N16 * 128;
     s.SY = 0;
     for (int S = TCW_MAXSTAGES; S >= 2; --S)
-        if (1024 + (size_t)s.KCX * TCW_CHUNK_A + S * RX <= TCW_SMEM_MAX) { s.SY = S; break; }
+        if (1024 + (size_t)s.KCX * CH + S * RX <= TCW_SMEM_MAX) { s.SY = S; break; }
     if (!s.SY) return false;
-    s.smem_y = 1024 + (size_t)s.KCX * TCW_CHUNK_A + s.SY * RX;
+    s.smem_y = 1024 + (size_t)s.KCX * CH + s.SY * RX;
     if ((f16 ? 2 : 1) * s.N16 > 512) return false;
     s.GPB = 64;
-    // Y images: per walker and spin NTILES x KC chunks of NT x 256 bytes; chunks of
-    // walkers sized to about 4 GB of images
+    // Y images: per walker and spin NTILES x KC chunks of NT x 128 bytes per part
     size_t per_walker = 0, aper = 0;
     for (int q = 0; q < 2; ++q) {
         if (s.sp[q].n == 0) continue;
-        per_walker = std::max(per_walker, (size_t)s.sp[q].NTILES * s.KC * s.sp[q].NT * 256);
-        aper = std::max(aper, (size_t)s.sp[q].MT * s.KC * TCW_CHUNK_A);
+        per_walker = std::max(per_walker, (size_t)s.sp[q].NTILES * s.KC * s.sp[q].NT * 128 * NP);
+        aper = std::max(aper, (size_t)s.sp[q].MT * s.KC * CH);
     }
     // about 12 GB of Y images per chunk, and a chunk's GEMM-Z blocks (WB x MT per
     // spin) a whole number of waves of 152 blocks when the population allows
@@ -801,7 +881,7 @@ bool tcw_shape(int N, int nu, int nd, int G, long long W, int P, bool f16, TcwSh
     s.WB = std::max(1LL, std::min(W, (long long)(budget / per_walker)));
     const int mt = std::max(s.sp[0].MT, s.sp[1].MT);
     if (s.WB < W && s.WB * mt >= 152) s.WB = std::max(1LL, (s.WB * mt / 152) * 152 / mt);
-    s.ximg = (size_t)s.G1 * s.KCX * 2 * RX;
+    s.ximg = (size_t)s.G1 * s.KCX * NP * RX;
     s.yimg = (size_t)s.WB * per_walker;
     s.aimg = (size_t)s.WB * aper;
     s.yexp = (size_t)s.WB * s.G1 * nu * sizeof(int);
@@ -854,12 +934,12 @@ __global__ void tcw_lexp_kernel(int N, int G1, const double* __restrict__ h, con
     if (threadIdx.x == 0) lexp[g] = f16 ? exp_into(red[0], 7) : 0;
 }
 
-template <bool F16>
+template <int MODE>
 cudaError_t tcw_run(cudaStream_t st, const Dims& d, const TcwShape& s, const TcwWork& w, const double2* Bm,
                     const double2* phi, double2* vpair, double2* epair, int* status) {
     cudaError_t e;
-    if ((e = raise_smem_limit((const void*)tcw_y_kernel<F16>, s.smem_y)) != cudaSuccess) return e;
-    if ((e = raise_smem_limit((const void*)contract_tcw_kernel<F16>, std::max(s.sp[0].smem, s.sp[1].smem))) !=
+    if ((e = raise_smem_limit((const void*)tcw_y_kernel<MODE>, s.smem_y)) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void*)contract_tcw_kernel<MODE>, std::max(s.sp[0].smem, s.sp[1].smem))) !=
         cudaSuccess)
         return e;
     const long long W = d.pairs / d.P;
@@ -870,12 +950,12 @@ cudaError_t tcw_run(cudaStream_t st, const Dims& d, const TcwShape& s, const Tcw
             const TcwSpin& sp = s.sp[q];
             if (sp.n == 0) continue;
             const int col0 = q ? d.nu : 0;
-            tcw_y_kernel<F16><<<(unsigned)(wb * n_gblk), TCW_THREADS, s.smem_y, st>>>(
+            tcw_y_kernel<MODE><<<(unsigned)(wb * n_gblk), TCW_THREADS, s.smem_y, st>>>(
                 d.N, d.nt, col0, sp.n, s.G1, s.N16, s.KCX, s.SY, s.GPB, n_gblk, w0, phi, w.ximg, w.lexp, sp.NT, sp.GB,
                 s.KC, sp.NTILES, w.yimg, w.yexp, status, d.wait_polls);
-            tcw_a_kernel<F16><<<(unsigned)(wb * sp.MT), 256, 0, st>>>(d.N, d.nt, col0, sp.n, d.P, sp.PB, sp.MT, s.N16,
+            tcw_a_kernel<MODE><<<(unsigned)(wb * sp.MT), 256, 0, st>>>(d.N, d.nt, col0, sp.n, d.P, sp.PB, sp.MT, s.N16,
                                                                       s.KC, w0, Bm, w.aimg, w.aexp);
-            contract_tcw_kernel<F16><<<(unsigned)(wb * sp.MT), TCWZ_THREADS, sp.smem, st>>>(
+            contract_tcw_kernel<MODE><<<(unsigned)(wb * sp.MT), TCWZ_THREADS, sp.smem, st>>>(
                 sp.n, s.G1, s.KZ, s.KC, sp.NT, sp.GB, sp.NTILES, d.P, sp.PB, sp.MT, sp.S, sp.a_res, w0, w.aimg, w.aexp,
                 w.yimg, w.yexp, w.vpart[q], w.exsum[q], status, d.wait_polls);
             count_launches(3);
@@ -891,27 +971,29 @@ cudaError_t tcw_run(cudaStream_t st, const Dims& d, const TcwShape& s, const Tcw
 
 }  // namespace
 
-bool contract_tcw_supported(int N, int nu, int nd, int G, long long W, int P, bool f16) {
+bool contract_tcw_supported(int N, int nu, int nd, int G, long long W, int P, int mode) {
     TcwShape s;
-    return tcw_shape(N, nu, nd, G, W, P, f16, s);
+    return tcw_shape(N, nu, nd, G, W, P, mode, s);
 }
 
-size_t contract_tcw_work_bytes(int N, int nu, int nd, int G, long long W, int P, bool f16) {
+size_t contract_tcw_work_bytes(int N, int nu, int nd, int G, long long W, int P, int mode) {
     TcwShape s;
-    if (!tcw_shape(N, nu, nd, G, W, P, f16, s)) return 0;
+    if (!tcw_shape(N, nu, nd, G, W, P, mode, s)) return 0;
     return tcw_total(s, G, W * (long long)P);
 }
 
 cudaError_t contract_tcw_prepare(cudaStream_t st, const Dims& d, const double* h, const double* L, void* work,
-                                 bool f16) {
+                                 int mode) {
     TcwShape s;
-    if (!tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, f16, s)) return cudaErrorInvalidValue;
+    if (!tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, mode, s)) return cudaErrorInvalidValue;
     TcwWork w = tcw_carve(work, s, d.G, d.pairs);
-    tcw_lexp_kernel<<<(unsigned)s.G1, 256, 0, st>>>(d.N, s.G1, h, L, f16 ? 1 : 0, w.lexp);
-    if (f16)
-        tcw_x_image_kernel<true><<<1024, 256, 0, st>>>(d.N, s.N16, s.KCX, s.G1, h, L, w.lexp, w.ximg);
+    tcw_lexp_kernel<<<(unsigned)s.G1, 256, 0, st>>>(d.N, s.G1, h, L, mode != 0 ? 1 : 0, w.lexp);
+    if (mode == 2)
+        tcw_x_image_kernel<2><<<1024, 256, 0, st>>>(d.N, s.N16, s.KCX, s.G1, h, L, w.lexp, w.ximg);
+    else if (mode == 1)
+        tcw_x_image_kernel<1><<<1024, 256, 0, st>>>(d.N, s.N16, s.KCX, s.G1, h, L, w.lexp, w.ximg);
     else
-        tcw_x_image_kernel<false><<<1024, 256, 0, st>>>(d.N, s.N16, s.KCX, s.G1, h, L, w.lexp, w.ximg);
+        tcw_x_image_kernel<0><<<1024, 256, 0, st>>>(d.N, s.N16, s.KCX, s.G1, h, L, w.lexp, w.ximg);
     count_launches(2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -921,13 +1003,14 @@ cudaError_t contract_tcw_prepare(cudaStream_t st, const Dims& d, const double* h
 }
 
 cudaError_t contract_tcw(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,
-                         double2* vpair, double2* epair, int* status, bool f16) {
+                         double2* vpair, double2* epair, int* status, int mode) {
     TcwShape s;
-    if (!tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, f16, s)) return cudaErrorInvalidValue;
+    if (!tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, mode, s)) return cudaErrorInvalidValue;
     if (d.pairs <= 0) return cudaSuccess;
     TcwWork w = tcw_carve(work, s, d.G, d.pairs);
-    return f16 ? tcw_run<true>(st, d, s, w, Bm, phi, vpair, epair, status)
-               : tcw_run<false>(st, d, s, w, Bm, phi, vpair, epair, status);
+    if (mode == 2) return tcw_run<2>(st, d, s, w, Bm, phi, vpair, epair, status);
+    if (mode == 1) return tcw_run<1>(st, d, s, w, Bm, phi, vpair, epair, status);
+    return tcw_run<0>(st, d, s, w, Bm, phi, vpair, epair, status);
 }
 
 }  // namespace afq

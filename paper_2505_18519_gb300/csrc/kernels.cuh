@@ -108,12 +108,13 @@ cudaError_t contract_tc(cudaStream_t st, const Dims& d, const void* image, const
 // overlap_lu with OVL_TRIAL.  work: contract_tcw_work_bytes bytes (the split
 // image of X_g, per chunk of walkers the images of Y_g and B_p, per-pair traces);
 // contract_tcw_prepare fills the X image once (h and L must not change after).
-bool contract_tcw_supported(int N, int nu, int nd, int G, long long W, int P, bool f16);
-size_t contract_tcw_work_bytes(int N, int nu, int nd, int G, long long W, int P, bool f16);
+// mode: operand arithmetic, 0 bf16x3, 1 fp16x3, 2 fp16x6 (tc_mode of the config).
+bool contract_tcw_supported(int N, int nu, int nd, int G, long long W, int P, int mode);
+size_t contract_tcw_work_bytes(int N, int nu, int nd, int G, long long W, int P, int mode);
 cudaError_t contract_tcw_prepare(cudaStream_t st, const Dims& d, const double* h, const double* L, void* work,
-                                 bool f16);
+                                 int mode);
 cudaError_t contract_tcw(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,
-                         double2* vpair, double2* epair, int* status, bool f16);
+                         double2* vpair, double2* epair, int* status, int mode);
 
 // trial_complex.cu: complex and multi-slice trial samples (FP64 path).
 // Out = exp(alpha S) V0 per problem (S real symmetric in S_all; V0 = the real

@@ -97,6 +97,53 @@ def test_general_walker_side_form_bf16(name):
     assert np.max(np.abs(obs["force_bias"] - m["v_bar"])[live]) < 1e-4
 
 
+FP16X6_SYSTEMS = [n for n in SYSTEMS if SYSTEMS[n][0].N <= 192 and n != "one_spin_n150"]
+
+
+@pytest.mark.parametrize("name", FP16X6_SYSTEMS)
+def test_three_part_operands_against_oracle(name):
+    """fp16x6 (integer FP16 part and two FP16 remainders per operand, six products)
+    with its refinement on: the same targets as fp16x3."""
+    e, obs, m, ost = _measure_case(name, "fp16x6")
+    live = ost.weight > 0
+    d_walker = np.abs(e["e_walker"] - m["e_bar"])[live]
+    print("%s: worst walker %.2e" % (name, d_walker.max()))
+    assert np.max(np.abs(obs["logov"].real - m["logov"].real)) < 1e-9
+    assert np.max(d_walker) < E_WALKER_TOL
+    assert np.max(np.abs(obs["force_bias"] - m["v_bar"])[live]) < 1e-4
+    num, den = oa.mixed_energy(ost.weight, m["e_bar"])
+    assert abs(e["e_mix"] - num / den) < E_MIX_TOL
+
+
+def test_three_part_operands_are_more_precise():
+    """Without refinement, the per-pair local energies of fp16x6 against the FP64
+    path sit well below fp16x3's (its operands carry about 31 bits against 20, the
+    traces see FP32 entries): on the 120-orbital system the median error falls at
+    least eightfold."""
+    spec, run = ai.CONFIGS["large_n120"]
+    s = ai.make_system(spec)
+    W, P = 8, run.n_paths
+    res, state = {}, None
+    for prec in ("fp64", "fp16x3", "fp16x6"):
+        kw = dict(tc_form="walker", wait_polls=1 << 24) if prec != "fp64" else {}
+        cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau,
+                              ai.philox_run_seed(4), n_burn=20, precision=prec, refine_tol=0.0, **kw)
+        ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U)
+        if state is None:
+            state = ctx.save_state()
+        else:
+            ctx.load_state(state)
+        ctx.energy()
+        res[prec] = ctx.observables()["e_local"]
+        ctx.close()
+    d3 = np.abs(res["fp16x3"] - res["fp64"]).ravel()
+    d6 = np.abs(res["fp16x6"] - res["fp64"]).ravel()
+    print("median per-pair error fp16x3 %.2e, fp16x6 %.2e; max %.2e, %.2e"
+          % (np.median(d3), np.median(d6), d3.max(), d6.max()))
+    assert np.median(d6) * 8 < np.median(d3)
+    assert d6.max() * 4 < d3.max()
+
+
 def test_refining_every_pair_matches_the_oracle():
     """With a vanishing tolerance every pair is recomputed in double-float by the
     refinement (Theta formed for the listed pairs in place of B_p), so per-pair
@@ -135,8 +182,10 @@ def test_large_systems_against_fp64_gpu_path(config, W):
     spec, run = ai.CONFIGS[config]
     s = ai.make_system(spec)
     P = run.n_paths
-    res, refined, state = {}, None, None
-    for prec, tol in (("fp64", 1e-4), ("fp16x3", 1e-4), ("fp16x3", 0.0)):
+    res, refined, state = {}, {}, None
+    for prec, tol in (("fp64", 1e-4), ("fp16x3", 1e-4), ("fp16x3", 0.0), ("fp16x6", 1e-4)):
+        if prec == "fp16x6" and spec.N > 192:
+            continue
         kw = dict(tc_form="walker", wait_polls=1 << 24) if prec != "fp64" else {}
         cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau,
                               ai.philox_run_seed(4), n_burn=20, precision=prec, refine_tol=tol, **kw)
@@ -146,15 +195,22 @@ def test_large_systems_against_fp64_gpu_path(config, W):
         else:
             ctx.load_state(state)
         res[(prec, tol)] = ctx.energy(walkers=True)
-        if prec == "fp16x3" and tol > 0:
-            refined = ctx.stats()["refined_pairs"]
+        if prec != "fp64" and tol > 0:
+            refined[(prec, tol)] = ctx.stats()["refined_pairs"]
         ctx.close()
     ref = res[("fp64", 1e-4)]
     d_walker = np.abs(res[("fp16x3", 1e-4)]["e_walker"] - ref["e_walker"])
     d_raw = np.abs(res[("fp16x3", 0.0)]["e_walker"] - ref["e_walker"])
     d_mix = abs(res[("fp16x3", 1e-4)]["e_mix"] - ref["e_mix"])
     print("%s: refined %d of %d pairs; worst walker %.2e (tensor cores alone %.2e), median %.2e, dE_mix %.2e"
-          % (config, refined, W * P, d_walker.max(), d_raw.max(), np.median(d_walker), d_mix))
+          % (config, refined[("fp16x3", 1e-4)], W * P, d_walker.max(), d_raw.max(), np.median(d_walker), d_mix))
     assert np.max(d_walker) < E_WALKER_TOL
     assert d_mix < E_MIX_TOL
-    assert 0 < refined <= W * P
+    assert 0 < refined[("fp16x3", 1e-4)] <= W * P
+    if ("fp16x6", 1e-4) in res:
+        d6 = np.abs(res[("fp16x6", 1e-4)]["e_walker"] - ref["e_walker"])
+        print("%s fp16x6: refined %d, worst walker %.2e, dE_mix %.2e"
+              % (config, refined[("fp16x6", 1e-4)], d6.max(), abs(res[("fp16x6", 1e-4)]["e_mix"] - ref["e_mix"])))
+        assert np.max(d6) < E_WALKER_TOL
+        assert abs(res[("fp16x6", 1e-4)]["e_mix"] - ref["e_mix"]) < E_MIX_TOL
+        assert refined[("fp16x6", 1e-4)] < refined[("fp16x3", 1e-4)]

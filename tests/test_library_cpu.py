@@ -126,6 +126,26 @@ def test_tensor_core_form_and_wait_limit_fields_reach_the_library(L):
     assert a > 0 and b > 0 and a != b
 
 
+def test_three_part_precision_takes_only_the_general_walker_side_form(L):
+    """fp16x6 (three FP16 parts per operand) runs only on the general walker-side
+    form, up to N = 192: the auto form picks it, the per-pair form and N = 200 are
+    refused, and its work space holds three-part images (more than fp16x3's)."""
+    kw = dict(precision="fp16x6")
+    for shape in ((50, 10, 10, 250, 50, 8, 32), (120, 24, 24, 600, 120, 8, 64), (192, 40, 40, 100, 20, 4, 16)):
+        assert lib.contract_kernel(lib.make_config(*shape, 0.005, 1, **kw)) == "contract_tcw_kernel", shape
+    with pytest.raises(lib.AfqmcError):
+        lib.contract_kernel(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, tc_form="per_pair", **kw))
+    with pytest.raises(lib.AfqmcError):
+        lib.contract_kernel(lib.make_config(200, 40, 40, 1000, 200, 8, 16, 0.005, 1, **kw))
+    a = lib.workspace_bytes(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, tc_form="walker",
+                                            precision="fp16x3"))
+    b = lib.workspace_bytes(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, **kw))
+    assert b > a > 0
+    c = lib.make_config(8, 4, 4, 32, 8, 64, 16, 0.01, 1, **kw)
+    c.precision = 4
+    assert lib.workspace_bytes(c) == 0
+
+
 def test_trial_fields_reach_the_library(L):
     """The trial's alpha and slice count select the complex-trial contraction, and
     the combinations it does not support are refused (host only)."""
