@@ -173,7 +173,15 @@ typedef struct {
                            than alpha = 1, one slice needs precision FP64, a proposal other than the
                            learned one, rcache = 0, and 48 N n_up bytes of shared memory at most
                            200 KB; Phi is then stored and returned as complex (state buffer) */
+    int trial_form;     /* mixed precision: how the trial orbitals exp(S) Phi0 of Eq. (20)-(21) are formed.
+                           AFQMC_TRIAL_AUTO (0, default): the Chebyshev products S V on the tensor cores
+                           (each operand split into five 8-bit integer digits, the digit products of orders
+                           0-5 accumulated exactly in FP32, combined in double-float: about 40 bits) where
+                           N <= 128 and n_up <= 32, else as AFQMC_TRIAL_DF; AFQMC_TRIAL_DF (1): the whole
+                           recurrence in double-float arithmetic (about 44 bits) on the CUDA cores */
 } afqmc_config;
+
+enum { AFQMC_TRIAL_AUTO = 0, AFQMC_TRIAL_DF = 1 };
 
 enum { AFQMC_TC_AUTO = 0, AFQMC_TC_PER_PAIR = 1, AFQMC_TC_WALKER = 2 };
 
@@ -246,6 +254,17 @@ afqmc_status afqmc_energy(afqmc_ctx* ctx, double* e_mix, double* sum_w, double* 
  * word is set. */
 afqmc_status afqmc_energy_paths(afqmc_ctx* ctx, int rounds, int sweeps, double* e_mix, double* e_walker,
                                 double* ratio);
+
+/* Trial samples Phi(x) (Eq. (20)-(21): exp(sum_k x_k U_k) Phi0; the complex or
+ * multi-slice forms of Eq. (19), (30) when the context has them) for n rows of
+ * hidden variables, in the arithmetic the context's precision uses for its own
+ * paths (FP64; mixed precision: trial_form).  Uses the proposal buffers only:
+ * the walkers and paths are left as they are.
+ *   x    n*K doubles, row-major, host or device
+ *   out  n*N*n_up doubles (real trial) or n*N*n_up complex values (interleaved),
+ *        row-major per sample, host or device
+ * 0 <= n <= n_walkers * n_paths, else AFQMC_ERR_ARG.  Synchronises the stream. */
+afqmc_status afqmc_trial_orbitals(afqmc_ctx* ctx, const double* x, int64_t n, double* out);
 
 /* After afqmc_energy: copy per-pair and per-walker measurements to host arrays
  * (each nullable):

@@ -23,6 +23,7 @@ PROPOSALS = {"prior": 0, "pcn": 1, "rw": 2, "mlp": 3}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "fp16x3": 2, "fp16x6": 3}
 IMPORTANCE = {"hybrid": 0, "local_energy": 1}
 TC_FORMS = {"auto": 0, "per_pair": 1, "walker": 2}
+TRIAL_FORMS = {"auto": 0, "df": 1}
 STATE_MAGIC = 0x4146514D43535431
 
 
@@ -39,6 +40,7 @@ class AfqmcConfig(ctypes.Structure):
         ("importance", ctypes.c_int), ("pop_period", ctypes.c_int), ("rcache", ctypes.c_int),
         ("wait_polls", ctypes.c_int64), ("tc_form", ctypes.c_int),
         ("trial_alpha_re", ctypes.c_double), ("trial_alpha_im", ctypes.c_double), ("trial_slices", ctypes.c_int),
+        ("trial_form", ctypes.c_int),
     ]
 
 
@@ -51,7 +53,7 @@ EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc
            "afqmc_launch_count", "afqmc_contract_kernel", "afqmc_autotune", "afqmc_batch_create", "afqmc_batch_step", "afqmc_batch_sync",
            "afqmc_batch_destroy", "afqmc_mlp_n_params", "afqmc_mlp_params", "afqmc_mlp_eval", "afqmc_mlp_state",
            "afqmc_fp64_fma_rate", "afqmc_local_energy_noalloc", "afqmc_noalloc_scratch_bytes",
-           "afqmc_noalloc_last_error")
+           "afqmc_noalloc_last_error", "afqmc_trial_orbitals")
 
 PHASES = ("overlap", "contract", "average", "fields", "propagate", "ratio", "propose", "trial_orbitals",
           "mcmc_overlap", "accept", "finish", "comb", "refine")
@@ -83,6 +85,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.afqmc_energy_paths.restype = I
     lib.afqmc_observables.argtypes = [P, P, P, P]
     lib.afqmc_observables.restype = I
+    lib.afqmc_trial_orbitals.argtypes = [P, P, ctypes.c_int64, P]
+    lib.afqmc_trial_orbitals.restype = I
     lib.afqmc_history.argtypes = [P, P, I, ctypes.POINTER(I)]
     lib.afqmc_history.restype = I
     lib.afqmc_stats.argtypes = [P, P, I]
@@ -152,7 +156,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
                 pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10, walker_offset=0, rw_step=0.3, mlp_mix=0.1,
                 mlp_lr=1e-3, mlp_train=False, refine_tol=1e-4, importance="hybrid",
                 pop_period=0, rcache=False, wait_polls=0, tc_form="auto", trial_alpha=1.0,
-                trial_slices=1) -> AfqmcConfig:
+                trial_slices=1, trial_form="auto") -> AfqmcConfig:
     lib = load_library()
     c = AfqmcConfig()
     lib.afqmc_config_default(ctypes.byref(c))
@@ -170,6 +174,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
     c.tc_form = TC_FORMS[tc_form]
     c.trial_alpha_re, c.trial_alpha_im = complex(trial_alpha).real, complex(trial_alpha).imag
     c.trial_slices = int(trial_slices)
+    c.trial_form = TRIAL_FORMS[trial_form]
     return c
 
 
@@ -232,6 +237,14 @@ class Context:
         out = dict(e_mix=e.value, sum_w=sw.value, mean_sign=ms.value)
         if walkers:
             out["e_walker"] = ew.view(np.complex128)
+        return out
+
+    def trial_orbitals(self, x) -> np.ndarray:
+        """Phi(x) for the rows of x (n x K): (n, N, n_up), complex for a complex or multi-slice trial."""
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, self.K)
+        cplx = complex(self.cfg.trial_alpha_re, self.cfg.trial_alpha_im) != 1.0 or self.cfg.trial_slices > 1
+        out = np.empty((x.shape[0], self.N, self.nu), dtype=np.complex128 if cplx else np.float64)
+        _check(load_library().afqmc_trial_orbitals(self._ctx, x.ctypes.data, x.shape[0], out.ctypes.data))
         return out
 
     def energy_paths(self, rounds: int, sweeps: int):

@@ -69,6 +69,9 @@ static int tc_mode(const afqmc_config* c) {
 int tc_kind(const afqmc_config* c) {
     const bool f16 = c->precision == AFQMC_PRECISION_FP16X3;
     const bool tcw = contract_tcw_supported(c->N, c->n_up, c->n_dn, c->n_chol, c->n_walkers, c->n_paths, tc_mode(c));
+    // complex or multi-slice trial samples: the walker-side form, whose per-pair
+    // operand B_p = conj(Phi_p) A_p^-T is complex for a real trial already
+    if (general_trial(c)) return c->tc_form != AFQMC_TC_PER_PAIR && tcw ? 5 : -1;
     if (c->precision == AFQMC_PRECISION_FP16X6) {   // the walker-side form only
         if (c->tc_form == AFQMC_TC_PER_PAIR) return -1;
         return tcw ? 5 : -1;
@@ -228,6 +231,7 @@ static const char* check_config(const afqmc_config* c) {
     if (c->pop_period > 0 && c->n_walkers > 65535) return "population control supports at most 65535 walkers";
     if (c->rcache != 0 && c->rcache != 1) return "rcache must be 0 or 1";
     if (c->wait_polls < 0 || c->wait_polls > (1ll << 31)) return "wait_polls must be in [0, 2^31]";
+    if (c->trial_form != AFQMC_TRIAL_AUTO && c->trial_form != AFQMC_TRIAL_DF) return "unknown trial_form";
     if (c->rcache && c->precision != AFQMC_PRECISION_FP64) return "rcache needs precision FP64";
     if (c->rcache && !contract_fp64r_supported(c->N, c->n_up, c->n_dn))
         return "sizes too large for the cached half-rotation form (Theta and one matrix per warp, 4 warps per block)";
@@ -241,7 +245,6 @@ static const char* check_config(const afqmc_config* c) {
         (c->trial_alpha_re == 0.0 && c->trial_alpha_im == 0.0))
         return "trial alpha must be finite and non-zero";
     if (general_trial(c)) {
-        if (c->precision != AFQMC_PRECISION_FP64) return "complex or multi-slice trials need precision FP64";
         if (c->proposal == AFQMC_PROPOSAL_MLP)
             return "the learned proposal is defined for the one-slice real trial only";
         if (c->rcache) return "complex or multi-slice trials need rcache = 0";
@@ -362,6 +365,9 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     w.xprop = (double*)take(pairs * K * 8);
     w.Sprop = (double*)take(pairs * NN * 8);
     w.Phiprop = (double*)take(pairs * phi_stride(d) * 8);
+    if (c->precision != AFQMC_PRECISION_FP64) {
+        w.cheb_redo = (int*)take((pairs + 1) * 4);   // list, then its count at [pairs]
+    }
     w.logdet_prop = (double2*)take(pairs * 2 * 16);
     w.history = (double*)take((size_t)c->history_capacity * 4 * 8);
     w.reduce = (double*)take(8 * 8);
@@ -435,6 +441,12 @@ static bool s_in_df(const afqmc_ctx* ctx) {
     return ctx->cfg.precision != AFQMC_PRECISION_FP64 && trial_orbitals_df_supported(ctx->d.N, ctx->d.nu);
 }
 
+// Trial orbitals of the mixed-precision path on the tensor cores (trial_tc.cu).
+static bool trial_on_tc(const afqmc_ctx* ctx) {
+    return ctx->cfg.precision != AFQMC_PRECISION_FP64 && ctx->cfg.trial_form == AFQMC_TRIAL_AUTO &&
+           trial_orbitals_tc_supported(ctx->d.N, ctx->d.nu);
+}
+
 // S_m = sum_k X[m, k] U_k into ws.Sprop for `M` rows of X.
 static cudaError_t form_S(afqmc_ctx* ctx, const double* X, long long M) {
     const Dims& d = ctx->d;
@@ -452,6 +464,9 @@ static cudaError_t trial_orbitals_of(afqmc_ctx* ctx, long long problems, double*
     Workspace& w = ctx->ws;
     if (ctx->cfg.precision == AFQMC_PRECISION_FP64)
         return trial_orbitals(ctx->stream, d.N, d.nu, problems, w.Sprop, w.Phi0, Out, alive, P, w.status, d.cheb_threads);
+    if (trial_on_tc(ctx))
+        return trial_orbitals_tc(ctx->stream, d.N, d.nu, problems, w.Sprop, s_in_df(ctx), w.Phi0, Out, alive, P, w.status,
+                                 w.cheb_redo, w.cheb_redo + d.pairs, d.wait_polls);
     return trial_orbitals_df(ctx->stream, d.N, d.nu, problems, w.Sprop, w.Phi0, Out, alive, P, w.status, d.cheb_threads,
                              s_in_df(ctx));
 }
@@ -558,13 +573,17 @@ static afqmc_status measure(afqmc_ctx* ctx) {
         for (int spin = 0; spin < 2; ++spin)
             CK(overlap_lu(s, d, spin, w.Phi, phi_stride(d), w.phi, w.logdet_new, w.Theta, nullptr, w.status, d.pairs,
                           d.P, OVL_THETA, nullptr, w.refine_items, w.refine_n));
-        CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n, d.pairs,
-                                w.hdf, w.Ldf));
+        if (d.cphi)   // complex trial samples: the listed pairs in FP64
+            CK(contract_fp64c(s, d, w.h, w.L, reinterpret_cast<const double2*>(w.Phi), w.Theta, w.vpair, w.epair,
+                              w.refine_items, w.refine_n));
+        else
+            CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n,
+                                    d.pairs, w.hdf, w.Ldf, w.refine_th2, d.pairs));
     } else if (w.refine_items) {   // per-pair form: Theta is at hand
         CK(refine_select(s, d, ctx->cfg.refine_tol, w.refine_lam + d.G, w.logdet, w.Theta, w.refine_th2, w.alive,
                          w.refine_items, w.refine_n, w.counters));
         CK(contract_fp64_listed(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, w.refine_items, w.refine_n, d.pairs,
-                                w.hdf, w.Ldf));
+                                w.hdf, w.Ldf, w.refine_th2, d.pairs));
     }
     if ((st = prof_mark(ctx, PH_REFINE)) != AFQMC_OK) return st;
     CK(walker_average(s, d, w.logdet, w.vpair, w.epair, w.logov, w.sumS, w.vbar, w.ebar));
@@ -781,6 +800,20 @@ extern "C" afqmc_status afqmc_energy(afqmc_ctx* ctx, double* e_mix, double* sum_
     if (sum_w) *sum_w = r[1];
     if (mean_sign) *mean_sign = r[1] > 0 ? r[2] / r[1] : 0.0;
     return status_result(status);
+}
+
+extern "C" afqmc_status afqmc_trial_orbitals(afqmc_ctx* ctx, const double* x, int64_t n, double* out) {
+    if (!ctx || !x || !out || n < 0) return fail(AFQMC_ERR_ARG, "bad arguments");
+    const Dims& d = ctx->d;
+    if (n > d.pairs) return fail(AFQMC_ERR_ARG, "n = %lld exceeds n_walkers * n_paths = %lld", (long long)n, d.pairs);
+    if (n == 0) return AFQMC_OK;
+    Workspace& w = ctx->ws;
+    CK(cudaMemcpyAsync(w.xprop, x, (size_t)n * d.K * 8, cudaMemcpyDefault, ctx->stream));
+    CK(trial_samples(ctx, w.xprop, n, w.Phiprop, nullptr, 1));
+    CK(cudaMemcpyAsync(out, w.Phiprop, (size_t)n * phi_stride(d) * 8, cudaMemcpyDefault, ctx->stream));
+    int status = 0;
+    afqmc_status st = read_status(ctx, &status);
+    return st != AFQMC_OK ? st : status_result(status);
 }
 
 extern "C" afqmc_status afqmc_observables(afqmc_ctx* ctx, double* logov, double* e_local, double* force_bias) {

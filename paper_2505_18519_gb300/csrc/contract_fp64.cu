@@ -71,13 +71,22 @@ __host__ __device__ __forceinline__ Fp64Layout fp64_layout(int N, int nu, int nd
 // OWN: M entries owned per thread (n_up^2 + n_dn^2 <= OWN * CT); the double-float
 // mode with OWN = 8 fits two blocks per SM (slab layout, at most 128 registers;
 // the FP64 instances keep the same 128-register budget).
+// Runs per listed pair of the split double-float refinement: up to 16, as many
+// as the partial-sum space (part_cap double2 values) holds for n pairs.
+__device__ __forceinline__ int split_count(long long n, long long part_cap) {
+    if (n <= 0) return 1;
+    const long long g = part_cap / n;
+    return (int)(g < 1 ? 1 : (g > 16 ? 16 : g));
+}
+
 template <bool SLAB, bool DF, int OWN>
 __global__ void __launch_bounds__(CT, (DF && OWN > 8) ? 1 : 2) contract_fp64_kernel(int N, int nu, int nd, int G, int JB,
                                                            const double* __restrict__ h, const double* __restrict__ L,
                                                            const double* __restrict__ Phi, const double2* __restrict__ Theta,
                                                            double2* __restrict__ vpair, double2* __restrict__ epair,
                                                            const int* __restrict__ items, const int* __restrict__ n_items,
-                                                           const dfl* __restrict__ hdf, const dfl* __restrict__ Ldf) {
+                                                           const dfl* __restrict__ hdf, const dfl* __restrict__ Ldf,
+                                                           double2* __restrict__ epart, long long part_cap) {
     extern __shared__ double smc[];
     __shared__ double2 red[CT / 32];
     const int nt = nu + nd;
@@ -101,9 +110,15 @@ __global__ void __launch_bounds__(CT, (DF && OWN > 8) ? 1 : 2) contract_fp64_ker
         if (o < nu * nu) { own_a[r] = o / nu; own_b[r] = o % nu; own_c[r] = o % nu; }
         else { int q = o - nu * nu; own_a[r] = q / nd; own_b[r] = q % nd; own_c[r] = nu + q % nd; }
     }
-    const long long n_work = items ? (long long)*n_items : (long long)gridDim.x;
+    // with epart, the matrices of each listed pair are split into gs runs, one work
+    // item each, so that a few listed pairs still fill the GPU
+    const long long n_list = items ? (long long)*n_items : (long long)gridDim.x;
+    const int gs = epart ? split_count(n_list, part_cap) : 1;
+    const long long n_work = n_list * gs;
     for (long long item = blockIdx.x; item < n_work; item += gridDim.x) {
-    const long long pair = items ? (long long)items[item] : item;
+    const long long pair = items ? (long long)items[item / gs] : item;
+    const int run = (int)(item % gs);
+    const int g_begin = -1 + (int)((long long)(G + 1) * run / gs), g_end = -1 + (int)((long long)(G + 1) * (run + 1) / gs);
     const double* gPhi = Phi + pair * (long long)N * nu;
     const double2* gTh = Theta + pair * (long long)N * nt;
     dfl* const sPhiD = reinterpret_cast<dfl*>(sPhi);
@@ -122,7 +137,7 @@ __global__ void __launch_bounds__(CT, (DF && OWN > 8) ? 1 : 2) contract_fp64_ker
         }
     double2 e_acc = cmk(0.0, 0.0);   // thread 0 accumulates E_L
     __syncthreads();
-    for (int g = -1; g < G; ++g) {
+    for (int g = g_begin; g < g_end; ++g) {
         const double* Lg = (g < 0) ? h : L + (long long)g * N * N;
         const dfl* LgD = DF ? ((g < 0) ? hdf : Ldf + (long long)g * N * N) : nullptr;
         double2 acc[OWN];
@@ -226,8 +241,23 @@ __global__ void __launch_bounds__(CT, (DF && OWN > 8) ? 1 : 2) contract_fp64_ker
             }
         }
     }
-    if (tid == 0) epair[pair] = e_acc;
+    if (tid == 0) {
+        if (epart) epart[item] = e_acc;
+        else epair[pair] = e_acc;
+    }
     __syncthreads();   // the next item overwrites shared memory
+    }
+}
+
+// E_L of the listed pairs from their runs' partial sums, in run order.
+__global__ void refine_sum_kernel(const int* __restrict__ items, const int* __restrict__ n_items,
+                                  const double2* __restrict__ epart, long long part_cap, double2* __restrict__ epair) {
+    const long long n = *n_items;
+    const int gs = split_count(n, part_cap);
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += (long long)gridDim.x * blockDim.x) {
+        double2 e = epart[it * gs];
+        for (int r = 1; r < gs; ++r) e = cadd(e, epart[it * gs + r]);
+        epair[items[it]] = e;
     }
 }
 
@@ -473,7 +503,8 @@ template <bool SLAB, bool DF, int OWN>
 static cudaError_t launch_fp64_shape(cudaStream_t s, const Dims& d, int JB, size_t smem, const double* h,
                                      const double* L, const double* Phi, const double2* Theta, double2* vpair,
                                      double2* epair, long long blocks, const int* items, const int* n_items,
-                                     const dfl* hdf, const dfl* Ldf) {
+                                     const dfl* hdf, const dfl* Ldf, double2* epart = nullptr,
+                                     long long part_cap = 0) {
     const void* k = (const void*)contract_fp64_kernel<SLAB, DF, OWN>;
     cudaError_t e = raise_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
@@ -484,18 +515,25 @@ static cudaError_t launch_fp64_shape(cudaStream_t s, const Dims& d, int JB, size
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, CT, smem);
         if (e != cudaSuccess) return e;
         const long long cap = (long long)sms * (per_sm > 0 ? per_sm : 1);
+        if (epart) blocks = blocks * 16;   // up to 16 runs per listed pair
         if (blocks > cap) blocks = cap;
     }
     contract_fp64_kernel<SLAB, DF, OWN><<<(unsigned)blocks, CT, smem, s>>>(d.N, d.nu, d.nd, d.G, JB, h, L, Phi, Theta,
-                                                                           vpair, epair, items, n_items, hdf, Ldf);
+                                                                           vpair, epair, items, n_items, hdf, Ldf,
+                                                                           epart, part_cap);
     count_launches(1);
+    if (epart) {
+        refine_sum_kernel<<<64, 256, 0, s>>>(items, n_items, epart, part_cap, epair);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 
 template <bool DF>
 static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                                const double2* Theta, double2* vpair, double2* epair, long long blocks, const int* items,
-                               const int* n_items, const dfl* hdf = nullptr, const dfl* Ldf = nullptr) {
+                               const int* n_items, const dfl* hdf = nullptr, const dfl* Ldf = nullptr,
+                               double2* epart = nullptr, long long part_cap = 0) {
     if (DF && (!hdf || !Ldf || !items)) return cudaErrorInvalidValue;
     if (!contract_fp64_supported(d.N, d.nu, d.nd)) return cudaErrorInvalidValue;
     if (blocks <= 0) return cudaSuccess;
@@ -507,9 +545,9 @@ static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, c
         const size_t smem = contract_fp64_slab_smem(d.N, d.nu, d.nd, JB);
         if (d.nu * d.nu + d.nd * d.nd <= 8 * CT)
             return launch_fp64_shape<true, true, 8>(s, d, JB, smem, h, L, Phi, Theta, vpair, epair, blocks, items,
-                                                    n_items, hdf, Ldf);
+                                                    n_items, hdf, Ldf, epart, part_cap);
         return launch_fp64_shape<true, true, MAXOWN>(s, d, JB, smem, h, L, Phi, Theta, vpair, epair, blocks, items,
-                                                     n_items, hdf, Ldf);
+                                                     n_items, hdf, Ldf, epart, part_cap);
     }
     const size_t smem = contract_fp64_smem(d.N, d.nu, d.nd, JB);
     if (smem > 220 * 1024)
@@ -527,11 +565,13 @@ cudaError_t contract_fp64(cudaStream_t s, const Dims& d, const double* h, const 
 
 cudaError_t contract_fp64_listed(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                                  const double2* Theta, double2* vpair, double2* epair, const int* items,
-                                 const int* n_items, long long max_items, const void* hdf, const void* Ldf) {
+                                 const int* n_items, long long max_items, const void* hdf, const void* Ldf,
+                                 void* part, long long part_cap) {
     if (!items || !n_items) return cudaErrorInvalidValue;
     if (hdf || Ldf)
         return launch_fp64<true>(s, d, h, L, Phi, Theta, vpair, epair, max_items, items, n_items,
-                                 static_cast<const dfl*>(hdf), static_cast<const dfl*>(Ldf));
+                                 static_cast<const dfl*>(hdf), static_cast<const dfl*>(Ldf),
+                                 static_cast<double2*>(part), part ? part_cap : 0);
     return launch_fp64<false>(s, d, h, L, Phi, Theta, vpair, epair, max_items, items, n_items);
 }
 

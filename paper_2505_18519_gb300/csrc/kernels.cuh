@@ -44,6 +44,22 @@ cudaError_t trial_orbitals_df(cudaStream_t s, int N, int nu, long long problems,
                               double* Out, const int* alive, int P, int* status, int threads = 256,
                               bool s_is_df = false);
 bool trial_orbitals_df_supported(int N, int nu);
+// The double-float kernel for the problems list[0 .. *count) (a device list), on
+// one block per SM.
+cudaError_t trial_orbitals_df_list(cudaStream_t s, int N, int nu, const double* S_all, bool s_is_df, const double* Phi0,
+                                   double* Out, const int* alive, int P, int* status, const int* list,
+                                   const int* count);
+// trial_tc.cu: the same series with the products S V on the tensor cores (8-bit
+// digit splitting, exact integer accumulation, about 40 bits per product);
+// N <= 128, n_up <= 32.  Problems whose Chebyshev vectors grow (the Lanczos
+// interval missed part of the spectrum) are listed in redo_list / *redo_count
+// (workspace of `problems` + 1 ints) and redone by the double-float kernel.
+// lim: polls of an mbarrier wait before it gives up (0: 2^26).
+bool trial_orbitals_tc_supported(int N, int nu);
+size_t trial_orbitals_tc_smem(int nu);
+cudaError_t trial_orbitals_tc(cudaStream_t s, int N, int nu, long long problems, const double* S_all, bool s_is_df,
+                              const double* Phi0, double* Out, const int* alive, int P, int* status, int* redo_list,
+                              int* redo_count, uint32_t lim);
 // S = X U in double-float (X FP64 M x K, U as double-float K x Nc from u_to_df);
 // S is written as double-float pairs, 8 bytes per element
 cudaError_t u_to_df(cudaStream_t s, long long n, const double* U, void* Ud);
@@ -77,7 +93,10 @@ cudaError_t refine_select(cudaStream_t s, const Dims& d, double tol, const doubl
 cudaError_t contract_fp64_listed(cudaStream_t s, const Dims& d, const double* h, const double* L, const double* Phi,
                                  const double2* Theta, double2* vpair, double2* epair, const int* items,
                                  const int* n_items, long long max_items, const void* hdf = nullptr,
-                                 const void* Ldf = nullptr);
+                                 const void* Ldf = nullptr, void* part = nullptr, long long part_cap = 0);
+// (part, part_cap: with the double-float copies, space for part_cap double2 partial
+// sums; each listed pair's matrices are then split into up to 16 runs, one block
+// each, and the runs' sums added in order: a few listed pairs fill the GPU.)
 // Walker-side FP64 form (Y_g = X_g phi_w once per block of a walker's pairs,
 // Z = Phi_p^T Y_g, Q = Z A_p^-1; Tr Q and Tr Q^2 are those of M_g): needs A^-1
 // per pair and spin (overlap_lu with OVL_INVERSE) and the walkers.
@@ -128,10 +147,12 @@ cudaError_t trial_orbitals_c(cudaStream_t s, int N, int nu, long long problems, 
 cudaError_t slice_propagate(cudaStream_t s, int N, int nu, long long problems, const double* Pm, const double2* V,
                             double2* Out, const int* alive, int P);
 cudaError_t walkers_from_trial_c(cudaStream_t s, const Dims& d, const double2* Phi_w, double2* phi);
-// The per-pair FP64 contraction with complex Phi (R_g = Phi^dagger X_g).
+// The per-pair FP64 contraction with complex Phi (R_g = Phi^dagger X_g); with
+// list, n_list (device) only the pairs list[0 .. *n_list).
 bool contract_fp64c_supported(int N, int nu, int nd);
 cudaError_t contract_fp64c(cudaStream_t s, const Dims& d, const double* h, const double* L, const double2* Phi,
-                           const double2* Theta, double2* vpair, double2* epair);
+                           const double2* Theta, double2* vpair, double2* epair, const int* list = nullptr,
+                           const int* n_list = nullptr);
 
 // walker.cu
 struct StepParams {

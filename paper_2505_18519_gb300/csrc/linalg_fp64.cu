@@ -265,15 +265,21 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
     }
     double2* Th = Theta + pair * (long long)N * nt + col0;
     if (trial_side) {
-        // B = Phi A^-T (trial side): B[i][b] = sum_a Phi[i][a] (A^-1)[b][a]
+        // B = Phi A^-T (trial side): B[i][b] = sum_a Phi[i][a] (A^-1)[b][a]; for complex
+        // trial orbitals B = conj(Phi) A^-T, so that B^T X phi = A^-1 Phi^dagger X phi
         for (int e = lane; e < N * n; e += 32) {
             int i = e / n, b = e - i * n;
             double2 s = cmk(0.0, 0.0);
-            const double* row = Ph + (long long)i * nu;
-            for (int a = 0; a < n; ++a) {
-                const double2 t = Ainv[b * n + a];
-                s.x = fma(row[a], t.x, s.x);
-                s.y = fma(row[a], t.y, s.y);
+            if (cphi) {
+                const double2* rowc = reinterpret_cast<const double2*>(Ph) + (long long)i * nu;
+                for (int a = 0; a < n; ++a) cfma(s, cmk(rowc[a].x, -rowc[a].y), Ainv[b * n + a]);
+            } else {
+                const double* row = Ph + (long long)i * nu;
+                for (int a = 0; a < n; ++a) {
+                    const double2 t = Ainv[b * n + a];
+                    s.x = fma(row[a], t.x, s.x);
+                    s.y = fma(row[a], t.y, s.y);
+                }
             }
             Th[(long long)i * nt + b] = s;
         }
@@ -500,15 +506,20 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
         return;
     }
     double2* Th = Theta + pair * (long long)N * nt + col0;
-    if (trial_side) {
+    if (trial_side) {   // B = Phi A^-T, or conj(Phi) A^-T for complex trial orbitals
         for (int e = hl; e < N * n; e += 16) {
             const int i = e / n, b = e - i * n;
             double2 s = cmk(0.0, 0.0);
-            const double* row = Ph + (long long)i * nu;
-            for (int a = 0; a < n; ++a) {
-                const double2 t = Ainv[b * n + a];
-                s.x = fma(row[a], t.x, s.x);
-                s.y = fma(row[a], t.y, s.y);
+            if (cphi) {
+                const double2* rowc = reinterpret_cast<const double2*>(Ph) + (long long)i * nu;
+                for (int a = 0; a < n; ++a) cfma(s, cmk(rowc[a].x, -rowc[a].y), Ainv[b * n + a]);
+            } else {
+                const double* row = Ph + (long long)i * nu;
+                for (int a = 0; a < n; ++a) {
+                    const double2 t = Ainv[b * n + a];
+                    s.x = fma(row[a], t.x, s.x);
+                    s.y = fma(row[a], t.y, s.y);
+                }
             }
             Th[(long long)i * nt + b] = s;
         }

@@ -283,7 +283,8 @@ __global__ void __launch_bounds__(CC_T) contract_fp64c_kernel(int N, int nu, int
                                                               const double* __restrict__ L,
                                                               const double2* __restrict__ Phi,
                                                               const double2* __restrict__ Theta,
-                                                              double2* __restrict__ vpair, double2* __restrict__ epair) {
+                                                              double2* __restrict__ vpair, double2* __restrict__ epair,
+                                                              const int* __restrict__ list, const int* __restrict__ n_list) {
     extern __shared__ double2 scc[];
     __shared__ double2 red[CC_T / 32];
     const int nt = nu + nd, tid = threadIdx.x;
@@ -293,7 +294,11 @@ __global__ void __launch_bounds__(CC_T) contract_fp64c_kernel(int N, int nu, int
     double2* sR = sTh + (size_t)N * nt;                // nu x CC_JB
     double2* sM = sR + (size_t)nu * CC_JB;             // nM
     double* sL = reinterpret_cast<double*>(sM + nM);   // N x CC_JB
-    const long long pair = blockIdx.x;
+    long long pair = blockIdx.x;
+    if (list) {   // only the listed pairs (uniform per block)
+        if (pair >= *n_list) return;
+        pair = list[pair];
+    }
     const double2* gPhi = Phi + pair * (long long)N * nu;
     const double2* gTh = Theta + pair * (long long)N * nt;
     for (int e = tid; e < N * nu; e += CC_T) sPhi[e] = gPhi[e];
@@ -391,13 +396,14 @@ bool contract_fp64c_supported(int N, int nu, int nd) {
 }
 
 cudaError_t contract_fp64c(cudaStream_t s, const Dims& d, const double* h, const double* L, const double2* Phi,
-                           const double2* Theta, double2* vpair, double2* epair) {
+                           const double2* Theta, double2* vpair, double2* epair, const int* list, const int* n_list) {
     if (!contract_fp64c_supported(d.N, d.nu, d.nd)) return cudaErrorInvalidValue;
     if (d.pairs <= 0) return cudaSuccess;
     const size_t smem = contract_fp64c_smem(d.N, d.nu, d.nd);
     cudaError_t e = raise_smem_limit((const void*)contract_fp64c_kernel, smem);
     if (e != cudaSuccess) return e;
-    contract_fp64c_kernel<<<(unsigned)d.pairs, CC_T, smem, s>>>(d.N, d.nu, d.nd, d.G, h, L, Phi, Theta, vpair, epair);
+    contract_fp64c_kernel<<<(unsigned)d.pairs, CC_T, smem, s>>>(d.N, d.nu, d.nd, d.G, h, L, Phi, Theta, vpair, epair,
+                                                                 list, n_list);
     count_launches(1);
     return cudaGetLastError();
 }

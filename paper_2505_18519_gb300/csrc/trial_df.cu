@@ -18,63 +18,15 @@
 // and the number of terms; the Gershgorin half-width of the sampled S is
 // 3 to 4 times the spectral one.  So the interval comes from a short Lanczos
 // run, checked a posteriori (see chebyshev_expm_df_kernel).
+#include <algorithm>
+
+#include "cheb.cuh"
 #include "df.cuh"
 #include "kernels.cuh"
 
 namespace afq {
 
-constexpr int CHEB_DF_MAX = 320;
 constexpr double RHO_DF = 6.5;   // largest Gershgorin half-width run in double-float
-constexpr int LZ_STEPS = 12;     // Lanczos steps of the spectral estimate
-constexpr int LZ_NMAX = 256;
-
-// Sum over the block (256 threads); every thread gets the result.
-__device__ __forceinline__ float block_sum_f(float v, float* red8) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    __syncthreads();   // red8 may still be read from the previous call
-    if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float t = 0.f;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) t += red8[w];
-    return t;
-}
-
-// Chebyshev coefficients of exp on [c - rho, c + rho] (Miller's backward
-// recurrence for I_k(rho), normalised by sum = e^rho), scaled by e^(c + rho);
-// returns the number of terms m.  One thread.
-__device__ int cheb_coefs(double c, double rho, double tol, double* coef, int* status) {
-    int start = (int)ceil(rho) + 48;
-    if (!isfinite(rho) || start > CHEB_DF_MAX) {
-        atomicOr(status, STATUS_NONFINITE);
-        start = CHEB_DF_MAX;
-    }
-    const double r2 = 2.0 / rho;
-    double ip1 = 0.0, ik = 1e-280;
-    for (int k = start; k >= 1; --k) {
-        coef[k] = ik;
-        const double im1 = fma((double)k * r2, ik, ip1);
-        ip1 = ik;
-        ik = im1;
-        if (ik > 1e250) {   // rescale everything computed so far
-            for (int j = k; j <= start; ++j) coef[j] *= 1e-250;
-            ip1 *= 1e-250;
-            ik *= 1e-250;
-        }
-    }
-    coef[0] = ik;
-    double norm = coef[0];
-    for (int k = 1; k <= start; ++k) norm += 2.0 * coef[k];   // = e^rho in Miller's units
-    int m = start;
-    for (int k = 1; k <= start; ++k) {
-        if (coef[k] < tol * norm) { m = k; break; }
-    }
-    const double scale = exp(c + rho) / norm;
-    coef[0] *= scale;
-    for (int k = 1; k <= m; ++k) coef[k] *= 2.0 * scale;
-    return m;
-}
 
 // Interval of the expansion: first an estimate from LZ_STEPS Lanczos steps on S
 // (FP32; the Gershgorin disks of the Lanczos tridiagonal, which includes the
@@ -85,20 +37,19 @@ __device__ int cheb_coefs(double c, double rho, double tol, double* coef, int* s
 // ||V_k||_F <= ||Phi0||_F); if they do, the problem is done again on the
 // Gershgorin interval of S, in double-float if its half-width is at most
 // RHO_DF and in FP64 otherwise.
-__global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, long long problems,
-                                                                const double* __restrict__ S_all,
-                                                                const double* __restrict__ Phi0, double* __restrict__ Out,
-                                                                const int* __restrict__ alive, int P, int* status,
-                                                                int allow_df, int s_is_df) {
+// One problem per call; the whole block of 256 threads takes part.
+__device__ __forceinline__ void cheb_df_problem(long long prob, int N, int nu, const double* __restrict__ S_all,
+                                                const double* __restrict__ Phi0, double* __restrict__ Out,
+                                                const int* __restrict__ alive, int P, int* status, int allow_df,
+                                                int s_is_df) {
     extern __shared__ dfl smf[];
     __shared__ double coef[CHEB_DF_MAX + 2];
     __shared__ dfl coefd[CHEB_DF_MAX + 2];
-    __shared__ float red_lo[256], red_hi[256], red8[8];
-    __shared__ float lz_v[3][LZ_NMAX], lz_a[LZ_STEPS], lz_b[LZ_STEPS];
+    __shared__ ChebScratch sc;
+    float* red8 = sc.red8;
     __shared__ int nterms, mode;
     __shared__ dfl cshift_d, irho_d;
-    __shared__ double cshift, irho, gers_c, gers_rho, est_c, est_rho;
-    const long long prob = blockIdx.x;
+    __shared__ double cshift, irho;
     if (alive && !alive[prob / P]) return;
     const double* Sg = S_all + prob * (long long)N * N;
     dfl* S = smf;
@@ -108,89 +59,11 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
     const int tid = threadIdx.x, nth = blockDim.x;
     const int nn = N * nu;
     // S to double-float (or as given, when the caller formed it in double-float);
-    // Gershgorin interval of S in FP32 (widened so it stays a bound)
+    // the Gershgorin interval and the Lanczos estimate from its high parts
     const dfl* Sgd = reinterpret_cast<const dfl*>(Sg);
     for (int e = tid; e < N * N; e += nth) S[e] = s_is_df ? Sgd[e] : df_from(Sg[e]);
     __syncthreads();
-    float lo = INFINITY, hi = -INFINITY;
-    for (int i = tid; i < N; i += nth) {
-        float r = 0.f;
-        const float dgi = S[(size_t)i * N + i].hi;
-        for (int j = 0; j < N; ++j)
-            if (j != i) r += fabsf(S[(size_t)i * N + j].hi);
-        const float slack = 1e-5f * (r + fabsf(dgi)) + 1e-30f;
-        lo = fminf(lo, dgi - r - slack);
-        hi = fmaxf(hi, dgi + r + slack);
-    }
-    red_lo[tid] = lo;
-    red_hi[tid] = hi;
-    __syncthreads();
-    for (int off = nth / 2; off > 0; off >>= 1) {
-        if (tid < off) {
-            red_lo[tid] = fminf(red_lo[tid], red_lo[tid + off]);
-            red_hi[tid] = fmaxf(red_hi[tid], red_hi[tid + off]);
-        }
-        __syncthreads();
-    }
-    const float g_lo = red_lo[0], g_hi = red_hi[0];
-    // Lanczos on S from a fixed start vector
-    for (int i = tid; i < N; i += nth) {
-        lz_v[0][i] = 0.f;
-        lz_v[1][i] = 1.f + 0.5f * __sinf(1.3f * (float)i + 0.7f);
-    }
-    float nrm = 0.f;
-    for (int i = tid; i < N; i += nth) nrm += lz_v[1][i] * lz_v[1][i];
-    nrm = block_sum_f(nrm, red8);
-    for (int i = tid; i < N; i += nth) lz_v[1][i] *= rsqrtf(nrm);
-    int ksteps = 0;
-    float beta_prev = 0.f;
-    for (int j = 0; j < LZ_STEPS && j < N; ++j) {
-        __syncthreads();
-        float part = 0.f;
-        for (int i = tid; i < N; i += nth) {
-            float wsum = 0.f;
-            for (int q = 0; q < N; ++q) wsum = fmaf(S[(size_t)i * N + q].hi, lz_v[1][q], wsum);
-            lz_v[2][i] = wsum;
-            part = fmaf(wsum, lz_v[1][i], part);
-        }
-        const float alpha = block_sum_f(part, red8);
-        float part2 = 0.f;
-        for (int i = tid; i < N; i += nth) {
-            const float wv = lz_v[2][i] - alpha * lz_v[1][i] - beta_prev * lz_v[0][i];
-            lz_v[2][i] = wv;
-            part2 = fmaf(wv, wv, part2);
-        }
-        const float beta = sqrtf(block_sum_f(part2, red8));
-        if (tid == 0) { lz_a[j] = alpha; lz_b[j] = beta; }
-        ksteps = j + 1;
-        if (!(beta > 1e-6f * (fabsf(alpha) + 1e-30f))) break;   // invariant subspace found
-        const float ib = 1.f / beta;
-        for (int i = tid; i < N; i += nth) {
-            lz_v[0][i] = lz_v[1][i];
-            lz_v[1][i] = lz_v[2][i] * ib;
-        }
-        beta_prev = beta;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        float tl = INFINITY, th = -INFINITY;
-        for (int j = 0; j < ksteps; ++j) {
-            const float r = (j > 0 ? fabsf(lz_b[j - 1]) : 0.f) + fabsf(lz_b[j]);
-            tl = fminf(tl, lz_a[j] - r);
-            th = fmaxf(th, lz_a[j] + r);
-        }
-        const float margin = 0.02f * (th - tl) + 1e-6f;
-        const double elo = fmax((double)g_lo, (double)(tl - margin)), ehi = fmin((double)g_hi, (double)(th + margin));
-        gers_c = 0.5 * ((double)g_lo + (double)g_hi);
-        gers_rho = fmax(0.5 * ((double)g_hi - (double)g_lo), 1e-3);
-        if (ehi > elo && isfinite(elo) && isfinite(ehi)) {
-            est_c = 0.5 * (elo + ehi);
-            est_rho = fmax(0.5 * (ehi - elo), 1e-3);
-        } else {
-            est_c = gers_c;
-            est_rho = gers_rho;
-        }
-    }
+    cheb_interval(N, &S[0].hi, 2, sc);
     float phi_ss = 0.f;   // ||Phi0||_F^2
     for (int e = tid; e < nn; e += nth) phi_ss = fmaf((float)Phi0[e], (float)Phi0[e], phi_ss);
     phi_ss = block_sum_f(phi_ss, red8);
@@ -198,7 +71,7 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
 
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (tid == 0) {
-            const double c = attempt == 0 ? est_c : gers_c, rho = attempt == 0 ? est_rho : gers_rho;
+            const double c = attempt == 0 ? sc.est_c : sc.gers_c, rho = attempt == 0 ? sc.est_rho : sc.gers_rho;
             // 0 double-float with the growth check, 1 double-float, 2 FP64 with the
             // growth check, 3 FP64
             if (allow_df) mode = attempt == 0 ? 0 : (rho <= RHO_DF ? 1 : 3);
@@ -369,6 +242,27 @@ __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, l
     }
 }
 
+__global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, const double* __restrict__ S_all,
+                                                                const double* __restrict__ Phi0, double* __restrict__ Out,
+                                                                const int* __restrict__ alive, int P, int* status,
+                                                                int allow_df, int s_is_df) {
+    cheb_df_problem(blockIdx.x, N, nu, S_all, Phi0, Out, alive, P, status, allow_df, s_is_df);
+}
+
+// The problems list[0 .. *count), grid-stride (the tensor-core kernel's redo list).
+__global__ void __launch_bounds__(256) chebyshev_expm_df_list_kernel(int N, int nu, const double* __restrict__ S_all,
+                                                                     const double* __restrict__ Phi0,
+                                                                     double* __restrict__ Out,
+                                                                     const int* __restrict__ alive, int P, int* status,
+                                                                     int s_is_df, const int* __restrict__ list,
+                                                                     const int* __restrict__ count) {
+    const int n = *count;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        cheb_df_problem(list[i], N, nu, S_all, Phi0, Out, alive, P, status, 1, s_is_df);
+        __syncthreads();   // the shared memory is reused by the next problem
+    }
+}
+
 // Same contract as trial_orbitals (S_all is only read).
 bool trial_orbitals_df_supported(int N, int nu) {
     return (3 * (size_t)N * nu + (size_t)N * N) * sizeof(dfl) <= 200 * 1024 && N <= LZ_NMAX;
@@ -385,7 +279,7 @@ static cudaError_t trial_orbitals_lanczos(cudaStream_t s, int N, int nu, long lo
     }
     cudaError_t e = raise_smem_limit((const void*)chebyshev_expm_df_kernel, bytes);
     if (e != cudaSuccess) return e;
-    chebyshev_expm_df_kernel<<<(unsigned)problems, 256, bytes, s>>>(N, nu, problems, S_all, Phi0, Out, alive, P, status,
+    chebyshev_expm_df_kernel<<<(unsigned)problems, 256, bytes, s>>>(N, nu, S_all, Phi0, Out, alive, P, status,
                                                                    allow_df ? 1 : 0, s_is_df ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
@@ -394,6 +288,22 @@ static cudaError_t trial_orbitals_lanczos(cudaStream_t s, int N, int nu, long lo
 cudaError_t trial_orbitals_df(cudaStream_t s, int N, int nu, long long problems, double* S_all, const double* Phi0,
                               double* Out, const int* alive, int P, int* status, int threads, bool s_is_df) {
     return trial_orbitals_lanczos(s, N, nu, problems, S_all, Phi0, Out, alive, P, status, threads, true, s_is_df);
+}
+
+cudaError_t trial_orbitals_df_list(cudaStream_t s, int N, int nu, const double* S_all, bool s_is_df, const double* Phi0,
+                                   double* Out, const int* alive, int P, int* status, const int* list,
+                                   const int* count) {
+    if (!trial_orbitals_df_supported(N, nu)) return cudaErrorInvalidValue;
+    const size_t bytes = (3 * (size_t)N * nu + (size_t)N * N) * sizeof(dfl);
+    cudaError_t e = raise_smem_limit((const void*)chebyshev_expm_df_list_kernel, bytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    chebyshev_expm_df_list_kernel<<<(unsigned)std::max(1, sms), 256, bytes, s>>>(N, nu, S_all, Phi0, Out, alive, P,
+                                                                                 status, s_is_df ? 1 : 0, list, count);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t trial_orbitals(cudaStream_t s, int N, int nu, long long problems, const double* S_all, const double* Phi0,

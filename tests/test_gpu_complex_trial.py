@@ -127,3 +127,61 @@ def test_complex_trial_checkpoint_resume_is_bitwise():
     assert a.save_state() == b.save_state()
     a.close()
     b.close()
+
+
+# Mixed precision: the walker-side tensor-core contraction with the complex
+# trial-side factor B_p = conj(Phi_p) A_p^-T; its stated targets are 1e-4 Ha per
+# walker and on the mixed energy.  Overlaps, trial orbitals and every step after
+# the contraction stay FP64 or double-float.
+MIXED_TOL = 1e-4
+
+
+def _setup_mixed(name, seed, precision, **kw):
+    spec, W, P, dtau, alpha, slices = CASES[name]
+    s = ai.make_system(spec)
+    Pm = sla.expm(-0.2 * s.h) if slices > 1 else None
+    cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, dtau, seed, trial_alpha=alpha,
+                          trial_slices=slices, precision=precision, **kw)
+    assert lib.contract_kernel(cfg) == "contract_tcw_kernel"
+    return lib.Context(cfg, s.h, s.L, s.Phi0, s.U, slice_prop=Pm)
+
+
+@pytest.mark.parametrize("precision", ["fp16x6", "fp16x3"])
+@pytest.mark.parametrize("name", ["complex_c0", "complex_ragged", "complex_two_slices",
+                                  "complex_three_slices_one_spin"])
+def test_mixed_precision_measure_and_step_match_oracle(name, precision):
+    """The measurement of the oracle's state after one step: log-overlaps to
+    1e-9 (FP64), per-pair and per-walker local energies, force bias and the
+    mixed energy to 1e-4; then one step: the same Metropolis decisions and
+    weights within 1e-4 relative (the mixed force bias enters the propagation);
+    with a vanishing refinement tolerance every pair is recomputed in FP64 and
+    the measurement matches the oracle to 1e-9."""
+    ham, ocfg, _ = _setup(name, 77, n_burn=2, n_sweeps=2)
+    ost = oa.init(ham, ocfg)
+    ost, _ = oa.step(ham, ocfg, ost)
+    m = oa.measure(ham, ost)
+    live = ost.weight > 0
+    assert np.any(live)
+    ctx = _setup_mixed(name, 77, precision, n_burn=2, n_sweeps=2)
+    ctx.load_state_arrays(_as_dict(ost))
+    e = ctx.energy(walkers=True)
+    obs = ctx.observables()
+    assert np.max(np.abs(obs["logov"].real - m["logov"].real)) < TOL
+    assert np.max(np.abs(obs["e_local"] - m["e_pair"])[live]) < MIXED_TOL
+    assert np.max(np.abs(e["e_walker"] - m["e_bar"])[live]) < MIXED_TOL
+    assert np.max(np.abs(obs["force_bias"] - m["v_bar"])[live]) < MIXED_TOL
+    num, den = oa.mixed_energy(ost.weight, m["e_bar"])
+    assert abs(e["e_mix"] - num / den) < MIXED_TOL
+    ctx.step(1)
+    ost2, _ = oa.step(ham, ocfg, ost)
+    g = ctx.state_arrays()
+    assert np.max(np.abs(g["x"] - ost2.x)) < TOL                 # the same Metropolis decisions
+    assert np.allclose(g["weight"], ost2.weight, rtol=MIXED_TOL, atol=0)
+    ctx.close()
+    exact = _setup_mixed(name, 77, precision, n_burn=2, n_sweeps=2, refine_tol=1e-300)
+    exact.load_state_arrays(_as_dict(ost))
+    e = exact.energy(walkers=True)
+    obs = exact.observables()
+    assert np.max(np.abs(obs["e_local"] - m["e_pair"])[live]) < TOL
+    assert np.max(np.abs(e["e_walker"] - m["e_bar"])[live]) < TOL
+    exact.close()

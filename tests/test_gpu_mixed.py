@@ -256,21 +256,77 @@ def test_refinement_selects_the_pairs_of_its_rule():
     assert abs(n_gpu - n_host) <= max(2, 0.02 * n_host)
 
 
-@pytest.mark.parametrize("name", ["c0", "ragged", "n70_two_k_blocks", "medium"])
-def test_double_float_trial_orbitals_against_exact_exponential(name):
+TRIAL_SYSTEMS = dict(SYSTEMS)
+# the largest workload's orbital count with 24 + 24 electrons: two K blocks and 32 MMA columns
+# in the tensor-core trial kernel; and its largest size, N = 128 with 32 electrons per spin
+TRIAL_SYSTEMS["n120_24"] = (ai.SystemSpec(120, 24, 24, 60, 40, True, 1002), 3, 4, 0.005)
+TRIAL_SYSTEMS["n128_32"] = (ai.SystemSpec(128, 32, 32, 40, 16, True, 86), 2, 3, 0.005)
+# Relative agreement with the exact exponential: double-float (about 44 bits per
+# product; 1.9e-11 measured at N = 128 with 32 electrons, where the dot products are
+# longest and the series cancels most) and the 8-bit digit products on the tensor
+# cores (about 40 bits).
+TRIAL_TOL = {"df": 5e-11, "auto": 1e-10}
+
+
+@pytest.mark.parametrize("trial_form", ["df", "auto"])
+@pytest.mark.parametrize("name", ["c0", "ragged", "n70_two_k_blocks", "medium", "n120_24", "n128_32"])
+def test_trial_orbitals_against_exact_exponential(name, trial_form):
     """The mixed path forms Phi(x) = exp(sum_k x_k U_k) Phi0 in double-float
-    arithmetic: after burn-in every stored path orbital must equal the exact
-    exponential (the oracle's, by eigendecomposition) of its own x to 1e-11
-    relative, and the paths' x must match the FP64 path's (same Metropolis
-    decisions)."""
-    spec, W, P, dtau = SYSTEMS[name]
-    s, ctx = _ctx(spec, W, P, dtau, 91, "fp16x3", n_burn=4)
+    arithmetic (trial_form df) or with the Chebyshev products on the tensor
+    cores (auto): after burn-in every stored path orbital must equal the exact
+    exponential (the oracle's, by eigendecomposition) of its own x to the
+    form's relative tolerance, and the paths' x must match the FP64 path's
+    (same Metropolis decisions)."""
+    spec, W, P, dtau = TRIAL_SYSTEMS[name]
+    s, ctx = _ctx(spec, W, P, dtau, 91, "fp16x3", n_burn=4, trial_form=trial_form)
     st = ctx.state_arrays()
     ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, dtau)
     exact = oa.trial_orbitals(ham, st["x"])
     scale = np.max(np.abs(exact), axis=(-2, -1), keepdims=True)
-    assert np.max(np.abs(st["Phi"] - exact) / scale) < 1e-11
+    err = np.max(np.abs(st["Phi"] - exact) / scale)
+    print(f"{name} {trial_form}: max relative error of Phi(x) {err:.2e}")
+    assert err < TRIAL_TOL[trial_form]
     s64, ctx64 = _ctx(spec, W, P, dtau, 91, "fp64", n_burn=4)
     assert np.array_equal(ctx64.state_arrays()["x"], st["x"])
     ctx.close()
     ctx64.close()
+
+
+def test_tensor_core_trial_orbitals_redo_a_missed_interval():
+    """A sampled S whose Lanczos interval misses part of the spectrum makes the
+    Chebyshev vectors grow; the tensor-core kernel lists such problems and the
+    double-float kernel redoes them on the Gershgorin interval.  Large hidden
+    variables (x scaled by 6) widen the spectrum enough that some estimates
+    fall short: every orbital must still match the exact exponential."""
+    spec, W, P, dtau = TRIAL_SYSTEMS["n70_two_k_blocks"]
+    s, ctx = _ctx(spec, W, P, dtau, 93, "fp16x3", n_burn=0)
+    x = 6.0 * ctx.state_arrays()["x"].reshape(-1, spec.K)
+    n0 = lib.launch_count()
+    got = ctx.trial_orbitals(x)
+    ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, dtau)
+    exact = oa.trial_orbitals(ham, x)
+    scale = np.max(np.abs(exact), axis=(-2, -1), keepdims=True)
+    err = np.max(np.abs(got - exact) / scale)
+    print(f"x scaled by 6: max relative error {err:.2e}, {lib.launch_count() - n0} launches")
+    assert err < 1e-9
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["c0", "n70_two_k_blocks", "n120_24"])
+def test_trial_orbitals_entry_matches_both_forms(name):
+    """afqmc_trial_orbitals on arbitrary rows of x: the tensor-core and the
+    double-float forms agree with each other and with the exact exponential."""
+    spec, W, P, dtau = TRIAL_SYSTEMS[name]
+    s, ctc = _ctx(spec, W, P, dtau, 94, "fp16x3", n_burn=0)
+    s, cdf = _ctx(spec, W, P, dtau, 94, "fp16x3", n_burn=0, trial_form="df")
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((W * P, spec.K))
+    a, b = ctc.trial_orbitals(x), cdf.trial_orbitals(x)
+    ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, dtau)
+    exact = oa.trial_orbitals(ham, x)
+    scale = np.max(np.abs(exact), axis=(-2, -1), keepdims=True)
+    ea, eb = np.max(np.abs(a - exact) / scale), np.max(np.abs(b - exact) / scale)
+    print(f"{name}: tensor cores {ea:.2e}, double-float {eb:.2e}")
+    assert ea < TRIAL_TOL["auto"] and eb < TRIAL_TOL["df"]
+    ctc.close()
+    cdf.close()

@@ -153,7 +153,22 @@ def test_trial_fields_reach_the_library(L):
     assert lib.contract_kernel(c) == "contract_fp64c_kernel"
     real = lib.make_config(8, 4, 4, 32, 8, 8, 4, 0.01, 1)
     assert lib.workspace_bytes(c) > lib.workspace_bytes(real)        # complex Phi, slice buffers
-    for kw in (dict(precision="fp16x3"), dict(proposal="mlp"), dict(rcache=True), dict(trial_slices=9),
-               dict(trial_alpha=0.0)):
+    for kw in (dict(precision="fp16x3", tc_form="per_pair"), dict(proposal="mlp"), dict(rcache=True),
+               dict(trial_slices=9), dict(trial_alpha=0.0)):
         bad = lib.make_config(8, 4, 4, 32, 8, 8, 4, 0.01, 1, **{"trial_alpha": -0.5j, **kw})
         assert lib.workspace_bytes(bad) == 0, kw
+    # mixed precision: the walker-side tensor-core form, whatever the requested form
+    for prec in ("fp16x3", "fp16x6", "bf16x3"):
+        m = lib.make_config(8, 4, 4, 32, 8, 8, 4, 0.01, 1, trial_alpha=-0.5j, trial_slices=2, precision=prec)
+        assert lib.contract_kernel(m) == "contract_tcw_kernel"
+        assert lib.workspace_bytes(m) > 0
+
+
+def test_trial_form_field_reaches_the_library(L):
+    """trial_form selects how the mixed path forms exp(S) Phi0; an unknown value is refused."""
+    for form in ("auto", "df"):
+        c = lib.make_config(50, 10, 10, 250, 50, 4, 8, 0.005, 1, precision="fp16x6", trial_form=form)
+        assert lib.workspace_bytes(c) > 0
+    c = lib.make_config(50, 10, 10, 250, 50, 4, 8, 0.005, 1, precision="fp16x6")
+    c.trial_form = 7
+    assert lib.workspace_bytes(c) == 0
