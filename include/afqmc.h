@@ -284,7 +284,10 @@ afqmc_status afqmc_history(afqmc_ctx* ctx, double* out, int n, int* n_out);
  *   8 pairs recomputed by the refinement (see refine_tol) since init,
  *   9 population-control combs applied since init (see pop_period),
  *   10 walkers those combs replaced by copies of others,
- *   11 pairs whose cached half-rotated matrices were formed since init (see rcache) */
+ *   11 pairs whose cached half-rotated matrices were formed since init (see rcache),
+ *   12 Chebyshev terms summed by the tensor-core trial-orbital kernel since init (see
+ *      trial_form), 13 trial samples it handed to the double-float kernel because
+ *      the Lanczos interval missed part of the spectrum */
 afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len);
 
 /* Checkpoint.  The state buffer (host memory) is, in order, with no padding:

@@ -272,10 +272,10 @@ class Context:
         return out[: 4 * k.value].reshape(k.value, 4)
 
     def stats(self):
-        out = np.empty(12)
-        _check(load_library().afqmc_stats(self._ctx, out.ctypes.data, 12))
+        out = np.empty(14)
+        _check(load_library().afqmc_stats(self._ctx, out.ctypes.data, 14))
         keys = ("steps", "accepted", "proposed", "live_walkers", "status", "min_weight", "max_weight", "sum_weight",
-                "refined_pairs", "combs", "comb_replaced", "rcache_formed")
+                "refined_pairs", "combs", "comb_replaced", "rcache_formed", "cheb_terms", "cheb_redone")
         return dict(zip(keys, out.tolist()))
 
     def autotune(self):

@@ -466,7 +466,7 @@ static cudaError_t trial_orbitals_of(afqmc_ctx* ctx, long long problems, double*
         return trial_orbitals(ctx->stream, d.N, d.nu, problems, w.Sprop, w.Phi0, Out, alive, P, w.status, d.cheb_threads);
     if (trial_on_tc(ctx))
         return trial_orbitals_tc(ctx->stream, d.N, d.nu, problems, w.Sprop, s_in_df(ctx), w.Phi0, Out, alive, P, w.status,
-                                 w.cheb_redo, w.cheb_redo + d.pairs, d.wait_polls);
+                                 w.cheb_redo, w.cheb_redo + d.pairs, w.counters, d.wait_polls);
     return trial_orbitals_df(ctx->stream, d.N, d.nu, problems, w.Sprop, w.Phi0, Out, alive, P, w.status, d.cheb_threads,
                              s_in_df(ctx));
 }
@@ -876,9 +876,9 @@ extern "C" afqmc_status afqmc_stats(afqmc_ctx* ctx, double* out, int len) {
     CK(cudaMemcpyAsync(ws4, ctx->ws.reduce + 4, sizeof ws4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(&status, ctx->ws.status, sizeof status, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    double v[12] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3],
-                    (double)c[5], (double)c[6], (double)c[7], (double)c[8]};
-    for (int i = 0; i < len && i < 12; ++i) out[i] = v[i];
+    double v[14] = {(double)c[0], (double)c[1], (double)c[2], ws4[0], (double)status, ws4[1], ws4[2], ws4[3],
+                    (double)c[5], (double)c[6], (double)c[7], (double)c[8], (double)c[9], (double)c[10]};
+    for (int i = 0; i < len && i < 14; ++i) out[i] = v[i];
     return (status & STATUS_TIMEOUT) ? status_result(status) : AFQMC_OK;
 }
 

@@ -695,13 +695,15 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
                         for (int qq = 0; qq < 32; ++qq) v[qq] += w[qq];
                     }
                     if (row_ok) {
+                        // columns (b, re), (b, im) are adjacent and j0, c0 even: one 8-byte
+                        // store per entry (ld odd, so a warp's rows fall in distinct bank pairs)
 #pragma unroll
-                        for (int qq = 0; qq < 32; ++qq) {
+                        for (int qq = 0; qq < 32; qq += 2) {
                             const int col = j0 + qq;
                             if (col >= c0 && col < c1) {
                                 const int bb = (col - gl * 2 * n) >> 1;
-                                float* dst = reinterpret_cast<float*>(&Ms[(size_t)r * ld + bb]);
-                                dst[col & 1] = v[qq] * rowf * sc[bb];
+                                const float f = rowf * sc[bb];
+                                Ms[(size_t)r * ld + bb] = make_float2(v[qq] * f, v[qq + 1] * f);
                             }
                         }
                     }

@@ -57,9 +57,10 @@ cudaError_t trial_orbitals_df_list(cudaStream_t s, int N, int nu, const double* 
 // lim: polls of an mbarrier wait before it gives up (0: 2^26).
 bool trial_orbitals_tc_supported(int N, int nu);
 size_t trial_orbitals_tc_smem(int nu);
+// counters[9] += the terms of every finished problem, counters[10] += the problems redone.
 cudaError_t trial_orbitals_tc(cudaStream_t s, int N, int nu, long long problems, const double* S_all, bool s_is_df,
                               const double* Phi0, double* Out, const int* alive, int P, int* status, int* redo_list,
-                              int* redo_count, uint32_t lim);
+                              int* redo_count, unsigned long long* counters, uint32_t lim);
 // S = X U in double-float (X FP64 M x K, U as double-float K x Nc from u_to_df);
 // S is written as double-float pairs, 8 bytes per element
 cudaError_t u_to_df(cudaStream_t s, long long n, const double* U, void* Ud);

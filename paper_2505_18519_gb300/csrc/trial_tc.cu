@@ -140,7 +140,8 @@ template <int KB, int NB>
 __global__ void __launch_bounds__(TT_THREADS, 1)
     chebyshev_expm_tc_kernel(int N, int nu, long long problems, const double* __restrict__ S_all, int s_is_df,
                              const double* __restrict__ Phi0, double* __restrict__ Out, const int* __restrict__ alive,
-                             int P, int* status, int* redo_list, int* redo_count, uint32_t lim) {
+                             int P, int* status, int* redo_list, int* redo_count, unsigned long long* counters,
+                             uint32_t lim) {
     constexpr int NW = TT_THREADS / 32;    // warps; NW / 4 share each tensor-memory lane quadrant
     constexpr int CPT = NB / (NW / 4);     // columns of V per thread
     constexpr int CH = CPT < 8 ? CPT : 8;  // columns per tensor-memory load
@@ -370,13 +371,17 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         tc::mbar_wait(&mma_bar, (uint32_t)((k - 1) & 1), 1u << 22);   // the issued MMAs complete
     }
     if (grew || failed) {
-        if (tid == 0) redo_list[atomicAdd(redo_count, 1)] = (int)prob;
+        if (tid == 0) {
+            redo_list[atomicAdd(redo_count, 1)] = (int)prob;
+            atomicAdd(&counters[10], 1ull);
+        }
     } else if (row < N) {
         double* o = Out + prob * (long long)N * nu + (size_t)row * nu;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
             if (col0 + c < nu) o[col0 + c] = df_to(acc[c]);
     }
+    if (!grew && !failed && tid == 0) atomicAdd(&counters[9], (unsigned long long)m);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(taddr, TALLOC);
@@ -394,7 +399,7 @@ size_t trial_orbitals_tc_smem(int nu) { return tt_smem_bytes(nu <= 16 ? 16 : 32)
 
 cudaError_t trial_orbitals_tc(cudaStream_t s, int N, int nu, long long problems, const double* S_all, bool s_is_df,
                               const double* Phi0, double* Out, const int* alive, int P, int* status, int* redo_list,
-                              int* redo_count, uint32_t lim) {
+                              int* redo_count, unsigned long long* counters, uint32_t lim) {
     if (problems <= 0) return cudaSuccess;
     if (!trial_orbitals_tc_supported(N, nu) || problems > (1LL << 31) - 1) return cudaErrorInvalidValue;
     const int NB = nu <= 16 ? 16 : 32, KB = N <= 64 ? 1 : 2;
@@ -408,16 +413,16 @@ cudaError_t trial_orbitals_tc(cudaStream_t s, int N, int nu, long long problems,
     const uint32_t l = lim ? lim : (1u << 26);
     if (KB == 1 && NB == 16)
         chebyshev_expm_tc_kernel<1, 16><<<(unsigned)problems, TT_THREADS, bytes, s>>>(N, nu, problems, S_all, sdf, Phi0, Out,
-                                                                                     alive, P, status, redo_list, redo_count, l);
+                                                                                     alive, P, status, redo_list, redo_count, counters, l);
     else if (KB == 1)
         chebyshev_expm_tc_kernel<1, 32><<<(unsigned)problems, TT_THREADS, bytes, s>>>(N, nu, problems, S_all, sdf, Phi0, Out,
-                                                                                     alive, P, status, redo_list, redo_count, l);
+                                                                                     alive, P, status, redo_list, redo_count, counters, l);
     else if (NB == 16)
         chebyshev_expm_tc_kernel<2, 16><<<(unsigned)problems, TT_THREADS, bytes, s>>>(N, nu, problems, S_all, sdf, Phi0, Out,
-                                                                                     alive, P, status, redo_list, redo_count, l);
+                                                                                     alive, P, status, redo_list, redo_count, counters, l);
     else
         chebyshev_expm_tc_kernel<2, 32><<<(unsigned)problems, TT_THREADS, bytes, s>>>(N, nu, problems, S_all, sdf, Phi0, Out,
-                                                                                     alive, P, status, redo_list, redo_count, l);
+                                                                                     alive, P, status, redo_list, redo_count, counters, l);
     count_launches(2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return trial_orbitals_df_list(s, N, nu, S_all, s_is_df, Phi0, Out, alive, P, status, redo_list, redo_count);
