@@ -58,3 +58,19 @@ def test_flop_counts_of_the_medium_workload(bench):
     assert bench.contract_flops_refresh(spec) == pytest.approx(12.55e6, rel=1e-3)
     # the cached form's share per refreshed pair: (G + 1) matrices of 2 n_up N^2
     assert bench.contract_flops_refresh(spec) == (spec.n_chol + 1) * 2 * spec.n_up * spec.N ** 2
+
+
+def test_headline_contraction_summary_gives_its_traffic(bench):
+    """The headline's contraction summary records DRAM bytes per pair for the
+    walker-side tensor-core kernel; bench.py reports them (scaled by pairs)
+    only while the kernel's device code has the recorded digest."""
+    src = os.path.join(ROOT, "paper_2505_18519_gb300", "csrc", "contract_tcw.cu")
+    summary, end, start = bench.TCW_TRAFFIC
+    fields = dict(line[2:].split(":", 1) for line in open(os.path.join(ROOT, "profiles", summary))
+                  if line.startswith("- ") and ":" in line)
+    recorded = fields["source_sha256_16"].strip().strip("`")
+    got = bench.tcw_traffic(1024, 64)
+    if recorded == bench.kernel_digest(src, end, start):
+        assert got == pytest.approx(1590968 * 1024 * 64)
+    else:
+        assert got is None
