@@ -84,12 +84,14 @@ struct ChebScratch {
 // may read the results in sc.
 __device__ __forceinline__ void cheb_interval(int N, const float* S32, int stride, ChebScratch& sc) {
     const int tid = threadIdx.x, nth = blockDim.x;
+    // S is symmetric: row i is read as column i, so that the threads of a warp
+    // (consecutive i) read consecutive words
     float lo = INFINITY, hi = -INFINITY;
     for (int i = tid; i < N; i += nth) {
         float r = 0.f;
         const float dgi = S32[((size_t)i * N + i) * stride];
         for (int j = 0; j < N; ++j)
-            if (j != i) r += fabsf(S32[((size_t)i * N + j) * stride]);
+            if (j != i) r += fabsf(S32[((size_t)j * N + i) * stride]);
         const float slack = 1e-5f * (r + fabsf(dgi)) + 1e-30f;   // keeps the FP32 sums a bound
         lo = fminf(lo, dgi - r - slack);
         hi = fmaxf(hi, dgi + r + slack);
@@ -116,15 +118,33 @@ __device__ __forceinline__ void cheb_interval(int N, const float* S32, int strid
     for (int i = tid; i < N; i += nth) sc.lz_v[1][i] *= rsqrtf(nrm);
     int ksteps = 0;
     float beta_prev = 0.f;
+    // S v: `parts` threads per row when the rows fit the block (partial sums over every
+    // parts-th column, added in a fixed order), else one thread per row
+    const int Np = (N + 31) & ~31;
+    const int parts = N <= nth ? nth / Np : 1;
     for (int j = 0; j < LZ_STEPS && j < N; ++j) {
         __syncthreads();
         float part = 0.f;
-        for (int i = tid; i < N; i += nth) {
-            float wsum = 0.f;
-            const float* Srow = S32 + (size_t)i * N * stride;
-            for (int q = 0; q < N; ++q) wsum = fmaf(Srow[(size_t)q * stride], sc.lz_v[1][q], wsum);
-            sc.lz_v[2][i] = wsum;
-            part = fmaf(wsum, sc.lz_v[1][i], part);
+        if (parts > 1) {
+            const int i = tid % Np, pr = tid / Np;
+            float ps = 0.f;
+            if (pr < parts && i < N)
+                for (int q = pr; q < N; q += parts) ps = fmaf(S32[((size_t)q * N + i) * stride], sc.lz_v[1][q], ps);
+            if (pr < parts) sc.red_lo[pr * Np + i] = ps;
+            __syncthreads();
+            if (tid < N) {
+                float wsum = 0.f;
+                for (int r = 0; r < parts; ++r) wsum += sc.red_lo[r * Np + tid];
+                sc.lz_v[2][tid] = wsum;
+                part = wsum * sc.lz_v[1][tid];
+            }
+        } else {
+            for (int i = tid; i < N; i += nth) {
+                float wsum = 0.f;
+                for (int q = 0; q < N; ++q) wsum = fmaf(S32[((size_t)q * N + i) * stride], sc.lz_v[1][q], wsum);
+                sc.lz_v[2][i] = wsum;
+                part = fmaf(wsum, sc.lz_v[1][i], part);
+            }
         }
         const float alpha = block_sum_f(part, sc.red8);
         float part2 = 0.f;

@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
     __shared__ float2 red_tr[2][2][128], red_ex[2][2][128];   // [matrix parity][column half][row]
     __shared__ double2 exacc[128];
     __shared__ int sA[128];
-    __shared__ float scl[128];                                 // 2^-yexp of the tile's columns
+    __shared__ __align__(16) float scl[128];                   // 2^-yexp of the tile's columns
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long wl = blockIdx.x / MT;
@@ -655,6 +655,7 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
         const float rowf = p2f(-sA[r]);
         const int nbh = (n + 1) >> 1;
         const int bh0 = half * nbh, bh1 = min(n, bh0 + nbh);
+        const bool n8 = (n & 7) == 0;
         // per-pair sums: lpp consecutive threads share a pair's rows
         int lpp = 32;
         while (lpp > 1 && lpp * PB > TCWZ_EPI) lpp >>= 1;
@@ -676,6 +677,39 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
                 if (g >= G1) break;                              // uniform
                 const int c0 = gl * 2 * n + 2 * bh0, c1 = gl * 2 * n + 2 * bh1;
                 const float* sc = scl + gl * n;
+                if (n8) {
+                    // n a multiple of 8: this half's columns [c0, c1) are whole groups of 8 (four
+                    // complex entries) starting on a multiple of 8; up to four groups per wait
+                    for (int jb = c0; jb < c1; jb += 32) {
+                        const int cnt = min(32, c1 - jb) >> 3;       // uniform across the warp
+                        float v[32], w[32];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (k < cnt) {
+                                tc::tmem_ld8(dh + (uint32_t)(jb + 8 * k), *reinterpret_cast<float(*)[8]>(v + 8 * k));
+                                if (F16)
+                                    tc::tmem_ld8(dl + (uint32_t)(jb + 8 * k), *reinterpret_cast<float(*)[8]>(w + 8 * k));
+                            }
+                        tc::tmem_ld_wait();
+                        if (row_ok) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (k < cnt) {
+                                    const int b0 = (jb + 8 * k - gl * 2 * n) >> 1;   // a multiple of 4
+                                    const float4 s4 = *reinterpret_cast<const float4*>(sc + b0);
+                                    const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                                    for (int t = 0; t < 4; ++t) {
+                                        const int qq = 8 * k + 2 * t;
+                                        const float re = F16 ? v[qq] + w[qq] : v[qq];
+                                        const float im = F16 ? v[qq + 1] + w[qq + 1] : v[qq + 1];
+                                        const float f = rowf * sv[t];
+                                        Ms[(size_t)r * ld + b0 + t] = make_float2(re * f, im * f);
+                                    }
+                                }
+                        }
+                    }
+                } else
                 for (int j0 = (c0 / 16) * 16; j0 < c1; j0 += 32) {   // up to two 16-column chunks per wait
                     // the second chunk only while it holds columns of this range: reads stay inside the
                     // buffer's NT columns (uniform across the warp)

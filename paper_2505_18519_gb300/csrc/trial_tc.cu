@@ -120,19 +120,8 @@ __device__ __forceinline__ dfl tt_combine(float a0, float a1, float a2, float a3
 // 32 lanes x C (4 or 8) columns of 32-bit data from tensor memory.
 template <int C>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[C]) {
-    uint32_t r[8];
-    if constexpr (C == 8) {
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                     : "r"(taddr));
-    } else {
-        static_assert(C == 4, "4 or 8 columns");
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                     : "r"(taddr));
-    }
-#pragma unroll
-    for (int i = 0; i < C; ++i) v[i] = __uint_as_float(r[i]);
+    if constexpr (C == 8) tc::tmem_ld8(taddr, v);
+    else tc::tmem_ld4(taddr, v);
 }
 
 // KB: K blocks of 64 (1 for N <= 64, else 2); NB: columns of V in the MMA (16 or 32).
@@ -187,7 +176,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         float m = 0.f;
         if (tid < N) {
             const float cf = (float)cst;
-            for (int j = 0; j < N; ++j) m = fmaxf(m, fabsf(S32[(size_t)tid * N + j] - (j == tid ? cf : 0.f)));
+            for (int j = 0; j < N; ++j) m = fmaxf(m, fabsf(S32[(size_t)j * N + tid] - (j == tid ? cf : 0.f)));   // S symmetric
         }
         sexp[tid] = tt_exp(m * (float)(1.0 / rho));
     }
