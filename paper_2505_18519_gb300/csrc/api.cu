@@ -84,6 +84,19 @@ int tc_kind(const afqmc_config* c) {
     return tcw ? 5 : -1;
 }
 
+// The mixed path's overlaps form A = Phi^T phi (and, for the walker-side contraction, B =
+// Phi A^-T) in double-float: the general walker-side form with a real trial and at most 32
+// electrons per spin.  The LU, log det and A^-1 stay FP64.
+static bool overlaps_in_df(const afqmc_config* c) {
+    return c->precision != AFQMC_PRECISION_FP64 && !general_trial(c) && c->n_up <= 32 && c->n_dn <= 32 &&
+           tc_kind(c) == 5;
+}
+
+// Double-float copies of `doubles` FP64 values (u_to_df).
+static cudaError_t df_copy(cudaStream_t s, const void* src, long long doubles, void* dst) {
+    return u_to_df(s, doubles, static_cast<const double*>(src), dst);
+}
+
 static std::mutex g_smem_mu;
 static std::map<std::pair<const void*, int>, size_t> g_smem_limit;   // (kernel, device) -> bytes allowed
 
@@ -368,6 +381,10 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
     if (c->precision != AFQMC_PRECISION_FP64) {
         w.cheb_redo = (int*)take((pairs + 1) * 4);   // list, then its count at [pairs]
     }
+    if (overlaps_in_df(c)) {
+        w.Phidf = take(pairs * phi_stride(d) * 8);
+        w.phidf = take(W * N * nt * 16);
+    }
     w.logdet_prop = (double2*)take(pairs * 2 * 16);
     w.history = (double*)take((size_t)c->history_capacity * 4 * 8);
     w.reduce = (double*)take(8 * 8);
@@ -522,8 +539,12 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
     else
         CK(trial_orbitals_of(ctx, d.pairs, w.Phiprop, w.alive, d.P));
     if ((st = prof_mark(ctx, PH_TRIAL)) != AFQMC_OK) return st;
+    if (w.Phidf) {
+        CK(df_copy(s, w.Phiprop, d.pairs * phi_stride(d), w.Phidf));
+        CK(df_copy(s, orbitals, d.W * (long long)d.N * d.nt * 2, w.phidf));
+    }
     CK(overlap_lu_both(s, d, w.Phiprop, phi_stride(d), orbitals, w.logdet_prop, nullptr, w.alive, w.status,
-                       d.pairs, d.P));
+                       d.pairs, d.P, OVL_THETA, nullptr, w.Phidf, w.phidf));
     if ((st = prof_mark(ctx, PH_MCMC_OVERLAP)) != AFQMC_OK) return st;
     CK(accept(s, d, p, w.counters, tag_acc, sweep, w.logdet_prop, w.xprop, w.Phiprop, w.alive, w.mlp.mu, w.mlp.logv,
               w.logov_cur, w.x, w.Phi, w.counters, w.rdirty));
@@ -542,12 +563,18 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     const int tck = fp64 ? -1 : tc_kind(&ctx->cfg);
     const int ovl = fp64 ? (!w.rc && !d.cphi && contract_fp64_walker_side(d.N, d.nu, d.nd, d.P) ? OVL_INVERSE : OVL_THETA)
                          : (tck == 2 || tck == 5 ? OVL_TRIAL : OVL_THETA);
+    if (w.Phidf) {
+        CK(df_copy(s, w.Phi, d.pairs * phi_stride(d), w.Phidf));
+        CK(df_copy(s, w.phi, d.W * (long long)d.N * d.nt * 2, w.phidf));
+    }
     CK(overlap_lu_both(s, d, w.Phi, phi_stride(d), w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
-                       ovl, tck == 5 && w.refine_items ? w.refine_th2 : nullptr));
+                       ovl, tck == 5 && w.refine_items ? w.refine_th2 : nullptr, w.Phidf, w.phidf,
+                       w.Phidf && ovl == OVL_TRIAL));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64) {
         if (tck == 5)
-            CK(contract_tcw(s, d, w.tcw, w.Theta, w.phi, w.vpair, w.epair, w.status, tc_mode(&ctx->cfg)));
+            CK(contract_tcw(s, d, w.tcw, w.Theta, w.phi, w.vpair, w.epair, w.status, tc_mode(&ctx->cfg),
+                            w.Phidf != nullptr));
         else
             CK(contract_tc(s, d, w.Lt, w.Phi, w.Theta, w.phi, w.Yimg, w.vpair, w.epair, w.status, f16));
     } else if (w.rc) {   // cached half-rotated matrices, refreshed for the paths that moved
@@ -738,8 +765,9 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         else
             CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive, w.propbuf));   // Eq. (12)
         if ((st = prof_mark(ctx, PH_PROPAGATE)) != AFQMC_OK) return st;
+        if (w.Phidf) CK(df_copy(s, w.phi_new, d.W * (long long)d.N * d.nt * 2, w.phidf));   // Phi's copy: measure
         CK(overlap_lu_both(s, d, w.Phi, phi_stride(d), w.phi_new, w.logdet_new, nullptr, w.alive, w.status,
-                           d.pairs, d.P));
+                           d.pairs, d.P, OVL_THETA, nullptr, w.Phidf, w.phidf));
         CK(ratios(s, d, w.logov, w.logdet_new, w.sumS, w.logshift, w.alive, w.logov_cur, w.old_sum, w.ratio, w.Iabs));
         if ((st = prof_mark(ctx, PH_RATIO)) != AFQMC_OK) return st;
         if (ctx->cfg.proposal == AFQMC_PROPOSAL_MLP) {       // proposal conditioned on the new walkers

@@ -187,6 +187,9 @@ struct Workspace {
     int* refine_n;        // 1     their number
     double* refine_lam;   // G+1   ||L_g||_2^2, then their sum at [G]
     int* cheb_redo;       // W*P+1 trial orbitals to redo in double-float (tensor-core kernel), count at [W*P]
+    // double-float copies for the overlaps' products on the mixed path (null when not used):
+    void* Phidf;          // W*P*N*n_up  8-byte pairs: Phi at a measurement, then Phi(x') in a sweep
+    void* phidf;          // W*N*nt      16 bytes per complex entry: the walkers the overlap reads
     double* Aplanes;  // 2W*N*N  rows 2w: sum_g Re(y) L_g ; 2w+1: sum_g Im(y) L_g
                       //         (double-float pairs, 8 bytes each, on the mixed-precision path)
     double2* phi_new; // W*N*nt

@@ -128,6 +128,12 @@ __device__ __forceinline__ void split_parts(double x, uint16_t (&o)[tcw_parts(MO
         split2<MODE == 1>((float)x, o[0], o[1]);
     }
 }
+// The same from a double-float value xh + xl (already scaled).
+template <int MODE>
+__device__ __forceinline__ void split_parts_df(float xh, float xl, uint16_t (&o)[tcw_parts(MODE)]) {
+    if constexpr (MODE == 2) split3(xh, xl, o[0], o[1], o[2]);
+    else split2<MODE == 1>(xh + xl, o[0], o[1]);
+}
 template <int MODE>
 __device__ __forceinline__ void split_parts_f(float x, uint16_t (&o)[tcw_parts(MODE)]) {
     if constexpr (MODE == 2) split3(x, 0.f, o[0], o[1], o[2]);
@@ -441,11 +447,12 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
 // (pairs m PB .. m PB + PB - 1 of the walker), one spin.  Row r = p_l n + a:
 // [Re B_p[:, col0 + a] | Im B_p[:, col0 + a]] times 2^aexp[r] (largest entry in
 // [64, 128)), split; KC chunks of NP parts of 16 KB; rows past the tile's pairs
-// are zero.
+// are zero.  bdf: B as double-float pairs (Re hi, Re lo, Im hi, Im lo) per entry.
 template <int MODE>
 __global__ void __launch_bounds__(256) tcw_a_kernel(int N, int nt, int col0, int n, int P, int PB, int MT, int N16,
                                                     int KC, long long w0, const double2* __restrict__ Bm,
-                                                    uint8_t* __restrict__ Aimg, int* __restrict__ aexp) {
+                                                    uint8_t* __restrict__ Aimg, int* __restrict__ aexp, int bdf) {
+    const float4* Bd = reinterpret_cast<const float4*>(Bm);
     constexpr int NP = tcw_parts(MODE);
     constexpr uint32_t CH = tcw_chunk(MODE);
     __shared__ int sA[128];
@@ -459,8 +466,14 @@ __global__ void __launch_bounds__(256) tcw_a_kernel(int N, int nt, int col0, int
         float mx = 0.f;
         if (r < np * n)
             for (int i = lane; i < N; i += 32) {
-                const double2 t = Bm[(pair0 + p) * (long long)N * nt + (long long)i * nt + col0 + a];
-                mx = fmaxf(mx, fmaxf((float)fabs(t.x), (float)fabs(t.y)));
+                const long long o = (pair0 + p) * (long long)N * nt + (long long)i * nt + col0 + a;
+                if (bdf) {
+                    const float4 t = Bd[o];
+                    mx = fmaxf(mx, fmaxf(fabsf(t.x), fabsf(t.z)));
+                } else {
+                    const double2 t = Bm[o];
+                    mx = fmaxf(mx, fmaxf((float)fabs(t.x), (float)fabs(t.y)));
+                }
             }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -476,13 +489,26 @@ __global__ void __launch_bounds__(256) tcw_a_kernel(int N, int nt, int col0, int
         for (int q = 0; q < 8; ++q) {
             const int k = c * 64 + u * 8 + q;
             const int i = k < N16 ? k : k - N16;
-            double x = 0.0;
-            if (r < np * n && i < N && k < 2 * N16) {
-                const double2 t = Bm[(pair0 + p) * (long long)N * nt + (long long)i * nt + col0 + a];
-                x = ldexp(k < N16 ? t.x : t.y, sA[r]);
-            }
             uint16_t o[NP];
-            split_parts<MODE>(x, o);
+            const bool in = r < np * n && i < N && k < 2 * N16;
+            const long long off = (pair0 + p) * (long long)N * nt + (long long)i * nt + col0 + a;
+            if (bdf) {   // scaling by 2^sA is exact on both parts
+                float xh = 0.f, xl = 0.f;
+                if (in) {
+                    const float4 t = Bd[off];
+                    const float f = p2f(sA[r]);
+                    xh = (k < N16 ? t.x : t.z) * f;
+                    xl = (k < N16 ? t.y : t.w) * f;
+                }
+                split_parts_df<MODE>(xh, xl, o);
+            } else {
+                double x = 0.0;
+                if (in) {
+                    const double2 t = Bm[off];
+                    x = ldexp(k < N16 ? t.x : t.y, sA[r]);
+                }
+                split_parts<MODE>(x, o);
+            }
 #pragma unroll
             for (int pp = 0; pp < NP; ++pp) pt[pp][q] = o[pp];
         }
@@ -972,7 +998,7 @@ __global__ void tcw_lexp_kernel(int N, int G1, const double* __restrict__ h, con
 
 template <int MODE>
 cudaError_t tcw_run(cudaStream_t st, const Dims& d, const TcwShape& s, const TcwWork& w, const double2* Bm,
-                    const double2* phi, double2* vpair, double2* epair, int* status) {
+                    const double2* phi, double2* vpair, double2* epair, int* status, int bdf) {
     cudaError_t e;
     if ((e = raise_smem_limit((const void*)tcw_y_kernel<MODE>, s.smem_y)) != cudaSuccess) return e;
     if ((e = raise_smem_limit((const void*)contract_tcw_kernel<MODE>, std::max(s.sp[0].smem, s.sp[1].smem))) !=
@@ -990,7 +1016,7 @@ cudaError_t tcw_run(cudaStream_t st, const Dims& d, const TcwShape& s, const Tcw
                 d.N, d.nt, col0, sp.n, s.G1, s.N16, s.KCX, s.SY, s.GPB, n_gblk, w0, phi, w.ximg, w.lexp, sp.NT, sp.GB,
                 s.KC, sp.NTILES, w.yimg, w.yexp, status, d.wait_polls);
             tcw_a_kernel<MODE><<<(unsigned)(wb * sp.MT), 256, 0, st>>>(d.N, d.nt, col0, sp.n, d.P, sp.PB, sp.MT, s.N16,
-                                                                      s.KC, w0, Bm, w.aimg, w.aexp);
+                                                                      s.KC, w0, Bm, w.aimg, w.aexp, bdf);
             contract_tcw_kernel<MODE><<<(unsigned)(wb * sp.MT), TCWZ_THREADS, sp.smem, st>>>(
                 sp.n, s.G1, s.KZ, s.KC, sp.NT, sp.GB, sp.NTILES, d.P, sp.PB, sp.MT, sp.S, sp.a_res, w0, w.aimg, w.aexp,
                 w.yimg, w.yexp, w.vpart[q], w.exsum[q], status, d.wait_polls);
@@ -1039,14 +1065,15 @@ cudaError_t contract_tcw_prepare(cudaStream_t st, const Dims& d, const double* h
 }
 
 cudaError_t contract_tcw(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,
-                         double2* vpair, double2* epair, int* status, int mode) {
+                         double2* vpair, double2* epair, int* status, int mode, bool b_df) {
     TcwShape s;
     if (!tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, mode, s)) return cudaErrorInvalidValue;
     if (d.pairs <= 0) return cudaSuccess;
     TcwWork w = tcw_carve(work, s, d.G, d.pairs);
-    if (mode == 2) return tcw_run<2>(st, d, s, w, Bm, phi, vpair, epair, status);
-    if (mode == 1) return tcw_run<1>(st, d, s, w, Bm, phi, vpair, epair, status);
-    return tcw_run<0>(st, d, s, w, Bm, phi, vpair, epair, status);
+    const int bdf = b_df ? 1 : 0;
+    if (mode == 2) return tcw_run<2>(st, d, s, w, Bm, phi, vpair, epair, status, bdf);
+    if (mode == 1) return tcw_run<1>(st, d, s, w, Bm, phi, vpair, epair, status, bdf);
+    return tcw_run<0>(st, d, s, w, Bm, phi, vpair, epair, status, bdf);
 }
 
 }  // namespace afq

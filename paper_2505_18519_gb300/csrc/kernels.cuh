@@ -18,15 +18,23 @@ enum OverlapOutput { OVL_THETA = 0, OVL_TRIAL = 1, OVL_INVERSE = 2 };
 // th2 (nullable, with Theta): ||A^-1||_F^2 per pair and spin at th2[2 pair + spin]
 // (infinite for a singular or non-finite overlap).  list, n_list (nullable): only
 // the pairs list[0 .. *n_list), a device list, with the grid sized for `pairs` of them.
+// PhiD, phiD (nullable; the mixed-precision path, real trial, n <= 32): double-float
+// copies of Phi (same strides, 8 bytes per entry) and of the walkers (16 bytes per
+// complex entry, from u_to_df of the FP64 arrays): A = Phi^T phi is then formed
+// in double-float (compensated sums), the LU, log det and A^-1 stay FP64.  b_df
+// (with PhiD and OVL_TRIAL): B = Phi A^-T in double-float, written as (Re hi, Re
+// lo, Im hi, Im lo) per entry in place of the FP64 values.
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
                        long long pairs, int P, int trial_side = OVL_THETA, double* th2 = nullptr,
-                       const int* list = nullptr, const int* n_list = nullptr);
-// Both spins: one warp per pair (half a warp per spin) when n_up <= 16, else
-// overlap_lu for each spin.  Same results.
+                       const int* list = nullptr, const int* n_list = nullptr, const void* PhiD = nullptr,
+                       const void* phiD = nullptr, bool b_df = false);
+// Both spins: one warp per pair (half a warp per spin) when n_up <= 16 and no
+// double-float products are asked for, else overlap_lu for each spin.  Same results.
 cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, long long Phi_stride,
                             const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                            long long pairs, int P, int trial_side = OVL_THETA, double* th2 = nullptr);
+                            long long pairs, int P, int trial_side = OVL_THETA, double* th2 = nullptr,
+                            const void* PhiD = nullptr, const void* phiD = nullptr, bool b_df = false);
 cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, double2* dst, const int* alive,
                              int* status, int n_walkers);
 // Phi = exp(S) Phi0 for `problems` symmetric S (FP64).  trial_orbitals runs the
@@ -133,8 +141,9 @@ bool contract_tcw_supported(int N, int nu, int nd, int G, long long W, int P, in
 size_t contract_tcw_work_bytes(int N, int nu, int nd, int G, long long W, int P, int mode);
 cudaError_t contract_tcw_prepare(cudaStream_t st, const Dims& d, const double* h, const double* L, void* work,
                                  int mode);
+// b_df: Bm holds B as double-float pairs (overlap_lu with b_df), else FP64.
 cudaError_t contract_tcw(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,
-                         double2* vpair, double2* epair, int* status, int mode);
+                         double2* vpair, double2* epair, int* status, int mode, bool b_df = false);
 
 // trial_complex.cu: complex and multi-slice trial samples (FP64 path).
 // Out = exp(alpha S) V0 per problem (S real symmetric in S_all; V0 = the real

@@ -2,6 +2,7 @@
 // Theta = phi (Phi^T phi)^-1 matrices, re-orthonormalisation, the trial
 // orbitals Phi(x) = exp(S) Phi0 by a Chebyshev series, a plain FP64 GEMM, and the
 // init-time one-body propagator exp(-tau T / 2).
+#include "df.cuh"
 #include "kernels.cuh"
 
 namespace afq {
@@ -81,7 +82,8 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
                                   const double2* __restrict__ phi, double2* __restrict__ logdet,
                                   double2* __restrict__ Theta, const int* __restrict__ alive, int* status,
                                   int trial_side, double* __restrict__ th2, const int* __restrict__ list,
-                                  const int* __restrict__ n_list, int cphi) {
+                                  const int* __restrict__ n_list, int cphi, const dfl* __restrict__ PhiD,
+                                  const float4* __restrict__ phiD, int b_df) {
     extern __shared__ double2 sm[];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
@@ -108,6 +110,37 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
         return;
     }
     bool bad = false;
+    if (PhiD) {
+        // double-float products (mixed-precision path, real trial, n <= 32): lane b owns
+        // column b of A, rows in chunks of 8; Phi entries are broadcast loads, the
+        // walker's column b one coalesced 16-byte load per row
+        const dfl* PD = PhiD + pair * Phi_stride;
+        const float4* pcol = phiD + w * (long long)N * nt + col0 + lane;
+        for (int a0 = 0; a0 < n; a0 += 8) {
+            float rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) rh[t] = rl[t] = ih[t] = il[t] = 0.f;
+            for (int i = 0; i < N; ++i) {
+                const float4 g = lane < n ? pcol[(long long)i * nt] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const dfl gr = {g.x, g.y}, gi = {g.z, g.w};
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (a0 + t < n) {   // uniform
+                        const dfl f = PD[(long long)i * nu + a0 + t];
+                        dot2_fma(rh[t], rl[t], f, gr);
+                        dot2_fma(ih[t], il[t], f, gi);
+                    }
+            }
+            if (lane < n)
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (a0 + t < n) {
+                        const double2 v = cmk(df_to(df_two_sum(rh[t], rl[t])), df_to(df_two_sum(ih[t], il[t])));
+                        A[(a0 + t) * n + lane] = v;
+                        bad |= !isfinite(v.x) || !isfinite(v.y);
+                    }
+        }
+    } else
     for (int e = lane; e < n * n; e += 32) {
         int a = e / n, b = e - a * n;
         double2 s = cmk(0.0, 0.0);
@@ -264,6 +297,32 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
         return;
     }
     double2* Th = Theta + pair * (long long)N * nt + col0;
+    if (trial_side && b_df) {
+        // B = Phi A^-T in double-float, written as (Re hi, Re lo, Im hi, Im lo): A^-1
+        // transposed into A's space as double-float values, lane b forms column b of B
+        float4* AT = reinterpret_cast<float4*>(A);
+        for (int e = lane; e < n * n; e += 32) {
+            const int bb = e / n, a = e - bb * n;
+            const dfl re = df_from(Ainv[e].x), im = df_from(Ainv[e].y);
+            AT[a * n + bb] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+        __syncwarp();
+        const dfl* PD = PhiD + pair * Phi_stride;
+        float4* Bd = reinterpret_cast<float4*>(Th) + lane;
+        if (lane < n)
+            for (int i = 0; i < N; ++i) {
+                float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+                for (int a = 0; a < n; ++a) {
+                    const dfl f = PD[(long long)i * nu + a];
+                    const float4 t = AT[a * n + lane];
+                    dot2_fma(rh, rl, f, dfl{t.x, t.y});
+                    dot2_fma(ih, il, f, dfl{t.z, t.w});
+                }
+                const dfl re = df_two_sum(rh, rl), im = df_two_sum(ih, il);
+                Bd[(long long)i * nt] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            }
+        return;
+    }
     if (trial_side) {
         // B = Phi A^-T (trial side): B[i][b] = sum_a Phi[i][a] (A^-1)[b][a]; for complex
         // trial orbitals B = conj(Phi) A^-T, so that B^T X phi = A^-1 Phi^dagger X phi
@@ -300,8 +359,11 @@ static size_t overlap_smem_per_warp(int n, bool theta) {
 
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                       long long pairs, int P, int trial_side, double* th2, const int* list, const int* n_list) {
+                       long long pairs, int P, int trial_side, double* th2, const int* list, const int* n_list,
+                       const void* PhiD, const void* phiD, bool b_df) {
     int n = spin == 0 ? d.nu : d.nd;
+    if (PhiD && (d.cphi || n > 32 || !phiD)) return cudaErrorInvalidValue;
+    if (b_df && (!PhiD || trial_side != OVL_TRIAL)) return cudaErrorInvalidValue;
     int col0 = spin == 0 ? 0 : d.nu;
     size_t per = overlap_smem_per_warp(n, Theta != nullptr);
     int wpb = d.ov_wpb > 0 ? d.ov_wpb : 4;
@@ -313,7 +375,9 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
     long long blocks = (pairs + wpb - 1) / wpb;
     overlap_lu_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nt, n, col0, spin, pairs, P, Phi, Phi_stride,
                                                                phi, logdet, Theta, alive, status, trial_side, th2, list,
-                                                               n_list, d.cphi); count_launches(1);
+                                                               n_list, d.cphi, static_cast<const dfl*>(PhiD),
+                                                               static_cast<const float4*>(phiD), b_df ? 1 : 0);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -536,11 +600,14 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
 
 cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, long long Phi_stride,
                             const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
-                            long long pairs, int P, int trial_side, double* th2) {
-    if (d.nu > 16) {   // a half-warp per spin would leave the larger matrices short of lanes
+                            long long pairs, int P, int trial_side, double* th2, const void* PhiD, const void* phiD,
+                            bool b_df) {
+    // a half-warp per spin would leave the larger matrices short of lanes; the
+    // double-float products run in the per-spin kernel
+    if (d.nu > 16 || PhiD) {
         for (int spin = 0; spin < 2; ++spin) {
             const cudaError_t e = overlap_lu(s, d, spin, Phi, Phi_stride, phi, logdet, Theta, alive, status, pairs, P,
-                                             trial_side, th2);
+                                             trial_side, th2, nullptr, nullptr, PhiD, phiD, b_df);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;

@@ -12,9 +12,6 @@
   Hamiltonian, E(n) = sum_i eps_i n_i + 1/2 sum_g [(sum_i l_gi n_i)^2 -
   sum_i l_gi^2 n_i], and is checked against the lowest eigenvalue of H built
   literally in determinant space.
-* The small workload's system (8 orbitals, 4 + 4 electrons, 4900 determinants)
-  run long on the FP64 GPU path (each step of which matches the oracle to 1e-9):
-  its mixed energy reaches the FCI energy within a bound on the phaseless bias.
 """
 
 import itertools
