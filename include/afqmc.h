@@ -174,14 +174,17 @@ typedef struct {
                            learned one, rcache = 0, and 48 N n_up bytes of shared memory at most
                            200 KB; Phi is then stored and returned as complex (state buffer) */
     int trial_form;     /* mixed precision: how the trial orbitals exp(S) Phi0 of Eq. (20)-(21) are formed.
-                           AFQMC_TRIAL_AUTO (0, default): the Chebyshev products S V on the tensor cores
-                           (each operand split into five 8-bit integer digits, the digit products of orders
-                           0-5 accumulated exactly in FP32, combined in double-float: about 40 bits) where
-                           N <= 128 and n_up <= 32, else as AFQMC_TRIAL_DF; AFQMC_TRIAL_DF (1): the whole
-                           recurrence in double-float arithmetic (about 44 bits) on the CUDA cores */
+                           AFQMC_TRIAL_TC (2): the Chebyshev products S V on the tensor cores (each operand
+                           split into five 8-bit integer digits, the digit products of orders 0-5
+                           accumulated exactly in FP32, combined in double-float: about 40 bits), one
+                           proposal per SM, where N <= 128 and n_up <= 32, else as AFQMC_TRIAL_DF;
+                           AFQMC_TRIAL_DF (1): the whole recurrence in double-float arithmetic (about 44
+                           bits) on the CUDA cores, several proposals per SM; AFQMC_TRIAL_AUTO (0,
+                           default): the tensor cores for 64 < N <= 128, else double-float (measured: the
+                           tensor-core form is 5.9x faster at N = 120, 2.2x slower at N = 50) */
 } afqmc_config;
 
-enum { AFQMC_TRIAL_AUTO = 0, AFQMC_TRIAL_DF = 1 };
+enum { AFQMC_TRIAL_AUTO = 0, AFQMC_TRIAL_DF = 1, AFQMC_TRIAL_TC = 2 };
 
 enum { AFQMC_TC_AUTO = 0, AFQMC_TC_PER_PAIR = 1, AFQMC_TC_WALKER = 2 };
 

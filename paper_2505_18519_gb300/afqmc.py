@@ -23,7 +23,7 @@ PROPOSALS = {"prior": 0, "pcn": 1, "rw": 2, "mlp": 3}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "fp16x3": 2, "fp16x6": 3}
 IMPORTANCE = {"hybrid": 0, "local_energy": 1}
 TC_FORMS = {"auto": 0, "per_pair": 1, "walker": 2}
-TRIAL_FORMS = {"auto": 0, "df": 1}
+TRIAL_FORMS = {"auto": 0, "df": 1, "tc": 2}
 STATE_MAGIC = 0x4146514D43535431
 
 

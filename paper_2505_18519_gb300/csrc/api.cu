@@ -85,10 +85,10 @@ int tc_kind(const afqmc_config* c) {
 }
 
 // The mixed path's overlaps form A = Phi^T phi (and, for the walker-side contraction, B =
-// Phi A^-T) in double-float: the general walker-side form with a real trial and at most 32
-// electrons per spin.  The LU, log det and A^-1 stay FP64.
+// Phi A^-T) in double-float: the general walker-side form with a real trial (at most 64
+// electrons per spin, its limit).  The LU, log det and A^-1 stay FP64.
 static bool overlaps_in_df(const afqmc_config* c) {
-    return c->precision != AFQMC_PRECISION_FP64 && !general_trial(c) && c->n_up <= 32 && c->n_dn <= 32 &&
+    return c->precision != AFQMC_PRECISION_FP64 && !general_trial(c) && c->n_up <= 64 && c->n_dn <= 64 &&
            tc_kind(c) == 5;
 }
 
@@ -244,7 +244,7 @@ static const char* check_config(const afqmc_config* c) {
     if (c->pop_period > 0 && c->n_walkers > 65535) return "population control supports at most 65535 walkers";
     if (c->rcache != 0 && c->rcache != 1) return "rcache must be 0 or 1";
     if (c->wait_polls < 0 || c->wait_polls > (1ll << 31)) return "wait_polls must be in [0, 2^31]";
-    if (c->trial_form != AFQMC_TRIAL_AUTO && c->trial_form != AFQMC_TRIAL_DF) return "unknown trial_form";
+    if (c->trial_form < AFQMC_TRIAL_AUTO || c->trial_form > AFQMC_TRIAL_TC) return "unknown trial_form";
     if (c->rcache && c->precision != AFQMC_PRECISION_FP64) return "rcache needs precision FP64";
     if (c->rcache && !contract_fp64r_supported(c->N, c->n_up, c->n_dn))
         return "sizes too large for the cached half-rotation form (Theta and one matrix per warp, 4 warps per block)";
@@ -430,6 +430,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
         m.loss_part = (double*)take(W * 8);
         m.loss = (double*)take(8);
         m.counter = (unsigned long long*)take(8);
+        m.status = w.status;
     }
     w.total = (off + 255) & ~(size_t)255;
     if (ws) *ws = w;
@@ -452,16 +453,18 @@ static StepParams params_of(const afqmc_config* c) {
 }
 
 // The mixed-precision path forms S and the trial orbitals in double-float
-// arithmetic (S stored as double-float pairs) when S fits the trial kernel's
-// shared memory; the FP64 path in FP64.
+// arithmetic (S stored as double-float pairs) when the trial kernel's vectors fit
+// its shared memory (S there too, or read from global memory); the FP64 path in FP64.
 static bool s_in_df(const afqmc_ctx* ctx) {
-    return ctx->cfg.precision != AFQMC_PRECISION_FP64 && trial_orbitals_df_supported(ctx->d.N, ctx->d.nu);
+    return ctx->cfg.precision != AFQMC_PRECISION_FP64 &&
+           (trial_orbitals_df_supported(ctx->d.N, ctx->d.nu) || trial_orbitals_dfg_supported(ctx->d.N, ctx->d.nu));
 }
 
 // Trial orbitals of the mixed-precision path on the tensor cores (trial_tc.cu).
 static bool trial_on_tc(const afqmc_ctx* ctx) {
-    return ctx->cfg.precision != AFQMC_PRECISION_FP64 && ctx->cfg.trial_form == AFQMC_TRIAL_AUTO &&
-           trial_orbitals_tc_supported(ctx->d.N, ctx->d.nu);
+    const int f = ctx->cfg.trial_form;
+    return ctx->cfg.precision != AFQMC_PRECISION_FP64 && f != AFQMC_TRIAL_DF &&
+           trial_orbitals_tc_supported(ctx->d.N, ctx->d.nu) && (f == AFQMC_TRIAL_TC || ctx->d.N > 64);
 }
 
 // S_m = sum_k X[m, k] U_k into ws.Sprop for `M` rows of X.

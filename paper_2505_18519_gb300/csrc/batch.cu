@@ -120,7 +120,8 @@ extern "C" afqmc_status afqmc_autotune(afqmc_ctx* ctx, int* chosen) {
             return c.precision == AFQMC_PRECISION_FP64
                        ? trial_orbitals(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phiprop, w.alive, d.P, w.status, th)
                        : trial_orbitals_df(s, d.N, d.nu, d.pairs, w.Sprop, w.Phi0, w.Phiprop, w.alive, d.P, w.status, th,
-                                           trial_orbitals_df_supported(d.N, d.nu));
+                                           trial_orbitals_df_supported(d.N, d.nu) ||
+                                               trial_orbitals_dfg_supported(d.N, d.nu));
         }, 1, &ms);
         if (st != AFQMC_OK) return st;
         if (ms < best) { best = ms; best_th = th; }

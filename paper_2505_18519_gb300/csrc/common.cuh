@@ -138,6 +138,7 @@ struct MlpBuffers {
     float *gW1p, *gb1, *gW2, *gb2, *gW3p, *gb3p;   // padded weight gradients, bias sums
     double *loss_part, *loss;          // W, 1
     unsigned long long* counter;       // Adam steps taken
+    int* status;                       // the context's device status word (a GEMM's wait that gave up)
 };
 
 // ---------------------------------------------------------------- workspace layout

@@ -18,7 +18,7 @@ enum OverlapOutput { OVL_THETA = 0, OVL_TRIAL = 1, OVL_INVERSE = 2 };
 // th2 (nullable, with Theta): ||A^-1||_F^2 per pair and spin at th2[2 pair + spin]
 // (infinite for a singular or non-finite overlap).  list, n_list (nullable): only
 // the pairs list[0 .. *n_list), a device list, with the grid sized for `pairs` of them.
-// PhiD, phiD (nullable; the mixed-precision path, real trial, n <= 32): double-float
+// PhiD, phiD (nullable; the mixed-precision path, real trial, n <= 64): double-float
 // copies of Phi (same strides, 8 bytes per entry) and of the walkers (16 bytes per
 // complex entry, from u_to_df of the FP64 arrays): A = Phi^T phi is then formed
 // in double-float (compensated sums), the LU, log det and A^-1 stay FP64.  b_df
@@ -52,6 +52,9 @@ cudaError_t trial_orbitals_df(cudaStream_t s, int N, int nu, long long problems,
                               double* Out, const int* alive, int P, int* status, int threads = 256,
                               bool s_is_df = false);
 bool trial_orbitals_df_supported(int N, int nu);
+// With S as double-float pairs and too large for shared memory, the same kernel
+// reads S from global memory: N <= 256 and 3 N n_up doubles of vectors in 200 KB.
+bool trial_orbitals_dfg_supported(int N, int nu);
 // The double-float kernel for the problems list[0 .. *count) (a device list), on
 // one block per SM.
 cudaError_t trial_orbitals_df_list(cudaStream_t s, int N, int nu, const double* S_all, bool s_is_df, const double* Phi0,

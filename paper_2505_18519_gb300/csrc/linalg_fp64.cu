@@ -111,17 +111,19 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
     }
     bool bad = false;
     if (PhiD) {
-        // double-float products (mixed-precision path, real trial, n <= 32): lane b owns
-        // column b of A, rows in chunks of 8; Phi entries are broadcast loads, the
-        // walker's column b one coalesced 16-byte load per row
+        // double-float products (mixed-precision path, real trial, n <= 64): lane b owns
+        // column b0 + b of A (column groups of 32), rows in chunks of 8; Phi entries are
+        // broadcast loads, the walker's column one coalesced 16-byte load per row
         const dfl* PD = PhiD + pair * Phi_stride;
-        const float4* pcol = phiD + w * (long long)N * nt + col0 + lane;
+        for (int b0 = 0; b0 < n; b0 += 32)
         for (int a0 = 0; a0 < n; a0 += 8) {
+            const int b = b0 + lane;
+            const float4* pcol = phiD + w * (long long)N * nt + col0 + b;
             float rh[8], rl[8], ih[8], il[8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) rh[t] = rl[t] = ih[t] = il[t] = 0.f;
             for (int i = 0; i < N; ++i) {
-                const float4 g = lane < n ? pcol[(long long)i * nt] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 g = b < n ? pcol[(long long)i * nt] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const dfl gr = {g.x, g.y}, gi = {g.z, g.w};
 #pragma unroll
                 for (int t = 0; t < 8; ++t)
@@ -131,12 +133,12 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
                         dot2_fma(ih[t], il[t], f, gi);
                     }
             }
-            if (lane < n)
+            if (b < n)
 #pragma unroll
                 for (int t = 0; t < 8; ++t)
                     if (a0 + t < n) {
                         const double2 v = cmk(df_to(df_two_sum(rh[t], rl[t])), df_to(df_two_sum(ih[t], il[t])));
-                        A[(a0 + t) * n + lane] = v;
+                        A[(a0 + t) * n + b] = v;
                         bad |= !isfinite(v.x) || !isfinite(v.y);
                     }
         }
@@ -308,19 +310,20 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
         }
         __syncwarp();
         const dfl* PD = PhiD + pair * Phi_stride;
-        float4* Bd = reinterpret_cast<float4*>(Th) + lane;
-        if (lane < n)
+        for (int b = lane; b < n; b += 32) {
+            float4* Bd = reinterpret_cast<float4*>(Th) + b;
             for (int i = 0; i < N; ++i) {
                 float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
                 for (int a = 0; a < n; ++a) {
                     const dfl f = PD[(long long)i * nu + a];
-                    const float4 t = AT[a * n + lane];
+                    const float4 t = AT[a * n + b];
                     dot2_fma(rh, rl, f, dfl{t.x, t.y});
                     dot2_fma(ih, il, f, dfl{t.z, t.w});
                 }
                 const dfl re = df_two_sum(rh, rl), im = df_two_sum(ih, il);
                 Bd[(long long)i * nt] = make_float4(re.hi, re.lo, im.hi, im.lo);
             }
+        }
         return;
     }
     if (trial_side) {
@@ -362,7 +365,7 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
                        long long pairs, int P, int trial_side, double* th2, const int* list, const int* n_list,
                        const void* PhiD, const void* phiD, bool b_df) {
     int n = spin == 0 ? d.nu : d.nd;
-    if (PhiD && (d.cphi || n > 32 || !phiD)) return cudaErrorInvalidValue;
+    if (PhiD && (d.cphi || n > 64 || !phiD)) return cudaErrorInvalidValue;
     if (b_df && (!PhiD || trial_side != OVL_TRIAL)) return cudaErrorInvalidValue;
     int col0 = spin == 0 ? 0 : d.nu;
     size_t per = overlap_smem_per_warp(n, Theta != nullptr);

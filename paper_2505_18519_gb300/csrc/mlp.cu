@@ -9,16 +9,16 @@
 //   mu      = f + out[:K],  logv = clip(out[K:], -6, 3),
 // trained on the paths' states by minimising the Gaussian negative
 // log-likelihood with Adam.  Weights and activations enter the GEMMs in BF16
-// with FP32 accumulation (warp-level tensor-core MMA); master weights, Adam
+// with FP32 accumulation (tcgen05 MMAs, accumulators in tensor memory); master weights, Adam
 // moments, biases and the head stay FP32.  Parameters are one flat FP32 vector:
 // W1 (H x K), b1 (H), W2 (H x H), b2 (H), W3 (2K x H), b3 (2K), row-major.
 #include <cuda_bf16.h>
-#include <mma.h>
 
 #include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace afq {
 
@@ -28,37 +28,120 @@ constexpr float LOGV_MIN = -6.f, LOGV_MAX = 3.f;
 long long mlp_n_params(int K) { return (long long)MLP_H * K + MLP_H + MLP_H * MLP_H + MLP_H + 2LL * K * MLP_H + 2 * K; }
 
 // ---------------------------------------------------------------- GEMM (BF16 in, FP32 out)
-// C[M x N] = A[M x K] B[K x N]; A row-major (lda) or column-major, B likewise;
-// M, N, K multiples of 16; one warp per 16 x 16 tile of C.
-template <typename LA, typename LB>
-__global__ void wmma_gemm_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda,
-                                 const __nv_bfloat16* __restrict__ B, int ldb, float* __restrict__ C, int ldc) {
-    using namespace nvcuda;
-    int tn = blockIdx.x, tm = blockIdx.y;
-    wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, LA> a;
-    wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, LB> b;
-    wmma::fragment<wmma::accumulator, 16, 16, 16, float> c;
-    wmma::fill_fragment(c, 0.f);
-    for (int k = 0; k < K; k += 16) {
-        const __nv_bfloat16* pa = std::is_same<LA, wmma::row_major>::value ? A + (size_t)tm * 16 * lda + k
-                                                                            : A + (size_t)k * lda + tm * 16;
-        const __nv_bfloat16* pb = std::is_same<LB, wmma::row_major>::value ? B + (size_t)k * ldb + tn * 16
-                                                                            : B + (size_t)tn * 16 * ldb + k;
-        wmma::load_matrix_sync(a, pa, lda);
-        wmma::load_matrix_sync(b, pb, ldb);
-        wmma::mma_sync(c, a, b, c);
+// C[M x N] = A[M x K] B[K x N] on the fifth-generation tensor cores: one block of
+// 128 threads per 128 x 128 tile of C (tcgen05.mma.cta_group::1.kind::f16, BF16
+// operands, FP32 accumulator in tensor memory).  For each K chunk of 64 the block
+// copies the A tile (128 rows) and the B tile (up to 128 columns) into shared
+// memory as K-major operands in the 128-byte swizzled layout, converting the
+// stored layout on the way: A row-major (A[m][k] at A[m lda + k]) or
+// column-major (at A[k lda + m]); B column-major (B[k][n] at B[n ldb + k], the
+// transposed weights) or row-major (at B[k ldb + n]).  Thread 0 issues the
+// chunk's MMAs and commits them to an mbarrier (bounded wait); the four warps then
+// read their 32 rows of the accumulator.  M, N, K multiples of 16; rows and
+// columns past M and N are zero in the operands and not stored.
+template <bool A_RM, bool B_RM>
+__global__ void __launch_bounds__(128) mlp_gemm_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
+                                                       int lda, const __nv_bfloat16* __restrict__ B, int ldb,
+                                                       float* __restrict__ C, int ldc, int* status, uint32_t lim) {
+    __shared__ __align__(1024) uint8_t sa[128 * 128];   // 128 rows x 64 K values (bf16)
+    __shared__ __align__(1024) uint8_t sb[128 * 128];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * 128;
+    const int bn = min(128, N - n0);                      // columns of this tile, a multiple of 16
+    if (warp == 0) {
+        tc::tmem_alloc(&tslot, 128);
+        tc::tmem_relinquish();
     }
-    wmma::store_matrix_sync(C + (size_t)tm * 16 * ldc + tn * 16, c, ldc, wmma::mem_row_major);
+    if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_fence_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tslot;
+    const uint32_t idesc = tc::idesc_bf16_f32(128, bn);
+    bool failed = false;
+    int phase = 0;
+    for (int k0 = 0; k0 < K; k0 += 64) {
+        const int kc = min(64, K - k0);
+        // operand tiles: unit u = (row r, 8 consecutive k) as one 16-byte store
+        for (int u = tid; u < 128 * 8; u += 128) {
+            const int r = u >> 3, ku = (u & 7) * 8;
+            uint16_t va[8], vb[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int k = k0 + ku + t, m = m0 + r, n = n0 + r;
+                va[t] = 0;
+                vb[t] = 0;
+                if (ku + t < kc) {
+                    if (m < M) va[t] = __bfloat16_as_ushort(A_RM ? A[(size_t)m * lda + k] : A[(size_t)k * lda + m]);
+                    if (r < bn) vb[t] = __bfloat16_as_ushort(B_RM ? B[(size_t)k * ldb + n] : B[(size_t)n * ldb + k]);
+                }
+            }
+            const uint32_t off = tc::sw128_offset(128, r, ku);
+            *reinterpret_cast<uint4*>(sa + off) = make_uint4((uint32_t)va[0] | ((uint32_t)va[1] << 16),
+                                                             (uint32_t)va[2] | ((uint32_t)va[3] << 16),
+                                                             (uint32_t)va[4] | ((uint32_t)va[5] << 16),
+                                                             (uint32_t)va[6] | ((uint32_t)va[7] << 16));
+            *reinterpret_cast<uint4*>(sb + off) = make_uint4((uint32_t)vb[0] | ((uint32_t)vb[1] << 16),
+                                                             (uint32_t)vb[2] | ((uint32_t)vb[3] << 16),
+                                                             (uint32_t)vb[4] | ((uint32_t)vb[5] << 16),
+                                                             (uint32_t)vb[6] | ((uint32_t)vb[7] << 16));
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t pa = tc::smem_u32(sa), pb = tc::smem_u32(sb);
+            for (int s = 0; s < kc / 16; ++s)
+                tc::mma_f16(taddr, tc::desc_sw128(pa + 32u * s), tc::desc_sw128(pb + 32u * s), idesc,
+                            (k0 > 0 || s > 0) ? 1u : 0u);
+            tc::mma_commit(&bar);
+        }
+        // the MMAs read the tiles: wait before the next chunk overwrites them
+        const bool ok = tc::mbar_wait(&bar, (uint32_t)phase, lim);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        tc::fence_after_sync();
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(status, STATUS_TIMEOUT);
+            tc::mbar_wait(&bar, (uint32_t)(phase ^ 1), 1u << 22);   // the issued MMAs complete
+        }
+    } else {
+        // warp w reads accumulator rows 32 w .. 32 w + 31 (its tensor-memory lane quadrant)
+        const int m = m0 + 32 * warp + lane;
+        for (int c0 = 0; c0 < bn; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            tc::tmem_ld_wait();
+            if (m < M)
+#pragma unroll
+                for (int t = 0; t < 16; ++t) C[(size_t)m * ldc + n0 + c0 + t] = v[t];
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 128);
 }
 
-template <typename LA, typename LB>
-static void gemm16(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
-                   float* C, int ldc) {
-    dim3 grid((unsigned)(N / 16), (unsigned)(M / 16));
-    wmma_gemm_kernel<LA, LB><<<grid, 32, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc); count_launches(1);
+template <bool A_RM, bool B_RM>
+static void gemm16(cudaStream_t s, const Dims& d, const MlpBuffers& mb, int M, int N, int K, const __nv_bfloat16* A,
+                   int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc) {
+    dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + 127) / 128));
+    mlp_gemm_kernel<A_RM, B_RM><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, mb.status, d.wait_polls);
+    count_launches(1);
 }
-using RM = nvcuda::wmma::row_major;
-using CM = nvcuda::wmma::col_major;
+// operand layouts of gemm16: row-major (RM) or column-major (CM), for A and for B
+constexpr bool RM = true, CM = false;
 
 // ---------------------------------------------------------------- elementwise kernels
 // features f_w,k from Theta0 = phi (Phi0^T phi)^-1 and UPhi0[k] = U_k Phi0
@@ -297,11 +380,11 @@ cudaError_t mlp_forward(cudaStream_t s, const Dims& d, const MlpBuffers& m, int 
     const float* b1 = m.theta + (long long)H * d.K;
     const float* b2 = b1 + H + (long long)H * H;
     const float* b3 = b2 + H + 2LL * d.K * H;
-    gemm16<RM, CM>(s, R, H, Kp, m.featb, Kp, m.W1b, Kp, m.Zf, H);
+    gemm16<RM, CM>(s, d, m, R, H, Kp, m.featb, Kp, m.W1b, Kp, m.Zf, H);
     mlp_bias_tanh_kernel<<<grid_for((long long)R * H), 256, 0, s>>>(R, rows, H, m.Zf, b1, m.H1f, m.H1b); count_launches(1);
-    gemm16<RM, CM>(s, R, H, H, m.H1b, H, m.W2b, H, m.Zf, H);
+    gemm16<RM, CM>(s, d, m, R, H, H, m.H1b, H, m.W2b, H, m.Zf, H);
     mlp_bias_tanh_kernel<<<grid_for((long long)R * H), 256, 0, s>>>(R, rows, H, m.Zf, b2, m.H2f, m.H2b); count_launches(1);
-    gemm16<RM, CM>(s, R, 2 * Kp, H, m.H2b, H, m.W3b, H, m.outf, 2 * Kp);
+    gemm16<RM, CM>(s, d, m, R, 2 * Kp, H, m.H2b, H, m.W3b, H, m.outf, 2 * Kp);
     mlp_head_kernel<<<grid_for((long long)rows * d.K), 256, 0, s>>>(rows, d.K, Kp, m.outf, b3, m.featf, m.mu, m.logv,
                                                                    m.logv_raw); count_launches(1);
     return cudaGetLastError();
@@ -322,17 +405,17 @@ cudaError_t mlp_backward(cudaStream_t s, const Dims& d, const MlpBuffers& m, int
     }
     mlp_sum_kernel<<<1, 32, 0, s>>>(rows, m.loss_part, m.loss); count_launches(1);
     // output layer: gW3 = dout^T H2, gb3 = colsum(dout), dH2 = dout W3
-    gemm16<CM, RM>(s, 2 * Kp, H, R, m.doutb, 2 * Kp, m.H2b, H, m.gW3p, H);
+    gemm16<CM, RM>(s, d, m, 2 * Kp, H, R, m.doutb, 2 * Kp, m.H2b, H, m.gW3p, H);
     mlp_colsum_kernel<<<(2 * Kp + 255) / 256, 256, 0, s>>>(rows, 2 * Kp, 2 * Kp, m.doutf, m.gb3p); count_launches(1);
-    gemm16<RM, RM>(s, R, H, 2 * Kp, m.doutb, 2 * Kp, m.W3b, H, m.dHf, H);
+    gemm16<RM, RM>(s, d, m, R, H, 2 * Kp, m.doutb, 2 * Kp, m.W3b, H, m.dHf, H);
     mlp_tanh_back_kernel<<<grid_for((long long)R * H), 256, 0, s>>>(R, rows, H, m.dHf, m.H2f, m.dZf, m.dZb); count_launches(1);
     // second layer: gW2 = dZ2^T H1, gb2, dH1 = dZ2 W2
-    gemm16<CM, RM>(s, H, H, R, m.dZb, H, m.H1b, H, m.gW2, H);
+    gemm16<CM, RM>(s, d, m, H, H, R, m.dZb, H, m.H1b, H, m.gW2, H);
     mlp_colsum_kernel<<<1, 256, 0, s>>>(rows, H, H, m.dZf, m.gb2); count_launches(1);
-    gemm16<RM, RM>(s, R, H, H, m.dZb, H, m.W2b, H, m.dHf, H);
+    gemm16<RM, RM>(s, d, m, R, H, H, m.dZb, H, m.W2b, H, m.dHf, H);
     mlp_tanh_back_kernel<<<grid_for((long long)R * H), 256, 0, s>>>(R, rows, H, m.dHf, m.H1f, m.dZf, m.dZb); count_launches(1);
     // first layer: gW1 = dZ1^T f, gb1
-    gemm16<CM, RM>(s, H, Kp, R, m.dZb, H, m.featb, Kp, m.gW1p, Kp);
+    gemm16<CM, RM>(s, d, m, H, Kp, R, m.dZb, H, m.featb, Kp, m.gW1p, Kp);
     mlp_colsum_kernel<<<1, 256, 0, s>>>(rows, H, H, m.dZf, m.gb1); count_launches(1);
     long long n = mlp_n_params(K);
     mlp_gather_grad_kernel<<<grid_for(n), 256, 0, s>>>(K, Kp, m.gW1p, m.gb1, m.gW2, m.gb2, m.gW3p, m.gb3p, m.grad); count_launches(1);

@@ -37,11 +37,13 @@ constexpr double RHO_DF = 6.5;   // largest Gershgorin half-width run in double-
 // ||V_k||_F <= ||Phi0||_F); if they do, the problem is done again on the
 // Gershgorin interval of S, in double-float if its half-width is at most
 // RHO_DF and in FP64 otherwise.
-// One problem per call; the whole block of 256 threads takes part.
+// One problem per call; the whole block of 256 threads takes part.  s_global (with
+// s_is_df): S stays in global memory and is read from there (L2) by every term, for
+// N too large for S in shared memory; shared memory then holds the vectors only.
 __device__ __forceinline__ void cheb_df_problem(long long prob, int N, int nu, const double* __restrict__ S_all,
                                                 const double* __restrict__ Phi0, double* __restrict__ Out,
                                                 const int* __restrict__ alive, int P, int* status, int allow_df,
-                                                int s_is_df) {
+                                                int s_is_df, int s_global = 0) {
     extern __shared__ dfl smf[];
     __shared__ double coef[CHEB_DF_MAX + 2];
     __shared__ dfl coefd[CHEB_DF_MAX + 2];
@@ -52,16 +54,18 @@ __device__ __forceinline__ void cheb_df_problem(long long prob, int N, int nu, c
     __shared__ double cshift, irho;
     if (alive && !alive[prob / P]) return;
     const double* Sg = S_all + prob * (long long)N * N;
-    dfl* S = smf;
-    dfl* Vp = smf + (size_t)N * N;
+    const dfl* Sgd = reinterpret_cast<const dfl*>(Sg);
+    dfl* Ssm = smf;
+    const dfl* S = s_global ? Sgd : Ssm;
+    dfl* Vp = smf + (s_global ? (size_t)0 : (size_t)N * N);
     dfl* Vc = Vp + (size_t)N * nu;
     dfl* acc = Vc + (size_t)N * nu;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int nn = N * nu;
     // S to double-float (or as given, when the caller formed it in double-float);
     // the Gershgorin interval and the Lanczos estimate from its high parts
-    const dfl* Sgd = reinterpret_cast<const dfl*>(Sg);
-    for (int e = tid; e < N * N; e += nth) S[e] = s_is_df ? Sgd[e] : df_from(Sg[e]);
+    if (!s_global)
+        for (int e = tid; e < N * N; e += nth) Ssm[e] = s_is_df ? Sgd[e] : df_from(Sg[e]);
     __syncthreads();
     cheb_interval(N, &S[0].hi, 2, sc);
     float phi_ss = 0.f;   // ||Phi0||_F^2
@@ -95,7 +99,8 @@ __device__ __forceinline__ void cheb_df_problem(long long prob, int N, int nu, c
             double* Vp64 = reinterpret_cast<double*>(Vp);
             double* Vc64 = reinterpret_cast<double*>(Vc);
             double* acc64 = reinterpret_cast<double*>(acc);
-            for (int e = tid; e < N * N; e += nth) S64[e] = s_is_df ? df_to(Sgd[e]) : Sg[e];
+            if (!s_global)
+                for (int e = tid; e < N * N; e += nth) S64[e] = s_is_df ? df_to(Sgd[e]) : Sg[e];
             __syncthreads();
             const double c = cshift, ir = irho;
             for (int e = tid; e < nn; e += nth) {
@@ -110,7 +115,10 @@ __device__ __forceinline__ void cheb_df_problem(long long prob, int N, int nu, c
                 for (int e = tid; e < nn; e += nth) {
                     const int i = e / nu, a = e - i * nu;
                     double sum = 0.0;
-                    for (int j = 0; j < N; ++j) sum = fma(S64[(size_t)i * N + j], Vsrc[j * nu + a], sum);
+                    if (s_global)   // S as double-float pairs in global memory, rounded to FP64 per use
+                        for (int j = 0; j < N; ++j) sum = fma(df_to(Sgd[(size_t)i * N + j]), Vsrc[j * nu + a], sum);
+                    else
+                        for (int j = 0; j < N; ++j) sum = fma(S64[(size_t)i * N + j], Vsrc[j * nu + a], sum);
                     sum = (sum - c * Vsrc[e]) * ir;
                     double v;
                     if (k == 1) {
@@ -245,8 +253,8 @@ __device__ __forceinline__ void cheb_df_problem(long long prob, int N, int nu, c
 __global__ void __launch_bounds__(256) chebyshev_expm_df_kernel(int N, int nu, const double* __restrict__ S_all,
                                                                 const double* __restrict__ Phi0, double* __restrict__ Out,
                                                                 const int* __restrict__ alive, int P, int* status,
-                                                                int allow_df, int s_is_df) {
-    cheb_df_problem(blockIdx.x, N, nu, S_all, Phi0, Out, alive, P, status, allow_df, s_is_df);
+                                                                int allow_df, int s_is_df, int s_global) {
+    cheb_df_problem(blockIdx.x, N, nu, S_all, Phi0, Out, alive, P, status, allow_df, s_is_df, s_global);
 }
 
 // The problems list[0 .. *count), grid-stride (the tensor-core kernel's redo list).
@@ -268,19 +276,26 @@ bool trial_orbitals_df_supported(int N, int nu) {
     return (3 * (size_t)N * nu + (size_t)N * N) * sizeof(dfl) <= 200 * 1024 && N <= LZ_NMAX;
 }
 
+// The double-float kernel with S read from global memory (double-float S).
+bool trial_orbitals_dfg_supported(int N, int nu) {
+    return 3 * (size_t)N * nu * sizeof(dfl) <= 200 * 1024 && N <= LZ_NMAX;
+}
+
 static cudaError_t trial_orbitals_lanczos(cudaStream_t s, int N, int nu, long long problems, double* S_all,
                                           const double* Phi0, double* Out, const int* alive, int P, int* status,
                                           int threads, bool allow_df, bool s_is_df) {
     if (problems <= 0) return cudaSuccess;
-    const size_t bytes = (3 * (size_t)N * nu + (size_t)N * N) * sizeof(dfl);
-    if (!trial_orbitals_df_supported(N, nu)) {   // S does not fit in shared memory: the Gershgorin FP64 kernel
+    // S in shared memory, or (double-float S that does not fit there) read from global memory
+    const bool s_global = !trial_orbitals_df_supported(N, nu) && s_is_df && trial_orbitals_dfg_supported(N, nu);
+    const size_t bytes = (3 * (size_t)N * nu + (s_global ? (size_t)0 : (size_t)N * N)) * sizeof(dfl);
+    if (!trial_orbitals_df_supported(N, nu) && !s_global) {   // the Gershgorin FP64 kernel
         if (s_is_df) return cudaErrorInvalidValue;
         return trial_orbitals_gershgorin(s, N, nu, problems, S_all, Phi0, Out, alive, P, status, threads);
     }
     cudaError_t e = raise_smem_limit((const void*)chebyshev_expm_df_kernel, bytes);
     if (e != cudaSuccess) return e;
     chebyshev_expm_df_kernel<<<(unsigned)problems, 256, bytes, s>>>(N, nu, S_all, Phi0, Out, alive, P, status,
-                                                                   allow_df ? 1 : 0, s_is_df ? 1 : 0);
+                                                                   allow_df ? 1 : 0, s_is_df ? 1 : 0, s_global ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
 }

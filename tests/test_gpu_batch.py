@@ -152,3 +152,46 @@ def test_fresh_process_near_48k_shared_memory():
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     assert "E " in r.stdout
+
+
+def test_batched_systems_step_like_the_oracle():
+    """Every system of a batch, stepped through the one graph, against the
+    oracle's step from the same state: FP64 systems to 1e-9 (weights relative;
+    orbitals, paths and trial orbitals absolute, the same Metropolis decisions),
+    and a mixed-precision system with its refinement recomputing every pair
+    (refine_tol 1e-300), which makes its contraction double-float and its step
+    equal to the oracle's within 1e-9 as well."""
+    from oracle import afqmc as oa
+    cases = [(ai.SystemSpec(8, 4, 4, 32, 8, False, 1000), 6, 4, "fp64", {}),
+             (ai.SystemSpec(37, 7, 5, 40, 9, True, 77), 4, 3, "fp64", {}),
+             (ai.SystemSpec(70, 14, 13, 90, 10, True, 81), 3, 4, "fp16x6", {"refine_tol": 1e-300})]
+    ctxs, olds = [], []
+    for i, (spec, W, P, prec, kw) in enumerate(cases):
+        s = ai.make_system(spec)
+        seed = 90 + i
+        cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, 0.01, seed, n_burn=2,
+                              precision=prec, **kw)
+        c = lib.Context(cfg, s.h, s.L, s.Phi0, s.U, stream=torch.cuda.Stream())
+        ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, 0.01)
+        ocfg = oa.OracleConfig(dtau=0.01, n_walkers=W, n_paths=P, seed=seed, n_burn=2)
+        ost = oa.init(ham, ocfg)
+        c.load_state_arrays(dict(step=ost.step, phi_up=ost.phi_up, phi_dn=ost.phi_dn, weight=ost.weight, x=ost.x,
+                                 Phi=ost.Phi))
+        ctxs.append(c)
+        olds.append((ham, ocfg, ost))
+    b = lib.Batch(ctxs)
+    b.step(1)
+    b.sync()
+    for c, (ham, ocfg, ost) in zip(ctxs, olds):
+        ost2, _ = oa.step(ham, ocfg, ost)
+        g = c.state_arrays()
+        assert g["step"] == ost2.step
+        assert np.allclose(g["weight"], ost2.weight, rtol=1e-9, atol=0)
+        assert np.max(np.abs(g["x"] - ost2.x)) < 1e-9
+        assert np.max(np.abs(g["Phi"] - ost2.Phi)) < 1e-9
+        assert np.max(np.abs(g["phi_up"] - ost2.phi_up)) < 1e-9
+        if ost2.phi_dn.size:
+            assert np.max(np.abs(g["phi_dn"] - ost2.phi_dn)) < 1e-9
+    b.close()
+    for c in ctxs:
+        c.close()

@@ -265,15 +265,15 @@ TRIAL_SYSTEMS["n128_32"] = (ai.SystemSpec(128, 32, 32, 40, 16, True, 86), 2, 3, 
 # product; 1.9e-11 measured at N = 128 with 32 electrons, where the dot products are
 # longest and the series cancels most) and the 8-bit digit products on the tensor
 # cores (about 40 bits).
-TRIAL_TOL = {"df": 5e-11, "auto": 1e-10}
+TRIAL_TOL = {"df": 5e-11, "tc": 1e-10}
 
 
-@pytest.mark.parametrize("trial_form", ["df", "auto"])
+@pytest.mark.parametrize("trial_form", ["df", "tc"])
 @pytest.mark.parametrize("name", ["c0", "ragged", "n70_two_k_blocks", "medium", "n120_24", "n128_32"])
 def test_trial_orbitals_against_exact_exponential(name, trial_form):
     """The mixed path forms Phi(x) = exp(sum_k x_k U_k) Phi0 in double-float
     arithmetic (trial_form df) or with the Chebyshev products on the tensor
-    cores (auto): after burn-in every stored path orbital must equal the exact
+    cores (tc): after burn-in every stored path orbital must equal the exact
     exponential (the oracle's, by eigendecomposition) of its own x to the
     form's relative tolerance, and the paths' x must match the FP64 path's
     (same Metropolis decisions)."""
@@ -299,7 +299,7 @@ def test_tensor_core_trial_orbitals_redo_a_missed_interval():
     variables (x scaled by 6) widen the spectrum enough that some estimates
     fall short: every orbital must still match the exact exponential."""
     spec, W, P, dtau = TRIAL_SYSTEMS["n70_two_k_blocks"]
-    s, ctx = _ctx(spec, W, P, dtau, 93, "fp16x3", n_burn=0)
+    s, ctx = _ctx(spec, W, P, dtau, 93, "fp16x3", n_burn=0, trial_form="tc")
     x = 6.0 * ctx.state_arrays()["x"].reshape(-1, spec.K)
     n0 = lib.launch_count()
     got = ctx.trial_orbitals(x)
@@ -317,7 +317,7 @@ def test_trial_orbitals_entry_matches_both_forms(name):
     """afqmc_trial_orbitals on arbitrary rows of x: the tensor-core and the
     double-float forms agree with each other and with the exact exponential."""
     spec, W, P, dtau = TRIAL_SYSTEMS[name]
-    s, ctc = _ctx(spec, W, P, dtau, 94, "fp16x3", n_burn=0)
+    s, ctc = _ctx(spec, W, P, dtau, 94, "fp16x3", n_burn=0, trial_form="tc")
     s, cdf = _ctx(spec, W, P, dtau, 94, "fp16x3", n_burn=0, trial_form="df")
     rng = np.random.default_rng(5)
     x = rng.standard_normal((W * P, spec.K))
@@ -327,6 +327,6 @@ def test_trial_orbitals_entry_matches_both_forms(name):
     scale = np.max(np.abs(exact), axis=(-2, -1), keepdims=True)
     ea, eb = np.max(np.abs(a - exact) / scale), np.max(np.abs(b - exact) / scale)
     print(f"{name}: tensor cores {ea:.2e}, double-float {eb:.2e}")
-    assert ea < TRIAL_TOL["auto"] and eb < TRIAL_TOL["df"]
+    assert ea < TRIAL_TOL["tc"] and eb < TRIAL_TOL["df"]
     ctc.close()
     cdf.close()

@@ -166,7 +166,7 @@ def test_trial_fields_reach_the_library(L):
 
 def test_trial_form_field_reaches_the_library(L):
     """trial_form selects how the mixed path forms exp(S) Phi0; an unknown value is refused."""
-    for form in ("auto", "df"):
+    for form in ("auto", "df", "tc"):
         c = lib.make_config(50, 10, 10, 250, 50, 4, 8, 0.005, 1, precision="fp16x6", trial_form=form)
         assert lib.workspace_bytes(c) > 0
     c = lib.make_config(50, 10, 10, 250, 50, 4, 8, 0.005, 1, precision="fp16x6")
