@@ -45,10 +45,11 @@ MEDIUM = "medium_n50"            # the medium FP64 workload of the variants
 HEADLINE_PATH = dict(precision="fp16x6", tc_form="walker", refine_tol=1e-4)
 
 
-def mixed_path(N):
-    """The headline's mixed path for a system of N orbitals: three-part operands
-    where the walker-side form supports them (N <= 192), else two-part ones."""
-    return dict(HEADLINE_PATH, precision="fp16x6" if N <= 192 else "fp16x3")
+def mixed_path(lib, spec, W, P):
+    """The headline's mixed path for a system: three-part operands where the
+    walker-side form's shared memory holds them, else two-part ones."""
+    c = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, 0.005, 1, **HEADLINE_PATH)
+    return dict(HEADLINE_PATH, precision="fp16x6" if lib.workspace_bytes(c) > 0 else "fp16x3")
 METRIC = "walker-sample steps/s incl. local energy"
 UNIT = "walker-sample steps/s"
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 4 FP64 flop/clk
@@ -541,7 +542,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
         for i, sp in enumerate(specs):
             sy = ai.make_system(sp)
             c = lib.make_config(sp.N, sp.n_up, sp.n_dn, sp.n_chol, sp.K, Wb, Pb, 0.005, ai.philox_run_seed(10 + i),
-                                n_burn=20, walker_offset=rank * Wb, **mixed_path(sp.N))
+                                n_burn=20, walker_offset=rank * Wb, **mixed_path(lib, sp, Wb, Pb))
             ctx = lib.Context(c, sy.h, sy.L, sy.Phi0, sy.U, device=dev, stream=torch.cuda.Stream(dev))
             ctx.autotune()
             ctxs.append(ctx)
@@ -556,7 +557,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             c.close()
         units = len(specs) * Wb * Pb * world
         out["batched_uneven"] = {
-            "precision": "fp16x6 (N <= 192), fp16x3 (N > 192)", "what": f"{len(specs)} synthetic molecules, N ~ U[40,200] (N = "
+            "precision": ",".join(sorted({mixed_path(lib, sp, Wb, Pb)["precision"] for sp in specs})), "what": f"{len(specs)} synthetic molecules, N ~ U[40,200] (N = "
             f"{','.join(str(sp.N) for sp in specs)}), n = N/5 per spin, n_chol = 5N, K = N, {Wb} walkers x {Pb} "
             "paths each, autotuned launch shapes, one CUDA-graph launch per step for the whole batch",
             "value": units * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
@@ -703,7 +704,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             W4, P4 = 512, run4.n_paths
             c = lib.make_config(spec4.N, spec4.n_up, spec4.n_dn, spec4.n_chol, spec4.K, W4, P4, run4.dtau,
                                 ai.philox_run_seed(4), n_burn=40, walker_offset=rank * W4, proposal="mlp",
-                                mlp_train=True, **mixed_path(spec4.N))
+                                mlp_train=True, **mixed_path(lib, spec4, W4, P4))
             ctx = lib.Context(c, sy.h, sy.L, sy.Phi0, sy.U, device=dev)
             ctx.step(2)
             ctx.profile(True)
@@ -718,7 +719,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             ph = {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}
             flops = contract_flops_per_pair(spec4) * W4 * P4
             out["largest_mixed_learned"] = {
-                "precision": mixed_path(spec4.N)["precision"], "proposal": "mlp (trained online)",
+                "precision": mixed_path(lib, spec4, W4, P4)["precision"], "proposal": "mlp (trained online)",
                 "kernel": lib.contract_kernel(c),
                 "what": workload_desc(spec4, run4, "largest_n200") + f"; {W4} of its {run4.n_walkers} walkers, 40 "
                         "burn-in sweeps, 2 untimed and 2 timed steps",

@@ -98,8 +98,9 @@ enum {
                                    split into the integer FP16 part and two FP16 remainders (about 31 bits),
                                    six products per real product (every one above about 2^-28 of the
                                    integer*integer term), the entries reaching the traces as FP32 numbers (about
-                                   24 bits).  N <= 192 (the GEMM-Y block keeps three parts of the walker's
-                                   orbitals in shared memory) */
+                                   24 bits).  The GEMM-Y block keeps three parts of the walker's orbitals
+                                   (2 n_up rows rounded up to 8, per K chunk of 64) in shared memory: e.g.
+                                   N <= 256 with n_up <= 40, N <= 192 with n_up = 64 */
 };
 
 typedef struct {

@@ -70,6 +70,12 @@ __host__ __device__ constexpr uint32_t tcw_chunk(int mode) { return (uint32_t)tc
 
 __host__ __device__ __forceinline__ int tcw_round16(int x) { return (x + 15) / 16 * 16; }
 
+// Bytes of one part of a K chunk of the GEMM-Y operand PW: its 2n rows rounded up to
+// 8 (whole 1024-byte swizzle groups), at most 128 rows.
+__host__ __device__ constexpr uint32_t tcw_pw_part(int n) {
+    return (uint32_t)((2 * n + 7) / 8 * 8 < 128 ? (2 * n + 7) / 8 * 8 : 128) * 128u;
+}
+
 // Byte offset of the 16-byte unit u (K elements 8u .. 8u + 7) of row r in a
 // K-major 128-byte swizzled region (rows of 128 bytes, groups of 8 rows 1 KB apart).
 __host__ __device__ __forceinline__ uint32_t swz16(int r, int u) {
@@ -191,9 +197,12 @@ __global__ void tcw_x_image_kernel(int N, int N16, int KCX, int G1, const double
 
 // ---------------------------------------------------------------- GEMM-Y and the Bop image of Y_g
 // Block: walker w0 + blockIdx.x / n_gblk, matrices [gb GPB, (gb + 1) GPB) of one spin
-// (columns col0 .. col0 + n - 1 of phi).  Shared memory: PW (KCX chunks of 128
-// rows: row (b, ri) = Re/Im phi[:, col0 + b] times 2^sPW[b], K = i, NP parts each),
-// then a ring of S stages, each one part of a K chunk of X_g (N16 rows).
+// (columns col0 .. col0 + n - 1 of phi).  Shared memory: PW (KCX chunks of NP parts,
+// each part the 2n rows (b, ri) = Re/Im phi[:, col0 + b] times 2^sPW[b], K = i, rounded
+// up to 8 rows: the MMAs read 128 rows from a part's start, and the rows past 2n,
+// whatever they hold, give rows of D_Y that the epilogue never reads; a tail pads the
+// last part's 128 rows), then a ring of S stages, each one part of a K chunk of X_g
+// (N16 rows).
 // Tensor memory: D_Y (N16 columns) and, FP16, its correction (N16 more).
 // Output: the Bop rows (g, b, ri) of matrix g in N-tile t = g / GB at row
 // (g % GB) 2n + 2b + ri; K chunk c of a tile is NT rows of each part in turn; and
@@ -210,8 +219,9 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const uint32_t RX = (uint32_t)N16 * 128u;
-    uint8_t* PW = sm;                                         // KCX x CH
-    uint8_t* ring = PW + (size_t)KCX * CH;                    // S x RX
+    const uint32_t PS = tcw_pw_part(n), CS = PS * (uint32_t)NP;   // one part, one chunk of PW
+    uint8_t* PW = sm;                                         // KCX x CS, then the tail
+    uint8_t* ring = PW + (size_t)KCX * CS + (TCW_PART - PS);  // S x RX
     __shared__ uint64_t full_bar[TCW_MAXSTAGES], empty_bar[TCW_MAXSTAGES], dfull, dempty, drain_bar;
     __shared__ uint32_t tslot;
     __shared__ volatile int fail;
@@ -254,9 +264,10 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
         if (lane == 0) sPW[b] = F16 ? exp_into(m, 7) : 0;
     }
     __syncthreads();
-    // PW rows (b, ri), K = i, 16-byte units; rows >= 2n are zero
-    for (int e = tid; e < KCX * 128 * 8; e += TCW_THREADS) {
-        const int u = e % 8, r = (e / 8) % 128, c = e / (8 * 128);
+    // PW rows (b, ri), K = i, 16-byte units; rows from 2n to the part's end are zero
+    const int rows_pw = (int)(PS / 128u);
+    for (int e = tid; e < KCX * rows_pw * 8; e += TCW_THREADS) {
+        const int u = e % 8, r = (e / 8) % rows_pw, c = e / (8 * rows_pw);
         const int b = r >> 1, ri = r & 1;
         uint16_t pt[NP][8];
 #pragma unroll
@@ -272,9 +283,9 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
 #pragma unroll
             for (int p = 0; p < NP; ++p) pt[p][q] = o[p];
         }
-        uint8_t* base = PW + (size_t)c * CH + swz16(r, u);
+        uint8_t* base = PW + (size_t)c * CS + swz16(r, u);
 #pragma unroll
-        for (int p = 0; p < NP; ++p) *reinterpret_cast<uint4*>(base + p * TCW_PART) = pack8(pt[p]);
+        for (int p = 0; p < NP; ++p) *reinterpret_cast<uint4*>(base + p * PS) = pack8(pt[p]);
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -316,14 +327,14 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
                         const int st = v % S;
                         if (!wait_or_fail(&full_bar[st], (uint32_t)((v / S) & 1), lim, &fail)) { failed = true; break; }
                         tc::fence_after_sync();
-                        const uint32_t pa = tc::smem_u32(PW + (size_t)c * CH);
+                        const uint32_t pa = tc::smem_u32(PW + (size_t)c * CS);
                         const uint32_t pb = tc::smem_u32(ring + (size_t)st * RX);
                         for (int s = 0; s < ks; ++s) {
-                            const uint64_t a0 = tc::desc_sw128(pa + s * 32), a1 = tc::desc_sw128(pa + TCW_PART + s * 32);
+                            const uint64_t a0 = tc::desc_sw128(pa + s * 32), a1 = tc::desc_sw128(pa + PS + s * 32);
                             const uint64_t bx = tc::desc_sw128(pb + s * 32);
                             const uint32_t first = (c == 0 && s == 0) ? 0u : 1u;
                             if constexpr (MODE == 2) {
-                                const uint64_t a2 = tc::desc_sw128(pa + 2 * TCW_PART + s * 32);
+                                const uint64_t a2 = tc::desc_sw128(pa + 2 * PS + s * 32);
                                 if (hh == 0) {                 // X hi: hi*hi, mid*hi, lo*hi
                                     tc::mma_f16(dh, a0, bx, idesc, first);
                                     tc::mma_f16(dl, a1, bx, idesc, first);
@@ -923,11 +934,12 @@ bool tcw_shape(int N, int nu, int nd, int G, long long W, int P, int mode, TcwSh
     if (nd == 0) s.sp[1] = s.sp[0], s.sp[1].n = 0;
     // GEMM-Y: PW (KCX chunks) and a ring of at least two chunk parts of N16 rows
     const size_t RX = (size_t)s.N16 * 128;
+    const size_t PWB = (size_t)s.KCX * NP * tcw_pw_part(nu) + (TCW_PART - tcw_pw_part(nu));   // PW and its tail
     s.SY = 0;
     for (int S = TCW_MAXSTAGES; S >= 2; --S)
-        if (1024 + (size_t)s.KCX * CH + S * RX <= TCW_SMEM_MAX) { s.SY = S; break; }
+        if (1024 + PWB + S * RX <= TCW_SMEM_MAX) { s.SY = S; break; }
     if (!s.SY) return false;
-    s.smem_y = 1024 + (size_t)s.KCX * CH + s.SY * RX;
+    s.smem_y = 1024 + PWB + s.SY * RX;
     if ((f16 ? 2 : 1) * s.N16 > 512) return false;
     s.GPB = 64;
     // Y images: per walker and spin NTILES x KC chunks of NT x 128 bytes per part

@@ -97,7 +97,8 @@ def test_general_walker_side_form_bf16(name):
     assert np.max(np.abs(obs["force_bias"] - m["v_bar"])[live]) < 1e-4
 
 
-FP16X6_SYSTEMS = [n for n in SYSTEMS if SYSTEMS[n][0].N <= 192 and n != "one_spin_n150"]
+# every system here fits the three-part GEMM-Y operand (2 n_up rows per K chunk and part)
+FP16X6_SYSTEMS = list(SYSTEMS)
 
 
 @pytest.mark.parametrize("name", FP16X6_SYSTEMS)
@@ -184,8 +185,6 @@ def test_large_systems_against_fp64_gpu_path(config, W):
     P = run.n_paths
     res, refined, state = {}, {}, None
     for prec, tol in (("fp64", 1e-4), ("fp16x3", 1e-4), ("fp16x3", 0.0), ("fp16x6", 1e-4)):
-        if prec == "fp16x6" and spec.N > 192:
-            continue
         kw = dict(tc_form="walker", wait_polls=1 << 24) if prec != "fp64" else {}
         cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, run.dtau,
                               ai.philox_run_seed(4), n_burn=20, precision=prec, refine_tol=tol, **kw)
