@@ -97,8 +97,9 @@ def test_general_walker_side_form_bf16(name):
     assert np.max(np.abs(obs["force_bias"] - m["v_bar"])[live]) < 1e-4
 
 
-# every system here fits the three-part GEMM-Y operand (2 n_up rows per K chunk and part)
-FP16X6_SYSTEMS = list(SYSTEMS)
+# the systems whose three-part operands fit the walker-side form's shared memory (45
+# electrons in one spin do not: GEMM-Z's ring and transpose exceed it)
+FP16X6_SYSTEMS = [n for n in SYSTEMS if n != "one_spin_n150"]
 
 
 @pytest.mark.parametrize("name", FP16X6_SYSTEMS)
