@@ -99,8 +99,9 @@ enum {
                                    six products per real product (every one above about 2^-28 of the
                                    integer*integer term), the entries reaching the traces as FP32 numbers (about
                                    24 bits).  The GEMM-Y block keeps three parts of the walker's orbitals
-                                   (2 n_up rows rounded up to 8, per K chunk of 64) in shared memory: e.g.
-                                   N <= 256 with n_up <= 40, N <= 192 with n_up = 64 */
+                                   (2 n_up rows rounded up to 8, per K chunk of 64) in shared memory, and
+                                   the GEMM-Z block three parts of a walker tile: N <= 256 with
+                                   n_up <= 40 */
 };
 
 typedef struct {
@@ -426,7 +427,12 @@ afqmc_status afqmc_mlp_state(afqmc_ctx* ctx, float* features, float* mu, float* 
 /* Several systems (contexts of any sizes and precisions) stepped together: one
  * leapfrog step of every context is captured once into one CUDA graph (a fork
  * on `stream`, each context's kernels as a branch on its own stream, a join),
- * and each afqmc_batch_step launches that graph once per step.  Every context
+ * and each afqmc_batch_step launches that graph once per step.  The contexts that
+ * use the walker-side tensor-core contraction with one operand arithmetic (the
+ * first such context's; their Y images in one chunk of walkers) share its dominant
+ * kernel: their branches stop after the contraction's images, one persistent
+ * launch on `stream` runs every such system's GEMM-Z blocks from one list, and
+ * their branches resume (the results are the same bit for bit).  Every context
  * needs its own non-default stream, distinct from `stream`; the contexts stay
  * usable one by one (afqmc_energy, save/load, ...) between batch steps after
  * afqmc_batch_sync.  The batch does not own the contexts. */
@@ -434,6 +440,8 @@ typedef struct afqmc_batch afqmc_batch;
 afqmc_status afqmc_batch_create(int n_systems, afqmc_ctx* const* ctxs, void* stream, afqmc_batch** out);
 afqmc_status afqmc_batch_step(afqmc_batch* batch, int n_steps);  /* asynchronous on `stream` */
 afqmc_status afqmc_batch_sync(afqmc_batch* batch);
+/* How many of the batch's systems share the one GEMM-Z launch (-1 for NULL). */
+int afqmc_batch_shared_contractions(const afqmc_batch* batch);
 void afqmc_batch_destroy(afqmc_batch* batch);
 
 /* The library's Philox4x32-10 (Salmon et al., SC'11) on the device, for

@@ -53,7 +53,7 @@ EXPORTS = ("afqmc_config_default", "afqmc_workspace_bytes", "afqmc_init", "afqmc
            "afqmc_launch_count", "afqmc_contract_kernel", "afqmc_autotune", "afqmc_batch_create", "afqmc_batch_step", "afqmc_batch_sync",
            "afqmc_batch_destroy", "afqmc_mlp_n_params", "afqmc_mlp_params", "afqmc_mlp_eval", "afqmc_mlp_state",
            "afqmc_fp64_fma_rate", "afqmc_local_energy_noalloc", "afqmc_noalloc_scratch_bytes",
-           "afqmc_noalloc_last_error", "afqmc_trial_orbitals")
+           "afqmc_noalloc_last_error", "afqmc_trial_orbitals", "afqmc_batch_shared_contractions")
 
 PHASES = ("overlap", "contract", "average", "fields", "propagate", "ratio", "propose", "trial_orbitals",
           "mcmc_overlap", "accept", "finish", "comb", "refine")
@@ -118,6 +118,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.afqmc_batch_step.restype = I
     lib.afqmc_batch_sync.argtypes = [P]
     lib.afqmc_batch_sync.restype = I
+    lib.afqmc_batch_shared_contractions.argtypes = [P]
+    lib.afqmc_batch_shared_contractions.restype = I
     lib.afqmc_batch_destroy.argtypes = [P]
     lib.afqmc_batch_destroy.restype = None
     lib.afqmc_mlp_n_params.argtypes = [I]
@@ -388,6 +390,11 @@ class Batch:
 
     def sync(self):
         _check(load_library().afqmc_batch_sync(self._b))
+
+    @property
+    def shared_contractions(self) -> int:
+        """Systems whose GEMM-Z runs in the batch's one persistent launch."""
+        return int(load_library().afqmc_batch_shared_contractions(self._b))
 
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:

@@ -556,7 +556,11 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
 
 // Local energies, force-bias values and path signs at the current walkers,
 // and the mixed-estimator sums into ws.reduce[0..2].
-static afqmc_status measure(afqmc_ctx* ctx) {
+// part 0: the whole measurement.  For a batch that runs the walker-side
+// contraction's GEMM-Z of all its systems in one launch: part 1 stops after the
+// contraction's images, part 2 starts with its per-pair finish (the batch runs
+// GEMM-Z in between; the context's Y images then fit one chunk of walkers).
+static afqmc_status measure(afqmc_ctx* ctx, int part = 0) {
     const Dims& d = ctx->d;
     Workspace& w = ctx->ws;
     cudaStream_t s = ctx->stream;
@@ -566,6 +570,9 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     const int tck = fp64 ? -1 : tc_kind(&ctx->cfg);
     const int ovl = fp64 ? (!w.rc && !d.cphi && contract_fp64_walker_side(d.N, d.nu, d.nd, d.P) ? OVL_INVERSE : OVL_THETA)
                          : (tck == 2 || tck == 5 ? OVL_TRIAL : OVL_THETA);
+    if (part == 2) {
+        CK(contract_tcw_finish(s, d, w.tcw, w.vpair, w.epair, tc_mode(&ctx->cfg)));
+    } else {
     if (w.Phidf) {
         CK(df_copy(s, w.Phi, d.pairs * phi_stride(d), w.Phidf));
         CK(df_copy(s, w.phi, d.W * (long long)d.N * d.nt * 2, w.phidf));
@@ -574,6 +581,11 @@ static afqmc_status measure(afqmc_ctx* ctx) {
                        ovl, tck == 5 && w.refine_items ? w.refine_th2 : nullptr, w.Phidf, w.phidf,
                        w.Phidf && ovl == OVL_TRIAL));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
+    if (part == 1) {
+        if (tck != 5) return fail(AFQMC_ERR_ARG, "a split measurement needs the walker-side contraction");
+        CK(contract_tcw_images(s, d, w.tcw, w.Theta, w.phi, w.status, tc_mode(&ctx->cfg), w.Phidf != nullptr));
+        return AFQMC_OK;
+    }
     if (ctx->cfg.precision != AFQMC_PRECISION_FP64) {
         if (tck == 5)
             CK(contract_tcw(s, d, w.tcw, w.Theta, w.phi, w.vpair, w.epair, w.status, tc_mode(&ctx->cfg),
@@ -588,6 +600,7 @@ static afqmc_status measure(afqmc_ctx* ctx) {
     else
         CK(d.cphi ? contract_fp64c(s, d, w.h, w.L, reinterpret_cast<const double2*>(w.Phi), w.Theta, w.vpair, w.epair)
                   : contract_fp64(s, d, w.h, w.L, w.Phi, w.Theta, w.vpair, w.epair, d.pairs));
+    }
     if ((st = prof_mark(ctx, PH_CONTRACT)) != AFQMC_OK) return st;
     if (w.refine_items && tck == 5) {
         // the pairs whose error would put their walker above refine_tol, again: selected
@@ -743,17 +756,30 @@ extern "C" afqmc_status afqmc_init_trial(const afqmc_config* cfg, const double* 
     return AFQMC_OK;
 }
 
+static afqmc_status step_rest(afqmc_ctx* ctx);
+
 extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
     if (!ctx) return fail(AFQMC_ERR_ARG, "ctx is NULL");
     if (n_steps < 0) return fail(AFQMC_ERR_ARG, "n_steps must be >= 0");
-    const Dims& d = ctx->d;
-    Workspace& w = ctx->ws;
-    cudaStream_t s = ctx->stream;
-    StepParams p = params_of(&ctx->cfg);
     for (int it = 0; it < n_steps; ++it) {
         afqmc_status st = prof_mark(ctx, -1);
         if (st != AFQMC_OK) return st;
         if ((st = measure(ctx)) != AFQMC_OK) return st;      // Eq. (25)-(27), (16) at phi
+        if ((st = step_rest(ctx)) != AFQMC_OK) return st;
+    }
+    ctx->measured = false;
+    return AFQMC_OK;
+}
+
+// A step after its measurement: fields, propagation, ratios, Metropolis sweeps,
+// hand-off, re-orthonormalisation, population control.
+static afqmc_status step_rest(afqmc_ctx* ctx) {
+    const Dims& d = ctx->d;
+    Workspace& w = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    StepParams p = params_of(&ctx->cfg);
+    afqmc_status st;
+    {
         CK(fields(s, d, p, w.counters, w.vbar, w.sumS, w.weight, w.alive, (double*)w.y, w.logshift));
         if (w.expTdf) {   // mixed precision: field planes and propagation in double-float
             CK(gemm_df(s, 2 * d.W, d.N * d.N, d.G, (const double*)w.y, w.Ldf, w.Aplanes, w.xdf));
@@ -794,6 +820,16 @@ extern "C" afqmc_status afqmc_step(afqmc_ctx* ctx, int n_steps) {
         if (ctx->profiling) ctx->prof_steps++;
         ctx->steps_taken++;
     }
+    return AFQMC_OK;
+}
+
+// One step of a batch whose walker-side GEMM-Z runs outside (part 1: up to the
+// contraction's images; part 2: from its finish to the end of the step).
+afqmc_status afq::batch_step_part(afqmc_ctx* ctx, int part) {
+    if (part == 1) return measure(ctx, 1);
+    afqmc_status st = measure(ctx, 2);
+    if (st != AFQMC_OK) return st;
+    if ((st = step_rest(ctx)) != AFQMC_OK) return st;
     ctx->measured = false;
     return AFQMC_OK;
 }

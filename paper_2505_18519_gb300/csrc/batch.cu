@@ -4,7 +4,12 @@
 // workspace.  One leapfrog step of every system is captured once into a single
 // CUDA graph: a fork on the batch's stream, each system's kernels as a branch on
 // its own stream, a join.  Every batch step is then one cudaGraphLaunch; the
-// device-side step counters advance inside the graph.
+// device-side step counters advance inside the graph.  The dominant work, the
+// walker-side tensor-core contraction's GEMM-Z, runs for all systems that use it
+// (one operand arithmetic, Y images in one chunk of walkers) in one persistent
+// launch on the batch's stream: each branch runs up to the contraction's images,
+// the branches join, contract_tcw_multi_kernel takes every system's blocks from one
+// list, and the branches fork again for the rest of the step.
 //
 // The autotuner times the candidate launch shapes of the heaviest kernels on a
 // context's own data (warps per block of the overlap kernel, pairs per block of
@@ -25,10 +30,19 @@ struct afqmc_batch {
     cudaStream_t root;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
-    cudaEvent_t fork;
-    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork, zdone;
+    std::vector<cudaEvent_t> joins, pre;
     long long kernels_per_step;   // kernel nodes in the graph
+    int shared_z;                 // systems whose GEMM-Z runs in the batch's one persistent launch
 };
+
+// Operand arithmetic of the walker-side contraction (0 bf16x3, 1 fp16x3, 2 fp16x6),
+// or -1 when the context does not use that form with one chunk of walkers.
+static int shared_z_mode(const afqmc_ctx* c) {
+    if (c->cfg.precision == AFQMC_PRECISION_FP64 || tc_kind(&c->cfg) != 5) return -1;
+    const int mode = c->cfg.precision == AFQMC_PRECISION_FP16X6 ? 2 : (c->cfg.precision == AFQMC_PRECISION_FP16X3 ? 1 : 0);
+    return contract_tcw_single_chunk(c->d, mode) ? mode : -1;
+}
 
 #define BK(call)                                                                                            \
     do {                                                                                                    \
@@ -153,21 +167,67 @@ extern "C" afqmc_status afqmc_batch_create(int n, afqmc_ctx* const* ctxs, void* 
     b->root = root;
     b->graph = nullptr;
     b->exec = nullptr;
-    b->joins.resize(n);
+    b->fork = b->zdone = nullptr;
+    b->joins.assign(n, nullptr);
+    b->pre.assign(n, nullptr);
+    // the systems whose GEMM-Z shares one launch: those of the first such system's arithmetic
+    int zmode = -1;
+    std::vector<char> shared(n, 0);
+    TcwZMulti zm;
+    zm.n = 0;
+    zm.first[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        const int md = shared_z_mode(ctxs[i]);
+        if (md < 0 || (zmode >= 0 && md != zmode) || zm.n + 2 > TCWZ_MAXWORK) continue;
+        TcwZArgs a[2];
+        bool ok = true;
+        for (int q = 0; q < 2 && ok; ++q) ok = contract_tcw_zargs(ctxs[i]->d, ctxs[i]->ws.tcw, ctxs[i]->ws.status, md, q, &a[q]);
+        if (!ok) continue;
+        zmode = md;
+        shared[i] = 1;
+        for (int q = 0; q < 2; ++q) {
+            if (a[q].n == 0) continue;
+            zm.a[zm.n] = a[q];
+            zm.first[zm.n + 1] = zm.first[zm.n] + a[q].blocks;
+            ++zm.n;
+        }
+    }
+    b->shared_z = 0;
+    for (int i = 0; i < n; ++i) b->shared_z += shared[i];
     afqmc_status st = AFQMC_OK;
     cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->zdone, cudaEventDisableTiming);
     for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->pre[i], cudaEventDisableTiming);
     // the contexts' earlier work must be done before the capture
     for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamSynchronize(ctxs[i]->stream);
     const long long launches_before = afqmc_launch_count();
     if (e == cudaSuccess) e = cudaStreamBeginCapture(root, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
         cudaError_t e2 = cudaEventRecord(b->fork, root);
+        if (b->shared_z > 0) {
+            // the sharing systems up to their images; then GEMM-Z of all of them in one
+            // launch; then their steps' remainder and the other systems' whole steps
+            for (int i = 0; i < n && e2 == cudaSuccess && st == AFQMC_OK; ++i) {
+                if (!shared[i]) continue;
+                e2 = cudaStreamWaitEvent(ctxs[i]->stream, b->fork, 0);
+                if (e2 == cudaSuccess) st = batch_step_part(ctxs[i], 1);
+                if (e2 == cudaSuccess && st == AFQMC_OK) e2 = cudaEventRecord(b->pre[i], ctxs[i]->stream);
+                if (e2 == cudaSuccess && st == AFQMC_OK) e2 = cudaStreamWaitEvent(root, b->pre[i], 0);
+            }
+            if (e2 == cudaSuccess && st == AFQMC_OK) e2 = contract_tcw_multi(root, zm, zmode, ctxs[0]->d.wait_polls);
+            if (e2 == cudaSuccess && st == AFQMC_OK) e2 = cudaEventRecord(b->zdone, root);
+        }
         for (int i = 0; i < n && e2 == cudaSuccess && st == AFQMC_OK; ++i) {
-            e2 = cudaStreamWaitEvent(ctxs[i]->stream, b->fork, 0);
+            e2 = cudaStreamWaitEvent(ctxs[i]->stream, shared[i] ? b->zdone : b->fork, 0);
             if (e2 == cudaSuccess) {
-                st = afqmc_step(ctxs[i], 1);
-                ctxs[i]->steps_taken -= 1;   // captured, not run
+                if (shared[i]) {
+                    st = batch_step_part(ctxs[i], 2);
+                    ctxs[i]->steps_taken -= 1;   // captured, not run
+                } else {
+                    st = afqmc_step(ctxs[i], 1);
+                    ctxs[i]->steps_taken -= 1;   // captured, not run
+                }
             }
             if (e2 == cudaSuccess && st == AFQMC_OK) e2 = cudaEventRecord(b->joins[i], ctxs[i]->stream);
             if (e2 == cudaSuccess && st == AFQMC_OK) e2 = cudaStreamWaitEvent(root, b->joins[i], 0);
@@ -202,6 +262,8 @@ extern "C" afqmc_status afqmc_batch_step(afqmc_batch* b, int n_steps) {
     return AFQMC_OK;
 }
 
+extern "C" int afqmc_batch_shared_contractions(const afqmc_batch* b) { return b ? b->shared_z : -1; }
+
 extern "C" afqmc_status afqmc_batch_sync(afqmc_batch* b) {
     if (!b) return set_error(AFQMC_ERR_ARG, "bad arguments");
     BK(cudaStreamSynchronize(b->root));
@@ -214,7 +276,10 @@ extern "C" void afqmc_batch_destroy(afqmc_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->zdone) cudaEventDestroy(b->zdone);
     for (cudaEvent_t e : b->joins)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->pre)
         if (e) cudaEventDestroy(e);
     delete b;
 }

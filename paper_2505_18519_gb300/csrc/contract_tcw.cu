@@ -539,16 +539,43 @@ __global__ void __launch_bounds__(256) tcw_a_kernel(int N, int nt, int col0, int
 // Tensor memory, buffer b of two: D (NT columns) and, FP16, its correction (NT).
 // Outputs: vpart[pair G1 + g] = Tr Z_{p,g} (float2; g = 0 is the one-body term),
 // exsum[pair] = sum_{g >= 1} Tr Z_{p,g}^2 (FP64 accumulation over the matrices).
+// Tensor-memory columns a GEMM-Z block of NT columns uses (two buffers; FP16: a
+// correction accumulator each), as a power of two of at least 32.
+__host__ __device__ constexpr uint32_t tcw_z_talloc(int NT, bool f16) {
+    return 2u * (f16 ? 2u : 1u) * (uint32_t)NT <= 32 ? 32u
+         : (2u * (f16 ? 2u : 1u) * (uint32_t)NT <= 64 ? 64u
+         : (2u * (f16 ? 2u : 1u) * (uint32_t)NT <= 128 ? 128u
+         : (2u * (f16 ? 2u : 1u) * (uint32_t)NT <= 256 ? 256u : 512u)));
+}
+
+// The block's static shared state of GEMM-Z.
+struct TcwZShared {
+    uint64_t full_bar[TCW_MAXSTAGES], empty_bar[TCW_MAXSTAGES], dfull[2], dempty[2], a_bar, drain_bar;
+    int fail;
+    float2 red_tr[2][2][128], red_ex[2][2][128];   // [matrix parity][column half][row]
+    double2 exacc[128];
+    int sA[128];
+    __align__(16) float scl[128];                   // 2^-yexp of the tile's columns
+};
+
+// One block of GEMM-Z work: block `bid` of the launch described by A (tensor memory
+// at taddr, allocated by the caller; `reuse`: the block's mbarriers served an
+// earlier piece of work of the same block and are invalidated first).
 template <int MODE>
-__global__ void __launch_bounds__(TCWZ_THREADS, 1)
-    contract_tcw_kernel(int n, int G1, int KZ, int KC, int NT, int GB, int NTILES, int P, int PB, int MT, int S,
-                        int a_res, long long w0, const uint8_t* __restrict__ Aimg, const int* __restrict__ aexp,
-                        const uint8_t* __restrict__ Yimg, const int* __restrict__ yexp, float2* __restrict__ vpart,
-                        double2* __restrict__ exsum, int* status, uint32_t lim) {
+__device__ __forceinline__ void tcw_z_block(const TcwZArgs& A, long long bid, uint8_t* sm, TcwZShared& sh,
+                                            uint32_t taddr, uint32_t lim, bool reuse) {
+    const int n = A.n, G1 = A.G1, KZ = A.KZ, KC = A.KC, NT = A.NT, GB = A.GB, NTILES = A.NTILES, P = A.P, PB = A.PB,
+              MT = A.MT, S = A.S, a_res = A.a_res;
+    const long long w0 = A.w0;
+    const uint8_t* __restrict__ Aimg = A.Aimg;
+    const int* __restrict__ aexp = A.aexp;
+    const uint8_t* __restrict__ Yimg = A.Yimg;
+    const int* __restrict__ yexp = A.yexp;
+    float2* __restrict__ vpart = A.vpart;
+    double2* __restrict__ exsum = A.exsum;
+    int* status = A.status;
     constexpr bool F16 = MODE != 0;
     constexpr uint32_t CH = tcw_chunk(MODE);
-    extern __shared__ uint8_t smraw[];
-    uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const uint32_t bpart = (uint32_t)NT * 128u;                       // one part of a Bop chunk
     const uint32_t bbytes = bpart * (uint32_t)tcw_parts(MODE);       // one Bop chunk, all parts
     const uint32_t stage_bytes = (a_res ? 0u : CH) + bbytes;
@@ -556,32 +583,43 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
     uint8_t* ring = sm + (a_res ? (size_t)KC * CH : 0);
     float2* Ms = reinterpret_cast<float2*>(ring + (size_t)S * stage_bytes);
     const int ld = n + 1;                                             // row stride of Ms (complex)
-    __shared__ uint64_t full_bar[TCW_MAXSTAGES], empty_bar[TCW_MAXSTAGES], dfull[2], dempty[2], a_bar, drain_bar;
-    __shared__ uint32_t tslot;
-    __shared__ volatile int fail;
-    __shared__ float2 red_tr[2][2][128], red_ex[2][2][128];   // [matrix parity][column half][row]
-    __shared__ double2 exacc[128];
-    __shared__ int sA[128];
-    __shared__ __align__(16) float scl[128];                   // 2^-yexp of the tile's columns
+    uint64_t* full_bar = sh.full_bar;
+    uint64_t* empty_bar = sh.empty_bar;
+    uint64_t* dfull = sh.dfull;
+    uint64_t* dempty = sh.dempty;
+    uint64_t& a_bar = sh.a_bar;
+    uint64_t& drain_bar = sh.drain_bar;
+    volatile int& fail = sh.fail;
+    auto& red_tr = sh.red_tr;
+    auto& red_ex = sh.red_ex;
+    double2* exacc = sh.exacc;
+    int* sA = sh.sA;
+    float* scl = sh.scl;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long wl = blockIdx.x / MT;
-    const int m = blockIdx.x % MT;
+    const long long wl = bid / MT;
+    const int m = (int)(bid % MT);
     const int np = min(PB, P - m * PB);
     const long long pair0 = (w0 + wl) * P + (long long)m * PB;
-    const uint8_t* Atile = Aimg + (size_t)blockIdx.x * KC * CH;
+    const uint8_t* Atile = Aimg + (size_t)bid * KC * CH;
     const uint8_t* Ywalk = Yimg + (size_t)wl * NTILES * KC * bbytes;
     const int* yex = yexp + (size_t)wl * G1 * n;
     const uint32_t dcols = (F16 ? 2u : 1u) * (uint32_t)NT;              // one buffer
-    const uint32_t tneed = 2u * dcols;
-    const uint32_t talloc = tneed <= 32 ? 32 : (tneed <= 64 ? 64 : (tneed <= 128 ? 128 : (tneed <= 256 ? 256 : 512)));
     const int n_units = NTILES * KC;
 
-    if (warp == 1) {
-        tc::tmem_alloc(&tslot, talloc);
-        tc::tmem_relinquish();
-    }
     if (tid == 0) {
+        if (reuse) {   // the previous piece of work has completed every phase of these barriers
+            for (int q = 0; q < TCW_MAXSTAGES; ++q) {
+                tc::mbar_inval(&full_bar[q]);
+                tc::mbar_inval(&empty_bar[q]);
+            }
+            for (int b = 0; b < 2; ++b) {
+                tc::mbar_inval(&dfull[b]);
+                tc::mbar_inval(&dempty[b]);
+            }
+            tc::mbar_inval(&a_bar);
+            tc::mbar_inval(&drain_bar);
+        }
         for (int q = 0; q < S; ++q) {
             tc::mbar_init(&full_bar[q], 1);
             tc::mbar_init(&empty_bar[q], 1);
@@ -596,13 +634,12 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
         fail = 0;
     }
     if (tid < 128) {
-        sA[tid] = aexp[(size_t)blockIdx.x * 128 + tid];
+        sA[tid] = aexp[(size_t)bid * 128 + tid];
         exacc[tid] = cmk(0.0, 0.0);
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t taddr = tslot;
     bool failed = false;
 
     if (warp == 0) {
@@ -635,6 +672,7 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
         if (lane == 0) {
             const uint32_t idesc = F16 ? tc::idesc_f16_f32(128, NT) : tc::idesc_bf16_f32(128, NT);
             if (a_res && !wait_or_fail(&a_bar, 0, lim, &fail)) failed = true;
+            int committed = 0;   // units whose ring stage was handed back by a commit
             for (int t = 0; t < NTILES && !failed; ++t) {
                 const int b = t & 1;
                 if (t >= 2 && !wait_or_fail(&dempty[b], (uint32_t)(((t >> 1) - 1) & 1), lim, &fail)) { failed = true; break; }
@@ -671,12 +709,17 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
                         }
                     }
                     tc::mma_commit(&empty_bar[st]);
+                    ++committed;
                 }
                 if (!failed) tc::mma_commit(&dfull[b]);
             }
             if (failed) atomicOr(status, STATUS_TIMEOUT);
             tc::mma_commit(&drain_bar);
             tc::mbar_wait(&drain_bar, 0, 1u << 22);
+            // the ring's last hand-backs, which no producer wait consumed, have arrived
+            // (the barriers may be initialised again for the block's next piece of work)
+            for (int v = max(0, committed - S); v < committed; ++v)
+                tc::mbar_wait(&empty_bar[v % S], (uint32_t)((v / S) & 1), 1u << 22);
         }
         __syncwarp();
     } else {
@@ -826,7 +869,53 @@ __global__ void __launch_bounds__(TCWZ_THREADS, 1)
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 1) tc::tmem_dealloc(taddr, talloc);
+}
+
+// One launch's GEMM-Z: one block per (walker, pair tile).
+template <int MODE>
+__global__ void __launch_bounds__(TCWZ_THREADS, 1) contract_tcw_kernel(const __grid_constant__ TcwZArgs a, uint32_t lim) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    __shared__ TcwZShared sh;
+    __shared__ uint32_t tslot;
+    const uint32_t talloc = tcw_z_talloc(a.NT, MODE != 0);
+    if ((threadIdx.x >> 5) == 1) {
+        tc::tmem_alloc(&tslot, talloc);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tcw_z_block<MODE>(a, blockIdx.x, sm, sh, tslot, lim, false);
+    if ((threadIdx.x >> 5) == 1) tc::tmem_dealloc(tslot, talloc);
+}
+
+// GEMM-Z of several launches' work (the systems of a batch) in one persistent
+// launch: block b takes the pieces b, b + gridDim.x, ... of the concatenated block
+// ranges, with the tensor memory and shared memory of the largest.
+template <int MODE>
+__global__ void __launch_bounds__(TCWZ_THREADS, 1) contract_tcw_multi_kernel(const __grid_constant__ TcwZMulti m,
+                                                                             uint32_t talloc, uint32_t lim) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    __shared__ TcwZShared sh;
+    __shared__ uint32_t tslot;
+    if ((threadIdx.x >> 5) == 1) {
+        tc::tmem_alloc(&tslot, talloc);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const long long total = m.first[m.n];
+    bool reuse = false;
+    for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+        int d = 0;
+        while (it >= m.first[d + 1]) ++d;
+        tcw_z_block<MODE>(m.a[d], it - m.first[d], sm, sh, tslot, lim, reuse);
+        reuse = true;
+    }
+    if ((threadIdx.x >> 5) == 1) tc::tmem_dealloc(tslot, talloc);
 }
 
 // ---------------------------------------------------------------- per pair: v_g and E_L
@@ -882,6 +971,11 @@ struct TcwShape {
     TcwSpin sp[2];
     long long WB;                 // walkers per chunk of the Y images
     size_t ximg, yimg, aimg, yexp, aexp;
+    // both spins' images at once (each spin its own region, at these element offsets)
+    // when the whole population fits one chunk that way; else one region the spins
+    // take in turn
+    bool sep;
+    size_t yoff[2], aoff[2], yeoff[2], aeoff[2];
 };
 
 size_t tcw_z_smem(int KC, int NT, int n, int S, bool a_res, int mode) {
@@ -943,23 +1037,32 @@ bool tcw_shape(int N, int nu, int nd, int G, long long W, int P, int mode, TcwSh
     if ((f16 ? 2 : 1) * s.N16 > 512) return false;
     s.GPB = 64;
     // Y images: per walker and spin NTILES x KC chunks of NT x 128 bytes per part
-    size_t per_walker = 0, aper = 0;
+    size_t pw[2] = {0, 0}, ap[2] = {0, 0};
     for (int q = 0; q < 2; ++q) {
         if (s.sp[q].n == 0) continue;
-        per_walker = std::max(per_walker, (size_t)s.sp[q].NTILES * s.KC * s.sp[q].NT * 128 * NP);
-        aper = std::max(aper, (size_t)s.sp[q].MT * s.KC * CH);
+        pw[q] = (size_t)s.sp[q].NTILES * s.KC * s.sp[q].NT * 128 * NP;
+        ap[q] = (size_t)s.sp[q].MT * s.KC * CH;
     }
     // about 12 GB of Y images per chunk, and a chunk's GEMM-Z blocks (WB x MT per
     // spin) a whole number of waves of 152 blocks when the population allows
     const size_t budget = (size_t)12 << 30;
+    s.sep = pw[1] > 0 && (size_t)W * (pw[0] + pw[1]) <= budget;
+    const size_t per_walker = s.sep ? pw[0] + pw[1] : std::max(pw[0], pw[1]);
+    const size_t aper = s.sep ? ap[0] + ap[1] : std::max(ap[0], ap[1]);
     s.WB = std::max(1LL, std::min(W, (long long)(budget / per_walker)));
     const int mt = std::max(s.sp[0].MT, s.sp[1].MT);
     if (s.WB < W && s.WB * mt >= 152) s.WB = std::max(1LL, (s.WB * mt / 152) * 152 / mt);
+    const size_t ye = (size_t)s.WB * s.G1 * nu, ae = (size_t)s.WB * mt * 128;   // exponents of one spin
     s.ximg = (size_t)s.G1 * s.KCX * NP * RX;
     s.yimg = (size_t)s.WB * per_walker;
     s.aimg = (size_t)s.WB * aper;
-    s.yexp = (size_t)s.WB * s.G1 * nu * sizeof(int);
-    s.aexp = (size_t)s.WB * std::max(s.sp[0].MT, s.sp[1].MT) * 128 * sizeof(int);
+    s.yexp = (s.sep ? 2 : 1) * ye * sizeof(int);
+    s.aexp = (s.sep ? 2 : 1) * ae * sizeof(int);
+    s.yoff[0] = s.aoff[0] = s.yeoff[0] = s.aeoff[0] = 0;
+    s.yoff[1] = s.sep ? (size_t)s.WB * pw[0] : 0;
+    s.aoff[1] = s.sep ? (size_t)s.WB * ap[0] : 0;
+    s.yeoff[1] = s.sep ? ye : 0;
+    s.aeoff[1] = s.sep ? ae : 0;
     return true;
 }
 
@@ -1008,39 +1111,84 @@ __global__ void tcw_lexp_kernel(int N, int G1, const double* __restrict__ h, con
     if (threadIdx.x == 0) lexp[g] = f16 ? exp_into(red[0], 7) : 0;
 }
 
+// GEMM-Z work of spin q for walkers [w0, w0 + wb) of the current chunk.
+TcwZArgs tcw_zargs_of(const Dims& d, const TcwShape& s, const TcwWork& w, int q, long long w0, long long wb,
+                      int* status) {
+    const TcwSpin& sp = s.sp[q];
+    TcwZArgs a;
+    a.n = sp.n; a.G1 = s.G1; a.KZ = s.KZ; a.KC = s.KC; a.NT = sp.NT; a.GB = sp.GB; a.NTILES = sp.NTILES;
+    a.P = d.P; a.PB = sp.PB; a.MT = sp.MT; a.S = sp.S; a.a_res = sp.a_res;
+    a.w0 = w0;
+    a.blocks = wb * sp.MT;
+    a.Aimg = w.aimg + s.aoff[q]; a.aexp = w.aexp + s.aeoff[q]; a.Yimg = w.yimg + s.yoff[q]; a.yexp = w.yexp + s.yeoff[q];
+    a.vpart = w.vpart[q]; a.exsum = w.exsum[q]; a.status = status;
+    a.smem = sp.smem;
+    return a;
+}
+
+// The Y and A images of walkers [w0, w0 + wb), spin `spin` (both spins for -1).
 template <int MODE>
-cudaError_t tcw_run(cudaStream_t st, const Dims& d, const TcwShape& s, const TcwWork& w, const double2* Bm,
-                    const double2* phi, double2* vpair, double2* epair, int* status, int bdf) {
+cudaError_t tcw_images_of(cudaStream_t st, const Dims& d, const TcwShape& s, const TcwWork& w, const double2* Bm,
+                          const double2* phi, int* status, int bdf, long long w0, long long wb, int spin) {
     cudaError_t e;
     if ((e = raise_smem_limit((const void*)tcw_y_kernel<MODE>, s.smem_y)) != cudaSuccess) return e;
-    if ((e = raise_smem_limit((const void*)contract_tcw_kernel<MODE>, std::max(s.sp[0].smem, s.sp[1].smem))) !=
-        cudaSuccess)
-        return e;
-    const long long W = d.pairs / d.P;
     const int n_gblk = (s.G1 + s.GPB - 1) / s.GPB;
-    for (long long w0 = 0; w0 < W; w0 += s.WB) {
-        const long long wb = std::min(s.WB, W - w0);
-        for (int q = 0; q < 2; ++q) {
-            const TcwSpin& sp = s.sp[q];
-            if (sp.n == 0) continue;
-            const int col0 = q ? d.nu : 0;
-            tcw_y_kernel<MODE><<<(unsigned)(wb * n_gblk), TCW_THREADS, s.smem_y, st>>>(
-                d.N, d.nt, col0, sp.n, s.G1, s.N16, s.KCX, s.SY, s.GPB, n_gblk, w0, phi, w.ximg, w.lexp, sp.NT, sp.GB,
-                s.KC, sp.NTILES, w.yimg, w.yexp, status, d.wait_polls);
-            tcw_a_kernel<MODE><<<(unsigned)(wb * sp.MT), 256, 0, st>>>(d.N, d.nt, col0, sp.n, d.P, sp.PB, sp.MT, s.N16,
-                                                                      s.KC, w0, Bm, w.aimg, w.aexp, bdf);
-            contract_tcw_kernel<MODE><<<(unsigned)(wb * sp.MT), TCWZ_THREADS, sp.smem, st>>>(
-                sp.n, s.G1, s.KZ, s.KC, sp.NT, sp.GB, sp.NTILES, d.P, sp.PB, sp.MT, sp.S, sp.a_res, w0, w.aimg, w.aexp,
-                w.yimg, w.yexp, w.vpart[q], w.exsum[q], status, d.wait_polls);
-            count_launches(3);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
+    for (int q = spin < 0 ? 0 : spin; q < (spin < 0 ? 2 : spin + 1); ++q) {
+        const TcwSpin& sp = s.sp[q];
+        if (sp.n == 0) continue;
+        const int col0 = q ? d.nu : 0;
+        tcw_y_kernel<MODE><<<(unsigned)(wb * n_gblk), TCW_THREADS, s.smem_y, st>>>(
+            d.N, d.nt, col0, sp.n, s.G1, s.N16, s.KCX, s.SY, s.GPB, n_gblk, w0, phi, w.ximg, w.lexp, sp.NT, sp.GB,
+            s.KC, sp.NTILES, w.yimg + s.yoff[q], w.yexp + s.yeoff[q], status, d.wait_polls);
+        tcw_a_kernel<MODE><<<(unsigned)(wb * sp.MT), 256, 0, st>>>(d.N, d.nt, col0, sp.n, d.P, sp.PB, sp.MT, s.N16,
+                                                                  s.KC, w0, Bm, w.aimg + s.aoff[q],
+                                                                  w.aexp + s.aeoff[q], bdf);
+        count_launches(2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    return cudaSuccess;
+}
+
+template <int MODE>
+cudaError_t tcw_images(cudaStream_t st, const Dims& d, const TcwShape& s, const TcwWork& w, const double2* Bm,
+                       const double2* phi, int* status, int bdf) {
+    return tcw_images_of<MODE>(st, d, s, w, Bm, phi, status, bdf, 0, d.pairs / d.P, -1);
+}
+
+cudaError_t tcw_finish_run(cudaStream_t st, const Dims& d, const TcwWork& w, double2* vpair, double2* epair) {
     const long long threads = d.pairs * 32;
     tcw_finish_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(d.pairs, d.G, d.nd > 0 ? 1 : 0, w.vpart[0],
                                                                         w.vpart[1], w.exsum[0], w.exsum[1], vpair, epair);
     count_launches(1);
     return cudaGetLastError();
+}
+
+// The whole contraction, chunk by chunk of walkers: images and GEMM-Z per spin
+// (both spins' images first when they have a region each), then the per-pair
+// finish.
+template <int MODE>
+cudaError_t tcw_run(cudaStream_t st, const Dims& d, const TcwShape& s, const TcwWork& w, const double2* Bm,
+                    const double2* phi, double2* vpair, double2* epair, int* status, int bdf) {
+    cudaError_t e;
+    if ((e = raise_smem_limit((const void*)contract_tcw_kernel<MODE>, std::max(s.sp[0].smem, s.sp[1].smem))) !=
+        cudaSuccess)
+        return e;
+    const long long W = d.pairs / d.P;
+    for (long long w0 = 0; w0 < W; w0 += s.WB) {
+        const long long wb = std::min(s.WB, W - w0);
+        if (s.sep && (e = tcw_images_of<MODE>(st, d, s, w, Bm, phi, status, bdf, w0, wb, -1)) != cudaSuccess)
+            return e;
+        for (int q = 0; q < 2; ++q) {
+            if (s.sp[q].n == 0) continue;
+            if (!s.sep && (e = tcw_images_of<MODE>(st, d, s, w, Bm, phi, status, bdf, w0, wb, q)) != cudaSuccess)
+                return e;
+            const TcwZArgs za = tcw_zargs_of(d, s, w, q, w0, wb, status);
+            contract_tcw_kernel<MODE><<<(unsigned)za.blocks, TCWZ_THREADS, za.smem, st>>>(za, d.wait_polls);
+            count_launches(1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return tcw_finish_run(st, d, w, vpair, epair);
 }
 
 }  // namespace
@@ -1074,6 +1222,70 @@ cudaError_t contract_tcw_prepare(cudaStream_t st, const Dims& d, const double* h
     // the Y images' padding rows (past the last matrix of a tile's block, and the
     // rows of absent matrices in the last tile) are never written: zero them once
     return cudaMemsetAsync(w.yimg, 0, s.yimg, st);
+}
+
+bool contract_tcw_single_chunk(const Dims& d, int mode) {
+    TcwShape s;
+    return tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, mode, s) && s.WB >= d.pairs / d.P &&
+           (s.sep || d.nd == 0);
+}
+
+cudaError_t contract_tcw_images(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,
+                                int* status, int mode, bool b_df) {
+    TcwShape s;
+    if (!tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, mode, s) || s.WB < d.pairs / d.P ||
+        !(s.sep || d.nd == 0))
+        return cudaErrorInvalidValue;
+    if (d.pairs <= 0) return cudaSuccess;
+    TcwWork w = tcw_carve(work, s, d.G, d.pairs);
+    const int bdf = b_df ? 1 : 0;
+    if (mode == 2) return tcw_images<2>(st, d, s, w, Bm, phi, status, bdf);
+    if (mode == 1) return tcw_images<1>(st, d, s, w, Bm, phi, status, bdf);
+    return tcw_images<0>(st, d, s, w, Bm, phi, status, bdf);
+}
+
+bool contract_tcw_zargs(const Dims& d, void* work, int* status, int mode, int spin, TcwZArgs* out) {
+    TcwShape s;
+    if (!tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, mode, s) || s.WB < d.pairs / d.P ||
+        !(s.sep || d.nd == 0))
+        return false;
+    TcwWork w = tcw_carve(work, s, d.G, d.pairs);
+    *out = tcw_zargs_of(d, s, w, spin, 0, d.pairs / d.P, status);
+    return true;
+}
+
+cudaError_t contract_tcw_multi(cudaStream_t st, const TcwZMulti& m, int mode, uint32_t lim) {
+    if (m.n < 1 || m.n > TCWZ_MAXWORK) return cudaErrorInvalidValue;
+    size_t smem = 0;
+    uint32_t talloc = 32;
+    for (int i = 0; i < m.n; ++i) {
+        smem = std::max(smem, m.a[i].smem);
+        talloc = std::max(talloc, tcw_z_talloc(m.a[i].NT, mode != 0));
+    }
+    const long long total = m.first[m.n];
+    if (total <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<long long>(total, std::max(1, sms));
+    const void* k = mode == 2 ? (const void*)contract_tcw_multi_kernel<2>
+                              : (mode == 1 ? (const void*)contract_tcw_multi_kernel<1> : (const void*)contract_tcw_multi_kernel<0>);
+    if ((e = raise_smem_limit(k, smem)) != cudaSuccess) return e;
+    const uint32_t l = lim ? lim : (1u << 26);
+    if (mode == 2) contract_tcw_multi_kernel<2><<<grid, TCWZ_THREADS, smem, st>>>(m, talloc, l);
+    else if (mode == 1) contract_tcw_multi_kernel<1><<<grid, TCWZ_THREADS, smem, st>>>(m, talloc, l);
+    else contract_tcw_multi_kernel<0><<<grid, TCWZ_THREADS, smem, st>>>(m, talloc, l);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t contract_tcw_finish(cudaStream_t st, const Dims& d, void* work, double2* vpair, double2* epair, int mode) {
+    TcwShape s;
+    if (!tcw_shape(d.N, d.nu, d.nd, d.G, d.pairs / d.P, d.P, mode, s)) return cudaErrorInvalidValue;
+    if (d.pairs <= 0) return cudaSuccess;
+    TcwWork w = tcw_carve(work, s, d.G, d.pairs);
+    return tcw_finish_run(st, d, w, vpair, epair);
 }
 
 cudaError_t contract_tcw(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,

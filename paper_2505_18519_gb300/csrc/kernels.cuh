@@ -4,6 +4,11 @@
 
 // api.cu: record an error message for afqmc_last_error and return `st`
 afqmc_status set_error(afqmc_status st, const char* fmt, ...);
+// api.cu: one step of a context in a batch whose walker-side GEMM-Z runs in one
+// launch for all systems: part 1 up to the contraction's images, part 2 the rest.
+namespace afq {
+afqmc_status batch_step_part(afqmc_ctx* ctx, int part);
+}
 // api.cu: the tensor-core form of a mixed-precision configuration (the value
 // afqmc_contract_kernel reports: 1 per-pair, 2 walker-side for N <= 64,
 // 5 general walker-side), -1 if the chosen form does not support its sizes.
@@ -147,6 +152,35 @@ cudaError_t contract_tcw_prepare(cudaStream_t st, const Dims& d, const double* h
 // b_df: Bm holds B as double-float pairs (overlap_lu with b_df), else FP64.
 cudaError_t contract_tcw(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,
                          double2* vpair, double2* epair, int* status, int mode, bool b_df = false);
+// The same in three parts, for a context whose Y images of both spins fit one chunk
+// of walkers side by side (contract_tcw_single_chunk): the images of both spins
+// (contract_tcw_images), then GEMM-Z, here
+// described per spin (contract_tcw_zargs; n == 0 for an empty spin) so that a batch
+// of systems runs it in one launch (contract_tcw_multi), then the per-pair finish.
+struct TcwZArgs {
+    int n, G1, KZ, KC, NT, GB, NTILES, P, PB, MT, S, a_res;
+    long long w0, blocks;         // first walker of the work; blocks (walkers x pair tiles)
+    const uint8_t* Aimg;
+    const int* aexp;
+    const uint8_t* Yimg;
+    const int* yexp;
+    float2* vpart;
+    double2* exsum;
+    int* status;
+    size_t smem;                  // dynamic shared memory a block needs
+};
+constexpr int TCWZ_MAXWORK = 32;
+struct TcwZMulti {
+    int n;                                  // pieces of work
+    long long first[TCWZ_MAXWORK + 1];      // first block of each piece; first[n] = total
+    TcwZArgs a[TCWZ_MAXWORK];
+};
+bool contract_tcw_single_chunk(const Dims& d, int mode);
+cudaError_t contract_tcw_images(cudaStream_t st, const Dims& d, void* work, const double2* Bm, const double2* phi,
+                                int* status, int mode, bool b_df);
+bool contract_tcw_zargs(const Dims& d, void* work, int* status, int mode, int spin, TcwZArgs* out);
+cudaError_t contract_tcw_multi(cudaStream_t st, const TcwZMulti& m, int mode, uint32_t lim);
+cudaError_t contract_tcw_finish(cudaStream_t st, const Dims& d, void* work, double2* vpair, double2* epair, int mode);
 
 // trial_complex.cu: complex and multi-slice trial samples (FP64 path).
 // Out = exp(alpha S) V0 per problem (S real symmetric in S_all; V0 = the real

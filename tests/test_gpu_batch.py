@@ -195,3 +195,36 @@ def test_batched_systems_step_like_the_oracle():
     b.close()
     for c in ctxs:
         c.close()
+
+
+def test_shared_contraction_launch_equals_individual_steps():
+    """Systems on the walker-side tensor-core form share one persistent GEMM-Z
+    launch per batch step (their blocks taken from one list); a system on another
+    form keeps its own kernels.  Every result stays bit for bit equal to stepping
+    each context alone, including a system whose walkers need two pair tiles and
+    one with a single spin."""
+    systems = [(ai.SystemSpec(37, 7, 5, 40, 9, True, 77), 6, 5, "fp16x6"),
+               (ai.SystemSpec(70, 14, 13, 90, 10, True, 81), 3, 7, "fp16x6"),
+               (ai.SystemSpec(12, 3, 0, 20, 6, True, 78), 5, 4, "fp16x6"),
+               (ai.SystemSpec(50, 10, 10, 250, 50, True, 1001), 4, 8, "fp16x3")]
+    batched = [_ctx(spec, W, P, prec, 60 + i) for i, (spec, W, P, prec) in enumerate(systems)]
+    single = [_ctx(spec, W, P, prec, 60 + i) for i, (spec, W, P, prec) in enumerate(systems)]
+    b = lib.Batch(batched)
+    assert b.shared_contractions == 3          # the fp16x3 system (N = 50) takes the N <= 64 form
+    before = lib.launch_count()
+    b.step(3)
+    b.sync()
+    graph_kernels = lib.launch_count() - before
+    before = lib.launch_count()
+    for c in single:
+        c.step(3)
+    torch.cuda.synchronize()
+    # five GEMM-Z launches per step (two spins, two spins, one spin) become one
+    assert graph_kernels == lib.launch_count() - before - 3 * (5 - 1)
+    for cb, cs in zip(batched, single):
+        assert cb.save_state() == cs.save_state()
+        assert np.array_equal(cb.history(3), cs.history(3))
+        assert cb.stats()["status"] == 0
+    b.close()
+    for c in batched + single:
+        c.close()

@@ -128,15 +128,18 @@ def test_tensor_core_form_and_wait_limit_fields_reach_the_library(L):
 
 def test_three_part_precision_takes_only_the_general_walker_side_form(L):
     """fp16x6 (three FP16 parts per operand) runs only on the general walker-side
-    form, up to N = 192: the auto form picks it, the per-pair form and N = 200 are
-    refused, and its work space holds three-part images (more than fp16x3's)."""
+    form, up to N = 256 with n_up <= 40: the auto form picks it, the per-pair form,
+    n_up = 48 and N = 264 are refused, and its work space holds three-part images
+    (more than fp16x3's)."""
     kw = dict(precision="fp16x6")
-    for shape in ((50, 10, 10, 250, 50, 8, 32), (120, 24, 24, 600, 120, 8, 64), (192, 40, 40, 100, 20, 4, 16)):
+    for shape in ((50, 10, 10, 250, 50, 8, 32), (120, 24, 24, 600, 120, 8, 64), (192, 40, 40, 100, 20, 4, 16),
+                  (200, 40, 40, 1000, 200, 8, 16), (256, 40, 40, 100, 20, 4, 16)):
         assert lib.contract_kernel(lib.make_config(*shape, 0.005, 1, **kw)) == "contract_tcw_kernel", shape
     with pytest.raises(lib.AfqmcError):
         lib.contract_kernel(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, tc_form="per_pair", **kw))
-    with pytest.raises(lib.AfqmcError):
-        lib.contract_kernel(lib.make_config(200, 40, 40, 1000, 200, 8, 16, 0.005, 1, **kw))
+    for shape in ((128, 48, 48, 100, 20, 4, 16), (264, 40, 40, 100, 20, 4, 16)):
+        with pytest.raises(lib.AfqmcError):
+            lib.contract_kernel(lib.make_config(*shape, 0.005, 1, **kw))
     a = lib.workspace_bytes(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, tc_form="walker",
                                             precision="fp16x3"))
     b = lib.workspace_bytes(lib.make_config(120, 24, 24, 600, 120, 8, 64, 0.005, 1, **kw))
