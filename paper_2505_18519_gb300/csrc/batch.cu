@@ -8,7 +8,7 @@
 // walker-side tensor-core contraction's GEMM-Z, runs for all systems that use it
 // (one operand arithmetic, Y images in one chunk of walkers) in one persistent
 // launch on the batch's stream: each branch runs up to the contraction's images,
-// the branches join, contract_tcw_multi_kernel takes every system's blocks from one
+// the branches join, contract_tcw_kernel takes every system's blocks from one
 // list, and the branches fork again for the rest of the step.
 //
 // The autotuner times the candidate launch shapes of the heaviest kernels on a

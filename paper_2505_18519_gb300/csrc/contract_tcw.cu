@@ -22,11 +22,13 @@
 //                       and its epilogue, which writes the Bop image of Y_g
 //                       (per-column power-of-two scale, split) to global memory;
 //   tcw_a_kernel        per (walker, spin, tile of pairs): the A image of B_p;
-//   contract_tcw_kernel per (walker, spin, tile of pairs): GEMM-Z over every block
-//                       of matrices, a producer warp streaming the Bop image
-//                       through a ring of bulk copies, an MMA warp filling two
-//                       tensor-memory buffers, four epilogue warps forming Tr Z and
-//                       Tr Z^2 through a shared-memory transpose;
+//   contract_tcw_kernel GEMM-Z, persistent: each block loops over pieces of work
+//                       (walker, spin, tile of pairs), of one system or of several
+//                       (a batch); per piece a producer warp streams the Bop image
+//                       through a ring of bulk copies, an MMA warp fills two
+//                       tensor-memory buffers (the products of one A part in a row,
+//                       A kept in the collector buffer), eight epilogue warps form
+//                       Tr Z and Tr Z^2 through a shared-memory transpose;
 //   tcw_finish_kernel   per pair: v_g = sum over spins, E_L.
 //
 // Split 16-bit arithmetic (fp16x3): every operand row is scaled by a power of two
@@ -690,21 +692,25 @@ __device__ __forceinline__ void tcw_z_block(const TcwZArgs& A, long long bid, ui
                         const uint64_t a0 = tc::desc_sw128(pa + s * 32), a1 = tc::desc_sw128(pa + TCW_PART + s * 32);
                         const uint64_t b0 = tc::desc_sw128(pb + s * 32), b1 = tc::desc_sw128(pb + bpart + s * 32);
                         const uint32_t first = (c == 0 && s == 0) ? 0u : 1u;
-                        tc::mma_f16(dh, a0, b0, idesc, first);
+                        // products grouped by their A part, which the collector buffer keeps
+                        // between them (each part read from shared memory once per K step)
                         if constexpr (MODE == 2) {
                             const uint64_t a2 = tc::desc_sw128(pa + 2 * TCW_PART + s * 32),
                                            b2 = tc::desc_sw128(pb + 2 * bpart + s * 32);
-                            tc::mma_f16(dl, a0, b1, idesc, first);
-                            tc::mma_f16(dl, a1, b0, idesc, 1u);
-                            tc::mma_f16(dl, a1, b1, idesc, 1u);
-                            tc::mma_f16(dl, a0, b2, idesc, 1u);
+                            tc::mma_f16_ca<1>(dh, a0, b0, idesc, first);
+                            tc::mma_f16_ca<2>(dl, a0, b1, idesc, first);
+                            tc::mma_f16_ca<3>(dl, a0, b2, idesc, 1u);
+                            tc::mma_f16_ca<1>(dl, a1, b0, idesc, 1u);
+                            tc::mma_f16_ca<3>(dl, a1, b1, idesc, 1u);
                             tc::mma_f16(dl, a2, b0, idesc, 1u);
                         } else if constexpr (MODE == 1) {
-                            tc::mma_f16(dl, a0, b1, idesc, first);
-                            tc::mma_f16(dl, a1, b0, idesc, 1u);
-                            tc::mma_f16(dl, a1, b1, idesc, 1u);
+                            tc::mma_f16_ca<1>(dh, a0, b0, idesc, first);
+                            tc::mma_f16_ca<3>(dl, a0, b1, idesc, first);
+                            tc::mma_f16_ca<1>(dl, a1, b0, idesc, 1u);
+                            tc::mma_f16_ca<3>(dl, a1, b1, idesc, 1u);
                         } else {
-                            tc::mma_f16(dh, a0, b1, idesc, 1u);
+                            tc::mma_f16_ca<1>(dh, a0, b0, idesc, first);
+                            tc::mma_f16_ca<3>(dh, a0, b1, idesc, 1u);
                             tc::mma_f16(dh, a1, b0, idesc, 1u);
                         }
                     }
@@ -871,31 +877,13 @@ __device__ __forceinline__ void tcw_z_block(const TcwZArgs& A, long long bid, ui
     __syncthreads();
 }
 
-// One launch's GEMM-Z: one block per (walker, pair tile).
+// GEMM-Z of one or several pieces of work (a spin of a chunk of walkers, both
+// spins, or the systems of a batch) in one persistent launch: block b takes the
+// blocks b, b + gridDim.x, ... of the concatenated block ranges, with the tensor
+// memory and shared memory of the largest piece.
 template <int MODE>
-__global__ void __launch_bounds__(TCWZ_THREADS, 1) contract_tcw_kernel(const __grid_constant__ TcwZArgs a, uint32_t lim) {
-    extern __shared__ uint8_t smraw[];
-    uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    __shared__ TcwZShared sh;
-    __shared__ uint32_t tslot;
-    const uint32_t talloc = tcw_z_talloc(a.NT, MODE != 0);
-    if ((threadIdx.x >> 5) == 1) {
-        tc::tmem_alloc(&tslot, talloc);
-        tc::tmem_relinquish();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    tcw_z_block<MODE>(a, blockIdx.x, sm, sh, tslot, lim, false);
-    if ((threadIdx.x >> 5) == 1) tc::tmem_dealloc(tslot, talloc);
-}
-
-// GEMM-Z of several launches' work (the systems of a batch) in one persistent
-// launch: block b takes the pieces b, b + gridDim.x, ... of the concatenated block
-// ranges, with the tensor memory and shared memory of the largest.
-template <int MODE>
-__global__ void __launch_bounds__(TCWZ_THREADS, 1) contract_tcw_multi_kernel(const __grid_constant__ TcwZMulti m,
-                                                                             uint32_t talloc, uint32_t lim) {
+__global__ void __launch_bounds__(TCWZ_THREADS, 1) contract_tcw_kernel(const __grid_constant__ TcwZMulti m,
+                                                                       uint32_t talloc, uint32_t lim) {
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     __shared__ TcwZShared sh;
@@ -1163,30 +1151,60 @@ cudaError_t tcw_finish_run(cudaStream_t st, const Dims& d, const TcwWork& w, dou
     return cudaGetLastError();
 }
 
+// GEMM-Z of the pieces in m (one launch; blocks loop over the concatenated block
+// ranges): as many blocks as fit the GPU at once, counting the tensor-memory
+// columns one block holds.
+template <int MODE>
+cudaError_t tcw_z_launch(cudaStream_t st, const TcwZMulti& m, uint32_t lim) {
+    size_t smem = 0;
+    uint32_t talloc = 32;
+    for (int i = 0; i < m.n; ++i) {
+        smem = std::max(smem, m.a[i].smem);
+        talloc = std::max(talloc, tcw_z_talloc(m.a[i].NT, MODE != 0));
+    }
+    const long long total = m.first[m.n];
+    if (total <= 0) return cudaSuccess;
+    const void* k = (const void*)contract_tcw_kernel<MODE>;
+    cudaError_t e = raise_smem_limit(k, smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, TCWZ_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(1, std::min(per_sm, (int)(512u / talloc)));
+    const unsigned grid = (unsigned)std::min<long long>(total, (long long)std::max(1, sms) * per_sm);
+    contract_tcw_kernel<MODE><<<grid, TCWZ_THREADS, smem, st>>>(m, talloc, lim ? lim : (1u << 26));
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // The whole contraction, chunk by chunk of walkers: images and GEMM-Z per spin
-// (both spins' images first when they have a region each), then the per-pair
-// finish.
+// (both spins' images first and one GEMM-Z launch for both when they have a region
+// each), then the per-pair finish.
 template <int MODE>
 cudaError_t tcw_run(cudaStream_t st, const Dims& d, const TcwShape& s, const TcwWork& w, const double2* Bm,
                     const double2* phi, double2* vpair, double2* epair, int* status, int bdf) {
     cudaError_t e;
-    if ((e = raise_smem_limit((const void*)contract_tcw_kernel<MODE>, std::max(s.sp[0].smem, s.sp[1].smem))) !=
-        cudaSuccess)
-        return e;
     const long long W = d.pairs / d.P;
     for (long long w0 = 0; w0 < W; w0 += s.WB) {
         const long long wb = std::min(s.WB, W - w0);
+        TcwZMulti m;
+        m.n = 0;
+        m.first[0] = 0;
         if (s.sep && (e = tcw_images_of<MODE>(st, d, s, w, Bm, phi, status, bdf, w0, wb, -1)) != cudaSuccess)
             return e;
         for (int q = 0; q < 2; ++q) {
             if (s.sp[q].n == 0) continue;
-            if (!s.sep && (e = tcw_images_of<MODE>(st, d, s, w, Bm, phi, status, bdf, w0, wb, q)) != cudaSuccess)
-                return e;
-            const TcwZArgs za = tcw_zargs_of(d, s, w, q, w0, wb, status);
-            contract_tcw_kernel<MODE><<<(unsigned)za.blocks, TCWZ_THREADS, za.smem, st>>>(za, d.wait_polls);
-            count_launches(1);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (!s.sep) {
+                if ((e = tcw_images_of<MODE>(st, d, s, w, Bm, phi, status, bdf, w0, wb, q)) != cudaSuccess) return e;
+                m.n = 0;
+            }
+            m.a[m.n] = tcw_zargs_of(d, s, w, q, w0, wb, status);
+            m.first[m.n + 1] = m.first[m.n] + m.a[m.n].blocks;
+            ++m.n;
+            if (!s.sep && (e = tcw_z_launch<MODE>(st, m, d.wait_polls)) != cudaSuccess) return e;
         }
+        if (s.sep && (e = tcw_z_launch<MODE>(st, m, d.wait_polls)) != cudaSuccess) return e;
     }
     return tcw_finish_run(st, d, w, vpair, epair);
 }
@@ -1256,28 +1274,9 @@ bool contract_tcw_zargs(const Dims& d, void* work, int* status, int mode, int sp
 
 cudaError_t contract_tcw_multi(cudaStream_t st, const TcwZMulti& m, int mode, uint32_t lim) {
     if (m.n < 1 || m.n > TCWZ_MAXWORK) return cudaErrorInvalidValue;
-    size_t smem = 0;
-    uint32_t talloc = 32;
-    for (int i = 0; i < m.n; ++i) {
-        smem = std::max(smem, m.a[i].smem);
-        talloc = std::max(talloc, tcw_z_talloc(m.a[i].NT, mode != 0));
-    }
-    const long long total = m.first[m.n];
-    if (total <= 0) return cudaSuccess;
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)std::min<long long>(total, std::max(1, sms));
-    const void* k = mode == 2 ? (const void*)contract_tcw_multi_kernel<2>
-                              : (mode == 1 ? (const void*)contract_tcw_multi_kernel<1> : (const void*)contract_tcw_multi_kernel<0>);
-    if ((e = raise_smem_limit(k, smem)) != cudaSuccess) return e;
-    const uint32_t l = lim ? lim : (1u << 26);
-    if (mode == 2) contract_tcw_multi_kernel<2><<<grid, TCWZ_THREADS, smem, st>>>(m, talloc, l);
-    else if (mode == 1) contract_tcw_multi_kernel<1><<<grid, TCWZ_THREADS, smem, st>>>(m, talloc, l);
-    else contract_tcw_multi_kernel<0><<<grid, TCWZ_THREADS, smem, st>>>(m, talloc, l);
-    count_launches(1);
-    return cudaGetLastError();
+    if (mode == 2) return tcw_z_launch<2>(st, m, lim);
+    if (mode == 1) return tcw_z_launch<1>(st, m, lim);
+    return tcw_z_launch<0>(st, m, lim);
 }
 
 cudaError_t contract_tcw_finish(cudaStream_t st, const Dims& d, void* work, double2* vpair, double2* epair, int mode) {

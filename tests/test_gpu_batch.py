@@ -219,8 +219,9 @@ def test_shared_contraction_launch_equals_individual_steps():
     for c in single:
         c.step(3)
     torch.cuda.synchronize()
-    # five GEMM-Z launches per step (two spins, two spins, one spin) become one
-    assert graph_kernels == lib.launch_count() - before - 3 * (5 - 1)
+    # a context alone runs GEMM-Z of both its spins in one launch: three launches
+    # per step become one
+    assert graph_kernels == lib.launch_count() - before - 3 * (3 - 1)
     for cb, cs in zip(batched, single):
         assert cb.save_state() == cs.save_state()
         assert np.array_equal(cb.history(3), cs.history(3))
