@@ -198,46 +198,53 @@ __global__ void tcw_x_image_kernel(int N, int N16, int KCX, int G1, const double
 }
 
 // ---------------------------------------------------------------- GEMM-Y and the Bop image of Y_g
-// Block: walker w0 + blockIdx.x / n_gblk, matrices [gb GPB, (gb + 1) GPB) of one spin
-// (columns col0 .. col0 + n - 1 of phi).  Shared memory: PW (KCX chunks of NP parts,
-// each part the 2n rows (b, ri) = Re/Im phi[:, col0 + b] times 2^sPW[b], K = i, rounded
-// up to 8 rows: the MMAs read 128 rows from a part's start, and the rows past 2n,
+// Block: the WPB walkers w0 + (blockIdx.x / n_gblk) WPB + v (v < WPB, those below wb),
+// matrices [gb GPB, (gb + 1) GPB) of one spin (columns col0 .. col0 + n - 1 of phi).
+// Shared memory: PW (KCX chunks of NP parts, each part the WPB 2n rows
+// (v, b, ri) = Re/Im phi_v[:, col0 + b] times 2^sPW[v n + b], K = i, rounded up to 8
+// rows: the MMAs read 128 rows from a part's start, and the rows past WPB 2n,
 // whatever they hold, give rows of D_Y that the epilogue never reads; a tail pads the
 // last part's 128 rows), then a ring of S stages, each one part of a K chunk of X_g
-// (N16 rows).
-// Tensor memory: D_Y (N16 columns) and, FP16, its correction (N16 more).
+// (N16 rows).  Stacking the walkers fills the MMA's 128 rows (2n alone would leave
+// most of them empty) and streams each X_g once for all of them.
+// Tensor memory: NBUF buffers (two when they fit, so that the epilogue of one
+// matrix overlaps the products of the next) of D_Y (N16 columns) and, FP16, its
+// correction (N16 more).
 // Output: the Bop rows (g, b, ri) of matrix g in N-tile t = g / GB at row
 // (g % GB) 2n + 2b + ri; K chunk c of a tile is NT rows of each part in turn; and
 // yexp[(wl G1 + g) n + b], the exponent of column b (image = Y 2^yexp).
 template <int MODE>
 __global__ void __launch_bounds__(TCW_THREADS, 1)
     tcw_y_kernel(int N, int nt, int col0, int n, int G1, int N16, int KCX, int S, int GPB, int n_gblk, long long w0,
-                 const double2* __restrict__ phi, const uint8_t* __restrict__ Ximg, const int* __restrict__ lexp,
-                 int NT, int GB, int KC, int NTILES, uint8_t* __restrict__ Yimg, int* __restrict__ yexp, int* status,
-                 uint32_t lim) {
+                 int WPB, long long wb, int NBUF, const double2* __restrict__ phi, const uint8_t* __restrict__ Ximg,
+                 const int* __restrict__ lexp, int NT, int GB, int KC, int NTILES, uint8_t* __restrict__ Yimg,
+                 int* __restrict__ yexp, int* status, uint32_t lim) {
     constexpr bool F16 = MODE != 0;
     constexpr int NP = tcw_parts(MODE);
     constexpr uint32_t CH = tcw_chunk(MODE);
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const uint32_t RX = (uint32_t)N16 * 128u;
-    const uint32_t PS = tcw_pw_part(n), CS = PS * (uint32_t)NP;   // one part, one chunk of PW
+    const int rows = WPB * 2 * n;                                  // rows (v, b, ri) of PW and D_Y
+    const uint32_t PS = tcw_pw_part(WPB * n), CS = PS * (uint32_t)NP;   // one part, one chunk of PW
     uint8_t* PW = sm;                                         // KCX x CS, then the tail
     uint8_t* ring = PW + (size_t)KCX * CS + (TCW_PART - PS);  // S x RX
-    __shared__ uint64_t full_bar[TCW_MAXSTAGES], empty_bar[TCW_MAXSTAGES], dfull, dempty, drain_bar;
+    __shared__ uint64_t full_bar[TCW_MAXSTAGES], empty_bar[TCW_MAXSTAGES], dfull[2], dempty[2], drain_bar;
     __shared__ uint32_t tslot;
     __shared__ volatile int fail;
     __shared__ int sPW[64];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wl = blockIdx.x / n_gblk;
+    const long long wl0 = (long long)(blockIdx.x / n_gblk) * WPB;   // first walker of the block (in the chunk)
+    const int nw = (int)min((long long)WPB, wb - wl0);              // walkers present
     const int gb = blockIdx.x % n_gblk;
     const int g0 = gb * GPB, g1 = min(G1, g0 + GPB);
     const int ng = max(0, g1 - g0);
     const int n_units = ng * KCX * NP;
-    const double2* ph = phi + (w0 + wl) * (long long)N * nt + col0;
+    const double2* ph = phi + (w0 + wl0) * (long long)N * nt + col0;   // walker v at ph + v N nt
     const uint32_t tcols = F16 ? 2u * (uint32_t)N16 : (uint32_t)N16;
-    const uint32_t talloc = tcols <= 32 ? 32 : (tcols <= 64 ? 64 : (tcols <= 128 ? 128 : (tcols <= 256 ? 256 : 512)));
+    const uint32_t tall = (uint32_t)NBUF * tcols;
+    const uint32_t talloc = tall <= 32 ? 32 : (tall <= 64 ? 64 : (tall <= 128 ? 128 : (tall <= 256 ? 256 : 512)));
 
     if (warp == 1) {
         tc::tmem_alloc(&tslot, talloc);
@@ -248,37 +255,42 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
             tc::mbar_init(&full_bar[q], 1);
             tc::mbar_init(&empty_bar[q], 1);
         }
-        tc::mbar_init(&dfull, 1);
-        tc::mbar_init(&dempty, 1);
+        for (int q = 0; q < 2; ++q) {
+            tc::mbar_init(&dfull[q], 1);
+            tc::mbar_init(&dempty[q], 1);
+        }
         tc::mbar_init(&drain_bar, 1);
         tc::mbar_fence_init();
         fail = 0;
     }
-    // column exponents of PW: the larger of |Re|, |Im| of phi[:, b] into [128, 256)
-    for (int b = warp; b < n; b += TCW_THREADS / 32) {
+    // column exponents of PW: the larger of |Re|, |Im| of phi_v[:, b] into [128, 256)
+    for (int vb = warp; vb < WPB * n; vb += TCW_THREADS / 32) {
+        const int v = vb / n, b = vb % n;
         float m = 0.f;
-        for (int i = lane; i < N; i += 32) {
-            const double2 t = ph[(long long)i * nt + b];
-            m = fmaxf(m, fmaxf((float)fabs(t.x), (float)fabs(t.y)));
-        }
+        if (v < nw)
+            for (int i = lane; i < N; i += 32) {
+                const double2 t = ph[((long long)v * N + i) * nt + b];
+                m = fmaxf(m, fmaxf((float)fabs(t.x), (float)fabs(t.y)));
+            }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) sPW[b] = F16 ? exp_into(m, 7) : 0;
+        if (lane == 0) sPW[vb] = F16 ? exp_into(m, 7) : 0;
     }
     __syncthreads();
-    // PW rows (b, ri), K = i, 16-byte units; rows from 2n to the part's end are zero
+    // PW rows (v, b, ri), K = i, 16-byte units; rows from WPB 2n to the part's end, and
+    // those of absent walkers, are zero
     const int rows_pw = (int)(PS / 128u);
     for (int e = tid; e < KCX * rows_pw * 8; e += TCW_THREADS) {
         const int u = e % 8, r = (e / 8) % rows_pw, c = e / (8 * rows_pw);
-        const int b = r >> 1, ri = r & 1;
+        const int v = r / (2 * n), b = (r % (2 * n)) >> 1, ri = r & 1;
         uint16_t pt[NP][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int i = c * 64 + u * 8 + q;
             double x = 0.0;
-            if (r < 2 * n && i < N) {
-                const double2 t = ph[(long long)i * nt + b];
-                x = ldexp(ri ? t.y : t.x, sPW[b]);
+            if (r < rows && v < nw && i < N) {
+                const double2 t = ph[((long long)v * N + i) * nt + b];
+                x = ldexp(ri ? t.y : t.x, sPW[r >> 1]);
             }
             uint16_t o[NP];
             split_parts<MODE>(x, o);
@@ -318,11 +330,15 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
         // ---- MMA issue (one thread): D_Y = PW X_g^T, the part products of the header
         if (lane == 0) {
             const uint32_t idesc = F16 ? tc::idesc_f16_f32(128, N16) : tc::idesc_bf16_f32(128, N16);
-            const uint32_t dh = taddr, dl = taddr + (F16 ? (uint32_t)N16 : 0u);
             int v = 0;
             for (int gi = 0; gi < ng && !failed; ++gi) {
-                if (gi > 0 && !wait_or_fail(&dempty, (uint32_t)((gi - 1) & 1), lim, &fail)) { failed = true; break; }
+                const int buf = gi % NBUF;
+                if (gi >= NBUF && !wait_or_fail(&dempty[buf], (uint32_t)(((gi / NBUF) - 1) & 1), lim, &fail)) {
+                    failed = true;
+                    break;
+                }
                 tc::fence_after_sync();
+                const uint32_t dh = taddr + (uint32_t)buf * tcols, dl = dh + (F16 ? (uint32_t)N16 : 0u);
                 for (int c = 0; c < KCX && !failed; ++c) {
                     const int ks = min(4, (N16 - 64 * c) / 16);
                     for (int hh = 0; hh < NP; ++hh, ++v) {
@@ -358,7 +374,7 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
                         tc::mma_commit(&empty_bar[st]);
                     }
                 }
-                if (!failed) tc::mma_commit(&dfull);
+                if (!failed) tc::mma_commit(&dfull[buf]);
             }
             if (failed) atomicOr(status, STATUS_TIMEOUT);
             tc::mma_commit(&drain_bar);                 // every issued MMA completes before the block leaves
@@ -366,16 +382,18 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
         }
         __syncwarp();
     } else {
-        // ---- epilogue (warps 2-5): lane r = (b, ri) of D_Y holds Re/Im Y_g[:, b]
+        // ---- epilogue (warps 2-5): lane r = (v, b, ri) of D_Y holds Re/Im Y_g[:, b] of walker v
         const int quarter = warp & 3;
         const int r = 32 * quarter + lane;
-        const uint32_t lb = (uint32_t)(32 * quarter) << 16;
-        const int b = r >> 1, ri = r & 1;
-        const bool row_ok = r < 2 * n;
-        const int e_pw = row_ok ? sPW[b] : 0;
+        const int vw = r / (2 * n), b = (r % (2 * n)) >> 1, ri = r & 1;
+        const bool row_ok = r < rows && vw < nw;
+        const int e_pw = row_ok ? sPW[r >> 1] : 0;
+        const long long wl = wl0 + (row_ok ? vw : 0);                  // the row's walker (in the chunk)
         for (int gi = 0; gi < ng; ++gi) {
             const int g = g0 + gi;
-            const bool ok = wait_or_fail(&dfull, (uint32_t)(gi & 1), lim, &fail);
+            const int buf = gi % NBUF;
+            const uint32_t lb = ((uint32_t)(32 * quarter) << 16) + (uint32_t)buf * tcols;
+            const bool ok = wait_or_fail(&dfull[buf], (uint32_t)((gi / NBUF) & 1), lim, &fail);
             if (tc::named_sync_or<TCW_EPI>(!ok)) { failed = true; break; }
             tc::fence_after_sync();
             // pass 1: the largest |Y| of column b (its Re and Im lanes)
@@ -443,10 +461,10 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
                 }
             }
             if (row_ok && ri == 0) yexp[((size_t)wl * G1 + g) * n + b] = et + e_pw + lexp[g];
-            // D_Y has been read: the next matrix's MMAs may overwrite it
+            // this buffer of D_Y has been read: a later matrix's MMAs may overwrite it
             tc::fence_before_sync();
             tc::named_sync<TCW_EPI>();
-            if (r == 0) tc::mbar_arrive(&dempty);
+            if (r == 0) tc::mbar_arrive(&dempty[buf]);
         }
         if (failed && r == 0) atomicOr(status, STATUS_TIMEOUT);
     }
@@ -955,6 +973,7 @@ struct TcwSpin {
 struct TcwShape {
     int N16, KZ, KC, KCX, G1;
     int SY, GPB;
+    int WPBY, YBUF;               // GEMM-Y: walkers per block, tensor-memory buffers
     size_t smem_y;
     TcwSpin sp[2];
     long long WB;                 // walkers per chunk of the Y images
@@ -1014,14 +1033,26 @@ bool tcw_shape(int N, int nu, int nd, int G, long long W, int P, int mode, TcwSh
     if (!tcw_spin(nu, P, s.KC, s.G1, mode, s.sp[0])) return false;
     if (nd > 0 && !tcw_spin(nd, P, s.KC, s.G1, mode, s.sp[1])) return false;
     if (nd == 0) s.sp[1] = s.sp[0], s.sp[1].n = 0;
-    // GEMM-Y: PW (KCX chunks) and a ring of at least two chunk parts of N16 rows
+    // GEMM-Y: PW (KCX chunks of the rows of WPBY walkers, as many as fill the MMA's
+    // 128 rows, at most 8) and a ring of at least two chunk parts of N16 rows
     const size_t RX = (size_t)s.N16 * 128;
-    const size_t PWB = (size_t)s.KCX * NP * tcw_pw_part(nu) + (TCW_PART - tcw_pw_part(nu));   // PW and its tail
     s.SY = 0;
-    for (int S = TCW_MAXSTAGES; S >= 2; --S)
-        if (1024 + PWB + S * RX <= TCW_SMEM_MAX) { s.SY = S; break; }
+    for (s.WPBY = std::max(1, std::min(8, 64 / nu)); s.WPBY >= 1; --s.WPBY) {
+        const uint32_t ps = tcw_pw_part(s.WPBY * nu);
+        const size_t PWB = (size_t)s.KCX * NP * ps + (TCW_PART - ps);   // PW and its tail
+        for (int S = TCW_MAXSTAGES; S >= 2; --S)
+            if (1024 + PWB + S * RX <= TCW_SMEM_MAX) {
+                s.SY = S;
+                s.smem_y = 1024 + PWB + S * RX;
+                break;
+            }
+        if (s.SY) break;
+    }
     if (!s.SY) return false;
-    s.smem_y = 1024 + PWB + s.SY * RX;
+    // two tensor-memory buffers when they fit 512 columns and one block fills an SM's
+    // shared memory (two blocks of one buffer each overlap the same way otherwise)
+    const int ycols = (f16 ? 2 : 1) * s.N16;
+    s.YBUF = (2 * ycols <= 512 && 2 * (s.smem_y + 12 * 1024) > 227 * 1024) ? 2 : 1;
     if ((f16 ? 2 : 1) * s.N16 > 512) return false;
     s.GPB = 64;
     // Y images: per walker and spin NTILES x KC chunks of NT x 128 bytes per part
@@ -1125,8 +1156,10 @@ cudaError_t tcw_images_of(cudaStream_t st, const Dims& d, const TcwShape& s, con
         const TcwSpin& sp = s.sp[q];
         if (sp.n == 0) continue;
         const int col0 = q ? d.nu : 0;
-        tcw_y_kernel<MODE><<<(unsigned)(wb * n_gblk), TCW_THREADS, s.smem_y, st>>>(
-            d.N, d.nt, col0, sp.n, s.G1, s.N16, s.KCX, s.SY, s.GPB, n_gblk, w0, phi, w.ximg, w.lexp, sp.NT, sp.GB,
+        const long long ngrp = (wb + s.WPBY - 1) / s.WPBY;
+        tcw_y_kernel<MODE><<<(unsigned)(ngrp * n_gblk), TCW_THREADS, s.smem_y, st>>>(
+            d.N, d.nt, col0, sp.n, s.G1, s.N16, s.KCX, s.SY, s.GPB, n_gblk, w0, s.WPBY, wb, s.YBUF, phi, w.ximg, w.lexp,
+            sp.NT, sp.GB,
             s.KC, sp.NTILES, w.yimg + s.yoff[q], w.yexp + s.yeoff[q], status, d.wait_polls);
         tcw_a_kernel<MODE><<<(unsigned)(wb * sp.MT), 256, 0, st>>>(d.N, d.nt, col0, sp.n, d.P, sp.PB, sp.MT, s.N16,
                                                                   s.KC, w0, Bm, w.aimg + s.aoff[q],
