@@ -184,9 +184,18 @@ typedef struct {
                            bits) on the CUDA cores, several proposals per SM; AFQMC_TRIAL_AUTO (0,
                            default): the tensor cores for 64 < N <= 128, else double-float (measured: the
                            tensor-core form is 5.9x faster at N = 120, 2.2x slower at N = 50) */
+    int overlap_form;   /* mixed precision, real trial: how the overlap matrices A_p = Phi_p^T phi_w behind
+                           the path signs and ratios (Eq. (25)-(26)) are formed.  AFQMC_OVERLAP_AUTO (0,
+                           default): on the tensor cores (each operand split into five 8-bit integer
+                           digits, the digit products of orders 0-4 accumulated exactly in FP32, combined
+                           in double-float: about 40 bits) where N <= 128 and n_up <= 40, else as
+                           AFQMC_OVERLAP_DF; AFQMC_OVERLAP_DF (1): compensated double-float sums on the
+                           CUDA cores (about 44 bits).  The LU, log-determinants and inverses are FP64
+                           either way */
 } afqmc_config;
 
 enum { AFQMC_TRIAL_AUTO = 0, AFQMC_TRIAL_DF = 1, AFQMC_TRIAL_TC = 2 };
+enum { AFQMC_OVERLAP_AUTO = 0, AFQMC_OVERLAP_DF = 1 };
 
 enum { AFQMC_TC_AUTO = 0, AFQMC_TC_PER_PAIR = 1, AFQMC_TC_WALKER = 2 };
 

@@ -24,6 +24,7 @@ PRECISIONS = {"fp64": 0, "bf16x3": 1, "fp16x3": 2, "fp16x6": 3}
 IMPORTANCE = {"hybrid": 0, "local_energy": 1}
 TC_FORMS = {"auto": 0, "per_pair": 1, "walker": 2}
 TRIAL_FORMS = {"auto": 0, "df": 1, "tc": 2}
+OVERLAP_FORMS = {"auto": 0, "df": 1}
 STATE_MAGIC = 0x4146514D43535431
 
 
@@ -41,6 +42,7 @@ class AfqmcConfig(ctypes.Structure):
         ("wait_polls", ctypes.c_int64), ("tc_form", ctypes.c_int),
         ("trial_alpha_re", ctypes.c_double), ("trial_alpha_im", ctypes.c_double), ("trial_slices", ctypes.c_int),
         ("trial_form", ctypes.c_int),
+        ("overlap_form", ctypes.c_int),
     ]
 
 
@@ -158,7 +160,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
                 pcn_beta=1.0, e_shift=0.0, kill_threshold=1e-10, walker_offset=0, rw_step=0.3, mlp_mix=0.1,
                 mlp_lr=1e-3, mlp_train=False, refine_tol=1e-4, importance="hybrid",
                 pop_period=0, rcache=False, wait_polls=0, tc_form="auto", trial_alpha=1.0,
-                trial_slices=1, trial_form="auto") -> AfqmcConfig:
+                trial_slices=1, trial_form="auto", overlap_form="auto") -> AfqmcConfig:
     lib = load_library()
     c = AfqmcConfig()
     lib.afqmc_config_default(ctypes.byref(c))
@@ -177,6 +179,7 @@ def make_config(N, n_up, n_dn, n_chol, K, n_walkers, n_paths, dtau, seed, *, n_s
     c.trial_alpha_re, c.trial_alpha_im = complex(trial_alpha).real, complex(trial_alpha).imag
     c.trial_slices = int(trial_slices)
     c.trial_form = TRIAL_FORMS[trial_form]
+    c.overlap_form = OVERLAP_FORMS[overlap_form]
     return c
 
 

@@ -92,6 +92,12 @@ static bool overlaps_in_df(const afqmc_config* c) {
            tc_kind(c) == 5;
 }
 
+// The overlap matrices of the double-float path formed on the tensor cores (overlap_tc).
+static bool overlaps_on_tc(const afqmc_config* c) {
+    return overlaps_in_df(c) && c->overlap_form == AFQMC_OVERLAP_AUTO && overlap_tc_supported(c->N, c->n_up) &&
+           (c->n_dn == 0 || overlap_tc_supported(c->N, c->n_dn));
+}
+
 // Double-float copies of `doubles` FP64 values (u_to_df).
 static cudaError_t df_copy(cudaStream_t s, const void* src, long long doubles, void* dst) {
     return u_to_df(s, doubles, static_cast<const double*>(src), dst);
@@ -245,6 +251,7 @@ static const char* check_config(const afqmc_config* c) {
     if (c->rcache != 0 && c->rcache != 1) return "rcache must be 0 or 1";
     if (c->wait_polls < 0 || c->wait_polls > (1ll << 31)) return "wait_polls must be in [0, 2^31]";
     if (c->trial_form < AFQMC_TRIAL_AUTO || c->trial_form > AFQMC_TRIAL_TC) return "unknown trial_form";
+    if (c->overlap_form < AFQMC_OVERLAP_AUTO || c->overlap_form > AFQMC_OVERLAP_DF) return "unknown overlap_form";
     if (c->rcache && c->precision != AFQMC_PRECISION_FP64) return "rcache needs precision FP64";
     if (c->rcache && !contract_fp64r_supported(c->N, c->n_up, c->n_dn))
         return "sizes too large for the cached half-rotation form (Theta and one matrix per warp, 4 warps per block)";
@@ -385,6 +392,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
         w.Phidf = take(pairs * phi_stride(d) * 8);
         w.phidf = take(W * N * nt * 16);
     }
+    if (overlaps_on_tc(c)) w.Aov = take(pairs * ((size_t)c->n_up * c->n_up + (size_t)c->n_dn * c->n_dn) * 16);
     w.logdet_prop = (double2*)take(pairs * 2 * 16);
     w.history = (double*)take((size_t)c->history_capacity * 4 * 8);
     w.reduce = (double*)take(8 * 8);
@@ -546,8 +554,9 @@ static afqmc_status mcmc_sweep(afqmc_ctx* ctx, const double2* orbitals, uint32_t
         CK(df_copy(s, w.Phiprop, d.pairs * phi_stride(d), w.Phidf));
         CK(df_copy(s, orbitals, d.W * (long long)d.N * d.nt * 2, w.phidf));
     }
+    if (w.Aov) CK(overlap_tc(s, d, w.Phidf, phi_stride(d), w.phidf, w.alive, w.Aov, w.status));
     CK(overlap_lu_both(s, d, w.Phiprop, phi_stride(d), orbitals, w.logdet_prop, nullptr, w.alive, w.status,
-                       d.pairs, d.P, OVL_THETA, nullptr, w.Phidf, w.phidf));
+                       d.pairs, d.P, OVL_THETA, nullptr, w.Phidf, w.phidf, false, w.Aov));
     if ((st = prof_mark(ctx, PH_MCMC_OVERLAP)) != AFQMC_OK) return st;
     CK(accept(s, d, p, w.counters, tag_acc, sweep, w.logdet_prop, w.xprop, w.Phiprop, w.alive, w.mlp.mu, w.mlp.logv,
               w.logov_cur, w.x, w.Phi, w.counters, w.rdirty));
@@ -577,9 +586,10 @@ static afqmc_status measure(afqmc_ctx* ctx, int part = 0) {
         CK(df_copy(s, w.Phi, d.pairs * phi_stride(d), w.Phidf));
         CK(df_copy(s, w.phi, d.W * (long long)d.N * d.nt * 2, w.phidf));
     }
+    if (w.Aov) CK(overlap_tc(s, d, w.Phidf, phi_stride(d), w.phidf, nullptr, w.Aov, w.status));
     CK(overlap_lu_both(s, d, w.Phi, phi_stride(d), w.phi, w.logdet, w.Theta, nullptr, w.status, d.pairs, d.P,
                        ovl, tck == 5 && w.refine_items ? w.refine_th2 : nullptr, w.Phidf, w.phidf,
-                       w.Phidf && ovl == OVL_TRIAL));
+                       w.Phidf && ovl == OVL_TRIAL, w.Aov));
     if ((st = prof_mark(ctx, PH_OVERLAP)) != AFQMC_OK) return st;
     if (part == 1) {
         if (tck != 5) return fail(AFQMC_ERR_ARG, "a split measurement needs the walker-side contraction");
@@ -795,8 +805,9 @@ static afqmc_status step_rest(afqmc_ctx* ctx) {
             CK(propagate(s, d, p, w.expT, w.Aplanes, w.phi, w.phi_new, w.alive, w.propbuf));   // Eq. (12)
         if ((st = prof_mark(ctx, PH_PROPAGATE)) != AFQMC_OK) return st;
         if (w.Phidf) CK(df_copy(s, w.phi_new, d.W * (long long)d.N * d.nt * 2, w.phidf));   // Phi's copy: measure
+        if (w.Aov) CK(overlap_tc(s, d, w.Phidf, phi_stride(d), w.phidf, w.alive, w.Aov, w.status));
         CK(overlap_lu_both(s, d, w.Phi, phi_stride(d), w.phi_new, w.logdet_new, nullptr, w.alive, w.status,
-                           d.pairs, d.P, OVL_THETA, nullptr, w.Phidf, w.phidf));
+                           d.pairs, d.P, OVL_THETA, nullptr, w.Phidf, w.phidf, false, w.Aov));
         CK(ratios(s, d, w.logov, w.logdet_new, w.sumS, w.logshift, w.alive, w.logov_cur, w.old_sum, w.ratio, w.Iabs));
         if ((st = prof_mark(ctx, PH_RATIO)) != AFQMC_OK) return st;
         if (ctx->cfg.proposal == AFQMC_PROPOSAL_MLP) {       // proposal conditioned on the new walkers

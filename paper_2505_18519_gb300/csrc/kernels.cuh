@@ -28,18 +28,30 @@ enum OverlapOutput { OVL_THETA = 0, OVL_TRIAL = 1, OVL_INVERSE = 2 };
 // complex entry, from u_to_df of the FP64 arrays): A = Phi^T phi is then formed
 // in double-float (compensated sums), the LU, log det and A^-1 stay FP64.  b_df
 // (with PhiD and OVL_TRIAL): B = Phi A^-T in double-float, written as (Re hi, Re
-// lo, Im hi, Im lo) per entry in place of the FP64 values.
+// lo, Im hi, Im lo) per entry in place of the FP64 values.  Apre (nullable): A of
+// every pair already formed (overlap_tc; n x n entries per pair, row-major, as
+// double-float (Re hi, Re lo, Im hi, Im lo)), read instead of the products.
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
                        long long pairs, int P, int trial_side = OVL_THETA, double* th2 = nullptr,
                        const int* list = nullptr, const int* n_list = nullptr, const void* PhiD = nullptr,
-                       const void* phiD = nullptr, bool b_df = false);
+                       const void* phiD = nullptr, bool b_df = false, const void* Apre = nullptr);
 // Both spins: one warp per pair (half a warp per spin) when n_up <= 16 and no
 // double-float products are asked for, else overlap_lu for each spin.  Same results.
+// Apre: both spins' A from overlap_tc (spin down at offset d.pairs n_up^2 entries).
 cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, long long Phi_stride,
                             const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
                             long long pairs, int P, int trial_side = OVL_THETA, double* th2 = nullptr,
-                            const void* PhiD = nullptr, const void* phiD = nullptr, bool b_df = false);
+                            const void* PhiD = nullptr, const void* phiD = nullptr, bool b_df = false,
+                            const void* Apre = nullptr);
+// overlap_tc.cu: A_p = Phi_p^T phi_w of every pair and spin on the tensor cores
+// (exact 8-bit digit products, about 40 bits) from the double-float copies PhiD,
+// phiD of the mixed-precision path, real trial, N <= 128, n <= 40 per spin;
+// written to Aout (d.pairs (n_up^2 + n_dn^2) entries of 16 bytes) for overlap_lu.
+// Pairs of walkers with alive[w] == 0 are skipped (alive nullable).
+bool overlap_tc_supported(int N, int n);
+cudaError_t overlap_tc(cudaStream_t s, const Dims& d, const void* PhiD, long long Phi_stride, const void* phiD,
+                       const int* alive, void* Aout, int* status);
 cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, double2* dst, const int* alive,
                              int* status, int n_walkers);
 // Phi = exp(S) Phi0 for `problems` symmetric S (FP64).  trial_orbitals runs the

@@ -83,7 +83,7 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
                                   double2* __restrict__ Theta, const int* __restrict__ alive, int* status,
                                   int trial_side, double* __restrict__ th2, const int* __restrict__ list,
                                   const int* __restrict__ n_list, int cphi, const dfl* __restrict__ PhiD,
-                                  const float4* __restrict__ phiD, int b_df) {
+                                  const float4* __restrict__ phiD, int b_df, const float4* __restrict__ Apre) {
     extern __shared__ double2 sm[];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
@@ -110,7 +110,16 @@ __global__ void overlap_lu_kernel(int N, int nu, int nt, int n, int col0, int sp
         return;
     }
     bool bad = false;
-    if (PhiD) {
+    if (Apre) {
+        // A formed on the tensor cores (overlap_tc), as double-float entries
+        const float4* Ap = Apre + pair * (long long)n * n;
+        for (int e = lane; e < n * n; e += 32) {
+            const float4 v = Ap[e];
+            const double2 t = cmk((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+            A[e] = t;
+            bad |= !isfinite(t.x) || !isfinite(t.y);
+        }
+    } else if (PhiD) {
         // double-float products (mixed-precision path, real trial, n <= 64): lane b owns
         // column b0 + b of A (column groups of 32), rows in chunks of 8; Phi entries are
         // broadcast loads, the walker's column one coalesced 16-byte load per row
@@ -363,7 +372,7 @@ static size_t overlap_smem_per_warp(int n, bool theta) {
 cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Phi, long long Phi_stride,
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
                        long long pairs, int P, int trial_side, double* th2, const int* list, const int* n_list,
-                       const void* PhiD, const void* phiD, bool b_df) {
+                       const void* PhiD, const void* phiD, bool b_df, const void* Apre) {
     int n = spin == 0 ? d.nu : d.nd;
     if (PhiD && (d.cphi || n > 64 || !phiD)) return cudaErrorInvalidValue;
     if (b_df && (!PhiD || trial_side != OVL_TRIAL)) return cudaErrorInvalidValue;
@@ -379,7 +388,8 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
     overlap_lu_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(d.N, d.nu, d.nt, n, col0, spin, pairs, P, Phi, Phi_stride,
                                                                phi, logdet, Theta, alive, status, trial_side, th2, list,
                                                                n_list, d.cphi, static_cast<const dfl*>(PhiD),
-                                                               static_cast<const float4*>(phiD), b_df ? 1 : 0);
+                                                               static_cast<const float4*>(phiD), b_df ? 1 : 0,
+                                                               static_cast<const float4*>(Apre));
     count_launches(1);
     return cudaGetLastError();
 }
@@ -604,13 +614,15 @@ __global__ void overlap_lu_both_kernel(int N, int nu, int nd, int nt, long long 
 cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, long long Phi_stride,
                             const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
                             long long pairs, int P, int trial_side, double* th2, const void* PhiD, const void* phiD,
-                            bool b_df) {
+                            bool b_df, const void* Apre) {
     // a half-warp per spin would leave the larger matrices short of lanes; the
     // double-float products run in the per-spin kernel
-    if (d.nu > 16 || PhiD) {
+    if (d.nu > 16 || PhiD || Apre) {
         for (int spin = 0; spin < 2; ++spin) {
+            const void* Ap = Apre ? static_cast<const float4*>(Apre) + (spin ? d.pairs * (long long)d.nu * d.nu : 0)
+                                  : nullptr;
             const cudaError_t e = overlap_lu(s, d, spin, Phi, Phi_stride, phi, logdet, Theta, alive, status, pairs, P,
-                                             trial_side, th2, nullptr, nullptr, PhiD, phiD, b_df);
+                                             trial_side, th2, nullptr, nullptr, PhiD, phiD, b_df, Ap);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;

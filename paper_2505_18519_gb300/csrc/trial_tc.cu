@@ -44,6 +44,7 @@
 
 #include "cheb.cuh"
 #include "df.cuh"
+#include "digits.cuh"
 #include "kernels.cuh"
 #include "tcgen05.cuh"
 
@@ -64,57 +65,6 @@ constexpr double TT_TOL = 1e-14;           // series truncation, relative to e^r
 __host__ __device__ constexpr uint32_t tt_vkb(int nb) { return (uint32_t)(TT_DIG + 1) * (uint32_t)nb * 128u; }
 __host__ __device__ constexpr size_t tt_smem_bytes(int nb) {
     return (size_t)TT_DIG * TT_SDIG + 2 * (size_t)tt_vkb(nb) + 1024;
-}
-
-// 2^e as a float, for |e| <= 126.
-__device__ __forceinline__ float tt_p2f(int e) {
-    e = max(-126, min(126, e));
-    return __int_as_float((e + 127) << 23);
-}
-
-// Exponent e with m 2^e in [128, 256) (0 for m = 0 or not finite).
-__device__ __forceinline__ int tt_exp(float m) {
-    if (!(m > 0.f) || !isfinite(m)) return 0;
-    return max(-100, min(100, 7 - ilogbf(m)));
-}
-
-// Byte offset of element (row r, K index k < 64) in a K-major 128-byte swizzled
-// region (rows of 128 bytes, groups of 8 rows 1024 bytes apart).
-__device__ __forceinline__ uint32_t tt_swz(int r, int k) {
-    return (uint32_t)(r >> 3) * 1024u + (uint32_t)(r & 7) * 128u + (uint32_t)((((k >> 3) ^ (r & 7)) << 4) | ((k & 7) << 1));
-}
-
-// The five digits of y = yh + yl (|y| < 257, scaled), as FP16 bit patterns.
-// Every subtraction below is exact; the one rounded addition (b) errs by
-// less than 2^-41.
-__device__ __forceinline__ void tt_digits(float yh, float yl, uint16_t (&d)[TT_DIG]) {
-    const float d0 = rintf(yh);
-    float a = yh - d0;                                    // |a| <= 1/2
-    const float d1 = rintf(a * 0x1p8f);
-    a -= d1 * 0x1p-8f;                                    // |a| <= 2^-9
-    const float d2 = rintf((a + yl) * 0x1p16f);
-    a -= d2 * 0x1p-16f;
-    const dfl r = df_two_sum(a, yl);                      // |r| <= about 2^-17
-    const float d3 = rintf(r.hi * 0x1p24f);
-    const float b = (r.hi - d3 * 0x1p-24f) + r.lo;
-    const float d4 = rintf(b * 0x1p32f);
-    d[0] = __half_as_ushort(__float2half_rn(d0));
-    d[1] = __half_as_ushort(__float2half_rn(d1));
-    d[2] = __half_as_ushort(__float2half_rn(d2));
-    d[3] = __half_as_ushort(__float2half_rn(d3));
-    d[4] = __half_as_ushort(__float2half_rn(d4));
-}
-
-// sum_q A_q 2^-8q of six exact integer accumulators, as a double-float value.
-__device__ __forceinline__ dfl tt_combine(float a0, float a1, float a2, float a3, float a4, float a5) {
-    const float t1 = a1 * 0x1p-8f, t2 = a2 * 0x1p-16f;
-    const float t3 = fmaf(a5, 0x1p-40f, fmaf(a4, 0x1p-32f, a3 * 0x1p-24f));
-    const dfl x = df_two_sum(t2, t3);
-    dfl y = df_two_sum(t1, x.hi);
-    y.lo += x.lo;
-    dfl z = df_two_sum(a0, y.hi);
-    z.lo += y.lo;
-    return df_quick(z.hi, z.lo);
 }
 
 // 32 lanes x C (4 or 8) columns of 32-bit data from tensor memory.
@@ -178,7 +128,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
             const float cf = (float)cst;
             for (int j = 0; j < N; ++j) m = fmaxf(m, fabsf(S32[(size_t)j * N + tid] - (j == tid ? cf : 0.f)));   // S symmetric
         }
-        sexp[tid] = tt_exp(m * (float)(1.0 / rho));
+        sexp[tid] = dg_exp(m * (float)(1.0 / rho));
     }
     __syncthreads();   // the copy is read for the last time above
 
@@ -192,7 +142,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         // unit u = (row r, 8 consecutive columns 8 uc .. 8 uc + 7)
         for (int u = tid - 32; u < 128 * 16; u += TT_THREADS - 32) {
             const int r = u >> 4, uc = u & 15;
-            const float sc_r = tt_p2f(sexp[r]);
+            const float sc_r = dg_p2f(sexp[r]);
             uint16_t dg[TT_DIG][8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
@@ -204,11 +154,11 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
                     x = df_mul(x, ird);
                 }
                 uint16_t dd[TT_DIG];
-                tt_digits(x.hi * sc_r, x.lo * sc_r, dd);
+                dg_digits(x.hi * sc_r, x.lo * sc_r, dd);
 #pragma unroll
                 for (int q = 0; q < TT_DIG; ++q) dg[q][t] = dd[q];
             }
-            const uint32_t off = (uint32_t)(uc >> 3) * TT_SKB + tt_swz(r, (uc & 7) * 8);
+            const uint32_t off = (uint32_t)(uc >> 3) * TT_SKB + dg_swz(r, (uc & 7) * 8);
 #pragma unroll
             for (int q = 0; q < TT_DIG; ++q) {
                 uint4 v;
@@ -255,25 +205,25 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     // digits of V (scaled by 2^f) into VD: digit q of element (row, a) at row q NB + a,
     // K index row
     auto write_vdigits = [&](const dfl (&V)[CPT], int f) {
-        const float sf = tt_p2f(f);
+        const float sf = dg_p2f(f);
         uint8_t* vk = VD + (size_t)(row >> 6) * VKB;
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             uint16_t dd[TT_DIG];
-            tt_digits(V[c].hi * sf, V[c].lo * sf, dd);
+            dg_digits(V[c].hi * sf, V[c].lo * sf, dd);
 #pragma unroll
             for (int q = 0; q < TT_DIG; ++q)
-                *reinterpret_cast<uint16_t*>(vk + tt_swz(q * NB + col0 + c, row & 63)) = dd[q];
+                *reinterpret_cast<uint16_t*>(vk + dg_swz(q * NB + col0 + c, row & 63)) = dd[q];
         }
     };
     // the block of zeros (digit 5) in both K blocks
     for (int e = tid; e < 2 * NB * 128 / 16; e += TT_THREADS) {
         const int kb = e / (NB * 8), r = (e / 8) % NB, u = e % 8;
-        *reinterpret_cast<uint4*>(VD + (size_t)kb * VKB + tt_swz(TT_DIG * NB + r, 8 * u)) = make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(VD + (size_t)kb * VKB + dg_swz(TT_DIG * NB + r, 8 * u)) = make_uint4(0, 0, 0, 0);
     }
     reduce2(mx, ss, 0);   // its barrier also publishes the coefficients and the digits of S'
     const float grow_limit = 1.5625f * ss + 1e-30f;
-    int fexp = tt_exp(mx);
+    int fexp = dg_exp(mx);
 #pragma unroll
     for (int c = 0; c < CPT; ++c) acc[c] = df_mul(coefd[0], V1[c]);
     write_vdigits(V1, fexp);
@@ -319,7 +269,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         }
         tc::fence_after_sync();
         // 3b. t V_{k-1} = S' V_{k-1} -> V_k, acc
-        const float sc_row = tt_p2f(-(erow + fexp));
+        const float sc_row = dg_p2f(-(erow + fexp));
         const dfl ck = coefd[k];
         mx = 0.f;
         ss = 0.f;
@@ -332,7 +282,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
 #pragma unroll
             for (int t = 0; t < CH; ++t) {
                 const int c = CH * ch + t;
-                const dfl z = tt_combine(A[0][t], A[1][t], A[2][t], A[3][t], A[4][t], A[5][t]);
+                const dfl z = dg_combine6(A[0][t], A[1][t], A[2][t], A[3][t], A[4][t], A[5][t]);
                 const dfl u = {z.hi * sc_row, z.lo * sc_row};
                 const dfl vn = k == 1 ? u : df_add(dfl{2.f * u.hi, 2.f * u.lo}, df_neg(V0[c]));
                 acc[c] = df_add(acc[c], df_mul(ck, vn));
@@ -349,7 +299,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
             break;
         }
         if (k == m) break;
-        fexp = tt_exp(mx);
+        fexp = dg_exp(mx);
         write_vdigits(V1, fexp);
         tc::fence_proxy_async();
         tc::fence_before_sync();

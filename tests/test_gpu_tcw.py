@@ -97,6 +97,49 @@ def test_general_walker_side_form_bf16(name):
     assert np.max(np.abs(obs["force_bias"] - m["v_bar"])[live]) < 1e-4
 
 
+@pytest.mark.parametrize("name", ["c0", "ragged", "one_spin", "one_electron_each", "n70_two_k_chunks", "wide"])
+def test_tensor_core_overlaps_match_double_float(name):
+    """The overlap matrices A_p = Phi_p^T phi_w on the tensor cores (exact 8-bit digit
+    products, about 40 bits; overlap_form "auto") against the compensated
+    double-float sums (overlap_form "df") from the same state: the log-overlaps of a
+    measurement agree to 1e-10 (an entry's error of about 2^-38 of
+    N max|Phi| max|phi|, times ||A^-1|| in log det A; 4.4e-11 measured at N = 8) and
+    both match the oracle to 1e-9; two steps (ratio and Metropolis overlaps from the
+    tensor cores as well) take the same Metropolis decisions and give the same
+    weights to 1e-9 and paths and walkers to 1e-10."""
+    spec, W, P, dtau, seed_off = SYSTEMS[name]
+    seed = 500 + seed_off
+    s = ai.make_system(spec)
+    ham = oa.prepare(s.h, s.L, s.Phi0, s.U, spec.n_up, spec.n_dn, dtau)
+    ocfg = oa.OracleConfig(dtau=dtau, n_walkers=W, n_paths=P, seed=seed, n_burn=2)
+    ost = oa.init(ham, ocfg)
+    ost, _ = oa.step(ham, ocfg, ost)
+    m = oa.measure(ham, ost)
+    res = {}
+    for form in ("auto", "df"):
+        cfg = lib.make_config(spec.N, spec.n_up, spec.n_dn, spec.n_chol, spec.K, W, P, dtau, seed, n_burn=2,
+                              precision="fp16x6", tc_form="walker", wait_polls=1 << 22, overlap_form=form)
+        ctx = lib.Context(cfg, s.h, s.L, s.Phi0, s.U)
+        ctx.load_state_arrays(dict(step=ost.step, phi_up=ost.phi_up, phi_dn=ost.phi_dn, weight=ost.weight, x=ost.x,
+                                   Phi=ost.Phi))
+        ctx.energy()
+        lo = ctx.observables()["logov"]
+        ctx.step(2)
+        res[form] = (lo, ctx.state_arrays(), ctx.stats()["status"])
+        ctx.close()
+    (lt, gt, st_t), (ld, gd, st_d) = res["auto"], res["df"]
+    assert st_t == 0 and st_d == 0
+    print("%s: |dlogov| tc-df %.2e, tc-oracle %.2e" % (name, np.max(np.abs(lt - ld)),
+                                                      np.max(np.abs(lt.real - m["logov"].real))))
+    assert np.max(np.abs(lt - ld)) < 1e-10
+    assert np.max(np.abs(lt.real - m["logov"].real)) < 1e-9
+    assert np.array_equal(gt["x"], gd["x"])
+    assert np.array_equal(gt["weight"] == 0, gd["weight"] == 0)
+    assert np.allclose(gt["weight"], gd["weight"], rtol=1e-9, atol=0)
+    assert np.max(np.abs(gt["Phi"] - gd["Phi"])) < 1e-10
+    assert np.max(np.abs(gt["phi_up"] - gd["phi_up"])) < 1e-10
+
+
 # the systems whose three-part operands fit the walker-side form's shared memory (45
 # electrons in one spin do not: GEMM-Z's ring and transpose exceed it)
 FP16X6_SYSTEMS = [n for n in SYSTEMS if n != "one_spin_n150"]

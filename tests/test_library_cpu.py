@@ -175,3 +175,22 @@ def test_trial_form_field_reaches_the_library(L):
     c = lib.make_config(50, 10, 10, 250, 50, 4, 8, 0.005, 1, precision="fp16x6")
     c.trial_form = 7
     assert lib.workspace_bytes(c) == 0
+
+
+def test_overlap_form_field_reaches_the_library(L):
+    """overlap_form selects how the mixed path forms the overlap matrices: the
+    tensor-core form holds them in the work space (16 bytes per entry, both spins),
+    the double-float form does not; an unknown value is refused."""
+    N, nu, nd, W, P = 120, 24, 24, 8, 16
+    a = lib.workspace_bytes(lib.make_config(N, nu, nd, 600, N, W, P, 0.005, 1, precision="fp16x6"))
+    d = lib.workspace_bytes(lib.make_config(N, nu, nd, 600, N, W, P, 0.005, 1, precision="fp16x6",
+                                            overlap_form="df"))
+    assert a - d >= W * P * (nu * nu + nd * nd) * 16
+    assert a - d < W * P * (nu * nu + nd * nd) * 16 + 512
+    # beyond the tensor-core form's sizes (N > 128) both forms are the double-float one
+    big = [lib.workspace_bytes(lib.make_config(200, 40, 40, 1000, 200, 4, 4, 0.005, 1, precision="fp16x6",
+                                               overlap_form=f)) for f in ("auto", "df")]
+    assert big[0] == big[1] > 0
+    c = lib.make_config(N, nu, nd, 600, N, W, P, 0.005, 1, precision="fp16x6")
+    c.overlap_form = 3
+    assert lib.workspace_bytes(c) == 0
