@@ -71,6 +71,6 @@ def test_headline_contraction_summary_gives_its_traffic(bench):
     recorded = fields["source_sha256_16"].strip().strip("`")
     got = bench.tcw_traffic(1024, 64)
     if recorded == bench.kernel_digest(src, end, start):
-        assert got == pytest.approx(1589444 * 1024 * 64)
+        assert got == pytest.approx(1837315 * 1024 * 64)
     else:
         assert got is None
