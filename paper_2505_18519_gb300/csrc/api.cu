@@ -98,6 +98,15 @@ static bool overlaps_on_tc(const afqmc_config* c) {
            (c->n_dn == 0 || overlap_tc_supported(c->N, c->n_dn));
 }
 
+// The proposal matrices S formed on the tensor cores (sprop_tc): for the tensor-core
+// trial orbitals only, whose digits of S' carry the same precision.
+static bool s_on_tc_cfg(const afqmc_config* c) {
+    const int f = c->trial_form;
+    return c->precision != AFQMC_PRECISION_FP64 && !general_trial(c) && f != AFQMC_TRIAL_DF &&
+           trial_orbitals_tc_supported(c->N, c->n_up) && (f == AFQMC_TRIAL_TC || c->N > 64) &&
+           sprop_tc_supported(c->K, (long long)c->N * c->N);
+}
+
 // Double-float copies of `doubles` FP64 values (u_to_df).
 static cudaError_t df_copy(cudaStream_t s, const void* src, long long doubles, void* dst) {
     return u_to_df(s, doubles, static_cast<const double*>(src), dst);
@@ -393,6 +402,7 @@ static size_t layout(const afqmc_config* c, char* base, Workspace* ws) {
         w.phidf = take(W * N * nt * 16);
     }
     if (overlaps_on_tc(c)) w.Aov = take(pairs * ((size_t)c->n_up * c->n_up + (size_t)c->n_dn * c->n_dn) * 16);
+    if (s_on_tc_cfg(c)) w.Uimg = take(sprop_u_image_bytes(c->K, (long long)c->N * c->N));
     w.logdet_prop = (double2*)take(pairs * 2 * 16);
     w.history = (double*)take((size_t)c->history_capacity * 4 * 8);
     w.reduce = (double*)take(8 * 8);
@@ -480,6 +490,8 @@ static cudaError_t form_S(afqmc_ctx* ctx, const double* X, long long M) {
     const Dims& d = ctx->d;
     Workspace& w = ctx->ws;
     const long long NN = (long long)d.N * d.N;
+    if (w.Uimg && trial_on_tc(ctx) && s_in_df(ctx))
+        return sprop_tc(ctx->stream, M, d.K, NN, X, w.Uimg, w.Sprop, w.status, d.wait_polls);
     if (s_in_df(ctx)) return gemm_df(ctx->stream, (int)M, (int)NN, d.K, X, w.Udf, w.Sprop, w.xdf);
     gemm_nn_f64(ctx->stream, (int)M, (int)NN, d.K, 1.0, X, d.K, w.U, NN, 0.0, w.Sprop, NN);
     return cudaGetLastError();
@@ -718,6 +730,10 @@ extern "C" afqmc_status afqmc_init_trial(const afqmc_config* cfg, const double* 
                       (w.hdf && (e = u_to_df(s, (long long)NN, w.h, w.hdf)) != cudaSuccess) ||
                       (w.expTdf && (e = u_to_df(s, (long long)NN, w.expT, w.expTdf)) != cudaSuccess))) {
             st = fail(AFQMC_ERR_CUDA, "double-float copies of U, L and exp(-tau T/2): %s", cudaGetErrorString(e));
+            break;
+        }
+        if (w.Uimg && (e = sprop_u_images(s, d.K, NN, w.U, w.Uimg)) != cudaSuccess) {
+            st = fail(AFQMC_ERR_CUDA, "digit images of U: %s", cudaGetErrorString(e));
             break;
         }
         if ((e = trial_samples(ctx, w.xprop, d.W, w.Phiprop, nullptr, 1)) != cudaSuccess) {

@@ -192,6 +192,7 @@ struct Workspace {
     void* Phidf;          // W*P*N*n_up  8-byte pairs: Phi at a measurement, then Phi(x') in a sweep
     void* phidf;          // W*N*nt      16 bytes per complex entry: the walkers the overlap reads
     void* Aov;            // W*P*(n_up^2+n_dn^2) 16-byte double-float entries: A_p from the tensor cores
+    void* Uimg;           // digit images of U and its column exponents (proposal matrices on the tensor cores)
     double* Aplanes;  // 2W*N*N  rows 2w: sum_g Re(y) L_g ; 2w+1: sum_g Im(y) L_g
                       //         (double-float pairs, 8 bytes each, on the mixed-precision path)
     double2* phi_new; // W*N*nt

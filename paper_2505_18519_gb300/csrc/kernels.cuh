@@ -84,6 +84,15 @@ cudaError_t trial_orbitals_df_list(cudaStream_t s, int N, int nu, const double* 
 // (workspace of `problems` + 1 ints) and redone by the double-float kernel.
 // lim: polls of an mbarrier wait before it gives up (0: 2^26).
 bool trial_orbitals_tc_supported(int N, int nu);
+// sprop_tc.cu: S = X U (M rows of X, K <= 128 variables, NN = N^2 columns) on the
+// tensor cores as exact 8-bit digit products (about 40 bits), written as
+// double-float pairs (8 bytes per entry) like gemm_df; img holds U's digit images
+// and column exponents (sprop_u_image_bytes, formed once by sprop_u_images).
+bool sprop_tc_supported(int K, long long NN);
+size_t sprop_u_image_bytes(int K, long long NN);
+cudaError_t sprop_u_images(cudaStream_t s, int K, long long NN, const double* U, void* img);
+cudaError_t sprop_tc(cudaStream_t s, long long M, int K, long long NN, const double* X, const void* img, void* S,
+                     int* status, uint32_t lim);
 size_t trial_orbitals_tc_smem(int nu);
 // counters[9] += the terms of every finished problem, counters[10] += the problems redone.
 cudaError_t trial_orbitals_tc(cudaStream_t s, int N, int nu, long long problems, const double* S_all, bool s_is_df,
