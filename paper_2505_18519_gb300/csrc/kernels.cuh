@@ -50,6 +50,13 @@ cudaError_t overlap_lu_both(cudaStream_t s, const Dims& d, const double* Phi, lo
 // written to Aout (d.pairs (n_up^2 + n_dn^2) entries of 16 bytes) for overlap_lu.
 // Pairs of walkers with alive[w] == 0 are skipped (alive nullable).
 bool overlap_tc_supported(int N, int n);
+// overlap_lu_df.cu: the LU, log det A and (with Theta) A^-1, ||A^-1||_F^2 (th2) and
+// B = Phi A^-T (double-float, OVL_TRIAL layout) of one spin from the tensor-core
+// A (Apre of that spin), in double-float arithmetic on the FP32 pipe; overlap_lu
+// hands its calls with Apre to it.
+cudaError_t overlap_lu_df(cudaStream_t s, const Dims& d, int spin, const void* Apre, double2* logdet, double2* Theta,
+                          const int* alive, int* status, long long pairs, int P, double* th2, const void* PhiD,
+                          long long Phi_stride);
 cudaError_t overlap_tc(cudaStream_t s, const Dims& d, const void* PhiD, long long Phi_stride, const void* phiD,
                        const int* alive, void* Aout, int* status);
 cudaError_t reorthonormalise(cudaStream_t s, const Dims& d, const double2* src, double2* dst, const int* alive,

@@ -373,6 +373,9 @@ cudaError_t overlap_lu(cudaStream_t s, const Dims& d, int spin, const double* Ph
                        const double2* phi, double2* logdet, double2* Theta, const int* alive, int* status,
                        long long pairs, int P, int trial_side, double* th2, const int* list, const int* n_list,
                        const void* PhiD, const void* phiD, bool b_df, const void* Apre) {
+    // A from the tensor cores: LU, inverse and B in double-float (overlap_lu_df.cu)
+    if (Apre && !list && !d.cphi && (!Theta || (trial_side == OVL_TRIAL && b_df)))
+        return overlap_lu_df(s, d, spin, Apre, logdet, Theta, alive, status, pairs, P, th2, PhiD, Phi_stride);
     int n = spin == 0 ? d.nu : d.nd;
     if (PhiD && (d.cphi || n > 64 || !phiD)) return cudaErrorInvalidValue;
     if (b_df && (!PhiD || trial_side != OVL_TRIAL)) return cudaErrorInvalidValue;
