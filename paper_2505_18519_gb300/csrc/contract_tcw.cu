@@ -396,22 +396,24 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
             const bool ok = wait_or_fail(&dfull[buf], (uint32_t)((gi / NBUF) & 1), lim, &fail);
             if (tc::named_sync_or<TCW_EPI>(!ok)) { failed = true; break; }
             tc::fence_after_sync();
-            // pass 1: the largest |Y| of column b (its Re and Im lanes)
+            // pass 1: the largest |Y| of column b (its Re and Im lanes); up to 32 columns
+            // (and their corrections) per wait for the tensor-memory loads
             float mx = 0.f;
-            for (int j0 = 0; j0 < N16; j0 += 16) {
-                float v[16];
-                tc::tmem_ld16(taddr + lb + (uint32_t)j0, v);
+            for (int j0 = 0; j0 < N16; j0 += 32) {
+                const bool two = j0 + 16 < N16;               // uniform across the warp
+                float v[32], w[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = w[q] = 0.f;
+                tc::tmem_ld16(taddr + lb + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(v));
+                if (two) tc::tmem_ld16(taddr + lb + (uint32_t)(j0 + 16), *reinterpret_cast<float(*)[16]>(v + 16));
                 if (F16) {
-                    float w[16];
-                    tc::tmem_ld16(taddr + lb + (uint32_t)(N16 + j0), w);
-                    tc::tmem_ld_wait();
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] += w[q];
-                } else {
-                    tc::tmem_ld_wait();
+                    tc::tmem_ld16(taddr + lb + (uint32_t)(N16 + j0), *reinterpret_cast<float(*)[16]>(w));
+                    if (two)
+                        tc::tmem_ld16(taddr + lb + (uint32_t)(N16 + j0 + 16), *reinterpret_cast<float(*)[16]>(w + 16));
                 }
+                tc::tmem_ld_wait();
 #pragma unroll
-                for (int q = 0; q < 16; ++q) mx = fmaxf(mx, fabsf(v[q]));
+                for (int q = 0; q < 32; ++q) mx = fmaxf(mx, fabsf(v[q] + w[q]));
             }
             mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
             const int et = F16 ? exp_into(mx, 7) : 0;   // image = D_Y 2^et
@@ -422,22 +424,27 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
             const uint32_t neg = ri ? 0x8000u : 0u;
             const uint32_t nn = neg | (neg << 16);
             const float mul = p2f(et);
-            // pass 2: scale, split, and write 8 K elements (16 bytes) at a time
-            for (int j0 = 0; j0 < N16; j0 += 16) {
-                float v[16];
-                tc::tmem_ld16(taddr + lb + (uint32_t)j0, v);
-                if (F16) {
-                    float w[16];
-                    tc::tmem_ld16(taddr + lb + (uint32_t)(N16 + j0), w);
-                    tc::tmem_ld_wait();
+            // pass 2: scale, split, and write 8 K elements (16 bytes) at a time; up to 32
+            // columns per wait for the tensor-memory loads
+            for (int j0 = 0; j0 < N16; j0 += 32) {
+                const bool two = j0 + 16 < N16;               // uniform across the warp
+                float v[32], w[32];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] += w[q];
-                } else {
-                    tc::tmem_ld_wait();
+                for (int q = 0; q < 32; ++q) v[q] = w[q] = 0.f;
+                tc::tmem_ld16(taddr + lb + (uint32_t)j0, *reinterpret_cast<float(*)[16]>(v));
+                if (two) tc::tmem_ld16(taddr + lb + (uint32_t)(j0 + 16), *reinterpret_cast<float(*)[16]>(v + 16));
+                if (F16) {
+                    tc::tmem_ld16(taddr + lb + (uint32_t)(N16 + j0), *reinterpret_cast<float(*)[16]>(w));
+                    if (two)
+                        tc::tmem_ld16(taddr + lb + (uint32_t)(N16 + j0 + 16), *reinterpret_cast<float(*)[16]>(w + 16));
                 }
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] += w[q];
                 if (row_ok) {
 #pragma unroll
-                    for (int half = 0; half < 2; ++half) {
+                    for (int half = 0; half < 4; ++half) {
+                        if (half >= 2 && !two) break;
                         uint16_t pt[NP][8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
