@@ -20,10 +20,12 @@
 //
 // One block of 512 threads per problem (the series as in cheb.cuh):
 //   1. S (FP64 or double-float pairs) -> an FP32 copy in shared memory; the
-//      Gershgorin interval and the Lanczos estimate [c - rho, c + rho]; the row
+//      Gershgorin interval and the Lanczos estimate [c - rho, c + rho] (warps 0-3,
+//      one row per thread, without block-wide barriers); the row
 //      exponents e_i of the shifted and scaled S' = (S - c) / rho, whose product
 //      with V is the Chebyshev argument t V itself.
-//   2. thread 0: the coefficients; warps 1-15: the digits of S' (five 128 x 128
+//   2. warp 0: the coefficients (Miller's recurrence in double-float); warps 1-15:
+//      the digits of S' (five 128 x 128
 //      FP16 operands, K-major in the 128-byte swizzle, 160 KB) over the copy.
 //   3. per term k: thread 0 issues the 19 digit products as 5 K/16 MMAs
 //      (digit i of S', M = 128 rows, against digits 0 .. 5 - i of V side by
@@ -68,6 +70,180 @@ __host__ __device__ constexpr size_t tt_smem_bytes(int nb) {
 }
 
 // 32 lanes x C (4 or 8) columns of 32-bit data from tensor memory.
+// Warp sums and extrema (every lane gets the result).
+__device__ __forceinline__ float tt_wsum(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+__device__ __forceinline__ dfl tt_wsum_df(dfl v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const dfl o = {__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
+        v = df_add(v, o);
+    }
+    return v;
+}
+
+// The spectral intervals of cheb_interval (cheb.cuh) for N <= 128, computed by warps
+// 0-3 alone (one row i = thread of S and of the Lanczos vectors each, synchronised by
+// named barrier 1 over their 128 threads): the Gershgorin interval of S, and the
+// Lanczos estimate from the same start vector, LZ_STEPS steps, S v read as columns of
+// the symmetric S (consecutive threads, consecutive words), each dot product in four
+// interleaved partial sums.  red: 2 x 4 floats of scratch.  Results in sc, valid for
+// the 128 threads after the call.
+__device__ void tt_interval_q(int N, const float* S32, ChebScratch& sc, float (*red)[4]) {
+    const int i = threadIdx.x, lane = i & 31, w = i >> 5;
+    const bool ok = i < N;
+    // the sum (p = 0, 1: scratch slot) or min / max over the 128 threads
+    auto qsum = [&](float v, int p) {
+        v = tt_wsum(v);
+        if (lane == 0) red[p][w] = v;
+        tc::named_sync<128>();
+        return (red[p][0] + red[p][1]) + (red[p][2] + red[p][3]);
+    };
+    float lo = INFINITY, hi = -INFINITY;
+    if (ok) {
+        float r0 = 0.f, r1 = 0.f;
+        for (int j = 0; j + 1 < N; j += 2) {
+            r0 += j != i ? fabsf(S32[(size_t)j * N + i]) : 0.f;
+            r1 += j + 1 != i ? fabsf(S32[(size_t)(j + 1) * N + i]) : 0.f;
+        }
+        if (N & 1) r0 += N - 1 != i ? fabsf(S32[(size_t)(N - 1) * N + i]) : 0.f;
+        const float r = r0 + r1;
+        const float dgi = S32[(size_t)i * N + i];
+        const float slack = 1e-5f * (r + fabsf(dgi)) + 1e-30f;   // keeps the FP32 sums a bound
+        lo = dgi - r - slack;
+        hi = dgi + r + slack;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    if (lane == 0) { red[0][w] = lo; red[1][w] = hi; }
+    tc::named_sync<128>();
+    lo = fminf(fminf(red[0][0], red[0][1]), fminf(red[0][2], red[0][3]));
+    hi = fmaxf(fmaxf(red[1][0], red[1][1]), fmaxf(red[1][2], red[1][3]));
+    tc::named_sync<128>();                                   // red is free again
+    float v0 = 0.f, v1 = ok ? 1.f + 0.5f * __sinf(1.3f * (float)i + 0.7f) : 0.f;
+    v1 *= rsqrtf(qsum(v1 * v1, 0));
+    if (ok) sc.lz_v[1][i] = v1;
+    tc::named_sync<128>();
+    int ksteps = 0;
+    float beta_prev = 0.f;
+    for (int j = 0; j < LZ_STEPS && j < N; ++j) {
+        float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
+        if (ok) {
+            int q = 0;
+            for (; q + 3 < N; q += 4) {
+                w0 = fmaf(S32[(size_t)q * N + i], sc.lz_v[1][q], w0);
+                w1 = fmaf(S32[(size_t)(q + 1) * N + i], sc.lz_v[1][q + 1], w1);
+                w2 = fmaf(S32[(size_t)(q + 2) * N + i], sc.lz_v[1][q + 2], w2);
+                w3 = fmaf(S32[(size_t)(q + 3) * N + i], sc.lz_v[1][q + 3], w3);
+            }
+            for (; q < N; ++q) w0 = fmaf(S32[(size_t)q * N + i], sc.lz_v[1][q], w0);
+        }
+        float wv = (w0 + w1) + (w2 + w3);
+        const float alpha = qsum(wv * v1, 1);               // its barrier: every thread has read lz_v
+        wv = wv - alpha * v1 - beta_prev * v0;
+        const float beta = sqrtf(qsum(wv * wv, 0));
+        if (i == 0) { sc.lz_a[j] = alpha; sc.lz_b[j] = beta; }
+        ksteps = j + 1;
+        if (!(beta > 1e-6f * (fabsf(alpha) + 1e-30f))) break;   // invariant subspace found (uniform)
+        v0 = v1;
+        v1 = wv / beta;
+        if (ok) sc.lz_v[1][i] = v1;
+        beta_prev = beta;
+        tc::named_sync<128>();
+    }
+    tc::named_sync<128>();
+    if (i == 0) {
+        float tl = INFINITY, th = -INFINITY;
+        for (int j = 0; j < ksteps; ++j) {
+            const float r = (j > 0 ? fabsf(sc.lz_b[j - 1]) : 0.f) + fabsf(sc.lz_b[j]);
+            tl = fminf(tl, sc.lz_a[j] - r);
+            th = fmaxf(th, sc.lz_a[j] + r);
+        }
+        const float margin = 0.02f * (th - tl) + 1e-6f;
+        const double elo = fmax((double)lo, (double)(tl - margin)), ehi = fmin((double)hi, (double)(th + margin));
+        sc.gers_c = 0.5 * ((double)lo + (double)hi);
+        sc.gers_rho = fmax(0.5 * ((double)hi - (double)lo), 1e-3);
+        if (ehi > elo && isfinite(elo) && isfinite(ehi)) {
+            sc.est_c = 0.5 * (elo + ehi);
+            sc.est_rho = fmax(0.5 * (ehi - elo), 1e-3);
+        } else {
+            sc.est_c = sc.gers_c;
+            sc.est_rho = sc.gers_rho;
+        }
+    }
+}
+
+// The Chebyshev coefficients of cheb_coefs (cheb.cuh: exp on [c - rho, c + rho],
+// e^(c + rho) [I_0(rho) + 2 sum_k I_k(rho) T_k] / e^rho, truncated at the first k with
+// I_k(rho) < tol e^rho), in double-float arithmetic on the FP32 pipe by the calling
+// warp: Miller's backward recurrence I_(k-1) = (2k / rho) I_k + I_(k+1) on lane 0 (all
+// terms positive, so each step adds a rounding error of about 2^-46 and nothing
+// cancels), rescaled by 2^-64 whenever it passes 2^64 with the count of rescalings
+// kept per entry; the normalising sum, the truncation and the scaling by the warp.
+// coefd[0 .. m] and the returned m are valid in every lane of the warp.
+__device__ int tt_coefs_warp(double c, double rho, double tol, dfl* coefd, int* shift, int* status) {
+    const int lane = threadIdx.x & 31;
+    int start = (int)ceil(rho) + 48;
+    if (!isfinite(rho) || start > CHEB_DF_MAX) {
+        if (lane == 0) atomicOr(status, STATUS_NONFINITE);
+        start = CHEB_DF_MAX;
+    }
+    if (lane == 0) {
+        const dfl r2 = df_from(2.0 / rho);
+        dfl ip1 = {0.f, 0.f}, ik = {0x1p-60f, 0.f};
+        int sh = 0;
+        for (int k = start; k >= 1; --k) {
+            coefd[k] = ik;
+            shift[k] = sh;
+            const dfl im1 = df_add(df_mul(df_mul(dfl{(float)k, 0.f}, r2), ik), ip1);
+            ip1 = ik;
+            ik = im1;
+            if (ik.hi > 0x1p64f) {
+                ik = dfl{ik.hi * 0x1p-64f, ik.lo * 0x1p-64f};
+                ip1 = dfl{ip1.hi * 0x1p-64f, ip1.lo * 0x1p-64f};
+                ++sh;
+            }
+        }
+        coefd[0] = ik;
+        shift[0] = sh;
+    }
+    __syncwarp();
+    const int S = shift[0];
+    // entry k in the final units (the entries stored before a rescaling scaled down with
+    // it; two or more rescalings put an entry below 2^-64 of the largest: negligible)
+    auto fin = [&](int k) -> dfl {
+        const int d = S - shift[k];
+        if (d == 0) return coefd[k];
+        if (d >= 2) return dfl{0.f, 0.f};
+        return dfl{coefd[k].hi * 0x1p-64f, coefd[k].lo * 0x1p-64f};
+    };
+    dfl part = {0.f, 0.f};
+    for (int k = 1 + lane; k <= start; k += 32) part = df_add(part, fin(k));
+    part = tt_wsum_df(part);
+    const dfl norm = df_add(fin(0), dfl{2.f * part.hi, 2.f * part.lo});   // e^rho in these units
+    const float thr = (float)(tol * df_to(norm));
+    int m = start;
+    for (int k = 1 + lane; k <= start; k += 32)
+        if (fin(k).hi < thr) { m = k; break; }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, off));
+    const dfl q = df_from(exp(c + rho) / df_to(norm));
+    // every lane has finished reading other lanes' entries (the reductions above); each
+    // now scales its own
+    for (int k = lane; k <= m; k += 32) {
+        const dfl v = df_mul(fin(k), q);
+        coefd[k] = k == 0 ? v : dfl{2.f * v.hi, 2.f * v.lo};
+    }
+    __syncwarp();
+    return m;
+}
+
 template <int C>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[C]) {
     if constexpr (C == 8) tc::tmem_ld8(taddr, v);
@@ -91,7 +267,8 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     uint8_t* VD = sm + (size_t)TT_DIG * TT_SDIG;         // digits of V
     float* S32 = reinterpret_cast<float*>(sm);           // FP32 copy of S (steps 1-2 only)
     __shared__ ChebScratch sc;
-    __shared__ double coef[CHEB_DF_MAX + 2];
+    __shared__ int cshift[CHEB_DF_MAX + 2];
+    __shared__ float ired[2][4];
     __shared__ dfl coefd[CHEB_DF_MAX + 2];
     __shared__ int sexp[128];
     __shared__ float redm[2][NW], reds[2][NW];
@@ -120,7 +297,8 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     const dfl* Sgd = reinterpret_cast<const dfl*>(Sg);
     for (int e = tid; e < N * N; e += TT_THREADS) S32[e] = s_is_df ? Sgd[e].hi : (float)Sg[e];
     __syncthreads();
-    cheb_interval(N, S32, 1, sc);
+    if (warp < 4) tt_interval_q(N, S32, sc, ired);          // the other warps wait at the barrier
+    __syncthreads();
     const double cst = sc.est_c, rho = sc.est_rho;
     if (tid < 128) {
         float m = 0.f;
@@ -132,12 +310,11 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     }
     __syncthreads();   // the copy is read for the last time above
 
-    // 2. coefficients (thread 0) and the digits of S' (warps 1 ..)
-    if (tid == 0) {
-        const int m = cheb_coefs(cst, rho, TT_TOL, coef, status);
-        for (int k = 0; k <= m; ++k) coefd[k] = df_from(coef[k]);
-        nterms = m;
-    } else if (warp > 0) {
+    // 2. coefficients (warp 0) and the digits of S' (warps 1 ..)
+    if (warp == 0) {
+        const int m = tt_coefs_warp(cst, rho, TT_TOL, coefd, cshift, status);
+        if (lane == 0) nterms = m;
+    } else {
         const dfl cd = df_from(cst), ird = df_from(1.0 / rho);
         // unit u = (row r, 8 consecutive columns 8 uc .. 8 uc + 7)
         for (int u = tid - 32; u < 128 * 16; u += TT_THREADS - 32) {
