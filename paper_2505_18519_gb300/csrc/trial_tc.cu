@@ -271,7 +271,8 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     __shared__ float ired[2][4];
     __shared__ dfl coefd[CHEB_DF_MAX + 2];
     __shared__ int sexp[128];
-    __shared__ float redm[2][NW], reds[2][NW];
+    __shared__ __align__(16) float redm[2][NW];
+    __shared__ __align__(16) float reds[2][NW];
     __shared__ uint64_t mma_bar;
     __shared__ uint32_t tslot;
     __shared__ int nterms;
@@ -316,34 +317,44 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         if (lane == 0) nterms = m;
     } else {
         const dfl cd = df_from(cst), ird = df_from(1.0 / rho);
-        // unit u = (row r, 8 consecutive columns 8 uc .. 8 uc + 7)
-        for (int u = tid - 32; u < 128 * 16; u += TT_THREADS - 32) {
-            const int r = u >> 4, uc = u & 15;
-            const float sc_r = dg_p2f(sexp[r]);
-            uint16_t dg[TT_DIG][8];
+        // unit u = (row r, 8 consecutive columns 8 uc .. 8 uc + 7); two units per pass, both
+        // loaded before either is converted (the loads come from L2)
+        constexpr int US = TT_THREADS - 32;
+        for (int u0 = tid - 32; u0 < 128 * 16; u0 += 2 * US) {
+            dfl xs[2][8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int j = 8 * uc + t;
-                dfl x = {0.f, 0.f};
-                if (r < N && j < N) {
-                    x = s_is_df ? Sgd[(size_t)r * N + j] : df_from(Sg[(size_t)r * N + j]);
-                    if (j == r) x = df_add(x, df_neg(cd));
-                    x = df_mul(x, ird);
+            for (int h = 0; h < 2; ++h) {
+                const int u = u0 + h * US, r = u >> 4, uc = u & 15;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int j = 8 * uc + t;
+                    xs[h][t] = (u < 128 * 16 && r < N && j < N)
+                                   ? (s_is_df ? Sgd[(size_t)r * N + j] : df_from(Sg[(size_t)r * N + j]))
+                                   : dfl{0.f, 0.f};
                 }
-                uint16_t dd[TT_DIG];
-                dg_digits(x.hi * sc_r, x.lo * sc_r, dd);
-#pragma unroll
-                for (int q = 0; q < TT_DIG; ++q) dg[q][t] = dd[q];
             }
-            const uint32_t off = (uint32_t)(uc >> 3) * TT_SKB + dg_swz(r, (uc & 7) * 8);
 #pragma unroll
-            for (int q = 0; q < TT_DIG; ++q) {
-                uint4 v;
-                v.x = (uint32_t)dg[q][0] | ((uint32_t)dg[q][1] << 16);
-                v.y = (uint32_t)dg[q][2] | ((uint32_t)dg[q][3] << 16);
-                v.z = (uint32_t)dg[q][4] | ((uint32_t)dg[q][5] << 16);
-                v.w = (uint32_t)dg[q][6] | ((uint32_t)dg[q][7] << 16);
-                *reinterpret_cast<uint4*>(SD + (size_t)q * TT_SDIG + off) = v;
+            for (int h = 0; h < 2; ++h) {
+                const int u = u0 + h * US, r = u >> 4, uc = u & 15;
+                if (u >= 128 * 16) break;
+                const float sc_r = dg_p2f(sexp[r]);
+                uint16_t dg[TT_DIG][8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int j = 8 * uc + t;
+                    dfl x = xs[h][t];
+                    if (r < N && j < N) {
+                        if (j == r) x = df_add(x, df_neg(cd));
+                        x = df_mul(x, ird);
+                    }
+                    uint16_t dd[TT_DIG];
+                    dg_digits(x.hi * sc_r, x.lo * sc_r, dd);
+#pragma unroll
+                    for (int q = 0; q < TT_DIG; ++q) dg[q][t] = dd[q];
+                }
+                const uint32_t off = (uint32_t)(uc >> 3) * TT_SKB + dg_swz(r, (uc & 7) * 8);
+#pragma unroll
+                for (int q = 0; q < TT_DIG; ++q) *reinterpret_cast<uint4*>(SD + (size_t)q * TT_SDIG + off) = dg_pack8(dg[q]);
             }
         }
     }
@@ -374,9 +385,11 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         m = 0.f;
         s = 0.f;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            m = fmaxf(m, redm[p][w]);
-            s += reds[p][w];
+        for (int w = 0; w < NW; w += 4) {
+            const float4 a = *reinterpret_cast<const float4*>(&redm[p][w]);
+            const float4 b = *reinterpret_cast<const float4*>(&reds[p][w]);
+            m = fmaxf(m, fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w)));
+            s += (b.x + b.y) + (b.z + b.w);
         }
     };
     // digits of V (scaled by 2^f) into VD: digit q of element (row, a) at row q NB + a,
@@ -461,8 +474,10 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
                 const int c = CH * ch + t;
                 const dfl z = dg_combine6(A[0][t], A[1][t], A[2][t], A[3][t], A[4][t], A[5][t]);
                 const dfl u = {z.hi * sc_row, z.lo * sc_row};
-                const dfl vn = k == 1 ? u : df_add(dfl{2.f * u.hi, 2.f * u.lo}, df_neg(V0[c]));
-                acc[c] = df_add(acc[c], df_mul(ck, vn));
+                // the recurrence and the sum with the one-two-sum addition: its 2^-44 of the
+                // larger operand stays below the digit products' 2^-39
+                const dfl vn = k == 1 ? u : df_add_fast(dfl{2.f * u.hi, 2.f * u.lo}, df_neg(V0[c]));
+                acc[c] = df_add_fast(acc[c], df_mul(ck, vn));
                 V0[c] = V1[c];
                 V1[c] = vn;
                 mx = fmaxf(mx, fabsf(vn.hi));
