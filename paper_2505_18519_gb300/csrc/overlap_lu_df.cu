@@ -5,7 +5,8 @@
 // (Eq. (25)), and B_p = Phi_p A_p^-T for the walker-side contraction.  The same
 // steps as overlap_lu_kernel in FP64: partial pivoting on the largest |Re| + |Im|
 // (lowest row on ties), log det A = sum log|u_kk| + i Arg(prod u_kk (-1)^swaps)
-// with the product of the pivots carried in FP64 as z 2^zexp, A^-1 by forward and
+// with the product of the pivots carried as z 2^zexp (z in double-float, the log and
+// the argument taken once in FP64), A^-1 by forward and
 // back substitution, one column per lane.  On GB300 the FP64 pipe runs at 1/64 of
 // the FP32 rate, so about 60 FP32 operations per complex double-float
 // multiply-subtract still come out several times faster than 4 FP64 FMAs.
@@ -119,7 +120,7 @@ __global__ void overlap_lu_df_kernel(int N, int nu, int nt, int n, int col0, int
         give_up(cmk(qnan, qnan), STATUS_NONFINITE);
         return;
     }
-    double2 z = cmk(1.0, 0.0);   // product of the pivots, z 2^zexp
+    cdf z = {{1.f, 0.f}, {0.f, 0.f}};   // product of the pivots, z 2^zexp (double-float)
     int zexp = 0;
     bool odd = false, singular = false;
     for (int k = 0; k < n; ++k) {
@@ -154,13 +155,12 @@ __global__ void overlap_lu_df_kernel(int N, int nu, int nt, int n, int col0, int
         const dfl id = df_recip(den);
         const cdf rinv = {df_mul(piv.re, id), df_neg(df_mul(piv.im, id))};
         if (lane == 0) dinv[k] = cdf_store(rinv);
-        z = cmul(z, cmk(df_to(piv.re), df_to(piv.im)));
+        z = cdf_mul(z, piv);
         {
-            const double mz = fmax(fabs(z.x), fabs(z.y));
-            int ex = (int)((__double_as_longlong(mz) >> 52) & 0x7FF) - 1023;
-            ex = max(-1000, min(1000, ex));
-            const double f = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex, exact
-            z = cmk(z.x * f, z.y * f);
+            const float mz = fmaxf(fabsf(z.re.hi), fabsf(z.im.hi));
+            const int ex = mz > 0.f ? max(-100, min(100, ilogbf(mz))) : 0;
+            const float f = __int_as_float((127 - ex) << 23);                   // 2^-ex, exact
+            z = {{z.re.hi * f, z.re.lo * f}, {z.im.hi * f, z.im.lo * f}};
             zexp += ex;
         }
         for (int r = k + 1 + lane; r < n; r += 32) A[r * n + k] = cdf_store(cdf_mul(cdf_load(A[r * n + k]), rinv));
@@ -177,8 +177,9 @@ __global__ void overlap_lu_df_kernel(int N, int nu, int nt, int n, int col0, int
         return;
     }
     if (lane == 0) {
-        const double logabs = 0.5 * log(fma(z.x, z.x, z.y * z.y)) + zexp * 0.69314718055994530942;
-        logdet[pair * 2 + spin] = odd ? cmk(logabs, atan2(-z.y, -z.x)) : cmk(logabs, atan2(z.y, z.x));
+        const double zx = df_to(z.re), zy = df_to(z.im);
+        const double logabs = 0.5 * log(fma(zx, zx, zy * zy)) + zexp * 0.69314718055994530942;
+        logdet[pair * 2 + spin] = odd ? cmk(logabs, atan2(-zy, -zx)) : cmk(logabs, atan2(zy, zx));
     }
     if (!with_b) return;
     // A^-1 column c: solve L y = P e_c (unit lower), then U x = y
