@@ -547,6 +547,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             ctx.autotune()
             ctxs.append(ctx)
         b = lib.Batch(ctxs, stream=torch.cuda.Stream(dev))
+        shared = b.shared_contractions
         b.step(warmup)
         b.sync()
         ms, clocks, launches = _timed(b.step, b.sync, b.stream, steps, world, local)
@@ -566,6 +567,9 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             "refined_pairs_per_step": refined, "refined_frac": refined / (len(specs) * Wb * Pb),
             "refine_tol_ha": 1e-4,
             "tensor_core_forms": sorted({lib.contract_kernel(c.cfg) for c in ctxs}),
+            "shared_contractions": shared,
+            "shared_note": "systems whose GEMM-Z runs in the batch's one persistent launch (both spins' Y images "
+                           "must fit one chunk of walkers: the smaller systems)",
             "device_status_words": [int(st["status"]) for st in stats],
             "status_bits": "1 singular overlap, 2 non-finite value (the walker is removed), 4 tensor-core wait timed out"}
 
@@ -1007,7 +1011,8 @@ def our_arm(args):
         "dtype": HEADLINE_PATH["precision"] + " contraction (operands split into " +
                  ("three" if HEADLINE_PATH["precision"] == "fp16x6" else "two") + " FP16 parts on the tensor cores, "
                  "FP32 accumulation) + double-float refinement; trial orbitals as exact 8-bit digit products on the "
-                 "tensor cores (about 40 bits); f64 overlaps, LU, weights, energy sums",
+                 "tensor cores (about 40 bits); overlap matrices and proposal matrices as exact 8-bit digit "
+                 "products (about 40 bits), LU and inverses in double-float; f64 weights, energy sums",
         "data": "synthetic",
         "config": {"workload": workload_desc(spec, run), "walkers_total": W * world, "paths": P,
                    "system_seed": spec.seed, "philox_seed": seed, "path": dict(HEADLINE_PATH),
