@@ -717,10 +717,30 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
             prof = ctx.profile_read()
             st4 = ctx.stats()
             hist = ctx.history(2)
+            state4 = ctx.save_state()
             ctx.close()
             del ctx
             torch.cuda.empty_cache()
             ph = {k: round(v / max(1, prof["steps"]), 3) for k, v in prof["ms"].items()}
+            try:   # the mixed and the FP64 paths from the saved state, on 16 of the walkers (256 pairs)
+                Ws = 16
+                st = lib.unpack_state(state4)
+                sub = dict(step=st["step"], phi_up=st["phi_up"][:Ws], phi_dn=st["phi_dn"][:Ws], weight=st["weight"][:Ws],
+                           x=st["x"][:Ws], Phi=st["Phi"][:Ws])
+                cm = lib.make_config(spec4.N, spec4.n_up, spec4.n_dn, spec4.n_chol, spec4.K, Ws, P4, run4.dtau,
+                                     ai.philox_run_seed(4), n_burn=0, walker_offset=rank * W4,
+                                     **mixed_path(lib, spec4, Ws, P4))
+                cmx = lib.Context(cm, sy.h, sy.L, sy.Phi0, sy.U, device=dev)
+                cmx.load_state_arrays(sub)
+                ew4 = cmx.energy(walkers=True)["e_walker"]
+                cmx.close()
+                fp4 = fp64_sample_leg(lib, sy, spec4, run4, ai.philox_run_seed(4), rank, W4, dev, state4, ew4, local,
+                                      world, n_walk=Ws)
+                fp4["speedup"] = fp4["full_workload_ms_per_step_extrapolated"] / (ms / 2)
+                fp4["state"] = ("the mixed run's state after its timed steps; both paths measured from it in fresh "
+                                "contexts; walkers with zero weight (removed for non-finite values) excluded")
+            except Exception as exc:
+                fp4 = {"error": f"{type(exc).__name__}: {exc}"}
             flops = contract_flops_per_pair(spec4) * W4 * P4
             out["largest_mixed_learned"] = {
                 "precision": mixed_path(lib, spec4, W4, P4)["precision"], "proposal": "mlp (trained online)",
@@ -733,6 +753,7 @@ def run_variants(args, lib, s, spec, run, seed, rank, world, dev, ew64, hist64, 
                 "refined_frac": (st4["refined_pairs"] - r0) / (2 * W4 * P4),
                 "live_walkers": int(st4["live_walkers"]), "device_status": int(st4["status"]),
                 "tensor_contraction_tflops": flops / (ph["contract"] / 1e3) / 1e12 if ph["contract"] > 0 else None,
+                "vs_fp64_same_state": fp4,
                 "phases_ms_per_step": ph}
         except Exception as exc:   # the measurement is optional; the line must still print
             out["largest_mixed_learned"] = {"error": f"{type(exc).__name__}: {exc}"}
