@@ -330,19 +330,34 @@ __global__ void __launch_bounds__(256) propagate_df_kernel(int N, int nt, int or
         V[e] = df_pack(df_from(v.x), df_from(v.y));
     }
     __syncthreads();
+    // Every product below: a thread takes row i and the four columns c = cg + k NG
+    // (k < 4, NG = ceil(nt / 4); consecutive threads, consecutive columns), so that each
+    // load of a matrix entry serves four sums; every sum runs over j in order as before.
+    const int NG = (nt + 3) / 4;
     // acc <- E phi
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-        const int i = e / nt, c = e - i * nt;
-        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int it = threadIdx.x; it < N * NG; it += blockDim.x) {
+        const int i = it / NG, cg = it - i * NG;
+        float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rh[k] = rl[k] = ih[k] = il[k] = 0.f;
         for (int j = 0; j < N; ++j) {
             const dfl ev = E[(long long)i * N + j];
-            const float4 v = V[j * nt + c];
-            dot2_fma(rh, rl, ev, dfl{v.x, v.y});
-            dot2_fma(ih, il, ev, dfl{v.z, v.w});
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = min(cg + k * NG, nt - 1);
+                const float4 v = V[j * nt + c];
+                dot2_fma(rh[k], rl[k], ev, dfl{v.x, v.y});
+                dot2_fma(ih[k], il[k], ev, dfl{v.z, v.w});
+            }
         }
-        const dfl re = df_two_sum(rh, rl), im = df_two_sum(ih, il);
-        Wt[e] = df_pack(re, im);
-        acc[e] = make_double2(df_to(re), df_to(im));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = cg + k * NG;
+            if (c >= nt) continue;
+            const dfl re = df_two_sum(rh[k], rl[k]), im = df_two_sum(ih[k], il[k]);
+            Wt[i * nt + c] = df_pack(re, im);
+            acc[i * nt + c] = make_double2(df_to(re), df_to(im));
+        }
     }
     __syncthreads();
     float4* cur = Wt;
@@ -350,23 +365,35 @@ __global__ void __launch_bounds__(256) propagate_df_kernel(int N, int nt, int or
     const double st = sqrt(dtau);
     for (int m = 1; m <= order; ++m) {
         const dfl scale = df_from(st / m);
-        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-            const int i = e / nt, c = e - i * nt;
+        for (int it = threadIdx.x; it < N * NG; it += blockDim.x) {
+            const int i = it / NG, cg = it - i * NG;
             // A V = (-st Q + i st P) V: Re = -(Q Re V) - (P Im V), Im = (P Re V) - (Q Im V)
-            float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+            float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) rh[k] = rl[k] = ih[k] = il[k] = 0.f;
             for (int j = 0; j < N; ++j) {
                 const dfl pv = Pm[(long long)i * N + j], qv = Qm[(long long)i * N + j];
-                const float4 v = cur[j * nt + c];
-                const dfl vr{v.x, v.y}, vi{v.z, v.w};
-                dot2_fma(rh, rl, df_neg(qv), vr);
-                dot2_fma(rh, rl, df_neg(pv), vi);
-                dot2_fma(ih, il, pv, vr);
-                dot2_fma(ih, il, df_neg(qv), vi);
+                const dfl npv = df_neg(pv), nqv = df_neg(qv);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int c = min(cg + k * NG, nt - 1);
+                    const float4 v = cur[j * nt + c];
+                    const dfl vr{v.x, v.y}, vi{v.z, v.w};
+                    dot2_fma(rh[k], rl[k], nqv, vr);
+                    dot2_fma(rh[k], rl[k], npv, vi);
+                    dot2_fma(ih[k], il[k], pv, vr);
+                    dot2_fma(ih[k], il[k], nqv, vi);
+                }
             }
-            const dfl re = df_mul(df_two_sum(rh, rl), scale), im = df_mul(df_two_sum(ih, il), scale);
-            nxt[e] = df_pack(re, im);
-            const double2 a = acc[e];
-            acc[e] = make_double2(a.x + df_to(re), a.y + df_to(im));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = cg + k * NG;
+                if (c >= nt) continue;
+                const dfl re = df_mul(df_two_sum(rh[k], rl[k]), scale), im = df_mul(df_two_sum(ih[k], il[k]), scale);
+                nxt[i * nt + c] = df_pack(re, im);
+                const double2 a = acc[i * nt + c];
+                acc[i * nt + c] = make_double2(a.x + df_to(re), a.y + df_to(im));
+            }
         }
         __syncthreads();   // every read of cur is done before it is overwritten as nxt
         float4* t = cur; cur = nxt; nxt = t;
@@ -377,16 +404,27 @@ __global__ void __launch_bounds__(256) propagate_df_kernel(int N, int nt, int or
     }
     __syncthreads();
     // phi' <- E acc
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-        const int i = e / nt, c = e - i * nt;
-        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int it = threadIdx.x; it < N * NG; it += blockDim.x) {
+        const int i = it / NG, cg = it - i * NG;
+        float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rh[k] = rl[k] = ih[k] = il[k] = 0.f;
         for (int j = 0; j < N; ++j) {
             const dfl ev = E[(long long)i * N + j];
-            const float4 v = V[j * nt + c];
-            dot2_fma(rh, rl, ev, dfl{v.x, v.y});
-            dot2_fma(ih, il, ev, dfl{v.z, v.w});
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = min(cg + k * NG, nt - 1);
+                const float4 v = V[j * nt + c];
+                dot2_fma(rh[k], rl[k], ev, dfl{v.x, v.y});
+                dot2_fma(ih[k], il[k], ev, dfl{v.z, v.w});
+            }
         }
-        acc[e] = make_double2(df_to(df_two_sum(rh, rl)), df_to(df_two_sum(ih, il)));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = cg + k * NG;
+            if (c >= nt) continue;
+            acc[i * nt + c] = make_double2(df_to(df_two_sum(rh[k], rl[k])), df_to(df_two_sum(ih[k], il[k])));
+        }
     }
 }
 
