@@ -149,10 +149,26 @@ __global__ void __launch_bounds__(CT, (DF && OWN > 8) ? 1 : 2) contract_fp64_ker
         }
         for (int j0 = 0; j0 < N; j0 += JB) {
             int jb = min(JB, N - j0);
-            for (int e = tid; e < N * jb; e += CT) {
-                int i = e / jb, j = e - i * jb;
-                if constexpr (DF) sLD[i * JB + j] = LgD[(long long)i * N + j0 + j];
-                else sL[i * JB + j] = Lg[(long long)i * N + j0 + j];
+            if constexpr (DF) {   // four loads in flight per thread before their stores
+                const int ne = N * jb;
+                for (int e0 = tid; e0 < ne; e0 += 4 * CT) {
+                    dfl v[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int e = min(e0 + k * CT, ne - 1), i = e / jb;
+                        v[k] = LgD[(long long)i * N + j0 + (e - i * jb)];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int e = e0 + k * CT, i = e / jb;
+                        if (e < ne) sLD[i * JB + (e - i * jb)] = v[k];
+                    }
+                }
+            } else {
+                for (int e = tid; e < N * jb; e += CT) {
+                    int i = e / jb, j = e - i * jb;
+                    sL[i * JB + j] = Lg[(long long)i * N + j0 + j];
+                }
             }
             if (SLAB)   // rows j0 .. j0 + jb - 1 of Theta, contiguous in global memory
                 for (int e = tid; e < jb * nt; e += CT) {
@@ -160,34 +176,64 @@ __global__ void __launch_bounds__(CT, (DF && OWN > 8) ? 1 : 2) contract_fp64_ker
                     else sTh[e] = gTh[(size_t)j0 * nt + e];
                 }
             __syncthreads();
-            for (int e = tid; e < nu * jb; e += CT) {
-                int a = e / jb, j = e - a * jb;
-                if constexpr (DF) {
-                    float sh = 0.f, sl = 0.f;
-                    for (int i = 0; i < N; ++i) dot2_fma(sh, sl, sPhiD[i * nu + a], sLD[i * JB + j]);
-                    sRD[a * JB + j] = df_two_sum(sh, sl);
-                } else {
+            if constexpr (DF) {
+                // a thread takes row a and the four columns j = jq + k JQ (k < 4, JQ = ceil(jb / 4)):
+                // four independent Dot2 chains, each in the order of i as for one column
+                const int JQ = (jb + 3) >> 2;
+                for (int e = tid; e < nu * JQ; e += CT) {
+                    const int a = e / JQ, jq = e - a * JQ;
+                    int jc[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) jc[k] = min(jq + k * JQ, jb - 1);
+                    float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int i = 0; i < N; ++i) {
+                        const dfl pv = sPhiD[i * nu + a];
+                        const dfl* Li = sLD + i * JB;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) dot2_fma(sh[k], sl[k], pv, Li[jc[k]]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (jq + k * JQ < jb) sRD[a * JB + jq + k * JQ] = df_two_sum(sh[k], sl[k]);
+                }
+            } else {
+                for (int e = tid; e < nu * jb; e += CT) {
+                    int a = e / jb, j = e - a * jb;
                     double s = 0.0;
                     for (int i = 0; i < N; ++i) s = fma(sPhi[i * nu + a], sL[i * JB + j], s);
                     sR[a * JB + j] = s;
                 }
             }
             __syncthreads();
+            if constexpr (DF) {
+                // two owned entries at a time: four independent Dot2 chains over j (an odd last
+                // entry runs beside a copy of itself whose sums are dropped)
+                static_assert(OWN % 2 == 0, "entries are taken in pairs");
+                const float4* Tb = sThD + (SLAB ? 0 : (size_t)j0 * nt);
 #pragma unroll
-            for (int r = 0; r < OWN; ++r) {
-                if (r >= nown) break;
-                if constexpr (DF) {
-                    const dfl* Ra = sRD + own_a[r] * JB;
-                    const float4* Tc = sThD + (SLAB ? 0 : (size_t)j0 * nt) + own_c[r];
-                    float4 s = accd[r];
+                for (int r = 0; r < OWN; r += 2) {
+                    if (r >= nown) break;
+                    const bool two = r + 1 < nown;
+                    const dfl* Ra0 = sRD + own_a[r] * JB;
+                    const dfl* Ra1 = sRD + (two ? own_a[r + 1] : own_a[r]) * JB;
+                    const float4* Tc0 = Tb + own_c[r];
+                    const float4* Tc1 = Tb + (two ? own_c[r + 1] : own_c[r]);
+                    float4 s0 = accd[r], s1 = two ? accd[r + 1] : accd[r];
                     for (int j = 0; j < jb; ++j) {
-                        const dfl rv = Ra[j];
-                        const float4 t = Tc[(size_t)j * nt];
-                        dot2_fma(s.x, s.y, rv, dfl{t.x, t.y});
-                        dot2_fma(s.z, s.w, rv, dfl{t.z, t.w});
+                        const dfl rv0 = Ra0[j], rv1 = Ra1[j];
+                        const float4 t0 = Tc0[(size_t)j * nt], t1 = Tc1[(size_t)j * nt];
+                        dot2_fma(s0.x, s0.y, rv0, dfl{t0.x, t0.y});
+                        dot2_fma(s0.z, s0.w, rv0, dfl{t0.z, t0.w});
+                        dot2_fma(s1.x, s1.y, rv1, dfl{t1.x, t1.y});
+                        dot2_fma(s1.z, s1.w, rv1, dfl{t1.z, t1.w});
                     }
-                    accd[r] = s;
-                } else {
+                    accd[r] = s0;
+                    if (two) accd[r + 1] = s1;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < OWN; ++r) {
+                    if (r >= nown) break;
                     const double* Ra = sR + own_a[r] * JB;
                     const double2* Tc = sTh + (SLAB ? 0 : (size_t)j0 * nt) + own_c[r];
                     double2 s = acc[r];
@@ -476,6 +522,15 @@ static size_t contract_fp64_slab_smem(int N, int nu, int nd, int JB) {
 
 int contract_fp64_jb(int N) { return N <= 64 ? N : 32; }
 
+// The double-float form takes 40 columns per block where two blocks per SM still
+// fit (N = 120 then splits into three full blocks, and a thread's four R chains
+// keep 240 of the 256 threads busy at n_up = 24).
+static int contract_fp64_df_jb(int N, int nu, int nd) {
+    const int jb = contract_fp64_jb(N);
+    if (jb < 40 && N >= 40 && contract_fp64_slab_smem(N, nu, nd, 40) <= 110 * 1024) return 40;
+    return jb;
+}
+
 bool contract_fp64_supported(int N, int nu, int nd) {
     if (nu * nu + nd * nd > MAXOWN * CT) return false;
     const int JB = contract_fp64_jb(N);
@@ -537,7 +592,7 @@ static cudaError_t launch_fp64(cudaStream_t s, const Dims& d, const double* h, c
     if (DF && (!hdf || !Ldf || !items)) return cudaErrorInvalidValue;
     if (!contract_fp64_supported(d.N, d.nu, d.nd)) return cudaErrorInvalidValue;
     if (blocks <= 0) return cudaSuccess;
-    const int JB = contract_fp64_jb(d.N);
+    const int JB = DF ? contract_fp64_df_jb(d.N, d.nu, d.nd) : contract_fp64_jb(d.N);
     if (DF) {   // always the slab layout (half the shared memory); Theta converted first
         theta_to_df_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, s>>>(
             d.N * d.nt, items, n_items, const_cast<double2*>(Theta));
