@@ -55,6 +55,11 @@ UNIT = "walker-sample steps/s"
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 4 FP64 flop/clk
 # (2 DFMA) x 2070 MHz.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+# Double-float multiply-add peak from unit counts and clock: 152 SMs x 128 FP32
+# lanes x 2070 MHz instructions, 12 FP32 instructions per double-float
+# multiply-add (Dot2 step: a product with its error in 4, the compensated sum in 8),
+# 2 flops each.
+DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 L2_BYTES = 129e6
 
 
@@ -997,7 +1002,10 @@ def our_arm(args):
                "ms_per_launch": r_ms, "pairs_per_launch": refined_per_step,
                "refined_frac": refined_per_step / (W * P),
                "achieved": rf_flops / (r_ms / 1e3) / 1e12 if r_ms > 0 else None, "unit": "TFLOP/s (double-float)",
-               "peak": None, "frac": None, "traffic": None,
+               "peak": DF_PEAK_TFLOPS,
+               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz, 12 FP32 instructions per double-float "
+                              "multiply-add",
+               "frac": rf_flops / (r_ms / 1e3) / 1e12 / DF_PEAK_TFLOPS if r_ms > 0 else None, "traffic": None,
                "note": "recomputes in double-float (about 44 bits) the pairs whose estimated tensor-core error would "
                        "put their walker above refine_tol; CUDA-core FP32 pipe"}
     dominant = roof_tc if c_ms >= r_ms else dict(roof_rf, tensor_contraction=roof_tc)
